@@ -1,0 +1,247 @@
+/*
+ * grpic.h -- C ABI of the GB300 (sm_103a) library for the per-step hot path of
+ * the 2D-axisymmetric general-relativistic particle-in-cell method of
+ * arXiv:2511.17701 (Entity, GR module): GR pusher -> charge-conserving current
+ * deposit -> GR Maxwell update of D and B through the auxiliary E and H.
+ *
+ * Conventions common to every entry point
+ *  - Errors are returned as grpic_status; grpic_last_error() gives a one-line
+ *    message. Nothing traps, aborts or throws.
+ *  - All work is queued on the stream given to grpic_bind() and is asynchronous,
+ *    except where an entry point says it synchronises.
+ *  - Device memory: the library allocates none. The caller allocates one arena of
+ *    grpic_arena_bytes() bytes (any allocator: cudaMalloc, a torch tensor, ...),
+ *    passes it to grpic_bind() and keeps it alive until grpic_destroy(). The
+ *    library carves every table, field plane, particle array and scratch buffer
+ *    out of it. Host memory for the context itself comes from malloc.
+ *  - A context is not thread safe; use one per host thread and stream.
+ *  - Calling an entry point before its prerequisites (bind, init_metric,
+ *    init_fields, particles) returns GRPIC_ESTATE.
+ *
+ * Field storage (same convention as the CPU oracle, so planes compare element by
+ * element): every plane is a row-major [NY][NX] array of doubles,
+ * NX = n_r + 2*GRPIC_GHOSTS + 1, NY = n_theta + 2*GRPIC_GHOSTS + 1; the grid
+ * point x1 = i or i+1/2, x2 = j or j+1/2 is stored at [j + G][i + G] (a half
+ * integer position is stored at its lower integer). Yee locations (Fig. 1 of the
+ * paper): B^1 (i, j+1/2), B^2 (i+1/2, j), B^3 (i+1/2, j+1/2), D^1 (i+1/2, j),
+ * D^2 (i, j+1/2), D^3 (i, j); currents as D.
+ */
+#ifndef GRPIC_H
+#define GRPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GRPIC_API __attribute__((visibility("default")))
+#else
+#define GRPIC_API
+#endif
+
+#define GRPIC_GHOSTS 2
+#define GRPIC_MAX_SPECIES 8
+
+typedef struct grpic_ctx grpic_ctx;
+
+typedef enum {
+  GRPIC_OK = 0,
+  GRPIC_EINVAL = 1,      /* bad argument or configuration                       */
+  GRPIC_ENOMEM = 2,      /* arena smaller than grpic_arena_bytes()              */
+  GRPIC_ECUDA = 3,       /* a CUDA call failed (message in grpic_last_error)    */
+  GRPIC_ESTATE = 4,      /* prerequisites missing                               */
+  GRPIC_ECAPACITY = 5,   /* more particles than the species capacity           */
+  GRPIC_ENONFINITE = 6   /* non-finite particle state was found (diagnostics)   */
+} grpic_status;
+
+typedef enum { GRPIC_METRIC_KS0 = 0, GRPIC_METRIC_KS = 1 } grpic_metric_kind;
+typedef enum { GRPIC_FP64 = 0 } grpic_precision;
+typedef enum {
+  GRPIC_FIELD_ZERO = 0,     /* all fields zero                                    */
+  GRPIC_FIELD_WALD = 1,     /* Wald vacuum field, Eq. (Wald), Sec. 4.1.2          */
+  GRPIC_FIELD_VERTICAL = 2, /* its zero-spin limit, A_phi = B0 r^2 sin^2(theta)/2 */
+  GRPIC_FIELD_USER = 3      /* caller wrote em (B, D); the library derives the rest */
+} grpic_field_kind;
+typedef enum { GRPIC_PREDICT = 0, GRPIC_ADVANCE = 1 } grpic_field_phase;
+
+/* field planes, in the order of the CPU oracle's planes */
+typedef enum {
+  GRPIC_B1 = 0, GRPIC_B2, GRPIC_B3, GRPIC_D1, GRPIC_D2, GRPIC_D3,        /* em  : B^{n-1/2}, D^n     */
+  GRPIC_B01, GRPIC_B02, GRPIC_B03, GRPIC_D01, GRPIC_D02, GRPIC_D03,      /* em0 : B^{n-3/2}, D^{n-1} */
+  GRPIC_J1, GRPIC_J2, GRPIC_J3,                                          /* cur : J^{n+1/2}          */
+  GRPIC_J01, GRPIC_J02, GRPIC_J03,                                       /* cur0: J^{n-1/2}          */
+  GRPIC_BN1, GRPIC_BN2, GRPIC_BN3,                                       /* B^n from PREDICT         */
+  GRPIC_BI1, GRPIC_BI2, GRPIC_BI3, GRPIC_DI1, GRPIC_DI2, GRPIC_DI3,      /* initial field            */
+  GRPIC_NPLANES
+} grpic_plane;
+
+/* Everything the paper makes a parameter of the step. */
+typedef struct {
+  int metric;          /* grpic_metric_kind: kerr_schild_0 (flat) or Kerr-Schild, App. A   */
+  double a;            /* black-hole spin, 0 <= a < 1 (ignored for KS0)                     */
+  int n_r, n_theta;    /* cells along x1 (radial) and x2 (polar), Sec. 3                    */
+  double r_min, r_max; /* x1 in [0, n_r] maps to r = r_min exp(x1 dxi), dxi = ln(r_max/r_min)/n_r
+                          (quasi-spherical map of App. A with r0 = 0, h0 = 0);
+                          x2 in [0, n_theta] maps to theta = x2 pi / n_theta                 */
+  double cfl;          /* used when dt <= 0: dt = cfl * min over cells of
+                          1 / (alpha sqrt(h^11 + h^22) + |beta^1|)                           */
+  double dt;           /* time step; > 0 overrides cfl                                       */
+  int n_iter;          /* fixed iteration count of both implicit geodesic pushes, Sec. 3.1   */
+  double small_angle;  /* SMALL_ANGLE_GR, Sec. 3.3.2 (1e-5)                                  */
+  int n_filter;        /* n_f, Sec. 3.3.3: fields in cells i1 <= n_f copy cell n_f + 1       */
+  double r_absorb;     /* absorbing (MATCH) layer for r > r_absorb, Sec. 3.3.3               */
+  double absorb_coef;  /* its strength                                                       */
+  int n_species;       /* 1 .. GRPIC_MAX_SPECIES                                             */
+  int64_t capacity[GRPIC_MAX_SPECIES]; /* particles per species the arena holds              */
+  int sort_every;      /* grpic_step sorts particles by cell every k steps (0: never)        */
+  int tile_r, tile_theta; /* sort tile, in cells                                             */
+  int precision;       /* grpic_precision                                                     */
+} grpic_config;
+
+/* Pointers to one species' particle arrays (SoA, length >= n). Positions are a cell
+ * index plus an offset in [0, 1] (Sec. 3: i1, dx1, i2, dx2); u are covariant code-unit
+ * momenta u_i; phi the out-of-plane angle (Eq. discretized-geodesic-x-phi); w the
+ * weight; tag 1 alive, 2 left the domain in the last push (its move is still
+ * deposited), 0 dead. i1p..dx2p is the previous position (Sec. 3.2). */
+typedef struct {
+  int32_t *i1, *i2;
+  double *dx1, *dx2, *u1, *u2, *u3, *phi, *w;
+  uint8_t *tag;
+  int32_t *i1p, *i2p;
+  double *dx1p, *dx2p;
+} grpic_particles;
+
+/* Initial particles for grpic_load_particles: position, momentum in the local
+ * orthonormal FIDO tetrad frame (App. A) and a base weight. */
+typedef struct {
+  const int32_t *i1, *i2;
+  const double *dx1, *dx2;
+  const double *uh1, *uh2, *uh3;
+  const double *w0;
+} grpic_particle_init;
+
+typedef struct {
+  int64_t left_inner;    /* particles removed through the horizon layer            */
+  int64_t left_outer;    /* particles removed through r = r_max                     */
+  int64_t reflections;   /* axis reflections, Sec. 3.3.3                           */
+  int64_t nonfinite;     /* particles dropped for non-finite or runaway state       */
+  int64_t alive[GRPIC_MAX_SPECIES];
+} grpic_diag;
+
+/* --- set-up ----------------------------------------------------------------------- */
+
+/* Validates cfg and creates a host context (no CUDA work). *out owns host memory
+ * only. Errors: GRPIC_EINVAL (bad sizes, spin, radii, species counts). */
+GRPIC_API grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out);
+
+/* Bytes of device memory the context needs (256-byte aligned sub-buffers). */
+GRPIC_API size_t grpic_arena_bytes(const grpic_ctx *ctx);
+
+/* Binds the caller-owned device arena (>= grpic_arena_bytes, 256-byte aligned)
+ * and the CUDA stream (cudaStream_t, NULL = legacy default) on the current device.
+ * Errors: GRPIC_ENOMEM (too small), GRPIC_EINVAL (misaligned). */
+GRPIC_API grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream);
+
+/* Tabulates the code-unit metric of App. A (alpha, h_ij, sqrt(h), sqrt(h~),
+ * [sqrt(h~) h_13], [sqrt(h~ h) beta^1], 1/sqrt(h)) at the four Yee point classes and
+ * the polar areas of Sec. 3.3.2, and fixes dt (cfl rule when cfg.dt <= 0).
+ * Synchronises the stream once (dt is read back). */
+GRPIC_API grpic_status grpic_init_metric(grpic_ctx *ctx);
+
+/* The time step in use (after grpic_init_metric). */
+GRPIC_API double grpic_dt(const grpic_ctx *ctx);
+
+/* Initial fields (Sec. 4.1.2, 4.2): B^1, B^2 from the discrete curl of A_3 at the nodes,
+ * B^3 from the discrete curl of A_1; D at each Yee point from the inverse of Eq. (aux)
+ * with E_i = d_i A_0. Then em0 = em (stationary start), cur0 = 0, and the initial field
+ * is kept as the absorbing-layer target. kind GRPIC_FIELD_USER keeps em as written by
+ * the caller and only does the copies and boundary fills. */
+GRPIC_API grpic_status grpic_init_fields(grpic_ctx *ctx, int kind, double B0);
+
+/* --- particles -------------------------------------------------------------------- */
+
+/* Loads n particles of a species from positions and tetrad-frame momenta: u_i =
+ * e_i^j u_j^ (App. A) at the particle, w = w0 r^{-density_power} sqrt(h)(x_p),
+ * phi = 0, tag = 1, previous position = position. qm is the Lorentz coefficient
+ * (q/m) per unit stored field; qc the deposit coefficient (sign of q included).
+ * Pointers may be host or device memory (copied with cudaMemcpyDefault).
+ * Errors: GRPIC_ECAPACITY when n > capacity. */
+GRPIC_API grpic_status grpic_load_particles(grpic_ctx *ctx, int species, int64_t n, double qm, double qc,
+                                  double density_power, const grpic_particle_init *in);
+
+/* Sets the full state of a species (every array of grpic_particles), host or device
+ * pointers. Used for restarts and to feed identical states to parity checks. */
+GRPIC_API grpic_status grpic_set_particles(grpic_ctx *ctx, int species, int64_t n, double qm, double qc,
+                                 const grpic_particles *in);
+
+/* Copies a species' state out into caller arrays (host or device), and its count. */
+GRPIC_API grpic_status grpic_get_particles(grpic_ctx *ctx, int species, grpic_particles *out,
+                                 int64_t *n);
+
+/* Device pointers of a species' arrays inside the arena (valid until the next sort). */
+GRPIC_API grpic_status grpic_species_arrays(grpic_ctx *ctx, int species, grpic_particles *out,
+                                  int64_t *n);
+
+/* Device pointer of a field plane inside the arena (valid until the next ADVANCE,
+ * which rotates em/em0 and cur/cur0). */
+GRPIC_API grpic_status grpic_plane_ptr(grpic_ctx *ctx, int plane, double **out);
+
+/* --- the hot path ---------------------------------------------------------------- */
+
+/* One particle push of a species, steps 1-11 of Sec. 3.1 with the boundaries of
+ * Sec. 3.3.3: saves x^n as the previous position, interpolates B^n (BN planes) and D^n,
+ * Boris in the tetrad frame for dt/2, implicit geodesic momentum push (Eq.
+ * discretized-geodesic-u), Boris for dt/2, implicit coordinate push (Eq.
+ * discretized-geodesic-x), axis reflection, removal, phi update. */
+GRPIC_API grpic_status grpic_push(grpic_ctx *ctx, int species);
+
+/* Conformal current deposit of all species from previous and new positions, Sec. 3.2,
+ * Eq. (charge-conservation-disc): zeroes J, then deposits J^{n+1/2}. */
+GRPIC_API grpic_status grpic_deposit(grpic_ctx *ctx);
+
+/* GRPIC_PREDICT: loop step 2 of Sec. 3.4 (B^{n-1}, D^{n-1/2}, E^{n-1/2}, auxiliary
+ * Faraday B^{n-1} -> B^n into the BN planes). GRPIC_ADVANCE: loop steps 5-8 (J^n, E^n,
+ * H^n, Faraday B^{n-1/2} -> B^{n+1/2}, auxiliary Ampere D^{n-1/2} -> D^{n+1/2},
+ * H^{n+1/2}, Ampere D^n -> D^{n+1}, boundaries, rotation of em0/em and cur0/cur). */
+GRPIC_API grpic_status grpic_field_step(grpic_ctx *ctx, int phase);
+
+/* Stable sort of a species by tile-major cell key; particles not alive go last and
+ * are dropped (the count shrinks). Integer work: the permutation is unique. */
+GRPIC_API grpic_status grpic_sort(grpic_ctx *ctx, int species);
+
+/* n_steps full PIC steps (Sec. 3.4): PREDICT, sort every cfg.sort_every steps, fused
+ * push + deposit of all species, ADVANCE. */
+GRPIC_API grpic_status grpic_step(grpic_ctx *ctx, int n_steps);
+
+/* --- diagnostics ------------------------------------------------------------------ */
+
+/* Per-phase device time of the hot path, measured with CUDA events recorded on the
+ * bound stream around each phase of grpic_step / grpic_push / grpic_deposit /
+ * grpic_field_step / grpic_sort while timing is enabled, and the number of kernels
+ * the library launched (process-wide). */
+typedef struct {
+  double predict_ms, sort_ms, push_ms, deposit_ms, advance_ms;
+  int64_t push_calls;   /* particle-kernel launches timed in push_ms                 */
+  int64_t launches;     /* kernels launched by the library since the last reset      */
+} grpic_timing;
+
+/* Enables (1) or disables (0) the per-phase events. Off by default. */
+GRPIC_API grpic_status grpic_set_timing(grpic_ctx *ctx, int enable);
+
+/* Sums the recorded phases and resets the sums and the launch counter.
+ * Synchronises the stream. */
+GRPIC_API grpic_status grpic_get_timing(grpic_ctx *ctx, grpic_timing *out);
+
+/* Counters accumulated since the last call, and live counts. Synchronises the stream. */
+GRPIC_API grpic_status grpic_get_diagnostics(grpic_ctx *ctx, grpic_diag *out);
+
+GRPIC_API const char *grpic_last_error(const grpic_ctx *ctx);
+GRPIC_API void grpic_destroy(grpic_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

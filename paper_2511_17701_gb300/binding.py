@@ -1,0 +1,312 @@
+"""ctypes binding of libgrpic (include/grpic.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels. PyTorch provides the
+device arena (one uint8 tensor) and the stream; views into the arena are torch
+tensors that alias the library's buffers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+GHOSTS = 2
+MAX_SPECIES = 8
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ECAPACITY, ENONFINITE = range(7)
+METRIC_KS0, METRIC_KS = 0, 1
+FIELD_ZERO, FIELD_WALD, FIELD_VERTICAL, FIELD_USER = range(4)
+PREDICT, ADVANCE = 0, 1
+(B1, B2, B3, D1, D2, D3, B01, B02, B03, D01, D02, D03, J1, J2, J3, J01, J02, J03,
+ BN1, BN2, BN3, BI1, BI2, BI3, DI1, DI2, DI3, NPLANES) = range(28)
+
+EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric", "grpic_dt",
+           "grpic_init_fields", "grpic_load_particles", "grpic_set_particles",
+           "grpic_get_particles", "grpic_species_arrays", "grpic_plane_ptr", "grpic_push",
+           "grpic_deposit", "grpic_field_step", "grpic_sort", "grpic_step",
+           "grpic_get_diagnostics", "grpic_set_timing", "grpic_get_timing", "grpic_last_error",
+           "grpic_destroy"]
+
+
+class GrpicError(RuntimeError):
+    pass
+
+
+class Config(C.Structure):
+    _fields_ = [("metric", C.c_int), ("a", C.c_double), ("n_r", C.c_int), ("n_theta", C.c_int),
+                ("r_min", C.c_double), ("r_max", C.c_double), ("cfl", C.c_double),
+                ("dt", C.c_double), ("n_iter", C.c_int), ("small_angle", C.c_double),
+                ("n_filter", C.c_int), ("r_absorb", C.c_double), ("absorb_coef", C.c_double),
+                ("n_species", C.c_int), ("capacity", C.c_int64 * MAX_SPECIES),
+                ("sort_every", C.c_int), ("tile_r", C.c_int), ("tile_theta", C.c_int),
+                ("precision", C.c_int)]
+
+
+_VP = C.c_void_p
+PARTICLE_ARRAYS = [("i1", np.int32), ("i2", np.int32), ("dx1", np.float64), ("dx2", np.float64),
+                   ("u1", np.float64), ("u2", np.float64), ("u3", np.float64),
+                   ("phi", np.float64), ("w", np.float64), ("tag", np.uint8),
+                   ("i1p", np.int32), ("i2p", np.int32), ("dx1p", np.float64),
+                   ("dx2p", np.float64)]
+
+
+class Particles(C.Structure):
+    _fields_ = [(k, _VP) for k, _ in PARTICLE_ARRAYS]
+
+
+class ParticleInit(C.Structure):
+    _fields_ = [(k, _VP) for k in ("i1", "i2", "dx1", "dx2", "uh1", "uh2", "uh3", "w0")]
+
+
+class Timing(C.Structure):
+    _fields_ = [("predict_ms", C.c_double), ("sort_ms", C.c_double), ("push_ms", C.c_double),
+                ("deposit_ms", C.c_double), ("advance_ms", C.c_double),
+                ("push_calls", C.c_int64), ("launches", C.c_int64)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("left_inner", C.c_int64), ("left_outer", C.c_int64),
+                ("reflections", C.c_int64), ("nonfinite", C.c_int64),
+                ("alive", C.c_int64 * MAX_SPECIES)]
+
+
+_lib = None
+
+
+def lib(build: bool = True):
+    """Load libgrpic.so (building it first when it is missing or stale). Raises if the
+    library cannot be built or loaded: there is no fallback."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise GrpicError("libgrpic.so not found at %s" % path)
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.grpic_create.argtypes = [C.POINTER(Config), C.POINTER(P)]
+        L.grpic_arena_bytes.argtypes = [P]
+        L.grpic_arena_bytes.restype = C.c_size_t
+        L.grpic_bind.argtypes = [P, P, C.c_size_t, P]
+        L.grpic_init_metric.argtypes = [P]
+        L.grpic_dt.argtypes = [P]
+        L.grpic_dt.restype = C.c_double
+        L.grpic_init_fields.argtypes = [P, C.c_int, C.c_double]
+        L.grpic_load_particles.argtypes = [P, C.c_int, C.c_int64, C.c_double, C.c_double,
+                                           C.c_double, C.POINTER(ParticleInit)]
+        L.grpic_set_particles.argtypes = [P, C.c_int, C.c_int64, C.c_double, C.c_double,
+                                          C.POINTER(Particles)]
+        L.grpic_get_particles.argtypes = [P, C.c_int, C.POINTER(Particles), C.POINTER(C.c_int64)]
+        L.grpic_species_arrays.argtypes = [P, C.c_int, C.POINTER(Particles), C.POINTER(C.c_int64)]
+        L.grpic_plane_ptr.argtypes = [P, C.c_int, C.POINTER(C.c_void_p)]
+        L.grpic_push.argtypes = [P, C.c_int]
+        L.grpic_deposit.argtypes = [P]
+        L.grpic_field_step.argtypes = [P, C.c_int]
+        L.grpic_sort.argtypes = [P, C.c_int]
+        L.grpic_step.argtypes = [P, C.c_int]
+        L.grpic_get_diagnostics.argtypes = [P, C.POINTER(Diag)]
+        L.grpic_set_timing.argtypes = [P, C.c_int]
+        L.grpic_get_timing.argtypes = [P, C.POINTER(Timing)]
+        L.grpic_last_error.argtypes = [P]
+        L.grpic_last_error.restype = C.c_char_p
+        L.grpic_destroy.argtypes = [P]
+        L.grpic_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def make_config(cfg: dict, capacities) -> Config:
+    c = Config()
+    c.metric = METRIC_KS if cfg.get("metric", "ks") == "ks" else METRIC_KS0
+    c.a = float(cfg.get("a", 0.0))
+    c.n_r, c.n_theta = int(cfg["n_r"]), int(cfg["n_theta"])
+    c.r_min, c.r_max = float(cfg["r_min"]), float(cfg["r_max"])
+    c.cfl = float(cfg.get("cfl", 0.5))
+    c.dt = float(cfg.get("dt", 0.0))
+    c.n_iter = int(cfg.get("n_iter", 10))
+    c.small_angle = float(cfg.get("small_angle", 1e-5))
+    c.n_filter = int(cfg.get("n_filter", 0))
+    c.r_absorb = float(cfg.get("r_absorb", 1e300))
+    c.absorb_coef = float(cfg.get("absorb_coef", 1.0))
+    c.n_species = len(capacities)
+    for i, n in enumerate(list(capacities)[:MAX_SPECIES]):
+        c.capacity[i] = int(n)
+    c.sort_every = int(cfg.get("sort_every", 0))
+    c.tile_r = int(cfg.get("tile_r", 16))
+    c.tile_theta = int(cfg.get("tile_theta", 16))
+    c.precision = 0
+    return c
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (host or device), or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class Sim:
+    """One simulation context bound to a torch-allocated arena on a CUDA device."""
+
+    def __init__(self, cfg: dict, capacities, device="cuda:0"):
+        import torch
+        self.torch = torch
+        self.cfg = dict(cfg)
+        self.L = lib()
+        self.ctx = C.c_void_p()
+        self._check(self.L.grpic_create(C.byref(make_config(cfg, capacities)),
+                                        C.byref(self.ctx)), "create")
+        self.nbytes = self.L.grpic_arena_bytes(self.ctx)
+        self.device = torch.device(device)
+        self.arena_t = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.arena_t.data_ptr()
+        self.off0 = (-base) % 256
+        self.stream = torch.cuda.current_stream(self.device)
+        self._check(self.L.grpic_bind(self.ctx, base + self.off0, self.nbytes,
+                                      self.stream.cuda_stream), "bind")
+        self.NX = int(cfg["n_r"]) + 2 * GHOSTS + 1
+        self.NY = int(cfg["n_theta"]) + 2 * GHOSTS + 1
+        self.n_species = len(capacities)
+        self.qm = [0.0] * self.n_species
+        self.qc = [0.0] * self.n_species
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = self.L.grpic_last_error(self.ctx) if self.ctx else b""
+            raise GrpicError("grpic %s failed (status %d): %s" % (what, st, (msg or b"").decode()))
+
+    def close(self):
+        if self.ctx:
+            self.L.grpic_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- set-up ---------------------------------------------------------------------
+    def init_metric(self):
+        self._check(self.L.grpic_init_metric(self.ctx), "init_metric")
+
+    @property
+    def dt(self) -> float:
+        return self.L.grpic_dt(self.ctx)
+
+    def init_fields(self, kind: int, B0: float = 1.0):
+        self._check(self.L.grpic_init_fields(self.ctx, kind, B0), "init_fields")
+
+    def load_particles(self, s, pos, uhat, w0, qm, qc, density_power=0.0):
+        keep = [np.ascontiguousarray(pos["i1"], np.int32), np.ascontiguousarray(pos["i2"], np.int32),
+                np.ascontiguousarray(pos["dx1"], np.float64), np.ascontiguousarray(pos["dx2"], np.float64),
+                np.ascontiguousarray(uhat[0], np.float64), np.ascontiguousarray(uhat[1], np.float64),
+                np.ascontiguousarray(uhat[2], np.float64), np.ascontiguousarray(w0, np.float64)]
+        pi = ParticleInit(*[_ptr(a) for a in keep])
+        n = keep[0].size
+        self._check(self.L.grpic_load_particles(self.ctx, s, n, qm, qc, density_power,
+                                                C.byref(pi)), "load_particles")
+        self.qm[s], self.qc[s] = qm, qc
+        self.sync()
+
+    def set_particles(self, s, arrays: dict, qm, qc):
+        """Full species state from host (numpy) or device (torch) arrays."""
+        keep = []
+        for k, t in PARTICLE_ARRAYS:
+            a = arrays[k]
+            if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
+                a = np.ascontiguousarray(a, dtype=t)
+            keep.append(a)
+        n = len(keep[0])
+        p = Particles(*[_ptr(a) for a in keep])
+        self._check(self.L.grpic_set_particles(self.ctx, s, n, qm, qc, C.byref(p)), "set_particles")
+        self.qm[s], self.qc[s] = qm, qc
+        self.sync()
+
+    def get_particles(self, s) -> dict:
+        """Copy of a species' state as numpy arrays (synchronises)."""
+        n = C.c_int64()
+        self._check(self.L.grpic_species_arrays(self.ctx, s, None, C.byref(n)), "species_arrays")
+        out = {k: np.empty(n.value, dtype=t) for k, t in PARTICLE_ARRAYS}
+        p = Particles(*[_ptr(out[k]) for k, _ in PARTICLE_ARRAYS])
+        self._check(self.L.grpic_get_particles(self.ctx, s, C.byref(p), C.byref(n)), "get_particles")
+        return out
+
+    def count(self, s) -> int:
+        n = C.c_int64()
+        self._check(self.L.grpic_species_arrays(self.ctx, s, None, C.byref(n)), "species_arrays")
+        return n.value
+
+    def species_views(self, s) -> dict:
+        """Torch views of a species' device arrays (valid until the next sort)."""
+        torch = self.torch
+        p, n = Particles(), C.c_int64()
+        self._check(self.L.grpic_species_arrays(self.ctx, s, C.byref(p), C.byref(n)), "species_arrays")
+        dt = {np.int32: torch.int32, np.float64: torch.float64, np.uint8: torch.uint8}
+        out = {}
+        base = self.arena_t.data_ptr()
+        for k, t in PARTICLE_ARRAYS:
+            off = getattr(p, k) - base
+            size = np.dtype(t).itemsize
+            out[k] = self.arena_t[off: off + n.value * size].view(dt[t])
+        return out
+
+    def plane(self, k):
+        """Torch view [NY, NX] of a field plane (valid until the next ADVANCE)."""
+        ptr = C.c_void_p()
+        self._check(self.L.grpic_plane_ptr(self.ctx, k, C.byref(ptr)), "plane_ptr")
+        off = ptr.value - self.arena_t.data_ptr()
+        nb = self.NX * self.NY * 8
+        return self.arena_t[off: off + nb].view(self.torch.float64).view(self.NY, self.NX)
+
+    def planes(self) -> np.ndarray:
+        """Host copy of all field planes, shape (NPLANES, NY, NX) (synchronises)."""
+        self.sync()
+        return np.stack([self.plane(k).cpu().numpy() for k in range(NPLANES)])
+
+    def set_planes(self, F: np.ndarray, which=range(NPLANES)):
+        for k in which:
+            self.plane(k).copy_(self.torch.from_numpy(np.ascontiguousarray(F[k])))
+        self.sync()
+
+    # --- hot path -------------------------------------------------------------------
+    def push(self, s):
+        self._check(self.L.grpic_push(self.ctx, s), "push")
+
+    def deposit(self):
+        self._check(self.L.grpic_deposit(self.ctx), "deposit")
+
+    def predict(self):
+        self._check(self.L.grpic_field_step(self.ctx, PREDICT), "field_step(PREDICT)")
+
+    def advance(self):
+        self._check(self.L.grpic_field_step(self.ctx, ADVANCE), "field_step(ADVANCE)")
+
+    def sort(self, s):
+        self._check(self.L.grpic_sort(self.ctx, s), "sort")
+
+    def step(self, n=1):
+        self._check(self.L.grpic_step(self.ctx, n), "step")
+
+    def diagnostics(self) -> dict:
+        d = Diag()
+        self._check(self.L.grpic_get_diagnostics(self.ctx, C.byref(d)), "get_diagnostics")
+        return {"left_inner": d.left_inner, "left_outer": d.left_outer,
+                "reflections": d.reflections, "nonfinite": d.nonfinite,
+                "alive": [d.alive[i] for i in range(self.n_species)]}
+
+    def set_timing(self, on: bool):
+        self._check(self.L.grpic_set_timing(self.ctx, int(bool(on))), "set_timing")
+
+    def timing(self) -> dict:
+        t = Timing()
+        self._check(self.L.grpic_get_timing(self.ctx, C.byref(t)), "get_timing")
+        return {k: getattr(t, k) for k, _ in Timing._fields_}
+
+    def sync(self):
+        self.stream.synchronize()

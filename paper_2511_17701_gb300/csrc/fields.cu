@@ -1,0 +1,541 @@
+// fields.cu -- metric tables, initial fields and the GR field solver of Sec. 3.3 of
+// arXiv:2511.17701 (Faraday, Ampere, auxiliary E and H with volume-weighted averages,
+// axis treatment, horizon layer and absorbing layer), plus the loop steps 2 and 5-8 of
+// Sec. 3.4. Grid work is a small fraction of a step at the particle counts this library
+// targets (tens of particles per cell): one thread per grid point, metric from tables.
+#include "grpic_internal.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+
+__device__ __forceinline__ double tabv(const double *tab, const GridP &g, int cls, int q, int i,
+                                       int j) {
+  return __ldg(tab + ((int64_t)(cls * T_NQ + q)) * plane_size(g) + sidx(g, i, j));
+}
+
+// ---------------------------------------------------------------------------------
+// Tables: per Yee class, alpha, h_11, h_22, h_33, sqrt(h~), [sqrt(h~) h_13],
+// [sqrt(h~ h) beta^1], 1/sqrt(h) at every stored point; the polar area
+// A(x1) = dr (r^2 + a^2) sqrt(1 + 2 M r/(r^2 + a^2)) (1 - cos(dtheta/2)) (App. A, per unit phi).
+// ---------------------------------------------------------------------------------
+__global__ void k_metric_tables(GridP g, double *tab, double *polar) {
+  const int64_t ps = plane_size(g);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 4 * ps;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int cls = (int)(t / ps);
+    const int64_t q = t - cls * ps;
+    const int i = (int)(q % g.NX) - G_, j = (int)(q / g.NX) - G_;
+    const double s1 = (cls == CLS_HN || cls == CLS_HH) ? 0.5 : 0.0;
+    const double s2 = (cls == CLS_NH || cls == CLS_HH) ? 0.5 : 0.0;
+    MetricV m;
+    metric_eval<false>(g, i + s1, j + s2, false, m, nullptr);
+    double *o = tab + (int64_t)cls * T_NQ * ps + q;
+    o[T_ALPHA * ps] = m.alpha;
+    o[T_H11 * ps] = m.h11;
+    o[T_H22 * ps] = m.h22;
+    o[T_H33 * ps] = m.h33;
+    o[T_SHT * ps] = m.sqrt_ht;
+    o[T_WT13 * ps] = m.sqrt_ht * m.h13;
+    o[T_WB1 * ps] = m.sqrt_ht * m.sqrt_h * m.beta1;
+    o[T_ISH * ps] = 1.0 / m.sqrt_h;
+    if (cls == CLS_HN && j == 0) {
+      const double r = g.r_min * exp((i + 0.5) * g.dxi), a2 = g.a * g.a;
+      polar[i + G_] = g.dxi * r * (r * r + a2) * sqrt(1.0 + 2.0 * g.M * r / (r * r + a2)) *
+                      (1.0 - cos(0.5 * g.dth));
+    }
+  }
+}
+
+// dt = cfl * min over cell centres of 1 / (alpha sqrt(h^11 + h^22) + |beta^1|); positive
+// doubles order like their bit patterns, so the minimum is an integer atomicMin.
+__global__ void k_dt_min(GridP g, unsigned long long *out) {
+  __shared__ unsigned long long sm[TPB];
+  unsigned long long best = 0x7FF0000000000000ull;  // +inf
+  const int64_t n = (int64_t)g.n_r * g.n_th;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % g.n_r), j = (int)(t / g.n_r);
+    MetricV m;
+    metric_eval<false>(g, i + 0.5, j + 0.5, false, m, nullptr);
+    const double v = 1.0 / (m.alpha * sqrt(m.H11 + m.H22) + fabs(m.beta1));
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    best = b < best ? b : best;
+  }
+  sm[threadIdx.x] = best;
+  __syncthreads();
+  for (int s = TPB / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s && sm[threadIdx.x + s] < sm[threadIdx.x]) sm[threadIdx.x] = sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMin(out, sm[0]);
+}
+
+// ---------------------------------------------------------------------------------
+// Stationary potentials: Wald (Eq. Wald) and its zero-spin limit, and their
+// derivatives in code coordinates, written from the physical (r, theta) closed forms.
+// ---------------------------------------------------------------------------------
+struct Pot {
+  double A0, A1, A3;              // A_0, A_1 (code), A_3
+  double d1A0, d2A0, d1A3, d2A1;  // the derivatives the fields need
+};
+
+__device__ void potential(const GridP &g, int kind, double B0, double x1, double x2, bool derivs,
+                          Pot &p) {
+  const double a = g.a, M = g.M, a2 = a * a;
+  const double r = g.r_min * exp(x1 * g.dxi), th = x2 * g.dth;
+  double s, c;
+  sincos(th, &s, &c);
+  const double s2 = s * s, f = g.dxi * r, gg = g.dth;
+  if (kind == GRPIC_FIELD_VERTICAL) {
+    p.A0 = 0.0; p.A1 = 0.0; p.A3 = 0.5 * B0 * r * r * s2;
+    p.d1A0 = p.d2A0 = p.d2A1 = 0.0;
+    p.d1A3 = f * B0 * r * s2;
+    return;
+  }
+  const double Sig = r * r + a2 * c * c, Del = r * r - 2.0 * M * r + a2;
+  const double A = (r * r + a2) * (r * r + a2) - a2 * Del * s2;
+  const double z = 2.0 * M * r / Sig;
+  // physical Wald potential: A_t = (B0 a / 2)(z (2 - s^2) - 2), A_r = (B0 a / 2)(2 z - (1+z) s^2),
+  // A_phi = (B0 / 2)(A s^2 / Sigma - 2 a^2 z s^2)
+  const double hb = 0.5 * B0;
+  p.A0 = hb * a * (z * (2.0 - s2) - 2.0);
+  p.A1 = f * hb * a * (2.0 * z - (1.0 + z) * s2);
+  p.A3 = hb * (A * s2 / Sig - 2.0 * a2 * z * s2);
+  if (!derivs) return;
+  const double drS = 2.0 * r, dtS = -2.0 * a2 * s * c;
+  const double drz = 2.0 * M * (Sig - r * drS) / (Sig * Sig);
+  const double dtz = -2.0 * M * r * dtS / (Sig * Sig);
+  const double drA = 4.0 * r * (r * r + a2) - a2 * s2 * (2.0 * r - 2.0 * M);
+  const double dts2 = 2.0 * s * c;
+  p.d1A0 = f * hb * a * drz * (2.0 - s2);
+  p.d2A0 = gg * hb * a * (dtz * (2.0 - s2) - z * dts2);
+  p.d1A3 = f * hb * (s2 * (drA * Sig - A * drS) / (Sig * Sig) - 2.0 * a2 * s2 * drz);
+  p.d2A1 = gg * f * hb * a * (2.0 * dtz - dtz * s2 - (1.0 + z) * dts2);
+}
+
+// D at a Yee point from the inverse of Eq. (aux) with E_i = d_i A_0, E_3 = 0 and
+// sqrt(h) B^2 = -d_1 A_3, sqrt(h) B^3 = -d_2 A_1 (no division by sqrt(h) on the axis).
+__device__ void d_from_potential(const GridP &g, int kind, double B0, double x1, double x2,
+                                 int comp, double &out) {
+  Pot p;
+  potential(g, kind, B0, x1, x2, true, p);
+  MetricV m;
+  metric_eval<false>(g, x1, x2, false, m, nullptr);
+  if (comp == 0) out = (m.H11 * p.d1A0 + m.H13 * m.beta1 * p.d1A3) / m.alpha;
+  else if (comp == 1) out = m.H22 * (p.d2A0 - m.beta1 * p.d2A1) / m.alpha;
+  else out = (m.H13 * p.d1A0 + m.H33 * m.beta1 * p.d1A3) / m.alpha;
+}
+
+__global__ void k_init_fields(GridP g, FieldPtrs F, int kind, double B0) {
+  const int ni = g.n_r + 2 * G_ + 1, nj = g.n_th + 1;
+  const int64_t n = (int64_t)ni * nj;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % ni) - G_, j = (int)(t / ni);
+    const int64_t k = sidx(g, i, j);
+    const bool axis = (j == 0 || j == g.n_th);
+    Pot pa, pb;
+    if (j < g.n_th) {
+      potential(g, kind, B0, i, j, false, pa);
+      potential(g, kind, B0, i, j + 1, false, pb);
+      F.B[0][k] = (pb.A3 - pa.A3) * tabv(F.tab, g, CLS_NH, T_ISH, i, j);
+      potential(g, kind, B0, i + 0.5, j, false, pa);
+      potential(g, kind, B0, i + 0.5, j + 1, false, pb);
+      F.B[2][k] = -(pb.A1 - pa.A1) * tabv(F.tab, g, CLS_HH, T_ISH, i, j);
+      d_from_potential(g, kind, B0, i, j + 0.5, 1, F.D[1][k]);
+    }
+    if (!axis) {
+      potential(g, kind, B0, i, j, false, pa);
+      potential(g, kind, B0, i + 1, j, false, pb);
+      F.B[1][k] = -(pb.A3 - pa.A3) * tabv(F.tab, g, CLS_HN, T_ISH, i, j);
+      d_from_potential(g, kind, B0, i, j, 2, F.D[2][k]);
+    } else {
+      F.B[1][k] = 0.0;
+      F.D[2][k] = 0.0;
+    }
+    d_from_potential(g, kind, B0, i + 0.5, j, 0, F.D[0][k]);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Boundary conditions (Sec. 3.3.3).
+// ---------------------------------------------------------------------------------
+// Horizon layer: cells i1 in [-G, n_f] copy cell n_f + 1, all rows.
+__global__ void k_horizon(GridP g, double *p0, double *p1, double *p2) {
+  const int nl = g.n_f + 1 + G_, nj = g.NY;
+  const int64_t n = (int64_t)nl * nj * 3;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / ((int64_t)nl * nj));
+    const int64_t q = t - c * (int64_t)nl * nj;
+    const int i = (int)(q % nl) - G_, j = (int)(q / nl) - G_;
+    double *p = c == 0 ? p0 : (c == 1 ? p1 : p2);
+    p[sidx(g, i, j)] = p[sidx(g, g.n_f + 1, j)];
+  }
+}
+
+// Axis ghost rows by reflection (Fig. 1): r components even, theta and phi components
+// odd; half rows (x2 = j + 1/2) and node rows mirror differently. isB selects the B
+// classes (B^1 half, B^2 node, B^3 half) or the D classes (D^1 node, D^2 half, D^3 node).
+__global__ void k_axis(GridP g, double *p0, double *p1, double *p2, int isB) {
+  const int ni = g.NX;
+  const int nrow = 2 * G_ + 1;  // rows written per component (2 below, 3 above)
+  const int64_t n = (int64_t)ni * nrow * 3;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / ((int64_t)ni * nrow));
+    const int64_t q = t - c * (int64_t)ni * nrow;
+    const int i = (int)(q % ni) - G_, rr = (int)(q / ni);
+    double *p = c == 0 ? p0 : (c == 1 ? p1 : p2);
+    const bool half = isB ? (c != 1) : (c == 1);
+    const double par = (c == 0) ? 1.0 : -1.0;
+    const int N = g.n_th;
+    if (!half) {
+      if (rr < G_) {  // rows -1, -2 from 1, 2
+        const int k = rr + 1;
+        p[sidx(g, i, -k)] = par * p[sidx(g, i, k)];
+      } else if (rr < 2 * G_) {  // rows N+1, N+2 from N-1, N-2
+        const int k = rr - G_ + 1;
+        p[sidx(g, i, N + k)] = par * p[sidx(g, i, N - k)];
+      }
+    } else {
+      if (rr < G_) {  // rows -1, -2 from 0, 1
+        p[sidx(g, i, -1 - rr)] = par * p[sidx(g, i, rr)];
+      } else {  // rows N, N+1, N+2 from N-1, N-2, N-3
+        const int k = rr - G_;
+        p[sidx(g, i, N + k)] = par * p[sidx(g, i, N - 1 - k)];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Auxiliary fields, Eq. (discretized-auxE) with the averages of Eq. (discretized-auxH).
+// D (and for E also B) may be the mean of two time levels: X = wa Xa + wb Xb.
+// Computed on stored i in [-1, n_r + 1], rows [0, n_theta].
+// ---------------------------------------------------------------------------------
+struct Pair3 {
+  const double *a[3], *b[3];
+  double wa, wb;
+};
+__device__ __forceinline__ double pv(const Pair3 &P, int c, int64_t k) {
+  double v = P.wa * __ldg(P.a[c] + k);
+  if (P.wb != 0.0) v += P.wb * __ldg(P.b[c] + k);
+  return v;
+}
+
+__global__ void k_aux_E(GridP g, Pair3 B, Pair3 D, const double *tab, double *E1, double *E2,
+                        double *E3) {
+  const int ni = g.n_r + 3, nj = g.n_th + 1;
+  const int64_t n = (int64_t)ni * nj;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % ni) - 1, j = (int)(t / ni);
+    const int64_t k = sidx(g, i, j);
+    // E_1 at (i+1/2, j) = alpha [h_11 D^1 + <h_13 D^3>]
+    {
+      const double avg = (tabv(tab, g, CLS_NN, T_WT13, i, j) * pv(D, 2, k) +
+                          tabv(tab, g, CLS_NN, T_WT13, i + 1, j) * pv(D, 2, k + 1)) /
+                         (2.0 * tabv(tab, g, CLS_HN, T_SHT, i, j));
+      E1[k] = tabv(tab, g, CLS_HN, T_ALPHA, i, j) *
+              (tabv(tab, g, CLS_HN, T_H11, i, j) * pv(D, 0, k) + avg);
+    }
+    // E_3 at (i, j) = alpha [h_33 D^3 + <h_13 D^1>] + <sqrt(h) beta^1 B^2>; zero on the axes
+    if (j == 0 || j == g.n_th) {
+      E3[k] = 0.0;
+    } else {
+      const double d2 = 2.0 * tabv(tab, g, CLS_NN, T_SHT, i, j);
+      const double a13 = (tabv(tab, g, CLS_HN, T_WT13, i - 1, j) * pv(D, 0, k - 1) +
+                          tabv(tab, g, CLS_HN, T_WT13, i, j) * pv(D, 0, k)) / d2;
+      const double ab2 = (tabv(tab, g, CLS_HN, T_WB1, i - 1, j) * pv(B, 1, k - 1) +
+                          tabv(tab, g, CLS_HN, T_WB1, i, j) * pv(B, 1, k)) / d2;
+      E3[k] = tabv(tab, g, CLS_NN, T_ALPHA, i, j) *
+                  (tabv(tab, g, CLS_NN, T_H33, i, j) * pv(D, 2, k) + a13) + ab2;
+    }
+    // E_2 at (i, j+1/2) = alpha h_22 D^2 - <sqrt(h) beta^1 B^3>
+    if (j < g.n_th) {
+      const double ab3 = (tabv(tab, g, CLS_HH, T_WB1, i - 1, j) * pv(B, 2, k - 1) +
+                          tabv(tab, g, CLS_HH, T_WB1, i, j) * pv(B, 2, k)) /
+                         (2.0 * tabv(tab, g, CLS_NH, T_SHT, i, j));
+      E2[k] = tabv(tab, g, CLS_NH, T_ALPHA, i, j) * tabv(tab, g, CLS_NH, T_H22, i, j) *
+                  pv(D, 1, k) - ab3;
+    }
+  }
+}
+
+__global__ void k_aux_H(GridP g, Pair3 B, Pair3 D, const double *tab, double *H1, double *H2,
+                        double *H3) {
+  const int ni = g.n_r + 3, nj = g.n_th + 1;
+  const int64_t n = (int64_t)ni * nj;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % ni) - 1, j = (int)(t / ni);
+    const int64_t k = sidx(g, i, j);
+    if (j < g.n_th) {
+      // H_1 at (i, j+1/2) = alpha [h_11 B^1 + <h_13 B^3>]
+      const double a13 = (tabv(tab, g, CLS_HH, T_WT13, i - 1, j) * pv(B, 2, k - 1) +
+                          tabv(tab, g, CLS_HH, T_WT13, i, j) * pv(B, 2, k)) /
+                         (2.0 * tabv(tab, g, CLS_NH, T_SHT, i, j));
+      H1[k] = tabv(tab, g, CLS_NH, T_ALPHA, i, j) *
+              (tabv(tab, g, CLS_NH, T_H11, i, j) * pv(B, 0, k) + a13);
+      // H_3 at (i+1/2, j+1/2) = alpha [h_33 B^3 + <h_13 B^1>] - <sqrt(h) beta^1 D^2>
+      const double d3 = 2.0 * tabv(tab, g, CLS_HH, T_SHT, i, j);
+      const double b13 = (tabv(tab, g, CLS_NH, T_WT13, i, j) * pv(B, 0, k) +
+                          tabv(tab, g, CLS_NH, T_WT13, i + 1, j) * pv(B, 0, k + 1)) / d3;
+      const double bd2 = (tabv(tab, g, CLS_NH, T_WB1, i, j) * pv(D, 1, k) +
+                          tabv(tab, g, CLS_NH, T_WB1, i + 1, j) * pv(D, 1, k + 1)) / d3;
+      H3[k] = tabv(tab, g, CLS_HH, T_ALPHA, i, j) *
+                  (tabv(tab, g, CLS_HH, T_H33, i, j) * pv(B, 2, k) + b13) - bd2;
+    }
+    // H_2 at (i+1/2, j) = alpha h_22 B^2 + <sqrt(h) beta^1 D^3>
+    const double bd3 = (tabv(tab, g, CLS_NN, T_WB1, i, j) * pv(D, 2, k) +
+                        tabv(tab, g, CLS_NN, T_WB1, i + 1, j) * pv(D, 2, k + 1)) /
+                       (2.0 * tabv(tab, g, CLS_HN, T_SHT, i, j));
+    H2[k] = tabv(tab, g, CLS_HN, T_ALPHA, i, j) * tabv(tab, g, CLS_HN, T_H22, i, j) *
+                pv(B, 1, k) + bd3;
+  }
+}
+
+// MATCH absorbing layer (reading of paper I's form): F <- F - lambda (F - F_init),
+// lambda = coef min(1, ((r - r_abs)/(r_max - r_abs)))^3 for r > r_absorb, rows [0, n_theta].
+__device__ __forceinline__ double match(const GridP &g, double v, double vi, double x1, int j) {
+  if (!(g.r_absorb < g.r_max) || j < 0 || j > g.n_th) return v;
+  const double r = g.r_min * exp(x1 * g.dxi);
+  if (r <= g.r_absorb) return v;
+  double x = (r - g.r_absorb) / (g.r_max - g.r_absorb);
+  x = fmin(x, 1.0);
+  return v - g.absorb_coef * x * x * x * (v - vi);
+}
+
+// Faraday, Eq. (discretized-faraday): Bout = Bin - dt curl E / sqrt(h) on the evolved
+// points, Bout = Bin elsewhere; B^2 is not evolved on the axes. Covers every stored point.
+__global__ void k_faraday(GridP g, Pair3 Bin, const double *E1, const double *E2,
+                          const double *E3, const double *tab, double *B1, double *B2,
+                          double *B3, const double *Bi1, const double *Bi2, const double *Bi3,
+                          int do_match) {
+  const int64_t n = plane_size(g);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % g.NX) - G_, j = (int)(t / g.NX) - G_;
+    const int64_t k = t;
+    double b1 = pv(Bin, 0, k), b2 = pv(Bin, 1, k), b3 = pv(Bin, 2, k);
+    const bool rows_half = (j >= 0 && j < g.n_th);
+    if (rows_half && i >= 0 && i <= g.n_r)
+      b1 -= g.dt * (E3[k + g.NX] - E3[k]) * tabv(tab, g, CLS_NH, T_ISH, i, j);
+    if (j >= 1 && j < g.n_th && i >= 0 && i < g.n_r)
+      b2 += g.dt * (E3[k + 1] - E3[k]) * tabv(tab, g, CLS_HN, T_ISH, i, j);
+    if (rows_half && i >= 0 && i < g.n_r)
+      b3 -= g.dt * ((E2[k + 1] - E2[k]) - (E1[k + g.NX] - E1[k])) *
+            tabv(tab, g, CLS_HH, T_ISH, i, j);
+    if (do_match) {
+      b1 = match(g, b1, Bi1[k], i, j);
+      b2 = match(g, b2, Bi2[k], i + 0.5, j);
+      b3 = match(g, b3, Bi3[k], i + 0.5, j);
+    }
+    B1[k] = b1; B2[k] = b2; B3[k] = b3;
+  }
+}
+
+// Ampere, Eq. (discretized-ampere): Dout = Din + dt (curl H - 4 pi J) / sqrt(h); on the
+// axes D^1 follows the integral form of Sec. 3.3.2 with the polar area (reading: the
+// whole radial flux into the half cell, coefficient 4 pi; -H_3 at theta = pi) and D^3
+// is not evolved. J may be the mean of two time levels.
+__global__ void k_ampere(GridP g, Pair3 Din, const double *H1, const double *H2,
+                         const double *H3, Pair3 J, const double *tab, const double *polar,
+                         double *D1, double *D2, double *D3, const double *Di1,
+                         const double *Di2, const double *Di3, int do_match) {
+  const int64_t n = plane_size(g);
+  const double fpi = 4.0 * GRPIC_PI;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % g.NX) - G_, j = (int)(t / g.NX) - G_;
+    const int64_t k = t;
+    double d1 = pv(Din, 0, k), d2 = pv(Din, 1, k), d3 = pv(Din, 2, k);
+    if (i >= 0 && i < g.n_r && j >= 0 && j <= g.n_th) {
+      if (j == 0)
+        d1 += g.dt * (H3[k] - fpi * pv(J, 0, k)) / __ldg(polar + i + G_);
+      else if (j == g.n_th)
+        d1 += g.dt * (-H3[k - g.NX] - fpi * pv(J, 0, k)) / __ldg(polar + i + G_);
+      else
+        d1 += g.dt * ((H3[k] - H3[k - g.NX]) - fpi * pv(J, 0, k)) *
+              tabv(tab, g, CLS_HN, T_ISH, i, j);
+    }
+    if (i >= 0 && i <= g.n_r && j >= 0 && j < g.n_th)
+      d2 += g.dt * (-(H3[k] - H3[k - 1]) - fpi * pv(J, 1, k)) * tabv(tab, g, CLS_NH, T_ISH, i, j);
+    if (i >= 0 && i <= g.n_r && j >= 1 && j < g.n_th)
+      d3 += g.dt * ((H2[k] - H2[k - 1]) - (H1[k] - H1[k - g.NX]) - fpi * pv(J, 2, k)) *
+            tabv(tab, g, CLS_NN, T_ISH, i, j);
+    if (do_match) {
+      d1 = match(g, d1, Di1[k], i + 0.5, j);
+      d2 = match(g, d2, Di2[k], i, j);
+      d3 = match(g, d3, Di3[k], i, j);
+    }
+    D1[k] = d1; D2[k] = d2; D3[k] = d3;
+  }
+}
+
+__global__ void k_copy3(int64_t n, const double *a0, const double *a1, const double *a2,
+                        double *b0, double *b1, double *b2) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    b0[t] = a0[t]; b1[t] = a1[t]; b2[t] = a2[t];
+  }
+}
+
+__global__ void k_zero(double *p, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    p[t] = 0.0;
+}
+
+int blocks_for(int64_t n) {
+  int64_t b = (n + TPB - 1) / TPB;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+Pair3 one(double *const p[3]) {
+  Pair3 P;
+  for (int c = 0; c < 3; ++c) { P.a[c] = p[c]; P.b[c] = p[c]; }
+  P.wa = 1.0; P.wb = 0.0;
+  return P;
+}
+Pair3 mean(double *const p[3], double *const q[3]) {
+  Pair3 P;
+  for (int c = 0; c < 3; ++c) { P.a[c] = p[c]; P.b[c] = q[c]; }
+  P.wa = 0.5; P.wb = 0.5;
+  return P;
+}
+
+void horizon(const GridP &g, double *const p[3], cudaStream_t st) {
+  const int64_t n = (int64_t)(g.n_f + 1 + G_) * g.NY * 3;
+  k_horizon<<<blocks_for(n), TPB, 0, st>>>(g, p[0], p[1], p[2]);
+  COUNT_LAUNCH(1);
+}
+void axis(const GridP &g, double *const p[3], int isB, cudaStream_t st) {
+  const int64_t n = (int64_t)g.NX * (2 * G_ + 1) * 3;
+  k_axis<<<blocks_for(n), TPB, 0, st>>>(g, p[0], p[1], p[2], isB);
+  COUNT_LAUNCH(1);
+}
+void auxE(const GridP &g, Pair3 B, Pair3 D, const FieldPtrs &F, cudaStream_t st) {
+  const int64_t n = (int64_t)(g.n_r + 3) * (g.n_th + 1);
+  k_aux_E<<<blocks_for(n), TPB, 0, st>>>(g, B, D, F.tab, F.E[0], F.E[1], F.E[2]);
+  COUNT_LAUNCH(1);
+}
+void auxH(const GridP &g, Pair3 B, Pair3 D, const FieldPtrs &F, cudaStream_t st) {
+  const int64_t n = (int64_t)(g.n_r + 3) * (g.n_th + 1);
+  k_aux_H<<<blocks_for(n), TPB, 0, st>>>(g, B, D, F.tab, F.H[0], F.H[1], F.H[2]);
+  COUNT_LAUNCH(1);
+}
+
+}  // namespace
+
+cudaError_t launch_metric_tables(const GridP &g, double *tab, double *polar, cudaStream_t st) {
+  k_metric_tables<<<blocks_for(4 * plane_size(g)), TPB, 0, st>>>(g, tab, polar);
+  COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt_min(const GridP &g, double *scratch, int, double *out, cudaStream_t st) {
+  unsigned long long *u = reinterpret_cast<unsigned long long *>(scratch);
+  const unsigned long long inf = 0x7FF0000000000000ull;
+  cudaMemcpyAsync(u, &inf, sizeof(inf), cudaMemcpyHostToDevice, st);
+  k_dt_min<<<blocks_for((int64_t)g.n_r * g.n_th), TPB, 0, st>>>(g, u);
+  COUNT_LAUNCH(1);
+  cudaMemcpyAsync(out, u, sizeof(double), cudaMemcpyDeviceToHost, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(double *p, int64_t n, cudaStream_t st) {
+  k_zero<<<blocks_for(n), TPB, 0, st>>>(p, n);
+  COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_fields(const GridP &g, const FieldPtrs &F, int kind, double B0,
+                               cudaStream_t st) {
+  const int64_t ps = plane_size(g);
+  for (int c = 0; c < 3; ++c) {
+    launch_zero(F.B[c], ps, st);
+    launch_zero(F.D[c], ps, st);
+  }
+  if (kind == GRPIC_FIELD_WALD || kind == GRPIC_FIELD_VERTICAL) {
+    const int64_t n = (int64_t)(g.n_r + 2 * G_ + 1) * (g.n_th + 1);
+    k_init_fields<<<blocks_for(n), TPB, 0, st>>>(g, F, kind, B0);
+    COUNT_LAUNCH(1);
+  }
+  return cudaGetLastError();
+}
+
+// After em holds the initial B, D: boundary fills, em0 = em, initial-field copy,
+// cur0 = cur = 0, B^n = B.
+cudaError_t launch_field_finish_init(const GridP &g, const FieldPtrs &F, int, cudaStream_t st) {
+  const int64_t ps = plane_size(g);
+  horizon(g, F.B, st);
+  horizon(g, F.D, st);
+  axis(g, F.B, 1, st);
+  axis(g, F.D, 0, st);
+  k_copy3<<<blocks_for(ps), TPB, 0, st>>>(ps, F.B[0], F.B[1], F.B[2], F.B0[0], F.B0[1], F.B0[2]);
+  COUNT_LAUNCH(1);
+  k_copy3<<<blocks_for(ps), TPB, 0, st>>>(ps, F.D[0], F.D[1], F.D[2], F.D0[0], F.D0[1], F.D0[2]);
+  COUNT_LAUNCH(1);
+  k_copy3<<<blocks_for(ps), TPB, 0, st>>>(ps, F.B[0], F.B[1], F.B[2], F.Bi[0], F.Bi[1], F.Bi[2]);
+  COUNT_LAUNCH(1);
+  k_copy3<<<blocks_for(ps), TPB, 0, st>>>(ps, F.D[0], F.D[1], F.D[2], F.Di[0], F.Di[1], F.Di[2]);
+  COUNT_LAUNCH(1);
+  k_copy3<<<blocks_for(ps), TPB, 0, st>>>(ps, F.B[0], F.B[1], F.B[2], F.Bn[0], F.Bn[1], F.Bn[2]);
+  COUNT_LAUNCH(1);
+  for (int c = 0; c < 3; ++c) {
+    launch_zero(F.J[c], ps, st);
+    launch_zero(F.J0[c], ps, st);
+    launch_zero(F.E[c], ps, st);
+    launch_zero(F.H[c], ps, st);
+    launch_zero(F.Dh[c], ps, st);
+  }
+  return cudaGetLastError();
+}
+
+// Loop step 2 of Sec. 3.4: B^{n-1} = (B^{n-3/2} + B^{n-1/2})/2, D^{n-1/2} = (D^{n-1} + D^n)/2,
+// E^{n-1/2} from {B^{n-1/2}, D^{n-1/2}}, auxiliary Faraday B^{n-1} -> B^n (BN planes).
+cudaError_t launch_predict(const GridP &g, const FieldPtrs &F, cudaStream_t st) {
+  auxE(g, one(F.B), mean(F.D0, F.D), F, st);
+  const Pair3 Bm = mean(F.B0, F.B);
+  const int64_t ps = plane_size(g);
+  k_faraday<<<blocks_for(ps), TPB, 0, st>>>(g, Bm, F.E[0], F.E[1], F.E[2], F.tab, F.Bn[0],
+                                            F.Bn[1], F.Bn[2], nullptr, nullptr, nullptr, 0);
+  COUNT_LAUNCH(1);
+  horizon(g, F.Bn, st);
+  axis(g, F.Bn, 1, st);
+  return cudaGetLastError();
+}
+
+// Loop steps 5-7 of Sec. 3.4 (J holds J^{n+1/2}). Writes B^{n+1/2} into the B0 planes and
+// D^{n+1} into the D0 planes; the caller then swaps em/em0 and cur/cur0.
+cudaError_t launch_advance(const GridP &g, const FieldPtrs &F, cudaStream_t st) {
+  const int64_t ps = plane_size(g);
+  // step 6: E^n, H^n from {B^n, D^n}; Faraday B^{n-1/2} -> B^{n+1/2}
+  auxE(g, one(F.Bn), one(F.D), F, st);
+  auxH(g, one(F.Bn), one(F.D), F, st);
+  k_faraday<<<blocks_for(ps), TPB, 0, st>>>(g, one(F.B), F.E[0], F.E[1], F.E[2], F.tab,
+                                            F.B0[0], F.B0[1], F.B0[2], F.Bi[0], F.Bi[1],
+                                            F.Bi[2], 1);
+  COUNT_LAUNCH(1);
+  horizon(g, F.B0, st);
+  axis(g, F.B0, 1, st);
+  // step 7: auxiliary Ampere D^{n-1/2} -> D^{n+1/2} with H^n and J^n = (J^{n-1/2} + J^{n+1/2})/2
+  k_ampere<<<blocks_for(ps), TPB, 0, st>>>(g, mean(F.D0, F.D), F.H[0], F.H[1], F.H[2],
+                                           mean(F.J0, F.J), F.tab, F.polar, F.Dh[0], F.Dh[1],
+                                           F.Dh[2], nullptr, nullptr, nullptr, 0);
+  COUNT_LAUNCH(1);
+  horizon(g, F.Dh, st);
+  // H^{n+1/2} from {B^{n+1/2}, D^{n+1/2}}; final Ampere D^n -> D^{n+1} with J^{n+1/2}
+  auxH(g, one(F.B0), one(F.Dh), F, st);
+  k_ampere<<<blocks_for(ps), TPB, 0, st>>>(g, one(F.D), F.H[0], F.H[1], F.H[2], one(F.J),
+                                           F.tab, F.polar, F.D0[0], F.D0[1], F.D0[2], F.Di[0],
+                                           F.Di[1], F.Di[2], 1);
+  COUNT_LAUNCH(1);
+  horizon(g, F.D0, st);
+  axis(g, F.D0, 0, st);
+  return cudaGetLastError();
+}

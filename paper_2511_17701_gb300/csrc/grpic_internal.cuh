@@ -1,0 +1,211 @@
+// grpic_internal.cuh -- device helpers and kernel launch interfaces shared by the
+// translation units of libgrpic (not installed, not part of the C ABI).
+//
+// Geometry follows Appendix A of arXiv:2511.17701 in code units: the quasi-spherical
+// Kerr-Schild map with r0 = 0, h0 = 0 (r = r_min exp(x1 dxi), theta = x2 dtheta,
+// dphi = 1), with mass M = 1 (Kerr-Schild) or M = 0 and a = 0 (kerr_schild_0, flat).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/grpic.h"
+
+#define G_ GRPIC_GHOSTS
+#define GRPIC_PI 3.14159265358979323846
+
+// Grid and step parameters passed by value to every kernel.
+struct GridP {
+  int n_r, n_th, NX, NY, n_iter, n_f;
+  double r_min, r_max, dxi, dth, a, M, dt, small_angle, r_absorb, absorb_coef;
+};
+
+// Yee point classes of the metric tables: (i, j), (i+1/2, j), (i, j+1/2), (i+1/2, j+1/2).
+enum { CLS_NN = 0, CLS_HN = 1, CLS_NH = 2, CLS_HH = 3 };
+// Quantities tabulated per class (Eq. discretized-auxE/auxH and the curls).
+enum { T_ALPHA = 0, T_H11, T_H22, T_H33, T_SHT, T_WT13, T_WB1, T_ISH, T_NQ };
+
+__host__ __device__ inline int64_t plane_size(const GridP &g) { return (int64_t)g.NX * g.NY; }
+__host__ __device__ inline int64_t sidx(const GridP &g, int i, int j) {
+  return (int64_t)(j + G_) * g.NX + (i + G_);
+}
+
+// Device view of one species' arrays.
+struct SpeciesDev {
+  int32_t *i1, *i2;
+  double *dx1, *dx2, *u1, *u2, *u3, *phi, *w;
+  uint8_t *tag;
+  int32_t *i1p, *i2p;
+  double *dx1p, *dx2p;
+  const int64_t *n;  // live count, on the device
+  double qm, qc;
+};
+
+// Diagnostics counters on the device (unsigned long long for atomicAdd).
+enum { DG_LEFT_INNER = 0, DG_LEFT_OUTER, DG_REFLECT, DG_NONFINITE, DG_N };
+
+// ---------------------------------------------------------------------------------
+// Metric of Appendix A, written directly in the code-unit (xi, eta) form of the
+// quasi-spherical Kerr-Schild section, with the mass M kept explicit.
+// ---------------------------------------------------------------------------------
+struct MetricV {
+  double h11, h22, h33, h13, H11, H22, H33, H13, alpha, beta1, sqrt_h, sqrt_ht;
+};
+struct MetricD {
+  double d1H11, d1H22, d1H33, d1H13, d1alpha, d1beta1;
+  double d2H11, d2H22, d2H33, d2H13, d2alpha, d2beta1;
+};
+
+template <bool DERIV>
+__device__ __forceinline__ void metric_eval(const GridP &g, double x1, double x2, bool clamp,
+                                            MetricV &m, MetricD *d) {
+  const double a = g.a, M = g.M, a2 = a * a;
+  const double r = g.r_min * exp(x1 * g.dxi);
+  double th = x2 * g.dth;
+  if (clamp) th = fmin(fmax(th, g.small_angle), GRPIC_PI - g.small_angle);
+  double s, c;
+  sincos(th, &s, &c);
+  const double s2 = s * s, r2 = r * r;
+  const double Sig = r2 + a2 * c * c;
+  const double Del = r2 - 2.0 * M * r + a2;
+  const double A = (r2 + a2) * (r2 + a2) - a2 * Del * s2;
+  const double iSig = 1.0 / Sig;
+  const double z = 2.0 * M * r * iSig;
+  const double al2 = 1.0 / (1.0 + z);          // alpha^2 = 1/(1+z)
+  const double f = g.dxi * r, fi = 1.0 / f;     // d xi e^xi and its inverse
+  const double gg = g.dth;                      // d eta (d theta / d eta), h0 = 0
+  m.alpha = sqrt(al2);
+  m.h11 = f * f * (1.0 + z);
+  m.h13 = -f * a * (1.0 + z) * s2;
+  m.h22 = gg * gg * Sig;
+  m.h33 = A * s2 * iSig;
+  m.H11 = A * iSig * iSig * al2 * fi * fi;      // A / (Sigma (Sigma + 2 M r)) / f^2
+  m.H13 = a * iSig * fi;
+  m.H22 = iSig / (gg * gg);
+  m.H33 = iSig / s2;
+  m.beta1 = z * al2 * fi;
+  m.sqrt_ht = f * gg * Sig / m.alpha;
+  m.sqrt_h = m.sqrt_ht * s;
+  if (DERIV) {
+    const double dxS = 2.0 * r * f, deS = -2.0 * a2 * s * c * gg;
+    const double dxD = 2.0 * (r - M) * f;
+    const double dxA = 4.0 * r * f * (r2 + a2) - a2 * s2 * dxD;
+    const double deA = -2.0 * a2 * s * c * Del * gg;
+    const double P = Sig * Sig * (1.0 + z);     // Sigma (Sigma + 2 M r)
+    const double iP2 = 1.0 / (P * P);
+    const double iS2 = iSig * iSig;
+    const double al3 = m.alpha * al2;
+    d->d1H11 = (P * dxA - 2.0 * A * (M * r * dxS + Sig * (dxS + M * f))) * iP2 * fi * fi -
+               2.0 * g.dxi * m.H11;
+    d->d2H11 = (P * deA - 2.0 * A * deS * (M * r + Sig)) * iP2 * fi * fi;
+    d->d1H22 = -dxS * iS2 / (gg * gg);
+    d->d2H22 = -deS * iS2 / (gg * gg);
+    d->d1H33 = -dxS * iS2 / s2;
+    d->d2H33 = -(deS + 2.0 * (c / s) * Sig * gg) * iS2 / s2;
+    d->d1H13 = -a * iS2 * dxS * fi - g.dxi * a * iSig * fi;
+    d->d2H13 = -a * iS2 * deS * fi;
+    d->d1alpha = -M * (f * Sig - r * dxS) * iS2 * al3;
+    d->d2alpha = M * r * deS * iS2 * al3;
+    d->d1beta1 = fi * 2.0 * M * (f * Sig - r * dxS) * iS2 * al2 * al2 - g.dxi * m.beta1;
+    d->d2beta1 = -fi * 2.0 * M * r * deS * iS2 * al2 * al2;
+  }
+}
+
+// Tetrad maps of Appendix A (matrix form).
+__device__ __forceinline__ void t_vec_to_hat(const MetricV &m, const double A[3], double Ah[3]) {
+  const double s11 = sqrt(m.H11), s33 = sqrt(m.h33);
+  Ah[0] = A[0] / s11;
+  Ah[1] = sqrt(m.h22) * A[1];
+  Ah[2] = m.h13 / s33 * A[0] + s33 * A[2];
+}
+__device__ __forceinline__ void t_cov_to_hat(const MetricV &m, const double a[3], double ah[3]) {
+  const double s11 = sqrt(m.H11);
+  ah[0] = s11 * (a[0] - m.h13 / m.h33 * a[2]);
+  ah[1] = a[1] / sqrt(m.h22);
+  ah[2] = a[2] / sqrt(m.h33);
+}
+__device__ __forceinline__ void t_hat_to_cov(const MetricV &m, const double ah[3], double a[3]) {
+  const double s33 = sqrt(m.h33);
+  a[0] = ah[0] / sqrt(m.H11) + m.h13 / s33 * ah[2];
+  a[1] = sqrt(m.h22) * ah[1];
+  a[2] = s33 * ah[2];
+}
+
+__device__ __forceinline__ double gamma_of(const MetricV &m, const double u[3]) {
+  return sqrt(1.0 + m.H11 * u[0] * u[0] + m.H22 * u[1] * u[1] + m.H33 * u[2] * u[2] +
+              2.0 * m.H13 * u[0] * u[2]);
+}
+
+// Boris step over coordinate time dt/2 in the tetrad frame, hq = qm alpha dt / 2.
+__device__ __forceinline__ void boris_step(double u[3], const double D[3], const double B[3],
+                                           double hq) {
+  const double e = 0.5 * hq;
+  const double m0 = u[0] + e * D[0], m1 = u[1] + e * D[1], m2 = u[2] + e * D[2];
+  const double ig = rsqrt(1.0 + m0 * m0 + m1 * m1 + m2 * m2);
+  const double t0 = e * B[0] * ig, t1 = e * B[1] * ig, t2 = e * B[2] * ig;
+  const double sf = 2.0 / (1.0 + t0 * t0 + t1 * t1 + t2 * t2);
+  const double p0 = m0 + (m1 * t2 - m2 * t1);
+  const double p1 = m1 + (m2 * t0 - m0 * t2);
+  const double p2 = m2 + (m0 * t1 - m1 * t0);
+  u[0] = m0 + sf * (p1 * t2 - p2 * t1) + e * D[0];
+  u[1] = m1 + sf * (p2 * t0 - p0 * t2) + e * D[1];
+  u[2] = m2 + sf * (p0 * t1 - p1 * t0) + e * D[2];
+}
+
+// Bilinear interpolation of a plane at code position (x1, x2) for a component whose Yee
+// location is offset by (s1, s2); ghost rows across the axes hold the mirrored values.
+__device__ __forceinline__ double interp_plane(const double *__restrict__ pl, int NX, double x1,
+                                               double x2, double s1, double s2) {
+  const double y1 = x1 - s1, y2 = x2 - s2;
+  const double f1 = floor(y1), f2 = floor(y2);
+  const int i0 = (int)f1, j0 = (int)f2;
+  const double w1 = y1 - f1, w2 = y2 - f2;
+  const double *p = pl + (int64_t)(j0 + G_) * NX + (i0 + G_);
+  return (1.0 - w1) * (1.0 - w2) * __ldg(p) + w1 * (1.0 - w2) * __ldg(p + 1) +
+         (1.0 - w1) * w2 * __ldg(p + NX) + w1 * w2 * __ldg(p + NX + 1);
+}
+
+// Kernels launched by the library (host counter, reset by grpic_get_timing).
+extern long long grpic_launches;
+#define COUNT_LAUNCH(n) (grpic_launches += (n))
+
+// ---------------------------------------------------------------------------------
+// Launchers (host functions defined in fields.cu, particles.cu, sort.cu).
+// Every launcher returns cudaGetLastError() of its launches.
+// ---------------------------------------------------------------------------------
+struct FieldPtrs {
+  double *B[3], *D[3], *B0[3], *D0[3], *J[3], *J0[3], *Bn[3], *Bi[3], *Di[3];
+  double *E[3], *H[3], *Dh[3];
+  const double *tab;    // [4 classes][T_NQ][plane]
+  const double *polar;  // [NX], polar area at x1 = i + 1/2 stored at i
+};
+
+cudaError_t launch_metric_tables(const GridP &g, double *tab, double *polar, cudaStream_t st);
+cudaError_t launch_dt_min(const GridP &g, double *scratch, int nscratch, double *out,
+                          cudaStream_t st);
+cudaError_t launch_init_fields(const GridP &g, const FieldPtrs &F, int kind, double B0,
+                               cudaStream_t st);
+cudaError_t launch_field_finish_init(const GridP &g, const FieldPtrs &F, int user,
+                                     cudaStream_t st);
+cudaError_t launch_predict(const GridP &g, const FieldPtrs &F, cudaStream_t st);
+cudaError_t launch_advance(const GridP &g, const FieldPtrs &F, cudaStream_t st);
+cudaError_t launch_zero(double *p, int64_t n, cudaStream_t st);
+
+cudaError_t launch_load(const GridP &g, SpeciesDev s, int64_t n, const grpic_particle_init &in,
+                        double density_power, cudaStream_t st);
+cudaError_t launch_push(const GridP &g, const FieldPtrs &F, SpeciesDev s, int64_t n_bound,
+                        bool deposit, unsigned long long *diag, cudaStream_t st);
+cudaError_t launch_deposit(const GridP &g, const FieldPtrs &F, SpeciesDev s, int64_t n_bound,
+                           cudaStream_t st);
+
+struct SortScratch {
+  uint32_t *keys[2], *vals[2];
+  uint32_t *hist;     // [256][nblocks]
+  uint32_t *bsum;     // block sums of the scan
+  unsigned long long *alive;  // alive count of the species being sorted
+  int64_t max_n;
+  int max_blocks;
+};
+int64_t sort_hist_entries(int64_t max_n);
+int64_t sort_bsum_entries(int64_t max_n);
+cudaError_t launch_sort(const GridP &g, int tile_r, int tile_t, SpeciesDev in, SpeciesDev out,
+                        int64_t n_bound, int64_t *n_dev, const SortScratch &S, cudaStream_t st);

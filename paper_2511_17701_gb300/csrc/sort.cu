@@ -1,0 +1,207 @@
+// sort.cu -- stable counting sort of a species by tile-major cell key (an addition of
+// this library: the paper's loop does not sort). Least-significant-digit radix passes
+// of 8 bits; each pass is upsweep (per-block digit histogram), an exclusive scan of the
+// digit-major histogram, and a downsweep where each warp ranks its own contiguous run
+// with __match_any_sync, so the order of equal keys is the input order and the
+// permutation is unique (bit-exact). Particles not alive get the key 0xFFFFFFFF, sort
+// last and are dropped.
+#include "grpic_internal.cuh"
+
+namespace {
+
+constexpr int TPB = 256;                      // 8 warps
+constexpr int NWARP = TPB / 32;
+constexpr int ITEMS = 16;                     // per lane and pass
+constexpr int WCHUNK = 32 * ITEMS;            // contiguous elements per warp
+constexpr int BCHUNK = NWARP * WCHUNK;        // contiguous elements per block
+constexpr int SCAN_SEG = 1024;
+
+__device__ __forceinline__ uint32_t cell_key(int i1, int i2, uint8_t tag, int n_r, int tr, int tt) {
+  if (tag != 1) return 0xFFFFFFFFu;
+  const uint32_t ntr = (uint32_t)((n_r + tr - 1) / tr);
+  const uint32_t tile = (uint32_t)(i2 / tt) * ntr + (uint32_t)(i1 / tr);
+  return tile * (uint32_t)(tr * tt) + (uint32_t)(i2 % tt) * (uint32_t)tr + (uint32_t)(i1 % tr);
+}
+
+__global__ void k_keys(SpeciesDev s, int n_r, int tr, int tt, uint32_t *keys, uint32_t *vals,
+                       unsigned long long *alive) {
+  const int64_t n = *s.n;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t tag = s.tag[k];
+    keys[k] = cell_key(s.i1[k], s.i2[k], tag, n_r, tr, tt);
+    vals[k] = (uint32_t)k;
+    const unsigned m = __ballot_sync(__activemask(), tag == 1);
+    if ((threadIdx.x & 31) == __ffs(__activemask()) - 1 && m) atomicAdd(alive, (unsigned long long)__popc(m));
+  }
+}
+
+__global__ void k_hist(const uint32_t *keys, const int64_t *n_dev, int shift, int nblocks,
+                       uint32_t *hist) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t n = *n_dev;
+  const int64_t base = (int64_t)blockIdx.x * BCHUNK;
+  const int64_t end = min(n, base + BCHUNK);
+  for (int64_t e = base + threadIdx.x; e < end; e += TPB)
+    atomicAdd(&cnt[(keys[e] >> shift) & 255u], 1u);
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_scatter(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
+                          uint32_t *vout, const int64_t *n_dev, int shift, int nblocks,
+                          const uint32_t *offs) {
+  __shared__ uint32_t wcnt[NWARP][256];
+  __shared__ uint32_t wbase[NWARP][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < NWARP * 256; d += TPB) (&wcnt[0][0])[d] = 0;
+  __syncthreads();
+  const int64_t n = *n_dev;
+  const int64_t wb = (int64_t)blockIdx.x * BCHUNK + (int64_t)w * WCHUNK;
+  for (int b = 0; b < ITEMS; ++b) {
+    const int64_t e = wb + b * 32 + lane;
+    if (e < n) atomicAdd(&wcnt[w][(kin[e] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  {
+    const int d = threadIdx.x;  // TPB == 256 digits
+    uint32_t run = offs[(int64_t)d * nblocks + blockIdx.x];
+    for (int v = 0; v < NWARP; ++v) {
+      wbase[v][d] = run;
+      run += wcnt[v][d];
+    }
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int b = 0; b < ITEMS; ++b) {
+    const int64_t e = wb + b * 32 + lane;
+    const bool ok = e < n;
+    const uint32_t key = ok ? kin[e] : 0u;
+    const uint32_t d = ok ? ((key >> shift) & 255u) : (256u + lane);
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    uint32_t pos = 0;
+    if (ok) pos = wbase[w][d] + __popc(peers & lt);
+    __syncwarp();
+    if (ok) {
+      kout[pos] = key;
+      vout[pos] = vin[e];
+      if (lane == __ffs(peers) - 1) wbase[w][d] += __popc(peers);
+    }
+    __syncwarp();
+  }
+}
+
+// exclusive scan of a uint32 array in segments of SCAN_SEG, segment totals to bsum
+__global__ void k_scan_seg(uint32_t *a, int64_t L, uint32_t *bsum) {
+  __shared__ uint32_t s[SCAN_SEG];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_SEG;
+  for (int t = threadIdx.x; t < SCAN_SEG; t += blockDim.x)
+    s[t] = (base + t < L) ? a[base + t] : 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int t = 0; t < SCAN_SEG; ++t) {
+      const uint32_t v = s[t];
+      s[t] = run;
+      run += v;
+    }
+    bsum[blockIdx.x] = run;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < SCAN_SEG; t += blockDim.x)
+    if (base + t < L) a[base + t] = s[t];
+}
+
+__global__ void k_scan_sums(uint32_t *bsum, int64_t S) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    uint32_t run = 0;
+    for (int64_t t = 0; t < S; ++t) {
+      const uint32_t v = bsum[t];
+      bsum[t] = run;
+      run += v;
+    }
+  }
+}
+
+__global__ void k_scan_add(uint32_t *a, int64_t L, const uint32_t *bsum) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < L) a[t] += bsum[t / SCAN_SEG];
+}
+
+// gather every array of the species by the final permutation
+__global__ void k_gather(SpeciesDev in, SpeciesDev out, const uint32_t *perm,
+                         const int64_t *n_dev) {
+  const int64_t n = *n_dev;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = perm[k];
+    out.i1[k] = in.i1[p]; out.i2[k] = in.i2[p];
+    out.dx1[k] = in.dx1[p]; out.dx2[k] = in.dx2[p];
+    out.u1[k] = in.u1[p]; out.u2[k] = in.u2[p]; out.u3[k] = in.u3[p];
+    out.phi[k] = in.phi[p]; out.w[k] = in.w[p]; out.tag[k] = in.tag[p];
+    out.i1p[k] = in.i1p[p]; out.i2p[k] = in.i2p[p];
+    out.dx1p[k] = in.dx1p[p]; out.dx2p[k] = in.dx2p[p];
+  }
+}
+
+__global__ void k_set_n(int64_t *n_dev, const unsigned long long *alive) {
+  *n_dev = (int64_t)*alive;
+}
+
+int grid_for(int64_t n, int tpb) {
+  int64_t b = (n + tpb - 1) / tpb;
+  if (b > 152 * 64) b = 152 * 64;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int64_t sort_hist_entries(int64_t max_n) {
+  const int64_t nb = (max_n + BCHUNK - 1) / BCHUNK;
+  return 256 * (nb < 1 ? 1 : nb);
+}
+int64_t sort_bsum_entries(int64_t max_n) {
+  return (sort_hist_entries(max_n) + SCAN_SEG - 1) / SCAN_SEG;
+}
+
+cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDev in, SpeciesDev out,
+                        int64_t n_bound, int64_t *n_dev, const SortScratch &S, cudaStream_t st) {
+  if (n_bound <= 0) return cudaGetLastError();
+  // number of key bits: keys of alive particles are < tiles * tr * tt; 0xFFFFFFFF must
+  // sort after them, i.e. its low bits must exceed every alive key
+  const int64_t ntr = (g.n_r + tr - 1) / tr, ntt = (g.n_th + tt - 1) / tt;
+  const uint64_t maxkey = (uint64_t)ntr * ntt * tr * tt;  // exclusive bound
+  int bits = 1;
+  while (((uint64_t)1 << bits) - 1 < maxkey + 1 && bits < 32) ++bits;
+  const int passes = (bits + 7) / 8;
+  unsigned long long *alive = S.alive;
+  cudaMemsetAsync(alive, 0, sizeof(unsigned long long), st);
+  k_keys<<<grid_for(n_bound, TPB), TPB, 0, st>>>(in, g.n_r, tr, tt, S.keys[0], S.vals[0], alive);
+  COUNT_LAUNCH(1);
+  const int nblocks = (int)((n_bound + BCHUNK - 1) / BCHUNK);
+  const int64_t L = 256LL * nblocks;
+  const int64_t nseg = (L + SCAN_SEG - 1) / SCAN_SEG;
+  int cur = 0;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    k_hist<<<nblocks, TPB, 0, st>>>(S.keys[cur], in.n, shift, nblocks, S.hist);
+    COUNT_LAUNCH(1);
+    k_scan_seg<<<(int)nseg, 256, 0, st>>>(S.hist, L, S.bsum);
+    COUNT_LAUNCH(1);
+    k_scan_sums<<<1, 32, 0, st>>>(S.bsum, nseg);
+    COUNT_LAUNCH(1);
+    k_scan_add<<<(int)((L + 255) / 256), 256, 0, st>>>(S.hist, L, S.bsum);
+    COUNT_LAUNCH(1);
+    k_scatter<<<nblocks, TPB, 0, st>>>(S.keys[cur], S.vals[cur], S.keys[1 - cur],
+                                       S.vals[1 - cur], in.n, shift, nblocks, S.hist);
+    COUNT_LAUNCH(1);
+    cur = 1 - cur;
+  }
+  k_gather<<<grid_for(n_bound, TPB), TPB, 0, st>>>(in, out, S.vals[cur], in.n);
+  COUNT_LAUNCH(1);
+  k_set_n<<<1, 1, 0, st>>>(n_dev, alive);
+  COUNT_LAUNCH(1);
+  return cudaGetLastError();
+}

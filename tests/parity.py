@@ -1,0 +1,87 @@
+"""Shared set-up and comparisons for the GPU-vs-oracle parity tests.
+
+The oracle builds and owns every input state; the CUDA library receives copies of
+it (the reverse never happens: no value computed on the GPU feeds the oracle).
+
+Tolerances (the benchmark spec's bound for FP64): particle state and fields agree to
+1e-12 relative per step. The two sides differ only in rounding (fused multiply-adds
+on the GPU, a different but equivalent formulation of the metric, CUDA's vs glibc's
+transcendentals), i.e. ~1e-16 per operation along chains of a few hundred
+operations with condition numbers of at most ~1e2 near the horizon, which stays
+below 1e-12. Currents are summed by atomics in arbitrary order, so each cell is
+compared against 1e-12 times the sum of the absolute values of its contributions.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import workloads as W
+from oracle import oracle as O
+
+RTOL = 1e-12
+G = O.G
+STATE_PLANES = list(range(27))  # em, em0, cur, cur0, B^n, initial field
+
+
+def oracle_state(cfg: dict, cells=None, kind=O.FIELD_WALD, B0=1.0, species=2):
+    osim = O.OracleSim(cfg)
+    osim.init_fields(kind, B0)
+    if species:
+        pl = W.pair_plasma(cfg, cells=cells)
+        for s in range(species):
+            osim.add_species(pl["pos"], pl["uhat"][s], pl["w0"], pl["qm"][s], pl["qc"][s],
+                             pl["density_power"])
+    return osim
+
+
+def gpu_from_oracle(osim, extra_capacity=0, **over):
+    """A GPU context holding a copy of the oracle's full state."""
+    from paper_2511_17701_gb300 import FIELD_USER, Sim
+    cfg = dict(osim.cfg, dt=osim.dt, **over)
+    caps = [max(s.n + extra_capacity, 1) for s in osim.species] or [1]
+    g = Sim(cfg, caps)
+    g.init_metric()
+    g.init_fields(FIELD_USER)
+    g.set_planes(osim.F)
+    for k, s in enumerate(osim.species):
+        g.set_particles(k, s.view(), s.qm, s.qc)
+    return g
+
+
+def max_rel_plane(a, b):
+    scale = max(np.abs(b).max(), 1e-300)
+    return float(np.abs(a - b).max() / scale)
+
+
+def assert_planes(Fg, Fo, planes=STATE_PLANES, rtol=RTOL, what=""):
+    bad = []
+    for k in planes:
+        e = max_rel_plane(Fg[k], Fo[k])
+        if e > rtol:
+            bad.append((k, e))
+    assert not bad, "%s planes above %g: %s" % (what, rtol, bad)
+
+
+def assert_currents(Fg, Fo, rtol=RTOL):
+    for c in range(3):
+        d = np.abs(Fg[O.J1 + c] - Fo[O.J1 + c])
+        lim = rtol * Fo[O.JA1 + c] + 1e-300
+        assert np.all(d <= lim), ("J%d" % (c + 1), float((d / (Fo[O.JA1 + c] + 1e-300)).max()))
+
+
+def assert_particles(pg: dict, po: dict, rtol=RTOL, exact_order=True):
+    n = len(po["i1"])
+    assert len(pg["i1"]) == n
+    assert np.array_equal(pg["tag"], po["tag"])
+    for a, b in (("i1", "dx1"), ("i2", "dx2"), ("i1p", "dx1p"), ("i2p", "dx2p")):
+        xg = pg[a].astype(np.float64) + pg[b]
+        xo = po[a].astype(np.float64) + po[b]
+        err = np.abs(xg - xo) / np.maximum(1.0, np.abs(xo))
+        assert err.max(initial=0.0) <= rtol, (b, float(err.max()), int(err.argmax()))
+    for c in ("u1", "u2", "u3"):
+        scale = np.median(np.abs(po[c])) if n else 1.0
+        err = np.abs(pg[c] - po[c]) / (np.abs(po[c]) + scale + 1e-300)
+        assert err.max(initial=0.0) <= rtol, (c, float(err.max()), int(err.argmax()))
+    err = np.abs(pg["phi"] - po["phi"]) / np.maximum(1.0, np.abs(po["phi"]))
+    assert err.max(initial=0.0) <= rtol, ("phi", float(err.max()))
+    assert np.array_equal(pg["w"], po["w"]) or np.allclose(pg["w"], po["w"], rtol=rtol, atol=0)

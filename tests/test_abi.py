@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads, exports every entry point that
+include/grpic.h declares, and validates configurations on the host (no GPU needed:
+these calls do no CUDA work)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2511_17701_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "grpic.h")).read()
+    return sorted(set(re.findall(r"GRPIC_API[^;(]*?\b(grpic_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    L = B.lib()
+    names = declared()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(B.EXPORTS) == names
+
+
+def good_cfg():
+    return dict(metric="ks", a=0.9, n_r=64, n_theta=48, r_min=1.3641, r_max=10.0, cfl=0.5)
+
+
+def create(cfg, caps=(100, 100)):
+    ctx = C.c_void_p()
+    st = B.lib().grpic_create(C.byref(B.make_config(cfg, caps)), C.byref(ctx))
+    return st, ctx
+
+
+def test_create_and_arena_size():
+    st, ctx = create(good_cfg())
+    assert st == B.OK and ctx
+    nb = B.lib().grpic_arena_bytes(ctx)
+    ps = (64 + 5) * (48 + 5) * 8
+    assert nb >= 36 * ps + 32 * ps
+    assert nb % 256 == 0
+    # entry points that need a bound arena refuse politely
+    assert B.lib().grpic_init_metric(ctx) == B.ESTATE
+    assert b"grpic_bind" in B.lib().grpic_last_error(ctx)
+    assert B.lib().grpic_bind(ctx, None, nb, None) == B.EINVAL
+    assert B.lib().grpic_bind(ctx, 256, nb - 1, None) == B.ENOMEM
+    assert B.lib().grpic_bind(ctx, 1, nb, None) == B.EINVAL
+    B.lib().grpic_destroy(ctx)
+
+
+@pytest.mark.parametrize("bad", [dict(a=1.0), dict(a=-0.1), dict(n_r=2), dict(r_min=0.0),
+                                 dict(r_max=1.0), dict(n_iter=0), dict(small_angle=0.0),
+                                 dict(cfl=0.0), dict(cfl=1.5), dict(tile_r=0),
+                                 dict(n_filter=62)])
+def test_create_rejects_bad_configs(bad):
+    cfg = dict(good_cfg(), **bad)
+    st, ctx = create(cfg)
+    assert st == B.EINVAL and not ctx
+
+
+def test_create_rejects_bad_species():
+    assert create(good_cfg(), caps=())[0] == B.EINVAL
+    assert create(good_cfg(), caps=(1,) * 9)[0] == B.EINVAL
+    assert create(good_cfg(), caps=(-1,))[0] == B.EINVAL
+    assert create(good_cfg(), caps=(1 << 31,))[0] == B.EINVAL
