@@ -216,6 +216,35 @@ GRPIC_API grpic_status grpic_sort(grpic_ctx *ctx, int species);
  * push + deposit of all species, ADVANCE. */
 GRPIC_API grpic_status grpic_step(grpic_ctx *ctx, int n_steps);
 
+/* --- allocation-free sort ------------------------------------------------------- */
+
+/* Largest particle count grpic_sort_permutation_noalloc accepts. */
+#define GRPIC_NOALLOC_SORT_MAX (1 << 20)
+
+/* The paper has no counterpart to this entry point. It computes the same stable
+ * tile-major cell order as grpic_sort, but needs neither a context nor an arena: it is
+ * for callers that may not allocate device memory at all and cannot hand over scratch
+ * space either -- for example a host program whose memory manager owns every byte of the
+ * GPU through its own pool, or a time-critical loop that must not pay for the device-wide
+ * synchronisation a cudaMalloc can cause. The caller passes device arrays i1, i2, tag of
+ * n particles (as in grpic_particles, cells in [0, n_r) x [0, n_theta)) and receives on the
+ * device perm[k] = input index of the k-th particle in the sorted order (alive particles,
+ * tag 1, first and in key order, ties in input order; then the others in input order) and
+ * *n_alive, the number of alive particles. Work is queued on `stream` (cudaStream_t).
+ * Scratch lives in one file-scope device array of about 16.3 MiB, sized for
+ * GRPIC_NOALLOC_SORT_MAX particles, that every GPU using this entry point holds until the
+ * process exits. The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture. All calls on a
+ * device share the array, so calls whose work overlaps on the GPU (other streams, other
+ * host threads) race; serialise them. The entry point calls no cudaMalloc or cudaFree.
+ * Errors: GRPIC_ECAPACITY when n > GRPIC_NOALLOC_SORT_MAX, GRPIC_EINVAL for bad sizes or
+ * null pointers, GRPIC_ECUDA when a CUDA call fails. */
+GRPIC_API grpic_status grpic_sort_permutation_noalloc(int n_r, int n_theta, int tile_r,
+                                                      int tile_theta, const int32_t *i1,
+                                                      const int32_t *i2, const uint8_t *tag,
+                                                      int64_t n, uint32_t *perm,
+                                                      int64_t *n_alive, void *stream);
+
 /* --- diagnostics ------------------------------------------------------------------ */
 
 /* Per-phase device time of the hot path, measured with CUDA events recorded on the

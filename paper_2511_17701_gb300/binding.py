@@ -28,7 +28,7 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_get_particles", "grpic_species_arrays", "grpic_plane_ptr", "grpic_push",
            "grpic_deposit", "grpic_field_step", "grpic_sort", "grpic_step",
            "grpic_get_diagnostics", "grpic_set_timing", "grpic_get_timing", "grpic_last_error",
-           "grpic_destroy"]
+           "grpic_destroy", "grpic_sort_permutation_noalloc"]
 
 
 class GrpicError(RuntimeError):
@@ -111,6 +111,8 @@ def lib(build: bool = True):
         L.grpic_get_timing.argtypes = [P, C.POINTER(Timing)]
         L.grpic_last_error.argtypes = [P]
         L.grpic_last_error.restype = C.c_char_p
+        L.grpic_sort_permutation_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P,
+                                                     P, C.c_int64, P, P, P]
         L.grpic_destroy.argtypes = [P]
         L.grpic_destroy.restype = None
         _lib = L

@@ -205,3 +205,106 @@ cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDev in, SpeciesDe
   COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------------
+// grpic_sort_permutation_noalloc: the same stable cell sort, for callers that cannot
+// provide scratch memory. Its scratch (key/index ping-pong buffers, digit histograms,
+// scan sums, counters) is one file-scope device array below, shared by every call in
+// the process on a given GPU.
+// ---------------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int64_t NA_MAX = GRPIC_NOALLOC_SORT_MAX;
+constexpr int64_t NA_BLOCKS = (NA_MAX + BCHUNK - 1) / BCHUNK;
+constexpr int64_t NA_HIST = 256 * NA_BLOCKS;
+constexpr int64_t NA_BSUM = (NA_HIST + SCAN_SEG - 1) / SCAN_SEG;
+// byte offsets inside the scratch array (each a multiple of 256)
+constexpr size_t NA_OFF_KEYS0 = 0;
+constexpr size_t NA_OFF_KEYS1 = NA_OFF_KEYS0 + 4 * NA_MAX;
+constexpr size_t NA_OFF_VALS0 = NA_OFF_KEYS1 + 4 * NA_MAX;
+constexpr size_t NA_OFF_VALS1 = NA_OFF_VALS0 + 4 * NA_MAX;
+constexpr size_t NA_OFF_HIST = NA_OFF_VALS1 + 4 * NA_MAX;
+constexpr size_t NA_OFF_BSUM = NA_OFF_HIST + 4 * NA_HIST;
+constexpr size_t NA_OFF_CNT = NA_OFF_BSUM + ((4 * NA_BSUM + 255) / 256) * 256;
+constexpr size_t NA_BYTES = NA_OFF_CNT + 256;  // alive counter and element count
+
+static __device__ __align__(256) unsigned char g_sort_scratch[NA_BYTES];
+
+__global__ void k_store_count(int64_t *p, int64_t v) { *p = v; }
+
+std::mutex g_na_mutex;
+void *g_na_base[64] = {};
+
+}  // namespace
+
+extern "C" GRPIC_API grpic_status grpic_sort_permutation_noalloc(
+    int n_r, int n_theta, int tile_r, int tile_theta, const int32_t *i1, const int32_t *i2,
+    const uint8_t *tag, int64_t n, uint32_t *perm, int64_t *n_alive, void *stream) {
+  if (n_r < 1 || n_theta < 1 || tile_r < 1 || tile_theta < 1 || n < 0) return GRPIC_EINVAL;
+  if (n > NA_MAX) return GRPIC_ECAPACITY;
+  if (!n_alive || (n > 0 && (!i1 || !i2 || !tag || !perm))) return GRPIC_EINVAL;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // set-up, once per device with that device current: the device address of the
+  // scratch array (its host-side name is only a stand-in for it)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GRPIC_ECUDA;
+  unsigned char *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_base[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return GRPIC_ECUDA;
+      g_na_base[dev] = p;
+    }
+    base = static_cast<unsigned char *>(g_na_base[dev]);
+  }
+  unsigned long long *alive = reinterpret_cast<unsigned long long *>(base + NA_OFF_CNT);
+  int64_t *n_dev = reinterpret_cast<int64_t *>(base + NA_OFF_CNT + 8);
+  if (n == 0) {
+    k_store_count<<<1, 1, 0, st>>>(n_alive, 0);
+    COUNT_LAUNCH(1);
+    return cudaGetLastError() == cudaSuccess ? GRPIC_OK : GRPIC_ECUDA;
+  }
+  uint32_t *keys[2] = {reinterpret_cast<uint32_t *>(base + NA_OFF_KEYS0),
+                       reinterpret_cast<uint32_t *>(base + NA_OFF_KEYS1)};
+  uint32_t *vals[2] = {reinterpret_cast<uint32_t *>(base + NA_OFF_VALS0),
+                       reinterpret_cast<uint32_t *>(base + NA_OFF_VALS1)};
+  uint32_t *hist = reinterpret_cast<uint32_t *>(base + NA_OFF_HIST);
+  uint32_t *bsum = reinterpret_cast<uint32_t *>(base + NA_OFF_BSUM);
+  // the counter must start at zero: the array keeps the previous call's contents
+  if (cudaMemsetAsync(alive, 0, sizeof(unsigned long long), st) != cudaSuccess) return GRPIC_ECUDA;
+  k_store_count<<<1, 1, 0, st>>>(n_dev, n);
+  SpeciesDev s{};
+  s.i1 = const_cast<int32_t *>(i1);
+  s.i2 = const_cast<int32_t *>(i2);
+  s.tag = const_cast<uint8_t *>(tag);
+  s.n = n_dev;
+  const int64_t ntr = (n_r + tile_r - 1) / tile_r, ntt = (n_theta + tile_theta - 1) / tile_theta;
+  const uint64_t maxkey = (uint64_t)ntr * ntt * tile_r * tile_theta;
+  int bits = 1;
+  while (((uint64_t)1 << bits) - 1 < maxkey + 1 && bits < 32) ++bits;
+  const int passes = (bits + 7) / 8;
+  k_keys<<<grid_for(n, TPB), TPB, 0, st>>>(s, n_r, tile_r, tile_theta, keys[0], vals[0], alive);
+  const int nblocks = (int)((n + BCHUNK - 1) / BCHUNK);
+  const int64_t L = 256LL * nblocks;
+  const int64_t nseg = (L + SCAN_SEG - 1) / SCAN_SEG;
+  int cur = 0;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    k_hist<<<nblocks, TPB, 0, st>>>(keys[cur], n_dev, shift, nblocks, hist);
+    k_scan_seg<<<(int)nseg, 256, 0, st>>>(hist, L, bsum);
+    k_scan_sums<<<1, 32, 0, st>>>(bsum, nseg);
+    k_scan_add<<<(int)((L + 255) / 256), 256, 0, st>>>(hist, L, bsum);
+    k_scatter<<<nblocks, TPB, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], n_dev,
+                                       shift, nblocks, hist);
+    cur = 1 - cur;
+  }
+  COUNT_LAUNCH(2 + 5 * passes);
+  if (cudaMemcpyAsync(perm, vals[cur], (size_t)n * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return GRPIC_ECUDA;
+  k_set_n<<<1, 1, 0, st>>>(n_alive, alive);
+  COUNT_LAUNCH(1);
+  return cudaGetLastError() == cudaSuccess ? GRPIC_OK : GRPIC_ECUDA;
+}
