@@ -38,7 +38,7 @@ import workloads as W  # noqa: E402
 BYTES_PER_PARTICLE_STEP = 65 + 81
 # FP64 operations per particle-step of the same kernel, counted by ncu on this kernel
 # (2 x dfma + dmul + dadd instructions executed / particles); see profiles/.
-FP64_FLOP_PER_PARTICLE_STEP = None
+FP64_FLOP_PER_PARTICLE_STEP = 3806
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (2 DFMA / clk / SM x 152 SMs x 2.07 GHz)
 
 
@@ -211,6 +211,8 @@ def run_gpu(args, ws, rank, local):
     device = torch.device("cuda", local)
     cfg = W.grid_config(args.workload, sort_every=args.sort_every, tile_r=args.tile,
                         tile_theta=args.tile)
+    if args.ppc:
+        cfg["ppc"] = args.ppc
     pl = W.pair_plasma(cfg, seed=cfg["seed"] + 1000 * rank)
     n = pl["pos"]["i1"].size
     sim = Sim(cfg, [n, n], device=device)
@@ -336,6 +338,8 @@ def main():
     ap.add_argument("--workload", default="wald512", choices=sorted(W.CONFIGS))
     ap.add_argument("--sort-every", type=int, default=10)
     ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--ppc", type=int, default=0, help="override particles per cell per species "
+                    "(a smaller case of the same workload, e.g. for profiling)")
     ap.add_argument("--cpu-frac", type=float, default=1.0 / 16)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
