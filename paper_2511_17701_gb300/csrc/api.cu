@@ -206,6 +206,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   g.r_min = c.r_min; g.r_max = c.r_max;
   g.dxi = log(c.r_max / c.r_min) / c.n_r;
   g.dth = GRPIC_PI / c.n_theta;
+  g.ig2 = 1.0 / (g.dth * g.dth);
   g.a = c.metric == GRPIC_METRIC_KS ? c.a : 0.0;
   g.M = c.metric == GRPIC_METRIC_KS ? 1.0 : 0.0;
   g.dt = c.dt;

@@ -17,6 +17,7 @@
 struct GridP {
   int n_r, n_th, NX, NY, n_iter, n_f;
   double r_min, r_max, dxi, dth, a, M, dt, small_angle, r_absorb, absorb_coef;
+  double ig2;  // 1 / dth^2
 };
 
 // Yee point classes of the metric tables: (i, j), (i+1/2, j), (i, j+1/2), (i+1/2, j+1/2).
