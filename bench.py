@@ -152,50 +152,60 @@ def workload_desc(name, cfg, n_total):
                       cfg["ppc"], n_total, cfg["theta_T"], cfg.get("density_power", 0.0)))
 
 
-def cpu_oracle_rate(cfg, frac, steps, seed_shift=0):
-    """Oracle particle-steps/s on a bounded sample: the full grid, the particles of a
-    seeded random fraction of the cells, `steps` full PIC steps."""
+def oracle_workload(cfg, frac, seed=99):
+    """The oracle holding the workload's grid and, when frac < 1, the particles of a
+    seeded random fraction of the cells (a bounded sample)."""
     from oracle import oracle as O
-    cells = W.random_cells(cfg, max(1, int(cfg["n_r"] * cfg["n_theta"] * frac)), 99 + seed_shift)
+    cells = None
+    if frac < 1.0:
+        cells = W.random_cells(cfg, max(1, int(cfg["n_r"] * cfg["n_theta"] * frac)), seed)
     osim = O.OracleSim(cfg)
     osim.init_fields(O.FIELD_WALD, cfg["B0"])
     pl = W.pair_plasma(cfg, cells=cells)
     for s in range(2):
         osim.add_species(pl["pos"], pl["uhat"][s], pl["w0"], pl["qm"][s], pl["qc"][s],
                          pl["density_power"])
-    n = sum(s.n for s in osim.species)
-    t0 = time.perf_counter()
+    return osim
+
+
+def oracle_steps(osim, steps):
+    """Seconds of each of `steps` full oracle PIC steps, and the particles pushed."""
+    times, parts = [], 0
     for _ in range(steps):
+        parts += sum(s.n for s in osim.species)
+        t0 = time.perf_counter()
         osim.step(1)
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return n * steps / dt, cores, n, dt
+        times.append(time.perf_counter() - t0)
+    return times, parts
+
+
+def host_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     cfg = W.grid_config(args.workload)
-    frac = args.cpu_frac
-    total, per_step = 0.0, []
-    for k in range(args.warmup + args.steps):
-        rate, cores, n, dt = cpu_oracle_rate(cfg, frac, 1, seed_shift=k)
-        if k >= args.warmup:
-            per_step.append(dt)
-            total += n
-    value = total / sum(per_step)
+    frac = args.ref_frac
+    osim = oracle_workload(cfg, frac)
+    n = sum(s.n for s in osim.species)
+    oracle_steps(osim, args.warmup)
+    times, parts = oracle_steps(osim, args.steps)
+    value = parts / sum(times)
     line = {"metric": "particle-steps/s (push+deposit+field), FP64", "value": value,
             "unit": "particle-steps/s", "n_gpus": 0, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(per_step)),
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": workload_desc(args.workload, cfg,
                                                  2 * cfg["n_r"] * cfg["n_theta"] * cfg["ppc"])},
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores,
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": host_cores(),
                              "kind": "oracle",
-                             "sample": "each step: full %dx%d grid with the particles of %.1f%% "
-                                       "of the cells (%d particles)" % (
-                                           cfg["n_r"], cfg["n_theta"], 100 * frac, n)},
+                             "sample": "full %dx%d grid with the particles of %.1f%% of the "
+                                       "cells (%d particles), %d warm-up + %d timed steps" % (
+                                           cfg["n_r"], cfg["n_theta"], 100 * frac, n,
+                                           args.warmup, args.steps)},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -305,11 +315,18 @@ def run_gpu(args, ws, rank, local):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, cores, nn, dt = cpu_oracle_rate(W.grid_config(args.workload), args.cpu_frac, 1)
-        cpu = {"value": rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
-               "sample": "one full PIC step: full %dx%d grid with the particles of %.1f%% of "
-                         "the cells (%d particles), %.1f s" % (
-                             cfg["n_r"], cfg["n_theta"], 100 * args.cpu_frac, nn, dt)}
+        ocfg = W.grid_config(args.workload)
+        if args.ppc:
+            ocfg["ppc"] = args.ppc
+        osim = oracle_workload(ocfg, args.cpu_frac)
+        times, parts = oracle_steps(osim, args.cpu_steps)
+        cpu = {"value": parts / sum(times), "unit": "particle-steps/s", "cores": host_cores(),
+               "kind": "oracle",
+               "sample": "%d full PIC steps of the %s workload (%d particles%s), %.1f s" % (
+                   args.cpu_steps, args.workload, parts // max(args.cpu_steps, 1),
+                   "" if args.cpu_frac >= 1 else ", particles of %.1f%% of the cells"
+                   % (100 * args.cpu_frac), sum(times))}
+        del osim
     if rank == 0:
         line = {"metric": "particle-steps/s (push+deposit+field), FP64",
                 "value": value, "unit": "particle-steps/s", "n_gpus": ws, "steps": args.steps,
@@ -340,7 +357,11 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--ppc", type=int, default=0, help="override particles per cell per species "
                     "(a smaller case of the same workload, e.g. for profiling)")
-    ap.add_argument("--cpu-frac", type=float, default=1.0 / 16)
+    ap.add_argument("--cpu-frac", type=float, default=1.0,
+                    help="fraction of the cells whose particles the CPU baseline pushes")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--ref-frac", type=float, default=0.25,
+                    help="fraction of the cells whose particles the reference arm pushes")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

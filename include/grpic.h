@@ -99,6 +99,9 @@ typedef struct {
   int sort_every;      /* grpic_step sorts particles by cell every k steps (0: never)        */
   int tile_r, tile_theta; /* sort tile, in cells                                             */
   int precision;       /* grpic_precision                                                     */
+  int full_iterations; /* 0: the implicit pushes stop once an iterate repeats bit for bit (every
+                          later iteration would return the same bits, so the result equals the
+                          n_iter result exactly); 1: always run n_iter iterations             */
 } grpic_config;
 
 /* Pointers to one species' particle arrays (SoA, length >= n). Positions are a cell

@@ -42,7 +42,7 @@ class Config(C.Structure):
                 ("n_filter", C.c_int), ("r_absorb", C.c_double), ("absorb_coef", C.c_double),
                 ("n_species", C.c_int), ("capacity", C.c_int64 * MAX_SPECIES),
                 ("sort_every", C.c_int), ("tile_r", C.c_int), ("tile_theta", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("full_iterations", C.c_int)]
 
 
 _VP = C.c_void_p
@@ -139,6 +139,7 @@ def make_config(cfg: dict, capacities) -> Config:
     c.tile_r = int(cfg.get("tile_r", 16))
     c.tile_theta = int(cfg.get("tile_theta", 16))
     c.precision = 0
+    c.full_iterations = int(cfg.get("full_iterations", 0))
     return c
 
 

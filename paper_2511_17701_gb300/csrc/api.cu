@@ -203,6 +203,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   g.n_r = c.n_r; g.n_th = c.n_theta;
   g.NX = c.n_r + 2 * G_ + 1; g.NY = c.n_theta + 2 * G_ + 1;
   g.n_iter = c.n_iter; g.n_f = c.n_filter;
+  g.stop_on_repeat = c.full_iterations ? 0 : 1;
   g.r_min = c.r_min; g.r_max = c.r_max;
   g.dxi = log(c.r_max / c.r_min) / c.n_r;
   g.dth = GRPIC_PI / c.n_theta;

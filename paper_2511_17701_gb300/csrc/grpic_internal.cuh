@@ -16,6 +16,7 @@
 // Grid and step parameters passed by value to every kernel.
 struct GridP {
   int n_r, n_th, NX, NY, n_iter, n_f;
+  int stop_on_repeat;  // stop an implicit iteration once its iterate repeats exactly
   double r_min, r_max, dxi, dth, a, M, dt, small_angle, r_absorb, absorb_coef;
   double ig2;  // 1 / dth^2
 };

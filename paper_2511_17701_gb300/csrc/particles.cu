@@ -208,8 +208,14 @@ __device__ __forceinline__ void geodesic_momentum(const GridP &g, const Local &L
     const double ha = hdt * ig;                                        // dt / (2 u^0)
     const double k1 = fma(b0, fma(L.d1H11, b0, e2), fma(L.d1H22, b1s, e1));
     const double k2 = fma(b0, fma(L.d2H11, b0, f2), fma(L.d2H22, b1s, f1));
-    t0 = fma(b0, D1b, fma(-gb, D1a, fma(-ha, k1, u0)));
-    t1 = fma(b0, D2b, fma(-gb, D2a, fma(-ha, k2, u1)));
+    const double n0 = fma(b0, D1b, fma(-gb, D1a, fma(-ha, k1, u0)));
+    const double n1 = fma(b0, D2b, fma(-gb, D2a, fma(-ha, k2, u1)));
+    // once the iterate repeats exactly, every later iteration repeats it too (same inputs,
+    // deterministic arithmetic): stopping here returns bit for bit the n_iter result
+    const bool fixed = (n0 == t0) && (n1 == t1);
+    t0 = n0;
+    t1 = n1;
+    if (fixed && g.stop_on_repeat) break;
   }
   u[0] = t0;
   u[1] = t1;
@@ -342,8 +348,12 @@ __global__ void __launch_bounds__(TPB) k_push(GridP g, FieldPtrs F, SpeciesDev s
       const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
                        fma(o.H33 * u[2], u[2], fma(o.H13, uu0, 1.0))));
       const double ag = rsqrt(o.opz * q);  // alpha / gamma
-      t1 = fma(g.dt, fma(ag, fma(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
-      t2 = fma(g.dt, ag * o.H22 * u[1], dx2);
+      const double n1 = fma(g.dt, fma(ag, fma(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
+      const double n2 = fma(g.dt, ag * o.H22 * u[1], dx2);
+      const bool fixed = (n1 == t1) && (n2 == t2);  // exact repeat: later iterations are no-ops
+      t1 = n1;
+      t2 = n2;
+      if (fixed && g.stop_on_repeat) break;
     }
     if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(t1) &&
           isfinite(t2) && fabs(t1) < 1e6 && fabs(t2) < 1e6)) {

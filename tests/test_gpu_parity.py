@@ -232,3 +232,22 @@ def test_empty_species(torch_cuda):
     osim.step(2)
     assert_planes(g.planes(), osim.F, planes=range(12), what="empty")
     assert g.count(0) == 0
+
+
+@pytest.mark.parametrize("cfg", [BASE, RAGGED, FLAT])
+def test_stop_on_exact_repeat_is_bit_identical(torch_cuda, cfg):
+    """The implicit pushes stop once an iterate repeats bit for bit; forcing all n_iter
+    iterations must give the same bits (three pushes in frozen fields: no atomics feed
+    back, so both runs are deterministic)."""
+    osim = oracle_state(cfg, cells=None if cfg is BASE else odd_cells(cfg))
+    osim.predict()
+    g1 = gpu_from_oracle(osim)
+    g2 = gpu_from_oracle(osim, full_iterations=1)
+    for _ in range(3):
+        for s in range(2):
+            g1.push(s)
+            g2.push(s)
+    for s in range(2):
+        p1, p2 = g1.get_particles(s), g2.get_particles(s)
+        for k in p1:
+            assert np.array_equal(p1[k], p2[k]), k
