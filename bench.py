@@ -215,12 +215,11 @@ def run_gpu(args, ws, rank, local):
     import torch
 
     from paper_2511_17701_gb300 import FIELD_WALD, Sim
-    from paper_2511_17701_gb300.binding import PARTICLE_ARRAYS
 
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     cfg = W.grid_config(args.workload, sort_every=args.sort_every, tile_r=args.tile,
-                        tile_theta=args.tile)
+                        tile_theta=args.tile, precision=args.precision)
     if args.ppc:
         cfg["ppc"] = args.ppc
     pl = W.pair_plasma(cfg, seed=cfg["seed"] + 1000 * rank)
@@ -289,13 +288,13 @@ def run_gpu(args, ws, rank, local):
         for s in range(2):
             st = sim.get_particles(s)
             hs = {}
-            for k, t in PARTICLE_ARRAYS:
+            for k, t in sim.ptypes:
                 ht = torch.empty(st[k].shape, dtype=getattr(torch, np.dtype(t).name),
                                  pin_memory=True)
                 ht.numpy()[:] = st[k]
                 hs[k] = ht
             host.append((hs, len(st["i1"])))
-        bi = sum(n_s * sum(np.dtype(t).itemsize for _, t in PARTICLE_ARRAYS) for _, n_s in host)
+        bi = sum(n_s * sum(np.dtype(t).itemsize for _, t in sim.ptypes) for _, n_s in host)
         torch.cuda.synchronize(device)
         barrier(ws)
         t0 = time.perf_counter()
@@ -305,7 +304,7 @@ def run_gpu(args, ws, rank, local):
             sim.step(1)
             for s in range(2):
                 v = sim.species_views(s)
-                for k, _ in PARTICLE_ARRAYS:
+                for k, _ in sim.ptypes:
                     host[s][0][k][: v[k].numel()].copy_(v[k], non_blocking=True)
             torch.cuda.synchronize(device)
         t_e2e = time.perf_counter() - t0
@@ -329,10 +328,12 @@ def run_gpu(args, ws, rank, local):
         del osim
     if rank == 0:
         line = {"metric": "particle-steps/s (push+deposit+field), FP64",
+                "precision": args.precision,
                 "value": value, "unit": "particle-steps/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic (seeded workload generator)",
+                "dtype": "f64" if args.precision == "fp64" else "f32 (f64 within the guard cells)",
+                "data": "synthetic (seeded workload generator)",
                 "config": {"workload": workload_desc(args.workload, cfg, 2 * n),
                            "sort_every": args.sort_every, "tile": args.tile,
                            "l2": "inputs larger than L2: particle state %.2f GB" % (
@@ -355,6 +356,7 @@ def main():
     ap.add_argument("--workload", default="wald512", choices=sorted(W.CONFIGS))
     ap.add_argument("--sort-every", type=int, default=10)
     ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--ppc", type=int, default=0, help="override particles per cell per species "
                     "(a smaller case of the same workload, e.g. for profiling)")
     ap.add_argument("--cpu-frac", type=float, default=1.0,

@@ -58,7 +58,12 @@ typedef enum {
 } grpic_status;
 
 typedef enum { GRPIC_METRIC_KS0 = 0, GRPIC_METRIC_KS = 1 } grpic_metric_kind;
-typedef enum { GRPIC_FP64 = 0 } grpic_precision;
+typedef enum {
+  GRPIC_FP64 = 0,  /* FP64 state, fields and arithmetic                                  */
+  GRPIC_MIXED = 1  /* FP32 fields, momenta, offsets and currents (int32 cells); the push
+                      runs in FP64 for particles within fp64_guard_cells of the horizon
+                      or an axis, in FP32 elsewhere                                        */
+} grpic_precision;
 typedef enum {
   GRPIC_FIELD_ZERO = 0,     /* all fields zero                                    */
   GRPIC_FIELD_WALD = 1,     /* Wald vacuum field, Eq. (Wald), Sec. 4.1.2          */
@@ -102,19 +107,23 @@ typedef struct {
   int full_iterations; /* 0: the implicit pushes stop once an iterate repeats bit for bit (every
                           later iteration would return the same bits, so the result equals the
                           n_iter result exactly); 1: always run n_iter iterations             */
+  int fp64_guard_cells; /* GRPIC_MIXED: cells from the horizon and from each axis pushed in
+                           FP64 (default 4 when 0)                                            */
 } grpic_config;
 
 /* Pointers to one species' particle arrays (SoA, length >= n). Positions are a cell
  * index plus an offset in [0, 1] (Sec. 3: i1, dx1, i2, dx2); u are covariant code-unit
  * momenta u_i; phi the out-of-plane angle (Eq. discretized-geodesic-x-phi); w the
  * weight; tag 1 alive, 2 left the domain in the last push (its move is still
- * deposited), 0 dead. i1p..dx2p is the previous position (Sec. 3.2). */
+ * deposited), 0 dead. i1p..dx2p is the previous position (Sec. 3.2). The floating
+ * arrays (dx1, dx2, u1, u2, u3, phi, w, dx1p, dx2p) hold double for GRPIC_FP64 and
+ * float for GRPIC_MIXED. */
 typedef struct {
   int32_t *i1, *i2;
-  double *dx1, *dx2, *u1, *u2, *u3, *phi, *w;
+  void *dx1, *dx2, *u1, *u2, *u3, *phi, *w;
   uint8_t *tag;
   int32_t *i1p, *i2p;
-  double *dx1p, *dx2p;
+  void *dx1p, *dx2p;
 } grpic_particles;
 
 /* Initial particles for grpic_load_particles: position, momentum in the local
@@ -189,8 +198,18 @@ GRPIC_API grpic_status grpic_species_arrays(grpic_ctx *ctx, int species, grpic_p
                                   int64_t *n);
 
 /* Device pointer of a field plane inside the arena (valid until the next ADVANCE,
- * which rotates em/em0 and cur/cur0). */
-GRPIC_API grpic_status grpic_plane_ptr(grpic_ctx *ctx, int plane, double **out);
+ * which rotates em/em0 and cur/cur0); elements are double (GRPIC_FP64) or float
+ * (GRPIC_MIXED). */
+GRPIC_API grpic_status grpic_plane_ptr(grpic_ctx *ctx, int plane, void **out);
+
+/* Conserved energy and angular momentum per unit mass of each particle of a species
+ * (Sec. 2.3): E = -u_0 - (q/m) A_0, L = u_3 + (q/m) A_3 with u_0 = -alpha gamma + beta^1 u_1,
+ * A of the stationary field `kind` (GRPIC_FIELD_WALD or _VERTICAL, amplitude B0; ZERO gives
+ * the geodesic values), evaluated in FP64 at the midpoint of the previous and current
+ * positions (the velocity time level, as Sec. 4.1 does). E and L are device arrays of at
+ * least the species' count. */
+GRPIC_API grpic_status grpic_invariants(grpic_ctx *ctx, int species, int kind, double B0,
+                                        double *E, double *L);
 
 /* --- the hot path ---------------------------------------------------------------- */
 

@@ -17,6 +17,7 @@ GHOSTS = 2
 MAX_SPECIES = 8
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ECAPACITY, ENONFINITE = range(7)
+FP64, MIXED = 0, 1
 METRIC_KS0, METRIC_KS = 0, 1
 FIELD_ZERO, FIELD_WALD, FIELD_VERTICAL, FIELD_USER = range(4)
 PREDICT, ADVANCE = 0, 1
@@ -28,7 +29,7 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_get_particles", "grpic_species_arrays", "grpic_plane_ptr", "grpic_push",
            "grpic_deposit", "grpic_field_step", "grpic_sort", "grpic_step",
            "grpic_get_diagnostics", "grpic_set_timing", "grpic_get_timing", "grpic_last_error",
-           "grpic_destroy", "grpic_sort_permutation_noalloc"]
+           "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants"]
 
 
 class GrpicError(RuntimeError):
@@ -42,7 +43,8 @@ class Config(C.Structure):
                 ("n_filter", C.c_int), ("r_absorb", C.c_double), ("absorb_coef", C.c_double),
                 ("n_species", C.c_int), ("capacity", C.c_int64 * MAX_SPECIES),
                 ("sort_every", C.c_int), ("tile_r", C.c_int), ("tile_theta", C.c_int),
-                ("precision", C.c_int), ("full_iterations", C.c_int)]
+                ("precision", C.c_int), ("full_iterations", C.c_int),
+                ("fp64_guard_cells", C.c_int)]
 
 
 _VP = C.c_void_p
@@ -101,6 +103,7 @@ def lib(build: bool = True):
         L.grpic_get_particles.argtypes = [P, C.c_int, C.POINTER(Particles), C.POINTER(C.c_int64)]
         L.grpic_species_arrays.argtypes = [P, C.c_int, C.POINTER(Particles), C.POINTER(C.c_int64)]
         L.grpic_plane_ptr.argtypes = [P, C.c_int, C.POINTER(C.c_void_p)]
+        L.grpic_invariants.argtypes = [P, C.c_int, C.c_int, C.c_double, P, P]
         L.grpic_push.argtypes = [P, C.c_int]
         L.grpic_deposit.argtypes = [P]
         L.grpic_field_step.argtypes = [P, C.c_int]
@@ -138,9 +141,16 @@ def make_config(cfg: dict, capacities) -> Config:
     c.sort_every = int(cfg.get("sort_every", 0))
     c.tile_r = int(cfg.get("tile_r", 16))
     c.tile_theta = int(cfg.get("tile_theta", 16))
-    c.precision = 0
+    c.precision = MIXED if cfg.get("precision", "fp64") == "mixed" else FP64
     c.full_iterations = int(cfg.get("full_iterations", 0))
+    c.fp64_guard_cells = int(cfg.get("fp64_guard_cells", 0))
     return c
+
+
+def particle_dtypes(precision: str) -> list:
+    """(name, numpy dtype) of each particle array for a precision ("fp64" or "mixed")."""
+    f = np.float32 if precision == "mixed" else np.float64
+    return [(k, f if t == np.float64 else t) for k, t in PARTICLE_ARRAYS]
 
 
 def _ptr(a):
@@ -175,6 +185,10 @@ class Sim:
         self.NX = int(cfg["n_r"]) + 2 * GHOSTS + 1
         self.NY = int(cfg["n_theta"]) + 2 * GHOSTS + 1
         self.n_species = len(capacities)
+        self.precision = cfg.get("precision", "fp64")
+        self.ptypes = particle_dtypes(self.precision)
+        self.fdtype = np.float32 if self.precision == "mixed" else np.float64
+        self.tfdtype = torch.float32 if self.precision == "mixed" else torch.float64
         self.qm = [0.0] * self.n_species
         self.qc = [0.0] * self.n_species
 
@@ -220,7 +234,7 @@ class Sim:
     def set_particles(self, s, arrays: dict, qm, qc):
         """Full species state from host (numpy) or device (torch) arrays."""
         keep = []
-        for k, t in PARTICLE_ARRAYS:
+        for k, t in self.ptypes:
             a = arrays[k]
             if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
                 a = np.ascontiguousarray(a, dtype=t)
@@ -235,7 +249,7 @@ class Sim:
         """Copy of a species' state as numpy arrays (synchronises)."""
         n = C.c_int64()
         self._check(self.L.grpic_species_arrays(self.ctx, s, None, C.byref(n)), "species_arrays")
-        out = {k: np.empty(n.value, dtype=t) for k, t in PARTICLE_ARRAYS}
+        out = {k: np.empty(n.value, dtype=t) for k, t in self.ptypes}
         p = Particles(*[_ptr(out[k]) for k, _ in PARTICLE_ARRAYS])
         self._check(self.L.grpic_get_particles(self.ctx, s, C.byref(p), C.byref(n)), "get_particles")
         return out
@@ -250,10 +264,11 @@ class Sim:
         torch = self.torch
         p, n = Particles(), C.c_int64()
         self._check(self.L.grpic_species_arrays(self.ctx, s, C.byref(p), C.byref(n)), "species_arrays")
-        dt = {np.int32: torch.int32, np.float64: torch.float64, np.uint8: torch.uint8}
+        dt = {np.int32: torch.int32, np.float64: torch.float64, np.float32: torch.float32,
+              np.uint8: torch.uint8}
         out = {}
         base = self.arena_t.data_ptr()
-        for k, t in PARTICLE_ARRAYS:
+        for k, t in self.ptypes:
             off = getattr(p, k) - base
             size = np.dtype(t).itemsize
             out[k] = self.arena_t[off: off + n.value * size].view(dt[t])
@@ -264,18 +279,30 @@ class Sim:
         ptr = C.c_void_p()
         self._check(self.L.grpic_plane_ptr(self.ctx, k, C.byref(ptr)), "plane_ptr")
         off = ptr.value - self.arena_t.data_ptr()
-        nb = self.NX * self.NY * 8
-        return self.arena_t[off: off + nb].view(self.torch.float64).view(self.NY, self.NX)
+        nb = self.NX * self.NY * np.dtype(self.fdtype).itemsize
+        return self.arena_t[off: off + nb].view(self.tfdtype).view(self.NY, self.NX)
 
     def planes(self) -> np.ndarray:
-        """Host copy of all field planes, shape (NPLANES, NY, NX) (synchronises)."""
+        """Host copy of all field planes as float64, shape (NPLANES, NY, NX) (synchronises)."""
         self.sync()
-        return np.stack([self.plane(k).cpu().numpy() for k in range(NPLANES)])
+        return np.stack([self.plane(k).cpu().numpy().astype(np.float64) for k in range(NPLANES)])
 
     def set_planes(self, F: np.ndarray, which=range(NPLANES)):
         for k in which:
-            self.plane(k).copy_(self.torch.from_numpy(np.ascontiguousarray(F[k])))
+            self.plane(k).copy_(self.torch.from_numpy(
+                np.ascontiguousarray(F[k]).astype(self.fdtype)))
         self.sync()
+
+    def invariants(self, s, kind: int, B0: float):
+        """Conserved E and L per particle (FP64, computed on the device)."""
+        torch = self.torch
+        n = self.count(s)
+        E = torch.empty(max(n, 1), dtype=torch.float64, device=self.device)
+        L = torch.empty(max(n, 1), dtype=torch.float64, device=self.device)
+        self._check(self.L.grpic_invariants(self.ctx, s, kind, B0, E.data_ptr(), L.data_ptr()),
+                    "invariants")
+        self.sync()
+        return E[:n].cpu().numpy(), L[:n].cpu().numpy()
 
     # --- hot path -------------------------------------------------------------------
     def push(self, s):

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/grpic.h: context, arena layout, argument checks and the
 // order of launches for each entry point. No device memory is allocated here: every
-// buffer is carved out of the caller's arena.
+// buffer is carved out of the caller's arena. Each entry point dispatches on the
+// precision of the context (FP64 or mixed).
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -16,6 +17,9 @@
 namespace {
 
 constexpr size_t ALIGN = 256;
+constexpr int NARR = 14;
+// integer, floating or byte arrays of a species, in the order of grpic_particles
+constexpr int kKind[NARR] = {0, 0, 1, 1, 1, 1, 1, 1, 1, 2, 0, 0, 1, 1};
 
 struct SpeciesState {
   int64_t cap = 0, n_bound = 0;
@@ -24,10 +28,8 @@ struct SpeciesState {
   grpic_particles soa[2];
   int live = 0;
   int64_t *n_dev = nullptr;
-  size_t off_n = 0, off_soa[2][14] = {};
+  size_t off_n = 0, off_soa[2][NARR] = {};
 };
-
-constexpr size_t kElem[14] = {4, 4, 8, 8, 8, 8, 8, 8, 8, 1, 4, 4, 8, 8};
 
 size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -42,20 +44,24 @@ enum { PH_PREDICT = 0, PH_SORT, PH_PUSH, PH_DEPOSIT, PH_ADVANCE, PH_N };
 struct grpic_ctx {
   grpic_config cfg;
   GridP g;
+  bool mixed = false;
+  size_t fsz = 8;  // bytes of a floating element of fields and particles
   size_t need = 0;
   char *arena = nullptr;
   cudaStream_t stream = nullptr;
   bool bound = false, metric_ready = false, fields_ready = false;
-  // arena offsets
-  size_t off_planes = 0, off_tab = 0, off_polar = 0, off_dt = 0, off_diag = 0;
+  size_t off_planes = 0, off_tab = 0, off_polar = 0, off_dt = 0, off_diag = 0, off_ptab = 0;
   size_t off_keys[2] = {}, off_vals[2] = {}, off_hist = 0, off_bsum = 0, off_alive = 0;
+  size_t off_stage = 0;
+  int64_t load_chunk = 0;
   int64_t max_cap = 0;
-  FieldPtrs F;
+  FieldPtrsT<double> F64;
+  FieldPtrsT<float> F32;
+  PushTables tb{};
   SpeciesState sp[GRPIC_MAX_SPECIES];
   SortScratch S;
   unsigned long long *diag = nullptr;
   int64_t step = 0;
-  // optional per-phase timing with CUDA events on the bound stream
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PH_N];
   size_t ev_used[PH_N] = {};
@@ -91,33 +97,43 @@ T *at(grpic_ctx *c, size_t off) {
   return reinterpret_cast<T *>(c->arena + off);
 }
 
+size_t elem_bytes(const grpic_ctx *c, int a) {
+  return kKind[a] == 0 ? 4 : (kKind[a] == 1 ? c->fsz : 1);
+}
+
+void **slot(grpic_particles &p, int a) {
+  void **v[NARR] = {(void **)&p.i1, (void **)&p.i2, &p.dx1, &p.dx2, &p.u1, &p.u2, &p.u3,
+                    &p.phi, &p.w, (void **)&p.tag, (void **)&p.i1p, (void **)&p.i2p, &p.dx1p,
+                    &p.dx2p};
+  return v[a];
+}
+const void *cslot(const grpic_particles &p, int a) {
+  const void *v[NARR] = {p.i1, p.i2, p.dx1, p.dx2, p.u1, p.u2, p.u3,
+                         p.phi, p.w, p.tag, p.i1p, p.i2p, p.dx1p, p.dx2p};
+  return v[a];
+}
+
 void assign_species_ptrs(grpic_ctx *c, SpeciesState &s) {
-  for (int b = 0; b < 2; ++b) {
-    grpic_particles &p = s.soa[b];
-    const size_t *o = s.off_soa[b];
-    p.i1 = at<int32_t>(c, o[0]); p.i2 = at<int32_t>(c, o[1]);
-    p.dx1 = at<double>(c, o[2]); p.dx2 = at<double>(c, o[3]);
-    p.u1 = at<double>(c, o[4]); p.u2 = at<double>(c, o[5]); p.u3 = at<double>(c, o[6]);
-    p.phi = at<double>(c, o[7]); p.w = at<double>(c, o[8]);
-    p.tag = at<uint8_t>(c, o[9]);
-    p.i1p = at<int32_t>(c, o[10]); p.i2p = at<int32_t>(c, o[11]);
-    p.dx1p = at<double>(c, o[12]); p.dx2p = at<double>(c, o[13]);
-  }
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < NARR; ++a) *slot(s.soa[b], a) = c->arena + s.off_soa[b][a];
   s.n_dev = at<int64_t>(c, s.off_n);
 }
 
-SpeciesDev dev_view(const SpeciesState &s, int which) {
+template <typename T>
+SpeciesDevT<T> dev_view(const SpeciesState &s, int which) {
   const grpic_particles &p = s.soa[which];
-  SpeciesDev d;
-  d.i1 = p.i1; d.i2 = p.i2; d.dx1 = p.dx1; d.dx2 = p.dx2;
-  d.u1 = p.u1; d.u2 = p.u2; d.u3 = p.u3; d.phi = p.phi; d.w = p.w; d.tag = p.tag;
-  d.i1p = p.i1p; d.i2p = p.i2p; d.dx1p = p.dx1p; d.dx2p = p.dx2p;
+  SpeciesDevT<T> d;
+  d.i1 = p.i1; d.i2 = p.i2;
+  d.dx1 = (T *)p.dx1; d.dx2 = (T *)p.dx2;
+  d.u1 = (T *)p.u1; d.u2 = (T *)p.u2; d.u3 = (T *)p.u3;
+  d.phi = (T *)p.phi; d.w = (T *)p.w; d.tag = p.tag;
+  d.i1p = p.i1p; d.i2p = p.i2p; d.dx1p = (T *)p.dx1p; d.dx2p = (T *)p.dx2p;
   d.n = s.n_dev; d.qm = s.qm; d.qc = s.qc;
   return d;
 }
 
-double *plane_of(grpic_ctx *c, int k) {
-  FieldPtrs &F = c->F;
+template <typename T>
+T *plane_of(FieldPtrsT<T> &F, int k) {
   if (k < 3) return F.B[k];
   if (k < 6) return F.D[k - 3];
   if (k < 9) return F.B0[k - 6];
@@ -127,6 +143,30 @@ double *plane_of(grpic_ctx *c, int k) {
   if (k < 21) return F.Bn[k - 18];
   if (k < 24) return F.Bi[k - 21];
   return F.Di[k - 24];
+}
+
+template <typename T>
+void assign_fields(grpic_ctx *c, FieldPtrsT<T> &F) {
+  const size_t pb = up((size_t)plane_size(c->g) * sizeof(T));
+  T *pl[36];
+  for (int k = 0; k < 36; ++k) pl[k] = at<T>(c, c->off_planes + k * pb);
+  for (int i = 0; i < 3; ++i) {
+    F.B[i] = pl[i]; F.D[i] = pl[3 + i]; F.B0[i] = pl[6 + i]; F.D0[i] = pl[9 + i];
+    F.J[i] = pl[12 + i]; F.J0[i] = pl[15 + i]; F.Bn[i] = pl[18 + i];
+    F.Bi[i] = pl[21 + i]; F.Di[i] = pl[24 + i];
+    F.E[i] = pl[27 + i]; F.H[i] = pl[30 + i]; F.Dh[i] = pl[33 + i];
+  }
+  F.tab = at<T>(c, c->off_tab);
+  F.polar = at<T>(c, c->off_polar);
+}
+
+template <typename T>
+void rotate(FieldPtrsT<T> &F) {
+  for (int c = 0; c < 3; ++c) {
+    std::swap(F.B[c], F.B0[c]);
+    std::swap(F.D[c], F.D0[c]);
+    std::swap(F.J[c], F.J0[c]);
+  }
 }
 
 grpic_status need_bound(grpic_ctx *ctx) {
@@ -144,6 +184,11 @@ grpic_status need_fields(grpic_ctx *ctx) {
 grpic_status need_species(grpic_ctx *ctx, int s) {
   if (s < 0 || s >= ctx->cfg.n_species) return fail(ctx, GRPIC_EINVAL, "species %d out of range", s);
   return GRPIC_OK;
+}
+
+cudaError_t copy(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
 }
 
 // Records a start event on construction and a stop event on destruction when the
@@ -168,9 +213,20 @@ struct PhaseTimer {
   }
 };
 
-cudaError_t copy(void *dst, const void *src, size_t bytes, cudaStream_t st) {
-  if (bytes == 0) return cudaSuccess;
-  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
+// --- precision-dispatched pieces of the hot path
+template <typename T>
+cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, SpeciesState &sp, bool deposit) {
+  return launch_push<T>(c->g, F, dev_view<T>(sp, sp.live), c->tb, sp.n_bound, deposit, c->diag,
+                        c->stream);
+}
+template <typename T>
+cudaError_t do_zero_J(grpic_ctx *c, FieldPtrsT<T> &F) {
+  const int64_t ps = plane_size(c->g);
+  for (int i = 0; i < 3; ++i) {
+    cudaError_t e = launch_zero<T>(F.J[i], ps, c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -189,9 +245,10 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   if (!(c.small_angle > 0.0 && c.small_angle < 0.1)) return GRPIC_EINVAL;
   if (c.n_filter < 0 || c.n_filter + 2 >= c.n_r) return GRPIC_EINVAL;
   if (c.n_species < 1 || c.n_species > GRPIC_MAX_SPECIES) return GRPIC_EINVAL;
-  if (c.precision != GRPIC_FP64) return GRPIC_EINVAL;
+  if (c.precision != GRPIC_FP64 && c.precision != GRPIC_MIXED) return GRPIC_EINVAL;
   if (c.tile_r < 1 || c.tile_theta < 1 || c.sort_every < 0) return GRPIC_EINVAL;
   if (!(c.dt > 0.0) && !(c.cfl > 0.0 && c.cfl <= 1.0)) return GRPIC_EINVAL;
+  if (c.fp64_guard_cells < 0 || 2 * c.fp64_guard_cells >= c.n_theta) return GRPIC_EINVAL;
   for (int s = 0; s < c.n_species; ++s)
     if (c.capacity[s] < 0 || c.capacity[s] >= ((int64_t)1 << 31)) return GRPIC_EINVAL;
 
@@ -199,6 +256,8 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   if (!ctx) return GRPIC_ENOMEM;
   ctx->cfg = c;
   ctx->err[0] = 0;
+  ctx->mixed = c.precision == GRPIC_MIXED;
+  ctx->fsz = ctx->mixed ? 4 : 8;
   GridP &g = ctx->g;
   g.n_r = c.n_r; g.n_th = c.n_theta;
   g.NX = c.n_r + 2 * G_ + 1; g.NY = c.n_theta + 2 * G_ + 1;
@@ -214,13 +273,23 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   g.small_angle = c.small_angle;
   g.r_absorb = c.r_absorb;
   g.absorb_coef = c.absorb_coef;
+  // the FP64 guard of the mixed pusher: cells inside the horizon plus guard cells outside
+  // it, and guard cells next to each axis
+  const int guard = c.fp64_guard_cells > 0 ? c.fp64_guard_cells : 4;
+  int ih = 0;
+  if (g.M > 0.0) {
+    const double rh = 1.0 + sqrt(1.0 - g.a * g.a);
+    ih = rh > g.r_min ? (int)ceil(log(rh / g.r_min) / g.dxi) : 0;
+  }
+  ctx->tb.guard_i = ih + guard;
+  ctx->tb.guard_j = guard;
 
-  // arena layout
-  const size_t ps = (size_t)plane_size(g);
+  const size_t ps = (size_t)plane_size(g), fs = ctx->fsz;
   size_t off = 0;
-  ctx->off_planes = off; off += up(ps * 8) * 36;
-  ctx->off_tab = off;    off += up(ps * 8) * 4 * T_NQ;
-  ctx->off_polar = off;  off += up((size_t)g.NX * 8);
+  ctx->off_planes = off; off += up(ps * fs) * 36;
+  ctx->off_tab = off;    off += up(ps * fs) * 4 * T_NQ;
+  ctx->off_polar = off;  off += up((size_t)g.NX * fs);
+  ctx->off_ptab = off;   off += 3 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 4);
   ctx->off_dt = off;     off += up(64);
   ctx->off_diag = off;   off += up(DG_N * 8);
   ctx->max_cap = 1;
@@ -230,9 +299,9 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
     if (sp.cap > ctx->max_cap) ctx->max_cap = sp.cap;
     sp.off_n = off; off += up(8);
     for (int b = 0; b < 2; ++b)
-      for (int a = 0; a < 14; ++a) {
+      for (int a = 0; a < NARR; ++a) {
         sp.off_soa[b][a] = off;
-        off += up((size_t)(sp.cap > 0 ? sp.cap : 1) * kElem[a]);
+        off += up((size_t)(sp.cap > 0 ? sp.cap : 1) * elem_bytes(ctx, a));
       }
   }
   for (int b = 0; b < 2; ++b) {
@@ -242,6 +311,8 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   ctx->off_hist = off;  off += up((size_t)sort_hist_entries(ctx->max_cap) * 4);
   ctx->off_bsum = off;  off += up((size_t)sort_bsum_entries(ctx->max_cap) * 4);
   ctx->off_alive = off; off += up(8);
+  ctx->load_chunk = ctx->max_cap < ((int64_t)1 << 20) ? ctx->max_cap : ((int64_t)1 << 20);
+  ctx->off_stage = off; off += 6 * up((size_t)ctx->load_chunk * 8);
   ctx->need = off;
   *out = ctx;
   return GRPIC_OK;
@@ -257,19 +328,12 @@ grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream)
     return fail(ctx, GRPIC_ENOMEM, "arena has %zu bytes, %zu needed", bytes, ctx->need);
   ctx->arena = static_cast<char *>(arena);
   ctx->stream = static_cast<cudaStream_t>(stream);
-  const size_t ps = (size_t)plane_size(ctx->g);
-  const size_t pb = up(ps * 8);
-  double *pl[36];
-  for (int k = 0; k < 36; ++k) pl[k] = at<double>(ctx, ctx->off_planes + k * pb);
-  FieldPtrs &F = ctx->F;
-  for (int c = 0; c < 3; ++c) {
-    F.B[c] = pl[c]; F.D[c] = pl[3 + c]; F.B0[c] = pl[6 + c]; F.D0[c] = pl[9 + c];
-    F.J[c] = pl[12 + c]; F.J0[c] = pl[15 + c]; F.Bn[c] = pl[18 + c];
-    F.Bi[c] = pl[21 + c]; F.Di[c] = pl[24 + c];
-    F.E[c] = pl[27 + c]; F.H[c] = pl[30 + c]; F.Dh[c] = pl[33 + c];
-  }
-  F.tab = at<double>(ctx, ctx->off_tab);
-  F.polar = at<double>(ctx, ctx->off_polar);
+  if (ctx->mixed) assign_fields(ctx, ctx->F32);
+  else assign_fields(ctx, ctx->F64);
+  const size_t tstride = up((size_t)(ctx->g.NX > ctx->g.NY ? ctx->g.NX : ctx->g.NY) * 4);
+  ctx->tb.r = at<float>(ctx, ctx->off_ptab);
+  ctx->tb.s = at<float>(ctx, ctx->off_ptab + tstride);
+  ctx->tb.c = at<float>(ctx, ctx->off_ptab + 2 * tstride);
   ctx->diag = at<unsigned long long>(ctx, ctx->off_diag);
   for (int s = 0; s < ctx->cfg.n_species; ++s) assign_species_ptrs(ctx, ctx->sp[s]);
   SortScratch &S = ctx->S;
@@ -293,9 +357,15 @@ grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream)
 grpic_status grpic_init_metric(grpic_ctx *ctx) {
   grpic_status s = need_bound(ctx);
   if (s) return s;
-  FieldPtrs &F = ctx->F;
-  CK(launch_metric_tables(ctx->g, const_cast<double *>(F.tab), const_cast<double *>(F.polar),
-                          ctx->stream));
+  if (ctx->mixed) {
+    CK(launch_metric_tables<float>(ctx->g, const_cast<float *>(ctx->F32.tab),
+                                   const_cast<float *>(ctx->F32.polar), ctx->stream));
+  } else {
+    CK(launch_metric_tables<double>(ctx->g, const_cast<double *>(ctx->F64.tab),
+                                    const_cast<double *>(ctx->F64.polar), ctx->stream));
+  }
+  CK(launch_push_tables(ctx->g, const_cast<float *>(ctx->tb.r), const_cast<float *>(ctx->tb.s),
+                        const_cast<float *>(ctx->tb.c), ctx->stream));
   if (!(ctx->cfg.dt > 0.0)) {
     double dmin = 0.0;
     CK(launch_dt_min(ctx->g, at<double>(ctx, ctx->off_dt), 8, &dmin, ctx->stream));
@@ -316,8 +386,13 @@ grpic_status grpic_init_fields(grpic_ctx *ctx, int kind, double B0) {
   if (s) return s;
   if (!ctx->metric_ready) return fail(ctx, GRPIC_ESTATE, "metric not initialised");
   if (kind < GRPIC_FIELD_ZERO || kind > GRPIC_FIELD_USER) return fail(ctx, GRPIC_EINVAL, "bad field kind");
-  if (kind != GRPIC_FIELD_USER) CK(launch_init_fields(ctx->g, ctx->F, kind, B0, ctx->stream));
-  CK(launch_field_finish_init(ctx->g, ctx->F, kind == GRPIC_FIELD_USER, ctx->stream));
+  if (ctx->mixed) {
+    if (kind != GRPIC_FIELD_USER) CK(launch_init_fields<float>(ctx->g, ctx->F32, kind, B0, ctx->stream));
+    CK(launch_field_finish_init<float>(ctx->g, ctx->F32, kind == GRPIC_FIELD_USER, ctx->stream));
+  } else {
+    if (kind != GRPIC_FIELD_USER) CK(launch_init_fields<double>(ctx->g, ctx->F64, kind, B0, ctx->stream));
+    CK(launch_field_finish_init<double>(ctx->g, ctx->F64, kind == GRPIC_FIELD_USER, ctx->stream));
+  }
   ctx->fields_ready = true;
   ctx->step = 0;
   return GRPIC_OK;
@@ -335,19 +410,26 @@ grpic_status grpic_load_particles(grpic_ctx *ctx, int species, int64_t n, double
     return fail(ctx, GRPIC_EINVAL, "null particle array");
   sp.qm = qm; sp.qc = qc;
   const grpic_particles &L = sp.soa[sp.live];
-  const grpic_particles &T = sp.soa[1 - sp.live];  // staging for the momenta and weights
   const cudaStream_t st = ctx->stream;
   CK(copy(L.i1, in->i1, n * 4, st));
   CK(copy(L.i2, in->i2, n * 4, st));
-  CK(copy(L.dx1, in->dx1, n * 8, st));
-  CK(copy(L.dx2, in->dx2, n * 8, st));
-  CK(copy(T.u1, in->uh1, n * 8, st));
-  CK(copy(T.u2, in->uh2, n * 8, st));
-  CK(copy(T.u3, in->uh3, n * 8, st));
-  CK(copy(T.w, in->w0, n * 8, st));
-  grpic_particle_init dv = *in;
-  dv.uh1 = T.u1; dv.uh2 = T.u2; dv.uh3 = T.u3; dv.w0 = T.w;
-  CK(launch_load(ctx->g, dev_view(sp, sp.live), n, dv, density_power, st));
+  // the FP64 inputs go through a staging region of LOAD_CHUNK particles (host or device
+  // sources), then one kernel converts each chunk into the species arrays
+  double *stg = at<double>(ctx, ctx->off_stage);
+  for (int64_t k0 = 0; k0 < n; k0 += ctx->load_chunk) {
+    const int64_t m = n - k0 < ctx->load_chunk ? n - k0 : ctx->load_chunk;
+    const double *src[6] = {in->dx1, in->dx2, in->uh1, in->uh2, in->uh3, in->w0};
+    for (int a = 0; a < 6; ++a)
+      CK(copy(stg + a * ctx->load_chunk, src[a] + k0, (size_t)m * 8, st));
+    grpic_particle_init dv = *in;
+    dv.dx1 = stg; dv.dx2 = stg + ctx->load_chunk; dv.uh1 = stg + 2 * ctx->load_chunk;
+    dv.uh2 = stg + 3 * ctx->load_chunk; dv.uh3 = stg + 4 * ctx->load_chunk;
+    dv.w0 = stg + 5 * ctx->load_chunk;
+    if (ctx->mixed)
+      CK(launch_load<float>(ctx->g, dev_view<float>(sp, sp.live), k0, m, dv, density_power, st));
+    else
+      CK(launch_load<double>(ctx->g, dev_view<double>(sp, sp.live), k0, m, dv, density_power, st));
+  }
   k_set_i64<<<1, 1, 0, st>>>(sp.n_dev, n);
   COUNT_LAUNCH(1);
   CK(cudaGetLastError());
@@ -365,16 +447,13 @@ grpic_status grpic_set_particles(grpic_ctx *ctx, int species, int64_t n, double 
   if (n < 0 || n > sp.cap) return fail(ctx, GRPIC_ECAPACITY, "%lld particles, capacity %lld", (long long)n, (long long)sp.cap);
   if (n > 0 && !in) return fail(ctx, GRPIC_EINVAL, "null particle arrays");
   sp.qm = qm; sp.qc = qc;
-  const grpic_particles &L = sp.soa[sp.live];
+  grpic_particles &L = sp.soa[sp.live];
   const cudaStream_t st = ctx->stream;
   if (n > 0) {
-    const void *src[14] = {in->i1, in->i2, in->dx1, in->dx2, in->u1, in->u2, in->u3,
-                           in->phi, in->w, in->tag, in->i1p, in->i2p, in->dx1p, in->dx2p};
-    void *dst[14] = {L.i1, L.i2, L.dx1, L.dx2, L.u1, L.u2, L.u3,
-                     L.phi, L.w, L.tag, L.i1p, L.i2p, L.dx1p, L.dx2p};
-    for (int a = 0; a < 14; ++a) {
-      if (!src[a]) return fail(ctx, GRPIC_EINVAL, "null particle array %d", a);
-      CK(copy(dst[a], src[a], (size_t)n * kElem[a], st));
+    for (int a = 0; a < NARR; ++a) {
+      const void *src = cslot(*in, a);
+      if (!src) return fail(ctx, GRPIC_EINVAL, "null particle array %d", a);
+      CK(copy(*slot(L, a), src, (size_t)n * elem_bytes(ctx, a), st));
     }
   }
   k_set_i64<<<1, 1, 0, st>>>(sp.n_dev, n);
@@ -405,21 +484,36 @@ grpic_status grpic_get_particles(grpic_ctx *ctx, int species, grpic_particles *o
   if (s) return s;
   if (n) *n = cnt;
   if (!out) return GRPIC_OK;
-  const void *src[14] = {L.i1, L.i2, L.dx1, L.dx2, L.u1, L.u2, L.u3,
-                         L.phi, L.w, L.tag, L.i1p, L.i2p, L.dx1p, L.dx2p};
-  void *dst[14] = {out->i1, out->i2, out->dx1, out->dx2, out->u1, out->u2, out->u3,
-                   out->phi, out->w, out->tag, out->i1p, out->i2p, out->dx1p, out->dx2p};
-  for (int a = 0; a < 14; ++a)
-    if (dst[a]) CK(copy(dst[a], src[a], (size_t)cnt * kElem[a], ctx->stream));
+  for (int a = 0; a < NARR; ++a) {
+    void *dst = *slot(*out, a);
+    if (dst) CK(copy(dst, cslot(L, a), (size_t)cnt * elem_bytes(ctx, a), ctx->stream));
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   return GRPIC_OK;
 }
 
-grpic_status grpic_plane_ptr(grpic_ctx *ctx, int plane, double **out) {
+grpic_status grpic_plane_ptr(grpic_ctx *ctx, int plane, void **out) {
   grpic_status s = need_bound(ctx);
   if (s) return s;
   if (plane < 0 || plane >= GRPIC_NPLANES || !out) return fail(ctx, GRPIC_EINVAL, "bad plane %d", plane);
-  *out = plane_of(ctx, plane);
+  *out = ctx->mixed ? (void *)plane_of(ctx->F32, plane) : (void *)plane_of(ctx->F64, plane);
+  return GRPIC_OK;
+}
+
+grpic_status grpic_invariants(grpic_ctx *ctx, int species, int kind, double B0, double *E,
+                              double *L) {
+  grpic_status s = need_bound(ctx);
+  if (s) return s;
+  if ((s = need_species(ctx, species))) return s;
+  if (!ctx->metric_ready) return fail(ctx, GRPIC_ESTATE, "metric not initialised");
+  if (!E || !L) return fail(ctx, GRPIC_EINVAL, "null output");
+  SpeciesState &sp = ctx->sp[species];
+  if (ctx->mixed)
+    CK(launch_invariants<float>(ctx->g, dev_view<float>(sp, sp.live), kind, B0, E, L, sp.n_bound,
+                                ctx->stream));
+  else
+    CK(launch_invariants<double>(ctx->g, dev_view<double>(sp, sp.live), kind, B0, E, L,
+                                 sp.n_bound, ctx->stream));
   return GRPIC_OK;
 }
 
@@ -430,7 +524,8 @@ grpic_status grpic_push(grpic_ctx *ctx, int species) {
   SpeciesState &sp = ctx->sp[species];
   if (!sp.loaded) return fail(ctx, GRPIC_ESTATE, "species %d has no particles", species);
   PhaseTimer t(ctx, PH_PUSH);
-  CK(launch_push(ctx->g, ctx->F, dev_view(sp, sp.live), sp.n_bound, false, ctx->diag, ctx->stream));
+  if (ctx->mixed) CK(do_push(ctx, ctx->F32, sp, false));
+  else CK(do_push(ctx, ctx->F64, sp, false));
   ++ctx->push_calls;
   return GRPIC_OK;
 }
@@ -438,24 +533,20 @@ grpic_status grpic_push(grpic_ctx *ctx, int species) {
 grpic_status grpic_deposit(grpic_ctx *ctx) {
   grpic_status s = need_fields(ctx);
   if (s) return s;
-  const int64_t ps = plane_size(ctx->g);
   PhaseTimer t(ctx, PH_DEPOSIT);
-  for (int c = 0; c < 3; ++c) CK(launch_zero(ctx->F.J[c], ps, ctx->stream));
+  if (ctx->mixed) CK(do_zero_J(ctx, ctx->F32));
+  else CK(do_zero_J(ctx, ctx->F64));
   for (int k = 0; k < ctx->cfg.n_species; ++k) {
     SpeciesState &sp = ctx->sp[k];
     if (!sp.loaded) continue;
-    CK(launch_deposit(ctx->g, ctx->F, dev_view(sp, sp.live), sp.n_bound, ctx->stream));
+    if (ctx->mixed)
+      CK(launch_deposit<float>(ctx->g, ctx->F32, dev_view<float>(sp, sp.live), ctx->tb,
+                               sp.n_bound, ctx->stream));
+    else
+      CK(launch_deposit<double>(ctx->g, ctx->F64, dev_view<double>(sp, sp.live), ctx->tb,
+                                sp.n_bound, ctx->stream));
   }
   return GRPIC_OK;
-}
-
-static void rotate(grpic_ctx *ctx) {
-  FieldPtrs &F = ctx->F;
-  for (int c = 0; c < 3; ++c) {
-    double *t = F.B[c]; F.B[c] = F.B0[c]; F.B0[c] = t;
-    t = F.D[c]; F.D[c] = F.D0[c]; F.D0[c] = t;
-    t = F.J[c]; F.J[c] = F.J0[c]; F.J0[c] = t;
-  }
 }
 
 grpic_status grpic_field_step(grpic_ctx *ctx, int phase) {
@@ -463,11 +554,17 @@ grpic_status grpic_field_step(grpic_ctx *ctx, int phase) {
   if (s) return s;
   if (phase == GRPIC_PREDICT) {
     PhaseTimer t(ctx, PH_PREDICT);
-    CK(launch_predict(ctx->g, ctx->F, ctx->stream));
+    if (ctx->mixed) CK(launch_predict<float>(ctx->g, ctx->F32, ctx->stream));
+    else CK(launch_predict<double>(ctx->g, ctx->F64, ctx->stream));
   } else if (phase == GRPIC_ADVANCE) {
     PhaseTimer t(ctx, PH_ADVANCE);
-    CK(launch_advance(ctx->g, ctx->F, ctx->stream));
-    rotate(ctx);  // em <- (B^{n+1/2}, D^{n+1}), em0 <- (B^{n-1/2}, D^n), cur0 <- J^{n+1/2}
+    if (ctx->mixed) {
+      CK(launch_advance<float>(ctx->g, ctx->F32, ctx->stream));
+      rotate(ctx->F32);
+    } else {
+      CK(launch_advance<double>(ctx->g, ctx->F64, ctx->stream));
+      rotate(ctx->F64);  // em <- (B^{n+1/2}, D^{n+1}), em0 <- (B^{n-1/2}, D^n), cur0 <- J^{n+1/2}
+    }
   } else {
     return fail(ctx, GRPIC_EINVAL, "bad phase %d", phase);
   }
@@ -481,8 +578,14 @@ grpic_status grpic_sort(grpic_ctx *ctx, int species) {
   SpeciesState &sp = ctx->sp[species];
   if (!sp.loaded) return GRPIC_OK;
   PhaseTimer t(ctx, PH_SORT);
-  CK(launch_sort(ctx->g, ctx->cfg.tile_r, ctx->cfg.tile_theta, dev_view(sp, sp.live),
-                 dev_view(sp, 1 - sp.live), sp.n_bound, sp.n_dev, ctx->S, ctx->stream));
+  if (ctx->mixed)
+    CK(launch_sort<float>(ctx->g, ctx->cfg.tile_r, ctx->cfg.tile_theta, dev_view<float>(sp, sp.live),
+                          dev_view<float>(sp, 1 - sp.live), sp.n_bound, sp.n_dev, ctx->S,
+                          ctx->stream));
+  else
+    CK(launch_sort<double>(ctx->g, ctx->cfg.tile_r, ctx->cfg.tile_theta,
+                           dev_view<double>(sp, sp.live), dev_view<double>(sp, 1 - sp.live),
+                           sp.n_bound, sp.n_dev, ctx->S, ctx->stream));
   sp.live = 1 - sp.live;
   return GRPIC_OK;
 }
@@ -491,31 +594,37 @@ grpic_status grpic_step(grpic_ctx *ctx, int n_steps) {
   grpic_status s = need_fields(ctx);
   if (s) return s;
   if (n_steps < 0) return fail(ctx, GRPIC_EINVAL, "negative step count");
-  const int64_t ps = plane_size(ctx->g);
   for (int n = 0; n < n_steps; ++n) {
     {
       PhaseTimer t(ctx, PH_PREDICT);
-      CK(launch_predict(ctx->g, ctx->F, ctx->stream));
+      if (ctx->mixed) CK(launch_predict<float>(ctx->g, ctx->F32, ctx->stream));
+      else CK(launch_predict<double>(ctx->g, ctx->F64, ctx->stream));
     }
     if (ctx->cfg.sort_every > 0 && ctx->step % ctx->cfg.sort_every == 0)
       for (int k = 0; k < ctx->cfg.n_species; ++k)
         if ((s = grpic_sort(ctx, k))) return s;
     {
       PhaseTimer t(ctx, PH_PUSH);  // fused push + deposit of every species
-      for (int c = 0; c < 3; ++c) CK(launch_zero(ctx->F.J[c], ps, ctx->stream));
+      if (ctx->mixed) CK(do_zero_J(ctx, ctx->F32));
+      else CK(do_zero_J(ctx, ctx->F64));
       for (int k = 0; k < ctx->cfg.n_species; ++k) {
         SpeciesState &sp = ctx->sp[k];
         if (!sp.loaded) continue;
-        CK(launch_push(ctx->g, ctx->F, dev_view(sp, sp.live), sp.n_bound, true, ctx->diag,
-                       ctx->stream));
+        if (ctx->mixed) CK(do_push(ctx, ctx->F32, sp, true));
+        else CK(do_push(ctx, ctx->F64, sp, true));
         ++ctx->push_calls;
       }
     }
     {
       PhaseTimer t(ctx, PH_ADVANCE);
-      CK(launch_advance(ctx->g, ctx->F, ctx->stream));
+      if (ctx->mixed) {
+        CK(launch_advance<float>(ctx->g, ctx->F32, ctx->stream));
+        rotate(ctx->F32);
+      } else {
+        CK(launch_advance<double>(ctx->g, ctx->F64, ctx->stream));
+        rotate(ctx->F64);
+      }
     }
-    rotate(ctx);
     ++ctx->step;
   }
   return GRPIC_OK;

@@ -9,8 +9,8 @@ namespace {
 
 constexpr int TPB = 256;
 
-__device__ __forceinline__ double tabv(const double *tab, const GridP &g, int cls, int q, int i,
-                                       int j) {
+template <typename T>
+__device__ __forceinline__ T tabv(const T *tab, const GridP &g, int cls, int q, int i, int j) {
   return __ldg(tab + ((int64_t)(cls * T_NQ + q)) * plane_size(g) + sidx(g, i, j));
 }
 
@@ -19,7 +19,8 @@ __device__ __forceinline__ double tabv(const double *tab, const GridP &g, int cl
 // [sqrt(h~ h) beta^1], 1/sqrt(h) at every stored point; the polar area
 // A(x1) = dr (r^2 + a^2) sqrt(1 + 2 M r/(r^2 + a^2)) (1 - cos(dtheta/2)) (App. A, per unit phi).
 // ---------------------------------------------------------------------------------
-__global__ void k_metric_tables(GridP g, double *tab, double *polar) {
+template <typename T>
+__global__ void k_metric_tables(GridP g, T *tab, T *polar) {
   const int64_t ps = plane_size(g);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 4 * ps;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -30,19 +31,19 @@ __global__ void k_metric_tables(GridP g, double *tab, double *polar) {
     const double s2 = (cls == CLS_NH || cls == CLS_HH) ? 0.5 : 0.0;
     MetricV m;
     metric_eval<false>(g, i + s1, j + s2, false, m, nullptr);
-    double *o = tab + (int64_t)cls * T_NQ * ps + q;
-    o[T_ALPHA * ps] = m.alpha;
-    o[T_H11 * ps] = m.h11;
-    o[T_H22 * ps] = m.h22;
-    o[T_H33 * ps] = m.h33;
-    o[T_SHT * ps] = m.sqrt_ht;
-    o[T_WT13 * ps] = m.sqrt_ht * m.h13;
-    o[T_WB1 * ps] = m.sqrt_ht * m.sqrt_h * m.beta1;
-    o[T_ISH * ps] = 1.0 / m.sqrt_h;
+    T *o = tab + (int64_t)cls * T_NQ * ps + q;
+    o[T_ALPHA * ps] = (T)m.alpha;
+    o[T_H11 * ps] = (T)m.h11;
+    o[T_H22 * ps] = (T)m.h22;
+    o[T_H33 * ps] = (T)m.h33;
+    o[T_SHT * ps] = (T)m.sqrt_ht;
+    o[T_WT13 * ps] = (T)(m.sqrt_ht * m.h13);
+    o[T_WB1 * ps] = (T)(m.sqrt_ht * m.sqrt_h * m.beta1);
+    o[T_ISH * ps] = (T)(1.0 / m.sqrt_h);
     if (cls == CLS_HN && j == 0) {
       const double r = g.r_min * exp((i + 0.5) * g.dxi), a2 = g.a * g.a;
-      polar[i + G_] = g.dxi * r * (r * r + a2) * sqrt(1.0 + 2.0 * g.M * r / (r * r + a2)) *
-                      (1.0 - cos(0.5 * g.dth));
+      polar[i + G_] = (T)(g.dxi * r * (r * r + a2) * sqrt(1.0 + 2.0 * g.M * r / (r * r + a2)) *
+                          (1.0 - cos(0.5 * g.dth)));
     }
   }
 }
@@ -71,49 +72,6 @@ __global__ void k_dt_min(GridP g, unsigned long long *out) {
   if (threadIdx.x == 0) atomicMin(out, sm[0]);
 }
 
-// ---------------------------------------------------------------------------------
-// Stationary potentials: Wald (Eq. Wald) and its zero-spin limit, and their
-// derivatives in code coordinates, written from the physical (r, theta) closed forms.
-// ---------------------------------------------------------------------------------
-struct Pot {
-  double A0, A1, A3;              // A_0, A_1 (code), A_3
-  double d1A0, d2A0, d1A3, d2A1;  // the derivatives the fields need
-};
-
-__device__ void potential(const GridP &g, int kind, double B0, double x1, double x2, bool derivs,
-                          Pot &p) {
-  const double a = g.a, M = g.M, a2 = a * a;
-  const double r = g.r_min * exp(x1 * g.dxi), th = x2 * g.dth;
-  double s, c;
-  sincos(th, &s, &c);
-  const double s2 = s * s, f = g.dxi * r, gg = g.dth;
-  if (kind == GRPIC_FIELD_VERTICAL) {
-    p.A0 = 0.0; p.A1 = 0.0; p.A3 = 0.5 * B0 * r * r * s2;
-    p.d1A0 = p.d2A0 = p.d2A1 = 0.0;
-    p.d1A3 = f * B0 * r * s2;
-    return;
-  }
-  const double Sig = r * r + a2 * c * c, Del = r * r - 2.0 * M * r + a2;
-  const double A = (r * r + a2) * (r * r + a2) - a2 * Del * s2;
-  const double z = 2.0 * M * r / Sig;
-  // physical Wald potential: A_t = (B0 a / 2)(z (2 - s^2) - 2), A_r = (B0 a / 2)(2 z - (1+z) s^2),
-  // A_phi = (B0 / 2)(A s^2 / Sigma - 2 a^2 z s^2)
-  const double hb = 0.5 * B0;
-  p.A0 = hb * a * (z * (2.0 - s2) - 2.0);
-  p.A1 = f * hb * a * (2.0 * z - (1.0 + z) * s2);
-  p.A3 = hb * (A * s2 / Sig - 2.0 * a2 * z * s2);
-  if (!derivs) return;
-  const double drS = 2.0 * r, dtS = -2.0 * a2 * s * c;
-  const double drz = 2.0 * M * (Sig - r * drS) / (Sig * Sig);
-  const double dtz = -2.0 * M * r * dtS / (Sig * Sig);
-  const double drA = 4.0 * r * (r * r + a2) - a2 * s2 * (2.0 * r - 2.0 * M);
-  const double dts2 = 2.0 * s * c;
-  p.d1A0 = f * hb * a * drz * (2.0 - s2);
-  p.d2A0 = gg * hb * a * (dtz * (2.0 - s2) - z * dts2);
-  p.d1A3 = f * hb * (s2 * (drA * Sig - A * drS) / (Sig * Sig) - 2.0 * a2 * s2 * drz);
-  p.d2A1 = gg * f * hb * a * (2.0 * dtz - dtz * s2 - (1.0 + z) * dts2);
-}
-
 // D at a Yee point from the inverse of Eq. (aux) with E_i = d_i A_0, E_3 = 0 and
 // sqrt(h) B^2 = -d_1 A_3, sqrt(h) B^3 = -d_2 A_1 (no division by sqrt(h) on the axis).
 __device__ void d_from_potential(const GridP &g, int kind, double B0, double x1, double x2,
@@ -127,7 +85,14 @@ __device__ void d_from_potential(const GridP &g, int kind, double B0, double x1,
   else out = (m.H13 * p.d1A0 + m.H33 * m.beta1 * p.d1A3) / m.alpha;
 }
 
-__global__ void k_init_fields(GridP g, FieldPtrs F, int kind, double B0) {
+__device__ double inv_sqrt_h(const GridP &g, double x1, double x2) {
+  MetricV m;
+  metric_eval<false>(g, x1, x2, false, m, nullptr);
+  return 1.0 / m.sqrt_h;
+}
+
+template <typename T>
+__global__ void k_init_fields(GridP g, FieldPtrsT<T> F, int kind, double B0) {
   const int ni = g.n_r + 2 * G_ + 1, nj = g.n_th + 1;
   const int64_t n = (int64_t)ni * nj;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
@@ -139,22 +104,28 @@ __global__ void k_init_fields(GridP g, FieldPtrs F, int kind, double B0) {
     if (j < g.n_th) {
       potential(g, kind, B0, i, j, false, pa);
       potential(g, kind, B0, i, j + 1, false, pb);
-      F.B[0][k] = (pb.A3 - pa.A3) * tabv(F.tab, g, CLS_NH, T_ISH, i, j);
+      F.B[0][k] = (T)((pb.A3 - pa.A3) * inv_sqrt_h(g, i, j + 0.5));
       potential(g, kind, B0, i + 0.5, j, false, pa);
       potential(g, kind, B0, i + 0.5, j + 1, false, pb);
-      F.B[2][k] = -(pb.A1 - pa.A1) * tabv(F.tab, g, CLS_HH, T_ISH, i, j);
-      d_from_potential(g, kind, B0, i, j + 0.5, 1, F.D[1][k]);
+      F.B[2][k] = (T)(-(pb.A1 - pa.A1) * inv_sqrt_h(g, i + 0.5, j + 0.5));
+      double d;
+      d_from_potential(g, kind, B0, i, j + 0.5, 1, d);
+      F.D[1][k] = (T)d;
     }
     if (!axis) {
       potential(g, kind, B0, i, j, false, pa);
       potential(g, kind, B0, i + 1, j, false, pb);
-      F.B[1][k] = -(pb.A3 - pa.A3) * tabv(F.tab, g, CLS_HN, T_ISH, i, j);
-      d_from_potential(g, kind, B0, i, j, 2, F.D[2][k]);
+      F.B[1][k] = (T)(-(pb.A3 - pa.A3) * inv_sqrt_h(g, i + 0.5, j));
+      double d;
+      d_from_potential(g, kind, B0, i, j, 2, d);
+      F.D[2][k] = (T)d;
     } else {
-      F.B[1][k] = 0.0;
-      F.D[2][k] = 0.0;
+      F.B[1][k] = (T)0;
+      F.D[2][k] = (T)0;
     }
-    d_from_potential(g, kind, B0, i + 0.5, j, 0, F.D[0][k]);
+    double d0;
+    d_from_potential(g, kind, B0, i + 0.5, j, 0, d0);
+    F.D[0][k] = (T)d0;
   }
 }
 
@@ -162,7 +133,8 @@ __global__ void k_init_fields(GridP g, FieldPtrs F, int kind, double B0) {
 // Boundary conditions (Sec. 3.3.3).
 // ---------------------------------------------------------------------------------
 // Horizon layer: cells i1 in [-G, n_f] copy cell n_f + 1, all rows.
-__global__ void k_horizon(GridP g, double *p0, double *p1, double *p2) {
+template <typename T>
+__global__ void k_horizon(GridP g, T *p0, T *p1, T *p2) {
   const int nl = g.n_f + 1 + G_, nj = g.NY;
   const int64_t n = (int64_t)nl * nj * 3;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
@@ -170,7 +142,7 @@ __global__ void k_horizon(GridP g, double *p0, double *p1, double *p2) {
     const int c = (int)(t / ((int64_t)nl * nj));
     const int64_t q = t - c * (int64_t)nl * nj;
     const int i = (int)(q % nl) - G_, j = (int)(q / nl) - G_;
-    double *p = c == 0 ? p0 : (c == 1 ? p1 : p2);
+    T *p = c == 0 ? p0 : (c == 1 ? p1 : p2);
     p[sidx(g, i, j)] = p[sidx(g, g.n_f + 1, j)];
   }
 }
@@ -178,7 +150,8 @@ __global__ void k_horizon(GridP g, double *p0, double *p1, double *p2) {
 // Axis ghost rows by reflection (Fig. 1): r components even, theta and phi components
 // odd; half rows (x2 = j + 1/2) and node rows mirror differently. isB selects the B
 // classes (B^1 half, B^2 node, B^3 half) or the D classes (D^1 node, D^2 half, D^3 node).
-__global__ void k_axis(GridP g, double *p0, double *p1, double *p2, int isB) {
+template <typename T>
+__global__ void k_axis(GridP g, T *p0, T *p1, T *p2, int isB) {
   const int ni = g.NX;
   const int nrow = 2 * G_ + 1;  // rows written per component (2 below, 3 above)
   const int64_t n = (int64_t)ni * nrow * 3;
@@ -187,9 +160,9 @@ __global__ void k_axis(GridP g, double *p0, double *p1, double *p2, int isB) {
     const int c = (int)(t / ((int64_t)ni * nrow));
     const int64_t q = t - c * (int64_t)ni * nrow;
     const int i = (int)(q % ni) - G_, rr = (int)(q / ni);
-    double *p = c == 0 ? p0 : (c == 1 ? p1 : p2);
+    T *p = c == 0 ? p0 : (c == 1 ? p1 : p2);
     const bool half = isB ? (c != 1) : (c == 1);
-    const double par = (c == 0) ? 1.0 : -1.0;
+    const T par = (c == 0) ? (T)1 : (T)-1;
     const int N = g.n_th;
     if (!half) {
       if (rr < G_) {  // rows -1, -2 from 1, 2
@@ -215,18 +188,20 @@ __global__ void k_axis(GridP g, double *p0, double *p1, double *p2, int isB) {
 // D (and for E also B) may be the mean of two time levels: X = wa Xa + wb Xb.
 // Computed on stored i in [-1, n_r + 1], rows [0, n_theta].
 // ---------------------------------------------------------------------------------
+template <typename T>
 struct Pair3 {
-  const double *a[3], *b[3];
-  double wa, wb;
+  const T *a[3], *b[3];
+  T wa, wb;
 };
-__device__ __forceinline__ double pv(const Pair3 &P, int c, int64_t k) {
-  double v = P.wa * __ldg(P.a[c] + k);
-  if (P.wb != 0.0) v += P.wb * __ldg(P.b[c] + k);
+template <typename T>
+__device__ __forceinline__ T pv(const Pair3<T> &P, int c, int64_t k) {
+  T v = P.wa * __ldg(P.a[c] + k);
+  if (P.wb != (T)0) v += P.wb * __ldg(P.b[c] + k);
   return v;
 }
 
-__global__ void k_aux_E(GridP g, Pair3 B, Pair3 D, const double *tab, double *E1, double *E2,
-                        double *E3) {
+template <typename T>
+__global__ void k_aux_E(GridP g, Pair3<T> B, Pair3<T> D, const T *tab, T *E1, T *E2, T *E3) {
   const int ni = g.n_r + 3, nj = g.n_th + 1;
   const int64_t n = (int64_t)ni * nj;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
@@ -235,37 +210,37 @@ __global__ void k_aux_E(GridP g, Pair3 B, Pair3 D, const double *tab, double *E1
     const int64_t k = sidx(g, i, j);
     // E_1 at (i+1/2, j) = alpha [h_11 D^1 + <h_13 D^3>]
     {
-      const double avg = (tabv(tab, g, CLS_NN, T_WT13, i, j) * pv(D, 2, k) +
+      const T avg = (tabv(tab, g, CLS_NN, T_WT13, i, j) * pv(D, 2, k) +
                           tabv(tab, g, CLS_NN, T_WT13, i + 1, j) * pv(D, 2, k + 1)) /
-                         (2.0 * tabv(tab, g, CLS_HN, T_SHT, i, j));
+                         ((T)2 * tabv(tab, g, CLS_HN, T_SHT, i, j));
       E1[k] = tabv(tab, g, CLS_HN, T_ALPHA, i, j) *
               (tabv(tab, g, CLS_HN, T_H11, i, j) * pv(D, 0, k) + avg);
     }
     // E_3 at (i, j) = alpha [h_33 D^3 + <h_13 D^1>] + <sqrt(h) beta^1 B^2>; zero on the axes
     if (j == 0 || j == g.n_th) {
-      E3[k] = 0.0;
+      E3[k] = (T)0;
     } else {
-      const double d2 = 2.0 * tabv(tab, g, CLS_NN, T_SHT, i, j);
-      const double a13 = (tabv(tab, g, CLS_HN, T_WT13, i - 1, j) * pv(D, 0, k - 1) +
+      const T d2 = 2.0 * tabv(tab, g, CLS_NN, T_SHT, i, j);
+      const T a13 = (tabv(tab, g, CLS_HN, T_WT13, i - 1, j) * pv(D, 0, k - 1) +
                           tabv(tab, g, CLS_HN, T_WT13, i, j) * pv(D, 0, k)) / d2;
-      const double ab2 = (tabv(tab, g, CLS_HN, T_WB1, i - 1, j) * pv(B, 1, k - 1) +
+      const T ab2 = (tabv(tab, g, CLS_HN, T_WB1, i - 1, j) * pv(B, 1, k - 1) +
                           tabv(tab, g, CLS_HN, T_WB1, i, j) * pv(B, 1, k)) / d2;
       E3[k] = tabv(tab, g, CLS_NN, T_ALPHA, i, j) *
                   (tabv(tab, g, CLS_NN, T_H33, i, j) * pv(D, 2, k) + a13) + ab2;
     }
     // E_2 at (i, j+1/2) = alpha h_22 D^2 - <sqrt(h) beta^1 B^3>
     if (j < g.n_th) {
-      const double ab3 = (tabv(tab, g, CLS_HH, T_WB1, i - 1, j) * pv(B, 2, k - 1) +
+      const T ab3 = (tabv(tab, g, CLS_HH, T_WB1, i - 1, j) * pv(B, 2, k - 1) +
                           tabv(tab, g, CLS_HH, T_WB1, i, j) * pv(B, 2, k)) /
-                         (2.0 * tabv(tab, g, CLS_NH, T_SHT, i, j));
+                         ((T)2 * tabv(tab, g, CLS_NH, T_SHT, i, j));
       E2[k] = tabv(tab, g, CLS_NH, T_ALPHA, i, j) * tabv(tab, g, CLS_NH, T_H22, i, j) *
                   pv(D, 1, k) - ab3;
     }
   }
 }
 
-__global__ void k_aux_H(GridP g, Pair3 B, Pair3 D, const double *tab, double *H1, double *H2,
-                        double *H3) {
+template <typename T>
+__global__ void k_aux_H(GridP g, Pair3<T> B, Pair3<T> D, const T *tab, T *H1, T *H2, T *H3) {
   const int ni = g.n_r + 3, nj = g.n_th + 1;
   const int64_t n = (int64_t)ni * nj;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
@@ -274,24 +249,24 @@ __global__ void k_aux_H(GridP g, Pair3 B, Pair3 D, const double *tab, double *H1
     const int64_t k = sidx(g, i, j);
     if (j < g.n_th) {
       // H_1 at (i, j+1/2) = alpha [h_11 B^1 + <h_13 B^3>]
-      const double a13 = (tabv(tab, g, CLS_HH, T_WT13, i - 1, j) * pv(B, 2, k - 1) +
+      const T a13 = (tabv(tab, g, CLS_HH, T_WT13, i - 1, j) * pv(B, 2, k - 1) +
                           tabv(tab, g, CLS_HH, T_WT13, i, j) * pv(B, 2, k)) /
-                         (2.0 * tabv(tab, g, CLS_NH, T_SHT, i, j));
+                         ((T)2 * tabv(tab, g, CLS_NH, T_SHT, i, j));
       H1[k] = tabv(tab, g, CLS_NH, T_ALPHA, i, j) *
               (tabv(tab, g, CLS_NH, T_H11, i, j) * pv(B, 0, k) + a13);
       // H_3 at (i+1/2, j+1/2) = alpha [h_33 B^3 + <h_13 B^1>] - <sqrt(h) beta^1 D^2>
-      const double d3 = 2.0 * tabv(tab, g, CLS_HH, T_SHT, i, j);
-      const double b13 = (tabv(tab, g, CLS_NH, T_WT13, i, j) * pv(B, 0, k) +
+      const T d3 = 2.0 * tabv(tab, g, CLS_HH, T_SHT, i, j);
+      const T b13 = (tabv(tab, g, CLS_NH, T_WT13, i, j) * pv(B, 0, k) +
                           tabv(tab, g, CLS_NH, T_WT13, i + 1, j) * pv(B, 0, k + 1)) / d3;
-      const double bd2 = (tabv(tab, g, CLS_NH, T_WB1, i, j) * pv(D, 1, k) +
+      const T bd2 = (tabv(tab, g, CLS_NH, T_WB1, i, j) * pv(D, 1, k) +
                           tabv(tab, g, CLS_NH, T_WB1, i + 1, j) * pv(D, 1, k + 1)) / d3;
       H3[k] = tabv(tab, g, CLS_HH, T_ALPHA, i, j) *
                   (tabv(tab, g, CLS_HH, T_H33, i, j) * pv(B, 2, k) + b13) - bd2;
     }
     // H_2 at (i+1/2, j) = alpha h_22 B^2 + <sqrt(h) beta^1 D^3>
-    const double bd3 = (tabv(tab, g, CLS_NN, T_WB1, i, j) * pv(D, 2, k) +
+    const T bd3 = (tabv(tab, g, CLS_NN, T_WB1, i, j) * pv(D, 2, k) +
                         tabv(tab, g, CLS_NN, T_WB1, i + 1, j) * pv(D, 2, k + 1)) /
-                       (2.0 * tabv(tab, g, CLS_HN, T_SHT, i, j));
+                       ((T)2 * tabv(tab, g, CLS_HN, T_SHT, i, j));
     H2[k] = tabv(tab, g, CLS_HN, T_ALPHA, i, j) * tabv(tab, g, CLS_HN, T_H22, i, j) *
                 pv(B, 1, k) + bd3;
   }
@@ -299,34 +274,36 @@ __global__ void k_aux_H(GridP g, Pair3 B, Pair3 D, const double *tab, double *H1
 
 // MATCH absorbing layer (reading of paper I's form): F <- F - lambda (F - F_init),
 // lambda = coef min(1, ((r - r_abs)/(r_max - r_abs)))^3 for r > r_absorb, rows [0, n_theta].
-__device__ __forceinline__ double match(const GridP &g, double v, double vi, double x1, int j) {
+template <typename T>
+__device__ __forceinline__ T match(const GridP &g, T v, T vi, double x1, int j) {
   if (!(g.r_absorb < g.r_max) || j < 0 || j > g.n_th) return v;
   const double r = g.r_min * exp(x1 * g.dxi);
   if (r <= g.r_absorb) return v;
   double x = (r - g.r_absorb) / (g.r_max - g.r_absorb);
   x = fmin(x, 1.0);
-  return v - g.absorb_coef * x * x * x * (v - vi);
+  return v - (T)(g.absorb_coef * x * x * x) * (v - vi);
 }
 
 // Faraday, Eq. (discretized-faraday): Bout = Bin - dt curl E / sqrt(h) on the evolved
 // points, Bout = Bin elsewhere; B^2 is not evolved on the axes. Covers every stored point.
-__global__ void k_faraday(GridP g, Pair3 Bin, const double *E1, const double *E2,
-                          const double *E3, const double *tab, double *B1, double *B2,
-                          double *B3, const double *Bi1, const double *Bi2, const double *Bi3,
-                          int do_match) {
+template <typename T>
+__global__ void k_faraday(GridP g, Pair3<T> Bin, const T *E1, const T *E2, const T *E3,
+                          const T *tab, T *B1, T *B2, T *B3, const T *Bi1, const T *Bi2,
+                          const T *Bi3, int do_match) {
   const int64_t n = plane_size(g);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(t % g.NX) - G_, j = (int)(t / g.NX) - G_;
     const int64_t k = t;
-    double b1 = pv(Bin, 0, k), b2 = pv(Bin, 1, k), b3 = pv(Bin, 2, k);
+    const T dt = (T)g.dt;
+    T b1 = pv(Bin, 0, k), b2 = pv(Bin, 1, k), b3 = pv(Bin, 2, k);
     const bool rows_half = (j >= 0 && j < g.n_th);
     if (rows_half && i >= 0 && i <= g.n_r)
-      b1 -= g.dt * (E3[k + g.NX] - E3[k]) * tabv(tab, g, CLS_NH, T_ISH, i, j);
+      b1 -= dt * (E3[k + g.NX] - E3[k]) * tabv(tab, g, CLS_NH, T_ISH, i, j);
     if (j >= 1 && j < g.n_th && i >= 0 && i < g.n_r)
-      b2 += g.dt * (E3[k + 1] - E3[k]) * tabv(tab, g, CLS_HN, T_ISH, i, j);
+      b2 += dt * (E3[k + 1] - E3[k]) * tabv(tab, g, CLS_HN, T_ISH, i, j);
     if (rows_half && i >= 0 && i < g.n_r)
-      b3 -= g.dt * ((E2[k + 1] - E2[k]) - (E1[k + g.NX] - E1[k])) *
+      b3 -= dt * ((E2[k + 1] - E2[k]) - (E1[k + g.NX] - E1[k])) *
             tabv(tab, g, CLS_HH, T_ISH, i, j);
     if (do_match) {
       b1 = match(g, b1, Bi1[k], i, j);
@@ -341,30 +318,30 @@ __global__ void k_faraday(GridP g, Pair3 Bin, const double *E1, const double *E2
 // axes D^1 follows the integral form of Sec. 3.3.2 with the polar area (reading: the
 // whole radial flux into the half cell, coefficient 4 pi; -H_3 at theta = pi) and D^3
 // is not evolved. J may be the mean of two time levels.
-__global__ void k_ampere(GridP g, Pair3 Din, const double *H1, const double *H2,
-                         const double *H3, Pair3 J, const double *tab, const double *polar,
-                         double *D1, double *D2, double *D3, const double *Di1,
-                         const double *Di2, const double *Di3, int do_match) {
+template <typename T>
+__global__ void k_ampere(GridP g, Pair3<T> Din, const T *H1, const T *H2, const T *H3, Pair3<T> J,
+                         const T *tab, const T *polar, T *D1, T *D2, T *D3, const T *Di1,
+                         const T *Di2, const T *Di3, int do_match) {
   const int64_t n = plane_size(g);
-  const double fpi = 4.0 * GRPIC_PI;
+  const T fpi = (T)(4.0 * GRPIC_PI), dt = (T)g.dt;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(t % g.NX) - G_, j = (int)(t / g.NX) - G_;
     const int64_t k = t;
-    double d1 = pv(Din, 0, k), d2 = pv(Din, 1, k), d3 = pv(Din, 2, k);
+    T d1 = pv(Din, 0, k), d2 = pv(Din, 1, k), d3 = pv(Din, 2, k);
     if (i >= 0 && i < g.n_r && j >= 0 && j <= g.n_th) {
       if (j == 0)
-        d1 += g.dt * (H3[k] - fpi * pv(J, 0, k)) / __ldg(polar + i + G_);
+        d1 += dt * (H3[k] - fpi * pv(J, 0, k)) / __ldg(polar + i + G_);
       else if (j == g.n_th)
-        d1 += g.dt * (-H3[k - g.NX] - fpi * pv(J, 0, k)) / __ldg(polar + i + G_);
+        d1 += dt * (-H3[k - g.NX] - fpi * pv(J, 0, k)) / __ldg(polar + i + G_);
       else
-        d1 += g.dt * ((H3[k] - H3[k - g.NX]) - fpi * pv(J, 0, k)) *
+        d1 += dt * ((H3[k] - H3[k - g.NX]) - fpi * pv(J, 0, k)) *
               tabv(tab, g, CLS_HN, T_ISH, i, j);
     }
     if (i >= 0 && i <= g.n_r && j >= 0 && j < g.n_th)
-      d2 += g.dt * (-(H3[k] - H3[k - 1]) - fpi * pv(J, 1, k)) * tabv(tab, g, CLS_NH, T_ISH, i, j);
+      d2 += dt * (-(H3[k] - H3[k - 1]) - fpi * pv(J, 1, k)) * tabv(tab, g, CLS_NH, T_ISH, i, j);
     if (i >= 0 && i <= g.n_r && j >= 1 && j < g.n_th)
-      d3 += g.dt * ((H2[k] - H2[k - 1]) - (H1[k] - H1[k - g.NX]) - fpi * pv(J, 2, k)) *
+      d3 += dt * ((H2[k] - H2[k - 1]) - (H1[k] - H1[k - g.NX]) - fpi * pv(J, 2, k)) *
             tabv(tab, g, CLS_NN, T_ISH, i, j);
     if (do_match) {
       d1 = match(g, d1, Di1[k], i + 0.5, j);
@@ -375,18 +352,19 @@ __global__ void k_ampere(GridP g, Pair3 Din, const double *H1, const double *H2,
   }
 }
 
-__global__ void k_copy3(int64_t n, const double *a0, const double *a1, const double *a2,
-                        double *b0, double *b1, double *b2) {
+template <typename T>
+__global__ void k_copy3(int64_t n, const T *a0, const T *a1, const T *a2, T *b0, T *b1, T *b2) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     b0[t] = a0[t]; b1[t] = a1[t]; b2[t] = a2[t];
   }
 }
 
-__global__ void k_zero(double *p, int64_t n) {
+template <typename T>
+__global__ void k_zero(T *p, int64_t n) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x)
-    p[t] = 0.0;
+    p[t] = (T)0;
 }
 
 int blocks_for(int64_t n) {
@@ -395,44 +373,51 @@ int blocks_for(int64_t n) {
   return (int)(b < 1 ? 1 : b);
 }
 
-Pair3 one(double *const p[3]) {
-  Pair3 P;
+template <typename T>
+Pair3<T> one(T *const p[3]) {
+  Pair3<T> P;
   for (int c = 0; c < 3; ++c) { P.a[c] = p[c]; P.b[c] = p[c]; }
-  P.wa = 1.0; P.wb = 0.0;
+  P.wa = (T)1; P.wb = (T)0;
   return P;
 }
-Pair3 mean(double *const p[3], double *const q[3]) {
-  Pair3 P;
+template <typename T>
+Pair3<T> mean(T *const p[3], T *const q[3]) {
+  Pair3<T> P;
   for (int c = 0; c < 3; ++c) { P.a[c] = p[c]; P.b[c] = q[c]; }
-  P.wa = 0.5; P.wb = 0.5;
+  P.wa = (T)0.5; P.wb = (T)0.5;
   return P;
 }
 
-void horizon(const GridP &g, double *const p[3], cudaStream_t st) {
+template <typename T>
+void horizon(const GridP &g, T *const p[3], cudaStream_t st) {
   const int64_t n = (int64_t)(g.n_f + 1 + G_) * g.NY * 3;
-  k_horizon<<<blocks_for(n), TPB, 0, st>>>(g, p[0], p[1], p[2]);
+  k_horizon<T><<<blocks_for(n), TPB, 0, st>>>(g, p[0], p[1], p[2]);
   COUNT_LAUNCH(1);
 }
-void axis(const GridP &g, double *const p[3], int isB, cudaStream_t st) {
+template <typename T>
+void axis(const GridP &g, T *const p[3], int isB, cudaStream_t st) {
   const int64_t n = (int64_t)g.NX * (2 * G_ + 1) * 3;
-  k_axis<<<blocks_for(n), TPB, 0, st>>>(g, p[0], p[1], p[2], isB);
+  k_axis<T><<<blocks_for(n), TPB, 0, st>>>(g, p[0], p[1], p[2], isB);
   COUNT_LAUNCH(1);
 }
-void auxE(const GridP &g, Pair3 B, Pair3 D, const FieldPtrs &F, cudaStream_t st) {
+template <typename T>
+void auxE(const GridP &g, Pair3<T> B, Pair3<T> D, const FieldPtrsT<T> &F, cudaStream_t st) {
   const int64_t n = (int64_t)(g.n_r + 3) * (g.n_th + 1);
-  k_aux_E<<<blocks_for(n), TPB, 0, st>>>(g, B, D, F.tab, F.E[0], F.E[1], F.E[2]);
+  k_aux_E<T><<<blocks_for(n), TPB, 0, st>>>(g, B, D, F.tab, F.E[0], F.E[1], F.E[2]);
   COUNT_LAUNCH(1);
 }
-void auxH(const GridP &g, Pair3 B, Pair3 D, const FieldPtrs &F, cudaStream_t st) {
+template <typename T>
+void auxH(const GridP &g, Pair3<T> B, Pair3<T> D, const FieldPtrsT<T> &F, cudaStream_t st) {
   const int64_t n = (int64_t)(g.n_r + 3) * (g.n_th + 1);
-  k_aux_H<<<blocks_for(n), TPB, 0, st>>>(g, B, D, F.tab, F.H[0], F.H[1], F.H[2]);
+  k_aux_H<T><<<blocks_for(n), TPB, 0, st>>>(g, B, D, F.tab, F.H[0], F.H[1], F.H[2]);
   COUNT_LAUNCH(1);
 }
 
 }  // namespace
 
-cudaError_t launch_metric_tables(const GridP &g, double *tab, double *polar, cudaStream_t st) {
-  k_metric_tables<<<blocks_for(4 * plane_size(g)), TPB, 0, st>>>(g, tab, polar);
+template <typename T>
+cudaError_t launch_metric_tables(const GridP &g, T *tab, T *polar, cudaStream_t st) {
+  k_metric_tables<T><<<blocks_for(4 * plane_size(g)), TPB, 0, st>>>(g, tab, polar);
   COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
@@ -447,13 +432,15 @@ cudaError_t launch_dt_min(const GridP &g, double *scratch, int, double *out, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_zero(double *p, int64_t n, cudaStream_t st) {
-  k_zero<<<blocks_for(n), TPB, 0, st>>>(p, n);
+template <typename T>
+cudaError_t launch_zero(T *p, int64_t n, cudaStream_t st) {
+  k_zero<T><<<blocks_for(n), TPB, 0, st>>>(p, n);
   COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_fields(const GridP &g, const FieldPtrs &F, int kind, double B0,
+template <typename T>
+cudaError_t launch_init_fields(const GridP &g, const FieldPtrsT<T> &F, int kind, double B0,
                                cudaStream_t st) {
   const int64_t ps = plane_size(g);
   for (int c = 0; c < 3; ++c) {
@@ -462,7 +449,7 @@ cudaError_t launch_init_fields(const GridP &g, const FieldPtrs &F, int kind, dou
   }
   if (kind == GRPIC_FIELD_WALD || kind == GRPIC_FIELD_VERTICAL) {
     const int64_t n = (int64_t)(g.n_r + 2 * G_ + 1) * (g.n_th + 1);
-    k_init_fields<<<blocks_for(n), TPB, 0, st>>>(g, F, kind, B0);
+    k_init_fields<T><<<blocks_for(n), TPB, 0, st>>>(g, F, kind, B0);
     COUNT_LAUNCH(1);
   }
   return cudaGetLastError();
@@ -470,22 +457,19 @@ cudaError_t launch_init_fields(const GridP &g, const FieldPtrs &F, int kind, dou
 
 // After em holds the initial B, D: boundary fills, em0 = em, initial-field copy,
 // cur0 = cur = 0, B^n = B.
-cudaError_t launch_field_finish_init(const GridP &g, const FieldPtrs &F, int, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_field_finish_init(const GridP &g, const FieldPtrsT<T> &F, int, cudaStream_t st) {
   const int64_t ps = plane_size(g);
   horizon(g, F.B, st);
   horizon(g, F.D, st);
   axis(g, F.B, 1, st);
   axis(g, F.D, 0, st);
-  k_copy3<<<blocks_for(ps), TPB, 0, st>>>(ps, F.B[0], F.B[1], F.B[2], F.B0[0], F.B0[1], F.B0[2]);
-  COUNT_LAUNCH(1);
-  k_copy3<<<blocks_for(ps), TPB, 0, st>>>(ps, F.D[0], F.D[1], F.D[2], F.D0[0], F.D0[1], F.D0[2]);
-  COUNT_LAUNCH(1);
-  k_copy3<<<blocks_for(ps), TPB, 0, st>>>(ps, F.B[0], F.B[1], F.B[2], F.Bi[0], F.Bi[1], F.Bi[2]);
-  COUNT_LAUNCH(1);
-  k_copy3<<<blocks_for(ps), TPB, 0, st>>>(ps, F.D[0], F.D[1], F.D[2], F.Di[0], F.Di[1], F.Di[2]);
-  COUNT_LAUNCH(1);
-  k_copy3<<<blocks_for(ps), TPB, 0, st>>>(ps, F.B[0], F.B[1], F.B[2], F.Bn[0], F.Bn[1], F.Bn[2]);
-  COUNT_LAUNCH(1);
+  k_copy3<T><<<blocks_for(ps), TPB, 0, st>>>(ps, F.B[0], F.B[1], F.B[2], F.B0[0], F.B0[1], F.B0[2]);
+  k_copy3<T><<<blocks_for(ps), TPB, 0, st>>>(ps, F.D[0], F.D[1], F.D[2], F.D0[0], F.D0[1], F.D0[2]);
+  k_copy3<T><<<blocks_for(ps), TPB, 0, st>>>(ps, F.B[0], F.B[1], F.B[2], F.Bi[0], F.Bi[1], F.Bi[2]);
+  k_copy3<T><<<blocks_for(ps), TPB, 0, st>>>(ps, F.D[0], F.D[1], F.D[2], F.Di[0], F.Di[1], F.Di[2]);
+  k_copy3<T><<<blocks_for(ps), TPB, 0, st>>>(ps, F.B[0], F.B[1], F.B[2], F.Bn[0], F.Bn[1], F.Bn[2]);
+  COUNT_LAUNCH(5);
   for (int c = 0; c < 3; ++c) {
     launch_zero(F.J[c], ps, st);
     launch_zero(F.J0[c], ps, st);
@@ -498,12 +482,13 @@ cudaError_t launch_field_finish_init(const GridP &g, const FieldPtrs &F, int, cu
 
 // Loop step 2 of Sec. 3.4: B^{n-1} = (B^{n-3/2} + B^{n-1/2})/2, D^{n-1/2} = (D^{n-1} + D^n)/2,
 // E^{n-1/2} from {B^{n-1/2}, D^{n-1/2}}, auxiliary Faraday B^{n-1} -> B^n (BN planes).
-cudaError_t launch_predict(const GridP &g, const FieldPtrs &F, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_predict(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st) {
   auxE(g, one(F.B), mean(F.D0, F.D), F, st);
-  const Pair3 Bm = mean(F.B0, F.B);
+  const Pair3<T> Bm = mean(F.B0, F.B);
   const int64_t ps = plane_size(g);
-  k_faraday<<<blocks_for(ps), TPB, 0, st>>>(g, Bm, F.E[0], F.E[1], F.E[2], F.tab, F.Bn[0],
-                                            F.Bn[1], F.Bn[2], nullptr, nullptr, nullptr, 0);
+  k_faraday<T><<<blocks_for(ps), TPB, 0, st>>>(g, Bm, F.E[0], F.E[1], F.E[2], F.tab, F.Bn[0],
+                                               F.Bn[1], F.Bn[2], nullptr, nullptr, nullptr, 0);
   COUNT_LAUNCH(1);
   horizon(g, F.Bn, st);
   axis(g, F.Bn, 1, st);
@@ -512,30 +497,43 @@ cudaError_t launch_predict(const GridP &g, const FieldPtrs &F, cudaStream_t st) 
 
 // Loop steps 5-7 of Sec. 3.4 (J holds J^{n+1/2}). Writes B^{n+1/2} into the B0 planes and
 // D^{n+1} into the D0 planes; the caller then swaps em/em0 and cur/cur0.
-cudaError_t launch_advance(const GridP &g, const FieldPtrs &F, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_advance(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st) {
   const int64_t ps = plane_size(g);
   // step 6: E^n, H^n from {B^n, D^n}; Faraday B^{n-1/2} -> B^{n+1/2}
   auxE(g, one(F.Bn), one(F.D), F, st);
   auxH(g, one(F.Bn), one(F.D), F, st);
-  k_faraday<<<blocks_for(ps), TPB, 0, st>>>(g, one(F.B), F.E[0], F.E[1], F.E[2], F.tab,
-                                            F.B0[0], F.B0[1], F.B0[2], F.Bi[0], F.Bi[1],
-                                            F.Bi[2], 1);
+  k_faraday<T><<<blocks_for(ps), TPB, 0, st>>>(g, one(F.B), F.E[0], F.E[1], F.E[2], F.tab,
+                                               F.B0[0], F.B0[1], F.B0[2], F.Bi[0], F.Bi[1],
+                                               F.Bi[2], 1);
   COUNT_LAUNCH(1);
   horizon(g, F.B0, st);
   axis(g, F.B0, 1, st);
   // step 7: auxiliary Ampere D^{n-1/2} -> D^{n+1/2} with H^n and J^n = (J^{n-1/2} + J^{n+1/2})/2
-  k_ampere<<<blocks_for(ps), TPB, 0, st>>>(g, mean(F.D0, F.D), F.H[0], F.H[1], F.H[2],
-                                           mean(F.J0, F.J), F.tab, F.polar, F.Dh[0], F.Dh[1],
-                                           F.Dh[2], nullptr, nullptr, nullptr, 0);
+  k_ampere<T><<<blocks_for(ps), TPB, 0, st>>>(g, mean(F.D0, F.D), F.H[0], F.H[1], F.H[2],
+                                              mean(F.J0, F.J), F.tab, F.polar, F.Dh[0], F.Dh[1],
+                                              F.Dh[2], nullptr, nullptr, nullptr, 0);
   COUNT_LAUNCH(1);
   horizon(g, F.Dh, st);
   // H^{n+1/2} from {B^{n+1/2}, D^{n+1/2}}; final Ampere D^n -> D^{n+1} with J^{n+1/2}
   auxH(g, one(F.B0), one(F.Dh), F, st);
-  k_ampere<<<blocks_for(ps), TPB, 0, st>>>(g, one(F.D), F.H[0], F.H[1], F.H[2], one(F.J),
-                                           F.tab, F.polar, F.D0[0], F.D0[1], F.D0[2], F.Di[0],
-                                           F.Di[1], F.Di[2], 1);
+  k_ampere<T><<<blocks_for(ps), TPB, 0, st>>>(g, one(F.D), F.H[0], F.H[1], F.H[2], one(F.J),
+                                              F.tab, F.polar, F.D0[0], F.D0[1], F.D0[2], F.Di[0],
+                                              F.Di[1], F.Di[2], 1);
   COUNT_LAUNCH(1);
   horizon(g, F.D0, st);
   axis(g, F.D0, 0, st);
   return cudaGetLastError();
 }
+
+#define INSTANTIATE_FIELDS(T)                                                                    \
+  template cudaError_t launch_metric_tables<T>(const GridP &, T *, T *, cudaStream_t);         \
+  template cudaError_t launch_zero<T>(T *, int64_t, cudaStream_t);                              \
+  template cudaError_t launch_init_fields<T>(const GridP &, const FieldPtrsT<T> &, int, double, \
+                                             cudaStream_t);                                     \
+  template cudaError_t launch_field_finish_init<T>(const GridP &, const FieldPtrsT<T> &, int,   \
+                                                   cudaStream_t);                               \
+  template cudaError_t launch_predict<T>(const GridP &, const FieldPtrsT<T> &, cudaStream_t);   \
+  template cudaError_t launch_advance<T>(const GridP &, const FieldPtrsT<T> &, cudaStream_t);
+INSTANTIATE_FIELDS(double)
+INSTANTIATE_FIELDS(float)

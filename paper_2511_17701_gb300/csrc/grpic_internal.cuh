@@ -31,16 +31,18 @@ __host__ __device__ inline int64_t sidx(const GridP &g, int i, int j) {
   return (int64_t)(j + G_) * g.NX + (i + G_);
 }
 
-// Device view of one species' arrays.
-struct SpeciesDev {
+// Device view of one species' arrays; T is double (FP64 path) or float (mixed path).
+template <typename T>
+struct SpeciesDevT {
   int32_t *i1, *i2;
-  double *dx1, *dx2, *u1, *u2, *u3, *phi, *w;
+  T *dx1, *dx2, *u1, *u2, *u3, *phi, *w;
   uint8_t *tag;
   int32_t *i1p, *i2p;
-  double *dx1p, *dx2p;
+  T *dx1p, *dx2p;
   const int64_t *n;  // live count, on the device
   double qm, qc;
 };
+using SpeciesDev = SpeciesDevT<double>;
 
 // Diagnostics counters on the device (unsigned long long for atomicAdd).
 enum { DG_LEFT_INNER = 0, DG_LEFT_OUTER, DG_REFLECT, DG_NONFINITE, DG_N };
@@ -112,6 +114,49 @@ __device__ __forceinline__ void metric_eval(const GridP &g, double x1, double x2
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Stationary potentials: Wald (Eq. Wald) and its zero-spin limit, and their
+// derivatives in code coordinates, written from the physical (r, theta) closed forms.
+// ---------------------------------------------------------------------------------
+struct Pot {
+  double A0, A1, A3;              // A_0, A_1 (code), A_3
+  double d1A0, d2A0, d1A3, d2A1;  // the derivatives the fields need
+};
+
+__device__ __forceinline__ void potential(const GridP &g, int kind, double B0, double x1, double x2, bool derivs,
+                          Pot &p) {
+  const double a = g.a, M = g.M, a2 = a * a;
+  const double r = g.r_min * exp(x1 * g.dxi), th = x2 * g.dth;
+  double s, c;
+  sincos(th, &s, &c);
+  const double s2 = s * s, f = g.dxi * r, gg = g.dth;
+  if (kind == GRPIC_FIELD_VERTICAL) {
+    p.A0 = 0.0; p.A1 = 0.0; p.A3 = 0.5 * B0 * r * r * s2;
+    p.d1A0 = p.d2A0 = p.d2A1 = 0.0;
+    p.d1A3 = f * B0 * r * s2;
+    return;
+  }
+  const double Sig = r * r + a2 * c * c, Del = r * r - 2.0 * M * r + a2;
+  const double A = (r * r + a2) * (r * r + a2) - a2 * Del * s2;
+  const double z = 2.0 * M * r / Sig;
+  // physical Wald potential: A_t = (B0 a / 2)(z (2 - s^2) - 2), A_r = (B0 a / 2)(2 z - (1+z) s^2),
+  // A_phi = (B0 / 2)(A s^2 / Sigma - 2 a^2 z s^2)
+  const double hb = 0.5 * B0;
+  p.A0 = hb * a * (z * (2.0 - s2) - 2.0);
+  p.A1 = f * hb * a * (2.0 * z - (1.0 + z) * s2);
+  p.A3 = hb * (A * s2 / Sig - 2.0 * a2 * z * s2);
+  if (!derivs) return;
+  const double drS = 2.0 * r, dtS = -2.0 * a2 * s * c;
+  const double drz = 2.0 * M * (Sig - r * drS) / (Sig * Sig);
+  const double dtz = -2.0 * M * r * dtS / (Sig * Sig);
+  const double drA = 4.0 * r * (r * r + a2) - a2 * s2 * (2.0 * r - 2.0 * M);
+  const double dts2 = 2.0 * s * c;
+  p.d1A0 = f * hb * a * drz * (2.0 - s2);
+  p.d2A0 = gg * hb * a * (dtz * (2.0 - s2) - z * dts2);
+  p.d1A3 = f * hb * (s2 * (drA * Sig - A * drS) / (Sig * Sig) - 2.0 * a2 * s2 * drz);
+  p.d2A1 = gg * f * hb * a * (2.0 * dtz - dtz * s2 - (1.0 + z) * dts2);
+}
+
 // Tetrad maps of Appendix A (matrix form).
 __device__ __forceinline__ void t_vec_to_hat(const MetricV &m, const double A[3], double Ah[3]) {
   const double s11 = sqrt(m.H11), s33 = sqrt(m.h33);
@@ -174,30 +219,54 @@ extern long long grpic_launches;
 // Launchers (host functions defined in fields.cu, particles.cu, sort.cu).
 // Every launcher returns cudaGetLastError() of its launches.
 // ---------------------------------------------------------------------------------
-struct FieldPtrs {
-  double *B[3], *D[3], *B0[3], *D0[3], *J[3], *J0[3], *Bn[3], *Bi[3], *Di[3];
-  double *E[3], *H[3], *Dh[3];
-  const double *tab;    // [4 classes][T_NQ][plane]
-  const double *polar;  // [NX], polar area at x1 = i + 1/2 stored at i
+template <typename T>
+struct FieldPtrsT {
+  T *B[3], *D[3], *B0[3], *D0[3], *J[3], *J0[3], *Bn[3], *Bi[3], *Di[3];
+  T *E[3], *H[3], *Dh[3];
+  const T *tab;    // [4 classes][T_NQ][plane]
+  const T *polar;  // [NX], polar area at x1 = i + 1/2 stored at i
+};
+using FieldPtrs = FieldPtrsT<double>;
+
+// Per-cell tables of the FP32 pusher (mixed precision), computed in FP64: r at x1 = i,
+// sin and cos of theta at x2 = j, for stored i, j.
+struct PushTables {
+  const float *r, *s, *c;
+  int guard_i;  // cells i1 < guard_i and within guard_j of an axis take the FP64 pusher
+  int guard_j;
 };
 
-cudaError_t launch_metric_tables(const GridP &g, double *tab, double *polar, cudaStream_t st);
+template <typename T>
+cudaError_t launch_metric_tables(const GridP &g, T *tab, T *polar, cudaStream_t st);
 cudaError_t launch_dt_min(const GridP &g, double *scratch, int nscratch, double *out,
                           cudaStream_t st);
-cudaError_t launch_init_fields(const GridP &g, const FieldPtrs &F, int kind, double B0,
+template <typename T>
+cudaError_t launch_init_fields(const GridP &g, const FieldPtrsT<T> &F, int kind, double B0,
                                cudaStream_t st);
-cudaError_t launch_field_finish_init(const GridP &g, const FieldPtrs &F, int user,
+template <typename T>
+cudaError_t launch_field_finish_init(const GridP &g, const FieldPtrsT<T> &F, int user,
                                      cudaStream_t st);
-cudaError_t launch_predict(const GridP &g, const FieldPtrs &F, cudaStream_t st);
-cudaError_t launch_advance(const GridP &g, const FieldPtrs &F, cudaStream_t st);
-cudaError_t launch_zero(double *p, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_predict(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st);
+template <typename T>
+cudaError_t launch_advance(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st);
+template <typename T>
+cudaError_t launch_zero(T *p, int64_t n, cudaStream_t st);
 
-cudaError_t launch_load(const GridP &g, SpeciesDev s, int64_t n, const grpic_particle_init &in,
-                        double density_power, cudaStream_t st);
-cudaError_t launch_push(const GridP &g, const FieldPtrs &F, SpeciesDev s, int64_t n_bound,
-                        bool deposit, unsigned long long *diag, cudaStream_t st);
-cudaError_t launch_deposit(const GridP &g, const FieldPtrs &F, SpeciesDev s, int64_t n_bound,
-                           cudaStream_t st);
+cudaError_t launch_push_tables(const GridP &g, float *r, float *s, float *c, cudaStream_t st);
+template <typename T>
+cudaError_t launch_load(const GridP &g, SpeciesDevT<T> s, int64_t k0, int64_t n,
+                        const grpic_particle_init &in, double density_power, cudaStream_t st);
+template <typename T>
+cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
+                        const PushTables &tb, int64_t n_bound, bool deposit,
+                        unsigned long long *diag, cudaStream_t st);
+template <typename T>
+cudaError_t launch_deposit(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
+                           const PushTables &tb, int64_t n_bound, cudaStream_t st);
+template <typename T>
+cudaError_t launch_invariants(const GridP &g, SpeciesDevT<T> s, int kind, double B0,
+                              double *E, double *L, int64_t n_bound, cudaStream_t st);
 
 struct SortScratch {
   uint32_t *keys[2], *vals[2];
@@ -209,5 +278,7 @@ struct SortScratch {
 };
 int64_t sort_hist_entries(int64_t max_n);
 int64_t sort_bsum_entries(int64_t max_n);
-cudaError_t launch_sort(const GridP &g, int tile_r, int tile_t, SpeciesDev in, SpeciesDev out,
-                        int64_t n_bound, int64_t *n_dev, const SortScratch &S, cudaStream_t st);
+template <typename T>
+cudaError_t launch_sort(const GridP &g, int tile_r, int tile_t, SpeciesDevT<T> in,
+                        SpeciesDevT<T> out, int64_t n_bound, int64_t *n_dev, const SortScratch &S,
+                        cudaStream_t st);

@@ -23,7 +23,8 @@ __device__ __forceinline__ uint32_t cell_key(int i1, int i2, uint8_t tag, int n_
   return tile * (uint32_t)(tr * tt) + (uint32_t)(i2 % tt) * (uint32_t)tr + (uint32_t)(i1 % tr);
 }
 
-__global__ void k_keys(SpeciesDev s, int n_r, int tr, int tt, uint32_t *keys, uint32_t *vals,
+template <typename T>
+__global__ void k_keys(SpeciesDevT<T> s, int n_r, int tr, int tt, uint32_t *keys, uint32_t *vals,
                        unsigned long long *alive) {
   const int64_t n = *s.n;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -131,7 +132,8 @@ __global__ void k_scan_add(uint32_t *a, int64_t L, const uint32_t *bsum) {
 }
 
 // gather every array of the species by the final permutation
-__global__ void k_gather(SpeciesDev in, SpeciesDev out, const uint32_t *perm,
+template <typename T>
+__global__ void k_gather(SpeciesDevT<T> in, SpeciesDevT<T> out, const uint32_t *perm,
                          const int64_t *n_dev) {
   const int64_t n = *n_dev;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -166,7 +168,8 @@ int64_t sort_bsum_entries(int64_t max_n) {
   return (sort_hist_entries(max_n) + SCAN_SEG - 1) / SCAN_SEG;
 }
 
-cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDev in, SpeciesDev out,
+template <typename T>
+cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDevT<T> in, SpeciesDevT<T> out,
                         int64_t n_bound, int64_t *n_dev, const SortScratch &S, cudaStream_t st) {
   if (n_bound <= 0) return cudaGetLastError();
   // number of key bits: keys of alive particles are < tiles * tr * tt; 0xFFFFFFFF must
@@ -178,7 +181,8 @@ cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDev in, SpeciesDe
   const int passes = (bits + 7) / 8;
   unsigned long long *alive = S.alive;
   cudaMemsetAsync(alive, 0, sizeof(unsigned long long), st);
-  k_keys<<<grid_for(n_bound, TPB), TPB, 0, st>>>(in, g.n_r, tr, tt, S.keys[0], S.vals[0], alive);
+  k_keys<T><<<grid_for(n_bound, TPB), TPB, 0, st>>>(in, g.n_r, tr, tt, S.keys[0], S.vals[0],
+                                                     alive);
   COUNT_LAUNCH(1);
   const int nblocks = (int)((n_bound + BCHUNK - 1) / BCHUNK);
   const int64_t L = 256LL * nblocks;
@@ -199,12 +203,19 @@ cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDev in, SpeciesDe
     COUNT_LAUNCH(1);
     cur = 1 - cur;
   }
-  k_gather<<<grid_for(n_bound, TPB), TPB, 0, st>>>(in, out, S.vals[cur], in.n);
+  k_gather<T><<<grid_for(n_bound, TPB), TPB, 0, st>>>(in, out, S.vals[cur], in.n);
   COUNT_LAUNCH(1);
   k_set_n<<<1, 1, 0, st>>>(n_dev, alive);
   COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_sort<double>(const GridP &, int, int, SpeciesDevT<double>,
+                                         SpeciesDevT<double>, int64_t, int64_t *,
+                                         const SortScratch &, cudaStream_t);
+template cudaError_t launch_sort<float>(const GridP &, int, int, SpeciesDevT<float>,
+                                        SpeciesDevT<float>, int64_t, int64_t *,
+                                        const SortScratch &, cudaStream_t);
 
 // ---------------------------------------------------------------------------------
 // grpic_sort_permutation_noalloc: the same stable cell sort, for callers that cannot
@@ -276,7 +287,7 @@ extern "C" GRPIC_API grpic_status grpic_sort_permutation_noalloc(
   // the counter must start at zero: the array keeps the previous call's contents
   if (cudaMemsetAsync(alive, 0, sizeof(unsigned long long), st) != cudaSuccess) return GRPIC_ECUDA;
   k_store_count<<<1, 1, 0, st>>>(n_dev, n);
-  SpeciesDev s{};
+  SpeciesDevT<double> s{};
   s.i1 = const_cast<int32_t *>(i1);
   s.i2 = const_cast<int32_t *>(i2);
   s.tag = const_cast<uint8_t *>(tag);
@@ -286,7 +297,8 @@ extern "C" GRPIC_API grpic_status grpic_sort_permutation_noalloc(
   int bits = 1;
   while (((uint64_t)1 << bits) - 1 < maxkey + 1 && bits < 32) ++bits;
   const int passes = (bits + 7) / 8;
-  k_keys<<<grid_for(n, TPB), TPB, 0, st>>>(s, n_r, tile_r, tile_theta, keys[0], vals[0], alive);
+  k_keys<double><<<grid_for(n, TPB), TPB, 0, st>>>(s, n_r, tile_r, tile_theta, keys[0], vals[0],
+                                                   alive);
   const int nblocks = (int)((n + BCHUNK - 1) / BCHUNK);
   const int64_t L = 256LL * nblocks;
   const int64_t nseg = (L + SCAN_SEG - 1) / SCAN_SEG;

@@ -1,0 +1,169 @@
+"""Mixed precision (FP32 fields, momenta, offsets and currents; FP64 near the horizon and
+the axes) against the FP64 oracle, through the C ABI.
+
+The bound is the spec one: at most 1e-5 relative error per step on the particle
+state. Both sides start from the same oracle-built state, rounded to FP32 so that it is
+exactly representable on both (next to theta = pi the dynamics amplify a rounding of the
+input offset by ~1e2, which would otherwise dominate). Field planes are held to 1e-5
+normwise. Currents are held to 1e-5 normwise per plane: per cell they are not comparable
+at that level where only moves of less than ~1e-4 cell contribute, because FP32 offsets
+resolve ~6e-8 cell. The drift of the conserved energy and angular momentum of test
+particles over 10^4 steps in the frozen Wald field is measured for both precisions.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+from parity import G, gpu_from_oracle, oracle_state
+
+pytestmark = pytest.mark.gpu
+
+MIXED_RTOL = 1e-5
+BASE = dict(W.grid_config("wald64"), precision="mixed")
+BIG = dict(W.grid_config("wald512", n_r=256, n_theta=256, r_max=50.0, ppc=2, r_absorb=45.0),
+           precision="mixed")
+AFTER_ADVANCE = list(range(12)) + [15, 16, 17, 18, 19, 20]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def round_state_fp32(osim):
+    """Round the oracle's floating state (fields and particles) to FP32 values in place."""
+    osim.F[:] = osim.F.astype(np.float32).astype(np.float64)
+    for sp in osim.species:
+        for k in ("dx1", "dx2", "u1", "u2", "u3", "phi", "w", "dx1p", "dx2p"):
+            sp.a[k][:] = sp.a[k].astype(np.float32).astype(np.float64)
+
+
+def mixed_state(cfg):
+    osim = oracle_state(cfg)
+    round_state_fp32(osim)
+    return osim
+
+
+def particle_errors(pg, po):
+    """Max relative errors per quantity (positions relative to max(1, |x|), momentum
+    components relative to |u_c| + median |u_c|)."""
+    out = {}
+    assert len(pg["i1"]) == len(po["i1"])
+    assert np.array_equal(pg["tag"], po["tag"])
+    for a, b in (("i1", "dx1"), ("i2", "dx2")):
+        xg = pg[a].astype(np.float64) + pg[b].astype(np.float64)
+        xo = po[a].astype(np.float64) + po[b]
+        out[b] = float(np.max(np.abs(xg - xo) / np.maximum(1.0, np.abs(xo)), initial=0.0))
+    for c in ("u1", "u2", "u3"):
+        sc = np.median(np.abs(po[c])) if len(po[c]) else 1.0
+        out[c] = float(np.max(np.abs(pg[c] - po[c]) / (np.abs(po[c]) + sc + 1e-300), initial=0.0))
+    out["phi"] = float(np.max(np.abs(pg["phi"] - po["phi"]) / np.maximum(1.0, np.abs(po["phi"])),
+                              initial=0.0))
+    return out
+
+
+def plane_errors(Fg, Fo, planes):
+    return {k: float(np.abs(Fg[k] - Fo[k]).max() / max(np.abs(Fo[k]).max(), 1e-300))
+            for k in planes}
+
+
+@pytest.mark.parametrize("cfg", [BASE, BIG])
+def test_mixed_full_step_error_per_step(torch_cuda, cfg):
+    osim = mixed_state(cfg)
+    g = gpu_from_oracle(osim)
+    g.step(1)
+    osim.step(1)
+    for s in range(2):
+        e = particle_errors(g.get_particles(s), osim.species[s].view())
+        assert max(e.values()) <= MIXED_RTOL, e
+    pe = plane_errors(g.planes(), osim.F, AFTER_ADVANCE)
+    assert max(pe.values()) <= MIXED_RTOL, pe
+
+
+@pytest.mark.parametrize("cfg", [BASE, BIG])
+def test_mixed_push_and_deposit(torch_cuda, cfg):
+    osim = mixed_state(cfg)
+    osim.predict()
+    round_state_fp32(osim)
+    g = gpu_from_oracle(osim)
+    for s in range(2):
+        g.push(s)
+        osim.push(s)
+    g.deposit()
+    osim.deposit()
+    for s in range(2):
+        e = particle_errors(g.get_particles(s), osim.species[s].view())
+        assert max(e.values()) <= MIXED_RTOL, e
+    pe = plane_errors(g.planes(), osim.F, [O.J1, O.J2, O.J3])
+    assert max(pe.values()) <= MIXED_RTOL, pe
+
+
+def test_mixed_init_and_load(torch_cuda):
+    from paper_2511_17701_gb300 import FIELD_WALD, Sim
+    cfg = dict(BIG, density_power=1.0)
+    osim = oracle_state(cfg)
+    pl = W.pair_plasma(cfg)
+    g = Sim(dict(cfg, dt=osim.dt), [osim.species[0].n, osim.species[1].n])
+    g.init_metric()
+    g.init_fields(FIELD_WALD, 1.0)
+    pe = plane_errors(g.planes(), osim.F, range(12))
+    assert max(pe.values()) <= 1e-6, pe  # FP64 evaluation rounded to FP32
+    for s in range(2):
+        g.load_particles(s, pl["pos"], pl["uhat"][s], pl["w0"], pl["qm"][s], pl["qc"][s], 1.0)
+        pg, po = g.get_particles(s), osim.species[s].view()
+        e = particle_errors(pg, po)
+        assert max(e.values()) <= 1e-6, e
+        assert np.allclose(pg["w"], po["w"], rtol=1e-6, atol=0)
+
+
+def test_mixed_sort_bit_exact(torch_cuda):
+    rng = np.random.default_rng(4)
+    cfg = dict(BASE, tile_r=8, tile_theta=8)
+    n = 50001
+    osim = O.OracleSim(dict(cfg, dt=0.01))
+    a = {k: np.zeros(n, dtype=t) for k, t in O.PARTICLE_FIELDS.items()}
+    a["i1"] = rng.integers(0, cfg["n_r"], n).astype(np.int32)
+    a["i2"] = rng.integers(0, cfg["n_theta"], n).astype(np.int32)
+    a["tag"] = rng.choice([0, 1, 1, 1, 2], n).astype(np.uint8)
+    for k in ("dx1", "dx2", "u1", "u2", "u3", "phi", "w", "dx1p", "dx2p"):
+        a[k] = rng.random(n).astype(np.float32).astype(np.float64)
+    osim.add_raw_species(a, 1.0, 1.0)
+    g = gpu_from_oracle(osim)
+    g.sort(0)
+    osim.sort(0, 8, 8)
+    pg, po = g.get_particles(0), osim.species[0].view()
+    for k in po:
+        assert np.array_equal(pg[k].astype(po[k].dtype), po[k]), k
+
+
+def test_invariant_drift_fp64_and_mixed(torch_cuda):
+    """10^4 pushes of test particles in the frozen Wald field (a = 0.9, 128^2): the relative
+    drift of E and L of each particle that stays in the domain, for both precisions."""
+    from paper_2511_17701_gb300 import FIELD_WALD
+    cfg = W.grid_config("wald64", n_r=128, n_theta=128, r_max=20.0, r_absorb=1e300)
+    osim = O.OracleSim(cfg)
+    osim.init_fields(O.FIELD_WALD, 1.0)
+    tp = W.probe_particles(cfg, 4096, 7, (40.0, 100.0), (20.0, 108.0), 0.5)
+    qm, qc = W.species_coefficients(1.0)
+    osim.add_species(tp["pos"], tp["uhat"], tp["w0"], qm, qc)
+    osim.predict()
+    drift = {}
+    for prec in ("fp64", "mixed"):
+        g = gpu_from_oracle(osim, precision=prec)
+        g.push(0)
+        E0, L0 = g.invariants(0, FIELD_WALD, 1.0)
+        for _ in range(9999):
+            g.push(0)
+        E1, L1 = g.invariants(0, FIELD_WALD, 1.0)
+        p = g.get_particles(0)
+        keep = (p["tag"] == 1) & (p["i1"] > 10) & (p["i1"] < 118)
+        assert keep.sum() > 1000
+        drift[prec] = (float(np.max(np.abs(E1[keep] / E0[keep] - 1))),
+                       float(np.max(np.abs(L1[keep] / L0[keep] - 1))))
+    print("invariant drift over 1e4 steps (E, L):", drift)
+    assert drift["fp64"][0] < 1e-2 and drift["fp64"][1] < 1e-2
+    assert drift["mixed"][0] < 1e-2 and drift["mixed"][1] < 1e-2
