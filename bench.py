@@ -145,11 +145,17 @@ def allreduce_sum(ws, x, device):
     return float(t.item())
 
 
-def workload_desc(name, cfg, n_total):
+PRECISION_DESC = {"fp64": "FP64",
+                  "mixed": "mixed precision (FP32 state, fields and currents; FP64 metric "
+                           "within 4 cells of the horizon and the axes)"}
+
+
+def workload_desc(name, cfg, n_total, precision="fp64"):
     return ("%s: Kerr a=%g Wald B0=%g, %dx%d log-r grid, r in [0.95 r_h, %g], e+- pairs %d "
             "per cell per species (%d particles), Maxwell-Juttner theta_T=%g, density ~ r^-%g, "
-            "FP64" % (name, cfg["a"], cfg["B0"], cfg["n_r"], cfg["n_theta"], cfg["r_max"],
-                      cfg["ppc"], n_total, cfg["theta_T"], cfg.get("density_power", 0.0)))
+            "%s" % (name, cfg["a"], cfg["B0"], cfg["n_r"], cfg["n_theta"], cfg["r_max"],
+                    cfg["ppc"], n_total, cfg["theta_T"], cfg.get("density_power", 0.0),
+                    PRECISION_DESC[precision]))
 
 
 def oracle_workload(cfg, frac, seed=99):
@@ -334,7 +340,7 @@ def run_gpu(args, ws, rank, local):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else "f32 (f64 within the guard cells)",
                 "data": "synthetic (seeded workload generator)",
-                "config": {"workload": workload_desc(args.workload, cfg, 2 * n),
+                "config": {"workload": workload_desc(args.workload, cfg, 2 * n, args.precision),
                            "sort_every": args.sort_every, "tile": args.tile,
                            "l2": "inputs larger than L2: particle state %.2f GB" % (
                                2 * n * 89 / 1e9),

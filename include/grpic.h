@@ -60,9 +60,10 @@ typedef enum {
 typedef enum { GRPIC_METRIC_KS0 = 0, GRPIC_METRIC_KS = 1 } grpic_metric_kind;
 typedef enum {
   GRPIC_FP64 = 0,  /* FP64 state, fields and arithmetic                                  */
-  GRPIC_MIXED = 1  /* FP32 fields, momenta, offsets and currents (int32 cells); the push
-                      runs in FP64 for particles within fp64_guard_cells of the horizon
-                      or an axis, in FP32 elsewhere                                        */
+  GRPIC_MIXED = 1  /* FP32 fields, momenta, offsets and currents (int32 cells); FP32
+                      arithmetic, with the metric, lapse and shift evaluated in FP64 for
+                      particles within fp64_guard_cells of the horizon or an axis, and
+                      the whole push in FP64 for particles in the cell rows on the axes */
 } grpic_precision;
 typedef enum {
   GRPIC_FIELD_ZERO = 0,     /* all fields zero                                    */
@@ -107,8 +108,8 @@ typedef struct {
   int full_iterations; /* 0: the implicit pushes stop once an iterate repeats bit for bit (every
                           later iteration would return the same bits, so the result equals the
                           n_iter result exactly); 1: always run n_iter iterations             */
-  int fp64_guard_cells; /* GRPIC_MIXED: cells from the horizon and from each axis pushed in
-                           FP64 (default 4 when 0)                                            */
+  int fp64_guard_cells; /* GRPIC_MIXED: cells from the horizon and from each axis where the
+                           metric is evaluated in FP64 (default 4 when 0)                     */
 } grpic_config;
 
 /* Pointers to one species' particle arrays (SoA, length >= n). Positions are a cell
@@ -154,7 +155,10 @@ GRPIC_API size_t grpic_arena_bytes(const grpic_ctx *ctx);
 
 /* Binds the caller-owned device arena (>= grpic_arena_bytes, 256-byte aligned)
  * and the CUDA stream (cudaStream_t, NULL = legacy default) on the current device.
- * Errors: GRPIC_ENOMEM (too small), GRPIC_EINVAL (misaligned). */
+ * With GRPIC_MIXED the first bind also creates one internal stream and event pairs
+ * (no device memory): the push forks the FP64 guard-zone kernels onto it and joins
+ * them back to the bound stream before returning, so callers see one stream.
+ * Errors: GRPIC_ENOMEM (too small), GRPIC_EINVAL (misaligned), GRPIC_ECUDA. */
 GRPIC_API grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream);
 
 /* Tabulates the code-unit metric of App. A (alpha, h_ij, sqrt(h), sqrt(h~),

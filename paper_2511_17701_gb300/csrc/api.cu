@@ -29,6 +29,8 @@ struct SpeciesState {
   int live = 0;
   int64_t *n_dev = nullptr;
   size_t off_n = 0, off_soa[2][NARR] = {};
+  size_t off_gl = 0;  // guard list, mask and counters (mixed path)
+  GuardList gl{};
 };
 
 size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
@@ -49,6 +51,8 @@ struct grpic_ctx {
   size_t need = 0;
   char *arena = nullptr;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;  // guard kernels of the mixed push
+  cudaEvent_t ev_fork[GRPIC_MAX_SPECIES] = {}, ev_done[GRPIC_MAX_SPECIES] = {};
   bool bound = false, metric_ready = false, fields_ready = false;
   size_t off_planes = 0, off_tab = 0, off_polar = 0, off_dt = 0, off_diag = 0, off_ptab = 0;
   size_t off_keys[2] = {}, off_vals[2] = {}, off_hist = 0, off_bsum = 0, off_alive = 0;
@@ -128,7 +132,7 @@ SpeciesDevT<T> dev_view(const SpeciesState &s, int which) {
   d.u1 = (T *)p.u1; d.u2 = (T *)p.u2; d.u3 = (T *)p.u3;
   d.phi = (T *)p.phi; d.w = (T *)p.w; d.tag = p.tag;
   d.i1p = p.i1p; d.i2p = p.i2p; d.dx1p = (T *)p.dx1p; d.dx2p = (T *)p.dx2p;
-  d.n = s.n_dev; d.qm = s.qm; d.qc = s.qc;
+  d.n = s.n_dev; d.qm = s.qm; d.qc = s.qc; d.f_qm = (float)s.qm; d.f_qc = (float)s.qc;
   return d;
 }
 
@@ -215,9 +219,15 @@ struct PhaseTimer {
 
 // --- precision-dispatched pieces of the hot path
 template <typename T>
-cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, SpeciesState &sp, bool deposit) {
-  return launch_push<T>(c->g, F, dev_view<T>(sp, sp.live), c->tb, sp.n_bound, deposit, c->diag,
-                        c->stream);
+cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, int k, bool deposit) {
+  SpeciesState &sp = c->sp[k];
+  const PushStreams ps{c->stream, c->side, c->ev_fork[k], c->ev_done[k]};
+  return launch_push<T>(c->g, F, dev_view<T>(sp, sp.live), c->tb, sp.gl, sp.n_bound, deposit,
+                        c->diag, ps);
+}
+// the main stream waits for the guard kernels of species k (mixed path)
+cudaError_t join_push(grpic_ctx *c, int k) {
+  return c->mixed ? cudaStreamWaitEvent(c->stream, c->ev_done[k], 0) : cudaSuccess;
 }
 template <typename T>
 cudaError_t do_zero_J(grpic_ctx *c, FieldPtrsT<T> &F) {
@@ -239,6 +249,9 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   const grpic_config &c = *cfg;
   if (c.metric != GRPIC_METRIC_KS0 && c.metric != GRPIC_METRIC_KS) return GRPIC_EINVAL;
   if (c.n_r < 4 || c.n_theta < 4 || c.n_r > 65536 || c.n_theta > 65536) return GRPIC_EINVAL;
+  // plane indices are 32-bit in the deposit
+  if ((int64_t)(c.n_r + 2 * G_ + 1) * (c.n_theta + 2 * G_ + 1) >= ((int64_t)1 << 31))
+    return GRPIC_EINVAL;
   if (!(c.r_min > 0.0) || !(c.r_max > c.r_min)) return GRPIC_EINVAL;
   if (c.metric == GRPIC_METRIC_KS && !(c.a >= 0.0 && c.a < 1.0)) return GRPIC_EINVAL;
   if (c.n_iter < 1 || c.n_iter > 1000) return GRPIC_EINVAL;
@@ -273,15 +286,17 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   g.small_angle = c.small_angle;
   g.r_absorb = c.r_absorb;
   g.absorb_coef = c.absorb_coef;
-  // the FP64 guard of the mixed pusher: cells inside the horizon plus guard cells outside
-  // it, and guard cells next to each axis
+  grid_float_copies(g);
+  // the FP64 guard of the mixed pusher: guard cells on either side of the cell holding the
+  // horizon, and guard cells next to each axis
   const int guard = c.fp64_guard_cells > 0 ? c.fp64_guard_cells : 4;
-  int ih = 0;
+  int ih = -1000000;
   if (g.M > 0.0) {
     const double rh = 1.0 + sqrt(1.0 - g.a * g.a);
-    ih = rh > g.r_min ? (int)ceil(log(rh / g.r_min) / g.dxi) : 0;
+    ih = (int)floor(log(rh / g.r_min) / g.dxi);
   }
-  ctx->tb.guard_i = ih + guard;
+  ctx->tb.guard_ilo = ih - guard;
+  ctx->tb.guard_ihi = ih + guard + 1;
   ctx->tb.guard_j = guard;
 
   const size_t ps = (size_t)plane_size(g), fs = ctx->fsz;
@@ -289,7 +304,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   ctx->off_planes = off; off += up(ps * fs) * 36;
   ctx->off_tab = off;    off += up(ps * fs) * 4 * T_NQ;
   ctx->off_polar = off;  off += up((size_t)g.NX * fs);
-  ctx->off_ptab = off;   off += 3 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 4);
+  ctx->off_ptab = off;   off += 6 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 8);
   ctx->off_dt = off;     off += up(64);
   ctx->off_diag = off;   off += up(DG_N * 8);
   ctx->max_cap = 1;
@@ -311,6 +326,12 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   ctx->off_hist = off;  off += up((size_t)sort_hist_entries(ctx->max_cap) * 4);
   ctx->off_bsum = off;  off += up((size_t)sort_bsum_entries(ctx->max_cap) * 4);
   ctx->off_alive = off; off += up(8);
+  if (ctx->mixed)
+    for (int s = 0; s < c.n_species; ++s) {
+      const size_t cap = (size_t)(ctx->sp[s].cap > 0 ? ctx->sp[s].cap : 1);
+      ctx->sp[s].off_gl = off;
+      off += up(cap * 4) + up((cap + 31) / 32 * 4) + up(16);
+    }
   ctx->load_chunk = ctx->max_cap < ((int64_t)1 << 20) ? ctx->max_cap : ((int64_t)1 << 20);
   ctx->off_stage = off; off += 6 * up((size_t)ctx->load_chunk * 8);
   ctx->need = off;
@@ -330,10 +351,32 @@ grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream)
   ctx->stream = static_cast<cudaStream_t>(stream);
   if (ctx->mixed) assign_fields(ctx, ctx->F32);
   else assign_fields(ctx, ctx->F64);
-  const size_t tstride = up((size_t)(ctx->g.NX > ctx->g.NY ? ctx->g.NX : ctx->g.NY) * 4);
+  const size_t tstride = up((size_t)(ctx->g.NX > ctx->g.NY ? ctx->g.NX : ctx->g.NY) * 8);
   ctx->tb.r = at<float>(ctx, ctx->off_ptab);
   ctx->tb.s = at<float>(ctx, ctx->off_ptab + tstride);
   ctx->tb.c = at<float>(ctx, ctx->off_ptab + 2 * tstride);
+  ctx->tb.r64 = at<double>(ctx, ctx->off_ptab + 3 * tstride);
+  ctx->tb.s64 = at<double>(ctx, ctx->off_ptab + 4 * tstride);
+  ctx->tb.c64 = at<double>(ctx, ctx->off_ptab + 5 * tstride);
+  if (ctx->mixed) {
+    for (int s = 0; s < ctx->cfg.n_species; ++s) {
+      SpeciesState &sp = ctx->sp[s];
+      const size_t cap = (size_t)(sp.cap > 0 ? sp.cap : 1);
+      sp.gl.idx = at<uint32_t>(ctx, sp.off_gl);
+      sp.gl.mask = at<uint32_t>(ctx, sp.off_gl + up(cap * 4));
+      sp.gl.count = at<unsigned long long>(ctx, sp.off_gl + up(cap * 4) + up((cap + 31) / 32 * 4));
+      sp.gl.cap = (int64_t)cap;
+    }
+    if (!ctx->side) {  // the guard kernels are the longer chain: higher priority
+      int lo = 0, hi = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      CK(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi));
+      for (int s = 0; s < GRPIC_MAX_SPECIES; ++s) {
+        CK(cudaEventCreateWithFlags(&ctx->ev_fork[s], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_done[s], cudaEventDisableTiming));
+      }
+    }
+  }
   ctx->diag = at<unsigned long long>(ctx, ctx->off_diag);
   for (int s = 0; s < ctx->cfg.n_species; ++s) assign_species_ptrs(ctx, ctx->sp[s]);
   SortScratch &S = ctx->S;
@@ -364,8 +407,7 @@ grpic_status grpic_init_metric(grpic_ctx *ctx) {
     CK(launch_metric_tables<double>(ctx->g, const_cast<double *>(ctx->F64.tab),
                                     const_cast<double *>(ctx->F64.polar), ctx->stream));
   }
-  CK(launch_push_tables(ctx->g, const_cast<float *>(ctx->tb.r), const_cast<float *>(ctx->tb.s),
-                        const_cast<float *>(ctx->tb.c), ctx->stream));
+  CK(launch_push_tables(ctx->g, ctx->tb, ctx->stream));
   if (!(ctx->cfg.dt > 0.0)) {
     double dmin = 0.0;
     CK(launch_dt_min(ctx->g, at<double>(ctx, ctx->off_dt), 8, &dmin, ctx->stream));
@@ -375,6 +417,7 @@ grpic_status grpic_init_metric(grpic_ctx *ctx) {
   } else {
     ctx->g.dt = ctx->cfg.dt;
   }
+  grid_float_copies(ctx->g);
   ctx->metric_ready = true;
   return GRPIC_OK;
 }
@@ -524,8 +567,9 @@ grpic_status grpic_push(grpic_ctx *ctx, int species) {
   SpeciesState &sp = ctx->sp[species];
   if (!sp.loaded) return fail(ctx, GRPIC_ESTATE, "species %d has no particles", species);
   PhaseTimer t(ctx, PH_PUSH);
-  if (ctx->mixed) CK(do_push(ctx, ctx->F32, sp, false));
-  else CK(do_push(ctx, ctx->F64, sp, false));
+  if (ctx->mixed) CK(do_push(ctx, ctx->F32, species, false));
+  else CK(do_push(ctx, ctx->F64, species, false));
+  CK(join_push(ctx, species));
   ++ctx->push_calls;
   return GRPIC_OK;
 }
@@ -610,10 +654,13 @@ grpic_status grpic_step(grpic_ctx *ctx, int n_steps) {
       for (int k = 0; k < ctx->cfg.n_species; ++k) {
         SpeciesState &sp = ctx->sp[k];
         if (!sp.loaded) continue;
-        if (ctx->mixed) CK(do_push(ctx, ctx->F32, sp, true));
-        else CK(do_push(ctx, ctx->F64, sp, true));
+        if (ctx->mixed) CK(do_push(ctx, ctx->F32, k, true));
+        else CK(do_push(ctx, ctx->F64, k, true));
         ++ctx->push_calls;
       }
+      // the guard kernels of one species overlap the FP32 kernel of the next
+      for (int k = 0; k < ctx->cfg.n_species; ++k)
+        if (ctx->sp[k].loaded) CK(join_push(ctx, k));
     }
     {
       PhaseTimer t(ctx, PH_ADVANCE);
@@ -689,6 +736,14 @@ void grpic_destroy(grpic_ctx *ctx) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
     }
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+    for (int s = 0; s < GRPIC_MAX_SPECIES; ++s) {
+      cudaEventDestroy(ctx->ev_fork[s]);
+      cudaEventDestroy(ctx->ev_done[s]);
+    }
+  }
   delete ctx;
 }
 

@@ -19,7 +19,31 @@ struct GridP {
   int stop_on_repeat;  // stop an implicit iteration once its iterate repeats exactly
   double r_min, r_max, dxi, dth, a, M, dt, small_angle, r_absorb, absorb_coef;
   double ig2;  // 1 / dth^2
+  // FP32 copies for the mixed path (read from the kernel parameters, no conversions)
+  float f_a, f_M, f_dxi, f_dth, f_ig2, f_dt, f_idt;
 };
+
+// Fill the FP32 copies once a, M, dxi, dth and dt are set.
+inline void grid_float_copies(GridP &g) {
+  g.f_a = (float)g.a; g.f_M = (float)g.M; g.f_dxi = (float)g.dxi; g.f_dth = (float)g.dth;
+  g.f_ig2 = (float)g.ig2; g.f_dt = (float)g.dt; g.f_idt = g.dt > 0.0 ? (float)(1.0 / g.dt) : 0.0f;
+}
+
+// The grid constants in the arithmetic type R.
+template <typename R>
+struct Cst {
+  R a, M, dxi, dth, ig2, dt;
+};
+template <typename R>
+__device__ __forceinline__ Cst<R> cst(const GridP &g);
+template <>
+__device__ __forceinline__ Cst<double> cst<double>(const GridP &g) {
+  return {g.a, g.M, g.dxi, g.dth, g.ig2, g.dt};
+}
+template <>
+__device__ __forceinline__ Cst<float> cst<float>(const GridP &g) {
+  return {g.f_a, g.f_M, g.f_dxi, g.f_dth, g.f_ig2, g.f_dt};
+}
 
 // Yee point classes of the metric tables: (i, j), (i+1/2, j), (i, j+1/2), (i+1/2, j+1/2).
 enum { CLS_NN = 0, CLS_HN = 1, CLS_NH = 2, CLS_HH = 3 };
@@ -41,6 +65,7 @@ struct SpeciesDevT {
   T *dx1p, *dx2p;
   const int64_t *n;  // live count, on the device
   double qm, qc;
+  float f_qm, f_qc;  // FP32 copies
 };
 using SpeciesDev = SpeciesDevT<double>;
 
@@ -231,9 +256,29 @@ using FieldPtrs = FieldPtrsT<double>;
 // Per-cell tables of the FP32 pusher (mixed precision), computed in FP64: r at x1 = i,
 // sin and cos of theta at x2 = j, for stored i, j.
 struct PushTables {
-  const float *r, *s, *c;
-  int guard_i;  // cells i1 < guard_i and within guard_j of an axis take the FP64 pusher
-  int guard_j;
+  const float *r, *s, *c;           // r at cell corners i, sin/cos(theta) at corners j
+  const double *r64, *s64, *c64;    // the same in FP64, for the guard zones
+  int guard_ilo, guard_ihi;  // cells guard_ilo <= i1 < guard_ihi (around the horizon) and
+  int guard_j;               // within guard_j of an axis evaluate the metric in FP64
+};
+
+// The guard particles of one species for the current push (mixed path): zone 1 (FP64
+// metric) indices ascending from idx[0], zone 2 (the cell rows on the axes, FP64 routine)
+// descending from idx[cap - 1], counted in count[0], count[1]; bit k of mask marks particle
+// k as listed (written only by the classification, read by the FP32 kernel).
+struct GuardList {
+  uint32_t *idx;
+  uint32_t *mask;
+  int64_t cap;
+  unsigned long long *count;
+};
+
+// Streams of one push: the FP64-pipe-bound guard kernels run on `side`, forked from
+// `main` after the classification by `fork`; `done` is recorded on `side` after them and
+// the caller makes `main` wait on it before anything reads the currents or the particles.
+struct PushStreams {
+  cudaStream_t main, side;
+  cudaEvent_t fork, done;
 };
 
 template <typename T>
@@ -253,14 +298,14 @@ cudaError_t launch_advance(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t 
 template <typename T>
 cudaError_t launch_zero(T *p, int64_t n, cudaStream_t st);
 
-cudaError_t launch_push_tables(const GridP &g, float *r, float *s, float *c, cudaStream_t st);
+cudaError_t launch_push_tables(const GridP &g, const PushTables &tb, cudaStream_t st);
 template <typename T>
 cudaError_t launch_load(const GridP &g, SpeciesDevT<T> s, int64_t k0, int64_t n,
                         const grpic_particle_init &in, double density_power, cudaStream_t st);
 template <typename T>
 cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
-                        const PushTables &tb, int64_t n_bound, bool deposit,
-                        unsigned long long *diag, cudaStream_t st);
+                        const PushTables &tb, const GuardList &gl, int64_t n_bound, bool deposit,
+                        unsigned long long *diag, const PushStreams &ps);
 template <typename T>
 cudaError_t launch_deposit(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
                            const PushTables &tb, int64_t n_bound, cudaStream_t st);

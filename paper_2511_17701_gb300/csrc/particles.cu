@@ -2,9 +2,9 @@
 // charge-conserving conformal current deposit (Sec. 3.2), one thread per particle.
 //
 // FP64 path: the double-precision pipe, not HBM, bounds the kernel on GB300 (every
-// particle-step evaluates the metric up to 2 n_iter + 2 times). Mixed path: FP32 state,
-// fields and arithmetic, with the FP64 routine for particles within a few cells of the
-// horizon or an axis. Particle state is SoA; consecutive threads read consecutive elements,
+// particle-step evaluates the metric up to n_iter + 2 times). Mixed path: FP32 state,
+// fields and arithmetic; for particles within a few cells of the horizon or an axis the
+// metric, lapse and shift are evaluated in FP64 (and rounded), in a second kernel. Particle state is SoA; consecutive threads read consecutive elements,
 // and field gathers hit L1/L2 because the particles are kept sorted by cell.
 #include "grpic_internal.cuh"
 
@@ -30,12 +30,13 @@ struct Geo {
 };
 template <typename R>
 __device__ __forceinline__ void geo_from_rsc(const GridP &g, R r, R s, R c, Geo<R> &o) {
-  const R a = (R)g.a, M = (R)g.M, a2 = a * a;
+  const Cst<R> k = cst<R>(g);
+  const R a = k.a, M = k.M, a2 = a * a;
   const R r2 = r * r, s2 = s * s;
   const R Sig = fma_(a2, c * c, r2);
   const R S2 = fma_((R)2 * M, r, Sig);  // Sigma + 2 M r
   const R A = (r2 + a2) * (r2 + a2) - a2 * (r2 - (R)2 * M * r + a2) * s2;
-  const R f = (R)g.dxi * r;
+  const R f = k.dxi * r;
   const R u = Sig * S2 * f;
   const R iQ = (R)1 / (u * s2);         // the one division
   const R iu = iQ * s2;                 // 1 / (Sigma S2 f)
@@ -43,7 +44,7 @@ __device__ __forceinline__ void geo_from_rsc(const GridP &g, R r, R s, R c, Geo<
   o.opz = S2 * iSig;
   o.H11 = A * iSig * iS2 * fi * fi;
   o.H13 = a * iSig * fi;
-  o.H22 = iSig * (R)g.ig2;
+  o.H22 = iSig * k.ig2;
   o.H33 = iQ * u * iSig;                // 1 / (Sigma s^2)
   o.beta1 = (R)2 * M * r * iS2 * fi;
 }
@@ -60,7 +61,8 @@ struct Local {
 };
 template <typename R>
 __device__ __forceinline__ void local_full(const GridP &g, R r, R s, R c, Local<R> &L) {
-  const R a = (R)g.a, M = (R)g.M, a2 = a * a, gg = (R)g.dth, dxi = (R)g.dxi;
+  const Cst<R> k = cst<R>(g);
+  const R a = k.a, M = k.M, a2 = a * a, gg = k.dth, dxi = k.dxi;
   const R r2 = r * r, s2 = s * s;
   const R Sig = fma_(a2, c * c, r2);
   const R S2 = fma_((R)2 * M, r, Sig);
@@ -76,7 +78,7 @@ __device__ __forceinline__ void local_full(const GridP &g, R r, R s, R c, Local<
   o.opz = S2 * iSig;
   o.H11 = A * iSig * iS2 * fi * fi;
   o.H13 = a * iSig * fi;
-  o.H22 = iSig * (R)g.ig2;
+  o.H22 = iSig * k.ig2;
   o.H33 = iSig * is2;
   o.beta1 = (R)2 * M * r * iS2 * fi;
   const R al2 = Sig * iS2;
@@ -91,8 +93,8 @@ __device__ __forceinline__ void local_full(const GridP &g, R r, R s, R c, Local<
   L.d1H11 = (P * dxA - (R)2 * A * (M * r * dxS + Sig * (dxS + M * f))) * iP2 * fi2 -
             (R)2 * dxi * o.H11;
   L.d2H11 = (P * deA - (R)2 * A * deS * (M * r + Sig)) * iP2 * fi2;
-  L.d1H22 = -dxS * iSg2 * (R)g.ig2;
-  L.d2H22 = -deS * iSg2 * (R)g.ig2;
+  L.d1H22 = -dxS * iSg2 * k.ig2;
+  L.d2H22 = -deS * iSg2 * k.ig2;
   L.d1H33 = -dxS * iSg2 * is2;
   L.d2H33 = -(deS + (R)2 * c * s * is2 * Sig * gg) * iSg2 * is2;
   L.d1H13 = -a * fi * iSig * (iSig * dxS + dxi);
@@ -154,7 +156,7 @@ template <typename R>
 __device__ __forceinline__ void geodesic_momentum(const GridP &g, const Local<R> &L, R u[3]) {
   const R u0 = u[0], u1 = u[1], u3 = u[2];  // u_3 is not changed by this substep
   const Geo<R> &o = L.G;
-  const R dt = (R)g.dt;
+  const R dt = cst<R>(g).dt;
   const R c0 = fma_(o.H33 * u3, u3, (R)1), c1 = (R)2 * o.H13 * u3;
   const R e1 = L.d1H33 * u3 * u3, e2 = (R)2 * L.d1H13 * u3;
   const R f1 = L.d2H33 * u3 * u3, f2 = (R)2 * L.d2H13 * u3;
@@ -423,7 +425,7 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
 // r at x1 = i + o1 and sin/cos of theta at x2 = j + o2 (offsets from the corner of cell i, j)
 __device__ __forceinline__ void rsc32(const GridP &g, const PushTables &tb, int i, int j,
                                       float o1, float o2, float &r, float &s, float &c) {
-  const float e = o1 * (float)g.dxi;  // |e| <= 2 dxi
+  const float e = o1 * g.f_dxi;  // |e| <= 2 dxi
   float p = 1.0f / 720.0f;
   p = fmaf(p, e, 1.0f / 120.0f);
   p = fmaf(p, e, 1.0f / 24.0f);
@@ -431,7 +433,7 @@ __device__ __forceinline__ void rsc32(const GridP &g, const PushTables &tb, int 
   p = fmaf(p, e, 0.5f);
   p = fmaf(p, e, 1.0f);
   r = __ldg(tb.r + i + G_) * fmaf(p, e, 1.0f);
-  const float d = o2 * (float)g.dth;  // |d| <= 2 dtheta
+  const float d = o2 * g.f_dth;  // |d| <= 2 dtheta
   const float q = d * d;
   const float se = fmaf(fmaf(fmaf(-1.0f / 5040.0f, q, 1.0f / 120.0f), q, -1.0f / 6.0f) * q, d, d);
   const float ce = fmaf(fmaf(fmaf(fmaf(1.0f / 40320.0f, q, -1.0f / 720.0f), q, 1.0f / 24.0f), q,
@@ -439,6 +441,73 @@ __device__ __forceinline__ void rsc32(const GridP &g, const PushTables &tb, int 
   const float s0 = __ldg(tb.s + j + G_), c0 = __ldg(tb.c + j + G_);
   s = fmaf(s0, ce, c0 * se);
   c = fmaf(c0, ce, -s0 * se);
+}
+
+// The guard-zone form of rsc32: r, sin and cos in FP64 from the FP64 corner tables, with
+// theta clamped to [small_angle, pi - small_angle] as in the FP64 routine.
+__device__ __forceinline__ void rsc64(const GridP &g, const PushTables &tb, int i, int j,
+                                      float o1, float o2, double &r, double &s, double &c) {
+  const double e = (double)o1 * g.dxi;
+  r = fabs(e) <= 0.05 ? __ldg(tb.r64 + i + G_) * exp_small(e)  // truncation < 1e-15
+                      : g.r_min * exp(((double)i + (double)o1) * g.dxi);
+  const double th = ((double)j + (double)o2) * g.dth;
+  const double d = (double)o2 * g.dth;
+  if (th < g.small_angle || th > GRPIC_PI - g.small_angle) {
+    sincos(fmin(fmax(th, g.small_angle), GRPIC_PI - g.small_angle), &s, &c);
+  } else if (fabs(d) <= 0.1) {
+    const double q = d * d;  // Taylor series to d^9 and d^10: truncation below 3e-17
+    double sp = 1.0 / 362880.0;
+    sp = fma(sp, q, -1.0 / 5040.0);
+    sp = fma(sp, q, 1.0 / 120.0);
+    sp = fma(sp, q, -1.0 / 6.0);
+    const double se = fma(sp * q, d, d);
+    double cp = -1.0 / 3628800.0;
+    cp = fma(cp, q, 1.0 / 40320.0);
+    cp = fma(cp, q, -1.0 / 720.0);
+    cp = fma(cp, q, 1.0 / 24.0);
+    cp = fma(cp, q, -0.5);
+    const double ce = fma(cp, q, 1.0);
+    const double s0 = __ldg(tb.s64 + j + G_), c0 = __ldg(tb.c64 + j + G_);
+    s = fma(s0, ce, c0 * se);
+    c = fma(c0, ce, -s0 * se);
+  } else {
+    sincos(th, &s, &c);
+  }
+}
+
+// FP64 metric values rounded for the FP32 arithmetic of the guard zones
+__device__ __forceinline__ void narrow(const Geo<double> &a, Geo<float> &b) {
+  b.H11 = (float)a.H11; b.H13 = (float)a.H13; b.H22 = (float)a.H22; b.H33 = (float)a.H33;
+  b.beta1 = (float)a.beta1; b.opz = (float)a.opz;
+}
+__device__ __forceinline__ void narrow(const Local<double> &a, Local<float> &b) {
+  b.alpha = (float)a.alpha;
+  narrow(a.G, b.G);
+  b.d1H11 = (float)a.d1H11; b.d1H22 = (float)a.d1H22; b.d1H33 = (float)a.d1H33;
+  b.d1H13 = (float)a.d1H13; b.d1alpha = (float)a.d1alpha; b.d1beta1 = (float)a.d1beta1;
+  b.d2H11 = (float)a.d2H11; b.d2H22 = (float)a.d2H22; b.d2H33 = (float)a.d2H33;
+  b.d2H13 = (float)a.d2H13; b.d2alpha = (float)a.d2alpha; b.d2beta1 = (float)a.d2beta1;
+  b.rH11 = (float)a.rH11; b.sH11 = (float)a.sH11; b.rh22 = (float)a.rh22;
+  b.sh22 = (float)a.sh22; b.rh33 = (float)a.rh33; b.sh33 = (float)a.sh33;
+  b.k13 = (float)a.k13; b.m13 = (float)a.m13;
+}
+
+// The contravariant metric, shift and 1 + z at a cell-relative point, evaluated in FP64
+// (G64: guard zones) or in FP32, as FP32 values.
+template <bool G64>
+__device__ __forceinline__ void geo_at(const GridP &g, const PushTables &tb, int i, int j,
+                                       float o1, float o2, Geo<float> &o) {
+  if constexpr (G64) {
+    double r, s_, c_;
+    rsc64(g, tb, i, j, o1, o2, r, s_, c_);
+    Geo<double> od;
+    geo_from_rsc(g, r, s_, c_, od);
+    narrow(od, o);
+  } else {
+    float r, s_, c_;
+    rsc32(g, tb, i, j, o1, o2, r, s_, c_);
+    geo_from_rsc(g, r, s_, c_, o);
+  }
 }
 
 // bilinear interpolation from the cell-relative position (i, o) for a Yee offset (s1, s2)
@@ -454,59 +523,132 @@ __device__ __forceinline__ float interp32(const float *__restrict__ pl, int NX, 
   return fmaf(w2, b - a, a);
 }
 
-// zigzag deposit in coordinates relative to the start cell (ia, ja): the move goes from
-// (a1, a2) in [0, 1]^2 to (b1, b2) in cell (ia + di, ja + dj)
-__device__ __forceinline__ void deposit32(const GridP &g, const FieldPtrsT<float> &F, float q,
-                                          int ia, int ja, float a1, float a2, int di, int dj,
-                                          float b1, float b2, float v3) {
-  const float idt = (float)(1.0 / g.dt);
-  const float r1 = fminf((float)min(0, di) + 1.0f, fmaxf((float)max(0, di), 0.5f * (a1 + b1)));
-  const float r2 = fminf((float)min(0, dj) + 1.0f, fmaxf((float)max(0, dj), 0.5f * (a2 + b2)));
-  float *J1 = F.J[0], *J2 = F.J[1], *J3 = F.J[2];
-  const int NX = g.NX;
+// One move of the mixed path, relative to its start cell (ia, ja): from (a1, a2) in [0, 1]^2
+// to (b1, b2) in cell (ia + di, ja + dj), charge weight q and dphi/dt v3 at the midpoint.
+struct Move32 {
+  int ia, ja, di, dj;
+  float a1, a2, b1, b2, q, v3;
+};
+
+// The zigzag deposit of a move (Sec. 3.2, Eq. charge-conservation-disc; Umeda et al. 2003)
+// as three groups of four contributions, each group belonging to one cell: the segment in
+// the start cell and the segment in the end cell (J1 at (i, j) and (i, j+1), J2 at (i, j) and
+// (i+1, j) of that cell, as the plane stores edges), and J3 = q v3 at the four corners
+// around the midpoint. cell[g] is the plane index of group g's cell.
+__device__ __forceinline__ void zigzag32(const GridP &g, const Move32 &m, float c[3][4],
+                                         int cell[3]) {
+  const float idt = g.f_idt, q = m.q;
+  const float r1 = fminf((float)min(0, m.di) + 1.0f, fmaxf((float)max(0, m.di), 0.5f * (m.a1 + m.b1)));
+  const float r2 = fminf((float)min(0, m.dj) + 1.0f, fmaxf((float)max(0, m.dj), 0.5f * (m.a2 + m.b2)));
   {
-    const float F1 = q * (r1 - a1) * idt, F2 = q * (r2 - a2) * idt;
-    const float W1 = 0.5f * (a1 + r1), W2 = 0.5f * (a2 + r2);
-    const int64_t k = sidx(g, ia, ja);
-    atomicAdd(J1 + k, F1 * (1.0f - W2));
-    atomicAdd(J1 + k + NX, F1 * W2);
-    atomicAdd(J2 + k, F2 * (1.0f - W1));
-    atomicAdd(J2 + k + 1, F2 * W1);
+    const float F1 = q * (r1 - m.a1) * idt, F2 = q * (r2 - m.a2) * idt;
+    const float W1 = 0.5f * (m.a1 + r1), W2 = 0.5f * (m.a2 + r2);
+    c[0][0] = F1 * (1.0f - W2); c[0][1] = F1 * W2; c[0][2] = F2 * (1.0f - W1); c[0][3] = F2 * W1;
+    cell[0] = (int)sidx(g, m.ia, m.ja);
   }
   {
-    const float F1 = q * (b1 - r1) * idt, F2 = q * (b2 - r2) * idt;
-    const float W1 = 0.5f * (r1 + b1) - (float)di, W2 = 0.5f * (r2 + b2) - (float)dj;
-    const int64_t k = sidx(g, ia + di, ja + dj);
-    atomicAdd(J1 + k, F1 * (1.0f - W2));
-    atomicAdd(J1 + k + NX, F1 * W2);
-    atomicAdd(J2 + k, F2 * (1.0f - W1));
-    atomicAdd(J2 + k + 1, F2 * W1);
+    const float F1 = q * (m.b1 - r1) * idt, F2 = q * (m.b2 - r2) * idt;
+    const float W1 = 0.5f * (r1 + m.b1) - (float)m.di, W2 = 0.5f * (r2 + m.b2) - (float)m.dj;
+    c[1][0] = F1 * (1.0f - W2); c[1][1] = F1 * W2; c[1][2] = F2 * (1.0f - W1); c[1][3] = F2 * W1;
+    cell[1] = (int)sidx(g, m.ia + m.di, m.ja + m.dj);
   }
-  const float m1 = 0.5f * (a1 + b1), m2 = 0.5f * (a2 + b2);
+  const float m1 = 0.5f * (m.a1 + m.b1), m2 = 0.5f * (m.a2 + m.b2);
   const float f1 = floorf(m1), f2 = floorf(m2);
-  const float w1 = m1 - f1, w2 = m2 - f2, qv = q * v3;
-  const int64_t k = sidx(g, ia + (int)f1, ja + (int)f2);
-  atomicAdd(J3 + k, qv * (1.0f - w1) * (1.0f - w2));
-  atomicAdd(J3 + k + 1, qv * w1 * (1.0f - w2));
-  atomicAdd(J3 + k + NX, qv * (1.0f - w1) * w2);
-  atomicAdd(J3 + k + NX + 1, qv * w1 * w2);
+  const float w1 = m1 - f1, w2 = m2 - f2, qv = q * m.v3;
+  c[2][0] = qv * (1.0f - w1) * (1.0f - w2); c[2][1] = qv * w1 * (1.0f - w2);
+  c[2][2] = qv * (1.0f - w1) * w2;          c[2][3] = qv * w1 * w2;
+  cell[2] = (int)sidx(g, m.ia + (int)f1, m.ja + (int)f2);
 }
 
+__device__ __forceinline__ void add_group(const FieldPtrsT<float> &F, int NX, int grp, int k,
+                                          const float c[4]) {
+  if (grp < 2) {
+    atomicAdd(F.J[0] + k, c[0]);
+    atomicAdd(F.J[0] + k + NX, c[1]);
+    atomicAdd(F.J[1] + k, c[2]);
+    atomicAdd(F.J[1] + k + 1, c[3]);
+  } else {
+    atomicAdd(F.J[2] + k, c[0]);
+    atomicAdd(F.J[2] + k + 1, c[1]);
+    atomicAdd(F.J[2] + k + NX, c[2]);
+    atomicAdd(F.J[2] + k + NX + 1, c[3]);
+  }
+}
+
+// Sums of v over runs of equal keys in consecutive lanes (all 32 lanes call it): a suffix
+// scan bounded by the next run head, so the first lane of each run ends with the run's sum.
+// Returns whether this lane heads a run.
+__device__ __forceinline__ bool run_sums(int key, float v[4]) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int kp = __shfl_up_sync(FULL, key, 1);
+  const bool head = lane == 0 || kp != key;
+  const unsigned H = __ballot_sync(FULL, head);
+  if (H == FULL) return true;  // no two neighbouring lanes share a cell
+  const unsigned above = lane == 31 ? 0u : (H & (FULL << (lane + 1)));
+  const int nh = above ? __ffs(above) - 1 : 32;  // first lane of the next run
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float o = __shfl_down_sync(FULL, v[q], d);
+      if (lane + d < nh) v[q] += o;
+    }
+  }
+  return head;
+}
+
+// Warp-cooperative deposit (every lane of the warp calls it; on = false where a lane has no
+// move): per group, contributions to the same cell from consecutive lanes are summed with
+// shuffles (particles are kept sorted by cell, so a warp holds few runs) and the first lane
+// of each run issues the four atomics. A move that stays in its cell has both segments in
+// that cell; they are added before the reduction.
+__device__ __forceinline__ void deposit32_warp(const GridP &g, const FieldPtrsT<float> &F,
+                                               const Move32 &m, bool on) {
+  float c[3][4];
+  int cell[3] = {-1, -1, -1};
+  if (on) {
+    zigzag32(g, m, c, cell);
+    if (cell[1] == cell[0]) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[0][q] += c[1][q];
+      cell[1] = -1;
+    }
+  } else {
+#pragma unroll
+    for (int grp = 0; grp < 3; ++grp)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[grp][q] = 0.0f;
+  }
+#pragma unroll
+  for (int grp = 0; grp < 3; ++grp) {
+    if (!__any_sync(0xffffffffu, cell[grp] >= 0)) continue;
+    const bool head = run_sums(cell[grp], c[grp]);
+    if (head && cell[grp] >= 0) add_group(F, g.NX, grp, cell[grp], c[grp]);
+  }
+}
+
+template <bool G64>
 __device__ __forceinline__ float phi_rate32(const GridP &g, const PushTables &tb, int i, int j,
                                             float o1, float o2, const float u[3]) {
-  float r, s_, c_;
-  rsc32(g, tb, i, j, o1, o2, r, s_, c_);
   Geo<float> o;
-  geo_from_rsc(g, r, s_, c_, o);
+  geo_at<G64>(g, tb, i, j, o1, o2, o);
   const float q = fmaf(o.H11 * u[0], u[0], fmaf(o.H22 * u[1], u[1],
                   fmaf(o.H33 * u[2], u[2], fmaf(o.H13, 2.0f * u[0] * u[2], 1.0f))));
   return rsqrtf(o.opz * q) * fmaf(o.H13, u[0], o.H33 * u[2]);
 }
 
-template <bool DEPOSIT>
-__device__ __forceinline__ void push32(const GridP &g, const FieldPtrsT<float> &F,
+// One particle of the mixed path: steps 2-11 of Sec. 3.1 in FP32 with the metric, lapse
+// and shift evaluated in FP32 (G64 false: off the guard zones) or in FP64 (G64 true: guard
+// zone 1). Returns false when the particle was dropped, else its move (for the deposit). The cell rows on the axes (zone 2) take the
+// FP64 routine instead: there the FP32 rounding of the tetrad-frame momentum, about eps |u|,
+// enters dphi/dt divided by r sin(theta), which has no lower bound in those rows; one row
+// or more away sin(theta) >= dtheta and dt <= CFL r dtheta bound the phi error per step
+// by about eps CFL.
+template <bool G64>
+__device__ __forceinline__ bool push32(const GridP &g, const FieldPtrsT<float> &F,
                                        const PushTables &tb, const SpeciesDevT<float> &s,
-                                       int64_t k, unsigned long long *diag) {
+                                       int64_t k, unsigned long long *diag, Move32 &mv) {
   const int i1 = s.i1[k], i2 = s.i2[k];
   const float dx1 = s.dx1[k], dx2 = s.dx2[k];
   float Bv[3], Dv[3];
@@ -516,33 +658,36 @@ __device__ __forceinline__ void push32(const GridP &g, const FieldPtrsT<float> &
   Dv[0] = interp32(F.D[0], g.NX, i1, i2, dx1, dx2, 0.5f, 0.0f);
   Dv[1] = interp32(F.D[1], g.NX, i1, i2, dx1, dx2, 0.0f, 0.5f);
   Dv[2] = interp32(F.D[2], g.NX, i1, i2, dx1, dx2, 0.0f, 0.0f);
-  float r0, sn, cs;
-  rsc32(g, tb, i1, i2, dx1, dx2, r0, sn, cs);
   Local<float> L;
-  local_full(g, r0, sn, cs, L);
+  if constexpr (G64) {
+    double r0, sn, cs;
+    rsc64(g, tb, i1, i2, dx1, dx2, r0, sn, cs);
+    Local<double> Ld;
+    local_full(g, r0, sn, cs, Ld);
+    narrow(Ld, L);
+  } else {
+    float r0, sn, cs;
+    rsc32(g, tb, i1, i2, dx1, dx2, r0, sn, cs);
+    local_full(g, r0, sn, cs, L);
+  }
   float Bh[3], Dh[3], uh[3], u[3] = {s.u1[k], s.u2[k], s.u3[k]};
   vec_hat(L, Bv, Bh);
   vec_hat(L, Dv, Dh);
   cov_hat(L, u, uh);
-  const float hq = (float)s.qm * L.alpha * 0.5f * (float)g.dt;
+  const float hq = s.f_qm * L.alpha * 0.5f * g.f_dt;
   boris(uh, Dh, Bh, hq);
   hat_cov(L, uh, u);
   geodesic_momentum(g, L, u);
   cov_hat(L, u, uh);
   boris(uh, Dh, Bh, hq);
   hat_cov(L, uh, u);
-  const float dt = (float)g.dt;
+  const float dt = g.f_dt;
   const float uu0 = 2.0f * u[0] * u[2];
   float t1 = dx1, t2 = dx2;
   for (int it = 0; it < g.n_iter; ++it) {
     Geo<float> o;
-    if (it == 0) {
-      o = L.G;
-    } else {
-      float r, s_, c_;
-      rsc32(g, tb, i1, i2, 0.5f * (dx1 + t1), 0.5f * (dx2 + t2), r, s_, c_);
-      geo_from_rsc(g, r, s_, c_, o);
-    }
+    if (it == 0) o = L.G;
+    else geo_at<G64>(g, tb, i1, i2, 0.5f * (dx1 + t1), 0.5f * (dx2 + t2), o);
     const float q = fmaf(o.H11 * u[0], u[0], fmaf(o.H22 * u[1], u[1],
                     fmaf(o.H33 * u[2], u[2], fmaf(o.H13, uu0, 1.0f))));
     const float ag = rsqrtf(o.opz * q);
@@ -557,37 +702,45 @@ __device__ __forceinline__ void push32(const GridP &g, const FieldPtrsT<float> &
         fabsf(t1) < 1e6f && fabsf(t2) < 1e6f)) {
     s.tag[k] = 0;
     count(diag, DG_NONFINITE);
-    return;
+    return false;
   }
   const float f1 = floorf(t1), f2 = floorf(t2);
-  const int di = (int)f1, dj = (int)f2;
-  const int j1 = i1 + di, j2 = i2 + dj;
+  const int di = (int)f1;
+  const int j1 = i1 + di;
+  const int j2 = i2 + (int)f2;
   const float e1 = t1 - f1, e2 = t2 - f2;
-  // the FP32 zone keeps off the axes, so no reflection happens here; guard anyway
+  // off the axis rows a particle is at least one cell from either axis and moves less than
+  // a cell per step (CFL), so no reflection happens here; guard anyway
   if (j2 < 0 || j2 >= g.n_th) {
     s.tag[k] = 0;
     count(diag, DG_NONFINITE);
-    return;
+    return false;
   }
+  const int dj = j2 - i2;
   s.i1[k] = j1; s.i2[k] = j2; s.dx1[k] = e1; s.dx2[k] = e2;
   s.u1[k] = u[0]; s.u2[k] = u[1]; s.u3[k] = u[2];
   if (j1 < 0) { s.tag[k] = 2; count(diag, DG_LEFT_INNER); }
   else if (j1 >= g.n_r) { s.tag[k] = 2; count(diag, DG_LEFT_OUTER); }
   // phi at the midpoint, relative to the start cell
   const float b1 = (float)di + e1, b2 = (float)dj + e2;
-  const float v3 = phi_rate32(g, tb, i1, i2, 0.5f * (dx1 + b1), 0.5f * (dx2 + b2), u);
+  const float v3 = phi_rate32<G64>(g, tb, i1, i2, 0.5f * (dx1 + b1), 0.5f * (dx2 + b2), u);
   s.phi[k] = fmaf(dt, v3, s.phi[k]);
-  if (DEPOSIT) deposit32(g, F, (float)s.qc * s.w[k], i1, i2, dx1, dx2, di, dj, b1, b2, v3);
+  mv = Move32{i1, i2, di, dj, dx1, dx2, b1, b2, s.f_qc * s.w[k], v3};
+  return true;
 }
 
-__device__ __forceinline__ bool in_guard(const PushTables &tb, const GridP &g, int i1, int i2) {
-  return i1 < tb.guard_i || i2 < tb.guard_j || i2 >= g.n_th - tb.guard_j;
+// 0: FP32 metric; 1: FP64 metric (within guard_j rows of an axis or guard cells of the
+// horizon); 2: the cell rows on the axes, FP64 routine
+__device__ __forceinline__ int guard_zone(const PushTables &tb, const GridP &g, int i1, int i2) {
+  if (i2 == 0 || i2 == g.n_th - 1) return 2;
+  return ((i1 >= tb.guard_ilo && i1 < tb.guard_ihi) || i2 < tb.guard_j ||
+          i2 >= g.n_th - tb.guard_j) ? 1 : 0;
 }
 
-// One thread per particle: step 1 (previous location), then the FP64 or FP32 routine.
-template <typename T, bool DEPOSIT>
-__global__ void __launch_bounds__(TPB) k_push(GridP g, FieldPtrsT<T> F, SpeciesDevT<T> s,
-                                              PushTables tb, unsigned long long *diag) {
+// FP64 path: one thread per particle, step 1 (previous location) then the FP64 routine.
+template <bool DEPOSIT>
+__global__ void __launch_bounds__(TPB) k_push(GridP g, FieldPtrsT<double> F,
+                                              SpeciesDevT<double> s, unsigned long long *diag) {
   const int64_t n = *s.n;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
@@ -598,13 +751,94 @@ __global__ void __launch_bounds__(TPB) k_push(GridP g, FieldPtrsT<T> F, SpeciesD
       if (tag != 0) s.tag[k] = 0;
       continue;
     }
-    if constexpr (sizeof(T) == 4) {
-      if (!in_guard(tb, g, i1, i2)) {
-        push32<DEPOSIT>(g, F, tb, s, k, diag);
-        continue;
+    push64<double, DEPOSIT>(g, F, s, k, diag);
+  }
+}
+
+// Mixed path, classification: zone 1 and zone 2 particles are appended to their lists
+// (warp-aggregated) and marked in the mask, one ballot word per warp (blockDim and the grid
+// stride are multiples of 32, so a warp covers particles 32w .. 32w + 31).
+__global__ void __launch_bounds__(TPB) k_classify(GridP g, SpeciesDevT<float> s, PushTables tb,
+                                                  GuardList gl) {
+  const int64_t n = *s.n;
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int zone = s.tag[k] == 1 ? guard_zone(tb, g, s.i1[k], s.i2[k]) : 0;
+    const unsigned act = __activemask();
+    const unsigned m1 = __ballot_sync(act, zone == 1), m2 = __ballot_sync(act, zone == 2);
+    const int leader = __ffs(act) - 1;
+    if (lane == leader) gl.mask[k >> 5] = m1 | m2;
+    if (m1 | m2) {
+      unsigned long long b1 = 0, b2 = 0;
+      if (lane == leader) {
+        if (m1) b1 = atomicAdd(gl.count, (unsigned long long)__popc(m1));
+        if (m2) b2 = atomicAdd(gl.count + 1, (unsigned long long)__popc(m2));
       }
+      b1 = __shfl_sync(act, b1, leader);
+      b2 = __shfl_sync(act, b2, leader);
+      const unsigned below = (1u << lane) - 1u;
+      if (zone == 1) gl.idx[b1 + __popc(m1 & below)] = (uint32_t)k;
+      if (zone == 2) gl.idx[gl.cap - 1 - (int64_t)(b2 + __popc(m2 & below))] = (uint32_t)k;
     }
-    push64<T, DEPOSIT>(g, F, s, k, diag);
+  }
+}
+
+// Mixed path, FP32 kernel: step 1 and the FP32 routine for every unlisted particle (it runs
+// concurrently with the guard kernels, which own the listed ones). The loop runs while the
+// warp's first particle exists, so the whole warp reaches the cooperative deposit.
+template <bool DEPOSIT>
+__global__ void __launch_bounds__(TPB) k_push32(GridP g, FieldPtrsT<float> F,
+                                                SpeciesDevT<float> s, PushTables tb,
+                                                GuardList gl, unsigned long long *diag) {
+  const int64_t n = *s.n;
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k - lane < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    Move32 mv;
+    bool on = false;
+    if (k < n && !((__ldg(gl.mask + (k >> 5)) >> lane) & 1u)) {
+      const int i1 = s.i1[k], i2 = s.i2[k];
+      s.i1p[k] = i1; s.i2p[k] = i2; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+      const uint8_t tag = s.tag[k];
+      if (tag == 1) on = push32<false>(g, F, tb, s, k, diag, mv);
+      else if (tag != 0) s.tag[k] = 0;
+    }
+    if (DEPOSIT) deposit32_warp(g, F, mv, on);
+  }
+}
+
+// Mixed path, guard kernels (side stream): step 1 and the routine of the listed particles,
+// zone 1 with the metric in FP64, zone 2 with the FP64 routine.
+template <bool DEPOSIT>
+__global__ void __launch_bounds__(TPB) k_push_guard(GridP g, FieldPtrsT<float> F,
+                                                    SpeciesDevT<float> s, PushTables tb,
+                                                    GuardList gl, unsigned long long *diag) {
+  const int64_t n = (int64_t)gl.count[0];
+  const int lane = threadIdx.x & 31;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t - lane < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    Move32 mv;
+    bool on = false;
+    if (t < n) {
+      const int64_t k = gl.idx[t];
+      s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+      on = push32<true>(g, F, tb, s, k, diag, mv);
+    }
+    if (DEPOSIT) deposit32_warp(g, F, mv, on);
+  }
+}
+
+template <bool DEPOSIT>
+__global__ void __launch_bounds__(TPB) k_push_axis(GridP g, FieldPtrsT<float> F,
+                                                   SpeciesDevT<float> s, GuardList gl,
+                                                   unsigned long long *diag) {
+  const int64_t n = (int64_t)gl.count[1];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = gl.idx[gl.cap - 1 - t];
+    s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+    push64<float, DEPOSIT>(g, F, s, k, diag);
   }
 }
 
@@ -613,26 +847,37 @@ template <typename T>
 __global__ void __launch_bounds__(TPB) k_deposit(GridP g, FieldPtrsT<T> F, SpeciesDevT<T> s,
                                                  PushTables tb) {
   const int64_t n = *s.n;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k - lane < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    if (s.tag[k] == 0) continue;
-    const int ia = s.i1p[k], ja = s.i2p[k], ib = s.i1[k], jb = s.i2[k];
-    if constexpr (sizeof(T) == 4) {
-      if (!in_guard(tb, g, ia, ja)) {
+    const bool live = k < n && s.tag[k] != 0;
+    int ia = 0, ja = 0, ib = 0, jb = 0, zone = 2;
+    if (live) {
+      ia = s.i1p[k]; ja = s.i2p[k]; ib = s.i1[k]; jb = s.i2[k];
+      if constexpr (sizeof(T) == 4) zone = guard_zone(tb, g, ia, ja);
+    }
+    if constexpr (sizeof(T) == 4) {  // zones 0 and 1: the FP32 deposit of the mixed path
+      Move32 mv;
+      const bool on = live && zone < 2;
+      if (on) {
         const float a1 = s.dx1p[k], a2 = s.dx2p[k];
         const float b1 = (float)(ib - ia) + s.dx1[k], b2 = (float)(jb - ja) + s.dx2[k];
         const float u[3] = {s.u1[k], s.u2[k], s.u3[k]};
-        const float v3 = phi_rate32(g, tb, ia, ja, 0.5f * (a1 + b1), 0.5f * (a2 + b2), u);
-        deposit32(g, F, (float)s.qc * s.w[k], ia, ja, a1, a2, ib - ia, jb - ja, b1, b2, v3);
-        continue;
+        const float m1 = 0.5f * (a1 + b1), m2 = 0.5f * (a2 + b2);
+        const float v3 = zone ? phi_rate32<true>(g, tb, ia, ja, m1, m2, u)
+                              : phi_rate32<false>(g, tb, ia, ja, m1, m2, u);
+        mv = Move32{ia, ja, ib - ia, jb - ja, a1, a2, b1, b2, s.f_qc * s.w[k], v3};
       }
+      deposit32_warp(g, F, mv, on);
     }
-    const double xa1 = ia + (double)s.dx1p[k], xa2 = ja + (double)s.dx2p[k];
-    const double xb1 = ib + (double)s.dx1[k], xb2 = jb + (double)s.dx2[k];
-    const double u[3] = {(double)s.u1[k], (double)s.u2[k], (double)s.u3[k]};
-    const Base b = make_base(g, xa1, xa2);
-    const double v3 = phi_rate64(g, b, 0.5 * __dadd_rn(xa1, xb1), 0.5 * __dadd_rn(xa2, xb2), u);
-    deposit64(g, F, s.qc * (double)s.w[k], ia, ja, xa1, xa2, ib, jb, xb1, xb2, v3);
+    if (live && zone == 2) {  // FP64 path, and the axis rows of the mixed path
+      const double xa1 = ia + (double)s.dx1p[k], xa2 = ja + (double)s.dx2p[k];
+      const double xb1 = ib + (double)s.dx1[k], xb2 = jb + (double)s.dx2[k];
+      const double u[3] = {(double)s.u1[k], (double)s.u2[k], (double)s.u3[k]};
+      const Base b = make_base(g, xa1, xa2);
+      const double v3 = phi_rate64(g, b, 0.5 * __dadd_rn(xa1, xb1), 0.5 * __dadd_rn(xa2, xb2), u);
+      deposit64(g, F, s.qc * (double)s.w[k], ia, ja, xa1, xa2, ib, jb, xb1, xb2, v3);
+    }
   }
 }
 
@@ -687,15 +932,21 @@ __global__ void k_invariants(GridP g, SpeciesDevT<T> s, int kind, double B0, dou
   }
 }
 
-__global__ void k_push_tables(GridP g, float *r, float *sn, float *cs) {
+__global__ void k_push_tables(GridP g, PushTables tb) {
   const int n = max(g.NX, g.NY);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    if (t < g.NX) r[t] = (float)(g.r_min * exp((t - G_) * g.dxi));
+    if (t < g.NX) {
+      const double r = g.r_min * exp((t - G_) * g.dxi);
+      const_cast<double *>(tb.r64)[t] = r;
+      const_cast<float *>(tb.r)[t] = (float)r;
+    }
     if (t < g.NY) {
       double s, c;
       sincos((t - G_) * g.dth, &s, &c);
-      sn[t] = (float)s;
-      cs[t] = (float)c;
+      const_cast<double *>(tb.s64)[t] = s;
+      const_cast<double *>(tb.c64)[t] = c;
+      const_cast<float *>(tb.s)[t] = (float)s;
+      const_cast<float *>(tb.c)[t] = (float)c;
     }
   }
 }
@@ -709,8 +960,8 @@ int blocks_for(int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_push_tables(const GridP &g, float *r, float *s, float *c, cudaStream_t st) {
-  k_push_tables<<<8, 256, 0, st>>>(g, r, s, c);
+cudaError_t launch_push_tables(const GridP &g, const PushTables &tb, cudaStream_t st) {
+  k_push_tables<<<8, 256, 0, st>>>(g, tb);
   COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
@@ -727,14 +978,34 @@ cudaError_t launch_load(const GridP &g, SpeciesDevT<T> s, int64_t k0, int64_t n,
 
 template <typename T>
 cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
-                        const PushTables &tb, int64_t n_bound, bool deposit,
-                        unsigned long long *diag, cudaStream_t st) {
+                        const PushTables &tb, const GuardList &gl, int64_t n_bound, bool deposit,
+                        unsigned long long *diag, const PushStreams &ps) {
   if (n_bound <= 0) return cudaGetLastError();
-  if (deposit)
-    k_push<T, true><<<blocks_for(n_bound), TPB, 0, st>>>(g, F, s, tb, diag);
-  else
-    k_push<T, false><<<blocks_for(n_bound), TPB, 0, st>>>(g, F, s, tb, diag);
-  COUNT_LAUNCH(1);
+  if constexpr (sizeof(T) == 8) {
+    if (deposit) k_push<true><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, s, diag);
+    else k_push<false><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, s, diag);
+    COUNT_LAUNCH(1);
+  } else {
+    cudaError_t e = cudaMemsetAsync(gl.count, 0, 2 * sizeof(unsigned long long), ps.main);
+    if (e != cudaSuccess) return e;
+    const int nb = blocks_for(n_bound);
+    k_classify<<<nb, TPB, 0, ps.main>>>(g, s, tb, gl);
+    if ((e = cudaEventRecord(ps.fork, ps.main)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ps.side, ps.fork, 0)) != cudaSuccess) return e;
+    // the guard kernels are FP64-pipe bound: a few one-warp blocks per SM reach every SM
+    // sub-partition's FP64 unit and leave the registers to the concurrent FP32 kernel
+    if (deposit) {
+      k_push_guard<true><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+      k_push_axis<true><<<152 * 4, 32, 0, ps.side>>>(g, F, s, gl, diag);
+      k_push32<true><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
+    } else {
+      k_push_guard<false><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+      k_push_axis<false><<<152 * 4, 32, 0, ps.side>>>(g, F, s, gl, diag);
+      k_push32<false><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
+    }
+    if ((e = cudaEventRecord(ps.done, ps.side)) != cudaSuccess) return e;
+    COUNT_LAUNCH(4);
+  }
   return cudaGetLastError();
 }
 
@@ -760,8 +1031,8 @@ cudaError_t launch_invariants(const GridP &g, SpeciesDevT<T> s, int kind, double
   template cudaError_t launch_load<T>(const GridP &, SpeciesDevT<T>, int64_t, int64_t,        \
                                       const grpic_particle_init &, double, cudaStream_t);     \
   template cudaError_t launch_push<T>(const GridP &, const FieldPtrsT<T> &, SpeciesDevT<T>,    \
-                                      const PushTables &, int64_t, bool, unsigned long long *, \
-                                      cudaStream_t);                                           \
+                                      const PushTables &, const GuardList &, int64_t, bool,    \
+                                      unsigned long long *, const PushStreams &);              \
   template cudaError_t launch_deposit<T>(const GridP &, const FieldPtrsT<T> &, SpeciesDevT<T>, \
                                          const PushTables &, int64_t, cudaStream_t);           \
   template cudaError_t launch_invariants<T>(const GridP &, SpeciesDevT<T>, int, double,        \
