@@ -1,12 +1,14 @@
 """Throughput of the GR PIC hot path (push + deposit + field update) on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                [--workload wald512] [--sort-every 10]
+                [--workload wald512] [--precision both|fp64|mixed] [--sort-every 10]
 
 A step is one full PIC step (Sec. 3.4 of arXiv:2511.17701) over the whole workload:
 field predict, (sort), fused push + deposit of both species, field advance. The default
 workload is the 512^2 Kerr (a = 0.9) Wald configuration with 32 particles per cell per
-species (16,777,216 particles), FP64, synthetic and seeded. Prints one JSON line.
+species (16,777,216 particles), synthetic and seeded. By default it is timed in FP64 (the
+line's value, with the end-to-end leg and the CPU oracle beside it) and then in mixed
+precision on the same workload (the "mixed" object). Prints one JSON line.
 
 --impl reference times the CPU oracle (FP64, OpenMP over particles) on the host cores,
 each step on a bounded sample of the same workload.
@@ -31,15 +33,28 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-# Algorithmic bytes of one particle-step of the fused FP64 push + deposit kernel
-# (SoA, read: i1, i2, dx1, dx2, u1, u2, u3, phi, w, tag; write: the same minus w plus the
-# previous position i1p, i2p, dx1p, dx2p): 4+4+8+8+24+8+8+1 = 65 B read,
+METRIC = ("particle-steps/sec (push+deposit+field) & % HBM roofline, FP64 vs mixed, 1 GB300")
+
+# Algorithmic bytes of one particle-step of the dominant kernel of each precision.
+# FP64 k_push<deposit> (SoA; read: i1, i2, dx1, dx2, u1, u2, u3, phi, w, tag; write: the same
+# minus w plus the previous position i1p, i2p, dx1p, dx2p): 4+4+8+8+24+8+8+1 = 65 B read,
 # 4+4+8+8+24+8+1 + 4+4+8+8 = 81 B written.
-BYTES_PER_PARTICLE_STEP = 65 + 81
-# FP64 operations per particle-step of the same kernel, counted by ncu on this kernel
-# (2 x dfma + dmul + dadd instructions executed / particles); see profiles/.
-FP64_FLOP_PER_PARTICLE_STEP = 3806
-FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (2 DFMA / clk / SM x 152 SMs x 2.07 GHz)
+FP64_BYTES_PER_PARTICLE_STEP = 65 + 81
+# Mixed k_push32<deposit> (FP32 offsets, momenta, phi and w; the guard bitmask): 4+4+4+4+12+4+4
+# +1 + 1/8 = 37 B read; i1p, i2p, dx1p, dx2p, i1, i2, dx1, dx2 (32) + u (12) + phi (4) = 48 B
+# written.
+MIXED_BYTES_PER_PARTICLE_STEP = 37 + 48
+# FP64 pipe operations (DFMA + DMUL + DADD thread instructions) per particle-step of
+# k_push<deposit> on the wald512 workload, counted by ncu (476 + 548 + 120); as flops
+# (2 DFMA + DMUL + DADD) 1620. The FP64 pipe issues 2 such operations per clock per SM.
+FP64_PIPE_OPS_PER_PARTICLE_STEP = 1144
+FP64_FLOP_PER_PARTICLE_STEP = 1620
+SMS, MAX_SM_GHZ = 152, 2.07
+FP64_PIPE_PEAK_GOPS = 2 * SMS * MAX_SM_GHZ  # 629 G operations/s
+# Warp instructions issued per particle by k_push32<deposit> on the wald512 workload (ncu:
+# 390.5 M over 8.39 M particles); an SM issues at most 4 warp instructions per clock.
+MIXED_WARP_INST_PER_PARTICLE = 46.5
+ISSUE_PEAK_GINST = 4 * SMS * MAX_SM_GHZ  # 1259 G warp instructions/s
 
 
 def measured_peaks():
@@ -199,7 +214,7 @@ def run_reference(args, ws, rank):
     oracle_steps(osim, args.warmup)
     times, parts = oracle_steps(osim, args.steps)
     value = parts / sum(times)
-    line = {"metric": "particle-steps/s (push+deposit+field), FP64", "value": value,
+    line = {"metric": METRIC, "value": value,
             "unit": "particle-steps/s", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -217,15 +232,16 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args, ws, rank, local):
+def measure(args, precision, ws, rank, local):
+    """Time args.steps full steps of the workload at one precision; returns the pieces of
+    the JSON line (and the Sim for the end-to-end leg)."""
     import torch
 
     from paper_2511_17701_gb300 import FIELD_WALD, Sim
 
-    torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     cfg = W.grid_config(args.workload, sort_every=args.sort_every, tile_r=args.tile,
-                        tile_theta=args.tile, precision=args.precision)
+                        tile_theta=args.tile, precision=precision)
     if args.ppc:
         cfg["ppc"] = args.ppc
     pl = W.pair_plasma(cfg, seed=cfg["seed"] + 1000 * rank)
@@ -263,60 +279,95 @@ def run_gpu(args, ws, rank, local):
     psteps = allreduce_sum(ws, psteps_local, device)
     value = psteps / (ms_max * 1e-3)
 
-    # dominant kernel: fused FP64 push + deposit, average launch time from events
-    push_ms = tim["push_ms"] / max(tim["push_calls"], 1)
+    # the dominant kernel, timed by the library's events around each launch on its stream
+    calls = max(tim["push_calls"], 1)
+    kernel_ms = tim["kernel_ms"] / calls
     parts_per_launch = 0.5 * (n_before + n_after) / 2
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
-    bytes_launch = parts_per_launch * BYTES_PER_PARTICLE_STEP
-    hbm_achieved = bytes_launch / (push_ms * 1e-3) / 1e9
-    if FP64_FLOP_PER_PARTICLE_STEP:
-        fl = parts_per_launch * FP64_FLOP_PER_PARTICLE_STEP / (push_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": fl / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "nominal FP64 rate from unit counts and clocks"}
+    bpp = FP64_BYTES_PER_PARTICLE_STEP if precision == "fp64" else MIXED_BYTES_PER_PARTICLE_STEP
+    hbm_achieved = parts_per_launch * bpp / (kernel_ms * 1e-3) / 1e9
+    if precision == "fp64":
+        ops = parts_per_launch * FP64_PIPE_OPS_PER_PARTICLE_STEP / (kernel_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": ops, "peak": FP64_PIPE_PEAK_GOPS,
+                    "unit": "G FP64-pipe op/s", "frac": ops / FP64_PIPE_PEAK_GOPS,
+                    "traffic": None,
+                    "peak_source": "nominal: 2 FP64 operations/clk/SM x 152 SMs x 2.07 GHz",
+                    "tflops": parts_per_launch * FP64_FLOP_PER_PARTICLE_STEP
+                    / (kernel_ms * 1e-3) / 1e12,
+                    "kernel": "k_push<deposit> (fused FP64 push + deposit)"}
     else:
-        roofline = {"bound": "hbm", "achieved": hbm_achieved,
-                    "peak": hbm_peak or 6800.0, "unit": "GB/s",
-                    "frac": hbm_achieved / (hbm_peak or 6800.0), "traffic": None,
-                    "peak_source": "measured" if hbm_peak else "fallback"}
-    roofline["kernel"] = "k_push<deposit> (fused FP64 push + deposit)"
-    roofline["avg_launch_ms"] = push_ms
-    hbm = {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak,
-           "frac": hbm_achieved / hbm_peak if hbm_peak else None,
-           "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP}
+        gi = parts_per_launch * MIXED_WARP_INST_PER_PARTICLE / (kernel_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": gi, "peak": ISSUE_PEAK_GINST,
+                    "unit": "G warp-instructions/s", "frac": gi / ISSUE_PEAK_GINST,
+                    "traffic": None,
+                    "peak_source": "nominal: 4 warp instructions/clk/SM x 152 SMs x 2.07 GHz",
+                    "kernel": "k_push32<deposit> (FP32 push + warp-reduced deposit; the "
+                              "guard-zone kernels run beside it on a second stream)"}
+    roofline["avg_launch_ms"] = kernel_ms
+    hbm = {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak or 6800.0,
+           "frac": hbm_achieved / (hbm_peak or 6800.0),
+           "peak_source": "measured" if hbm_peak else "fallback",
+           "bytes_per_particle_step": bpp, "kernel": roofline["kernel"]}
+    out = {"value": value, "ms_per_step": ms_max / args.steps, "roofline": roofline,
+           "hbm_roofline": hbm,
+           "phase_ms_per_step": {k: tim[k] / args.steps for k in
+                                 ("predict_ms", "sort_ms", "push_ms", "advance_ms")},
+           "gpu_launches": tim["launches"], "clocks": clk.summary(),
+           "workload": workload_desc(args.workload, cfg, 2 * n, precision),
+           "particles": 2 * n, "psteps": psteps}
+    return out, sim
 
-    # end to end through the C ABI with host buffers: per step the particle state goes
-    # from pinned host memory to the device, one step runs, and the state comes back
-    e2e = None
-    if not args.no_e2e:
-        host = []
+
+def end_to_end(args, sim, psteps, ws, device):
+    """Through the C ABI with host buffers: per step the particle state goes from pinned
+    host memory to the device, one full step runs, and the state comes back."""
+    import torch
+    host = []
+    for s in range(2):
+        st = sim.get_particles(s)
+        hs = {}
+        for k, t in sim.ptypes:
+            ht = torch.empty(st[k].shape, dtype=getattr(torch, np.dtype(t).name),
+                             pin_memory=True)
+            ht.numpy()[:] = st[k]
+            hs[k] = ht
+        host.append((hs, len(st["i1"])))
+    bi = sum(n_s * sum(np.dtype(t).itemsize for _, t in sim.ptypes) for _, n_s in host)
+    torch.cuda.synchronize(device)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
         for s in range(2):
-            st = sim.get_particles(s)
-            hs = {}
-            for k, t in sim.ptypes:
-                ht = torch.empty(st[k].shape, dtype=getattr(torch, np.dtype(t).name),
-                                 pin_memory=True)
-                ht.numpy()[:] = st[k]
-                hs[k] = ht
-            host.append((hs, len(st["i1"])))
-        bi = sum(n_s * sum(np.dtype(t).itemsize for _, t in sim.ptypes) for _, n_s in host)
+            sim.set_particles(s, host[s][0], sim.qm[s], sim.qc[s])
+        sim.step(1)
+        for s in range(2):
+            v = sim.species_views(s)
+            for k, _ in sim.ptypes:
+                host[s][0][k][: v[k].numel()].copy_(v[k], non_blocking=True)
         torch.cuda.synchronize(device)
-        barrier(ws)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            for s in range(2):
-                sim.set_particles(s, host[s][0], sim.qm[s], sim.qc[s])
-            sim.step(1)
-            for s in range(2):
-                v = sim.species_views(s)
-                for k, _ in sim.ptypes:
-                    host[s][0][k][: v[k].numel()].copy_(v[k], non_blocking=True)
-            torch.cuda.synchronize(device)
-        t_e2e = time.perf_counter() - t0
-        t_e2e = allreduce_max(ws, t_e2e, device)
-        e2e = {"value": psteps / t_e2e, "unit": "particle-steps/s", "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": bi}
+    t_e2e = time.perf_counter() - t0
+    t_e2e = allreduce_max(ws, t_e2e, device)
+    return {"value": psteps / t_e2e, "unit": "particle-steps/s", "h2d_bytes_per_step": bi,
+            "d2h_bytes_per_step": bi}
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    precisions = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    res = {}
+    e2e = None
+    for prec in precisions:
+        out, sim = measure(args, prec, ws, rank, local)
+        if prec == precisions[0] and not args.no_e2e:
+            e2e = end_to_end(args, sim, out["psteps"], ws, device)
+        del sim
+        torch.cuda.empty_cache()
+        res[prec] = out
+    main = res[precisions[0]]
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -327,29 +378,38 @@ def run_gpu(args, ws, rank, local):
         times, parts = oracle_steps(osim, args.cpu_steps)
         cpu = {"value": parts / sum(times), "unit": "particle-steps/s", "cores": host_cores(),
                "kind": "oracle",
-               "sample": "%d full PIC steps of the %s workload (%d particles%s), %.1f s" % (
+               "sample": "%d full FP64 PIC steps of the %s workload (%d particles%s), %.1f s" % (
                    args.cpu_steps, args.workload, parts // max(args.cpu_steps, 1),
                    "" if args.cpu_frac >= 1 else ", particles of %.1f%% of the cells"
                    % (100 * args.cpu_frac), sum(times))}
         del osim
     if rank == 0:
-        line = {"metric": "particle-steps/s (push+deposit+field), FP64",
-                "precision": args.precision,
-                "value": value, "unit": "particle-steps/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        line = {"metric": METRIC, "precision": precisions[0],
+                "value": main["value"], "unit": "particle-steps/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.precision == "fp64" else "f32 (f64 within the guard cells)",
+                "dtype": "f64" if precisions[0] == "fp64" else "f32 (f64 metric in the guard zones)",
                 "data": "synthetic (seeded workload generator)",
-                "config": {"workload": workload_desc(args.workload, cfg, 2 * n, args.precision),
+                "config": {"workload": main["workload"],
                            "sort_every": args.sort_every, "tile": args.tile,
                            "l2": "inputs larger than L2: particle state %.2f GB" % (
-                               2 * n * 89 / 1e9),
+                               main["particles"] * (89 if precisions[0] == "fp64" else 49) / 1e9),
                            "parallelism": "replica per GPU" if ws > 1 else "1 GPU"},
-                "roofline": roofline, "hbm_roofline": hbm,
-                "phase_ms_per_step": {k: tim[k] / args.steps for k in
-                                      ("predict_ms", "sort_ms", "push_ms", "advance_ms")},
-                "gpu_launches": tim["launches"], "e2e": e2e, "cpu_baseline": cpu,
-                "clocks": clk.summary()}
+                "roofline": main["roofline"], "hbm_roofline": main["hbm_roofline"],
+                "phase_ms_per_step": main["phase_ms_per_step"],
+                "gpu_launches": main["gpu_launches"], "e2e": e2e, "cpu_baseline": cpu,
+                "clocks": main["clocks"]}
+        if len(precisions) == 2:
+            m = res["mixed"]
+            line["mixed"] = {"value": m["value"], "unit": "particle-steps/s",
+                             "ms_per_step": m["ms_per_step"],
+                             "speedup_vs_fp64": m["value"] / main["value"],
+                             "workload": m["workload"], "roofline": m["roofline"],
+                             "hbm_roofline": m["hbm_roofline"],
+                             "phase_ms_per_step": m["phase_ms_per_step"],
+                             "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
+                             "error_bound": "<= 1e-5 relative per step on particle state vs "
+                                            "the FP64 oracle (tests/test_gpu_mixed.py)"}
         print(json.dumps(line), flush=True)
 
 
@@ -362,7 +422,8 @@ def main():
     ap.add_argument("--workload", default="wald512", choices=sorted(W.CONFIGS))
     ap.add_argument("--sort-every", type=int, default=10)
     ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"],
+                    help="both: FP64 (the line's value) and then mixed on the same workload")
     ap.add_argument("--ppc", type=int, default=0, help="override particles per cell per species "
                     "(a smaller case of the same workload, e.g. for profiling)")
     ap.add_argument("--cpu-frac", type=float, default=1.0,

@@ -281,6 +281,9 @@ typedef struct {
   double predict_ms, sort_ms, push_ms, deposit_ms, advance_ms;
   int64_t push_calls;   /* particle-kernel launches timed in push_ms                 */
   int64_t launches;     /* kernels launched by the library since the last reset      */
+  double kernel_ms;     /* the main push kernel alone (FP64: k_push; mixed: the FP32
+                           kernel, which runs beside the guard kernels), summed over
+                           push_calls launches                                        */
 } grpic_timing;
 
 /* Enables (1) or disables (0) the per-phase events. Off by default. */

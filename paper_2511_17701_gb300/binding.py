@@ -66,7 +66,7 @@ class ParticleInit(C.Structure):
 class Timing(C.Structure):
     _fields_ = [("predict_ms", C.c_double), ("sort_ms", C.c_double), ("push_ms", C.c_double),
                 ("deposit_ms", C.c_double), ("advance_ms", C.c_double),
-                ("push_calls", C.c_int64), ("launches", C.c_int64)]
+                ("push_calls", C.c_int64), ("launches", C.c_int64), ("kernel_ms", C.c_double)]
 
 
 class Diag(C.Structure):

@@ -41,7 +41,7 @@ __global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
 
 long long grpic_launches = 0;
 
-enum { PH_PREDICT = 0, PH_SORT, PH_PUSH, PH_DEPOSIT, PH_ADVANCE, PH_N };
+enum { PH_PREDICT = 0, PH_SORT, PH_PUSH, PH_DEPOSIT, PH_ADVANCE, PH_KERNEL, PH_N };
 
 struct grpic_ctx {
   grpic_config cfg;
@@ -197,20 +197,25 @@ cudaError_t copy(void *dst, const void *src, size_t bytes, cudaStream_t st) {
 
 // Records a start event on construction and a stop event on destruction when the
 // context's timing is on.
+// the next unused event pair of a phase (null when timing is off or events run out)
+std::pair<cudaEvent_t, cudaEvent_t> *next_events(grpic_ctx *c, int ph) {
+  if (!c->timing) return nullptr;
+  if (c->ev_used[ph] == c->ev[ph].size()) {
+    std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+    if (cudaEventCreate(&e.first) != cudaSuccess || cudaEventCreate(&e.second) != cudaSuccess)
+      return nullptr;
+    c->ev[ph].push_back(e);
+  }
+  return &c->ev[ph][c->ev_used[ph]++];
+}
+
 struct PhaseTimer {
   grpic_ctx *c;
   int ph;
   std::pair<cudaEvent_t, cudaEvent_t> *pr = nullptr;
   PhaseTimer(grpic_ctx *ctx, int phase) : c(ctx), ph(phase) {
-    if (!c->timing) return;
-    if (c->ev_used[ph] == c->ev[ph].size()) {
-      std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
-      if (cudaEventCreate(&e.first) != cudaSuccess || cudaEventCreate(&e.second) != cudaSuccess)
-        return;
-      c->ev[ph].push_back(e);
-    }
-    pr = &c->ev[ph][c->ev_used[ph]++];
-    cudaEventRecord(pr->first, c->stream);
+    pr = next_events(c, ph);
+    if (pr) cudaEventRecord(pr->first, c->stream);
   }
   ~PhaseTimer() {
     if (pr) cudaEventRecord(pr->second, c->stream);
@@ -221,7 +226,9 @@ struct PhaseTimer {
 template <typename T>
 cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, int k, bool deposit) {
   SpeciesState &sp = c->sp[k];
-  const PushStreams ps{c->stream, c->side, c->ev_fork[k], c->ev_done[k]};
+  const std::pair<cudaEvent_t, cudaEvent_t> *kt = next_events(c, PH_KERNEL);
+  const PushStreams ps{c->stream, c->side, c->ev_fork[k], c->ev_done[k],
+                       kt ? kt->first : nullptr, kt ? kt->second : nullptr};
   return launch_push<T>(c->g, F, dev_view<T>(sp, sp.live), c->tb, sp.gl, sp.n_bound, deposit,
                         c->diag, ps);
 }
@@ -720,6 +727,7 @@ grpic_status grpic_get_timing(grpic_ctx *ctx, grpic_timing *out) {
   out->push_ms = ms[PH_PUSH];
   out->deposit_ms = ms[PH_DEPOSIT];
   out->advance_ms = ms[PH_ADVANCE];
+  out->kernel_ms = ms[PH_KERNEL];
   out->push_calls = ctx->push_calls;
   out->launches = grpic_launches;
   ctx->push_calls = 0;

@@ -279,6 +279,7 @@ struct GuardList {
 struct PushStreams {
   cudaStream_t main, side;
   cudaEvent_t fork, done;
+  cudaEvent_t t0, t1;  // when not null: recorded on `main` around the main push kernel
 };
 
 template <typename T>

@@ -980,10 +980,16 @@ template <typename T>
 cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
                         const PushTables &tb, const GuardList &gl, int64_t n_bound, bool deposit,
                         unsigned long long *diag, const PushStreams &ps) {
-  if (n_bound <= 0) return cudaGetLastError();
+  if (n_bound <= 0) {  // keep a requested event pair recorded (zero duration)
+    if (ps.t0) cudaEventRecord(ps.t0, ps.main);
+    if (ps.t1) cudaEventRecord(ps.t1, ps.main);
+    return cudaGetLastError();
+  }
   if constexpr (sizeof(T) == 8) {
+    if (ps.t0) cudaEventRecord(ps.t0, ps.main);
     if (deposit) k_push<true><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, s, diag);
     else k_push<false><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, s, diag);
+    if (ps.t1) cudaEventRecord(ps.t1, ps.main);
     COUNT_LAUNCH(1);
   } else {
     cudaError_t e = cudaMemsetAsync(gl.count, 0, 2 * sizeof(unsigned long long), ps.main);
@@ -997,12 +1003,14 @@ cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s
     if (deposit) {
       k_push_guard<true><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
       k_push_axis<true><<<152 * 4, 32, 0, ps.side>>>(g, F, s, gl, diag);
-      k_push32<true><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
     } else {
       k_push_guard<false><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
       k_push_axis<false><<<152 * 4, 32, 0, ps.side>>>(g, F, s, gl, diag);
-      k_push32<false><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
     }
+    if (ps.t0) cudaEventRecord(ps.t0, ps.main);
+    if (deposit) k_push32<true><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
+    else k_push32<false><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
+    if (ps.t1) cudaEventRecord(ps.t1, ps.main);
     if ((e = cudaEventRecord(ps.done, ps.side)) != cudaSuccess) return e;
     COUNT_LAUNCH(4);
   }
