@@ -39,75 +39,55 @@ static int64_t plane_size(const ora_params *p) { return (int64_t)NX_of(p) * NY_o
 /* element (i, j) of a plane in the storage convention of grpic_oracle.h */
 #define AT(pl, i, j) (pl)[(int64_t)((j) + G) * NX + ((i) + G)]
 
-/* ------------------------------------------------------------------------ */
-/* Metric, Appendix A.  The oracle works in physical (r, theta) from the      */
-/* closed forms of the Kerr-Schild 3+1 split and converts to code units by    */
-/* the chain rule with f = dr/dx1 = dxi r, g = dtheta/dx2 = dtheta, dphi = 1. */
-/* M = 1 for Kerr-Schild, M = 0 (and a = 0) for the flat kerr_schild_0.       */
-/* ------------------------------------------------------------------------ */
-static void metric_eval(const ora_params *p, double x1, double x2, int clamp, int derivs,
-                        ora_metric *m) {
-  const double M = p->metric == 1 ? 1.0 : 0.0;
-  const double a = p->metric == 1 ? p->a : 0.0;
-  const double dxi = dxi_of(p), dth = dth_of(p);
-  double r = p->r_min * exp(x1 * dxi);
-  double th = x2 * dth;
-  if (clamp) { /* Sec. 3.3.2: theta replaced by SMALL_ANGLE_GR near the axes */
-    if (th < p->small_angle) th = p->small_angle;
-    if (th > PI_ - p->small_angle) th = PI_ - p->small_angle;
-  }
-  double s = sin(th), c = cos(th), s2 = s * s, c2 = c * c;
-  double Sig = r * r + a * a * c2;
-  double Del = r * r - 2.0 * M * r + a * a;
-  double AA = (r * r + a * a) * (r * r + a * a) - a * a * Del * s2;
-  double z = 2.0 * M * r / Sig;
-  /* physical spatial metric h_ij and its inverse (Appendix A) */
-  double h_rr = 1.0 + z, h_rp = -a * (1.0 + z) * s2, h_tt = Sig, h_pp = AA * s2 / Sig;
-  double P = Sig * (Sig + 2.0 * M * r);
-  double H_rr = AA / P, H_rp = a / Sig, H_tt = 1.0 / Sig, H_pp = 1.0 / (Sig * s2);
-  double alpha = 1.0 / sqrt(1.0 + z);
-  double beta_r = z / (1.0 + z);
-  double f = dxi * r, g = dth;
-  m->r = r; m->th = th; m->f = f; m->g = g;
-  m->h11 = f * f * h_rr; m->h13 = f * h_rp; m->h22 = g * g * h_tt; m->h33 = h_pp;
-  m->H11 = H_rr / (f * f); m->H13 = H_rp / f; m->H22 = H_tt / (g * g); m->H33 = H_pp;
-  m->alpha = alpha; m->beta1 = beta_r / f;
-  m->sqrt_h = f * g * Sig * s * sqrt(1.0 + z);  /* sqrt(h) = Sigma sin(theta) / alpha */
-  m->sqrt_ht = f * g * Sig * sqrt(1.0 + z);     /* sqrt(h~), h~ = h / sin^2 theta    */
-  if (!derivs) return;
-  /* physical derivatives (d/dr, d/dtheta) of the building blocks */
-  double dr_Sig = 2.0 * r, dt_Sig = -2.0 * a * a * c * s;
-  double dr_Del = 2.0 * r - 2.0 * M;
-  double dr_A = 4.0 * r * (r * r + a * a) - a * a * s2 * dr_Del;
-  double dt_A = -2.0 * a * a * Del * s * c;
-  double dr_z = 2.0 * M / Sig - 2.0 * M * r * dr_Sig / (Sig * Sig);
-  double dt_z = -2.0 * M * r * dt_Sig / (Sig * Sig);
-  double dr_P = dr_Sig * (Sig + 2.0 * M * r) + Sig * (dr_Sig + 2.0 * M);
-  double dt_P = dt_Sig * (Sig + 2.0 * M * r) + Sig * dt_Sig;
-  double dr_Hrr = (dr_A * P - AA * dr_P) / (P * P);
-  double dt_Hrr = (dt_A * P - AA * dt_P) / (P * P);
-  double dr_Hrp = -a * dr_Sig / (Sig * Sig), dt_Hrp = -a * dt_Sig / (Sig * Sig);
-  double dr_Htt = -dr_Sig / (Sig * Sig), dt_Htt = -dt_Sig / (Sig * Sig);
-  double dr_Hpp = -dr_Sig / (Sig * Sig * s2);
-  double dt_Hpp = -(dt_Sig * s2 + Sig * 2.0 * s * c) / (Sig * s2 * Sig * s2);
-  double a3 = alpha * alpha * alpha;
-  double dr_alpha = -0.5 * a3 * dr_z, dt_alpha = -0.5 * a3 * dt_z;
-  double dr_beta = dr_z / ((1.0 + z) * (1.0 + z)), dt_beta = dt_z / ((1.0 + z) * (1.0 + z));
-  /* chain rule to code coordinates: d/dx1 = f d/dr with df/dx1 = dxi f, d/dx2 = g d/dtheta */
-  m->d1H11 = dr_Hrr / f - 2.0 * dxi * H_rr / (f * f);
-  m->d1H13 = dr_Hrp - dxi * H_rp / f;
-  m->d1H22 = f * dr_Htt / (g * g);
-  m->d1H33 = f * dr_Hpp;
-  m->d1alpha = f * dr_alpha;
-  m->d1beta1 = dr_beta - dxi * beta_r / f;
-  m->d2H11 = g * dt_Hrr / (f * f);
-  m->d2H13 = g * dt_Hrp / f;
-  m->d2H22 = dt_Htt / g;
-  m->d2H33 = g * dt_Hpp;
-  m->d2alpha = g * dt_alpha;
-  m->d2beta1 = g * dt_beta / f;
-}
+/* Yee offsets (Fig. 1): B^1 (i, j+1/2), B^2 (i+1/2, j), B^3 (i+1/2, j+1/2),
+ *                       D^1 (i+1/2, j), D^2 (i, j+1/2), D^3 (i, j).          */
+static const double SB[3][2] = {{0.0, 0.5}, {0.5, 0.0}, {0.5, 0.5}};
+static const double SD[3][2] = {{0.5, 0.0}, {0.0, 0.5}, {0.0, 0.0}};
 
+/* The metric, tetrads, Boris step, geodesic substep, interpolation and the frozen-field
+ * step, in double (the oracle) ... */
+#define REAL double
+#define FN(name) name
+#define METRIC ora_metric
+#define RSQRT sqrt
+#define REXP exp
+#define RSIN sin
+#define RCOS cos
+#define RE(x) (x)
+#include "pusher_generic.inc"
+#undef REAL
+#undef FN
+#undef METRIC
+#undef RSQRT
+#undef REXP
+#undef RSIN
+#undef RCOS
+#undef RE
+
+/* ... and in double complex, for complex-step derivatives of the frozen-field push */
+typedef struct {
+  double complex r, th, f, g, h11, h22, h33, h13, H11, H22, H33, H13;
+  double complex alpha, beta1, sqrt_h, sqrt_ht;
+  double complex d1H11, d1H22, d1H33, d1H13, d1alpha, d1beta1;
+  double complex d2H11, d2H22, d2H33, d2H13, d2alpha, d2beta1;
+} ora_metric_cs;
+#define REAL double complex
+#define FN(name) name##_cs
+#define METRIC ora_metric_cs
+#define RSQRT csqrt
+#define REXP cexp
+#define RSIN csin
+#define RCOS ccos
+#define RE(x) creal(x)
+#include "pusher_generic.inc"
+#undef REAL
+#undef FN
+#undef METRIC
+#undef RSQRT
+#undef REXP
+#undef RSIN
+#undef RCOS
+#undef RE
 /* Polar area of the half cell next to the axis at radius x1 (Sec. 3.3.2 and the
  * closed form of Appendix A), per unit phi: integral_0^{1/2} sqrt(h) dx2 with Sigma
  * taken at its axis value. Reading: no factor 2 pi (dphi = 1, as the closed form). */
@@ -191,107 +171,6 @@ static void wald_fields_point(const ora_params *p, int kind, double B0, double x
   D[1] = m.H22 * (E2 + m.beta1 * shB3) / m.alpha;
   D[2] = (m.H13 * E1 + m.H33 * rhs3) / m.alpha;
 }
-
-/* ------------------------------------------------------------------------ */
-/* Tetrads, Appendix A. Reading of the garbled explicit forms: the matrices   */
-/* are used, giving a_r = a_r^/sqrt(h^11) + (h_13/sqrt(h_33)) a_phi^ and      */
-/* A^phi = -sqrt(h^11)(h_13/h_33) A^r^ + A^phi^/sqrt(h_33).                   */
-/* ------------------------------------------------------------------------ */
-static void vec_to_hat(const ora_metric *m, const double A[3], double Ah[3]) {
-  Ah[0] = A[0] / sqrt(m->H11);
-  Ah[1] = sqrt(m->h22) * A[1];
-  Ah[2] = m->h13 / sqrt(m->h33) * A[0] + sqrt(m->h33) * A[2];
-}
-static void hat_to_vec(const ora_metric *m, const double Ah[3], double A[3]) {
-  A[0] = sqrt(m->H11) * Ah[0];
-  A[1] = Ah[1] / sqrt(m->h22);
-  A[2] = -sqrt(m->H11) * m->h13 / m->h33 * Ah[0] + Ah[2] / sqrt(m->h33);
-}
-static void cov_to_hat(const ora_metric *m, const double a[3], double ah[3]) {
-  ah[0] = sqrt(m->H11) * a[0] - sqrt(m->H11) * m->h13 / m->h33 * a[2];
-  ah[1] = a[1] / sqrt(m->h22);
-  ah[2] = a[2] / sqrt(m->h33);
-}
-static void hat_to_cov(const ora_metric *m, const double ah[3], double a[3]) {
-  a[0] = ah[0] / sqrt(m->H11) + m->h13 / sqrt(m->h33) * ah[2];
-  a[1] = sqrt(m->h22) * ah[1];
-  a[2] = sqrt(m->h33) * ah[2];
-}
-
-/* gamma = sqrt(1 + h^ij u_i u_j) for a massive particle (Sec. 2.3) */
-static double gamma_of(const ora_metric *m, const double u[3]) {
-  return sqrt(1.0 + m->H11 * u[0] * u[0] + m->H22 * u[1] * u[1] + m->H33 * u[2] * u[2] +
-              2.0 * m->H13 * u[0] * u[2]);
-}
-
-/* ------------------------------------------------------------------------ */
-/* EM stage: the special-relativistic Boris step in the tetrad frame          */
-/* (Sec. 3.1). One call advances u_hat over coordinate time dt/2, i.e. proper */
-/* FIDO time alpha dt/2; hq = qm * alpha * dt / 2. Reading: textbook Boris    */
-/* (half electric kick, rotation by t = (hq/2) B/gamma, s = 2t/(1+t^2), half  */
-/* kick); fields in the FIDO frame.                                            */
-/* ------------------------------------------------------------------------ */
-static void boris(double u[3], const double Dh[3], const double Bh[3], double hq) {
-  double e = 0.5 * hq;
-  double um[3] = {u[0] + e * Dh[0], u[1] + e * Dh[1], u[2] + e * Dh[2]};
-  double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-  double t[3] = {e * Bh[0] / gm, e * Bh[1] / gm, e * Bh[2] / gm};
-  double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-  double sf = 2.0 / (1.0 + t2);
-  double up[3] = {um[0] + (um[1] * t[2] - um[2] * t[1]),
-                  um[1] + (um[2] * t[0] - um[0] * t[2]),
-                  um[2] + (um[0] * t[1] - um[1] * t[0])};
-  double uq[3] = {um[0] + sf * (up[1] * t[2] - up[2] * t[1]),
-                  um[1] + sf * (up[2] * t[0] - up[0] * t[2]),
-                  um[2] + sf * (up[0] * t[1] - up[1] * t[0])};
-  u[0] = uq[0] + e * Dh[0];
-  u[1] = uq[1] + e * Dh[1];
-  u[2] = uq[2] + e * Dh[2];
-}
-
-/* ------------------------------------------------------------------------ */
-/* Geodesic momentum push, Eq. (discretized-geodesic-u): implicit midpoint    */
-/* with a fixed number of iterations, metric and its derivatives at x^n.      */
-/* Readings: the derivatives are those of the contravariant h^{jj}, h^{13};   */
-/* u_3 is not changed by this substep.                                         */
-/* ------------------------------------------------------------------------ */
-static void geodesic_u(const ora_params *p, const ora_metric *m, double u[3]) {
-  double u0[3] = {u[0], u[1], u[2]};
-  double ut[3] = {u[0], u[1], u[2]};
-  const double dt = p->dt;
-  for (int it = 0; it < p->n_iter; ++it) {
-    double ub[3] = {0.5 * (u0[0] + ut[0]), 0.5 * (u0[1] + ut[1]), 0.5 * (u0[2] + ut[2])};
-    double U0 = gamma_of(m, ub) / m->alpha; /* u^0 = gamma / alpha */
-    double dh1 = m->d1H11 * ub[0] * ub[0] + m->d1H22 * ub[1] * ub[1] +
-                 m->d1H33 * ub[2] * ub[2] + 2.0 * m->d1H13 * ub[0] * ub[2];
-    double dh2 = m->d2H11 * ub[0] * ub[0] + m->d2H22 * ub[1] * ub[1] +
-                 m->d2H33 * ub[2] * ub[2] + 2.0 * m->d2H13 * ub[0] * ub[2];
-    double F1 = -m->alpha * U0 * m->d1alpha + ub[0] * m->d1beta1 - dh1 / (2.0 * U0);
-    double F2 = -m->alpha * U0 * m->d2alpha + ub[0] * m->d2beta1 - dh2 / (2.0 * U0);
-    ut[0] = u0[0] + dt * F1;
-    ut[1] = u0[1] + dt * F2;
-    ut[2] = u0[2];
-  }
-  u[0] = ut[0]; u[1] = ut[1]; u[2] = ut[2];
-}
-
-/* ------------------------------------------------------------------------ */
-/* Field interpolation to the particle (step 2 of Sec. 3.1). Reading: bilinear */
-/* in code coordinates from each component's own Yee location (Fig. 1), ghost */
-/* rows across the axis filled with the symmetry parity beforehand.            */
-/* ------------------------------------------------------------------------ */
-static double interp(const double *pl, int NX, double x1, double x2, double s1, double s2) {
-  double y1 = x1 - s1, y2 = x2 - s2;
-  int i0 = (int)floor(y1), j0 = (int)floor(y2);
-  double w1 = y1 - i0, w2 = y2 - j0;
-  return (1.0 - w1) * (1.0 - w2) * AT(pl, i0, j0) + w1 * (1.0 - w2) * AT(pl, i0 + 1, j0) +
-         (1.0 - w1) * w2 * AT(pl, i0, j0 + 1) + w1 * w2 * AT(pl, i0 + 1, j0 + 1);
-}
-
-/* Yee offsets (Fig. 1): B^1 (i, j+1/2), B^2 (i+1/2, j), B^3 (i+1/2, j+1/2),
- *                       D^1 (i+1/2, j), D^2 (i, j+1/2), D^3 (i, j).          */
-static const double SB[3][2] = {{0.0, 0.5}, {0.5, 0.0}, {0.5, 0.5}};
-static const double SD[3][2] = {{0.5, 0.0}, {0.0, 0.5}, {0.0, 0.0}};
 
 /* ------------------------------------------------------------------------ */
 /* One particle, the eleven steps of Sec. 3.1, then the boundaries of         */
@@ -970,4 +849,45 @@ double ora_time_step(const ora_params *p, double cfl) {
     }
   return cfl * best;
 }
-int ora_version(void) { return 1; }
+/* Frozen-field push of n test particles for n_steps steps (steps 2-11 of Sec. 3.1, no
+ * deposit) with the em-plane fields of F times `scale` and both implicit pushes iterated
+ * p->n_iter times. state: [6][n] doubles x1, x2, phi, u1, u2, u3 (absolute code
+ * coordinates), advanced in place. A particle whose step would leave the domain interior
+ * (horizon layer, outer edge, an axis) is set to NaN and stays NaN. */
+void ora_push_frozen(const ora_params *p, const double *F, double scale, double qm,
+                     int n_steps, int64_t n, double *state) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t k = 0; k < n; ++k) {
+    double x[2] = {state[k], state[n + k]}, phi = state[2 * n + k];
+    double u[3] = {state[3 * n + k], state[4 * n + k], state[5 * n + k]};
+    int bad = !(x[0] == x[0]);
+    for (int st = 0; st < n_steps && !bad; ++st) bad = frozen_step(p, F, scale, qm, x, u, &phi);
+    const double v[6] = {x[0], x[1], phi, u[0], u[1], u[2]};
+    for (int q = 0; q < 6; ++q) state[q * n + k] = bad ? NAN : v[q];
+  }
+}
+
+/* The same in complex arithmetic: the state is re + i im and the scale scale_re + i scale_im.
+ * With the perturbation i e (e ~ 1e-30) on one input, Im(output) / e is the derivative of
+ * the double map with respect to that input, exact to rounding (complex step). */
+void ora_push_frozen_cs(const ora_params *p, const double *F, double scale_re, double scale_im,
+                        double qm, int n_steps, int64_t n, double *re, double *im) {
+  const double complex scale = scale_re + scale_im * I;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t k = 0; k < n; ++k) {
+    double complex x[2], u[3], phi;
+    for (int q = 0; q < 2; ++q) x[q] = re[q * n + k] + im[q * n + k] * I;
+    phi = re[2 * n + k] + im[2 * n + k] * I;
+    for (int q = 0; q < 3; ++q) u[q] = re[(3 + q) * n + k] + im[(3 + q) * n + k] * I;
+    int bad = !(creal(x[0]) == creal(x[0]));
+    for (int st = 0; st < n_steps && !bad; ++st)
+      bad = frozen_step_cs(p, F, scale, qm, x, u, &phi);
+    const double complex v[6] = {x[0], x[1], phi, u[0], u[1], u[2]};
+    for (int q = 0; q < 6; ++q) {
+      re[q * n + k] = bad ? NAN : creal(v[q]);
+      im[q * n + k] = bad ? NAN : cimag(v[q]);
+    }
+  }
+}
+
+int ora_version(void) { return 2; }

@@ -31,7 +31,8 @@ FIELD_ZERO, FIELD_WALD, FIELD_VERTICAL = 0, 1, 2
 def build(force: bool = False) -> str:
     """Compile the oracle (plain C, -O2 -ffp-contract=off, OpenMP over particles)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
-            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "grpic_oracle.h"))):
+            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "grpic_oracle.h")),
+            os.path.getmtime(os.path.join(HERE, "pusher_generic.inc"))):
         tmp = LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC",
                                "-shared", "-o", tmp, SRC, "-lm"])
@@ -110,6 +111,9 @@ def lib():
         L.ora_sort_key.restype = C.c_uint32
         L.ora_step.argtypes = [P, _PD, PP, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                C.c_int64, C.POINTER(C.c_int64)]
+        L.ora_push_frozen.argtypes = [P, _PD, C.c_double, C.c_double, C.c_int, C.c_int64, _PD]
+        L.ora_push_frozen_cs.argtypes = [P, _PD, C.c_double, C.c_double, C.c_double, C.c_int,
+                                         C.c_int64, _PD, _PD]
         _lib = L
     return _lib
 
@@ -308,3 +312,54 @@ class OracleSim:
         self._sync_n(arr)
         self.counters += cnt
         self.step_index += n_steps
+
+
+# ---------------------------------------------------------------------------------------
+# Frozen-field test particles and their exact FP64 Jacobian (complex step)
+# ---------------------------------------------------------------------------------------
+FROZEN_STATE = ("x1", "x2", "phi", "u1", "u2", "u3")
+CS_STEP = 1e-30
+
+
+def _frozen_params(osim, n_iter):
+    p = make_params(dict(osim.cfg, dt=osim.dt))
+    if n_iter:
+        p.n_iter = int(n_iter)
+    return p
+
+
+def frozen_push(osim, state, scale, qm, n_steps, n_iter=None):
+    """Push test particles n_steps steps in osim's em-plane fields times `scale` (steps 2-11
+    of Sec. 3.1, no deposit). state: (6, n) array x1, x2, phi, u1, u2, u3 (absolute code
+    coordinates). Both implicit pushes run n_iter times (default: the configuration's).
+    Returns the new state; particles that reached a boundary are NaN."""
+    st = np.array(state, dtype=np.float64, order="C").reshape(6, -1).copy()
+    lib().ora_push_frozen(C.byref(_frozen_params(osim, n_iter)), _dp(osim.F), float(scale),
+                          float(qm), int(n_steps), st.shape[1], _dp(st))
+    return st
+
+
+def frozen_jacobian(osim, state, scale, qm, n_steps, n_iter=None, inputs=None):
+    """d(final state)/d(inputs) of frozen_push by the complex step (exact to rounding).
+
+    inputs: names among FROZEN_STATE and "scale" (default all seven). Returns the final
+    state (6, n) and J with shape (n, 6, len(inputs))."""
+    inputs = list(inputs or (list(FROZEN_STATE) + ["scale"]))
+    st0 = np.array(state, dtype=np.float64, order="C").reshape(6, -1)
+    n = st0.shape[1]
+    p = _frozen_params(osim, n_iter)
+    J = np.zeros((n, 6, len(inputs)))
+    final = None
+    for c, name in enumerate(inputs):
+        re = st0.copy()
+        im = np.zeros_like(re)
+        s_im = 0.0
+        if name == "scale":
+            s_im = CS_STEP
+        else:
+            im[FROZEN_STATE.index(name)] = CS_STEP
+        lib().ora_push_frozen_cs(C.byref(p), _dp(osim.F), float(scale), s_im, float(qm),
+                                 int(n_steps), n, _dp(re), _dp(im))
+        J[:, :, c] = (im / CS_STEP).T
+        final = re
+    return final, J
