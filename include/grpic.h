@@ -271,6 +271,44 @@ GRPIC_API grpic_status grpic_sort_permutation_noalloc(int n_r, int n_theta, int 
                                                       int64_t n, uint32_t *perm,
                                                       int64_t *n_alive, void *stream);
 
+/* --- adjoint of the pusher over frozen fields ---------------------------------------- */
+
+/* Test particles pushed through the fields the context holds, frozen (steps 2-11 of
+ * Sec. 3.1, no deposit, no field update), and the gradients of their final state with
+ * respect to the initial state and the field amplitude. FP64 contexts only.
+ *
+ * State layout (device, caller-owned): [6][n] doubles, rows x1, x2 (absolute code
+ * coordinates), phi, u_1, u_2, u_3 (covariant momenta per unit mass). The fields are the
+ * em planes (B, D) times b0 / field_b0, where field_b0 is the amplitude given to
+ * grpic_init_fields (1 for GRPIC_FIELD_USER); the Wald and vertical fields are linear in B0,
+ * so b0 is the field amplitude. Both implicit substeps iterate to an exact repeat of the
+ * iterate, at most n_iter times. A particle whose step would leave 0 <= x1 < n_r,
+ * 0 <= x2 <= n_theta (the horizon layer, the outer edge or an axis, where the boundary rules
+ * of Sec. 3.3.3 act) is frozen and reported as NaN.
+ *
+ * grpic_adjoint_forward: state_out = the state after n_steps steps; ckpt receives the state
+ * at steps 0, ckpt_every, 2 ckpt_every, ... < n_steps: ceil(n_steps / ckpt_every) x 6 x n
+ * doubles (may be null when n_steps == 0).
+ * Errors: GRPIC_ESTATE (mixed context, fields not initialised), GRPIC_EINVAL (n < 0,
+ * n_steps < 0, ckpt_every < 1, n_iter outside [1, 1000], field_b0 = 0, null buffers). */
+GRPIC_API grpic_status grpic_adjoint_forward(grpic_ctx *ctx, int64_t n, double qm, double b0,
+                                             int n_steps, int ckpt_every, int n_iter,
+                                             const double *state0, double *state_out,
+                                             double *ckpt);
+
+/* The reverse sweep of the same push (same n, qm, b0, n_steps, ckpt_every, n_iter and the
+ * ckpt written by grpic_adjoint_forward): given grad_out = dL/d(final state) ([6][n]),
+ * writes grad_state0 = dL/d(initial state) ([6][n]), grad_b0_pp[k] = particle k's part of
+ * dL/db0 ([n]) and grad_b0[0] = their sum (deterministic order). Each checkpoint segment is
+ * recomputed into scratch (ckpt_every x 6 x n doubles); the step Jacobians use the
+ * implicit-function theorem at the implicit substeps. Particles reported NaN by the forward
+ * get zero gradients where their grad_out is zero, NaN otherwise. Errors: as the forward. */
+GRPIC_API grpic_status grpic_adjoint_backward(grpic_ctx *ctx, int64_t n, double qm, double b0,
+                                              int n_steps, int ckpt_every, int n_iter,
+                                              const double *ckpt, const double *grad_out,
+                                              double *grad_state0, double *grad_b0_pp,
+                                              double *grad_b0, double *scratch);
+
 /* --- diagnostics ------------------------------------------------------------------ */
 
 /* Per-phase device time of the hot path, measured with CUDA events recorded on the

@@ -6,5 +6,13 @@ from ._build import build
 from .binding import (ADVANCE, FIELD_USER, FIELD_VERTICAL, FIELD_WALD, FIELD_ZERO, NPLANES,
                       PREDICT, GrpicError, Sim, lib)
 
+
 __all__ = ["build", "lib", "Sim", "GrpicError", "FIELD_ZERO", "FIELD_WALD", "FIELD_VERTICAL",
-           "FIELD_USER", "PREDICT", "ADVANCE", "NPLANES"]
+           "FIELD_USER", "PREDICT", "ADVANCE", "NPLANES", "PushAdjoint", "push_adjoint"]
+
+
+def __getattr__(name):  # the autograd Function needs torch; import it on first use
+    if name in ("PushAdjoint", "push_adjoint"):
+        from . import adjoint
+        return getattr(adjoint, name)
+    raise AttributeError(name)

@@ -29,7 +29,8 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_get_particles", "grpic_species_arrays", "grpic_plane_ptr", "grpic_push",
            "grpic_deposit", "grpic_field_step", "grpic_sort", "grpic_step",
            "grpic_get_diagnostics", "grpic_set_timing", "grpic_get_timing", "grpic_last_error",
-           "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants"]
+           "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants",
+           "grpic_adjoint_forward", "grpic_adjoint_backward"]
 
 
 class GrpicError(RuntimeError):
@@ -118,6 +119,10 @@ def lib(build: bool = True):
                                                      P, C.c_int64, P, P, P]
         L.grpic_destroy.argtypes = [P]
         L.grpic_destroy.restype = None
+        L.grpic_adjoint_forward.argtypes = [P, C.c_int64, C.c_double, C.c_double, C.c_int,
+                                            C.c_int, C.c_int, P, P, P]
+        L.grpic_adjoint_backward.argtypes = [P, C.c_int64, C.c_double, C.c_double, C.c_int,
+                                             C.c_int, C.c_int, P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -303,6 +308,45 @@ class Sim:
                     "invariants")
         self.sync()
         return E[:n].cpu().numpy(), L[:n].cpu().numpy()
+
+    # --- adjoint of the pusher over frozen fields -------------------------------------
+    def _adjoint_state(self, t, what):
+        torch = self.torch
+        if t.dtype != torch.float64 or t.device != self.device or t.dim() != 2 or t.shape[0] != 6:
+            raise GrpicError("%s: expected a (6, n) float64 tensor on %s" % (what, self.device))
+        return t.contiguous()
+
+    def adjoint_forward(self, state0, qm, b0, n_steps, ckpt_every, n_iter):
+        """grpic_adjoint_forward: returns (final state (6, n), checkpoints)."""
+        torch = self.torch
+        state0 = self._adjoint_state(state0, "adjoint_forward")
+        n = state0.shape[1]
+        out = torch.empty_like(state0)
+        n_ck = (n_steps + ckpt_every - 1) // ckpt_every if n_steps > 0 else 0
+        ckpt = torch.empty((n_ck, 6, n), dtype=torch.float64, device=self.device)
+        self._check(self.L.grpic_adjoint_forward(self.ctx, n, qm, b0, n_steps, ckpt_every, n_iter,
+                                                 state0.data_ptr(), out.data_ptr(),
+                                                 ckpt.data_ptr() if n_ck else None),
+                    "adjoint_forward")
+        return out, ckpt
+
+    def adjoint_backward(self, ckpt, grad_out, qm, b0, n_steps, ckpt_every, n_iter):
+        """grpic_adjoint_backward: returns (d/d state0 (6, n), d/d b0 per particle (n,),
+        d/d b0 (1,))."""
+        torch = self.torch
+        grad_out = self._adjoint_state(grad_out, "adjoint_backward")
+        n = grad_out.shape[1]
+        gin = torch.empty_like(grad_out)
+        gpp = torch.empty(max(n, 1), dtype=torch.float64, device=self.device)
+        gsum = torch.empty(1, dtype=torch.float64, device=self.device)
+        scratch = torch.empty((min(ckpt_every, max(n_steps, 1)), 6, n), dtype=torch.float64,
+                              device=self.device) if n_steps > 0 else None
+        self._check(self.L.grpic_adjoint_backward(
+            self.ctx, n, qm, b0, n_steps, ckpt_every, n_iter,
+            ckpt.data_ptr() if ckpt.numel() else None, grad_out.data_ptr(), gin.data_ptr(),
+            gpp.data_ptr(), gsum.data_ptr(), scratch.data_ptr() if scratch is not None else None),
+            "adjoint_backward")
+        return gin, gpp[:n], gsum
 
     # --- hot path -------------------------------------------------------------------
     def push(self, s):

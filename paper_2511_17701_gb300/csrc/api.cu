@@ -54,6 +54,7 @@ struct grpic_ctx {
   cudaStream_t side = nullptr;  // guard kernels of the mixed push
   cudaEvent_t ev_fork[GRPIC_MAX_SPECIES] = {}, ev_done[GRPIC_MAX_SPECIES] = {};
   bool bound = false, metric_ready = false, fields_ready = false;
+  double field_b0 = 1.0;  // amplitude of the analytic field in the planes (1 for user fields)
   size_t off_planes = 0, off_tab = 0, off_polar = 0, off_dt = 0, off_diag = 0, off_ptab = 0;
   size_t off_keys[2] = {}, off_vals[2] = {}, off_hist = 0, off_bsum = 0, off_alive = 0;
   size_t off_stage = 0;
@@ -444,6 +445,7 @@ grpic_status grpic_init_fields(grpic_ctx *ctx, int kind, double B0) {
     CK(launch_field_finish_init<double>(ctx->g, ctx->F64, kind == GRPIC_FIELD_USER, ctx->stream));
   }
   ctx->fields_ready = true;
+  ctx->field_b0 = (kind == GRPIC_FIELD_WALD || kind == GRPIC_FIELD_VERTICAL) ? B0 : 1.0;
   ctx->step = 0;
   return GRPIC_OK;
 }
@@ -681,6 +683,46 @@ grpic_status grpic_step(grpic_ctx *ctx, int n_steps) {
     }
     ++ctx->step;
   }
+  return GRPIC_OK;
+}
+
+static grpic_status adjoint_args(grpic_ctx *ctx, int64_t n, double b0, int n_steps,
+                                 int ckpt_every, int n_iter) {
+  grpic_status s = need_fields(ctx);
+  if (s) return s;
+  if (ctx->mixed) return fail(ctx, GRPIC_ESTATE, "the adjoint needs an FP64 context");
+  if (n < 0 || n_steps < 0 || ckpt_every < 1 || n_iter < 1 || n_iter > 1000)
+    return fail(ctx, GRPIC_EINVAL, "bad adjoint sizes");
+  if (!(ctx->field_b0 != 0.0) || !isfinite(b0))
+    return fail(ctx, GRPIC_EINVAL, "field amplitude %g against planes of %g", b0, ctx->field_b0);
+  return GRPIC_OK;
+}
+
+grpic_status grpic_adjoint_forward(grpic_ctx *ctx, int64_t n, double qm, double b0, int n_steps,
+                                   int ckpt_every, int n_iter, const double *state0,
+                                   double *state_out, double *ckpt) {
+  grpic_status s = adjoint_args(ctx, n, b0, n_steps, ckpt_every, n_iter);
+  if (s) return s;
+  if (n > 0 && (!state0 || !state_out || (n_steps > 0 && !ckpt)))
+    return fail(ctx, GRPIC_EINVAL, "null adjoint buffer");
+  CK(launch_adjoint_forward(ctx->g, ctx->F64, n, qm, b0 / ctx->field_b0, n_steps, ckpt_every,
+                            n_iter, state0, state_out, ckpt, ctx->stream));
+  return GRPIC_OK;
+}
+
+grpic_status grpic_adjoint_backward(grpic_ctx *ctx, int64_t n, double qm, double b0, int n_steps,
+                                    int ckpt_every, int n_iter, const double *ckpt,
+                                    const double *grad_out, double *grad_state0,
+                                    double *grad_b0_pp, double *grad_b0, double *scratch) {
+  grpic_status s = adjoint_args(ctx, n, b0, n_steps, ckpt_every, n_iter);
+  if (s) return s;
+  if (!grad_b0 || (n > 0 && (!grad_out || !grad_state0 || !grad_b0_pp ||
+                             (n_steps > 0 && (!ckpt || !scratch)))))
+    return fail(ctx, GRPIC_EINVAL, "null adjoint buffer");
+  // the kernels differentiate with respect to the field scale b0 / field_b0
+  CK(launch_adjoint_backward(ctx->g, ctx->F64, n, qm, b0 / ctx->field_b0, 1.0 / ctx->field_b0,
+                             n_steps, ckpt_every, n_iter, ckpt, grad_out, grad_state0,
+                             grad_b0_pp, grad_b0, scratch, ctx->stream));
   return GRPIC_OK;
 }
 

@@ -35,7 +35,9 @@ struct Cst {
   R a, M, dxi, dth, ig2, dt;
 };
 template <typename R>
-__device__ __forceinline__ Cst<R> cst(const GridP &g);
+__device__ __forceinline__ Cst<R> cst(const GridP &g) {  // other arithmetic types (duals)
+  return {R(g.a), R(g.M), R(g.dxi), R(g.dth), R(g.ig2), R(g.dt)};
+}
 template <>
 __device__ __forceinline__ Cst<double> cst<double>(const GridP &g) {
   return {g.a, g.M, g.dxi, g.dth, g.ig2, g.dt};
@@ -300,6 +302,16 @@ template <typename T>
 cudaError_t launch_zero(T *p, int64_t n, cudaStream_t st);
 
 cudaError_t launch_push_tables(const GridP &g, const PushTables &tb, cudaStream_t st);
+cudaError_t launch_adjoint_forward(const GridP &g, const FieldPtrsT<double> &F, int64_t n,
+                                   double qm, double scale, int n_steps, int every, int n_iter,
+                                   const double *st0, double *out, double *ckpt,
+                                   cudaStream_t st);
+cudaError_t launch_adjoint_backward(const GridP &g, const FieldPtrsT<double> &F, int64_t n,
+                                    double qm, double scale, double gfac, int n_steps, int every,
+                                    int n_iter,
+                                    const double *ckpt, const double *gout, double *gin,
+                                    double *gscale_pp, double *gscale_sum, double *scratch,
+                                    cudaStream_t st);
 template <typename T>
 cudaError_t launch_load(const GridP &g, SpeciesDevT<T> s, int64_t k0, int64_t n,
                         const grpic_particle_init &in, double density_power, cudaStream_t st);

@@ -7,185 +7,11 @@
 // metric, lapse and shift are evaluated in FP64 (and rounded), in a second kernel. Particle state is SoA; consecutive threads read consecutive elements,
 // and field gathers hit L1/L2 because the particles are kept sorted by cell.
 #include "grpic_internal.cuh"
+#include "pusher.cuh"
 
 namespace {
 
 constexpr int TPB = 128;
-
-// precision-generic math
-__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
-__device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
-
-// =================================================================================
-// Metric pieces shared by both precisions (App. A, quasi-spherical Kerr-Schild with
-// r0 = h0 = 0, mass M explicit). All reciprocals of one evaluation come from one division.
-// =================================================================================
-
-// The contravariant metric, shift and 1 + z = 1/alpha^2 from r, sin, cos.
-template <typename R>
-struct Geo {
-  R H11, H13, H22, H33, beta1, opz;
-};
-template <typename R>
-__device__ __forceinline__ void geo_from_rsc(const GridP &g, R r, R s, R c, Geo<R> &o) {
-  const Cst<R> k = cst<R>(g);
-  const R a = k.a, M = k.M, a2 = a * a;
-  const R r2 = r * r, s2 = s * s;
-  const R Sig = fma_(a2, c * c, r2);
-  const R S2 = fma_((R)2 * M, r, Sig);  // Sigma + 2 M r
-  const R A = (r2 + a2) * (r2 + a2) - a2 * (r2 - (R)2 * M * r + a2) * s2;
-  const R f = k.dxi * r;
-  const R u = Sig * S2 * f;
-  const R iQ = (R)1 / (u * s2);         // the one division
-  const R iu = iQ * s2;                 // 1 / (Sigma S2 f)
-  const R iSig = iu * S2 * f, iS2 = iu * Sig * f, fi = iu * Sig * S2;
-  o.opz = S2 * iSig;
-  o.H11 = A * iSig * iS2 * fi * fi;
-  o.H13 = a * iSig * fi;
-  o.H22 = iSig * k.ig2;
-  o.H33 = iQ * u * iSig;                // 1 / (Sigma s^2)
-  o.beta1 = (R)2 * M * r * iS2 * fi;
-}
-
-// The metric at x^n with the derivatives the momentum push needs, and the tetrad
-// coefficients; one division, four reciprocal square roots.
-template <typename R>
-struct Local {
-  R alpha;
-  Geo<R> G;
-  R d1H11, d1H22, d1H33, d1H13, d1alpha, d1beta1;
-  R d2H11, d2H22, d2H33, d2H13, d2alpha, d2beta1;
-  R rH11, sH11, rh22, sh22, rh33, sh33, k13, m13;
-};
-template <typename R>
-__device__ __forceinline__ void local_full(const GridP &g, R r, R s, R c, Local<R> &L) {
-  const Cst<R> k = cst<R>(g);
-  const R a = k.a, M = k.M, a2 = a * a, gg = k.dth, dxi = k.dxi;
-  const R r2 = r * r, s2 = s * s;
-  const R Sig = fma_(a2, c * c, r2);
-  const R S2 = fma_((R)2 * M, r, Sig);
-  const R Del = r2 - (R)2 * M * r + a2;
-  const R A = (r2 + a2) * (r2 + a2) - a2 * Del * s2;
-  const R f = dxi * r;
-  const R u = Sig * S2 * f;
-  const R iQ = (R)1 / (u * s2);
-  const R iu = iQ * s2;
-  const R iSig = iu * S2 * f, iS2 = iu * Sig * f, fi = iu * Sig * S2;
-  const R is2 = iQ * u;
-  Geo<R> &o = L.G;
-  o.opz = S2 * iSig;
-  o.H11 = A * iSig * iS2 * fi * fi;
-  o.H13 = a * iSig * fi;
-  o.H22 = iSig * k.ig2;
-  o.H33 = iSig * is2;
-  o.beta1 = (R)2 * M * r * iS2 * fi;
-  const R al2 = Sig * iS2;
-  L.alpha = rsqrt_(o.opz);
-  const R dxS = (R)2 * r * f, deS = (R)-2 * a2 * s * c * gg;
-  const R dxA = (R)4 * r * f * (r2 + a2) - a2 * s2 * (R)2 * (r - M) * f;
-  const R deA = (R)-2 * a2 * s * c * Del * gg;
-  const R P = Sig * S2;
-  const R iP = iSig * iS2, iP2 = iP * iP, fi2 = fi * fi;
-  const R iSg2 = iSig * iSig;
-  const R al3 = L.alpha * al2;
-  L.d1H11 = (P * dxA - (R)2 * A * (M * r * dxS + Sig * (dxS + M * f))) * iP2 * fi2 -
-            (R)2 * dxi * o.H11;
-  L.d2H11 = (P * deA - (R)2 * A * deS * (M * r + Sig)) * iP2 * fi2;
-  L.d1H22 = -dxS * iSg2 * k.ig2;
-  L.d2H22 = -deS * iSg2 * k.ig2;
-  L.d1H33 = -dxS * iSg2 * is2;
-  L.d2H33 = -(deS + (R)2 * c * s * is2 * Sig * gg) * iSg2 * is2;
-  L.d1H13 = -a * fi * iSig * (iSig * dxS + dxi);
-  L.d2H13 = -a * iSg2 * deS * fi;
-  const R fsr = f * Sig - r * dxS;
-  L.d1alpha = -M * fsr * iSg2 * al3;
-  L.d2alpha = M * r * deS * iSg2 * al3;
-  L.d1beta1 = (R)2 * M * fi * fsr * iS2 * iS2 - dxi * o.beta1;
-  L.d2beta1 = (R)-2 * M * fi * r * deS * iS2 * iS2;
-  const R h22 = gg * gg * Sig, h33 = A * s2 * iSig, h13 = -f * a * o.opz * s2;
-  L.rH11 = rsqrt_(o.H11);
-  L.sH11 = o.H11 * L.rH11;
-  L.rh22 = rsqrt_(h22);
-  L.sh22 = h22 * L.rh22;
-  L.rh33 = rsqrt_(h33);
-  L.sh33 = h33 * L.rh33;
-  L.k13 = h13 * L.rh33;    // h_13 / sqrt(h_33)
-  L.m13 = L.k13 * L.rh33;  // h_13 / h_33
-}
-
-// App. A tetrad maps with the precomputed coefficients
-template <typename R>
-__device__ __forceinline__ void vec_hat(const Local<R> &L, const R A[3], R o[3]) {
-  o[0] = A[0] * L.rH11;
-  o[1] = L.sh22 * A[1];
-  o[2] = fma_(L.k13, A[0], L.sh33 * A[2]);
-}
-template <typename R>
-__device__ __forceinline__ void cov_hat(const Local<R> &L, const R a[3], R o[3]) {
-  o[0] = L.sH11 * fma_(-L.m13, a[2], a[0]);
-  o[1] = a[1] * L.rh22;
-  o[2] = a[2] * L.rh33;
-}
-template <typename R>
-__device__ __forceinline__ void hat_cov(const Local<R> &L, const R h[3], R o[3]) {
-  o[0] = fma_(h[0], L.rH11, L.k13 * h[2]);
-  o[1] = L.sh22 * h[1];
-  o[2] = L.sh33 * h[2];
-}
-
-// Boris step over coordinate time dt/2 in the tetrad frame (Sec. 3.1), hq = qm alpha dt/2.
-template <typename R>
-__device__ __forceinline__ void boris(R u[3], const R D[3], const R B[3], R hq) {
-  const R e = (R)0.5 * hq;
-  const R m0 = fma_(e, D[0], u[0]), m1 = fma_(e, D[1], u[1]), m2 = fma_(e, D[2], u[2]);
-  const R ig = rsqrt_(fma_(m0, m0, fma_(m1, m1, fma_(m2, m2, (R)1))));
-  const R t0 = e * B[0] * ig, t1 = e * B[1] * ig, t2 = e * B[2] * ig;
-  const R sf = (R)2 / fma_(t0, t0, fma_(t1, t1, fma_(t2, t2, (R)1)));
-  const R p0 = m0 + (m1 * t2 - m2 * t1);
-  const R p1 = m1 + (m2 * t0 - m0 * t2);
-  const R p2 = m2 + (m0 * t1 - m1 * t0);
-  u[0] = m0 + sf * (p1 * t2 - p2 * t1) + e * D[0];
-  u[1] = m1 + sf * (p2 * t0 - p0 * t2) + e * D[1];
-  u[2] = m2 + sf * (p0 * t1 - p1 * t0) + e * D[2];
-}
-
-// Eq. (discretized-geodesic-u): implicit midpoint with fixed n_iter, metric at x^n.
-template <typename R>
-__device__ __forceinline__ void geodesic_momentum(const GridP &g, const Local<R> &L, R u[3]) {
-  const R u0 = u[0], u1 = u[1], u3 = u[2];  // u_3 is not changed by this substep
-  const Geo<R> &o = L.G;
-  const R dt = cst<R>(g).dt;
-  const R c0 = fma_(o.H33 * u3, u3, (R)1), c1 = (R)2 * o.H13 * u3;
-  const R e1 = L.d1H33 * u3 * u3, e2 = (R)2 * L.d1H13 * u3;
-  const R f1 = L.d2H33 * u3 * u3, f2 = (R)2 * L.d2H13 * u3;
-  const R D1a = dt * L.d1alpha, D1b = dt * L.d1beta1;
-  const R D2a = dt * L.d2alpha, D2b = dt * L.d2beta1;
-  const R hdt = (R)0.5 * dt * L.alpha;
-  const R hu0 = (R)0.5 * u0, hu1 = (R)0.5 * u1;
-  R t0 = u0, t1 = u1;
-  for (int it = 0; it < g.n_iter; ++it) {
-    const R b0 = fma_((R)0.5, t0, hu0), b1 = fma_((R)0.5, t1, hu1);
-    const R b1s = b1 * b1;
-    const R q = fma_(b0, fma_(o.H11, b0, c1), fma_(o.H22, b1s, c0));  // gamma_bar^2
-    const R ig = rsqrt_(q);
-    const R gb = q * ig;                                              // gamma_bar
-    const R ha = hdt * ig;                                            // dt / (2 u^0)
-    const R k1 = fma_(b0, fma_(L.d1H11, b0, e2), fma_(L.d1H22, b1s, e1));
-    const R k2 = fma_(b0, fma_(L.d2H11, b0, f2), fma_(L.d2H22, b1s, f1));
-    const R n0 = fma_(b0, D1b, fma_(-gb, D1a, fma_(-ha, k1, u0)));
-    const R n1 = fma_(b0, D2b, fma_(-gb, D2a, fma_(-ha, k2, u1)));
-    // once the iterate repeats exactly, every later iteration repeats it too (same inputs,
-    // deterministic arithmetic): stopping here returns bit for bit the n_iter result
-    const bool fixed = (n0 == t0) && (n1 == t1);
-    t0 = n0;
-    t1 = n1;
-    if (fixed && g.stop_on_repeat) break;
-  }
-  u[0] = t0;
-  u[1] = t1;
-}
 
 __device__ __forceinline__ void count(unsigned long long *diag, int which) {
   atomicAdd(diag + which, 1ull);

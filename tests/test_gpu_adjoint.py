@@ -1,0 +1,163 @@
+"""The adjoint of the pusher over frozen fields (grpic_adjoint_forward / _backward and the
+torch.autograd.Function over them) against the oracle's frozen push and its exact FP64
+Jacobian (complex step), against central finite differences of the GPU forward, and for
+independence of the checkpoint interval."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+N_ITER = 64   # both implicit substeps iterated to an exact repeat (at most this often)
+N_STEPS = 100
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def setup(torch_cuda):
+    from paper_2511_17701_gb300 import FIELD_USER, Sim
+    torch = torch_cuda
+    cfg = W.grid_config("wald64", r_absorb=1e300)
+    osim = O.OracleSim(cfg)
+    osim.init_fields(O.FIELD_WALD, 1.0)
+    tp = W.probe_particles(cfg, 64, 3, (15.0, 50.0), (12.0, 52.0), 0.5)
+    qm, qc = W.species_coefficients(1.0)
+    sp = osim.add_species(tp["pos"], tp["uhat"], tp["w0"], qm, qc)
+    v = sp.view()
+    st0 = np.stack([v["i1"] + v["dx1"], v["i2"] + v["dx2"], v["phi"], v["u1"], v["u2"], v["u3"]])
+    g = Sim(dict(cfg, dt=osim.dt), [1])
+    g.init_metric()
+    g.init_fields(FIELD_USER)  # the oracle's planes, amplitude 1
+    g.set_planes(osim.F)
+    st0_t = torch.tensor(st0, dtype=torch.float64, device="cuda")
+    return osim, g, st0, st0_t, qm
+
+
+def test_adjoint_forward_matches_oracle(setup):
+    osim, g, st0, st0_t, qm = setup
+    out, ckpt = g.adjoint_forward(st0_t, qm, 1.0, N_STEPS, 10, N_ITER)
+    ref = O.frozen_push(osim, st0, 1.0, qm, N_STEPS, 60)
+    out = out.cpu().numpy()
+    assert np.array_equal(np.isnan(out[0]), np.isnan(ref[0]))
+    ok = ~np.isnan(ref[0])
+    assert ok.sum() >= 48
+    scale = np.maximum(1.0, np.abs(ref[:, ok]))
+    assert np.max(np.abs(out[:, ok] - ref[:, ok]) / scale) < 1e-10
+    assert ckpt.shape == (10, 6, st0.shape[1])
+    assert np.array_equal(ckpt[0].cpu().numpy(), st0)
+
+
+def vjp_gpu(g, st0_t, qm, b0, v, every):
+    torch = g.torch
+    out, ckpt = g.adjoint_forward(st0_t, qm, b0, N_STEPS, every, N_ITER)
+    gin, gpp, gsum = g.adjoint_backward(ckpt, torch.tensor(v, device="cuda"), qm, b0, N_STEPS,
+                                        every, N_ITER)
+    return out.cpu().numpy(), gin.cpu().numpy(), gpp.cpu().numpy(), float(gsum.cpu()[0])
+
+
+def test_adjoint_gradient_matches_oracle_jacobian(setup):
+    """J^T v from the reverse sweep against the oracle's complex-step Jacobian."""
+    osim, g, st0, st0_t, qm = setup
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(st0.shape)
+    fin, J = O.frozen_jacobian(osim, st0, 1.0, qm, N_STEPS, 60)
+    ok = ~np.isnan(fin[0])
+    v[:, ~ok] = 0.0
+    out, gin, gpp, gsum = vjp_gpu(g, st0_t, qm, 1.0, v, 10)
+    ref_in = np.einsum("kqi,qk->ik", J[:, :, :6], v)
+    ref_b0 = np.einsum("kq,qk->k", J[:, :, 6], v)
+    for k in np.flatnonzero(ok):
+        sc = np.abs(ref_in[:, k]).max()
+        assert np.max(np.abs(gin[:, k] - ref_in[:, k])) / sc < 1e-8, k
+        assert abs(gpp[k] - ref_b0[k]) / (abs(ref_b0[k]) + sc) < 1e-8, k
+    assert abs(gsum - ref_b0[ok].sum()) / np.abs(ref_b0[ok]).sum() < 1e-8
+    assert np.all(gin[:, ~ok] == 0.0) and np.all(gpp[~ok] == 0.0)
+
+
+def test_adjoint_matches_central_differences(setup):
+    """Gradient of L = sum(v * final state) against central differences of the GPU forward
+    (every particle is independent, so one perturbed run per input gives all particles)."""
+    osim, g, st0, st0_t, qm = setup
+    torch = g.torch
+    rng = np.random.default_rng(12)
+    v = rng.standard_normal(st0.shape)
+    out, gin, gpp, _ = vjp_gpu(g, st0_t, qm, 1.0, v, 25)
+    ok = ~np.isnan(out[0])
+    h = 1e-6
+
+    def loss(st, b0):
+        o, _ = g.adjoint_forward(torch.tensor(st, device="cuda"), qm, b0, N_STEPS, 25, N_ITER)
+        return (o.cpu().numpy() * v).sum(axis=0)
+
+    fd = np.zeros((7, st0.shape[1]))
+    for q in range(6):
+        sp, sm = st0.copy(), st0.copy()
+        sp[q] += h
+        sm[q] -= h
+        fd[q] = (loss(sp, 1.0) - loss(sm, 1.0)) / (2 * h)
+    fd[6] = (loss(st0, 1.0 + h) - loss(st0, 1.0 - h)) / (2 * h)
+    ad = np.vstack([gin, gpp[None]])
+    ok &= ~np.isnan(fd).any(axis=0)
+    assert ok.sum() >= 48
+    sc = np.abs(ad[:, ok]).max(axis=0)
+    err = np.abs(fd[:, ok] - ad[:, ok]) / sc
+    assert err.max() < 1e-6, err.max()
+
+
+def test_checkpoint_interval_does_not_change_gradients(setup):
+    """Segments are recomputed with the forward's own arithmetic, so the gradients are the
+    same bits for every checkpoint interval."""
+    osim, g, st0, st0_t, qm = setup
+    v = np.random.default_rng(13).standard_normal(st0.shape)
+    res = [vjp_gpu(g, st0_t, qm, 1.0, v, every) for every in (1, 7, 30, N_STEPS)]
+    for r in res[1:]:
+        for a, b in zip(r[:3], res[0][:3]):
+            assert np.array_equal(a, b, equal_nan=True)
+
+
+def test_push_adjoint_autograd(setup):
+    from paper_2511_17701_gb300 import push_adjoint
+    osim, g, st0, st0_t, qm = setup
+    torch = g.torch
+    v = np.random.default_rng(14).standard_normal(st0.shape)
+    x0 = st0_t.clone().requires_grad_(True)
+    b0 = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    out = push_adjoint(g, x0, b0, qm, N_STEPS, ckpt_every=20, n_iter=N_ITER)
+    ok = ~torch.isnan(out[0])
+    vt = torch.tensor(v, device="cuda") * ok
+    loss = (torch.nan_to_num(out) * vt).sum()
+    loss.backward()
+    _, gin, _, gsum = vjp_gpu(g, st0_t, qm, 1.0, vt.cpu().numpy(), 20)
+    assert np.array_equal(x0.grad.cpu().numpy(), gin)
+    assert float(b0.grad) == gsum
+
+
+def test_boundary_particles(setup):
+    """A particle started just outside the horizon moving inward leaves through the horizon
+    layer: NaN state, zero gradient when its cotangent is zero, NaN otherwise."""
+    osim, g, st0, st0_t, qm = setup
+    torch = g.torch
+    st = st0[:, :2].copy()
+    st[0, 0], st[3, 0] = 0.3, -5.0   # x1 near the inner edge, strongly infalling u_1
+    out, ckpt = g.adjoint_forward(torch.tensor(st, device="cuda"), qm, 1.0, N_STEPS, 10, N_ITER)
+    out = out.cpu().numpy()
+    assert np.isnan(out[:, 0]).all() and not np.isnan(out[:, 1]).any()
+    for val, expect_nan in ((0.0, False), (1.0, True)):
+        v = np.ones_like(st)
+        v[:, 0] = val
+        gin, gpp, _ = g.adjoint_backward(ckpt, torch.tensor(v, device="cuda"), qm, 1.0, N_STEPS,
+                                         10, N_ITER)
+        gin = gin.cpu().numpy()
+        assert np.isnan(gin[:, 0]).all() == expect_nan
+        if not expect_nan:
+            assert np.all(gin[:, 0] == 0.0)
+        assert np.isfinite(gin[:, 1]).all()
