@@ -413,6 +413,92 @@ def run_gpu(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, ws, rank, local):
+    """The adjoint of the pusher over a frozen field: test particles in the 512^2 Kerr
+    (a = 0.9) Wald field, forward n steps with checkpoints, then the reverse sweep for the
+    gradient of L = sum(v . final state) with respect to the initial state and B0, both timed
+    with CUDA events; central differences of the forward on a sample of particles."""
+    import torch
+
+    from paper_2511_17701_gb300 import FIELD_WALD, Sim
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    cfg = W.grid_config("wald512", r_absorb=1e300)
+    n, steps, every = args.adjoint_particles, args.adjoint_steps, args.adjoint_ckpt
+    tp = W.probe_particles(cfg, n, 77 + rank, (0.2 * cfg["n_r"], 0.8 * cfg["n_r"]),
+                           (0.15 * cfg["n_theta"], 0.85 * cfg["n_theta"]), 0.5)
+    qm, qc = W.species_coefficients(1.0)
+    sim = Sim(cfg, [n], device=device)
+    sim.init_metric()
+    sim.init_fields(FIELD_WALD, cfg["B0"])
+    sim.load_particles(0, tp["pos"], tp["uhat"], tp["w0"], qm, qc)  # u_i = e_i^j u_j^ on the GPU
+    v = sim.species_views(0)
+    st0 = torch.stack([v["i1"].double() + v["dx1"], v["i2"].double() + v["dx2"], v["phi"],
+                       v["u1"], v["u2"], v["u3"]]).contiguous()
+    gen = torch.Generator(device=device).manual_seed(5)
+    cot = torch.randn((6, n), dtype=torch.float64, device=device, generator=gen)
+    n_iter = 64
+    b0 = cfg["B0"]
+    stream = sim.stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    sim.adjoint_forward(st0[:, :1024].contiguous(), qm, b0, 4, 2, n_iter)  # warm-up
+    torch.cuda.synchronize(device)
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        out, ckpt = sim.adjoint_forward(st0, qm, b0, steps, every, n_iter)
+        ev[1].record(stream)
+        ok = ~torch.isnan(out[0])
+        gout = cot * ok
+        gin, gpp, gsum = sim.adjoint_backward(ckpt, gout, qm, b0, steps, every, n_iter)
+        ev[2].record(stream)
+        torch.cuda.synchronize(device)
+    fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    n_ok = int(ok.sum())
+    # central differences of the forward on a sample of particles that stayed inside
+    idx = torch.nonzero(ok).flatten()[: args.adjoint_fd_sample]
+    sub = st0[:, idx].contiguous()
+    csub = gout[:, idx]
+    h = 1e-6
+
+    def loss(st, b):
+        o, _ = sim.adjoint_forward(st, qm, b, steps, every, n_iter)
+        return (o * csub).sum(dim=0)
+
+    fd = torch.zeros((7, idx.numel()), dtype=torch.float64, device=device)
+    for q in range(6):
+        sp_, sm_ = sub.clone(), sub.clone()
+        sp_[q] += h
+        sm_[q] -= h
+        fd[q] = (loss(sp_, b0) - loss(sm_, b0)) / (2 * h)
+    fd[6] = (loss(sub, b0 + h) - loss(sub, b0 - h)) / (2 * h)
+    ad = torch.cat([gin[:, idx], gpp[idx][None]])
+    good = ~torch.isnan(fd).any(dim=0)
+    err = ((fd - ad).abs().amax(dim=0) / ad.abs().amax(dim=0))[good].cpu().numpy()
+    psteps = n_ok * steps
+    line = {"metric": "adjoint push: particle-steps/s (frozen field, forward + reverse sweep)",
+            "value": psteps / ((fwd_ms + bwd_ms) * 1e-3), "unit": "particle-steps/s",
+            "n_gpus": ws, "steps": steps, "warmup": 1, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic (seeded test particles)",
+            "config": {"workload": "adjoint: %d test particles (x1 in [0.2, 0.8] n_r, x2 in "
+                                   "[0.15, 0.85] n_theta, |u^| uniform in [0, 0.5]) in the frozen "
+                                   "Wald field, Kerr a=0.9, B0 as parameter, 512x512 log-r grid "
+                                   "r in [0.95 r_h, 50]; %d FP64 steps, checkpoints every %d"
+                                   % (n, steps, every)},
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "forward_particle_steps_per_s": n * steps / (fwd_ms * 1e-3),
+            "particles_kept": n_ok,
+            "dL_dB0": float(gsum.cpu()[0]),
+            "fd_check": {"sample": int(good.sum()), "step": h,
+                         "median_rel_err": float(np.median(err)) if err.size else None,
+                         "p90_rel_err": float(np.quantile(err, 0.9)) if err.size else None,
+                         "max_rel_err": float(err.max()) if err.size else None,
+                         "frac_within_1e-6": float((err < 1e-6).mean()) if err.size else None},
+            "gpu_launches": None, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,12 +517,20 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--ref-frac", type=float, default=0.25,
                     help="fraction of the cells whose particles the reference arm pushes")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the adjoint of the pusher over a frozen field instead")
+    ap.add_argument("--adjoint-particles", type=int, default=1 << 20)
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--adjoint-ckpt", type=int, default=100)
+    ap.add_argument("--adjoint-fd-sample", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.adjoint:
+        run_adjoint(args, ws, rank, local)
     else:
         run_gpu(args, ws, rank, local)
     if ws > 1:

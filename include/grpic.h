@@ -300,8 +300,9 @@ GRPIC_API grpic_status grpic_adjoint_forward(grpic_ctx *ctx, int64_t n, double q
  * ckpt written by grpic_adjoint_forward): given grad_out = dL/d(final state) ([6][n]),
  * writes grad_state0 = dL/d(initial state) ([6][n]), grad_b0_pp[k] = particle k's part of
  * dL/db0 ([n]) and grad_b0[0] = their sum (deterministic order). Each checkpoint segment is
- * recomputed into scratch (ckpt_every x 6 x n doubles); the step Jacobians use the
- * implicit-function theorem at the implicit substeps. Particles reported NaN by the forward
+ * recomputed and the Jacobians of its steps are kept in scratch (min(ckpt_every, n_steps) x
+ * 36 x n doubles); they use the implicit-function theorem at the implicit substeps, so the
+ * result does not depend on ckpt_every (to the bit). Particles reported NaN by the forward
  * get zero gradients where their grad_out is zero, NaN otherwise. Errors: as the forward. */
 GRPIC_API grpic_status grpic_adjoint_backward(grpic_ctx *ctx, int64_t n, double qm, double b0,
                                               int n_steps, int ckpt_every, int n_iter,

@@ -33,6 +33,9 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_adjoint_forward", "grpic_adjoint_backward"]
 
 
+ADJOINT_SCRATCH_PER_STEP = 36  # doubles per particle and step of grpic_adjoint_backward
+
+
 class GrpicError(RuntimeError):
     pass
 
@@ -339,8 +342,8 @@ class Sim:
         gin = torch.empty_like(grad_out)
         gpp = torch.empty(max(n, 1), dtype=torch.float64, device=self.device)
         gsum = torch.empty(1, dtype=torch.float64, device=self.device)
-        scratch = torch.empty((min(ckpt_every, max(n_steps, 1)), 6, n), dtype=torch.float64,
-                              device=self.device) if n_steps > 0 else None
+        scratch = torch.empty((min(ckpt_every, max(n_steps, 1)), ADJOINT_SCRATCH_PER_STEP, n),
+                              dtype=torch.float64, device=self.device) if n_steps > 0 else None
         self._check(self.L.grpic_adjoint_backward(
             self.ctx, n, qm, b0, n_steps, ckpt_every, n_iter,
             ckpt.data_ptr() if ckpt.numel() else None, grad_out.data_ptr(), gin.data_ptr(),

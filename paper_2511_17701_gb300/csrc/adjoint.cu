@@ -9,9 +9,12 @@
 // first, the segment's states are recomputed into scratch memory, then the steps are
 // traversed backwards with lambda <- J^T lambda, where J is the 6 x 7 Jacobian of one step
 // (inputs: the state and the scale). J comes from forward-mode dual numbers through the same
-// templates the pusher uses (pusher.cuh), in three passes of two seeded directions; at the two
-// implicit substeps the implicit-function theorem replaces differentiation through the
-// iterations: at the fixed point t* = G(t*, p), dt* = (I - dG/dt)^{-1} (dG/dp) dp.
+// templates the pusher uses (pusher.cuh): one pass seeding x1, x2 (the metric differentiated
+// too) and one seeding u_1, u_2, u_3 and the scale (metric values only; it depends on x
+// alone). At the two implicit substeps the implicit-function theorem replaces
+// differentiation through the iterations: at the fixed point t* = G(t*, p),
+// dt* = (I - dG/dt)^{-1} (dG/dp) dp. The Jacobians of a segment are formed while its states
+// are recomputed and kept in scratch memory for the reverse sweep.
 #include "dual.cuh"
 #include "grpic_internal.cuh"
 #include "pusher.cuh"
@@ -20,6 +23,7 @@ namespace {
 
 constexpr int TPB_ADJ = 64;
 using D2 = Dual<2>;
+using D4 = Dual<4>;
 
 // r, sin(theta), cos(theta) at absolute code coordinates; theta clamped to
 // [small_angle, pi - small_angle] for the metric (Sec. 3.3.2), with zero derivative there.
@@ -53,61 +57,67 @@ __device__ __forceinline__ R interp_abs(const double *__restrict__ pl, int NX, c
          w1 * w2 * p11;
 }
 
-// metric with derivatives, tetrad-frame fields and the Boris coefficient at x^n
+// metric with derivatives, tetrad-frame fields (at unit amplitude and at `scale`) and the
+// Boris coefficient at x^n
 template <typename R>
 struct Frame {
   Local<R> L;
+  R Bh1[3], Dh1[3];  // unit amplitude
   R Bh[3], Dh[3], hq;
 };
 template <typename R>
 __device__ __forceinline__ void frame_at(const GridP &g, const FieldPtrsT<double> &F,
                                          const R x[2], const R &scale, double qm, Frame<R> &fr) {
   R Bv[3], Dv[3];
-  Bv[0] = scale * interp_abs(F.B[0], g.NX, x[0], x[1], 0.0, 0.5);
-  Bv[1] = scale * interp_abs(F.B[1], g.NX, x[0], x[1], 0.5, 0.0);
-  Bv[2] = scale * interp_abs(F.B[2], g.NX, x[0], x[1], 0.5, 0.5);
-  Dv[0] = scale * interp_abs(F.D[0], g.NX, x[0], x[1], 0.5, 0.0);
-  Dv[1] = scale * interp_abs(F.D[1], g.NX, x[0], x[1], 0.0, 0.5);
-  Dv[2] = scale * interp_abs(F.D[2], g.NX, x[0], x[1], 0.0, 0.0);
+  Bv[0] = interp_abs(F.B[0], g.NX, x[0], x[1], 0.0, 0.5);
+  Bv[1] = interp_abs(F.B[1], g.NX, x[0], x[1], 0.5, 0.0);
+  Bv[2] = interp_abs(F.B[2], g.NX, x[0], x[1], 0.5, 0.5);
+  Dv[0] = interp_abs(F.D[0], g.NX, x[0], x[1], 0.5, 0.0);
+  Dv[1] = interp_abs(F.D[1], g.NX, x[0], x[1], 0.0, 0.5);
+  Dv[2] = interp_abs(F.D[2], g.NX, x[0], x[1], 0.0, 0.0);
   R r, s, c;
   rsc_abs(g, x[0], x[1], r, s, c);
   local_full(g, r, s, c, fr.L);
-  vec_hat(fr.L, Bv, fr.Bh);
-  vec_hat(fr.L, Dv, fr.Dh);
+  vec_hat(fr.L, Bv, fr.Bh1);
+  vec_hat(fr.L, Dv, fr.Dh1);
+  for (int i = 0; i < 3; ++i) {
+    fr.Bh[i] = scale * fr.Bh1[i];
+    fr.Dh[i] = scale * fr.Dh1[i];
+  }
   fr.hq = qm * fr.L.alpha * 0.5 * g.dt;
 }
 
 // one EM half step: to the tetrad frame, Boris over dt/2, back (steps 3-5 and 7-9)
-template <typename R>
-__device__ __forceinline__ void em_half(const Frame<R> &fr, const R uin[3], R uout[3]) {
+template <typename M, typename R>
+__device__ __forceinline__ void em_half(const Local<M> &L, const R Dh[3], const R Bh[3],
+                                        const R &hq, const R uin[3], R uout[3]) {
   R uh[3];
-  cov_hat(fr.L, uin, uh);
-  boris(uh, fr.Dh, fr.Bh, fr.hq);
-  hat_cov(fr.L, uh, uout);
+  cov_hat(L, uin, uh);
+  boris(uh, Dh, Bh, hq);
+  hat_cov(L, uh, uout);
 }
 
-// coordinate velocity dx^i/dt of Eq. (discretized-geodesic-x) at a point
-template <typename R>
-__device__ __forceinline__ void coord_velocity(const GridP &g, const R &xb1, const R &xb2,
-                                               const R u[3], R &v1, R &v2) {
-  R r, s, c;
-  rsc_abs(g, xb1, xb2, r, s, c);
-  Geo<R> o;
-  geo_from_rsc(g, r, s, c, o);
+// coordinate velocity dx^i/dt of Eq. (discretized-geodesic-x) from the metric at the point
+template <typename M, typename R>
+__device__ __forceinline__ void velocity(const Geo<M> &o, const R u[3], R &v1, R &v2) {
   const R q = fma_(o.H11 * u[0], u[0], fma_(o.H22 * u[1], u[1],
               fma_(o.H33 * u[2], u[2], fma_(o.H13, (R)2 * u[0] * u[2], (R)1))));
   const R ag = rsqrt_(o.opz * q);  // alpha / gamma
-  v1 = fma_(ag, fma_(o.H11, u[0], o.H13 * u[2]), -o.beta1);
+  v1 = fma_(ag, fma_(o.H11, u[0], o.H13 * u[2]), R(-o.beta1));
   v2 = ag * o.H22 * u[1];
+}
+template <typename R>
+__device__ __forceinline__ void geo_abs(const GridP &g, const R &x1, const R &x2, Geo<R> &o) {
+  R r, s, c;
+  rsc_abs(g, x1, x2, r, s, c);
+  geo_from_rsc(g, r, s, c, o);
 }
 
 // dphi/dt of Eq. (discretized-geodesic-x-phi) at a point
 template <typename R>
 __device__ __forceinline__ R phi_rate(const GridP &g, const R &x1, const R &x2, const R u[3]) {
-  R r, s, c;
-  rsc_abs(g, x1, x2, r, s, c);
   Geo<R> o;
-  geo_from_rsc(g, r, s, c, o);
+  geo_abs(g, x1, x2, o);
   const R q = fma_(o.H11 * u[0], u[0], fma_(o.H22 * u[1], u[1],
               fma_(o.H33 * u[2], u[2], fma_(o.H13, (R)2 * u[0] * u[2], (R)1))));
   return rsqrt_(o.opz * q) * fma_(o.H13, u[0], o.H33 * u[2]);
@@ -125,11 +135,10 @@ struct StepVals {
 
 __device__ __forceinline__ void step_values(const GridP &g, const FieldPtrsT<double> &F,
                                             const double st[6], double scale, double qm,
-                                            int n_iter, StepVals &sv) {
+                                            int n_iter, StepVals &sv, Frame<double> &fr) {
   const double x[2] = {st[0], st[1]}, u[3] = {st[3], st[4], st[5]};
-  Frame<double> fr;
   frame_at(g, F, x, scale, qm, fr);
-  em_half(fr, u, sv.u1);
+  em_half(fr.L, fr.Dh, fr.Bh, fr.hq, u, sv.u1);
   const GeoMap<double> gm(g, fr.L, sv.u1);
   double t0 = sv.u1[0], t1 = sv.u1[1];
   for (int it = 0; it < n_iter; ++it) {
@@ -143,11 +152,13 @@ __device__ __forceinline__ void step_values(const GridP &g, const FieldPtrsT<dou
   sv.t[0] = t0;
   sv.t[1] = t1;
   const double u2[3] = {t0, t1, sv.u1[2]};
-  em_half(fr, u2, sv.un);
+  em_half(fr.L, fr.Dh, fr.Bh, fr.hq, u2, sv.un);
   double a0 = x[0], a1 = x[1];  // the first iterate is x^n
   for (int it = 0; it < n_iter; ++it) {
+    Geo<double> o;
+    geo_abs(g, 0.5 * (x[0] + a0), 0.5 * (x[1] + a1), o);
     double v1, v2;
-    coord_velocity(g, 0.5 * (x[0] + a0), 0.5 * (x[1] + a1), sv.un, v1, v2);
+    velocity(o, sv.un, v1, v2);
     const double n0 = fma(g.dt, v1, x[0]), n1 = fma(g.dt, v2, x[1]);
     const bool fixed = n0 == a0 && n1 == a1;
     a0 = n0;
@@ -178,16 +189,16 @@ __device__ __forceinline__ void inv_i_minus(const double A[2][2], double M[2][2]
   M[1][1] = a * id;
 }
 
-// The step's Jacobian J[6 outputs][7 inputs] (inputs x1, x2, phi, u1, u2, u3, scale) at st.
+// The step's Jacobian at st: J[r][c] = d(output r)/d(input c), outputs x1, x2, phi, u1, u2,
+// u3 after the step, inputs x1, x2, u1, u2, u3, scale (the phi column is the unit vector).
+constexpr int JC = 6;  // stored input columns
 __device__ void step_jacobian(const GridP &g, const FieldPtrsT<double> &F, const double st[6],
-                              double scale, double qm, const StepVals &sv, double J[6][7]) {
-  // dG/dt of the geodesic map at its fixed point, and d(velocity)/d(x_bar) at the final
-  // coordinate midpoint: the matrices of the implicit-function theorem
+                              double scale, double qm, const StepVals &sv,
+                              const Frame<double> &fr, double J[6][JC]) {
+  // the implicit-function theorem's matrices: (I - dG/dt)^{-1} of the geodesic map at its fixed
+  // point and (I - dt/2 dV/dx_bar)^{-1} at the final coordinate midpoint
   double Mt[2][2], Mx[2][2];
   {
-    const double x[2] = {st[0], st[1]};
-    Frame<double> fr;
-    frame_at(g, F, x, scale, qm, fr);
     const GeoMap<double> gv(g, fr.L, sv.u1);
     GeoMap<D2> gd;
 #define WIDEN(m) gd.m = D2(gv.m);
@@ -204,28 +215,28 @@ __device__ void step_jacobian(const GridP &g, const FieldPtrsT<double> &F, const
     D2 xb1(0.5 * (st[0] + sv.xn[0])), xb2(0.5 * (st[1] + sv.xn[1]));
     xb1.d[0] = 1.0;
     xb2.d[1] = 1.0;
+    Geo<D2> ob;
+    geo_abs(g, xb1, xb2, ob);
     const D2 un[3] = {D2(sv.un[0]), D2(sv.un[1]), D2(sv.un[2])};
     D2 v1, v2;
-    coord_velocity(g, xb1, xb2, un, v1, v2);
+    velocity(ob, un, v1, v2);
     const double h = 0.5 * g.dt;
     const double B[2][2] = {{h * v1.d[0], h * v1.d[1]}, {h * v2.d[0], h * v2.d[1]}};
     inv_i_minus(B, Mx);
   }
-  // three passes of two seeded input directions: (x1, x2), (u1, u2), (u3, scale)
-  for (int pass = 0; pass < 3; ++pass) {
-    D2 X[2] = {D2(st[0]), D2(st[1])}, U[3] = {D2(st[3]), D2(st[4]), D2(st[5])}, S(scale);
-    int col[2];
-    if (pass == 0) { X[0].d[0] = 1.0; X[1].d[1] = 1.0; col[0] = 0; col[1] = 1; }
-    else if (pass == 1) { U[0].d[0] = 1.0; U[1].d[1] = 1.0; col[0] = 3; col[1] = 4; }
-    else { U[2].d[0] = 1.0; S.d[1] = 1.0; col[0] = 5; col[1] = 6; }
-    Frame<D2> fr;
-    frame_at(g, F, X, S, qm, fr);
-    D2 U1[3];
-    em_half(fr, U, U1);
-    const GeoMap<D2> gm(g, fr.L, U1);
+  // pass A: x1, x2 seeded; the metric, fields and tetrads differentiated
+  {
+    D2 X[2] = {D2(st[0]), D2(st[1])};
+    X[0].d[0] = 1.0;
+    X[1].d[1] = 1.0;
+    const D2 U[3] = {D2(st[3]), D2(st[4]), D2(st[5])};
+    Frame<D2> fd;
+    frame_at(g, F, X, D2(scale), qm, fd);
+    D2 U1[3], U2[3], U3[3];
+    em_half(fd.L, fd.Dh, fd.Bh, fd.hq, U, U1);
+    const GeoMap<D2> gm(g, fd.L, U1);
     D2 n0, n1;
     gm.apply(D2(sv.t[0]), D2(sv.t[1]), n0, n1);
-    D2 U2[3];
     U2[0] = D2(sv.t[0]);
     U2[1] = D2(sv.t[1]);
     U2[2] = U1[2];
@@ -233,10 +244,11 @@ __device__ void step_jacobian(const GridP &g, const FieldPtrsT<double> &F, const
       U2[0].d[k] = Mt[0][0] * n0.d[k] + Mt[0][1] * n1.d[k];
       U2[1].d[k] = Mt[1][0] * n0.d[k] + Mt[1][1] * n1.d[k];
     }
-    D2 U3[3];
-    em_half(fr, U2, U3);
+    em_half(fd.L, fd.Dh, fd.Bh, fd.hq, U2, U3);
+    Geo<D2> ob;
+    geo_abs(g, 0.5 * (X[0] + sv.xn[0]), 0.5 * (X[1] + sv.xn[1]), ob);
     D2 v1, v2;
-    coord_velocity(g, 0.5 * (X[0] + sv.xn[0]), 0.5 * (X[1] + sv.xn[1]), U3, v1, v2);
+    velocity(ob, U3, v1, v2);
     D2 XN[2] = {D2(sv.xn[0]), D2(sv.xn[1])};
     for (int k = 0; k < 2; ++k) {
       const double r0 = X[0].d[k] + g.dt * v1.d[k], r1 = X[1].d[k] + g.dt * v2.d[k];
@@ -245,17 +257,60 @@ __device__ void step_jacobian(const GridP &g, const FieldPtrsT<double> &F, const
     }
     const D2 v3 = phi_rate(g, 0.5 * (X[0] + XN[0]), 0.5 * (X[1] + XN[1]), U3);
     for (int k = 0; k < 2; ++k) {
-      const int c = col[k];
-      J[0][c] = XN[0].d[k];
-      J[1][c] = XN[1].d[k];
-      J[2][c] = g.dt * v3.d[k];
-      J[3][c] = U3[0].d[k];
-      J[4][c] = U3[1].d[k];
-      J[5][c] = U3[2].d[k];
+      J[0][k] = XN[0].d[k];
+      J[1][k] = XN[1].d[k];
+      J[2][k] = g.dt * v3.d[k];
+      J[3][k] = U3[0].d[k];
+      J[4][k] = U3[1].d[k];
+      J[5][k] = U3[2].d[k];
     }
   }
-  // phi does not feed back
-  for (int q = 0; q < 6; ++q) J[q][2] = q == 2 ? 1.0 : 0.0;
+  // pass B: u_1, u_2, u_3 and the scale seeded; the metric at x^n and at the final
+  // coordinate midpoint is fixed (values), the fields are linear in the scale
+  {
+    D4 U[3] = {D4(st[3]), D4(st[4]), D4(st[5])};
+    for (int i = 0; i < 3; ++i) U[i].d[i] = 1.0;
+    D4 Bh[3], Dh[3];
+    for (int i = 0; i < 3; ++i) {
+      Bh[i] = D4(fr.Bh[i]);
+      Bh[i].d[3] = fr.Bh1[i];
+      Dh[i] = D4(fr.Dh[i]);
+      Dh[i].d[3] = fr.Dh1[i];
+    }
+    const D4 hq(fr.hq);
+    D4 U1[3], U2[3], U3[3];
+    em_half(fr.L, Dh, Bh, hq, U, U1);
+    const GeoMap<D4> gm(g, fr.L, U1);
+    D4 n0, n1;
+    gm.apply(D4(sv.t[0]), D4(sv.t[1]), n0, n1);
+    U2[0] = D4(sv.t[0]);
+    U2[1] = D4(sv.t[1]);
+    U2[2] = U1[2];
+    for (int k = 0; k < 4; ++k) {
+      U2[0].d[k] = Mt[0][0] * n0.d[k] + Mt[0][1] * n1.d[k];
+      U2[1].d[k] = Mt[1][0] * n0.d[k] + Mt[1][1] * n1.d[k];
+    }
+    em_half(fr.L, Dh, Bh, hq, U2, U3);
+    Geo<double> ob;
+    geo_abs(g, 0.5 * (st[0] + sv.xn[0]), 0.5 * (st[1] + sv.xn[1]), ob);
+    D4 v1, v2;
+    velocity(ob, U3, v1, v2);
+    D4 XN[2] = {D4(sv.xn[0]), D4(sv.xn[1])};
+    for (int k = 0; k < 4; ++k) {
+      const double r0 = g.dt * v1.d[k], r1 = g.dt * v2.d[k];
+      XN[0].d[k] = Mx[0][0] * r0 + Mx[0][1] * r1;
+      XN[1].d[k] = Mx[1][0] * r0 + Mx[1][1] * r1;
+    }
+    const D4 v3 = phi_rate(g, 0.5 * (st[0] + XN[0]), 0.5 * (st[1] + XN[1]), U3);
+    for (int k = 0; k < 4; ++k) {
+      J[0][2 + k] = XN[0].d[k];
+      J[1][2 + k] = XN[1].d[k];
+      J[2][2 + k] = g.dt * v3.d[k];
+      J[3][2 + k] = U3[0].d[k];
+      J[4][2 + k] = U3[1].d[k];
+      J[5][2 + k] = U3[2].d[k];
+    }
+  }
 }
 
 __global__ void __launch_bounds__(TPB_ADJ) k_adj_forward(GridP g, FieldPtrsT<double> F, int64_t n,
@@ -276,7 +331,8 @@ __global__ void __launch_bounds__(TPB_ADJ) k_adj_forward(GridP g, FieldPtrsT<dou
       }
       if (bad) continue;
       StepVals sv;
-      step_values(g, F, st, scale, qm, n_iter, sv);
+      Frame<double> fr;
+      step_values(g, F, st, scale, qm, n_iter, sv, fr);
       if (!sv.ok) {
         bad = true;
         continue;
@@ -312,40 +368,36 @@ __global__ void __launch_bounds__(TPB_ADJ) k_adj_backward(
         bad = true;
         break;
       }
-      // recompute the segment's states (the checkpoint is the first)
+      // recompute the segment from its checkpoint, keeping each step's Jacobian
       for (int j = 0; j < len; ++j) {
-        for (int q = 0; q < 6; ++q) scratch[((int64_t)j * 6 + q) * n + k] = st[q];
-        if (j + 1 == len) break;
         StepVals sv;
-        step_values(g, F, st, scale, qm, n_iter, sv);
+        Frame<double> fr;
+        step_values(g, F, st, scale, qm, n_iter, sv, fr);
         if (!sv.ok) {
           bad = true;
           break;
         }
+        double J[6][JC];
+        step_jacobian(g, F, st, scale, qm, sv, fr, J);
+        double *w = scratch + (int64_t)j * 6 * JC * n + k;
+        for (int r = 0; r < 6; ++r)
+          for (int cc = 0; cc < JC; ++cc) w[(int64_t)(r * JC + cc) * n] = J[r][cc];
         st[0] = sv.xn[0]; st[1] = sv.xn[1]; st[2] = sv.phin;
         st[3] = sv.un[0]; st[4] = sv.un[1]; st[5] = sv.un[2];
       }
       // reverse sweep: lambda_n = J_n^T lambda_{n+1}
       for (int j = len - 1; j >= 0 && !bad; --j) {
-        for (int q = 0; q < 6; ++q) st[q] = scratch[((int64_t)j * 6 + q) * n + k];
-        StepVals sv;
-        step_values(g, F, st, scale, qm, n_iter, sv);
-        if (!sv.ok) {
-          bad = true;
-          break;
-        }
-        double J[6][7];
-        step_jacobian(g, F, st, scale, qm, sv, J);
-        double nl[6];
-        for (int i = 0; i < 6; ++i) {
-          double a = 0.0;
-          for (int q = 0; q < 6; ++q) a = fma(J[q][i], lam[q], a);
-          nl[i] = a;
-        }
-        double b = 0.0;
-        for (int q = 0; q < 6; ++q) b = fma(J[q][6], lam[q], b);
-        gs += b;
-        for (int i = 0; i < 6; ++i) lam[i] = nl[i];
+        const double *w = scratch + (int64_t)j * 6 * JC * n + k;
+        double nl[JC] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int r = 0; r < 6; ++r)
+          for (int cc = 0; cc < JC; ++cc) nl[cc] = fma(w[(int64_t)(r * JC + cc) * n], lam[r], nl[cc]);
+        // inputs x1, x2, u1, u2, u3 map to state rows 0, 1, 3, 4, 5; phi passes through
+        lam[0] = nl[0];
+        lam[1] = nl[1];
+        lam[3] = nl[2];
+        lam[4] = nl[3];
+        lam[5] = nl[4];
+        gs += nl[5];
       }
     }
     // a particle that reached a boundary has no gradient: zero where its cotangent was zero

@@ -90,6 +90,18 @@ __device__ __forceinline__ Dual<N> fma_(const Dual<N> &a, const Dual<N> &b, cons
   for (int i = 0; i < N; ++i) r.d[i] = fma(a.d[i], b.v, fma(a.v, b.d[i], c.d[i]));
   return r;
 }
+template <int N>
+__device__ __forceinline__ Dual<N> fma_(double a, const Dual<N> &b, const Dual<N> &c) {
+  Dual<N> r;
+  r.v = fma(a, b.v, c.v);
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = fma(a, b.d[i], c.d[i]);
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> fma_(const Dual<N> &a, double b, const Dual<N> &c) {
+  return fma_(b, a, c);
+}
 // 1/sqrt(a): derivative -a'/(2 a^{3/2})
 template <int N>
 __device__ __forceinline__ Dual<N> rsqrt_(const Dual<N> &a) {

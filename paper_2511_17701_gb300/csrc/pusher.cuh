@@ -110,21 +110,22 @@ __device__ __forceinline__ void local_full(const GridP &g, R r, R s, R c, Local<
   L.m13 = L.k13 * L.rh33;  // h_13 / h_33
 }
 
-// App. A tetrad maps with the precomputed coefficients
-template <typename R>
-__device__ __forceinline__ void vec_hat(const Local<R> &L, const R A[3], R o[3]) {
+// App. A tetrad maps with the precomputed coefficients (M: type of the metric values, R: of
+// the vectors; the same type everywhere except in the adjoint's momentum derivatives)
+template <typename M, typename R>
+__device__ __forceinline__ void vec_hat(const Local<M> &L, const R A[3], R o[3]) {
   o[0] = A[0] * L.rH11;
   o[1] = L.sh22 * A[1];
   o[2] = fma_(L.k13, A[0], L.sh33 * A[2]);
 }
-template <typename R>
-__device__ __forceinline__ void cov_hat(const Local<R> &L, const R a[3], R o[3]) {
+template <typename M, typename R>
+__device__ __forceinline__ void cov_hat(const Local<M> &L, const R a[3], R o[3]) {
   o[0] = L.sH11 * fma_(-L.m13, a[2], a[0]);
   o[1] = a[1] * L.rh22;
   o[2] = a[2] * L.rh33;
 }
-template <typename R>
-__device__ __forceinline__ void hat_cov(const Local<R> &L, const R h[3], R o[3]) {
+template <typename M, typename R>
+__device__ __forceinline__ void hat_cov(const Local<M> &L, const R h[3], R o[3]) {
   o[0] = fma_(h[0], L.rH11, L.k13 * h[2]);
   o[1] = L.sh22 * h[1];
   o[2] = L.sh33 * h[2];
@@ -155,9 +156,10 @@ struct GeoMap {
   R u0, u1, hu0, hu1, c0, c1, e1, e2, f1, f2, D1a, D1b, D2a, D2b, hdt;
   R H11, H22, d1H11, d1H22, d2H11, d2H22;
   GeoMap() = default;
-  __device__ __forceinline__ GeoMap(const GridP &g, const Local<R> &L, const R u[3]) {
+  template <typename M>
+  __device__ __forceinline__ GeoMap(const GridP &g, const Local<M> &L, const R u[3]) {
     const R u3 = u[2];
-    const Geo<R> &o = L.G;
+    const Geo<M> &o = L.G;
     const R dt = cst<R>(g).dt;
     u0 = u[0];
     u1 = u[1];
