@@ -161,3 +161,39 @@ def test_boundary_particles(setup):
         if not expect_nan:
             assert np.all(gin[:, 0] == 0.0)
         assert np.isfinite(gin[:, 1]).all()
+
+
+def test_adjoint_long_horizon_matches_oracle_on_the_512_grid(torch_cuda):
+    """The adjoint workload's grid (512^2, r_max = 50) and horizon (2000 steps): the reverse
+    sweep against the oracle's complex-step Jacobian for a handful of particles."""
+    from paper_2511_17701_gb300 import FIELD_USER, Sim
+    torch = torch_cuda
+    cfg = W.grid_config("wald512", r_absorb=1e300)
+    osim = O.OracleSim(cfg)
+    osim.init_fields(O.FIELD_WALD, 1.0)
+    tp = W.probe_particles(cfg, 12, 21, (0.2 * cfg["n_r"], 0.8 * cfg["n_r"]),
+                           (0.15 * cfg["n_theta"], 0.85 * cfg["n_theta"]), 0.5)
+    qm, qc = W.species_coefficients(1.0)
+    v = osim.add_species(tp["pos"], tp["uhat"], tp["w0"], qm, qc).view()
+    st0 = np.stack([v["i1"] + v["dx1"], v["i2"] + v["dx2"], v["phi"], v["u1"], v["u2"], v["u3"]])
+    g = Sim(dict(cfg, dt=osim.dt), [1])
+    g.init_metric()
+    g.init_fields(FIELD_USER)
+    g.set_planes(osim.F)
+    n_steps = 2000
+    fin, J = O.frozen_jacobian(osim, st0, 1.0, qm, n_steps, 60)
+    ok = ~np.isnan(fin[0])
+    assert ok.sum() >= 8
+    cot = np.random.default_rng(22).standard_normal(st0.shape)
+    cot[:, ~ok] = 0.0
+    st0_t = torch.tensor(st0, dtype=torch.float64, device="cuda")
+    out, ckpt = g.adjoint_forward(st0_t, qm, 1.0, n_steps, 100, N_ITER)
+    gin, gpp, _ = g.adjoint_backward(ckpt, torch.tensor(cot, device="cuda"), qm, 1.0, n_steps,
+                                     100, N_ITER)
+    gin, gpp = gin.cpu().numpy(), gpp.cpu().numpy()
+    ref_in = np.einsum("kqi,qk->ik", J[:, :, :6], cot)
+    ref_b0 = np.einsum("kq,qk->k", J[:, :, 6], cot)
+    for k in np.flatnonzero(ok):
+        sc = max(np.abs(ref_in[:, k]).max(), abs(ref_b0[k]))
+        assert np.max(np.abs(gin[:, k] - ref_in[:, k])) / sc < 1e-6, k
+        assert abs(gpp[k] - ref_b0[k]) / sc < 1e-6, k
