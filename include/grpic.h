@@ -271,6 +271,21 @@ GRPIC_API grpic_status grpic_sort_permutation_noalloc(int n_r, int n_theta, int 
                                                       int64_t n, uint32_t *perm,
                                                       int64_t *n_alive, void *stream);
 
+/* --- charge conservation ------------------------------------------------------------ */
+
+/* The discrete continuity equation of the deposit (Sec. 3.2, Eq. charge-conservation-disc),
+ * evaluated in FP64 for either precision at every node i in [-1, n_r + 1], j in [0, n_theta]:
+ *   res = J^1(i+1/2, j) - J^1(i-1/2, j) + J^2(i, j+1/2) - J^2(i, j-1/2)
+ *         + (rho^{n+1} - rho^n)(i, j) / dt,
+ * with rho the charge q w of every live particle shared over its cell's four nodes by
+ * linear weights at the previous (i1p, dx1p, ...) and the current position. The currents
+ * are those of the last deposit: after grpic_push + grpic_deposit pass after_step = 0;
+ * after grpic_step (whose field advance rotates the currents) pass 1. Writes out[0] =
+ * max |res|, out[1] = max |drho/dt|, out[2] = max over nodes of |res| / (|J terms| +
+ * |drho/dt|). Uses two FP64 planes of the arena; synchronises the stream.
+ * Errors: GRPIC_ESTATE (fields not initialised), GRPIC_EINVAL (null out). */
+GRPIC_API grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double out[3]);
+
 /* --- adjoint of the pusher over frozen fields ---------------------------------------- */
 
 /* Test particles pushed through the fields the context holds, frozen (steps 2-11 of

@@ -30,7 +30,7 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_deposit", "grpic_field_step", "grpic_sort", "grpic_step",
            "grpic_get_diagnostics", "grpic_set_timing", "grpic_get_timing", "grpic_last_error",
            "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants",
-           "grpic_adjoint_forward", "grpic_adjoint_backward"]
+           "grpic_adjoint_forward", "grpic_adjoint_backward", "grpic_charge_check"]
 
 
 ADJOINT_SCRATCH_PER_STEP = 36  # doubles per particle and step of grpic_adjoint_backward
@@ -122,6 +122,7 @@ def lib(build: bool = True):
                                                      P, C.c_int64, P, P, P]
         L.grpic_destroy.argtypes = [P]
         L.grpic_destroy.restype = None
+        L.grpic_charge_check.argtypes = [P, C.c_int, C.POINTER(C.c_double)]
         L.grpic_adjoint_forward.argtypes = [P, C.c_int64, C.c_double, C.c_double, C.c_int,
                                             C.c_int, C.c_int, P, P, P]
         L.grpic_adjoint_backward.argtypes = [P, C.c_int64, C.c_double, C.c_double, C.c_int,
@@ -311,6 +312,13 @@ class Sim:
                     "invariants")
         self.sync()
         return E[:n].cpu().numpy(), L[:n].cpu().numpy()
+
+    def charge_check(self, after_step: bool):
+        """grpic_charge_check: (max |residual|, max |drho/dt|, max node-relative residual)."""
+        out = (C.c_double * 3)()
+        self._check(self.L.grpic_charge_check(self.ctx, 1 if after_step else 0, out),
+                    "charge_check")
+        return float(out[0]), float(out[1]), float(out[2])
 
     # --- adjoint of the pusher over frozen fields -------------------------------------
     def _adjoint_state(self, t, what):
