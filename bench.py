@@ -241,7 +241,8 @@ def measure(args, precision, ws, rank, local):
 
     device = torch.device("cuda", local)
     cfg = W.grid_config(args.workload, sort_every=args.sort_every, tile_r=args.tile,
-                        tile_theta=args.tile, precision=precision)
+                        tile_theta=args.tile, precision=precision,
+                        tiled_push=1 if args.tiled_push else 0)
     if args.ppc:
         cfg["ppc"] = args.ppc
     pl = W.pair_plasma(cfg, seed=cfg["seed"] + 1000 * rank)
@@ -538,6 +539,9 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--adjoint-ckpt", type=int, default=100)
     ap.add_argument("--adjoint-fd-sample", type=int, default=256)
+    ap.add_argument("--tiled-push", action="store_true",
+                    help="mixed path: the shared-memory tiled FP32 kernel instead of the default "
+                         "one thread per particle")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -110,6 +110,11 @@ typedef struct {
                           n_iter result exactly); 1: always run n_iter iterations             */
   int fp64_guard_cells; /* GRPIC_MIXED: cells from the horizon and from each axis where the
                            metric is evaluated in FP64 (default 4 when 0)                     */
+  int tiled_push;       /* GRPIC_MIXED: 1 = after a sort, push each sort tile in one CTA with
+                           the fields of the tile and a 6-cell halo staged in shared memory and
+                           the currents accumulated there; 0 (default) = one thread per
+                           particle over the whole species with gathers through L1/L2, which
+                           measures faster on GB300 for this pusher                            */
 } grpic_config;
 
 /* Pointers to one species' particle arrays (SoA, length >= n). Positions are a cell

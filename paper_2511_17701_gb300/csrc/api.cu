@@ -31,6 +31,9 @@ struct SpeciesState {
   size_t off_n = 0, off_soa[2][NARR] = {};
   size_t off_gl = 0;  // guard list, mask and counters (mixed path)
   GuardList gl{};
+  size_t off_tiles = 0;       // tile ranges of the last sort (mixed path)
+  uint32_t *tile_start = nullptr;
+  bool tiles_valid = false;
 };
 
 size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
@@ -230,8 +233,12 @@ cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, int k, bool deposit) {
   const std::pair<cudaEvent_t, cudaEvent_t> *kt = next_events(c, PH_KERNEL);
   const PushStreams ps{c->stream, c->side, c->ev_fork[k], c->ev_done[k],
                        kt ? kt->first : nullptr, kt ? kt->second : nullptr};
-  return launch_push<T>(c->g, F, dev_view<T>(sp, sp.live), c->tb, sp.gl, sp.n_bound, deposit,
-                        c->diag, ps);
+  const int tr = c->cfg.tile_r, tt = c->cfg.tile_theta;
+  const int ntr = (c->g.n_r + tr - 1) / tr, ntt = (c->g.n_th + tt - 1) / tt;
+  const TileInfo ti{sp.tiles_valid && c->cfg.tiled_push ? sp.tile_start : nullptr, tr, tt, ntr,
+                    ntr * ntt};
+  return launch_push<T>(c->g, F, dev_view<T>(sp, sp.live), c->tb, sp.gl, ti, sp.n_bound,
+                        deposit, c->diag, ps);
 }
 // the main stream waits for the guard kernels of species k (mixed path)
 cudaError_t join_push(grpic_ctx *c, int k) {
@@ -350,12 +357,17 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   ctx->off_hist = off;  off += up((size_t)sort_hist_entries(ctx->max_cap) * 4);
   ctx->off_bsum = off;  off += up((size_t)sort_bsum_entries(ctx->max_cap) * 4);
   ctx->off_alive = off; off += up(8);
-  if (ctx->mixed)
+  if (ctx->mixed) {
+    const int64_t ntiles = (int64_t)((c.n_r + c.tile_r - 1) / c.tile_r) *
+                           ((c.n_theta + c.tile_theta - 1) / c.tile_theta);
     for (int s = 0; s < c.n_species; ++s) {
       const size_t cap = (size_t)(ctx->sp[s].cap > 0 ? ctx->sp[s].cap : 1);
       ctx->sp[s].off_gl = off;
       off += up(cap * 4) + up((cap + 31) / 32 * 4) + up(16);
+      ctx->sp[s].off_tiles = off;
+      off += up((size_t)(ntiles + 1) * 4);
     }
+  }
   ctx->off_rho = off; off += 2 * up(ps * 8) + up(64);  // FP64 charge planes of the check
   ctx->load_chunk = ctx->max_cap < ((int64_t)1 << 20) ? ctx->max_cap : ((int64_t)1 << 20);
   ctx->off_stage = off; off += 6 * up((size_t)ctx->load_chunk * 8);
@@ -391,6 +403,8 @@ grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream)
       sp.gl.mask = at<uint32_t>(ctx, sp.off_gl + up(cap * 4));
       sp.gl.count = at<unsigned long long>(ctx, sp.off_gl + up(cap * 4) + up((cap + 31) / 32 * 4));
       sp.gl.cap = (int64_t)cap;
+      sp.tile_start = at<uint32_t>(ctx, sp.off_tiles);
+      sp.tiles_valid = false;
     }
     if (!ctx->side) {  // the guard kernels are the longer chain: higher priority
       int lo = 0, hi = 0;
@@ -504,6 +518,7 @@ grpic_status grpic_load_particles(grpic_ctx *ctx, int species, int64_t n, double
   CK(cudaGetLastError());
   sp.n_bound = n;
   sp.loaded = true;
+  sp.tiles_valid = false;  // new particles: no tile ranges until the next sort
   return GRPIC_OK;
 }
 
@@ -530,6 +545,7 @@ grpic_status grpic_set_particles(grpic_ctx *ctx, int species, int64_t n, double 
   CK(cudaGetLastError());
   sp.n_bound = n;
   sp.loaded = true;
+  sp.tiles_valid = false;  // new particles: no tile ranges until the next sort
   return GRPIC_OK;
 }
 
@@ -648,14 +664,16 @@ grpic_status grpic_sort(grpic_ctx *ctx, int species) {
   SpeciesState &sp = ctx->sp[species];
   if (!sp.loaded) return GRPIC_OK;
   PhaseTimer t(ctx, PH_SORT);
-  if (ctx->mixed)
+  if (ctx->mixed) {
     CK(launch_sort<float>(ctx->g, ctx->cfg.tile_r, ctx->cfg.tile_theta, dev_view<float>(sp, sp.live),
                           dev_view<float>(sp, 1 - sp.live), sp.n_bound, sp.n_dev, ctx->S,
-                          ctx->stream));
-  else
+                          sp.tile_start, ctx->stream));
+    sp.tiles_valid = true;
+  } else {
     CK(launch_sort<double>(ctx->g, ctx->cfg.tile_r, ctx->cfg.tile_theta,
                            dev_view<double>(sp, sp.live), dev_view<double>(sp, 1 - sp.live),
-                           sp.n_bound, sp.n_dev, ctx->S, ctx->stream));
+                           sp.n_bound, sp.n_dev, ctx->S, nullptr, ctx->stream));
+  }
   sp.live = 1 - sp.live;
   return GRPIC_OK;
 }

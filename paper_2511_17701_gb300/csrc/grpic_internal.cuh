@@ -275,6 +275,14 @@ struct GuardList {
   unsigned long long *count;
 };
 
+// The particle range of every sort tile (mixed path): particles tile_start[t] ..
+// tile_start[t+1] - 1 were in tile t at the last sort (start is null when no sort has run
+// since the particles were last set, and the push does not use tiles).
+struct TileInfo {
+  const uint32_t *start;
+  int tr, tt, ntr, n_tiles;
+};
+
 // Streams of one push: the FP64-pipe-bound guard kernels run on `side`, forked from
 // `main` after the classification by `fork`; `done` is recorded on `side` after them and
 // the caller makes `main` wait on it before anything reads the currents or the particles.
@@ -323,8 +331,9 @@ cudaError_t launch_load(const GridP &g, SpeciesDevT<T> s, int64_t k0, int64_t n,
                         const grpic_particle_init &in, double density_power, cudaStream_t st);
 template <typename T>
 cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
-                        const PushTables &tb, const GuardList &gl, int64_t n_bound, bool deposit,
-                        unsigned long long *diag, const PushStreams &ps);
+                        const PushTables &tb, const GuardList &gl, const TileInfo &ti,
+                        int64_t n_bound, bool deposit, unsigned long long *diag,
+                        const PushStreams &ps);
 template <typename T>
 cudaError_t launch_deposit(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
                            const PushTables &tb, int64_t n_bound, cudaStream_t st);
@@ -345,4 +354,4 @@ int64_t sort_bsum_entries(int64_t max_n);
 template <typename T>
 cudaError_t launch_sort(const GridP &g, int tile_r, int tile_t, SpeciesDevT<T> in,
                         SpeciesDevT<T> out, int64_t n_bound, int64_t *n_dev, const SortScratch &S,
-                        cudaStream_t st);
+                        uint32_t *tile_start, cudaStream_t st);

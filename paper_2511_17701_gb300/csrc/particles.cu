@@ -336,18 +336,53 @@ __device__ __forceinline__ void geo_at(const GridP &g, const PushTables &tb, int
   }
 }
 
-// bilinear interpolation from the cell-relative position (i, o) for a Yee offset (s1, s2)
-__device__ __forceinline__ float interp32(const float *__restrict__ pl, int NX, int i1, int i2,
-                                          float o1, float o2, float s1, float s2) {
+// bilinear interpolation from the cell-relative position (i, o) for a Yee offset (s1, s2),
+// in a plane of row stride `stride` whose element (0, 0) is cell (0, 0) of the indices given
+// (read through the read-only data path from global memory, or plainly from shared memory)
+template <bool SMEM>
+__device__ __forceinline__ float interp_gen(const float *__restrict__ pl, int stride, int i1,
+                                            int i2, float o1, float o2, float s1, float s2) {
   const float y1 = o1 - s1, y2 = o2 - s2;
   const float f1 = floorf(y1), f2 = floorf(y2);
   const int i0 = i1 + (int)f1, j0 = i2 + (int)f2;
   const float w1 = y1 - f1, w2 = y2 - f2;
-  const float *p = pl + (int64_t)(j0 + G_) * NX + (i0 + G_);
-  const float a = fmaf(w1, __ldg(p + 1) - __ldg(p), __ldg(p));
-  const float b = fmaf(w1, __ldg(p + NX + 1) - __ldg(p + NX), __ldg(p + NX));
+  const float *p = pl + (int64_t)j0 * stride + i0;
+  float p00, p10, p01, p11;
+  if constexpr (SMEM) {
+    p00 = p[0]; p10 = p[1]; p01 = p[stride]; p11 = p[stride + 1];
+  } else {
+    p00 = __ldg(p); p10 = __ldg(p + 1); p01 = __ldg(p + stride); p11 = __ldg(p + stride + 1);
+  }
+  const float a = fmaf(w1, p10 - p00, p00);
+  const float b = fmaf(w1, p11 - p01, p01);
   return fmaf(w2, b - a, a);
 }
+
+// The fields of the push: B^n and D planes in global memory ...
+struct GlobalFields {
+  const float *pl[6];  // Bn1..3, D1..3, shifted so that index (j, i) is cell (i, j)
+  int NX;
+  __device__ __forceinline__ GlobalFields(const GridP &g, const FieldPtrsT<float> &F) : NX(g.NX) {
+    const int64_t o = (int64_t)G_ * g.NX + G_;
+    for (int c = 0; c < 3; ++c) {
+      pl[c] = F.Bn[c] + o;
+      pl[3 + c] = F.D[c] + o;
+    }
+  }
+  __device__ __forceinline__ float at(int c, int i1, int i2, float o1, float o2, float s1,
+                                      float s2) const {
+    return interp_gen<false>(pl[c], NX, i1, i2, o1, o2, s1, s2);
+  }
+};
+// ... or a shared-memory window of W1 x W2 nodes whose node (0, 0) is cell (iw0, jw0)
+struct WindowFields {
+  const float *win;  // 6 planes of W1 * W2
+  int W1, plane, iw0, jw0;
+  __device__ __forceinline__ float at(int c, int i1, int i2, float o1, float o2, float s1,
+                                      float s2) const {
+    return interp_gen<true>(win + c * plane, W1, i1 - iw0, i2 - jw0, o1, o2, s1, s2);
+  }
+};
 
 // One move of the mixed path, relative to its start cell (ia, ja): from (a1, a2) in [0, 1]^2
 // to (b1, b2) in cell (ia + di, ja + dj), charge weight q and dphi/dt v3 at the midpoint.
@@ -386,20 +421,55 @@ __device__ __forceinline__ void zigzag32(const GridP &g, const Move32 &m, float 
   cell[2] = (int)sidx(g, m.ia + (int)f1, m.ja + (int)f2);
 }
 
-__device__ __forceinline__ void add_group(const FieldPtrsT<float> &F, int NX, int grp, int k,
-                                          const float c[4]) {
-  if (grp < 2) {
-    atomicAdd(F.J[0] + k, c[0]);
-    atomicAdd(F.J[0] + k + NX, c[1]);
-    atomicAdd(F.J[1] + k, c[2]);
-    atomicAdd(F.J[1] + k + 1, c[3]);
-  } else {
-    atomicAdd(F.J[2] + k, c[0]);
-    atomicAdd(F.J[2] + k + 1, c[1]);
-    atomicAdd(F.J[2] + k + NX, c[2]);
-    atomicAdd(F.J[2] + k + NX + 1, c[3]);
+// Where the deposit goes: the current planes in global memory ...
+struct GlobalSink {
+  float *J[3];
+  int NX;
+  __device__ __forceinline__ GlobalSink(const GridP &g, const FieldPtrsT<float> &F) : NX(g.NX) {
+    for (int c = 0; c < 3; ++c) J[c] = F.J[c];
   }
-}
+  __device__ __forceinline__ void add(int grp, int k, const float c[4]) const {
+    if (grp < 2) {
+      atomicAdd(J[0] + k, c[0]);
+      atomicAdd(J[0] + k + NX, c[1]);
+      atomicAdd(J[1] + k, c[2]);
+      atomicAdd(J[1] + k + 1, c[3]);
+    } else {
+      atomicAdd(J[2] + k, c[0]);
+      atomicAdd(J[2] + k + 1, c[1]);
+      atomicAdd(J[2] + k + NX, c[2]);
+      atomicAdd(J[2] + k + NX + 1, c[3]);
+    }
+  }
+};
+// ... or a shared-memory window (as WindowFields) flushed to global memory by the caller;
+// a group whose four targets are not all inside it goes to global memory directly
+struct WindowSink {
+  GlobalSink glob;
+  float *win;  // 3 planes of W1 * W2
+  int W1, W2, plane, iw0, jw0;
+  __device__ __forceinline__ void add(int grp, int k, const float c[4]) const {
+    const int j = k / glob.NX - G_, i = k - (j + G_) * glob.NX - G_;
+    const int wi = i - iw0, wj = j - jw0;
+    if (wi < 0 || wj < 0 || wi > W1 - 2 || wj > W2 - 2) {
+      glob.add(grp, k, c);
+      return;
+    }
+    float *w = win + wj * W1 + wi;
+    if (grp < 2) {
+      atomicAdd(w, c[0]);
+      atomicAdd(w + W1, c[1]);
+      atomicAdd(w + plane, c[2]);
+      atomicAdd(w + plane + 1, c[3]);
+    } else {
+      w += 2 * plane;
+      atomicAdd(w, c[0]);
+      atomicAdd(w + 1, c[1]);
+      atomicAdd(w + W1, c[2]);
+      atomicAdd(w + W1 + 1, c[3]);
+    }
+  }
+};
 
 // Sums of v over runs of equal keys in consecutive lanes (all 32 lanes call it): a suffix
 // scan bounded by the next run head, so the first lane of each run ends with the run's sum.
@@ -429,7 +499,8 @@ __device__ __forceinline__ bool run_sums(int key, float v[4]) {
 // shuffles (particles are kept sorted by cell, so a warp holds few runs) and the first lane
 // of each run issues the four atomics. A move that stays in its cell has both segments in
 // that cell; they are added before the reduction.
-__device__ __forceinline__ void deposit32_warp(const GridP &g, const FieldPtrsT<float> &F,
+template <class Sink>
+__device__ __forceinline__ void deposit32_warp(const GridP &g, const Sink &sink,
                                                const Move32 &m, bool on) {
   float c[3][4];
   int cell[3] = {-1, -1, -1};
@@ -450,7 +521,7 @@ __device__ __forceinline__ void deposit32_warp(const GridP &g, const FieldPtrsT<
   for (int grp = 0; grp < 3; ++grp) {
     if (!__any_sync(0xffffffffu, cell[grp] >= 0)) continue;
     const bool head = run_sums(cell[grp], c[grp]);
-    if (head && cell[grp] >= 0) add_group(F, g.NX, grp, cell[grp], c[grp]);
+    if (head && cell[grp] >= 0) sink.add(grp, cell[grp], c[grp]);
   }
 }
 
@@ -471,19 +542,19 @@ __device__ __forceinline__ float phi_rate32(const GridP &g, const PushTables &tb
 // enters dphi/dt divided by r sin(theta), which has no lower bound in those rows; one row
 // or more away sin(theta) >= dtheta and dt <= CFL r dtheta bound the phi error per step
 // by about eps CFL.
-template <bool G64>
-__device__ __forceinline__ bool push32(const GridP &g, const FieldPtrsT<float> &F,
-                                       const PushTables &tb, const SpeciesDevT<float> &s,
-                                       int64_t k, unsigned long long *diag, Move32 &mv) {
+template <bool G64, class Fields>
+__device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const PushTables &tb,
+                                       const SpeciesDevT<float> &s, int64_t k,
+                                       unsigned long long *diag, Move32 &mv) {
   const int i1 = s.i1[k], i2 = s.i2[k];
   const float dx1 = s.dx1[k], dx2 = s.dx2[k];
   float Bv[3], Dv[3];
-  Bv[0] = interp32(F.Bn[0], g.NX, i1, i2, dx1, dx2, 0.0f, 0.5f);
-  Bv[1] = interp32(F.Bn[1], g.NX, i1, i2, dx1, dx2, 0.5f, 0.0f);
-  Bv[2] = interp32(F.Bn[2], g.NX, i1, i2, dx1, dx2, 0.5f, 0.5f);
-  Dv[0] = interp32(F.D[0], g.NX, i1, i2, dx1, dx2, 0.5f, 0.0f);
-  Dv[1] = interp32(F.D[1], g.NX, i1, i2, dx1, dx2, 0.0f, 0.5f);
-  Dv[2] = interp32(F.D[2], g.NX, i1, i2, dx1, dx2, 0.0f, 0.0f);
+  Bv[0] = F.at(0, i1, i2, dx1, dx2, 0.0f, 0.5f);
+  Bv[1] = F.at(1, i1, i2, dx1, dx2, 0.5f, 0.0f);
+  Bv[2] = F.at(2, i1, i2, dx1, dx2, 0.5f, 0.5f);
+  Dv[0] = F.at(3, i1, i2, dx1, dx2, 0.5f, 0.0f);
+  Dv[1] = F.at(4, i1, i2, dx1, dx2, 0.0f, 0.5f);
+  Dv[2] = F.at(5, i1, i2, dx1, dx2, 0.0f, 0.0f);
   Local<float> L;
   if constexpr (G64) {
     double r0, sn, cs;
@@ -627,11 +698,80 @@ __global__ void __launch_bounds__(TPB) k_push32(GridP g, FieldPtrsT<float> F,
       const int i1 = s.i1[k], i2 = s.i2[k];
       s.i1p[k] = i1; s.i2p[k] = i2; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
       const uint8_t tag = s.tag[k];
-      if (tag == 1) on = push32<false>(g, F, tb, s, k, diag, mv);
+      if (tag == 1) on = push32<false>(g, GlobalFields(g, F), tb, s, k, diag, mv);
       else if (tag != 0) s.tag[k] = 0;
     }
-    if (DEPOSIT) deposit32_warp(g, F, mv, on);
+    if (DEPOSIT) deposit32_warp(g, GlobalSink(g, F), mv, on);
   }
+}
+
+// Mixed path, FP32 kernel on sort tiles: one CTA per tile pushes the particles that were in
+// the tile at the last sort. The B^n and D planes of the tile and a halo of TILE_HALO cells
+// are staged in shared memory; the deposit (after the warp reduction) accumulates in a
+// shared-memory window of the same extent, flushed to global memory at the end. A particle
+// whose cell has drifted out of the window gathers from, and deposits to, global memory.
+constexpr int TILE_HALO = 6;
+constexpr int TILE_TPB = 256;
+template <bool DEPOSIT>
+__global__ void __launch_bounds__(TILE_TPB) k_push32_tiled(GridP g, FieldPtrsT<float> F,
+                                                          SpeciesDevT<float> s, PushTables tb,
+                                                          GuardList gl, TileInfo ti,
+                                                          unsigned long long *diag) {
+  extern __shared__ float sm[];
+  const int t = blockIdx.x;
+  const int tx = t % ti.ntr, ty = t / ti.ntr;
+  const int W1 = ti.tr + 2 * TILE_HALO, W2 = ti.tt + 2 * TILE_HALO, plane = W1 * W2;
+  const int iw0 = tx * ti.tr - TILE_HALO, jw0 = ty * ti.tt - TILE_HALO;
+  float *fwin = sm, *jwin = sm + 6 * plane;
+  // stage the fields (zero outside the stored planes) and clear the current window
+  for (int e = threadIdx.x; e < 6 * plane; e += blockDim.x) {
+    const int c = e / plane, r = e - c * plane, wj = r / W1, wi = r - wj * W1;
+    const int i = iw0 + wi, j = jw0 + wj;
+    float v = 0.0f;
+    if (i >= -G_ && i < g.NX - G_ && j >= -G_ && j < g.NY - G_)
+      v = __ldg((c < 3 ? F.Bn[c] : F.D[c - 3]) + sidx(g, i, j));
+    fwin[e] = v;
+  }
+  if (DEPOSIT)
+    for (int e = threadIdx.x; e < 3 * plane; e += blockDim.x) jwin[e] = 0.0f;
+  __syncthreads();
+  const WindowFields wf{fwin, W1, plane, iw0, jw0};
+  const GlobalFields gf(g, F);
+  const WindowSink ws{GlobalSink(g, F), jwin, W1, W2, plane, iw0, jw0};
+  const int64_t begin = ti.start[t], end = ti.start[t + 1];
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = begin + threadIdx.x; k - lane < end; k += blockDim.x) {
+    Move32 mv;
+    bool on = false;
+    if (k < end && !((__ldg(gl.mask + (k >> 5)) >> (k & 31)) & 1u)) {
+      const int i1 = s.i1[k], i2 = s.i2[k];
+      s.i1p[k] = i1; s.i2p[k] = i2; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+      const uint8_t tag = s.tag[k];
+      if (tag == 1) {
+        // the interpolation reads cells i +- 1, j +- 1
+        const bool inside = i1 - 1 >= iw0 && i1 + 1 < iw0 + W1 && i2 - 1 >= jw0 && i2 + 1 < jw0 + W2;
+        on = inside ? push32<false>(g, wf, tb, s, k, diag, mv)
+                    : push32<false>(g, gf, tb, s, k, diag, mv);
+      } else if (tag != 0) {
+        s.tag[k] = 0;
+      }
+    }
+    if (DEPOSIT) deposit32_warp(g, ws, mv, on);
+  }
+  if (DEPOSIT) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 3 * plane; e += blockDim.x) {
+      const float v = jwin[e];
+      if (v != 0.0f) {
+        const int c = e / plane, r = e - c * plane, wj = r / W1, wi = r - wj * W1;
+        atomicAdd(F.J[c] + sidx(g, iw0 + wi, jw0 + wj), v);
+      }
+    }
+  }
+}
+
+size_t tiled_smem_bytes(const TileInfo &ti) {
+  return (size_t)9 * (ti.tr + 2 * TILE_HALO) * (ti.tt + 2 * TILE_HALO) * sizeof(float);
 }
 
 // Mixed path, guard kernels (side stream): step 1 and the routine of the listed particles,
@@ -649,9 +789,9 @@ __global__ void __launch_bounds__(TPB) k_push_guard(GridP g, FieldPtrsT<float> F
     if (t < n) {
       const int64_t k = gl.idx[t];
       s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
-      on = push32<true>(g, F, tb, s, k, diag, mv);
+      on = push32<true>(g, GlobalFields(g, F), tb, s, k, diag, mv);
     }
-    if (DEPOSIT) deposit32_warp(g, F, mv, on);
+    if (DEPOSIT) deposit32_warp(g, GlobalSink(g, F), mv, on);
   }
 }
 
@@ -694,7 +834,7 @@ __global__ void __launch_bounds__(TPB) k_deposit(GridP g, FieldPtrsT<T> F, Speci
                               : phi_rate32<false>(g, tb, ia, ja, m1, m2, u);
         mv = Move32{ia, ja, ib - ia, jb - ja, a1, a2, b1, b2, s.f_qc * s.w[k], v3};
       }
-      deposit32_warp(g, F, mv, on);
+      deposit32_warp(g, GlobalSink(g, F), mv, on);
     }
     if (live && zone == 2) {  // FP64 path, and the axis rows of the mixed path
       const double xa1 = ia + (double)s.dx1p[k], xa2 = ja + (double)s.dx2p[k];
@@ -804,8 +944,9 @@ cudaError_t launch_load(const GridP &g, SpeciesDevT<T> s, int64_t k0, int64_t n,
 
 template <typename T>
 cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
-                        const PushTables &tb, const GuardList &gl, int64_t n_bound, bool deposit,
-                        unsigned long long *diag, const PushStreams &ps) {
+                        const PushTables &tb, const GuardList &gl, const TileInfo &ti,
+                        int64_t n_bound, bool deposit, unsigned long long *diag,
+                        const PushStreams &ps) {
   if (n_bound <= 0) {  // keep a requested event pair recorded (zero duration)
     if (ps.t0) cudaEventRecord(ps.t0, ps.main);
     if (ps.t1) cudaEventRecord(ps.t1, ps.main);
@@ -833,9 +974,25 @@ cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s
       k_push_guard<false><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
       k_push_axis<false><<<152 * 4, 32, 0, ps.side>>>(g, F, s, gl, diag);
     }
+    // the tiled kernel needs the tile ranges of a sort and a window that fits in shared memory
+    const size_t smem = tiled_smem_bytes(ti);
+    const bool tiled = ti.start != nullptr && smem <= 200 * 1024;
+    if (tiled && smem > 48 * 1024) {
+      if ((e = cudaFuncSetAttribute(k_push32_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess) return e;
+      if ((e = cudaFuncSetAttribute(k_push32_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess) return e;
+    }
     if (ps.t0) cudaEventRecord(ps.t0, ps.main);
-    if (deposit) k_push32<true><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
-    else k_push32<false><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
+    if (tiled) {
+      if (deposit)
+        k_push32_tiled<true><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
+      else
+        k_push32_tiled<false><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
+    } else {
+      if (deposit) k_push32<true><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
+      else k_push32<false><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
+    }
     if (ps.t1) cudaEventRecord(ps.t1, ps.main);
     if ((e = cudaEventRecord(ps.done, ps.side)) != cudaSuccess) return e;
     COUNT_LAUNCH(4);
@@ -865,8 +1022,9 @@ cudaError_t launch_invariants(const GridP &g, SpeciesDevT<T> s, int kind, double
   template cudaError_t launch_load<T>(const GridP &, SpeciesDevT<T>, int64_t, int64_t,        \
                                       const grpic_particle_init &, double, cudaStream_t);     \
   template cudaError_t launch_push<T>(const GridP &, const FieldPtrsT<T> &, SpeciesDevT<T>,    \
-                                      const PushTables &, const GuardList &, int64_t, bool,    \
-                                      unsigned long long *, const PushStreams &);              \
+                                      const PushTables &, const GuardList &, const TileInfo &, \
+                                      int64_t, bool, unsigned long long *,                     \
+                                      const PushStreams &);                                    \
   template cudaError_t launch_deposit<T>(const GridP &, const FieldPtrsT<T> &, SpeciesDevT<T>, \
                                          const PushTables &, int64_t, cudaStream_t);           \
   template cudaError_t launch_invariants<T>(const GridP &, SpeciesDevT<T>, int, double,        \

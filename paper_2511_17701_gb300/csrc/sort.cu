@@ -37,6 +37,23 @@ __global__ void k_keys(SpeciesDevT<T> s, int n_r, int tr, int tt, uint32_t *keys
   }
 }
 
+// After the sort: tile_start[t] = the first particle of tile t (keys ascending, the dropped
+// particles last), t = 0 .. n_tiles; tile_start[n_tiles] = the live count.
+__global__ void k_tile_ranges(const uint32_t *keys, const int64_t *n_dev, int n_tiles,
+                              uint32_t cells_per_tile, uint32_t *tile_start) {
+  const int64_t n = *n_dev;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= n_tiles; t += gridDim.x * blockDim.x) {
+    const uint64_t target = (uint64_t)t * cells_per_tile;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((uint64_t)keys[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    tile_start[t] = (uint32_t)lo;
+  }
+}
+
 __global__ void k_hist(const uint32_t *keys, const int64_t *n_dev, int shift, int nblocks,
                        uint32_t *hist) {
   __shared__ uint32_t cnt[256];
@@ -170,7 +187,8 @@ int64_t sort_bsum_entries(int64_t max_n) {
 
 template <typename T>
 cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDevT<T> in, SpeciesDevT<T> out,
-                        int64_t n_bound, int64_t *n_dev, const SortScratch &S, cudaStream_t st) {
+                        int64_t n_bound, int64_t *n_dev, const SortScratch &S,
+                        uint32_t *tile_start, cudaStream_t st) {
   if (n_bound <= 0) return cudaGetLastError();
   // number of key bits: keys of alive particles are < tiles * tr * tt; 0xFFFFFFFF must
   // sort after them, i.e. its low bits must exceed every alive key
@@ -203,6 +221,12 @@ cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDevT<T> in, Speci
     COUNT_LAUNCH(1);
     cur = 1 - cur;
   }
+  if (tile_start) {  // before k_set_n: the key count is the count before the sort
+    const int n_tiles = (int)(ntr * ntt);
+    k_tile_ranges<<<(n_tiles + 1 + 255) / 256, 256, 0, st>>>(S.keys[cur], in.n, n_tiles,
+                                                             (uint32_t)(tr * tt), tile_start);
+    COUNT_LAUNCH(1);
+  }
   k_gather<T><<<grid_for(n_bound, TPB), TPB, 0, st>>>(in, out, S.vals[cur], in.n);
   COUNT_LAUNCH(1);
   k_set_n<<<1, 1, 0, st>>>(n_dev, alive);
@@ -212,10 +236,10 @@ cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDevT<T> in, Speci
 
 template cudaError_t launch_sort<double>(const GridP &, int, int, SpeciesDevT<double>,
                                          SpeciesDevT<double>, int64_t, int64_t *,
-                                         const SortScratch &, cudaStream_t);
+                                         const SortScratch &, uint32_t *, cudaStream_t);
 template cudaError_t launch_sort<float>(const GridP &, int, int, SpeciesDevT<float>,
                                         SpeciesDevT<float>, int64_t, int64_t *,
-                                        const SortScratch &, cudaStream_t);
+                                        const SortScratch &, uint32_t *, cudaStream_t);
 
 // ---------------------------------------------------------------------------------
 // grpic_sort_permutation_noalloc: the same stable cell sort, for callers that cannot
