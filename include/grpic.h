@@ -287,9 +287,12 @@ GRPIC_API grpic_status grpic_sort_permutation_noalloc(int n_r, int n_theta, int 
  * are those of the last deposit: after grpic_push + grpic_deposit pass after_step = 0;
  * after grpic_step (whose field advance rotates the currents) pass 1. Writes out[0] =
  * max |res|, out[1] = max |drho/dt|, out[2] = max over nodes of |res| / (|J terms| +
- * |drho/dt|). Uses two FP64 planes of the arena; synchronises the stream.
+ * |drho/dt|), out[3] = max over nodes of sum |q w| S / dt at both positions (the scale of
+ * the rounding: charges of opposite sign cancel in rho but not here, so a rounded residual
+ * is a small multiple of eps * out[3]). Uses three FP64 planes of the arena; synchronises the
+ * stream.
  * Errors: GRPIC_ESTATE (fields not initialised), GRPIC_EINVAL (null out). */
-GRPIC_API grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double out[3]);
+GRPIC_API grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double out[4]);
 
 /* --- adjoint of the pusher over frozen fields ---------------------------------------- */
 

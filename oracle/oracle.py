@@ -187,6 +187,20 @@ def sort_key(cfg, tr, tt, i1, i2, tag):
     return lib().ora_sort_key(C.byref(make_params(cfg)), tr, tt, i1, i2, tag)
 
 
+def sort_keys(cfg, tr, tt, i1, i2, tag=None):
+    """ora_sort_key for whole arrays: tile-major cell key (tile = (i2 // tt) * ntr + i1 // tr,
+    ntr = ceil(n_r / tr); key = tile * tr * tt + (i2 % tt) * tr + i1 % tr), 0xFFFFFFFF for
+    particles not alive, for cells inside the grid (i1, i2 >= 0, as every live particle's).
+    A stable argsort of the keys is the sort's permutation."""
+    i1 = np.asarray(i1, dtype=np.int64)
+    i2 = np.asarray(i2, dtype=np.int64)
+    ntr = (int(cfg["n_r"]) + tr - 1) // tr
+    key = ((i2 // tt) * ntr + i1 // tr) * (tr * tt) + (i2 % tt) * tr + i1 % tr
+    if tag is not None:
+        key = np.where(np.asarray(tag) == 1, key, 0xFFFFFFFF)
+    return key.astype(np.uint32)
+
+
 class OracleSpecies:
     """Particle arrays of one species (numpy), mirrored into the C struct on use."""
 

@@ -315,11 +315,12 @@ class Sim:
         return E[:n].cpu().numpy(), L[:n].cpu().numpy()
 
     def charge_check(self, after_step: bool):
-        """grpic_charge_check: (max |residual|, max |drho/dt|, max node-relative residual)."""
-        out = (C.c_double * 3)()
+        """grpic_charge_check: (max |residual|, max |drho/dt|, max node-relative residual,
+        max absolute charge per node / dt, the rounding scale)."""
+        out = (C.c_double * 4)()
         self._check(self.L.grpic_charge_check(self.ctx, 1 if after_step else 0, out),
                     "charge_check")
-        return float(out[0]), float(out[1]), float(out[2])
+        return tuple(float(v) for v in out)
 
     # --- adjoint of the pusher over frozen fields -------------------------------------
     def _adjoint_state(self, t, what):

@@ -258,15 +258,18 @@ template <typename T>
 cudaError_t charge_check(grpic_ctx *ctx, FieldPtrsT<T> &F, bool after_step, double *out) {
   const int64_t ps = plane_size(ctx->g);
   double *rp = at<double>(ctx, ctx->off_rho), *rn = at<double>(ctx, ctx->off_rho + up(ps * 8));
+  double *ra = at<double>(ctx, ctx->off_rho + 2 * up(ps * 8));
   cudaError_t e = launch_zero<double>(rp, ps, ctx->stream);
   if (e == cudaSuccess) e = launch_zero<double>(rn, ps, ctx->stream);
+  if (e == cudaSuccess) e = launch_zero<double>(ra, ps, ctx->stream);
   for (int k = 0; k < ctx->cfg.n_species && e == cudaSuccess; ++k) {
     SpeciesState &sp = ctx->sp[k];
     if (sp.loaded) e = launch_charge_rho<T>(ctx->g, dev_view<T>(sp, sp.live), sp.n_bound, rp, rn,
-                                            ctx->stream);
+                                            ra, ctx->stream);
   }
   T *const *J = after_step ? F.J0 : F.J;
-  if (e == cudaSuccess) e = launch_continuity<T>(ctx->g, J[0], J[1], rp, rn, out, ctx->stream);
+  if (e == cudaSuccess)
+    e = launch_continuity<T>(ctx->g, J[0], J[1], rp, rn, ra, out, ctx->stream);
   return e;
 }
 
@@ -368,7 +371,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
       off += up((size_t)(ntiles + 1) * 4);
     }
   }
-  ctx->off_rho = off; off += 2 * up(ps * 8) + up(64);  // FP64 charge planes of the check
+  ctx->off_rho = off; off += 3 * up(ps * 8) + up(64);  // FP64 charge planes of the check
   ctx->load_chunk = ctx->max_cap < ((int64_t)1 << 20) ? ctx->max_cap : ((int64_t)1 << 20);
   ctx->off_stage = off; off += 6 * up((size_t)ctx->load_chunk * 8);
   ctx->need = off;
@@ -721,14 +724,14 @@ grpic_status grpic_step(grpic_ctx *ctx, int n_steps) {
   return GRPIC_OK;
 }
 
-grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double out[3]) {
+grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double out[4]) {
   grpic_status s = need_fields(ctx);
   if (s) return s;
   if (!out) return GRPIC_EINVAL;
-  double *dev = at<double>(ctx, ctx->off_rho + 2 * up((size_t)plane_size(ctx->g) * 8));
+  double *dev = at<double>(ctx, ctx->off_rho + 3 * up((size_t)plane_size(ctx->g) * 8));
   if (ctx->mixed) CK(charge_check(ctx, ctx->F32, after_step != 0, dev));
   else CK(charge_check(ctx, ctx->F64, after_step != 0, dev));
-  CK(cudaMemcpyAsync(out, dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(out, dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return GRPIC_OK;
 }

@@ -11,23 +11,32 @@ namespace {
 
 constexpr int TPB_Q = 256;
 
+// rho at the previous and current positions, and the charge magnitude sum |q w| S over both
+// (the scale of their rounding: charges of opposite sign cancel in rho, not in rho_abs)
 template <typename T>
 __global__ void __launch_bounds__(TPB_Q) k_rho(GridP g, SpeciesDevT<T> s, double *rho_prev,
-                                              double *rho_new) {
+                                              double *rho_new, double *rho_abs) {
   const int64_t n = *s.n;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     if (s.tag[k] == 0) continue;
-    const double q = s.qc * (double)s.w[k];
+    const double q = s.qc * (double)s.w[k], qa = fabs(q);
     for (int which = 0; which < 2; ++which) {
       const int i = which ? s.i1[k] : s.i1p[k], j = which ? s.i2[k] : s.i2p[k];
       const double w1 = which ? (double)s.dx1[k] : (double)s.dx1p[k];
       const double w2 = which ? (double)s.dx2[k] : (double)s.dx2p[k];
-      double *r = (which ? rho_new : rho_prev) + sidx(g, i, j);
-      atomicAdd(r, q * (1.0 - w1) * (1.0 - w2));
-      atomicAdd(r + 1, q * w1 * (1.0 - w2));
-      atomicAdd(r + g.NX, q * (1.0 - w1) * w2);
-      atomicAdd(r + g.NX + 1, q * w1 * w2);
+      const double c00 = (1.0 - w1) * (1.0 - w2), c10 = w1 * (1.0 - w2);
+      const double c01 = (1.0 - w1) * w2, c11 = w1 * w2;
+      const int64_t o = sidx(g, i, j);
+      double *r = (which ? rho_new : rho_prev) + o, *ra = rho_abs + o;
+      atomicAdd(r, q * c00);
+      atomicAdd(r + 1, q * c10);
+      atomicAdd(r + g.NX, q * c01);
+      atomicAdd(r + g.NX + 1, q * c11);
+      atomicAdd(ra, qa * c00);
+      atomicAdd(ra + 1, qa * c10);
+      atomicAdd(ra + g.NX, qa * c01);
+      atomicAdd(ra + g.NX + 1, qa * c11);
     }
   }
 }
@@ -38,13 +47,14 @@ __device__ __forceinline__ void max_pos(double *p, double v) {
 }
 
 // out[0] = max |residual|, out[1] = max |drho/dt|, out[2] = max |residual| / (|J terms| +
-// |drho/dt|) over the nodes
+// |drho/dt|), out[3] = max rho_abs / dt over the nodes (the scale of the rounding)
 template <typename T>
 __global__ void __launch_bounds__(TPB_Q) k_continuity(GridP g, const T *J1, const T *J2,
                                                      const double *rho_prev,
-                                                     const double *rho_new, double *out) {
+                                                     const double *rho_new,
+                                                     const double *rho_abs, double *out) {
   const int ni = g.n_r + 3, nj = g.n_th + 1;  // i in [-1, n_r + 1], j in [0, n_th]
-  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
   const double idt = 1.0 / g.dt;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)ni * nj;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -58,16 +68,19 @@ __global__ void __launch_bounds__(TPB_Q) k_continuity(GridP g, const T *J1, cons
     m0 = fmax(m0, res);
     m1 = fmax(m1, fabs(dr));
     if (sc > 0.0) m2 = fmax(m2, res / sc);
+    m3 = fmax(m3, rho_abs[k] * idt);
   }
   for (int o = 16; o > 0; o >>= 1) {
     m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
     m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
     m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    m3 = fmax(m3, __shfl_xor_sync(0xffffffffu, m3, o));
   }
   if ((threadIdx.x & 31) == 0) {
     max_pos(out, m0);
     max_pos(out + 1, m1);
     max_pos(out + 2, m2);
+    max_pos(out + 3, m3);
   }
 }
 
@@ -75,33 +88,35 @@ __global__ void __launch_bounds__(TPB_Q) k_continuity(GridP g, const T *J1, cons
 
 template <typename T>
 cudaError_t launch_charge_rho(const GridP &g, SpeciesDevT<T> s, int64_t n_bound,
-                              double *rho_prev, double *rho_new, cudaStream_t st) {
+                              double *rho_prev, double *rho_new, double *rho_abs,
+                              cudaStream_t st) {
   if (n_bound <= 0) return cudaGetLastError();
   int64_t b = (n_bound + TPB_Q - 1) / TPB_Q;
   if (b > 152 * 32) b = 152 * 32;
-  k_rho<T><<<(int)b, TPB_Q, 0, st>>>(g, s, rho_prev, rho_new);
+  k_rho<T><<<(int)b, TPB_Q, 0, st>>>(g, s, rho_prev, rho_new, rho_abs);
   COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_continuity(const GridP &g, const T *J1, const T *J2, const double *rho_prev,
-                              const double *rho_new, double *out, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(out, 0, 3 * sizeof(double), st);
+                              const double *rho_new, const double *rho_abs, double *out,
+                              cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(double), st);
   if (e != cudaSuccess) return e;
   const int64_t nodes = (int64_t)(g.n_r + 3) * (g.n_th + 1);
   int64_t b = (nodes + TPB_Q - 1) / TPB_Q;
   if (b > 152 * 8) b = 152 * 8;
-  k_continuity<T><<<(int)b, TPB_Q, 0, st>>>(g, J1, J2, rho_prev, rho_new, out);
+  k_continuity<T><<<(int)b, TPB_Q, 0, st>>>(g, J1, J2, rho_prev, rho_new, rho_abs, out);
   COUNT_LAUNCH(1);
   return cudaGetLastError();
 }
 
 #define INSTANTIATE_CHARGE(T)                                                                  \
   template cudaError_t launch_charge_rho<T>(const GridP &, SpeciesDevT<T>, int64_t, double *,   \
-                                            double *, cudaStream_t);                            \
+                                            double *, double *, cudaStream_t);                  \
   template cudaError_t launch_continuity<T>(const GridP &, const T *, const T *,               \
-                                            const double *, const double *, double *,           \
-                                            cudaStream_t);
+                                            const double *, const double *, const double *,     \
+                                            double *, cudaStream_t);
 INSTANTIATE_CHARGE(double)
 INSTANTIATE_CHARGE(float)

@@ -312,10 +312,12 @@ cudaError_t launch_zero(T *p, int64_t n, cudaStream_t st);
 cudaError_t launch_push_tables(const GridP &g, const PushTables &tb, cudaStream_t st);
 template <typename T>
 cudaError_t launch_charge_rho(const GridP &g, SpeciesDevT<T> s, int64_t n_bound,
-                              double *rho_prev, double *rho_new, cudaStream_t st);
+                              double *rho_prev, double *rho_new, double *rho_abs,
+                              cudaStream_t st);
 template <typename T>
 cudaError_t launch_continuity(const GridP &g, const T *J1, const T *J2, const double *rho_prev,
-                              const double *rho_new, double *out, cudaStream_t st);
+                              const double *rho_new, const double *rho_abs, double *out,
+                              cudaStream_t st);
 cudaError_t launch_adjoint_forward(const GridP &g, const FieldPtrsT<double> &F, int64_t n,
                                    double qm, double scale, int n_steps, int every, int n_iter,
                                    const double *st0, double *out, double *ckpt,

@@ -85,3 +85,35 @@ def assert_particles(pg: dict, po: dict, rtol=RTOL, exact_order=True):
     err = np.abs(pg["phi"] - po["phi"]) / np.maximum(1.0, np.abs(po["phi"]))
     assert err.max(initial=0.0) <= rtol, ("phi", float(err.max()))
     assert np.array_equal(pg["w"], po["w"]) or np.allclose(pg["w"], po["w"], rtol=rtol, atol=0)
+
+
+def round_state_fp32(osim):
+    """Round the oracle's floating state (fields and particles) to FP32 values in place, so
+    that both sides of a mixed-precision comparison start from the same numbers."""
+    osim.F[:] = osim.F.astype(np.float32).astype(np.float64)
+    for sp in osim.species:
+        for k in ("dx1", "dx2", "u1", "u2", "u3", "phi", "w", "dx1p", "dx2p"):
+            sp.a[k][:] = sp.a[k].astype(np.float32).astype(np.float64)
+
+
+def particle_errors(pg, po):
+    """Max relative errors per quantity (positions relative to max(1, |x|), momentum
+    components relative to |u_c| + median |u_c|)."""
+    out = {}
+    assert len(pg["i1"]) == len(po["i1"])
+    assert np.array_equal(pg["tag"], po["tag"])
+    for a, b in (("i1", "dx1"), ("i2", "dx2")):
+        xg = pg[a].astype(np.float64) + pg[b].astype(np.float64)
+        xo = po[a].astype(np.float64) + po[b]
+        out[b] = float(np.max(np.abs(xg - xo) / np.maximum(1.0, np.abs(xo)), initial=0.0))
+    for c in ("u1", "u2", "u3"):
+        sc = np.median(np.abs(po[c])) if len(po[c]) else 1.0
+        out[c] = float(np.max(np.abs(pg[c] - po[c]) / (np.abs(po[c]) + sc + 1e-300), initial=0.0))
+    out["phi"] = float(np.max(np.abs(pg["phi"] - po["phi"]) / np.maximum(1.0, np.abs(po["phi"])),
+                              initial=0.0))
+    return out
+
+
+def plane_errors(Fg, Fo, planes):
+    return {k: float(np.abs(Fg[k] - Fo[k]).max() / max(np.abs(Fo[k]).max(), 1e-300))
+            for k in planes}

@@ -1,0 +1,124 @@
+"""Parity at the workloads' full sizes, in the launch configuration the bench times (a sort
+every 10 steps in 16 x 16 tiles, so the first step sorts; fused push + deposit).
+
+* wald512 (512^2, 16,777,216 particles): one full step on both sides, every particle and
+  every field plane compared, in FP64 (1e-12) and in mixed precision (1e-5 against the
+  FP64 oracle on FP32-rounded inputs).
+* wald2048 (2048^2, 134,217,728 particles): the GPU runs the full step; the oracle computes
+  what it can one by one: the predicted field B^n on the whole grid, and the push of a
+  random sample of particles, located after the GPU's sort by the oracle's own sort keys
+  (a stable argsort). The currents of all particles and the fields they drive are checked
+  by the discrete continuity equation (FP64 charge check).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+from parity import (RTOL, assert_particles, assert_planes, gpu_from_oracle, oracle_state,
+                    particle_errors, plane_errors, round_state_fp32)
+
+pytestmark = pytest.mark.gpu
+
+BENCH = dict(sort_every=10, tile_r=16, tile_theta=16)
+AFTER_ADVANCE = list(range(12)) + [15, 16, 17, 18, 19, 20]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def test_wald512_full_step_fp64(torch_cuda):
+    cfg = W.grid_config("wald512", **BENCH)
+    osim = oracle_state(cfg)
+    g = gpu_from_oracle(osim)
+    g.step(1)
+    osim.step(1, sort_every=10, tr=16, tt=16)
+    assert_planes(g.planes(), osim.F, planes=AFTER_ADVANCE, what="wald512 step")
+    for s in range(2):
+        assert_particles(g.get_particles(s), osim.species[s].view())
+
+
+def test_wald512_full_step_mixed(torch_cuda):
+    cfg = W.grid_config("wald512", **BENCH)
+    osim = oracle_state(cfg)
+    round_state_fp32(osim)
+    g = gpu_from_oracle(osim, precision="mixed")
+    g.step(1)
+    osim.step(1, sort_every=10, tr=16, tt=16)
+    for s in range(2):
+        e = particle_errors(g.get_particles(s), osim.species[s].view())
+        assert max(e.values()) <= 1e-5, e
+    pe = plane_errors(g.planes(), osim.F, AFTER_ADVANCE)
+    assert max(pe.values()) <= 1e-5, pe
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_wald2048_sampled(torch_cuda, precision):
+    from paper_2511_17701_gb300 import FIELD_WALD, Sim
+    from paper_2511_17701_gb300.binding import BN1
+    torch = torch_cuda
+    cfg = W.grid_config("wald2048", **BENCH, precision=precision)
+    pl = W.pair_plasma(cfg)
+    n = pl["pos"]["i1"].size
+    g = Sim(cfg, [n, n])
+    g.init_metric()
+    g.init_fields(FIELD_WALD, cfg["B0"])
+    for s in range(2):
+        g.load_particles(s, pl["pos"], pl["uhat"][s], pl["w0"], pl["qm"][s], pl["qc"][s],
+                         pl["density_power"])
+
+    # the oracle: its own time step, fields and predict on the whole grid; the GPU's predict
+    # (a function of the two stored field levels, which the step recomputes the same way)
+    osim = O.OracleSim(cfg)
+    assert abs(osim.dt - g.dt) <= 1e-14 * osim.dt
+    osim.init_fields(O.FIELD_WALD, cfg["B0"])
+    osim.predict()
+    g.predict()
+    # mixed: the FP32 Faraday update of B^3 divides a nearly cancelling curl of E by
+    # sqrt(h) ~ sin(theta); next to the axis it keeps ~ eps32 / sin(dtheta / 2) ~ 8e-5 at 2048
+    # cells in theta (the particle state is what the 1e-5 bound is for, checked below)
+    tol = RTOL if precision == "fp64" else 1e-4
+    for k in range(3):
+        got = g.plane(BN1 + k).cpu().numpy().astype(np.float64)
+        ref = osim.F[O.BN1 + k]
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), k
+    g.step(1)
+
+    # a random sample of particles, pushed one by one by the oracle
+    rng = np.random.default_rng(2048)
+    idx = np.sort(rng.choice(n, 4096, replace=False))
+    pos = {k: v[idx] for k, v in pl["pos"].items()}
+    for s in range(2):
+        osim.add_species(pos, pl["uhat"][s][:, idx], pl["w0"][idx], pl["qm"][s], pl["qc"][s],
+                         pl["density_power"])
+    if precision == "mixed":
+        round_state_fp32(osim)
+    for s in range(2):
+        osim.push(s)
+    # where the GPU's sort (at the start of the step) put them: all are alive, so their keys
+    # are the tile-major cell keys of the loaded positions
+    keys = O.sort_keys(cfg, 16, 16, pl["pos"]["i1"], pl["pos"]["i2"])
+    order = np.argsort(keys, kind="stable")
+    where = np.empty(n, dtype=np.int64)
+    where[order] = np.arange(n)
+    sel = torch.tensor(where[idx], device="cuda")
+    for s in range(2):
+        v = g.species_views(s)
+        pg = {k: v[k][sel].cpu().numpy() for k in v}
+        po = osim.species[s].view()
+        if precision == "fp64":
+            assert_particles(pg, po)
+        else:
+            e = particle_errors(pg, po)
+            assert max(e.values()) <= 1e-5, e
+
+    # the currents of all particles against the charge they moved, to the rounding of the
+    # charge sums (FP64) and of the FP32 currents (mixed)
+    res, drho, _, scale = g.charge_check(after_step=True)
+    assert drho > 0.0
+    assert res <= (1e-13 if precision == "fp64" else 1e-6) * scale

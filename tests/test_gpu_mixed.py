@@ -15,7 +15,8 @@ import pytest
 
 import workloads as W
 from oracle import oracle as O
-from parity import G, gpu_from_oracle, oracle_state
+from parity import (G, gpu_from_oracle, oracle_state, particle_errors, plane_errors,
+                    round_state_fp32)
 
 pytestmark = pytest.mark.gpu
 
@@ -34,41 +35,10 @@ def torch_cuda():
     return torch
 
 
-def round_state_fp32(osim):
-    """Round the oracle's floating state (fields and particles) to FP32 values in place."""
-    osim.F[:] = osim.F.astype(np.float32).astype(np.float64)
-    for sp in osim.species:
-        for k in ("dx1", "dx2", "u1", "u2", "u3", "phi", "w", "dx1p", "dx2p"):
-            sp.a[k][:] = sp.a[k].astype(np.float32).astype(np.float64)
-
-
 def mixed_state(cfg):
     osim = oracle_state(cfg)
     round_state_fp32(osim)
     return osim
-
-
-def particle_errors(pg, po):
-    """Max relative errors per quantity (positions relative to max(1, |x|), momentum
-    components relative to |u_c| + median |u_c|)."""
-    out = {}
-    assert len(pg["i1"]) == len(po["i1"])
-    assert np.array_equal(pg["tag"], po["tag"])
-    for a, b in (("i1", "dx1"), ("i2", "dx2")):
-        xg = pg[a].astype(np.float64) + pg[b].astype(np.float64)
-        xo = po[a].astype(np.float64) + po[b]
-        out[b] = float(np.max(np.abs(xg - xo) / np.maximum(1.0, np.abs(xo)), initial=0.0))
-    for c in ("u1", "u2", "u3"):
-        sc = np.median(np.abs(po[c])) if len(po[c]) else 1.0
-        out[c] = float(np.max(np.abs(pg[c] - po[c]) / (np.abs(po[c]) + sc + 1e-300), initial=0.0))
-    out["phi"] = float(np.max(np.abs(pg["phi"] - po["phi"]) / np.maximum(1.0, np.abs(po["phi"])),
-                              initial=0.0))
-    return out
-
-
-def plane_errors(Fg, Fo, planes):
-    return {k: float(np.abs(Fg[k] - Fo[k]).max() / max(np.abs(Fo[k]).max(), 1e-300))
-            for k in planes}
 
 
 @pytest.mark.parametrize("cfg", [BASE, BIG])

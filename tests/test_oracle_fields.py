@@ -124,3 +124,37 @@ def test_wald_vacuum_stays_stationary_second_order():
     assert np.all(ratio > 2.4), ratio
     assert ratio[0] > 3.5 and ratio[3] > 3.5, ratio  # B^r and D^r: clean second order
     assert np.all(errs[64] < 0.05), errs[64]
+
+
+def test_initial_B3_equals_the_plain_curl_in_extended_precision():
+    """B^3 = -(A_1(j+1) - A_1(j)) / sqrt(h) at (i+1/2, j+1/2): the oracle takes the cell
+    difference of the Wald A_1 in product form; here the plain difference of the potential's
+    closed form (Eq. Wald, A_r = (B0 a / 2)(2 z - (1 + z) sin^2), A_1 = f A_r) is evaluated in
+    extended precision, where its cancellation next to the axes costs nothing at this
+    resolution. Rows at both axes and in the middle, 2048 cells in theta."""
+    cfg = W.grid_config("wald64", n_r=16, n_theta=2048, r_max=200.0, r_absorb=1e300)
+    osim = O.OracleSim(cfg)
+    osim.init_fields(O.FIELD_WALD, 1.0)
+    L = np.longdouble
+    a, M, B0 = L(cfg["a"]), L(1), L(1)
+    dxi = L(math.log(cfg["r_max"] / cfg["r_min"]) / cfg["n_r"])
+    dth = L(np.pi) / L(cfg["n_theta"])   # np.pi rounded to double, as the oracle's pi
+    nt = cfg["n_theta"]
+
+    def A1(x1, j):
+        r = L(cfg["r_min"]) * np.exp(L(x1) * dxi)
+        s, c = np.sin(L(j) * dth), np.cos(L(j) * dth)
+        z = 2 * M * r / (r * r + a * a * c * c)
+        return dxi * r * B0 * a / 2 * (2 * z - (1 + z) * s * s)
+
+    rows = list(range(0, 6)) + list(range(nt // 2 - 3, nt // 2 + 3)) + list(range(nt - 6, nt))
+    worst = 0.0
+    for i in range(1, cfg["n_r"], 3):  # i <= 0 is the horizon layer (a copy of cell 1)
+        for j in rows:
+            m = O.metric_point(cfg, i + 0.5, j + 0.5)
+            ref = float(-(A1(i + 0.5, j + 1) - A1(i + 0.5, j))) / m["sqrt_h"]
+            got = osim.F[O.B3][j + G, i + G]
+            worst = max(worst, abs(got - ref) / abs(ref))
+    # next to theta = pi the rounding of the argument (2j + 1) dtheta ~ pi leaves ~1e-13 of
+    # sin(theta_a + theta_b); the plain double difference is off by ~5e-11 there
+    assert worst < 5e-13, worst

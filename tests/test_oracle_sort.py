@@ -43,3 +43,19 @@ def test_sort_is_stable_and_drops_dead():
     assert np.array_equal(v["dx1"], want[:alive].astype(np.float64))
     assert np.all(v["tag"] == 1)
     assert np.all(np.diff(keys[want[:alive]].astype(np.int64)) >= 0)
+
+
+def test_vectorised_keys_equal_the_c_key():
+    """oracle.sort_keys (numpy, for the full-size tests) against ora_sort_key element by
+    element, on ragged tiles with dead and leaving particles."""
+    cfg = CFG
+    rng = np.random.default_rng(17)
+    n = 4000
+    i1 = rng.integers(0, CFG["n_r"], n)  # cells of the domain (live particles have no other)
+    i2 = rng.integers(0, CFG["n_theta"], n)
+    tag = rng.choice([0, 1, 1, 2], n)
+    for tr, tt in ((16, 16), (5, 7), (1, 1)):
+        got = O.sort_keys(cfg, tr, tt, i1, i2, tag)
+        want = np.array([O.sort_key(cfg, tr, tt, int(a), int(b), int(c))
+                         for a, b, c in zip(i1, i2, tag)], dtype=np.uint32)
+        assert np.array_equal(got, want), (tr, tt)
