@@ -45,10 +45,12 @@ FP64_BYTES_PER_PARTICLE_STEP = 65 + 81
 # written.
 MIXED_BYTES_PER_PARTICLE_STEP = 37 + 48
 # FP64 pipe operations (DFMA + DMUL + DADD thread instructions) per particle-step of
-# k_push<deposit> on the wald512 workload, counted by ncu (476 + 548 + 120); as flops
-# (2 DFMA + DMUL + DADD) 1620. The FP64 pipe issues 2 such operations per clock per SM.
-FP64_PIPE_OPS_PER_PARTICLE_STEP = 1144
-FP64_FLOP_PER_PARTICLE_STEP = 1620
+# k_push<deposit> on the wald512 workload, counted by ncu, and as flops (2 DFMA + DMUL +
+# DADD): with the implicit iterations refined from an FP32 predictor (iter_tol > 0):
+# 363 + 446 + 104 = 914 (1277 flop); stopped at an exact repeat (iter_tol = 0): 476 + 548 +
+# 120 = 1144 (1620 flop). The FP64 pipe issues 2 such operations per clock per SM.
+FP64_PIPE_OPS_PER_PARTICLE_STEP = {True: 914, False: 1144}
+FP64_FLOP_PER_PARTICLE_STEP = {True: 1277, False: 1620}
 SMS, MAX_SM_GHZ = 152, 2.07
 FP64_PIPE_PEAK_GOPS = 2 * SMS * MAX_SM_GHZ  # 629 G operations/s
 # Warp instructions issued per particle by k_push32<deposit> on the wald512 workload (ncu:
@@ -242,7 +244,7 @@ def measure(args, precision, ws, rank, local):
     device = torch.device("cuda", local)
     cfg = W.grid_config(args.workload, sort_every=args.sort_every, tile_r=args.tile,
                         tile_theta=args.tile, precision=precision,
-                        tiled_push=1 if args.tiled_push else 0)
+                        tiled_push=1 if args.tiled_push else 0, iter_tol=args.iter_tol)
     if args.ppc:
         cfg["ppc"] = args.ppc
     pl = W.pair_plasma(cfg, seed=cfg["seed"] + 1000 * rank)
@@ -289,12 +291,13 @@ def measure(args, precision, ws, rank, local):
     bpp = FP64_BYTES_PER_PARTICLE_STEP if precision == "fp64" else MIXED_BYTES_PER_PARTICLE_STEP
     hbm_achieved = parts_per_launch * bpp / (kernel_ms * 1e-3) / 1e9
     if precision == "fp64":
-        ops = parts_per_launch * FP64_PIPE_OPS_PER_PARTICLE_STEP / (kernel_ms * 1e-3) / 1e9
+        refined = args.iter_tol > 0
+        ops = parts_per_launch * FP64_PIPE_OPS_PER_PARTICLE_STEP[refined] / (kernel_ms * 1e-3) / 1e9
         roofline = {"bound": "alu", "achieved": ops, "peak": FP64_PIPE_PEAK_GOPS,
                     "unit": "G FP64-pipe op/s", "frac": ops / FP64_PIPE_PEAK_GOPS,
                     "traffic": None,
                     "peak_source": "nominal: 2 FP64 operations/clk/SM x 152 SMs x 2.07 GHz",
-                    "tflops": parts_per_launch * FP64_FLOP_PER_PARTICLE_STEP
+                    "tflops": parts_per_launch * FP64_FLOP_PER_PARTICLE_STEP[refined]
                     / (kernel_ms * 1e-3) / 1e12,
                     "kernel": "k_push<deposit> (fused FP64 push + deposit)"}
     else:
@@ -393,6 +396,7 @@ def run_gpu(args, ws, rank, local):
                 "data": "synthetic (seeded workload generator)",
                 "config": {"workload": main["workload"],
                            "sort_every": args.sort_every, "tile": args.tile,
+                           "iter_tol": args.iter_tol,
                            "l2": "inputs larger than L2: particle state %.2f GB" % (
                                main["particles"] * (89 if precisions[0] == "fp64" else 49) / 1e9),
                            "parallelism": "replica per GPU" if ws > 1 else "1 GPU"},
@@ -539,6 +543,9 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--adjoint-ckpt", type=int, default=100)
     ap.add_argument("--adjoint-fd-sample", type=int, default=256)
+    ap.add_argument("--iter-tol", type=float, default=1e-12,
+                    help="implicit pushes: FP64 iterations from an FP32 predictor to this "
+                         "tolerance (0: exact-repeat stop, bit-identical to n_iter iterations)")
     ap.add_argument("--tiled-push", action="store_true",
                     help="mixed path: the shared-memory tiled FP32 kernel instead of the default "
                          "one thread per particle")

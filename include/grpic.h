@@ -115,6 +115,13 @@ typedef struct {
                            the currents accumulated there; 0 (default) = one thread per
                            particle over the whole species with gathers through L1/L2, which
                            measures faster on GB300 for this pusher                            */
+  double iter_tol;      /* the implicit pushes (steps 6 and 10 of Sec. 3.1): 0 (default) = the
+                           stop rule of full_iterations; > 0 = an FP32 predictor iterates each
+                           to an exact FP32 repeat, then FP64 iterations start from it and stop
+                           once the update is at most iter_tol max(1, |value|) (at most n_iter
+                           of them): the FP64 fixed point to about rho iter_tol (rho < 1 the
+                           contraction of the iteration), in fewer FP64 operations. Must be
+                           below 1e-6                                                          */
 } grpic_config;
 
 /* Pointers to one species' particle arrays (SoA, length >= n). Positions are a cell

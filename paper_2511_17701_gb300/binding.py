@@ -48,7 +48,7 @@ class Config(C.Structure):
                 ("n_species", C.c_int), ("capacity", C.c_int64 * MAX_SPECIES),
                 ("sort_every", C.c_int), ("tile_r", C.c_int), ("tile_theta", C.c_int),
                 ("precision", C.c_int), ("full_iterations", C.c_int),
-                ("fp64_guard_cells", C.c_int), ("tiled_push", C.c_int)]
+                ("fp64_guard_cells", C.c_int), ("tiled_push", C.c_int), ("iter_tol", C.c_double)]
 
 
 _VP = C.c_void_p
@@ -154,6 +154,7 @@ def make_config(cfg: dict, capacities) -> Config:
     c.full_iterations = int(cfg.get("full_iterations", 0))
     c.fp64_guard_cells = int(cfg.get("fp64_guard_cells", 0))
     c.tiled_push = int(cfg.get("tiled_push", 0))
+    c.iter_tol = float(cfg.get("iter_tol", 0.0))
     return c
 
 

@@ -296,6 +296,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   if (c.tile_r < 1 || c.tile_theta < 1 || c.sort_every < 0) return GRPIC_EINVAL;
   if (!(c.dt > 0.0) && !(c.cfl > 0.0 && c.cfl <= 1.0)) return GRPIC_EINVAL;
   if (c.fp64_guard_cells < 0 || 2 * c.fp64_guard_cells >= c.n_theta) return GRPIC_EINVAL;
+  if (!(c.iter_tol >= 0.0 && c.iter_tol < 1e-6)) return GRPIC_EINVAL;
   for (int s = 0; s < c.n_species; ++s)
     if (c.capacity[s] < 0 || c.capacity[s] >= ((int64_t)1 << 31)) return GRPIC_EINVAL;
 
@@ -310,6 +311,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   g.NX = c.n_r + 2 * G_ + 1; g.NY = c.n_theta + 2 * G_ + 1;
   g.n_iter = c.n_iter; g.n_f = c.n_filter;
   g.stop_on_repeat = c.full_iterations ? 0 : 1;
+  g.iter_tol = c.iter_tol;
   g.r_min = c.r_min; g.r_max = c.r_max;
   g.dxi = log(c.r_max / c.r_min) / c.n_r;
   g.dth = GRPIC_PI / c.n_theta;

@@ -17,6 +17,8 @@
 struct GridP {
   int n_r, n_th, NX, NY, n_iter, n_f;
   int stop_on_repeat;  // stop an implicit iteration once its iterate repeats exactly
+  double iter_tol;     // > 0: FP64 implicit iterations start from an FP32 predictor and stop
+                       // once the update is at most iter_tol max(1, |value|)
   double r_min, r_max, dxi, dth, a, M, dt, small_angle, r_absorb, absorb_coef;
   double ig2;  // 1 / dth^2
   // FP32 copies for the mixed path (read from the kernel parameters, no conversions)

@@ -154,12 +154,168 @@ __device__ __forceinline__ void deposit64(const GridP &g, const FieldPtrsT<T> &F
   add_(J3 + k + NX + 1, qv * w1 * w2);
 }
 
+// Refined form of the two implicit substeps (iter_tol > 0): an FP32 predictor iterates the
+// same map to an exact FP32 repeat (metric from the FP32 cell tables), then FP64 iterations
+// start from it and stop once the update is at most iter_tol max(1, |value|); the result is
+// the FP64 fixed point to about rho iter_tol, rho the contraction of the map, whatever the
+// start (mixed-precision iterative refinement: the predictor only saves FP64 iterations).
+__device__ __forceinline__ bool converged(double n, double t, double tol) {
+  return fabs(n - t) <= tol * fmax(1.0, fabs(n));
+}
+// Whether the method's n_iter iterations from its start come within a tenth of tol of the
+// fixed point, so that the refined result stands for the method's n_iter result: d1 is the
+// method's first update (from the FP32 predictor's first step), rho = D2 / D1 the
+// contraction measured by the first two FP64 updates, the remainder d1 rho^n_iter.
+__device__ __forceinline__ bool method_converges(double d1, double D1, double D2, int n_iter,
+                                                 double tol, double scale) {
+  if (!(D1 > 1e-14 * scale)) return true;  // the predictor already sat on the fixed point
+  const float rho = (float)(D2 / D1);  // an estimate: FP32 (and the XU pipe) is enough
+  if (!(rho < 0.5f)) return false;
+  if (!(rho > 0.0f)) return true;
+  return (float)d1 * exp2f((float)n_iter * log2f(rho)) <= (float)(0.1 * tol * scale);
+}
+
+__device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTables &tb, int i1,
+                                                 int i2, float o1, float o2,
+                                                 const Local<double> &L, double u[3]) {
+  float r, sn, cs;
+  rsc32(g, tb, i1, i2, o1, o2, r, sn, cs);
+  Local<float> Lf;
+  local_full(g, r, sn, cs, Lf);
+  const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
+  const GeoMap<float> mf(g, Lf, uf);
+  float p0 = uf[0], p1 = uf[1], d1 = 0.0f;
+  for (int it = 0; it < g.n_iter; ++it) {
+    float n0, n1;
+    mf.apply(p0, p1, n0, n1);
+    if (it == 0) d1 = fmaxf(fabsf(n0 - p0), fabsf(n1 - p1));
+    const bool fixed = n0 == p0 && n1 == p1;
+    p0 = n0;
+    p1 = n1;
+    if (fixed) break;
+  }
+  const GeoMap<double> m(g, L, u);
+  double t0 = u[0], t1 = u[1];
+  if (isfinite(p0) && isfinite(p1)) {
+    t0 = p0;
+    t1 = p1;
+  }
+  double D1 = 0.0, D2 = 0.0;
+  for (int it = 0; it < g.n_iter; ++it) {
+    double n0, n1;
+    m.apply(t0, t1, n0, n1);
+    const double d = fmax(fabs(n0 - t0), fabs(n1 - t1));
+    if (it == 0) D1 = d;
+    else if (it == 1) D2 = d;
+    const bool conv = converged(n0, t0, g.iter_tol) && converged(n1, t1, g.iter_tol);
+    t0 = n0;
+    t1 = n1;
+    if (conv && it >= 1) break;
+  }
+  const double scale = fmax(1.0, fmax(fabs(t0), fabs(t1)));
+  if (!method_converges(d1, D1, D2, g.n_iter, g.iter_tol, scale)) {
+    geodesic_momentum(g, L, u);  // the method's n_iter iterations from u
+    return;
+  }
+  u[0] = t0;
+  u[1] = t1;
+}
+
+// The coordinate substep, Eq. (discretized-geodesic-x), as the method iterates it: metric at
+// x_bar = (x^n + x~)/2, the first iterate x^n itself (metric L.G), n_iter iterations or
+// until an exact repeat. t1, t2: the new offsets from cell (i1, i2).
+__device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const Local<double> &L,
+                                            int i1, int i2, double dx1, double dx2,
+                                            const double u[3], double &t1, double &t2) {
+  const double uu0 = 2.0 * u[0] * u[2];
+  t1 = dx1;
+  t2 = dx2;
+  for (int it = 0; it < g.n_iter; ++it) {
+    Geo<double> o;
+    if (it == 0) {
+      o = L.G;
+    } else {
+      double r, s_, c_;
+      // x_bar = i + (dx + x~)/2, rounded in that order
+      local_rsc(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
+                __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), r, s_, c_);
+      geo_from_rsc(g, r, s_, c_, o);
+    }
+    const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
+                     fma(o.H33 * u[2], u[2], fma(o.H13, uu0, 1.0))));
+    const double ag = rsqrt(o.opz * q);  // alpha / gamma
+    const double n1 = fma(g.dt, fma(ag, fma(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
+    const double n2 = fma(g.dt, ag * o.H22 * u[1], dx2);
+    const bool fixed = (n1 == t1) && (n2 == t2);  // exact repeat: later iterations are no-ops
+    t1 = n1;
+    t2 = n2;
+    if (fixed && g.stop_on_repeat) break;
+  }
+}
+
+// the coordinate substep's refined iterations; t1, t2: the new offsets from cell (i1, i2)
+__device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &tb, const Base &b,
+                                              const Local<double> &L, int i1, int i2,
+                                              double dx1, double dx2, const double u[3],
+                                              double &t1, double &t2) {
+  const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
+  const float a1 = (float)dx1, a2 = (float)dx2, dt = g.f_dt;
+  const float uuf = 2.0f * uf[0] * uf[2];
+  float p1 = a1, p2 = a2, d1 = 0.0f;
+  for (int it = 0; it < g.n_iter; ++it) {
+    float r, s_, c_;
+    rsc32(g, tb, i1, i2, 0.5f * (a1 + p1), 0.5f * (a2 + p2), r, s_, c_);
+    Geo<float> o;
+    geo_from_rsc(g, r, s_, c_, o);
+    const float q = fmaf(o.H11 * uf[0], uf[0], fmaf(o.H22 * uf[1], uf[1],
+                    fmaf(o.H33 * uf[2], uf[2], fmaf(o.H13, uuf, 1.0f))));
+    const float ag = rsqrtf(o.opz * q);
+    const float n1 = fmaf(dt, fmaf(ag, fmaf(o.H11, uf[0], o.H13 * uf[2]), -o.beta1), a1);
+    const float n2 = fmaf(dt, ag * o.H22 * uf[1], a2);
+    if (it == 0) d1 = fmaxf(fabsf(n1 - p1), fabsf(n2 - p2));
+    const bool fixed = n1 == p1 && n2 == p2;
+    p1 = n1;
+    p2 = n2;
+    if (fixed) break;
+  }
+  t1 = dx1;
+  t2 = dx2;
+  if (isfinite(p1) && isfinite(p2) && fabsf(p1) < 4.0f && fabsf(p2) < 4.0f) {
+    t1 = p1;
+    t2 = p2;
+  }
+  const double uu0 = 2.0 * u[0] * u[2];
+  double D1 = 0.0, D2 = 0.0;
+  for (int it = 0; it < g.n_iter; ++it) {
+    double r, s_, c_;
+    local_rsc(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
+              __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), r, s_, c_);
+    Geo<double> o;
+    geo_from_rsc(g, r, s_, c_, o);
+    const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
+                     fma(o.H33 * u[2], u[2], fma(o.H13, uu0, 1.0))));
+    const double ag = rsqrt(o.opz * q);
+    const double n1 = fma(g.dt, fma(ag, fma(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
+    const double n2 = fma(g.dt, ag * o.H22 * u[1], dx2);
+    const double d = fmax(fabs(n1 - t1), fabs(n2 - t2));
+    if (it == 0) D1 = d;
+    else if (it == 1) D2 = d;
+    const bool conv = converged(n1, t1, g.iter_tol) && converged(n2, t2, g.iter_tol);
+    t1 = n1;
+    t2 = n2;
+    if (conv && it >= 1) break;
+  }
+  const double scale = fmax(1.0, fmax(fabs(t1), fabs(t2)));
+  if (!method_converges(d1, D1, D2, g.n_iter, g.iter_tol, scale))
+    coord_exact(g, b, L, i1, i2, dx1, dx2, u, t1, t2);  // the method's n_iter iterations
+}
+
 // One particle in FP64: steps 2-11 of Sec. 3.1, the boundaries of Sec. 3.3.3, and
 // (DEPOSIT) the deposit of its move. T is the storage type of state and fields.
 template <typename T, bool DEPOSIT>
 __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
-                                       const SpeciesDevT<T> &s, int64_t k,
-                                       unsigned long long *diag) {
+                                       const PushTables &tb, const SpeciesDevT<T> &s,
+                                       int64_t k, unsigned long long *diag) {
   const int i1 = s.i1[k], i2 = s.i2[k];
   const double dx1 = (double)s.dx1[k], dx2 = (double)s.dx2[k];
   const double x1 = i1 + dx1, x2 = i2 + dx2;
@@ -184,35 +340,19 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   const double hq = s.qm * L.alpha * 0.5 * g.dt;
   boris(uh, Dh, Bh, hq);       // step 4
   hat_cov(L, uh, u);           // step 5
-  geodesic_momentum(g, L, u);  // step 6
+  // the refined iterations keep two cell rows away from the axes: there the coordinate map
+  // (metric terms ~ 1/sin^2(theta)) has more than one fixed point within reach, and the
+  // method's answer is the one its iteration from x^n finds
+  const bool refine = g.iter_tol > 0.0 && i2 >= 2 && i2 < g.n_th - 2;
+  if (refine) geodesic_refined(g, tb, i1, i2, (float)dx1, (float)dx2, L, u);
+  else geodesic_momentum(g, L, u);  // step 6
   cov_hat(L, u, uh);           // step 7
   boris(uh, Dh, Bh, hq);       // step 8
   hat_cov(L, uh, u);           // step 9
-  // step 10: implicit coordinate push, Eq. (discretized-geodesic-x), metric at
-  // x_bar = (x^n + x~)/2; the first iterate is x^n itself
-  const double uu0 = 2.0 * u[0] * u[2];
+  // step 10: implicit coordinate push, Eq. (discretized-geodesic-x)
   double t1 = dx1, t2 = dx2;
-  for (int it = 0; it < g.n_iter; ++it) {
-    Geo<double> o;
-    if (it == 0) {
-      o = L.G;
-    } else {
-      double r, s_, c_;
-      // x_bar = i + (dx + x~)/2, rounded in that order
-      local_rsc(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
-                __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), r, s_, c_);
-      geo_from_rsc(g, r, s_, c_, o);
-    }
-    const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
-                     fma(o.H33 * u[2], u[2], fma(o.H13, uu0, 1.0))));
-    const double ag = rsqrt(o.opz * q);  // alpha / gamma
-    const double n1 = fma(g.dt, fma(ag, fma(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
-    const double n2 = fma(g.dt, ag * o.H22 * u[1], dx2);
-    const bool fixed = (n1 == t1) && (n2 == t2);  // exact repeat: later iterations are no-ops
-    t1 = n1;
-    t2 = n2;
-    if (fixed && g.stop_on_repeat) break;
-  }
+  if (refine) coord_refined(g, tb, b, L, i1, i2, dx1, dx2, u, t1, t2);
+  else coord_exact(g, b, L, i1, i2, dx1, dx2, u, t1, t2);
   if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(t1) && isfinite(t2) &&
         fabs(t1) < 1e6 && fabs(t2) < 1e6)) {
     s.tag[k] = 0;
@@ -248,27 +388,6 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
 // of the offset from the cell corner, so FP32 keeps its relative accuracy at any cell
 // index and next to theta = pi.
 // =================================================================================
-// r at x1 = i + o1 and sin/cos of theta at x2 = j + o2 (offsets from the corner of cell i, j)
-__device__ __forceinline__ void rsc32(const GridP &g, const PushTables &tb, int i, int j,
-                                      float o1, float o2, float &r, float &s, float &c) {
-  const float e = o1 * g.f_dxi;  // |e| <= 2 dxi
-  float p = 1.0f / 720.0f;
-  p = fmaf(p, e, 1.0f / 120.0f);
-  p = fmaf(p, e, 1.0f / 24.0f);
-  p = fmaf(p, e, 1.0f / 6.0f);
-  p = fmaf(p, e, 0.5f);
-  p = fmaf(p, e, 1.0f);
-  r = __ldg(tb.r + i + G_) * fmaf(p, e, 1.0f);
-  const float d = o2 * g.f_dth;  // |d| <= 2 dtheta
-  const float q = d * d;
-  const float se = fmaf(fmaf(fmaf(-1.0f / 5040.0f, q, 1.0f / 120.0f), q, -1.0f / 6.0f) * q, d, d);
-  const float ce = fmaf(fmaf(fmaf(fmaf(1.0f / 40320.0f, q, -1.0f / 720.0f), q, 1.0f / 24.0f), q,
-                             -0.5f), q, 1.0f);
-  const float s0 = __ldg(tb.s + j + G_), c0 = __ldg(tb.c + j + G_);
-  s = fmaf(s0, ce, c0 * se);
-  c = fmaf(c0, ce, -s0 * se);
-}
-
 // The guard-zone form of rsc32: r, sin and cos in FP64 from the FP64 corner tables, with
 // theta clamped to [small_angle, pi - small_angle] as in the FP64 routine.
 __device__ __forceinline__ void rsc64(const GridP &g, const PushTables &tb, int i, int j,
@@ -636,7 +755,7 @@ __device__ __forceinline__ int guard_zone(const PushTables &tb, const GridP &g, 
 
 // FP64 path: one thread per particle, step 1 (previous location) then the FP64 routine.
 template <bool DEPOSIT>
-__global__ void __launch_bounds__(TPB) k_push(GridP g, FieldPtrsT<double> F,
+__global__ void __launch_bounds__(TPB) k_push(GridP g, FieldPtrsT<double> F, PushTables tb,
                                               SpeciesDevT<double> s, unsigned long long *diag) {
   const int64_t n = *s.n;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -648,7 +767,7 @@ __global__ void __launch_bounds__(TPB) k_push(GridP g, FieldPtrsT<double> F,
       if (tag != 0) s.tag[k] = 0;
       continue;
     }
-    push64<double, DEPOSIT>(g, F, s, k, diag);
+    push64<double, DEPOSIT>(g, F, tb, s, k, diag);
   }
 }
 
@@ -797,14 +916,14 @@ __global__ void __launch_bounds__(TPB) k_push_guard(GridP g, FieldPtrsT<float> F
 
 template <bool DEPOSIT>
 __global__ void __launch_bounds__(TPB) k_push_axis(GridP g, FieldPtrsT<float> F,
-                                                   SpeciesDevT<float> s, GuardList gl,
-                                                   unsigned long long *diag) {
+                                                   SpeciesDevT<float> s, PushTables tb,
+                                                   GuardList gl, unsigned long long *diag) {
   const int64_t n = (int64_t)gl.count[1];
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = gl.idx[gl.cap - 1 - t];
     s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
-    push64<float, DEPOSIT>(g, F, s, k, diag);
+    push64<float, DEPOSIT>(g, F, tb, s, k, diag);
   }
 }
 
@@ -954,8 +1073,8 @@ cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s
   }
   if constexpr (sizeof(T) == 8) {
     if (ps.t0) cudaEventRecord(ps.t0, ps.main);
-    if (deposit) k_push<true><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, s, diag);
-    else k_push<false><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, s, diag);
+    if (deposit) k_push<true><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, tb, s, diag);
+    else k_push<false><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, tb, s, diag);
     if (ps.t1) cudaEventRecord(ps.t1, ps.main);
     COUNT_LAUNCH(1);
   } else {
@@ -969,10 +1088,10 @@ cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s
     // sub-partition's FP64 unit and leave the registers to the concurrent FP32 kernel
     if (deposit) {
       k_push_guard<true><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
-      k_push_axis<true><<<152 * 4, 32, 0, ps.side>>>(g, F, s, gl, diag);
+      k_push_axis<true><<<152 * 4, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
     } else {
       k_push_guard<false><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
-      k_push_axis<false><<<152 * 4, 32, 0, ps.side>>>(g, F, s, gl, diag);
+      k_push_axis<false><<<152 * 4, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
     }
     // the tiled kernel needs the tile ranges of a sort and a window that fits in shared memory
     const size_t smem = tiled_smem_bytes(ti);

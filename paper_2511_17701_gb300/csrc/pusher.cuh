@@ -216,4 +216,28 @@ __device__ __forceinline__ void geodesic_momentum(const GridP &g, const Local<R>
   u[1] = t1;
 }
 
+// FP32 r, sin(theta), cos(theta) from FP64-computed per-cell tables and short Taylor series of
+// the offset from the cell corner (mixed path; and the FP32 predictor of the FP64 path's
+// refined implicit iterations).
+// r at x1 = i + o1 and sin/cos of theta at x2 = j + o2 (offsets from the corner of cell i, j)
+__device__ __forceinline__ void rsc32(const GridP &g, const PushTables &tb, int i, int j,
+                                      float o1, float o2, float &r, float &s, float &c) {
+  const float e = o1 * g.f_dxi;  // |e| <= 2 dxi
+  float p = 1.0f / 720.0f;
+  p = fmaf(p, e, 1.0f / 120.0f);
+  p = fmaf(p, e, 1.0f / 24.0f);
+  p = fmaf(p, e, 1.0f / 6.0f);
+  p = fmaf(p, e, 0.5f);
+  p = fmaf(p, e, 1.0f);
+  r = __ldg(tb.r + i + G_) * fmaf(p, e, 1.0f);
+  const float d = o2 * g.f_dth;  // |d| <= 2 dtheta
+  const float q = d * d;
+  const float se = fmaf(fmaf(fmaf(-1.0f / 5040.0f, q, 1.0f / 120.0f), q, -1.0f / 6.0f) * q, d, d);
+  const float ce = fmaf(fmaf(fmaf(fmaf(1.0f / 40320.0f, q, -1.0f / 720.0f), q, 1.0f / 24.0f), q,
+                             -0.5f), q, 1.0f);
+  const float s0 = __ldg(tb.s + j + G_), c0 = __ldg(tb.c + j + G_);
+  s = fmaf(s0, ce, c0 * se);
+  c = fmaf(c0, ce, -s0 * se);
+}
+
 }  // namespace

@@ -251,3 +251,62 @@ def test_stop_on_exact_repeat_is_bit_identical(torch_cuda, cfg):
         p1, p2 = g1.get_particles(s), g2.get_particles(s)
         for k in p1:
             assert np.array_equal(p1[k], p2[k]), k
+
+
+REFINED = 1e-12  # iter_tol of the refined implicit iterations (the bench's setting)
+
+
+@pytest.mark.parametrize("cfg", [BASE, RAGGED, FLAT])
+def test_refined_iterations_push(torch_cuda, cfg):
+    """FP32 predictor + FP64 iterations to iter_tol: the same FP64 fixed point as the oracle's
+    n_iter iterations, within the per-step parity bound."""
+    osim = oracle_state(cfg, cells=None if cfg is BASE else odd_cells(cfg))
+    osim.predict()
+    g = gpu_from_oracle(osim, iter_tol=REFINED)
+    for s in range(2):
+        g.push(s)
+        osim.push(s)
+    for s in range(2):
+        assert_particles(g.get_particles(s), osim.species[s].view())
+
+
+def test_refined_iterations_full_step_and_trajectory(torch_cuda):
+    cfg = dict(BASE, sort_every=1, tile_r=8, tile_theta=8)
+    osim = oracle_state(cfg)
+    g = gpu_from_oracle(osim, iter_tol=REFINED)
+    g.step(1)
+    osim.step(1, sort_every=1, tr=8, tt=8)
+    assert_planes(g.planes(), osim.F, planes=AFTER_ADVANCE, what="refined step")
+    for s in range(2):
+        assert_particles(g.get_particles(s), osim.species[s].view())
+    g.step(9)
+    osim.step(9, sort_every=1, tr=8, tt=8)
+    assert_planes(g.planes(), osim.F, planes=range(12), rtol=1e-9, what="refined 10 steps")
+    for s in range(2):
+        assert_particles(g.get_particles(s), osim.species[s].view(), rtol=1e-9)
+
+
+def test_refined_iterations_edge_particles(torch_cuda):
+    """Axis reflections, horizon and outer removals with the refined iterations."""
+    cfg = BASE
+    osim = O.OracleSim(cfg)
+    osim.init_fields(O.FIELD_WALD, 1.0)
+    n = 4000
+    rng = np.random.default_rng(19)
+    nt = cfg["n_theta"]
+    x2 = np.concatenate([rng.uniform(0.0, 0.3, n // 4), rng.uniform(nt - 0.3, nt, n // 4),
+                         rng.uniform(0.0, nt, n // 2)])
+    x1 = np.concatenate([rng.uniform(1.0, 60.0, n // 2), rng.uniform(0.0, 0.4, n // 4),
+                         rng.uniform(63.6, 64.0, n // 4)])
+    pos = {"i1": np.floor(x1).astype(np.int32), "i2": np.floor(x2).astype(np.int32)}
+    pos["dx1"], pos["dx2"] = x1 - pos["i1"], x2 - pos["i2"]
+    uh = W.maxwell_juttner(rng, n, 3.0)
+    qm, qc = W.species_coefficients(-1.0)
+    osim.add_species(pos, uh, np.full(n, 0.1), qm, qc)
+    osim.predict()
+    g = gpu_from_oracle(osim, iter_tol=REFINED)
+    for _ in range(3):
+        g.set_particles(0, osim.species[0].view(), qm, qc)
+        g.push(0)
+        osim.push(0)
+        assert_particles(g.get_particles(0), osim.species[0].view())
