@@ -102,8 +102,10 @@ __device__ __forceinline__ double interp64(const T *__restrict__ pl, int NX, dou
   const int i0 = (int)f1, j0 = (int)f2;
   const double w1 = y1 - f1, w2 = y2 - f2;
   const T *p = pl + (int64_t)(j0 + G_) * NX + (i0 + G_);
-  return (1.0 - w1) * (1.0 - w2) * (double)__ldg(p) + w1 * (1.0 - w2) * (double)__ldg(p + 1) +
-         (1.0 - w1) * w2 * (double)__ldg(p + NX) + w1 * w2 * (double)__ldg(p + NX + 1);
+  const double p00 = __ldg(p), p10 = __ldg(p + 1), p01 = __ldg(p + NX), p11 = __ldg(p + NX + 1);
+  // nested linear interpolations: the same bilinear value in 3 DADD + 3 DFMA
+  const double a = fma(w1, p10 - p00, p00), c = fma(w1, p11 - p01, p01);
+  return fma(w2, c - a, a);
 }
 
 template <typename T>
@@ -254,10 +256,12 @@ __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const
 }
 
 // the coordinate substep's refined iterations; t1, t2: the new offsets from cell (i1, i2)
+// v3 (dphi/dt) comes back from the metric of the last FP64 iteration, whose midpoint is within
+// iter_tol of the final one (or is NaN when the method's iteration ran instead).
 __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &tb, const Base &b,
                                               const Local<double> &L, int i1, int i2,
                                               double dx1, double dx2, const double u[3],
-                                              double &t1, double &t2) {
+                                              double &t1, double &t2, double &v3) {
   const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
   const float a1 = (float)dx1, a2 = (float)dx2, dt = g.f_dt;
   const float uuf = 2.0f * uf[0] * uf[2];
@@ -303,11 +307,14 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
     const bool conv = converged(n1, t1, g.iter_tol) && converged(n2, t2, g.iter_tol);
     t1 = n1;
     t2 = n2;
+    v3 = ag * fma(o.H13, u[0], o.H33 * u[2]);  // Eq. (discretized-geodesic-x-phi) at x_bar
     if (conv && it >= 1) break;
   }
   const double scale = fmax(1.0, fmax(fabs(t1), fabs(t2)));
-  if (!method_converges(d1, D1, D2, g.n_iter, g.iter_tol, scale))
+  if (!method_converges(d1, D1, D2, g.n_iter, g.iter_tol, scale)) {
     coord_exact(g, b, L, i1, i2, dx1, dx2, u, t1, t2);  // the method's n_iter iterations
+    v3 = NAN;
+  }
 }
 
 // One particle in FP64: steps 2-11 of Sec. 3.1, the boundaries of Sec. 3.3.3, and
@@ -350,8 +357,8 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   boris(uh, Dh, Bh, hq);       // step 8
   hat_cov(L, uh, u);           // step 9
   // step 10: implicit coordinate push, Eq. (discretized-geodesic-x)
-  double t1 = dx1, t2 = dx2;
-  if (refine) coord_refined(g, tb, b, L, i1, i2, dx1, dx2, u, t1, t2);
+  double t1 = dx1, t2 = dx2, v3r = NAN;
+  if (refine) coord_refined(g, tb, b, L, i1, i2, dx1, dx2, u, t1, t2, v3r);
   else coord_exact(g, b, L, i1, i2, dx1, dx2, u, t1, t2);
   if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(t1) && isfinite(t2) &&
         fabs(t1) < 1e6 && fabs(t2) < 1e6)) {
@@ -376,7 +383,8 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   else if (j1 >= g.n_r) { s.tag[k] = 2; count(diag, DG_LEFT_OUTER); }
   // step 11: phi at x^{n+1/2}, the midpoint of the stored x^n and the final x^{n+1}
   const double xb1 = j1 + e1, xb2 = j2 + e2;
-  const double v3 = phi_rate64(g, b, 0.5 * __dadd_rn(x1, xb1), 0.5 * __dadd_rn(x2, xb2), u);
+  const double v3 = isnan(v3r)
+      ? phi_rate64(g, b, 0.5 * __dadd_rn(x1, xb1), 0.5 * __dadd_rn(x2, xb2), u) : v3r;
   s.phi[k] = (T)((double)s.phi[k] + g.dt * v3);
   if (DEPOSIT) deposit64(g, F, s.qc * (double)s.w[k], i1, i2, x1, x2, j1, j2, xb1, xb2, v3);
 }
