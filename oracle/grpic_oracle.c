@@ -208,9 +208,12 @@ static void push_one(const ora_params *p, const double *F, ora_species *s, int64
   s->dx1p[k] = s->dx1[k]; s->dx2p[k] = s->dx2[k];
   if (s->tag[k] != 1) { s->tag[k] = 0; return; }
   double x1 = s->i1[k] + s->dx1[k], x2 = s->i2[k] + s->dx2[k];
-  /* step 2: fields at x^n */
+  const double m2 = s->massless ? 0.0 : 1.0;
+  /* step 2: fields at x^n (not needed by massless particles) */
   double Dv[3], Bv[3];
-  if (field_mode == 0) {
+  if (s->massless) {
+    for (int c = 0; c < 3; ++c) Bv[c] = Dv[c] = 0.0;
+  } else if (field_mode == 0) {
     for (int c = 0; c < 3; ++c) {
       Bv[c] = interp(F + (ORA_BN1 + c) * PS, NX, x1, x2, SB[c][0], SB[c][1]);
       Dv[c] = interp(F + (ORA_D1 + c) * PS, NX, x1, x2, SD[c][0], SD[c][1]);
@@ -229,12 +232,17 @@ static void push_one(const ora_params *p, const double *F, ora_species *s, int64
   vec_to_hat(&m, Bv, Bh);
   cov_to_hat(&m, u, uh);
   double hq = s->qm * m.alpha * 0.5 * dt;
-  boris(uh, Dh, Bh, hq);     /* step 4 */
-  hat_to_cov(&m, uh, u);     /* step 5 */
-  geodesic_u(p, &m, u);      /* step 6 */
-  cov_to_hat(&m, u, uh);     /* step 7 */
-  boris(uh, Dh, Bh, hq);     /* step 8 */
-  hat_to_cov(&m, uh, u);     /* step 9 */
+  /* steps 3-5 and 7-9 (the EM push) are skipped for massless particles (Sec. 3.1) */
+  if (!s->massless) {
+    boris(uh, Dh, Bh, hq);   /* step 4 */
+    hat_to_cov(&m, uh, u);   /* step 5 */
+  }
+  geodesic_u(p, &m, u, m2);  /* step 6 */
+  if (!s->massless) {
+    cov_to_hat(&m, u, uh);   /* step 7 */
+    boris(uh, Dh, Bh, hq);   /* step 8 */
+    hat_to_cov(&m, uh, u);   /* step 9 */
+  }
   /* step 10: implicit coordinate push, Eq. (discretized-geodesic-x), metric at the
    * midpoint x_bar = (x^n + x~)/2; positions kept as cell + offset */
   double dxt1 = s->dx1[k], dxt2 = s->dx2[k];
@@ -243,7 +251,7 @@ static void push_one(const ora_params *p, const double *F, ora_species *s, int64
     double xb2 = s->i2[k] + 0.5 * (s->dx2[k] + dxt2);
     ora_metric mb;
     metric_eval(p, xb1, xb2, 1, 0, &mb);
-    double gam = gamma_of(&mb, u);
+    double gam = gamma_of(&mb, u, m2);
     double v1 = mb.alpha / gam * (mb.H11 * u[0] + mb.H13 * u[2]) - mb.beta1;
     double v2 = mb.alpha / gam * (mb.H22 * u[1]);
     dxt1 = s->dx1[k] + dt * v1;
@@ -273,7 +281,7 @@ static void push_one(const ora_params *p, const double *F, ora_species *s, int64
   double xm2 = 0.5 * ((s->i2p[k] + s->dx2p[k]) + (i2n + dx2n));
   ora_metric mm;
   metric_eval(p, xm1, xm2, 1, 0, &mm);
-  double gam = gamma_of(&mm, u);
+  double gam = gamma_of(&mm, u, m2);
   s->phi[k] += dt * mm.alpha / gam * (mm.H13 * u[0] + mm.H33 * u[2]);
 }
 
@@ -317,6 +325,7 @@ void ora_deposit(const ora_params *p, double *F, ora_species *sp, int ns) {
   const double dt = p->dt;
   for (int si = 0; si < ns; ++si) {
     ora_species *s = &sp[si];
+    if (s->massless) continue; /* reading: massless particles are neutral */
     for (int64_t k = 0; k < s->n; ++k) {
       if (s->tag[k] == 0) continue;
       double q = s->qc * s->w[k];
@@ -344,7 +353,7 @@ void ora_deposit(const ora_params *p, double *F, ora_species *sp, int ns) {
       ora_metric mm;
       metric_eval(p, xm1, xm2, 1, 0, &mm);
       double u[3] = {s->u1[k], s->u2[k], s->u3[k]};
-      double v3 = mm.alpha / gamma_of(&mm, u) * (mm.H13 * u[0] + mm.H33 * u[2]);
+      double v3 = mm.alpha / gamma_of(&mm, u, 1.0) * (mm.H13 * u[0] + mm.H33 * u[2]);
       int i0 = (int)floor(xm1), j0 = (int)floor(xm2);
       double w1 = xm1 - i0, w2 = xm2 - j0;
       add_dep(J3, A3, NX, i0, j0, q * v3 * (1.0 - w1) * (1.0 - w2));
@@ -362,6 +371,7 @@ void ora_charge(const ora_params *p, const ora_species *sp, int ns, int prev, do
   memset(rho, 0, sizeof(double) * plane_size(p));
   for (int si = 0; si < ns; ++si) {
     const ora_species *s = &sp[si];
+    if (s->massless) continue;
     for (int64_t k = 0; k < s->n; ++k) {
       if (s->tag[k] == 0) continue;
       int i = prev ? s->i1p[k] : s->i1[k], j = prev ? s->i2p[k] : s->i2[k];
@@ -842,17 +852,17 @@ void ora_tetrad(const ora_params *p, double x1, double x2, int dir, const double
 }
 void ora_boris(double u[3], const double Dh[3], const double Bh[3], double hq) { boris(u, Dh, Bh, hq); }
 /* u_0 = -alpha gamma + beta^1 u_1 (footnote of Sec. 2.3, reading u^i = h^ij u_j - u^0 beta^i) */
-double ora_u_lower0(const ora_params *p, double x1, double x2, const double u[3]) {
+double ora_u_lower0(const ora_params *p, double x1, double x2, const double u[3], int massless) {
   ora_metric m;
   metric_eval(p, x1, x2, 1, 0, &m);
-  return -m.alpha * gamma_of(&m, u) + m.beta1 * u[0];
+  return -m.alpha * gamma_of(&m, u, massless ? 0.0 : 1.0) + m.beta1 * u[0];
 }
 /* conserved energy and angular momentum per unit mass (Sec. 2.3) with A of kind/B0 */
 void ora_invariants(const ora_params *p, int kind, double B0, double qm, double x1, double x2,
                     const double u[3], double out[2]) {
   double A[3] = {0.0, 0.0, 0.0};
   if (kind != 0) wald_potential(p, kind, B0, x1, x2, A);
-  out[0] = -ora_u_lower0(p, x1, x2, u) - qm * A[0];
+  out[0] = -ora_u_lower0(p, x1, x2, u, 0) - qm * A[0];
   out[1] = u[2] + qm * A[2];
 }
 double ora_time_step(const ora_params *p, double cfl) {
@@ -909,4 +919,4 @@ void ora_push_frozen_cs(const ora_params *p, const double *F, double scale_re, d
   }
 }
 
-int ora_version(void) { return 2; }
+int ora_version(void) { return 3; }

@@ -61,6 +61,8 @@ typedef struct {
   double *dx1p, *dx2p;
   double qm;                         /* Lorentz coefficient (q/m) per unit stored field   */
   double qc;                         /* deposit coefficient (sign of q included)          */
+  int massless;                      /* 1: massless (Sec. 2.3: gamma = sqrt(h^ij u_i u_j), no
+                                        EM push, Sec. 3.1); neutral, so nothing deposited  */
 } ora_species;
 
 #endif

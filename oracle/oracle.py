@@ -69,7 +69,7 @@ class Species(C.Structure):
     _fields_ = [("n", C.c_int64), ("i1", _PI32), ("i2", _PI32), ("dx1", _PD), ("dx2", _PD),
                 ("u1", _PD), ("u2", _PD), ("u3", _PD), ("phi", _PD), ("w", _PD),
                 ("tag", _PU8), ("i1p", _PI32), ("i2p", _PI32), ("dx1p", _PD), ("dx2p", _PD),
-                ("qm", C.c_double), ("qc", C.c_double)]
+                ("qm", C.c_double), ("qc", C.c_double), ("massless", C.c_int)]
 
 
 PARTICLE_FIELDS = {"i1": np.int32, "i2": np.int32, "dx1": np.float64, "dx2": np.float64,
@@ -92,7 +92,7 @@ def lib():
         L.ora_fields_point.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, _PD, _PD]
         L.ora_tetrad.argtypes = [P, C.c_double, C.c_double, C.c_int, _PD, _PD]
         L.ora_boris.argtypes = [_PD, _PD, _PD, C.c_double]
-        L.ora_u_lower0.argtypes = [P, C.c_double, C.c_double, _PD]
+        L.ora_u_lower0.argtypes = [P, C.c_double, C.c_double, _PD, C.c_int]
         L.ora_u_lower0.restype = C.c_double
         L.ora_invariants.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                      _PD, _PD]
@@ -168,8 +168,10 @@ def boris(u, Dh, Bh, hq):
     return u
 
 
-def u_lower0(cfg, x1, x2, u):
-    return lib().ora_u_lower0(C.byref(make_params(cfg)), x1, x2, _dp(np.asarray(u, np.float64)))
+def u_lower0(cfg, x1, x2, u, massless=False):
+    """u_0 = -alpha gamma + beta^1 u_1, gamma = sqrt(m2 + h^ij u_i u_j), m2 = 0 if massless."""
+    return lib().ora_u_lower0(C.byref(make_params(cfg)), x1, x2, _dp(np.asarray(u, np.float64)),
+                              int(bool(massless)))
 
 
 def invariants(cfg, kind, B0, qm, x1, x2, u):
@@ -204,8 +206,9 @@ def sort_keys(cfg, tr, tt, i1, i2, tag=None):
 class OracleSpecies:
     """Particle arrays of one species (numpy), mirrored into the C struct on use."""
 
-    def __init__(self, n: int, qm: float, qc: float):
+    def __init__(self, n: int, qm: float, qc: float, massless: bool = False):
         self.qm, self.qc = float(qm), float(qc)
+        self.massless = bool(massless)
         self.n = int(n)
         self.a = {k: np.zeros(max(n, 1), dtype=t) for k, t in PARTICLE_FIELDS.items()}
 
@@ -215,13 +218,13 @@ class OracleSpecies:
                        _dp(a["dx1"]), _dp(a["dx2"]), _dp(a["u1"]), _dp(a["u2"]), _dp(a["u3"]),
                        _dp(a["phi"]), _dp(a["w"]), a["tag"].ctypes.data_as(_PU8),
                        a["i1p"].ctypes.data_as(_PI32), a["i2p"].ctypes.data_as(_PI32),
-                       _dp(a["dx1p"]), _dp(a["dx2p"]), self.qm, self.qc)
+                       _dp(a["dx1p"]), _dp(a["dx2p"]), self.qm, self.qc, int(self.massless))
 
     def view(self) -> dict:
         return {k: v[: self.n] for k, v in self.a.items()}
 
     def copy(self) -> "OracleSpecies":
-        o = OracleSpecies(self.n, self.qm, self.qc)
+        o = OracleSpecies(self.n, self.qm, self.qc, self.massless)
         o.a = {k: v.copy() for k, v in self.a.items()}
         return o
 
@@ -251,10 +254,12 @@ class OracleSim:
     def init_fields(self, kind: int, B0: float):
         lib().ora_init_fields(C.byref(self.p), _dp(self.F), kind, B0)
 
-    def add_species(self, pos: dict, uhat, w0, qm, qc, density_power=0.0) -> OracleSpecies:
-        """pos: i1, i2, dx1, dx2 arrays; uhat: (3, n) tetrad-frame momenta; w0: base weights."""
+    def add_species(self, pos: dict, uhat, w0, qm, qc, density_power=0.0,
+                    massless=False) -> OracleSpecies:
+        """pos: i1, i2, dx1, dx2 arrays; uhat: (3, n) tetrad-frame momenta; w0: base weights.
+        massless: photons (gamma = |u|, no EM push, nothing deposited)."""
         n = len(pos["i1"])
-        s = OracleSpecies(n, qm, qc)
+        s = OracleSpecies(n, qm, qc, massless)
         for k in ("i1", "i2", "dx1", "dx2"):
             s.a[k][:n] = pos[k]
         uh = [np.ascontiguousarray(uhat[c], dtype=np.float64) for c in range(3)]
@@ -265,10 +270,10 @@ class OracleSim:
         self.species.append(s)
         return s
 
-    def add_raw_species(self, arrays: dict, qm, qc) -> OracleSpecies:
+    def add_raw_species(self, arrays: dict, qm, qc, massless=False) -> OracleSpecies:
         """A species from complete particle arrays (every key of PARTICLE_FIELDS)."""
         n = len(arrays["i1"])
-        s = OracleSpecies(n, qm, qc)
+        s = OracleSpecies(n, qm, qc, massless)
         for k in PARTICLE_FIELDS:
             s.a[k][:n] = arrays[k]
         self.species.append(s)
