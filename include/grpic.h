@@ -122,6 +122,12 @@ typedef struct {
                            of them): the FP64 fixed point to about rho iter_tol (rho < 1 the
                            contraction of the iteration), in fewer FP64 operations. Must be
                            below 1e-6                                                          */
+  int massless[GRPIC_MAX_SPECIES]; /* 1: a species of massless particles (photons): gamma =
+                           sqrt(h^ij u_i u_j) (Sec. 2.3), no field interpolation and no EM
+                           push (Sec. 3.1), only the two geodesic substeps and phi; they are
+                           neutral, so the deposit, the charge check and grpic_deposit skip
+                           them. 0: massive (gamma = sqrt(1 + h^ij u_i u_j)). Other values:
+                           GRPIC_EINVAL                                                        */
 } grpic_config;
 
 /* Pointers to one species' particle arrays (SoA, length >= n). Positions are a cell
@@ -367,6 +373,10 @@ GRPIC_API grpic_status grpic_get_diagnostics(grpic_ctx *ctx, grpic_diag *out);
 
 GRPIC_API const char *grpic_last_error(const grpic_ctx *ctx);
 GRPIC_API void grpic_destroy(grpic_ctx *ctx);
+
+/* sizeof(grpic_config) as this library was compiled: bindings compare it with their own
+ * layout of the struct before the first grpic_create. No CUDA work. */
+GRPIC_API size_t grpic_config_bytes(void);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,8 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_deposit", "grpic_field_step", "grpic_sort", "grpic_step",
            "grpic_get_diagnostics", "grpic_set_timing", "grpic_get_timing", "grpic_last_error",
            "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants",
-           "grpic_adjoint_forward", "grpic_adjoint_backward", "grpic_charge_check"]
+           "grpic_adjoint_forward", "grpic_adjoint_backward", "grpic_charge_check",
+           "grpic_config_bytes"]
 
 
 ADJOINT_SCRATCH_PER_STEP = 36  # doubles per particle and step of grpic_adjoint_backward
@@ -48,7 +49,8 @@ class Config(C.Structure):
                 ("n_species", C.c_int), ("capacity", C.c_int64 * MAX_SPECIES),
                 ("sort_every", C.c_int), ("tile_r", C.c_int), ("tile_theta", C.c_int),
                 ("precision", C.c_int), ("full_iterations", C.c_int),
-                ("fp64_guard_cells", C.c_int), ("tiled_push", C.c_int), ("iter_tol", C.c_double)]
+                ("fp64_guard_cells", C.c_int), ("tiled_push", C.c_int), ("iter_tol", C.c_double),
+                ("massless", C.c_int * MAX_SPECIES)]
 
 
 _VP = C.c_void_p
@@ -91,6 +93,10 @@ def lib(build: bool = True):
         if not os.path.exists(path):
             raise GrpicError("libgrpic.so not found at %s" % path)
         L = C.CDLL(path)
+        L.grpic_config_bytes.restype = C.c_size_t
+        if L.grpic_config_bytes() != C.sizeof(Config):
+            raise GrpicError("grpic_config layout mismatch: library %d bytes, binding %d"
+                             % (L.grpic_config_bytes(), C.sizeof(Config)))
         P = C.c_void_p
         L.grpic_create.argtypes = [C.POINTER(Config), C.POINTER(P)]
         L.grpic_arena_bytes.argtypes = [P]
@@ -155,6 +161,9 @@ def make_config(cfg: dict, capacities) -> Config:
     c.fp64_guard_cells = int(cfg.get("fp64_guard_cells", 0))
     c.tiled_push = int(cfg.get("tiled_push", 0))
     c.iter_tol = float(cfg.get("iter_tol", 0.0))
+    # species indices of massless particles (photons)
+    for i in cfg.get("massless", ()):
+        c.massless[int(i)] = 1
     return c
 
 

@@ -1,6 +1,7 @@
 // adjoint.cu -- adjoint of the GR pusher over frozen fields (Sec. 3.1 of arXiv:2511.17701):
 // gradients of the final test-particle state (x1, x2, phi, u_1, u_2, u_3) with respect to the
-// initial state and the field amplitude (the Wald field is linear in B0).
+// initial state and the field amplitude (the Wald field is linear in B0), for massive charged
+// test particles.
 //
 // Forward: every particle is pushed n_steps steps in the em-plane fields times
 // scale = B0 / (the amplitude the planes hold), both implicit substeps iterated to an exact
@@ -139,7 +140,7 @@ __device__ __forceinline__ void step_values(const GridP &g, const FieldPtrsT<dou
   const double x[2] = {st[0], st[1]}, u[3] = {st[3], st[4], st[5]};
   frame_at(g, F, x, scale, qm, fr);
   em_half(fr.L, fr.Dh, fr.Bh, fr.hq, u, sv.u1);
-  const GeoMap<double> gm(g, fr.L, sv.u1);
+  const GeoMap<double> gm(g, fr.L, sv.u1, 1.0);
   double t0 = sv.u1[0], t1 = sv.u1[1];
   for (int it = 0; it < n_iter; ++it) {
     double n0, n1;
@@ -199,7 +200,7 @@ __device__ void step_jacobian(const GridP &g, const FieldPtrsT<double> &F, const
   // point and (I - dt/2 dV/dx_bar)^{-1} at the final coordinate midpoint
   double Mt[2][2], Mx[2][2];
   {
-    const GeoMap<double> gv(g, fr.L, sv.u1);
+    const GeoMap<double> gv(g, fr.L, sv.u1, 1.0);
     GeoMap<D2> gd;
 #define WIDEN(m) gd.m = D2(gv.m);
     WIDEN(u0) WIDEN(u1) WIDEN(hu0) WIDEN(hu1) WIDEN(c0) WIDEN(c1) WIDEN(e1) WIDEN(e2)
@@ -234,7 +235,7 @@ __device__ void step_jacobian(const GridP &g, const FieldPtrsT<double> &F, const
     frame_at(g, F, X, D2(scale), qm, fd);
     D2 U1[3], U2[3], U3[3];
     em_half(fd.L, fd.Dh, fd.Bh, fd.hq, U, U1);
-    const GeoMap<D2> gm(g, fd.L, U1);
+    const GeoMap<D2> gm(g, fd.L, U1, D2(1.0));
     D2 n0, n1;
     gm.apply(D2(sv.t[0]), D2(sv.t[1]), n0, n1);
     U2[0] = D2(sv.t[0]);
@@ -280,7 +281,7 @@ __device__ void step_jacobian(const GridP &g, const FieldPtrsT<double> &F, const
     const D4 hq(fr.hq);
     D4 U1[3], U2[3], U3[3];
     em_half(fr.L, Dh, Bh, hq, U, U1);
-    const GeoMap<D4> gm(g, fr.L, U1);
+    const GeoMap<D4> gm(g, fr.L, U1, D4(1.0));
     D4 n0, n1;
     gm.apply(D4(sv.t[0]), D4(sv.t[1]), n0, n1);
     U2[0] = D4(sv.t[0]);

@@ -24,6 +24,7 @@ constexpr int kKind[NARR] = {0, 0, 1, 1, 1, 1, 1, 1, 1, 2, 0, 0, 1, 1};
 struct SpeciesState {
   int64_t cap = 0, n_bound = 0;
   double qm = 0.0, qc = 0.0;
+  bool massless = false;  // gamma without the mass term, no EM push, no deposit
   bool loaded = false;
   grpic_particles soa[2];
   int live = 0;
@@ -137,6 +138,8 @@ SpeciesDevT<T> dev_view(const SpeciesState &s, int which) {
   d.phi = (T *)p.phi; d.w = (T *)p.w; d.tag = p.tag;
   d.i1p = p.i1p; d.i2p = p.i2p; d.dx1p = (T *)p.dx1p; d.dx2p = (T *)p.dx2p;
   d.n = s.n_dev; d.qm = s.qm; d.qc = s.qc; d.f_qm = (float)s.qm; d.f_qc = (float)s.qc;
+  d.m2 = s.massless ? 0.0 : 1.0;
+  d.f_m2 = (float)d.m2;
   return d;
 }
 
@@ -237,8 +240,9 @@ cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, int k, bool deposit) {
   const int ntr = (c->g.n_r + tr - 1) / tr, ntt = (c->g.n_th + tt - 1) / tt;
   const TileInfo ti{sp.tiles_valid && c->cfg.tiled_push ? sp.tile_start : nullptr, tr, tt, ntr,
                     ntr * ntt};
+  // massless particles are neutral: their push deposits nothing
   return launch_push<T>(c->g, F, dev_view<T>(sp, sp.live), c->tb, sp.gl, ti, sp.n_bound,
-                        deposit, c->diag, ps);
+                        deposit && !sp.massless, c->diag, ps);
 }
 // the main stream waits for the guard kernels of species k (mixed path)
 cudaError_t join_push(grpic_ctx *c, int k) {
@@ -264,7 +268,7 @@ cudaError_t charge_check(grpic_ctx *ctx, FieldPtrsT<T> &F, bool after_step, doub
   if (e == cudaSuccess) e = launch_zero<double>(ra, ps, ctx->stream);
   for (int k = 0; k < ctx->cfg.n_species && e == cudaSuccess; ++k) {
     SpeciesState &sp = ctx->sp[k];
-    if (sp.loaded) e = launch_charge_rho<T>(ctx->g, dev_view<T>(sp, sp.live), sp.n_bound, rp, rn,
+    if (sp.loaded && !sp.massless) e = launch_charge_rho<T>(ctx->g, dev_view<T>(sp, sp.live), sp.n_bound, rp, rn,
                                             ra, ctx->stream);
   }
   T *const *J = after_step ? F.J0 : F.J;
@@ -297,8 +301,10 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   if (!(c.dt > 0.0) && !(c.cfl > 0.0 && c.cfl <= 1.0)) return GRPIC_EINVAL;
   if (c.fp64_guard_cells < 0 || 2 * c.fp64_guard_cells >= c.n_theta) return GRPIC_EINVAL;
   if (!(c.iter_tol >= 0.0 && c.iter_tol < 1e-6)) return GRPIC_EINVAL;
-  for (int s = 0; s < c.n_species; ++s)
+  for (int s = 0; s < c.n_species; ++s) {
     if (c.capacity[s] < 0 || c.capacity[s] >= ((int64_t)1 << 31)) return GRPIC_EINVAL;
+    if (c.massless[s] != 0 && c.massless[s] != 1) return GRPIC_EINVAL;
+  }
 
   grpic_ctx *ctx = new (std::nothrow) grpic_ctx;
   if (!ctx) return GRPIC_ENOMEM;
@@ -347,6 +353,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   for (int s = 0; s < c.n_species; ++s) {
     SpeciesState &sp = ctx->sp[s];
     sp.cap = c.capacity[s];
+    sp.massless = c.massless[s] == 1;
     if (sp.cap > ctx->max_cap) ctx->max_cap = sp.cap;
     sp.off_n = off; off += up(8);
     for (int b = 0; b < 2; ++b)
@@ -629,7 +636,7 @@ grpic_status grpic_deposit(grpic_ctx *ctx) {
   else CK(do_zero_J(ctx, ctx->F64));
   for (int k = 0; k < ctx->cfg.n_species; ++k) {
     SpeciesState &sp = ctx->sp[k];
-    if (!sp.loaded) continue;
+    if (!sp.loaded || sp.massless) continue;
     if (ctx->mixed)
       CK(launch_deposit<float>(ctx->g, ctx->F32, dev_view<float>(sp, sp.live), ctx->tb,
                                sp.n_bound, ctx->stream));
@@ -830,6 +837,8 @@ grpic_status grpic_get_timing(grpic_ctx *ctx, grpic_timing *out) {
 }
 
 const char *grpic_last_error(const grpic_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+size_t grpic_config_bytes(void) { return sizeof(grpic_config); }
 
 void grpic_destroy(grpic_ctx *ctx) {
   if (!ctx) return;

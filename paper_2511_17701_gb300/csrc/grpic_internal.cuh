@@ -70,6 +70,10 @@ struct SpeciesDevT {
   const int64_t *n;  // live count, on the device
   double qm, qc;
   float f_qm, f_qc;  // FP32 copies
+  // mass term of gamma = sqrt(m2 + h^ij u_i u_j) (Sec. 2.3): 1 for massive particles, 0 for
+  // massless ones, which skip the EM push (Sec. 3.1) and, being neutral, deposit nothing
+  double m2;
+  float f_m2;
 };
 using SpeciesDev = SpeciesDevT<double>;
 
@@ -206,8 +210,9 @@ __device__ __forceinline__ void t_hat_to_cov(const MetricV &m, const double ah[3
   a[2] = s33 * ah[2];
 }
 
-__device__ __forceinline__ double gamma_of(const MetricV &m, const double u[3]) {
-  return sqrt(1.0 + m.H11 * u[0] * u[0] + m.H22 * u[1] * u[1] + m.H33 * u[2] * u[2] +
+// gamma = sqrt(m2 + h^ij u_i u_j), m2 = 1 (massive) or 0 (massless), Sec. 2.3
+__device__ __forceinline__ double gamma_of(const MetricV &m, const double u[3], double m2) {
+  return sqrt(m2 + m.H11 * u[0] * u[0] + m.H22 * u[1] * u[1] + m.H33 * u[2] * u[2] +
               2.0 * m.H13 * u[0] * u[2]);
 }
 

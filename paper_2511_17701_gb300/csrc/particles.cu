@@ -82,13 +82,13 @@ __device__ __forceinline__ void local_rsc(const GridP &g, const Base &b, double 
 // dphi/dt = alpha/gamma h^{3j} u_j at (x1t, x2t) (Eq. discretized-geodesic-x-phi; q times
 // it is J^3 / sqrt(h) w, Sec. 3.2); alpha/gamma = 1/sqrt((1+z) gamma^2).
 __device__ __forceinline__ double phi_rate64(const GridP &g, const Base &b, double x1t,
-                                             double x2t, const double u[3]) {
+                                             double x2t, const double u[3], double m2) {
   double r, sn, cs;
   local_rsc(g, b, x1t, x2t, r, sn, cs);
   Geo<double> o;
   geo_from_rsc(g, r, sn, cs, o);
   const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1], fma(o.H33 * u[2], u[2],
-                   fma(2.0 * o.H13 * u[0], u[2], 1.0))));
+                   fma(2.0 * o.H13 * u[0], u[2], m2))));
   return rsqrt(o.opz * q) * fma(o.H13, u[0], o.H33 * u[2]);
 }
 
@@ -179,13 +179,14 @@ __device__ __forceinline__ bool method_converges(double d1, double D1, double D2
 
 __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTables &tb, int i1,
                                                  int i2, float o1, float o2,
-                                                 const Local<double> &L, double u[3]) {
+                                                 const Local<double> &L, double u[3],
+                                                 double m2) {
   float r, sn, cs;
   rsc32(g, tb, i1, i2, o1, o2, r, sn, cs);
   Local<float> Lf;
   local_full(g, r, sn, cs, Lf);
   const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
-  const GeoMap<float> mf(g, Lf, uf);
+  const GeoMap<float> mf(g, Lf, uf, (float)m2);
   float p0 = uf[0], p1 = uf[1], d1 = 0.0f;
   for (int it = 0; it < g.n_iter; ++it) {
     float n0, n1;
@@ -196,7 +197,7 @@ __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTable
     p1 = n1;
     if (fixed) break;
   }
-  const GeoMap<double> m(g, L, u);
+  const GeoMap<double> m(g, L, u, m2);
   double t0 = u[0], t1 = u[1];
   if (isfinite(p0) && isfinite(p1)) {
     t0 = p0;
@@ -216,7 +217,7 @@ __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTable
   }
   const double scale = fmax(1.0, fmax(fabs(t0), fabs(t1)));
   if (!method_converges(d1, D1, D2, g.n_iter, g.iter_tol, scale)) {
-    geodesic_momentum(g, L, u);  // the method's n_iter iterations from u
+    geodesic_momentum(g, L, u, m2);  // the method's n_iter iterations from u
     return;
   }
   u[0] = t0;
@@ -228,7 +229,8 @@ __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTable
 // until an exact repeat. t1, t2: the new offsets from cell (i1, i2).
 __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const Local<double> &L,
                                             int i1, int i2, double dx1, double dx2,
-                                            const double u[3], double &t1, double &t2) {
+                                            const double u[3], double m2, double &t1,
+                                            double &t2) {
   const double uu0 = 2.0 * u[0] * u[2];
   t1 = dx1;
   t2 = dx2;
@@ -244,7 +246,7 @@ __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const
       geo_from_rsc(g, r, s_, c_, o);
     }
     const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
-                     fma(o.H33 * u[2], u[2], fma(o.H13, uu0, 1.0))));
+                     fma(o.H33 * u[2], u[2], fma(o.H13, uu0, m2))));
     const double ag = rsqrt(o.opz * q);  // alpha / gamma
     const double n1 = fma(g.dt, fma(ag, fma(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
     const double n2 = fma(g.dt, ag * o.H22 * u[1], dx2);
@@ -261,7 +263,7 @@ __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const
 __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &tb, const Base &b,
                                               const Local<double> &L, int i1, int i2,
                                               double dx1, double dx2, const double u[3],
-                                              double &t1, double &t2, double &v3) {
+                                              double m2, double &t1, double &t2, double &v3) {
   const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
   const float a1 = (float)dx1, a2 = (float)dx2, dt = g.f_dt;
   const float uuf = 2.0f * uf[0] * uf[2];
@@ -272,7 +274,7 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
     Geo<float> o;
     geo_from_rsc(g, r, s_, c_, o);
     const float q = fmaf(o.H11 * uf[0], uf[0], fmaf(o.H22 * uf[1], uf[1],
-                    fmaf(o.H33 * uf[2], uf[2], fmaf(o.H13, uuf, 1.0f))));
+                    fmaf(o.H33 * uf[2], uf[2], fmaf(o.H13, uuf, (float)m2))));
     const float ag = rsqrtf(o.opz * q);
     const float n1 = fmaf(dt, fmaf(ag, fmaf(o.H11, uf[0], o.H13 * uf[2]), -o.beta1), a1);
     const float n2 = fmaf(dt, ag * o.H22 * uf[1], a2);
@@ -297,7 +299,7 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
     Geo<double> o;
     geo_from_rsc(g, r, s_, c_, o);
     const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
-                     fma(o.H33 * u[2], u[2], fma(o.H13, uu0, 1.0))));
+                     fma(o.H33 * u[2], u[2], fma(o.H13, uu0, m2))));
     const double ag = rsqrt(o.opz * q);
     const double n1 = fma(g.dt, fma(ag, fma(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
     const double n2 = fma(g.dt, ag * o.H22 * u[1], dx2);
@@ -312,7 +314,7 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
   }
   const double scale = fmax(1.0, fmax(fabs(t1), fabs(t2)));
   if (!method_converges(d1, D1, D2, g.n_iter, g.iter_tol, scale)) {
-    coord_exact(g, b, L, i1, i2, dx1, dx2, u, t1, t2);  // the method's n_iter iterations
+    coord_exact(g, b, L, i1, i2, dx1, dx2, u, m2, t1, t2);  // the method's n_iter iterations
     v3 = NAN;
   }
 }
@@ -326,40 +328,45 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   const int i1 = s.i1[k], i2 = s.i2[k];
   const double dx1 = (double)s.dx1[k], dx2 = (double)s.dx2[k];
   const double x1 = i1 + dx1, x2 = i2 + dx2;
-  // step 2: fields at x^n
-  double Bv[3], Dv[3];
-  Bv[0] = interp64(F.Bn[0], g.NX, x1, x2, 0.0, 0.5);
-  Bv[1] = interp64(F.Bn[1], g.NX, x1, x2, 0.5, 0.0);
-  Bv[2] = interp64(F.Bn[2], g.NX, x1, x2, 0.5, 0.5);
-  Dv[0] = interp64(F.D[0], g.NX, x1, x2, 0.5, 0.0);
-  Dv[1] = interp64(F.D[1], g.NX, x1, x2, 0.0, 0.5);
-  Dv[2] = interp64(F.D[2], g.NX, x1, x2, 0.0, 0.0);
+  const bool em = s.m2 != 0.0;  // massless particles skip the EM push (Sec. 3.1)
   const Base b = make_base(g, x1, x2);
   double sn, cs, r0;
   local_rsc(g, b, x1, x2, r0, sn, cs);  // clamps theta near the axes
   Local<double> L;
   local_full(g, b.r0, sn, cs, L);
-  // step 3: to the tetrad basis
   double Bh[3], Dh[3], uh[3], u[3] = {(double)s.u1[k], (double)s.u2[k], (double)s.u3[k]};
-  vec_hat(L, Bv, Bh);
-  vec_hat(L, Dv, Dh);
-  cov_hat(L, u, uh);
   const double hq = s.qm * L.alpha * 0.5 * g.dt;
-  boris(uh, Dh, Bh, hq);       // step 4
-  hat_cov(L, uh, u);           // step 5
+  if (em) {
+    // step 2: fields at x^n
+    double Bv[3], Dv[3];
+    Bv[0] = interp64(F.Bn[0], g.NX, x1, x2, 0.0, 0.5);
+    Bv[1] = interp64(F.Bn[1], g.NX, x1, x2, 0.5, 0.0);
+    Bv[2] = interp64(F.Bn[2], g.NX, x1, x2, 0.5, 0.5);
+    Dv[0] = interp64(F.D[0], g.NX, x1, x2, 0.5, 0.0);
+    Dv[1] = interp64(F.D[1], g.NX, x1, x2, 0.0, 0.5);
+    Dv[2] = interp64(F.D[2], g.NX, x1, x2, 0.0, 0.0);
+    // step 3: to the tetrad basis
+    vec_hat(L, Bv, Bh);
+    vec_hat(L, Dv, Dh);
+    cov_hat(L, u, uh);
+    boris(uh, Dh, Bh, hq);     // step 4
+    hat_cov(L, uh, u);         // step 5
+  }
   // the refined iterations keep two cell rows away from the axes: there the coordinate map
   // (metric terms ~ 1/sin^2(theta)) has more than one fixed point within reach, and the
   // method's answer is the one its iteration from x^n finds
   const bool refine = g.iter_tol > 0.0 && i2 >= 2 && i2 < g.n_th - 2;
-  if (refine) geodesic_refined(g, tb, i1, i2, (float)dx1, (float)dx2, L, u);
-  else geodesic_momentum(g, L, u);  // step 6
-  cov_hat(L, u, uh);           // step 7
-  boris(uh, Dh, Bh, hq);       // step 8
-  hat_cov(L, uh, u);           // step 9
+  if (refine) geodesic_refined(g, tb, i1, i2, (float)dx1, (float)dx2, L, u, s.m2);
+  else geodesic_momentum(g, L, u, s.m2);  // step 6
+  if (em) {
+    cov_hat(L, u, uh);         // step 7
+    boris(uh, Dh, Bh, hq);     // step 8
+    hat_cov(L, uh, u);         // step 9
+  }
   // step 10: implicit coordinate push, Eq. (discretized-geodesic-x)
   double t1 = dx1, t2 = dx2, v3r = NAN;
-  if (refine) coord_refined(g, tb, b, L, i1, i2, dx1, dx2, u, t1, t2, v3r);
-  else coord_exact(g, b, L, i1, i2, dx1, dx2, u, t1, t2);
+  if (refine) coord_refined(g, tb, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2, v3r);
+  else coord_exact(g, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2);
   if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(t1) && isfinite(t2) &&
         fabs(t1) < 1e6 && fabs(t2) < 1e6)) {
     s.tag[k] = 0;
@@ -384,7 +391,7 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   // step 11: phi at x^{n+1/2}, the midpoint of the stored x^n and the final x^{n+1}
   const double xb1 = j1 + e1, xb2 = j2 + e2;
   const double v3 = isnan(v3r)
-      ? phi_rate64(g, b, 0.5 * __dadd_rn(x1, xb1), 0.5 * __dadd_rn(x2, xb2), u) : v3r;
+      ? phi_rate64(g, b, 0.5 * __dadd_rn(x1, xb1), 0.5 * __dadd_rn(x2, xb2), u, s.m2) : v3r;
   s.phi[k] = (T)((double)s.phi[k] + g.dt * v3);
   if (DEPOSIT) deposit64(g, F, s.qc * (double)s.w[k], i1, i2, x1, x2, j1, j2, xb1, xb2, v3);
 }
@@ -654,11 +661,11 @@ __device__ __forceinline__ void deposit32_warp(const GridP &g, const Sink &sink,
 
 template <bool G64>
 __device__ __forceinline__ float phi_rate32(const GridP &g, const PushTables &tb, int i, int j,
-                                            float o1, float o2, const float u[3]) {
+                                            float o1, float o2, const float u[3], float m2) {
   Geo<float> o;
   geo_at<G64>(g, tb, i, j, o1, o2, o);
   const float q = fmaf(o.H11 * u[0], u[0], fmaf(o.H22 * u[1], u[1],
-                  fmaf(o.H33 * u[2], u[2], fmaf(o.H13, 2.0f * u[0] * u[2], 1.0f))));
+                  fmaf(o.H33 * u[2], u[2], fmaf(o.H13, 2.0f * u[0] * u[2], m2))));
   return rsqrtf(o.opz * q) * fmaf(o.H13, u[0], o.H33 * u[2]);
 }
 
@@ -675,13 +682,7 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
                                        unsigned long long *diag, Move32 &mv) {
   const int i1 = s.i1[k], i2 = s.i2[k];
   const float dx1 = s.dx1[k], dx2 = s.dx2[k];
-  float Bv[3], Dv[3];
-  Bv[0] = F.at(0, i1, i2, dx1, dx2, 0.0f, 0.5f);
-  Bv[1] = F.at(1, i1, i2, dx1, dx2, 0.5f, 0.0f);
-  Bv[2] = F.at(2, i1, i2, dx1, dx2, 0.5f, 0.5f);
-  Dv[0] = F.at(3, i1, i2, dx1, dx2, 0.5f, 0.0f);
-  Dv[1] = F.at(4, i1, i2, dx1, dx2, 0.0f, 0.5f);
-  Dv[2] = F.at(5, i1, i2, dx1, dx2, 0.0f, 0.0f);
+  const bool em = s.f_m2 != 0.0f;  // massless particles skip the EM push (Sec. 3.1)
   Local<float> L;
   if constexpr (G64) {
     double r0, sn, cs;
@@ -695,16 +696,27 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
     local_full(g, r0, sn, cs, L);
   }
   float Bh[3], Dh[3], uh[3], u[3] = {s.u1[k], s.u2[k], s.u3[k]};
-  vec_hat(L, Bv, Bh);
-  vec_hat(L, Dv, Dh);
-  cov_hat(L, u, uh);
   const float hq = s.f_qm * L.alpha * 0.5f * g.f_dt;
-  boris(uh, Dh, Bh, hq);
-  hat_cov(L, uh, u);
-  geodesic_momentum(g, L, u);
-  cov_hat(L, u, uh);
-  boris(uh, Dh, Bh, hq);
-  hat_cov(L, uh, u);
+  if (em) {
+    float Bv[3], Dv[3];
+    Bv[0] = F.at(0, i1, i2, dx1, dx2, 0.0f, 0.5f);
+    Bv[1] = F.at(1, i1, i2, dx1, dx2, 0.5f, 0.0f);
+    Bv[2] = F.at(2, i1, i2, dx1, dx2, 0.5f, 0.5f);
+    Dv[0] = F.at(3, i1, i2, dx1, dx2, 0.5f, 0.0f);
+    Dv[1] = F.at(4, i1, i2, dx1, dx2, 0.0f, 0.5f);
+    Dv[2] = F.at(5, i1, i2, dx1, dx2, 0.0f, 0.0f);
+    vec_hat(L, Bv, Bh);
+    vec_hat(L, Dv, Dh);
+    cov_hat(L, u, uh);
+    boris(uh, Dh, Bh, hq);
+    hat_cov(L, uh, u);
+  }
+  geodesic_momentum(g, L, u, s.f_m2);
+  if (em) {
+    cov_hat(L, u, uh);
+    boris(uh, Dh, Bh, hq);
+    hat_cov(L, uh, u);
+  }
   const float dt = g.f_dt;
   const float uu0 = 2.0f * u[0] * u[2];
   float t1 = dx1, t2 = dx2;
@@ -713,7 +725,7 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
     if (it == 0) o = L.G;
     else geo_at<G64>(g, tb, i1, i2, 0.5f * (dx1 + t1), 0.5f * (dx2 + t2), o);
     const float q = fmaf(o.H11 * u[0], u[0], fmaf(o.H22 * u[1], u[1],
-                    fmaf(o.H33 * u[2], u[2], fmaf(o.H13, uu0, 1.0f))));
+                    fmaf(o.H33 * u[2], u[2], fmaf(o.H13, uu0, s.f_m2))));
     const float ag = rsqrtf(o.opz * q);
     const float n1 = fmaf(dt, fmaf(ag, fmaf(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
     const float n2 = fmaf(dt, ag * o.H22 * u[1], dx2);
@@ -747,7 +759,8 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
   else if (j1 >= g.n_r) { s.tag[k] = 2; count(diag, DG_LEFT_OUTER); }
   // phi at the midpoint, relative to the start cell
   const float b1 = (float)di + e1, b2 = (float)dj + e2;
-  const float v3 = phi_rate32<G64>(g, tb, i1, i2, 0.5f * (dx1 + b1), 0.5f * (dx2 + b2), u);
+  const float v3 = phi_rate32<G64>(g, tb, i1, i2, 0.5f * (dx1 + b1), 0.5f * (dx2 + b2), u,
+                                   s.f_m2);
   s.phi[k] = fmaf(dt, v3, s.phi[k]);
   mv = Move32{i1, i2, di, dj, dx1, dx2, b1, b2, s.f_qc * s.w[k], v3};
   return true;
@@ -957,8 +970,8 @@ __global__ void __launch_bounds__(TPB) k_deposit(GridP g, FieldPtrsT<T> F, Speci
         const float b1 = (float)(ib - ia) + s.dx1[k], b2 = (float)(jb - ja) + s.dx2[k];
         const float u[3] = {s.u1[k], s.u2[k], s.u3[k]};
         const float m1 = 0.5f * (a1 + b1), m2 = 0.5f * (a2 + b2);
-        const float v3 = zone ? phi_rate32<true>(g, tb, ia, ja, m1, m2, u)
-                              : phi_rate32<false>(g, tb, ia, ja, m1, m2, u);
+        const float v3 = zone ? phi_rate32<true>(g, tb, ia, ja, m1, m2, u, s.f_m2)
+                              : phi_rate32<false>(g, tb, ia, ja, m1, m2, u, s.f_m2);
         mv = Move32{ia, ja, ib - ia, jb - ja, a1, a2, b1, b2, s.f_qc * s.w[k], v3};
       }
       deposit32_warp(g, GlobalSink(g, F), mv, on);
@@ -968,7 +981,8 @@ __global__ void __launch_bounds__(TPB) k_deposit(GridP g, FieldPtrsT<T> F, Speci
       const double xb1 = ib + (double)s.dx1[k], xb2 = jb + (double)s.dx2[k];
       const double u[3] = {(double)s.u1[k], (double)s.u2[k], (double)s.u3[k]};
       const Base b = make_base(g, xa1, xa2);
-      const double v3 = phi_rate64(g, b, 0.5 * __dadd_rn(xa1, xb1), 0.5 * __dadd_rn(xa2, xb2), u);
+      const double v3 = phi_rate64(g, b, 0.5 * __dadd_rn(xa1, xb1), 0.5 * __dadd_rn(xa2, xb2), u,
+                                   s.m2);
       deposit64(g, F, s.qc * (double)s.w[k], ia, ja, xa1, xa2, ib, jb, xb1, xb2, v3);
     }
   }
@@ -1015,7 +1029,7 @@ __global__ void k_invariants(GridP g, SpeciesDevT<T> s, int kind, double B0, dou
     MetricV m;
     metric_eval<false>(g, x1, x2, true, m, nullptr);
     const double u[3] = {(double)s.u1[k], (double)s.u2[k], (double)s.u3[k]};
-    const double u0 = -m.alpha * gamma_of(m, u) + m.beta1 * u[0];
+    const double u0 = -m.alpha * gamma_of(m, u, s.m2) + m.beta1 * u[0];
     Pot p;
     p.A0 = p.A3 = 0.0;
     if (kind == GRPIC_FIELD_WALD || kind == GRPIC_FIELD_VERTICAL)

@@ -149,7 +149,7 @@ __device__ __forceinline__ void boris(R u[3], const R D[3], const R B[3], R hq) 
 
 // Eq. (discretized-geodesic-u): the map t -> G(t) whose fixed point is the new covariant
 // (u_1, u_2): implicit midpoint with the metric and its derivatives at x^n, u_3 unchanged
-// (the substep conserves it). Everything that does not depend on the iterate t is
+// (the substep conserves it). m2: the mass term of gamma (1 massive, 0 massless). Everything that does not depend on the iterate t is
 // precomputed; apply() evaluates G once.
 template <typename R>
 struct GeoMap {
@@ -157,13 +157,13 @@ struct GeoMap {
   R H11, H22, d1H11, d1H22, d2H11, d2H22;
   GeoMap() = default;
   template <typename M>
-  __device__ __forceinline__ GeoMap(const GridP &g, const Local<M> &L, const R u[3]) {
+  __device__ __forceinline__ GeoMap(const GridP &g, const Local<M> &L, const R u[3], R m2) {
     const R u3 = u[2];
     const Geo<M> &o = L.G;
     const R dt = cst<R>(g).dt;
     u0 = u[0];
     u1 = u[1];
-    c0 = fma_(o.H33 * u3, u3, (R)1);
+    c0 = fma_(o.H33 * u3, u3, m2);
     c1 = (R)2 * o.H13 * u3;
     e1 = L.d1H33 * u3 * u3;
     e2 = (R)2 * L.d1H13 * u3;
@@ -199,8 +199,9 @@ struct GeoMap {
 
 // The geodesic substep: n_iter applications of G from t = u.
 template <typename R>
-__device__ __forceinline__ void geodesic_momentum(const GridP &g, const Local<R> &L, R u[3]) {
-  const GeoMap<R> m(g, L, u);
+__device__ __forceinline__ void geodesic_momentum(const GridP &g, const Local<R> &L, R u[3],
+                                                  R m2) {
+  const GeoMap<R> m(g, L, u, m2);
   R t0 = u[0], t1 = u[1];
   for (int it = 0; it < g.n_iter; ++it) {
     R n0, n1;

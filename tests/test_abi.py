@@ -62,6 +62,21 @@ def test_create_rejects_bad_configs(bad):
     assert st == B.EINVAL and not ctx
 
 
+def test_config_layout_matches_the_library():
+    assert B.lib().grpic_config_bytes() == C.sizeof(B.Config)
+
+
+def test_create_checks_the_massless_flags():
+    c = B.make_config(dict(good_cfg(), massless=[1]), (10, 10))
+    assert list(c.massless)[:2] == [0, 1]
+    ctx = C.c_void_p()
+    assert B.lib().grpic_create(C.byref(c), C.byref(ctx)) == B.OK
+    B.lib().grpic_destroy(ctx)
+    c.massless[0] = 2
+    ctx = C.c_void_p()
+    assert B.lib().grpic_create(C.byref(c), C.byref(ctx)) == B.EINVAL and not ctx
+
+
 def test_create_rejects_bad_species():
     assert create(good_cfg(), caps=())[0] == B.EINVAL
     assert create(good_cfg(), caps=(1,) * 9)[0] == B.EINVAL
