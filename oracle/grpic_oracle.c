@@ -617,6 +617,81 @@ void ora_field_predict(const ora_params *p, double *F) {
   free(tmp);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Current filter (Sec. 3.2: the deposit is followed by n_f filter passes;    */
+/* Sec. 3.3.3: the horizon layer i1 <= n_f keeps their effect off the         */
+/* domain). The filter itself is paper I's and not given here. Reading: one   */
+/* pass replaces each value by the binomial stencil (1 2 1)/4 x (1 2 1)/4 of   */
+/* its eight neighbours and itself, on the grid extended across each axis by   */
+/* the mirror image of the particles (positive weights): node-row quantities   */
+/* (J^1, J^3, rho) are even and half-row ones (J^2) odd across an axis, and    */
+/* the axis node, which holds the charge of a half cell, holds twice that in   */
+/* the extended grid. Values beyond the stored x1 range read as zero. Each     */
+/* pass maps the stored values to new stored values; rows outside the         */
+/* component's range stay zero. Convolution commutes with the differences of  */
+/* the continuity equation, so filtered currents conserve the filtered charge. */
+/* ------------------------------------------------------------------------ */
+/* the value of the mirror-extended grid at stored column i and row index j (position j for a
+ * node row, j + 1/2 for a half row) */
+static double filter_ext(const ora_params *p, const double *f, int i, int j, int half,
+                         double parity) {
+  const int NX = NX_of(p), N = p->n_th;
+  if (i < -G || i > p->n_r + G) return 0.0;
+  double sgn = 1.0;
+  /* reflect the position x = j (+ 1/2) into [0, N]: x -> -x, x -> 2N - x */
+  for (;;) {
+    if (!half) {
+      if (j < 0) { j = -j; sgn *= parity; continue; }
+      if (j > N) { j = 2 * N - j; sgn *= parity; continue; }
+      break;
+    } else {
+      if (j < 0) { j = -j - 1; sgn *= parity; continue; }
+      if (j > N - 1) { j = 2 * N - j - 1; sgn *= parity; continue; }
+      break;
+    }
+  }
+  double v = sgn * AT(f, i, j);
+  if (!half && (j == 0 || j == N)) v *= 2.0;
+  return v;
+}
+
+/* n passes of the filter on one plane; half = 1 for a half-row component */
+void ora_filter_plane(const ora_params *p, double *f, int half, double parity, int n) {
+  const int NX = NX_of(p), N = p->n_th;
+  const int64_t PS = plane_size(p);
+  double *src = malloc(sizeof(double) * PS);
+  const double w[3] = {1.0, 2.0, 1.0};
+  for (int pass = 0; pass < n; ++pass) {
+    memcpy(src, f, sizeof(double) * PS);
+    memset(f, 0, sizeof(double) * PS);
+    const int jmax = half ? N - 1 : N;
+    for (int j = 0; j <= jmax; ++j)
+      for (int i = -G; i <= p->n_r + G; ++i) {
+        double acc = 0.0;
+        for (int b = -1; b <= 1; ++b)
+          for (int a = -1; a <= 1; ++a)
+            acc += w[a + 1] * w[b + 1] * filter_ext(p, src, i + a, j + b, half, parity);
+        acc /= 16.0;
+        if (!half && (j == 0 || j == N)) acc *= 0.5; /* back to the half cell */
+        AT(f, i, j) = acc;
+      }
+  }
+  free(src);
+}
+
+/* the n_f passes on the currents J^1 (node rows, even), J^2 (half rows, odd), J^3 (node rows,
+ * even); the absolute-term sums JA (a rounding scale for the tests) with even parity */
+void ora_filter_currents(const ora_params *p, double *F) {
+  if (p->n_f <= 0) return;
+  const int64_t PS = plane_size(p);
+  const int half[3] = {0, 1, 0};
+  const double par[3] = {1.0, -1.0, 1.0};
+  for (int c = 0; c < 3; ++c) {
+    ora_filter_plane(p, F + (ORA_J1 + c) * PS, half[c], par[c], p->n_f);
+    ora_filter_plane(p, F + (ORA_JA1 + c) * PS, half[c], 1.0, p->n_f);
+  }
+}
+
 /* Loop steps 5-7 (Sec. 3.4), after the deposit wrote J^{n+1/2} into J. */
 void ora_field_advance(const ora_params *p, double *F) {
   const int64_t PS = plane_size(p);
@@ -822,6 +897,7 @@ void ora_step(const ora_params *p, double *F, ora_species *sp, int ns, int n_ste
       for (int si = 0; si < ns; ++si) ora_sort(p, &sp[si], tr, tt, NULL);
     for (int si = 0; si < ns; ++si) ora_push(p, F, &sp[si], 0, 0, 0.0, counters);
     ora_deposit(p, F, sp, ns);
+    ora_filter_currents(p, F);
     ora_field_advance(p, F);
   }
 }
@@ -919,4 +995,4 @@ void ora_push_frozen_cs(const ora_params *p, const double *F, double scale_re, d
   }
 }
 
-int ora_version(void) { return 3; }
+int ora_version(void) { return 4; }

@@ -111,6 +111,8 @@ def lib():
         L.ora_sort_key.restype = C.c_uint32
         L.ora_step.argtypes = [P, _PD, PP, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                C.c_int64, C.POINTER(C.c_int64)]
+        L.ora_filter_plane.argtypes = [P, _PD, C.c_int, C.c_double, C.c_int]
+        L.ora_filter_currents.argtypes = [P, _PD]
         L.ora_push_frozen.argtypes = [P, _PD, C.c_double, C.c_double, C.c_int, C.c_int64, _PD]
         L.ora_push_frozen_cs.argtypes = [P, _PD, C.c_double, C.c_double, C.c_double, C.c_int,
                                          C.c_int64, _PD, _PD]
@@ -309,6 +311,17 @@ class OracleSim:
         arr = self._structs()
         lib().ora_charge(C.byref(self.p), arr, len(self.species), int(prev), _dp(rho))
         return rho
+
+    def filter_currents(self):
+        """n_filter passes of the current filter on J (and on the rounding scales JA)."""
+        lib().ora_filter_currents(C.byref(self.p), _dp(self.F))
+
+    def filter_plane(self, plane, half: bool, parity: float, n: int):
+        """n passes of the current filter on a [NY][NX] array (returns a filtered copy);
+        half: a half-row (x2 = j + 1/2) quantity; parity: +1 even, -1 odd across the axes."""
+        f = np.ascontiguousarray(plane, dtype=np.float64).copy()
+        lib().ora_filter_plane(C.byref(self.p), _dp(f), int(half), float(parity), int(n))
+        return f
 
     def advance(self):
         lib().ora_field_advance(C.byref(self.p), _dp(self.F))

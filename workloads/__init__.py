@@ -36,6 +36,11 @@ CONFIGS = {
     "wald512": dict(metric="ks", a=_A, n_r=512, n_theta=512, r_min=_RMIN, r_max=50.0, ppc=32,
                     theta_T=1.0, density_power=0.0, steps=1000, cfl=0.5, seed=2, B0=1.0,
                     r_absorb=45.0),
+    # wald64 with 4 current-filter passes: the grid reaches 0.7 r_h (9.9 cells inside the
+    # horizon), so the horizon layer i1 <= n_f lies inside it
+    "wald64f": dict(metric="ks", a=_A, n_r=64, n_theta=64, r_min=0.7 * horizon_radius(_A),
+                    r_max=10.0, ppc=8, theta_T=0.3, density_power=0.0, steps=200, cfl=0.5,
+                    seed=4, B0=1.0, r_absorb=9.0, n_filter=4),
     # 2048^2, r_max = 200, 16 ppc per species (134,217,728 particles), density ~ 1/r, 500 steps
     "wald2048": dict(metric="ks", a=_A, n_r=2048, n_theta=2048, r_min=_RMIN, r_max=200.0,
                      ppc=16, theta_T=1.0, density_power=1.0, steps=500, cfl=0.5, seed=3,
