@@ -97,7 +97,13 @@ typedef struct {
   double dt;           /* time step; > 0 overrides cfl                                       */
   int n_iter;          /* fixed iteration count of both implicit geodesic pushes, Sec. 3.1   */
   double small_angle;  /* SMALL_ANGLE_GR, Sec. 3.3.2 (1e-5)                                  */
-  int n_filter;        /* n_f, Sec. 3.3.3: fields in cells i1 <= n_f copy cell n_f + 1       */
+  int n_filter;        /* n_f, Sec. 3.2 and 3.3.3: the deposit is followed by n_f passes of the
+                          current filter (binomial (1 2 1) x (1 2 1)/16 on the grid extended
+                          across the axes by mirror images: J^1, J^3 even, J^2 odd, axis nodes
+                          holding half cells), and the fields in cells i1 <= n_f copy cell
+                          n_f + 1. 0 .. 64; with the Kerr metric the grid must start at least
+                          n_f + 1 cells inside the horizon, r(x1 = n_f + 1) <= r_h (else
+                          GRPIC_EINVAL)                                                        */
   double r_absorb;     /* absorbing (MATCH) layer for r > r_absorb, Sec. 3.3.3               */
   double absorb_coef;  /* its strength                                                       */
   int n_species;       /* 1 .. GRPIC_MAX_SPECIES                                             */
@@ -243,7 +249,8 @@ GRPIC_API grpic_status grpic_invariants(grpic_ctx *ctx, int species, int kind, d
 GRPIC_API grpic_status grpic_push(grpic_ctx *ctx, int species);
 
 /* Conformal current deposit of all species from previous and new positions, Sec. 3.2,
- * Eq. (charge-conservation-disc): zeroes J, then deposits J^{n+1/2}. */
+ * Eq. (charge-conservation-disc): zeroes J, then deposits J^{n+1/2} and applies the n_f
+ * current-filter passes (config n_filter). */
 GRPIC_API grpic_status grpic_deposit(grpic_ctx *ctx);
 
 /* GRPIC_PREDICT: loop step 2 of Sec. 3.4 (B^{n-1}, D^{n-1/2}, E^{n-1/2}, auxiliary
@@ -292,7 +299,9 @@ GRPIC_API grpic_status grpic_sort_permutation_noalloc(int n_r, int n_theta, int 
 /* --- charge conservation ------------------------------------------------------------ */
 
 /* The discrete continuity equation of the deposit (Sec. 3.2, Eq. charge-conservation-disc),
- * evaluated in FP64 for either precision at every node i in [-1, n_r + 1], j in [0, n_theta]:
+ * evaluated in FP64 for either precision at every node i in [-1, n_r + 1], j in [0, n_theta]
+ * (with n_f > 0 filter passes: i in [max(-1, n_f - 2), min(n_r + 1, n_r + 3 - n_f)], and rho
+ * filtered by the same passes as the currents):
  *   res = J^1(i+1/2, j) - J^1(i-1/2, j) + J^2(i, j+1/2) - J^2(i, j-1/2)
  *         + (rho^{n+1} - rho^n)(i, j) / dt,
  * with rho the charge q w of every live particle shared over its cell's four nodes by
@@ -302,7 +311,7 @@ GRPIC_API grpic_status grpic_sort_permutation_noalloc(int n_r, int n_theta, int 
  * max |res|, out[1] = max |drho/dt|, out[2] = max over nodes of |res| / (|J terms| +
  * |drho/dt|), out[3] = max over nodes of sum |q w| S / dt at both positions (the scale of
  * the rounding: charges of opposite sign cancel in rho but not here, so a rounded residual
- * is a small multiple of eps * out[3]). Uses three FP64 planes of the arena; synchronises the
+ * is a small multiple of eps * out[3]). Uses six FP64 planes of the arena; synchronises the
  * stream.
  * Errors: GRPIC_ESTATE (fields not initialised), GRPIC_EINVAL (null out). */
 GRPIC_API grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double out[4]);

@@ -271,6 +271,16 @@ cudaError_t charge_check(grpic_ctx *ctx, FieldPtrsT<T> &F, bool after_step, doub
     if (sp.loaded && !sp.massless) e = launch_charge_rho<T>(ctx->g, dev_view<T>(sp, sp.live), sp.n_bound, rp, rn,
                                             ra, ctx->stream);
   }
+  // with current filtering the currents conserve the filtered charge
+  if (e == cudaSuccess && ctx->g.n_f > 0) {
+    double *const a[3] = {rp, rn, ra};
+    double *const s[3] = {at<double>(ctx, ctx->off_rho + 3 * up(ps * 8)),
+                          at<double>(ctx, ctx->off_rho + 4 * up(ps * 8)),
+                          at<double>(ctx, ctx->off_rho + 5 * up(ps * 8))};
+    const int half[3] = {0, 0, 0};
+    const double par[3] = {1.0, 1.0, 1.0};
+    e = launch_filter<double>(ctx->g, a, s, half, par, 3, ctx->g.n_f, ctx->stream);
+  }
   T *const *J = after_step ? F.J0 : F.J;
   if (e == cudaSuccess)
     e = launch_continuity<T>(ctx->g, J[0], J[1], rp, rn, ra, out, ctx->stream);
@@ -294,7 +304,11 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   if (c.metric == GRPIC_METRIC_KS && !(c.a >= 0.0 && c.a < 1.0)) return GRPIC_EINVAL;
   if (c.n_iter < 1 || c.n_iter > 1000) return GRPIC_EINVAL;
   if (!(c.small_angle > 0.0 && c.small_angle < 0.1)) return GRPIC_EINVAL;
-  if (c.n_filter < 0 || c.n_filter + 2 >= c.n_r) return GRPIC_EINVAL;
+  if (c.n_filter < 0 || c.n_filter + 2 >= c.n_r || c.n_filter > 64) return GRPIC_EINVAL;
+  // Sec. 3.3.3: the inner boundary lies at least n_f + 1 cells inside the event horizon
+  if (c.metric == GRPIC_METRIC_KS &&
+      !(c.r_min * exp((c.n_filter + 1) * log(c.r_max / c.r_min) / c.n_r) <= 1.0 + sqrt(1.0 - c.a * c.a)))
+    return GRPIC_EINVAL;
   if (c.n_species < 1 || c.n_species > GRPIC_MAX_SPECIES) return GRPIC_EINVAL;
   if (c.precision != GRPIC_FP64 && c.precision != GRPIC_MIXED) return GRPIC_EINVAL;
   if (c.tile_r < 1 || c.tile_theta < 1 || c.sort_every < 0) return GRPIC_EINVAL;
@@ -380,7 +394,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
       off += up((size_t)(ntiles + 1) * 4);
     }
   }
-  ctx->off_rho = off; off += 3 * up(ps * 8) + up(64);  // FP64 charge planes of the check
+  ctx->off_rho = off; off += 6 * up(ps * 8) + up(64);  // FP64 charge planes of the check
   ctx->load_chunk = ctx->max_cap < ((int64_t)1 << 20) ? ctx->max_cap : ((int64_t)1 << 20);
   ctx->off_stage = off; off += 6 * up((size_t)ctx->load_chunk * 8);
   ctx->need = off;
@@ -644,6 +658,8 @@ grpic_status grpic_deposit(grpic_ctx *ctx) {
       CK(launch_deposit<double>(ctx->g, ctx->F64, dev_view<double>(sp, sp.live), ctx->tb,
                                 sp.n_bound, ctx->stream));
   }
+  if (ctx->mixed) CK(launch_filter_currents<float>(ctx->g, ctx->F32, ctx->stream));
+  else CK(launch_filter_currents<double>(ctx->g, ctx->F64, ctx->stream));
   return GRPIC_OK;
 }
 
@@ -718,6 +734,11 @@ grpic_status grpic_step(grpic_ctx *ctx, int n_steps) {
       for (int k = 0; k < ctx->cfg.n_species; ++k)
         if (ctx->sp[k].loaded) CK(join_push(ctx, k));
     }
+    if (ctx->g.n_f > 0) {
+      PhaseTimer t(ctx, PH_DEPOSIT);  // the current filter, the deposit's last part
+      if (ctx->mixed) CK(launch_filter_currents<float>(ctx->g, ctx->F32, ctx->stream));
+      else CK(launch_filter_currents<double>(ctx->g, ctx->F64, ctx->stream));
+    }
     {
       PhaseTimer t(ctx, PH_ADVANCE);
       if (ctx->mixed) {
@@ -737,7 +758,7 @@ grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double out[4]) {
   grpic_status s = need_fields(ctx);
   if (s) return s;
   if (!out) return GRPIC_EINVAL;
-  double *dev = at<double>(ctx, ctx->off_rho + 3 * up((size_t)plane_size(ctx->g) * 8));
+  double *dev = at<double>(ctx, ctx->off_rho + 6 * up((size_t)plane_size(ctx->g) * 8));
   if (ctx->mixed) CK(charge_check(ctx, ctx->F32, after_step != 0, dev));
   else CK(charge_check(ctx, ctx->F64, after_step != 0, dev));
   CK(cudaMemcpyAsync(out, dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

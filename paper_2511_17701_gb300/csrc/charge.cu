@@ -3,8 +3,9 @@
 //   (J^1(i+1/2, j) - J^1(i-1/2, j)) + (J^2(i, j+1/2) - J^2(i, j-1/2))
 //       + (rho^{n+1}(i, j) - rho^n(i, j)) / dt = 0
 // at every node i in [-1, n_r + 1], j in [0, n_theta], where rho is the charge q w of every
-// live particle shared over the four nodes of its cell with linear weights, at the previous
-// and at the current position. The zigzag deposit satisfies it to rounding.
+// live massive particle shared over the four nodes of its cell with linear weights, at the
+// previous and at the current position. The zigzag deposit satisfies it to rounding. With
+// n_f current-filter passes the charge planes get the same passes as the currents.
 #include "grpic_internal.cuh"
 
 namespace {
@@ -53,12 +54,18 @@ __global__ void __launch_bounds__(TPB_Q) k_continuity(GridP g, const T *J1, cons
                                                      const double *rho_prev,
                                                      const double *rho_new,
                                                      const double *rho_abs, double *out) {
-  const int ni = g.n_r + 3, nj = g.n_th + 1;  // i in [-1, n_r + 1], j in [0, n_th]
+  // nodes i in [-1, n_r + 1], j in [0, n_th]; with n_f filter passes the zero fill beyond the
+  // stored x1 range (columns -G .. n_r + G) changes values up to n_f - G - 2 columns in from
+  // either edge, and the divergence at node i reads column i - 1, so nodes i < n_f - G and
+  // i > n_r + G + 1 - n_f are left out
+  const int ilo = max(-1, g.n_f - G_);
+  const int ihi = min(g.n_r + 1, g.n_r + G_ + 1 - g.n_f);
+  const int ni = ihi - ilo + 1, nj = g.n_th + 1;
   double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
   const double idt = 1.0 / g.dt;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)ni * nj;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t % ni) - 1, j = (int)(t / ni);
+    const int i = (int)(t % ni) + ilo, j = (int)(t / ni);
     const int64_t k = sidx(g, i, j);
     const double a = (double)J1[k], b = (double)J1[k - 1];
     const double c = (double)J2[k], d = (double)J2[k - g.NX];

@@ -77,6 +77,14 @@ def test_create_checks_the_massless_flags():
     assert B.lib().grpic_create(C.byref(c), C.byref(ctx)) == B.EINVAL and not ctx
 
 
+def test_create_requires_room_for_the_filter_inside_the_horizon():
+    # good_cfg starts 0.95 r_h: 1.65 cells inside the horizon, room for n_f = 0 only
+    assert create(dict(good_cfg(), n_filter=0))[0] == B.OK
+    assert create(dict(good_cfg(), n_filter=1))[0] == B.EINVAL
+    assert create(dict(good_cfg(), n_filter=4, r_min=0.7 * 1.4358898943540673))[0] == B.OK
+    assert create(dict(good_cfg(), n_filter=4, metric="ks0", r_min=1.0))[0] == B.OK
+
+
 def test_create_rejects_bad_species():
     assert create(good_cfg(), caps=())[0] == B.EINVAL
     assert create(good_cfg(), caps=(1,) * 9)[0] == B.EINVAL
