@@ -235,32 +235,37 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def measure(args, precision, ws, rank, local):
+def measure(args, precision, ws, rank, local, workload=None, photons=False, extra=None):
     """Time args.steps full steps of the workload at one precision; returns the pieces of
-    the JSON line (and the Sim for the end-to-end leg)."""
+    the JSON line (and the Sim for the end-to-end leg). photons: one species of massless
+    particles at the electrons' positions and momenta instead of the e+- pairs; extra:
+    further configuration (e.g. n_filter)."""
     import torch
 
     from paper_2511_17701_gb300 import FIELD_WALD, Sim
 
     device = torch.device("cuda", local)
-    cfg = W.grid_config(args.workload, sort_every=args.sort_every, tile_r=args.tile,
+    workload = workload or args.workload
+    cfg = W.grid_config(workload, sort_every=args.sort_every, tile_r=args.tile,
                         tile_theta=args.tile, precision=precision,
                         tiled_push=1 if args.tiled_push else 0, iter_tol=args.iter_tol)
-    if args.ppc:
+    if args.ppc and workload == args.workload:
         cfg["ppc"] = args.ppc
+    cfg.update(extra or {})
     pl = W.pair_plasma(cfg, seed=cfg["seed"] + 1000 * rank)
     n = pl["pos"]["i1"].size
-    sim = Sim(cfg, [n, n], device=device)
+    nsp = 1 if photons else 2
+    sim = Sim(dict(cfg, massless=[0] if photons else []), [n] * nsp, device=device)
     sim.init_metric()
     sim.init_fields(FIELD_WALD, cfg["B0"])
-    for s in range(2):
+    for s in range(nsp):
         sim.load_particles(s, pl["pos"], pl["uhat"][s], pl["w0"], pl["qm"][s], pl["qc"][s],
                            pl["density_power"])
     del pl
     for _ in range(args.warmup):
         sim.step(1)
     sim.sync()
-    n_before = sum(sim.count(s) for s in range(2))
+    n_before = sum(sim.count(s) for s in range(nsp))
     sim.timing()  # reset counters
     sim.set_timing(True)
     stream = sim.stream
@@ -277,7 +282,7 @@ def measure(args, precision, ws, rank, local):
     sim.set_timing(False)
     ms = e0.elapsed_time(e1)
     tim = sim.timing()
-    n_after = sum(sim.count(s) for s in range(2))
+    n_after = sum(sim.count(s) for s in range(nsp))
     psteps_local = 0.5 * (n_before + n_after) * args.steps
     ms_max = allreduce_max(ws, ms, device)
     psteps = allreduce_sum(ws, psteps_local, device)
@@ -286,7 +291,7 @@ def measure(args, precision, ws, rank, local):
     # the dominant kernel, timed by the library's events around each launch on its stream
     calls = max(tim["push_calls"], 1)
     kernel_ms = tim["kernel_ms"] / calls
-    parts_per_launch = 0.5 * (n_before + n_after) / 2
+    parts_per_launch = 0.5 * (n_before + n_after) / nsp
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     bpp = FP64_BYTES_PER_PARTICLE_STEP if precision == "fp64" else MIXED_BYTES_PER_PARTICLE_STEP
@@ -319,8 +324,8 @@ def measure(args, precision, ws, rank, local):
            "phase_ms_per_step": {k: tim[k] / args.steps for k in
                                  ("predict_ms", "sort_ms", "push_ms", "advance_ms")},
            "gpu_launches": tim["launches"], "clocks": clk.summary(),
-           "workload": workload_desc(args.workload, cfg, 2 * n, precision),
-           "particles": 2 * n, "psteps": psteps}
+           "workload": workload_desc(workload, cfg, nsp * n, precision),
+           "particles": nsp * n, "psteps": psteps, "timing": tim, "cfg": cfg}
     return out, sim
 
 
@@ -417,6 +422,79 @@ def run_gpu(args, ws, rank, local):
                              "error_bound": "<= 1e-5 relative per step on particle state vs "
                                             "the FP64 oracle (tests/test_gpu_mixed.py)"}
         print(json.dumps(line), flush=True)
+
+
+def run_extensions(args, ws, rank, local):
+    """The rows beyond the base path, each on the bench's grid: (1) massless particles: one
+    species of photons at the electrons' positions and momenta (16,777,216 on wald512,
+    gamma without the mass term, no EM push, no deposit), FP64 and mixed, against the e+-
+    pairs' push; (2) the current filter: the e+- workload with n_f = 4 passes (the grid
+    starts 7.3 cells inside the horizon), its share of the step, and the filter kernel's
+    HBM roofline on the 2048^2 grid (8 passes, planes larger than L2). Prints one JSON
+    line."""
+    import torch
+
+    torch.cuda.set_device(local)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    out = {"metric": "extensions: massless particles and the current filter",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup}
+    ph = {}
+    for prec in ("fp64", "mixed"):
+        pairs, sim = measure(args, prec, ws, rank, local)
+        del sim
+        phot, sim = measure(args, prec, ws, rank, local, photons=True)
+        del sim
+        torch.cuda.empty_cache()
+        ph[prec] = {"photon_steps_per_s": phot["value"],
+                    "pair_particle_steps_per_s": pairs["value"],
+                    "push_kernel_ns_per_photon": phot["roofline"]["avg_launch_ms"] * 1e6 /
+                    (phot["particles"]),
+                    "push_kernel_ns_per_pair_particle": pairs["roofline"]["avg_launch_ms"] * 1e6 /
+                    (pairs["particles"] / 2),
+                    "photon_hbm_gbs": phot["hbm_roofline"]["achieved_gbs"],
+                    "clocks": phot["clocks"], "workload": phot["workload"]}
+    out["massless"] = ph
+    # the filter on the bench workload: the step with and without it
+    base, sim = measure(args, "fp64", ws, rank, local)
+    del sim
+    filt, sim = measure(args, "fp64", ws, rank, local, extra={"n_filter": 4})
+    del sim
+    torch.cuda.empty_cache()
+    f_ms = filt["timing"]["deposit_ms"] / args.steps
+    cfg = filt["cfg"]
+    plane = (cfg["n_r"] + 5) * (cfg["n_theta"] + 5) * 8
+    out["filter_wald512"] = {
+        "n_filter": 4, "step_ms": filt["ms_per_step"], "step_ms_without": base["ms_per_step"],
+        "filter_ms_per_step": f_ms, "share_of_step": f_ms / filt["ms_per_step"],
+        "algorithmic_bytes_per_step": 6 * plane,
+        "note": "3 current planes read and written once per step (one launch runs the 4 "
+                "passes in shared memory); at 512^2 the planes (12.8 MB) stay in L2"}
+    # the filter kernel against HBM: 2048^2 planes (33.7 MB each), 8 passes in one launch
+    big, sim = measure(args, "fp64", ws, rank, local, workload="wald2048",
+                       extra={"n_filter": 8, "ppc": 1})
+    del sim
+    torch.cuda.empty_cache()
+    cfg = big["cfg"]
+    plane = (cfg["n_r"] + 5) * (cfg["n_theta"] + 5) * 8
+    f_ms = big["timing"]["deposit_ms"] / args.steps
+    gbs = 6 * plane / (f_ms * 1e-3) / 1e9
+    # FP64 operations the 8 passes need at least: per pass, cell and component one DFMA and
+    # one DADD along each of x1 and x2 (the kernel also recomputes its tiles' halos, 1.4x)
+    ops = 4 * 8 * 3 * (plane // 8) / (f_ms * 1e-3) / 1e9
+    out["filter_wald2048"] = {
+        "n_filter": 8, "filter_ms_per_step": f_ms, "algorithmic_bytes_per_launch": 6 * plane,
+        "algorithmic_fp64_ops_per_launch": 4 * 8 * 3 * (plane // 8),
+        "roofline": {"bound": "alu", "achieved": ops, "peak": FP64_PIPE_PEAK_GOPS,
+                     "unit": "G FP64-pipe op/s", "frac": ops / FP64_PIPE_PEAK_GOPS,
+                     "traffic": None,
+                     "peak_source": "nominal: 2 FP64 operations/clk/SM x 152 SMs x 2.07 GHz",
+                     "kernel": "k_filter<double> (8 passes fused in shared memory)"},
+        "hbm_roofline": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                         "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"},
+        "clocks": big["clocks"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def run_adjoint(args, ws, rank, local):
@@ -540,6 +618,9 @@ def main():
                     help="fraction of the cells whose particles the reference arm pushes")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the adjoint of the pusher over a frozen field instead")
+    ap.add_argument("--extensions", action="store_true",
+                    help="time the rows beyond the base path instead: massless particles and "
+                         "the current filter")
     ap.add_argument("--adjoint-particles", type=int, default=1 << 20)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--adjoint-ckpt", type=int, default=100)
@@ -558,6 +639,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.adjoint:
         run_adjoint(args, ws, rank, local)
+    elif args.extensions:
+        run_extensions(args, ws, rank, local)
     else:
         run_gpu(args, ws, rank, local)
     if ws > 1:

@@ -360,7 +360,8 @@ GRPIC_API grpic_status grpic_adjoint_backward(grpic_ctx *ctx, int64_t n, double 
 /* Per-phase device time of the hot path, measured with CUDA events recorded on the
  * bound stream around each phase of grpic_step / grpic_push / grpic_deposit /
  * grpic_field_step / grpic_sort while timing is enabled, and the number of kernels
- * the library launched (process-wide). */
+ * the library launched (process-wide). In grpic_step the deposit is fused into the push
+ * (push_ms) and deposit_ms holds the current filter. */
 typedef struct {
   double predict_ms, sort_ms, push_ms, deposit_ms, advance_ms;
   int64_t push_calls;   /* particle-kernel launches timed in push_ms                 */

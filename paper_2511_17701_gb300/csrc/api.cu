@@ -279,7 +279,7 @@ cudaError_t charge_check(grpic_ctx *ctx, FieldPtrsT<T> &F, bool after_step, doub
                           at<double>(ctx, ctx->off_rho + 5 * up(ps * 8))};
     const int half[3] = {0, 0, 0};
     const double par[3] = {1.0, 1.0, 1.0};
-    e = launch_filter<double>(ctx->g, a, s, half, par, 3, ctx->g.n_f, ctx->stream);
+    e = launch_filter<double>(ctx->g, a, s, half, par, 3, ctx->g.n_f, ctx->stream, nullptr);
   }
   T *const *J = after_step ? F.J0 : F.J;
   if (e == cudaSuccess)

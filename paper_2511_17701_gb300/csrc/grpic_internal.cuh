@@ -313,12 +313,14 @@ template <typename T>
 cudaError_t launch_predict(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st);
 template <typename T>
 cudaError_t launch_advance(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st);
-// current filter (filter.cu): n passes on n_comp planes a (scratch s), and the n_f passes on J
+// current filter (filter.cu): n passes on n_comp planes a (scratch s; in_s: see filter.cu),
+// and the n_f passes on J (may trade the J and E plane pointers of F)
 template <typename T>
 cudaError_t launch_filter(const GridP &g, T *const a[3], T *const s[3], const int half[3],
-                          const double parity[3], int n_comp, int n, cudaStream_t st);
+                          const double parity[3], int n_comp, int n, cudaStream_t st,
+                          bool *in_s);
 template <typename T>
-cudaError_t launch_filter_currents(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st);
+cudaError_t launch_filter_currents(const GridP &g, FieldPtrsT<T> &F, cudaStream_t st);
 template <typename T>
 cudaError_t launch_zero(T *p, int64_t n, cudaStream_t st);
 
