@@ -26,6 +26,7 @@ G = 2
  BN1, BN2, BN3, BI1, BI2, BI3, DI1, DI2, DI3, JA1, JA2, JA3, NPLANES) = range(31)
 
 FIELD_ZERO, FIELD_WALD, FIELD_VERTICAL = 0, 1, 2
+FIELD_MONOPOLE = 4  # A_phi = -B0 cos(theta), the BZ monopole test (Sec. 4.5)
 
 
 def build(force: bool = False) -> str:

@@ -41,6 +41,18 @@ CONFIGS = {
     "wald64f": dict(metric="ks", a=_A, n_r=64, n_theta=64, r_min=0.7 * horizon_radius(_A),
                     r_max=10.0, ppc=8, theta_T=0.3, density_power=0.0, steps=200, cfl=0.5,
                     seed=4, B0=1.0, r_absorb=9.0, n_filter=4),
+    # the BZ monopole test (Sec. 4.5): a = 0.2, r in [r_g, 10 r_g], absorbing layer 1 r_g
+    # thick, 1024^2, pairs with theta_T = 0.5 and density ~ r^-2, fiducial rho0 = 5e-5 and
+    # d0 = 2.5e-3 r_g (sigma0 = 2500); 45 ppc per species (90 per cell, the paper's
+    # performance setting)
+    "bz1024": dict(metric="ks", a=0.2, n_r=1024, n_theta=1024, r_min=1.0, r_max=10.0, ppc=45,
+                   theta_T=0.5, density_power=2.0, steps=200, cfl=0.5, seed=5, B0=1.0,
+                   r_absorb=9.0, rho0=5e-5, d0=2.5e-3, field="monopole"),
+    # the pusher benchmark of Sec. 3.5: the monopole test on a 2048^2 log-r grid with 90
+    # particles per cell (45 per species, 377,487,360 particles)
+    "bz2048": dict(metric="ks", a=0.2, n_r=2048, n_theta=2048, r_min=1.0, r_max=10.0, ppc=45,
+                   theta_T=0.5, density_power=2.0, steps=100, cfl=0.5, seed=6, B0=1.0,
+                   r_absorb=9.0, rho0=5e-5, d0=2.5e-3, field="monopole"),
     # 2048^2, r_max = 200, 16 ppc per species (134,217,728 particles), density ~ 1/r, 500 steps
     "wald2048": dict(metric="ks", a=_A, n_r=2048, n_theta=2048, r_min=_RMIN, r_max=200.0,
                      ppc=16, theta_T=1.0, density_power=1.0, steps=500, cfl=0.5, seed=3,
@@ -110,8 +122,9 @@ def pair_plasma(cfg: dict, seed: int | None = None, cells: np.ndarray | None = N
     n = pos["i1"].size
     ue = maxwell_juttner(rng, n, cfg["theta_T"])
     up = maxwell_juttner(rng, n, cfg["theta_T"])
-    qe, ce = species_coefficients(-1.0)
-    qp, cp = species_coefficients(+1.0)
+    rho0, d0 = cfg.get("rho0", RHO0), cfg.get("d0", D0)
+    qe, ce = species_coefficients(-1.0, rho0, d0)
+    qp, cp = species_coefficients(+1.0, rho0, d0)
     return {"pos": pos, "uhat": [ue, up], "w0": np.full(n, 1.0 / cfg["ppc"]),
             "qm": [qe, qp], "qc": [ce, cp], "density_power": cfg.get("density_power", 0.0)}
 
