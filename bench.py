@@ -168,12 +168,28 @@ PRECISION_DESC = {"fp64": "FP64",
                            "within 4 cells of the horizon and the axes)"}
 
 
+def field_kind(cfg, lib_side=True):
+    """The initial field of a workload: Wald (default) or the BZ monopole."""
+    if cfg.get("field") == "monopole":
+        if lib_side:
+            from paper_2511_17701_gb300 import FIELD_MONOPOLE
+            return FIELD_MONOPOLE
+        from oracle import oracle as O
+        return O.FIELD_MONOPOLE
+    if lib_side:
+        from paper_2511_17701_gb300 import FIELD_WALD
+        return FIELD_WALD
+    from oracle import oracle as O
+    return O.FIELD_WALD
+
+
 def workload_desc(name, cfg, n_total, precision="fp64"):
-    return ("%s: Kerr a=%g Wald B0=%g, %dx%d log-r grid, r in [0.95 r_h, %g], e+- pairs %d "
+    field = ("monopole A_phi=-B0 cos(theta)" if cfg.get("field") == "monopole" else "Wald")
+    return ("%s: Kerr a=%g, %s B0=%g, %dx%d log-r grid, r in [%.4g, %g], e+- pairs %d "
             "per cell per species (%d particles), Maxwell-Juttner theta_T=%g, density ~ r^-%g, "
-            "%s" % (name, cfg["a"], cfg["B0"], cfg["n_r"], cfg["n_theta"], cfg["r_max"],
-                    cfg["ppc"], n_total, cfg["theta_T"], cfg.get("density_power", 0.0),
-                    PRECISION_DESC[precision]))
+            "%s" % (name, cfg["a"], field, cfg["B0"], cfg["n_r"], cfg["n_theta"], cfg["r_min"],
+                    cfg["r_max"], cfg["ppc"], n_total, cfg["theta_T"],
+                    cfg.get("density_power", 0.0), PRECISION_DESC[precision]))
 
 
 def oracle_workload(cfg, frac, seed=99):
@@ -184,7 +200,7 @@ def oracle_workload(cfg, frac, seed=99):
     if frac < 1.0:
         cells = W.random_cells(cfg, max(1, int(cfg["n_r"] * cfg["n_theta"] * frac)), seed)
     osim = O.OracleSim(cfg)
-    osim.init_fields(O.FIELD_WALD, cfg["B0"])
+    osim.init_fields(field_kind(cfg, lib_side=False), cfg["B0"])
     pl = W.pair_plasma(cfg, cells=cells)
     for s in range(2):
         osim.add_species(pl["pos"], pl["uhat"][s], pl["w0"], pl["qm"][s], pl["qc"][s],
@@ -235,6 +251,9 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+_PLASMA = {}
+
+
 def measure(args, precision, ws, rank, local, workload=None, photons=False, extra=None):
     """Time args.steps full steps of the workload at one precision; returns the pieces of
     the JSON line (and the Sim for the end-to-end leg). photons: one species of massless
@@ -242,7 +261,7 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
     further configuration (e.g. n_filter)."""
     import torch
 
-    from paper_2511_17701_gb300 import FIELD_WALD, Sim
+    from paper_2511_17701_gb300 import Sim
 
     device = torch.device("cuda", local)
     workload = workload or args.workload
@@ -252,16 +271,21 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
     if args.ppc and workload == args.workload:
         cfg["ppc"] = args.ppc
     cfg.update(extra or {})
-    pl = W.pair_plasma(cfg, seed=cfg["seed"] + 1000 * rank)
+    # the seeded plasma of a workload is drawn once per process (the two precisions and the
+    # photon run share it: drawing 377 M particles takes a minute and a half)
+    key = (workload, cfg["seed"] + 1000 * rank, cfg["ppc"], cfg["n_r"], cfg["n_theta"])
+    if key not in _PLASMA:
+        _PLASMA.clear()
+        _PLASMA[key] = W.pair_plasma(cfg, seed=cfg["seed"] + 1000 * rank)
+    pl = _PLASMA[key]
     n = pl["pos"]["i1"].size
     nsp = 1 if photons else 2
     sim = Sim(dict(cfg, massless=[0] if photons else []), [n] * nsp, device=device)
     sim.init_metric()
-    sim.init_fields(FIELD_WALD, cfg["B0"])
+    sim.init_fields(field_kind(cfg), cfg["B0"])
     for s in range(nsp):
         sim.load_particles(s, pl["pos"], pl["uhat"][s], pl["w0"], pl["qm"][s], pl["qc"][s],
                            pl["density_power"])
-    del pl
     for _ in range(args.warmup):
         sim.step(1)
     sim.sync()
@@ -282,6 +306,19 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
     sim.set_timing(False)
     ms = e0.elapsed_time(e1)
     tim = sim.timing()
+    # the pusher alone (grpic_push: steps 1-11 of Sec. 3.1, no deposit), one launch per
+    # species after the timed steps, the component the paper times per particle (Sec. 3.5)
+    push_ms, push_n = 0.0, 0
+    for sp in range(nsp):
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cnt = sim.count(sp)
+        torch.cuda.synchronize(device)
+        p0.record(stream)
+        sim.push(sp)
+        p1.record(stream)
+        torch.cuda.synchronize(device)
+        push_ms += p0.elapsed_time(p1)
+        push_n += cnt
     n_after = sum(sim.count(s) for s in range(nsp))
     psteps_local = 0.5 * (n_before + n_after) * args.steps
     ms_max = allreduce_max(ws, ms, device)
@@ -325,7 +362,8 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
                                  ("predict_ms", "sort_ms", "push_ms", "advance_ms")},
            "gpu_launches": tim["launches"], "clocks": clk.summary(),
            "workload": workload_desc(workload, cfg, nsp * n, precision),
-           "particles": nsp * n, "psteps": psteps, "timing": tim, "cfg": cfg}
+           "particles": nsp * n, "psteps": psteps, "timing": tim, "cfg": cfg,
+           "pusher_ns_per_particle": push_ms * 1e6 / max(push_n, 1)}
     return out, sim
 
 
@@ -408,8 +446,14 @@ def run_gpu(args, ws, rank, local):
                            "parallelism": "replica per GPU" if ws > 1 else "1 GPU"},
                 "roofline": main["roofline"], "hbm_roofline": main["hbm_roofline"],
                 "phase_ms_per_step": main["phase_ms_per_step"],
+                "pusher_ns_per_particle": main["pusher_ns_per_particle"],
                 "gpu_launches": main["gpu_launches"], "e2e": e2e, "cpu_baseline": cpu,
                 "clocks": main["clocks"]}
+        if args.workload == "bz2048":
+            line["paper_context"] = {
+                "pusher_ns_per_particle": 6.2, "hardware": "1x A100, precision not stated",
+                "workload": "BZ monopole test, 2048^2 log-r mesh, 90 particles per cell "
+                            "(Sec. 3.5)"}
         if len(precisions) == 2:
             m = res["mixed"]
             line["mixed"] = {"value": m["value"], "unit": "particle-steps/s",
@@ -418,6 +462,7 @@ def run_gpu(args, ws, rank, local):
                              "workload": m["workload"], "roofline": m["roofline"],
                              "hbm_roofline": m["hbm_roofline"],
                              "phase_ms_per_step": m["phase_ms_per_step"],
+                             "pusher_ns_per_particle": m["pusher_ns_per_particle"],
                              "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
                              "error_bound": "<= 1e-5 relative per step on particle state vs "
                                             "the FP64 oracle (tests/test_gpu_mixed.py)"}

@@ -69,7 +69,9 @@ typedef enum {
   GRPIC_FIELD_ZERO = 0,     /* all fields zero                                    */
   GRPIC_FIELD_WALD = 1,     /* Wald vacuum field, Eq. (Wald), Sec. 4.1.2          */
   GRPIC_FIELD_VERTICAL = 2, /* its zero-spin limit, A_phi = B0 r^2 sin^2(theta)/2 */
-  GRPIC_FIELD_USER = 3      /* caller wrote em (B, D); the library derives the rest */
+  GRPIC_FIELD_USER = 3,     /* caller wrote em (B, D); the library derives the rest */
+  GRPIC_FIELD_MONOPOLE = 4  /* magnetic monopole of the BZ test, A_phi = -B0 cos(theta),
+                               B^r = B0 sin(theta)/sqrt(h), Sec. 4.5                 */
 } grpic_field_kind;
 typedef enum { GRPIC_PREDICT = 0, GRPIC_ADVANCE = 1 } grpic_field_phase;
 
@@ -232,8 +234,8 @@ GRPIC_API grpic_status grpic_plane_ptr(grpic_ctx *ctx, int plane, void **out);
 
 /* Conserved energy and angular momentum per unit mass of each particle of a species
  * (Sec. 2.3): E = -u_0 - (q/m) A_0, L = u_3 + (q/m) A_3 with u_0 = -alpha gamma + beta^1 u_1,
- * A of the stationary field `kind` (GRPIC_FIELD_WALD or _VERTICAL, amplitude B0; ZERO gives
- * the geodesic values), evaluated in FP64 at the midpoint of the previous and current
+ * A of the stationary field `kind` (GRPIC_FIELD_WALD, _VERTICAL or _MONOPOLE, amplitude B0;
+ * ZERO gives the geodesic values), evaluated in FP64 at the midpoint of the previous and current
  * positions (the velocity time level, as Sec. 4.1 does). E and L are device arrays of at
  * least the species' count. */
 GRPIC_API grpic_status grpic_invariants(grpic_ctx *ctx, int species, int kind, double B0,
@@ -325,7 +327,7 @@ GRPIC_API grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double
  * State layout (device, caller-owned): [6][n] doubles, rows x1, x2 (absolute code
  * coordinates), phi, u_1, u_2, u_3 (covariant momenta per unit mass). The fields are the
  * em planes (B, D) times b0 / field_b0, where field_b0 is the amplitude given to
- * grpic_init_fields (1 for GRPIC_FIELD_USER); the Wald and vertical fields are linear in B0,
+ * grpic_init_fields (1 for GRPIC_FIELD_USER); the Wald, vertical and monopole fields are linear in B0,
  * so b0 is the field amplitude. Both implicit substeps iterate to an exact repeat of the
  * iterate, at most n_iter times. A particle whose step would leave 0 <= x1 < n_r,
  * 0 <= x2 <= n_theta (the horizon layer, the outer edge or an axis, where the boundary rules

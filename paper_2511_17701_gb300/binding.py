@@ -19,7 +19,7 @@ MAX_SPECIES = 8
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ECAPACITY, ENONFINITE = range(7)
 FP64, MIXED = 0, 1
 METRIC_KS0, METRIC_KS = 0, 1
-FIELD_ZERO, FIELD_WALD, FIELD_VERTICAL, FIELD_USER = range(4)
+FIELD_ZERO, FIELD_WALD, FIELD_VERTICAL, FIELD_USER, FIELD_MONOPOLE = range(5)
 PREDICT, ADVANCE = 0, 1
 (B1, B2, B3, D1, D2, D3, B01, B02, B03, D01, D02, D03, J1, J2, J3, J01, J02, J03,
  BN1, BN2, BN3, BI1, BI2, BI3, DI1, DI2, DI3, NPLANES) = range(28)

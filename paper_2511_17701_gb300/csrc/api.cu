@@ -493,7 +493,8 @@ grpic_status grpic_init_fields(grpic_ctx *ctx, int kind, double B0) {
   grpic_status s = need_bound(ctx);
   if (s) return s;
   if (!ctx->metric_ready) return fail(ctx, GRPIC_ESTATE, "metric not initialised");
-  if (kind < GRPIC_FIELD_ZERO || kind > GRPIC_FIELD_USER) return fail(ctx, GRPIC_EINVAL, "bad field kind");
+  if (kind < GRPIC_FIELD_ZERO || kind > GRPIC_FIELD_MONOPOLE)
+    return fail(ctx, GRPIC_EINVAL, "bad field kind");
   if (ctx->mixed) {
     if (kind != GRPIC_FIELD_USER) CK(launch_init_fields<float>(ctx->g, ctx->F32, kind, B0, ctx->stream));
     CK(launch_field_finish_init<float>(ctx->g, ctx->F32, kind == GRPIC_FIELD_USER, ctx->stream));
@@ -502,7 +503,8 @@ grpic_status grpic_init_fields(grpic_ctx *ctx, int kind, double B0) {
     CK(launch_field_finish_init<double>(ctx->g, ctx->F64, kind == GRPIC_FIELD_USER, ctx->stream));
   }
   ctx->fields_ready = true;
-  ctx->field_b0 = (kind == GRPIC_FIELD_WALD || kind == GRPIC_FIELD_VERTICAL) ? B0 : 1.0;
+  ctx->field_b0 = (kind == GRPIC_FIELD_WALD || kind == GRPIC_FIELD_VERTICAL ||
+                   kind == GRPIC_FIELD_MONOPOLE) ? B0 : 1.0;
   ctx->step = 0;
   return GRPIC_OK;
 }

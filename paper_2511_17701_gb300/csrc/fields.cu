@@ -96,6 +96,17 @@ __device__ double inv_sqrt_h(const GridP &g, double x1, double x2) {
 // sin^2(b) - sin^2(a) = sin(b - a) sin(b + a) = -(cos^2(b) - cos^2(a)),
 //   dA_1 = -(B0/2) a f D (1 + 2 M r (r^2 - a^2) / (Sigma_a Sigma_b)), D = sin(dth) sin((2j+1) dth);
 // the plain difference loses ~1/dth^2 of its digits next to the axes (A_1 ~ theta^2 there).
+// A_3(x1, j + 1) - A_3(x1, j) for the discrete curl that gives B^1; for the monopole,
+// -B0 (cos((j+1) dth) - cos(j dth)) = 2 B0 sin((j + 1/2) dth) sin(dth / 2) in product form
+// (the plain difference of the cosines loses ~1/dth^2 of its digits next to the axes)
+__device__ double dA3_theta(const GridP &g, int kind, double B0, int i, int j) {
+  if (kind == GRPIC_FIELD_MONOPOLE) return 2.0 * B0 * sin((j + 0.5) * g.dth) * sin(0.5 * g.dth);
+  Pot pa, pb;
+  potential(g, kind, B0, i, j, false, pa);
+  potential(g, kind, B0, i, j + 1, false, pb);
+  return pb.A3 - pa.A3;
+}
+
 __device__ double dA1_theta(const GridP &g, int kind, double B0, double x1, int j) {
   if (kind != GRPIC_FIELD_WALD) return 0.0;  // the vertical field has A_1 = 0
   const double a = g.a, M = g.M;
@@ -117,9 +128,7 @@ __global__ void k_init_fields(GridP g, FieldPtrsT<T> F, int kind, double B0) {
     const bool axis = (j == 0 || j == g.n_th);
     Pot pa, pb;
     if (j < g.n_th) {
-      potential(g, kind, B0, i, j, false, pa);
-      potential(g, kind, B0, i, j + 1, false, pb);
-      F.B[0][k] = (T)((pb.A3 - pa.A3) * inv_sqrt_h(g, i, j + 0.5));
+      F.B[0][k] = (T)(dA3_theta(g, kind, B0, i, j) * inv_sqrt_h(g, i, j + 0.5));
       F.B[2][k] = (T)(-dA1_theta(g, kind, B0, i + 0.5, j) * inv_sqrt_h(g, i + 0.5, j + 0.5));
       double d;
       d_from_potential(g, kind, B0, i, j + 0.5, 1, d);
@@ -460,7 +469,7 @@ cudaError_t launch_init_fields(const GridP &g, const FieldPtrsT<T> &F, int kind,
     launch_zero(F.B[c], ps, st);
     launch_zero(F.D[c], ps, st);
   }
-  if (kind == GRPIC_FIELD_WALD || kind == GRPIC_FIELD_VERTICAL) {
+  if (kind == GRPIC_FIELD_WALD || kind == GRPIC_FIELD_VERTICAL || kind == GRPIC_FIELD_MONOPOLE) {
     const int64_t n = (int64_t)(g.n_r + 2 * G_ + 1) * (g.n_th + 1);
     k_init_fields<T><<<blocks_for(n), TPB, 0, st>>>(g, F, kind, B0);
     COUNT_LAUNCH(1);

@@ -169,6 +169,12 @@ __device__ __forceinline__ void potential(const GridP &g, int kind, double B0, d
     p.d1A3 = f * B0 * r * s2;
     return;
   }
+  if (kind == GRPIC_FIELD_MONOPOLE) {  // A_phi = -B0 cos(theta), Sec. 4.5
+    p.A0 = 0.0; p.A1 = 0.0; p.A3 = -B0 * c;
+    p.d1A0 = p.d2A0 = p.d2A1 = 0.0;
+    p.d1A3 = 0.0;
+    return;
+  }
   const double Sig = r * r + a2 * c * c, Del = r * r - 2.0 * M * r + a2;
   const double A = (r * r + a2) * (r * r + a2) - a2 * Del * s2;
   const double z = 2.0 * M * r / Sig;

@@ -1032,7 +1032,7 @@ __global__ void k_invariants(GridP g, SpeciesDevT<T> s, int kind, double B0, dou
     const double u0 = -m.alpha * gamma_of(m, u, s.m2) + m.beta1 * u[0];
     Pot p;
     p.A0 = p.A3 = 0.0;
-    if (kind == GRPIC_FIELD_WALD || kind == GRPIC_FIELD_VERTICAL)
+    if (kind == GRPIC_FIELD_WALD || kind == GRPIC_FIELD_VERTICAL || kind == GRPIC_FIELD_MONOPOLE)
       potential(g, kind, B0, x1, x2, false, p);
     E[k] = -u0 - s.qm * p.A0;
     Lout[k] = u[2] + s.qm * p.A3;

@@ -25,7 +25,7 @@ def torch_cuda():
     return torch
 
 
-CFG = dict(metric="ks", a=0.9, n_r=37, n_theta=23, r_min=1.3641, r_max=12.0, dt=0.01,
+CFG = dict(metric="ks", a=0.9, n_r=37, n_theta=23, r_min=1.3, r_max=12.0, dt=0.01,
            tile_r=8, tile_theta=4)
 
 
