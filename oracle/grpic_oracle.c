@@ -859,6 +859,100 @@ void ora_load(const ora_params *p, ora_species *s, const double *uh1, const doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* Pair injection of the BZ monopole test (Sec. 4.5): plasma is injected where */
+/* the local magnetization sigma = B_i B^i / (4 pi n m) exceeds sigma_th. The  */
+/* paper gives no more. Reading: per cell (i1 in [0, n_r), i2 in [0, n_th)),   */
+/* B at the cell centre from the em planes (B^1 and B^2 averaged over the two  */
+/* faces, B^3 as stored), B_i B^i = h_ij B^i B^j with h at the centre; n the   */
+/* summed |w| of the live particles of both species in the cell divided by     */
+/* sqrt(h) at the centre; sigma = sigma0 (B_i B^i / B0^2) / n in units of the  */
+/* fiducial density. Where sigma > sigma_th, one e- e+ pair is added at one    */
+/* point of the cell with weights w = dn sqrt(h_centre) / 2 each, dn the       */
+/* density that brings sigma down to sigma_th. Offsets and tetrad-frame        */
+/* momenta come from a pool of random draws (8 per pair: dx1, dx2, e- u^, e+   */
+/* u^), used in cell order (i1 fastest) from entry pool_offset on, cyclically. */
+/* Co-located opposite charges of equal weight: the charge density does not   */
+/* change.                                                                     */
+/* ------------------------------------------------------------------------ */
+static void cell_state(const ora_params *p, const double *F, const ora_species *se,
+                       const ora_species *sp, double *n_cell, double *b2, double *sqrt_hc) {
+  const int NX = NX_of(p);
+  const int64_t NC = (int64_t)p->n_r * p->n_th;
+  const double *B1 = F + ORA_B1 * plane_size(p), *B2 = F + ORA_B2 * plane_size(p);
+  const double *B3 = F + ORA_B3 * plane_size(p);
+  memset(n_cell, 0, sizeof(double) * NC);
+  const ora_species *both[2] = {se, sp};
+  for (int q = 0; q < 2; ++q)
+    for (int64_t k = 0; k < both[q]->n; ++k) {
+      if (both[q]->tag[k] != 1) continue;
+      int i = both[q]->i1[k], j = both[q]->i2[k];
+      if (i < 0 || i >= p->n_r || j < 0 || j >= p->n_th) continue;
+      n_cell[(int64_t)j * p->n_r + i] += fabs(both[q]->w[k]);
+    }
+  for (int j = 0; j < p->n_th; ++j)
+    for (int i = 0; i < p->n_r; ++i) {
+      const int64_t c = (int64_t)j * p->n_r + i;
+      ora_metric m;
+      metric_eval(p, i + 0.5, j + 0.5, 0, 0, &m);
+      const double b1 = 0.5 * (AT(B1, i, j) + AT(B1, i + 1, j));
+      const double bb2 = 0.5 * (AT(B2, i, j) + AT(B2, i, j + 1));
+      const double b3 = AT(B3, i, j);
+      b2[c] = m.h11 * b1 * b1 + m.h22 * bb2 * bb2 + m.h33 * b3 * b3 + 2.0 * m.h13 * b1 * b3;
+      sqrt_hc[c] = m.sqrt_h;
+      n_cell[c] /= m.sqrt_h;
+    }
+}
+
+/* the cell densities and B_i B^i the injection sees (for the pins) */
+void ora_cell_state(const ora_params *p, const double *F, const ora_species *se,
+                    const ora_species *sp, double *n_cell, double *b2) {
+  const int64_t NC = (int64_t)p->n_r * p->n_th;
+  double *sq = malloc(sizeof(double) * NC);
+  cell_state(p, F, se, sp, n_cell, b2, sq);
+  free(sq);
+}
+
+/* injects into se and sp (room for cap particles each); returns the pairs added */
+int64_t ora_inject(const ora_params *p, const double *F, ora_species *se, ora_species *sp,
+                   double sigma0, double sigma_th, double B0, const double *pool,
+                   int64_t pool_n, int64_t pool_offset, int64_t cap) {
+  const int64_t NC = (int64_t)p->n_r * p->n_th;
+  double *n_cell = malloc(sizeof(double) * NC), *b2 = malloc(sizeof(double) * NC);
+  double *sq = malloc(sizeof(double) * NC);
+  cell_state(p, F, se, sp, n_cell, b2, sq);
+  /* pairs that fit: the first ones in cell order */
+  const int64_t room = cap - (se->n > sp->n ? se->n : sp->n);
+  int64_t added = 0;
+  for (int j = 0; j < p->n_th; ++j)
+    for (int i = 0; i < p->n_r; ++i) {
+      const int64_t c = (int64_t)j * p->n_r + i;
+      /* sigma > sigma_th without dividing by n (n may be 0) */
+      if (!(sigma0 * b2[c] > sigma_th * B0 * B0 * n_cell[c])) continue;
+      if (added >= room) continue;
+      const double dn = sigma0 * b2[c] / (B0 * B0 * sigma_th) - n_cell[c];
+      const double *r = pool + 8 * ((pool_offset + added) % pool_n);
+      ora_species *both[2] = {se, sp};
+      for (int q = 0; q < 2; ++q) {
+        ora_species *s = both[q];
+        const int64_t k = s->n++;
+        s->i1[k] = i; s->i2[k] = j; s->dx1[k] = r[0]; s->dx2[k] = r[1];
+        ora_metric m;
+        metric_eval(p, i + r[0], j + r[1], 1, 0, &m);
+        double uh[3] = {r[2 + 3 * q], r[3 + 3 * q], r[4 + 3 * q]}, u[3];
+        hat_to_cov(&m, uh, u);
+        s->u1[k] = u[0]; s->u2[k] = u[1]; s->u3[k] = u[2];
+        s->w[k] = 0.5 * dn * sq[c];
+        s->phi[k] = 0.0;
+        s->tag[k] = 1;
+        s->i1p[k] = i; s->i2p[k] = j; s->dx1p[k] = r[0]; s->dx2p[k] = r[1];
+      }
+      ++added;
+    }
+  free(n_cell); free(b2); free(sq);
+  return added;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sort (added by this implementation, not in the paper): stable sort of the   */
 /* particles by tile-major cell key, particles not alive last and dropped.     */
 /* key = tile * (tr*tt) + (i2 % tt) * tr + (i1 % tr), tile = (i2/tt) * ntr +   */
@@ -1017,4 +1111,4 @@ void ora_push_frozen_cs(const ora_params *p, const double *F, double scale_re, d
   }
 }
 
-int ora_version(void) { return 4; }
+int ora_version(void) { return 5; }

@@ -114,6 +114,10 @@ def lib():
                                C.c_int64, C.POINTER(C.c_int64)]
         L.ora_filter_plane.argtypes = [P, _PD, C.c_int, C.c_double, C.c_int]
         L.ora_filter_currents.argtypes = [P, _PD]
+        L.ora_cell_state.argtypes = [P, _PD, PP, PP, _PD, _PD]
+        L.ora_inject.argtypes = [P, _PD, PP, PP, C.c_double, C.c_double, C.c_double, _PD,
+                                 C.c_int64, C.c_int64, C.c_int64]
+        L.ora_inject.restype = C.c_int64
         L.ora_push_frozen.argtypes = [P, _PD, C.c_double, C.c_double, C.c_int, C.c_int64, _PD]
         L.ora_push_frozen_cs.argtypes = [P, _PD, C.c_double, C.c_double, C.c_double, C.c_int,
                                          C.c_int64, _PD, _PD]
@@ -226,6 +230,14 @@ class OracleSpecies:
     def view(self) -> dict:
         return {k: v[: self.n] for k, v in self.a.items()}
 
+    def reserve(self, cap: int):
+        """Grow the arrays to hold at least cap particles."""
+        if cap > len(self.a["i1"]):
+            for k, v in self.a.items():
+                g = np.zeros(cap, dtype=v.dtype)
+                g[: len(v)] = v
+                self.a[k] = g
+
     def copy(self) -> "OracleSpecies":
         o = OracleSpecies(self.n, self.qm, self.qc, self.massless)
         o.a = {k: v.copy() for k, v in self.a.items()}
@@ -326,6 +338,31 @@ class OracleSim:
 
     def advance(self):
         lib().ora_field_advance(C.byref(self.p), _dp(self.F))
+
+    def cell_state(self, se=0, sp=1):
+        """(n, B_i B^i) per cell [n_th][n_r] as the pair injection sees them."""
+        nc = np.zeros((self.cfg["n_theta"], self.cfg["n_r"]))
+        b2 = np.zeros_like(nc)
+        a, b = self.species[se].struct(), self.species[sp].struct()
+        lib().ora_cell_state(C.byref(self.p), _dp(self.F), C.byref(a), C.byref(b), _dp(nc),
+                             _dp(b2))
+        return nc, b2
+
+    def inject(self, sigma0, sigma_th, B0, pool, pool_offset=0, cap=None, se=0, sp=1):
+        """Pair injection where sigma > sigma_th (pool: [pool_n, 8] random draws); returns
+        the pairs added. cap: room per species (default: every cell can take one pair)."""
+        pool = np.ascontiguousarray(pool, dtype=np.float64)
+        ncell = self.cfg["n_r"] * self.cfg["n_theta"]
+        if cap is None:
+            cap = max(self.species[se].n, self.species[sp].n) + ncell
+        for k in (se, sp):
+            self.species[k].reserve(cap)
+        a, b = self.species[se].struct(), self.species[sp].struct()
+        added = lib().ora_inject(C.byref(self.p), _dp(self.F), C.byref(a), C.byref(b),
+                                 float(sigma0), float(sigma_th), float(B0), _dp(pool),
+                                 pool.shape[0], int(pool_offset), int(cap))
+        self.species[se].n, self.species[sp].n = int(a.n), int(b.n)
+        return int(added)
 
     def sort(self, si: int, tr: int, tt: int):
         s = self.species[si]

@@ -47,7 +47,8 @@ CONFIGS = {
     # performance setting)
     "bz1024": dict(metric="ks", a=0.2, n_r=1024, n_theta=1024, r_min=1.0, r_max=10.0, ppc=45,
                    theta_T=0.5, density_power=2.0, steps=200, cfl=0.5, seed=5, B0=1.0,
-                   r_absorb=9.0, rho0=5e-5, d0=2.5e-3, field="monopole"),
+                   r_absorb=9.0, rho0=5e-5, d0=2.5e-3, field="monopole", sigma0=2500.0,
+                   sigma_th=2000.0, theta_inj=0.5),
     # the pusher benchmark of Sec. 3.5: the monopole test on a 2048^2 log-r grid with 90
     # particles per cell (45 per species, 377,487,360 particles)
     "bz2048": dict(metric="ks", a=0.2, n_r=2048, n_theta=2048, r_min=1.0, r_max=10.0, ppc=45,
@@ -127,6 +128,20 @@ def pair_plasma(cfg: dict, seed: int | None = None, cells: np.ndarray | None = N
     qp, cp = species_coefficients(+1.0, rho0, d0)
     return {"pos": pos, "uhat": [ue, up], "w0": np.full(n, 1.0 / cfg["ppc"]),
             "qm": [qe, qp], "qc": [ce, cp], "density_power": cfg.get("density_power", 0.0)}
+
+
+def injection_pool(cfg: dict, n: int, seed: int) -> np.ndarray:
+    """Random draws for pair injection, [n, 8]: cell offsets dx1, dx2 (uniform), then the
+    tetrad-frame momenta of the electron and of the positron (Maxwell-Juttner at the
+    workload's injection temperature, theta_inj, else theta_T)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    th = cfg.get("theta_inj", cfg["theta_T"])
+    out = np.empty((n, 8))
+    out[:, 0] = rng.random(n)
+    out[:, 1] = rng.random(n)
+    out[:, 2:5] = maxwell_juttner(rng, n, th).T
+    out[:, 5:8] = maxwell_juttner(rng, n, th).T
+    return out
 
 
 def random_cells(cfg: dict, n_cells: int, seed: int) -> np.ndarray:
