@@ -168,6 +168,8 @@ typedef struct {
   int64_t reflections;   /* axis reflections, Sec. 3.3.3                           */
   int64_t nonfinite;     /* particles dropped for non-finite or runaway state       */
   int64_t alive[GRPIC_MAX_SPECIES];
+  int64_t injected;      /* pairs added by grpic_inject                             */
+  int64_t inject_dropped; /* pairs grpic_inject found no room for                   */
 } grpic_diag;
 
 /* --- set-up ----------------------------------------------------------------------- */
@@ -298,6 +300,28 @@ GRPIC_API grpic_status grpic_sort_permutation_noalloc(int n_r, int n_theta, int 
                                                       int64_t n, uint32_t *perm,
                                                       int64_t *n_alive, void *stream);
 
+/* --- pair injection ----------------------------------------------------------------- */
+
+/* Pair injection of the BZ monopole test (Sec. 4.5: plasma is injected wherever the local
+ * magnetization exceeds sigma_th). Per cell (i1 in [0, n_r), i2 in [0, n_theta)): B at the
+ * cell centre from the em planes (B^1, B^2 averaged over the two faces, B^3 as stored),
+ * B_i B^i = h_ij B^i B^j with h at the centre, n = (sum of |w| of the live particles of both
+ * species in the cell) / sqrt(h) at the centre, sigma = sigma0 (B_i B^i / B0^2) / n. Where
+ * sigma > sigma_th one pair is added at one point of the cell: a particle of species_e and
+ * one of species_p, co-located, each of weight dn sqrt(h_centre) / 2 with dn the density
+ * that brings sigma to sigma_th. pool: device-accessible FP64 [pool_n][8] random draws per
+ * pair (dx1, dx2 in [0, 1); the tetrad-frame momenta u^ of the species_e and species_p
+ * particle), used cyclically in cell order (i1 fastest) from a cursor the library keeps:
+ * pool_offset >= 0 sets the cursor first, < 0 continues. The k-th pair goes to slot
+ * n + k of both species (n each species' count before the call): where the room of either
+ * species runs out, the remaining pairs are dropped and counted (grpic_diag). Counts stay
+ * on the device; no synchronisation. The new particles are unsorted (the next sort orders
+ * them). Errors: GRPIC_EINVAL (same or massless species, null pool, pool_n <= 0, sigma0 or
+ * sigma_th <= 0, B0 = 0), GRPIC_ESTATE (fields not initialised). */
+GRPIC_API grpic_status grpic_inject(grpic_ctx *ctx, int species_e, int species_p, double sigma0,
+                                    double sigma_th, double B0, const double *pool,
+                                    int64_t pool_n, int64_t pool_offset);
+
 /* --- charge conservation ------------------------------------------------------------ */
 
 /* The discrete continuity equation of the deposit (Sec. 3.2, Eq. charge-conservation-disc),
@@ -371,6 +395,7 @@ typedef struct {
   double kernel_ms;     /* the main push kernel alone (FP64: k_push; mixed: the FP32
                            kernel, which runs beside the guard kernels), summed over
                            push_calls launches                                        */
+  double inject_ms;     /* grpic_inject                                               */
 } grpic_timing;
 
 /* Enables (1) or disables (0) the per-phase events. Off by default. */

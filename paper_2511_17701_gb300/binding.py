@@ -31,7 +31,7 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_get_diagnostics", "grpic_set_timing", "grpic_get_timing", "grpic_last_error",
            "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants",
            "grpic_adjoint_forward", "grpic_adjoint_backward", "grpic_charge_check",
-           "grpic_config_bytes"]
+           "grpic_config_bytes", "grpic_inject"]
 
 
 ADJOINT_SCRATCH_PER_STEP = 36  # doubles per particle and step of grpic_adjoint_backward
@@ -72,13 +72,15 @@ class ParticleInit(C.Structure):
 class Timing(C.Structure):
     _fields_ = [("predict_ms", C.c_double), ("sort_ms", C.c_double), ("push_ms", C.c_double),
                 ("deposit_ms", C.c_double), ("advance_ms", C.c_double),
-                ("push_calls", C.c_int64), ("launches", C.c_int64), ("kernel_ms", C.c_double)]
+                ("push_calls", C.c_int64), ("launches", C.c_int64), ("kernel_ms", C.c_double),
+                ("inject_ms", C.c_double)]
 
 
 class Diag(C.Structure):
     _fields_ = [("left_inner", C.c_int64), ("left_outer", C.c_int64),
                 ("reflections", C.c_int64), ("nonfinite", C.c_int64),
-                ("alive", C.c_int64 * MAX_SPECIES)]
+                ("alive", C.c_int64 * MAX_SPECIES), ("injected", C.c_int64),
+                ("inject_dropped", C.c_int64)]
 
 
 _lib = None
@@ -129,6 +131,8 @@ def lib(build: bool = True):
         L.grpic_destroy.argtypes = [P]
         L.grpic_destroy.restype = None
         L.grpic_charge_check.argtypes = [P, C.c_int, C.POINTER(C.c_double)]
+        L.grpic_inject.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                   C.c_void_p, C.c_int64, C.c_int64]
         L.grpic_adjoint_forward.argtypes = [P, C.c_int64, C.c_double, C.c_double, C.c_int,
                                             C.c_int, C.c_int, P, P, P]
         L.grpic_adjoint_backward.argtypes = [P, C.c_int64, C.c_double, C.c_double, C.c_int,
@@ -332,6 +336,19 @@ class Sim:
                     "charge_check")
         return tuple(float(v) for v in out)
 
+    def inject(self, sigma0, sigma_th, B0, pool, pool_offset=-1, se=0, sp=1):
+        """grpic_inject: pairs where the magnetization exceeds sigma_th. pool: a float64
+        (pool_n, 8) tensor on the device (kept alive by the caller until the stream has run
+        the call); pool_offset >= 0 sets the library's pool cursor, < 0 continues."""
+        torch = self.torch
+        if (pool.dtype != torch.float64 or pool.device != self.device or pool.dim() != 2 or
+                pool.shape[1] != 8 or not pool.is_contiguous()):
+            raise GrpicError("inject: expected a contiguous (n, 8) float64 tensor on %s"
+                             % self.device)
+        self._check(self.L.grpic_inject(self.ctx, se, sp, float(sigma0), float(sigma_th),
+                                        float(B0), pool.data_ptr(), pool.shape[0],
+                                        int(pool_offset)), "inject")
+
     # --- adjoint of the pusher over frozen fields -------------------------------------
     def _adjoint_state(self, t, what):
         torch = self.torch
@@ -395,7 +412,8 @@ class Sim:
         self._check(self.L.grpic_get_diagnostics(self.ctx, C.byref(d)), "get_diagnostics")
         return {"left_inner": d.left_inner, "left_outer": d.left_outer,
                 "reflections": d.reflections, "nonfinite": d.nonfinite,
-                "alive": [d.alive[i] for i in range(self.n_species)]}
+                "alive": [d.alive[i] for i in range(self.n_species)],
+                "injected": d.injected, "inject_dropped": d.inject_dropped}
 
     def set_timing(self, on: bool):
         self._check(self.L.grpic_set_timing(self.ctx, int(bool(on))), "set_timing")

@@ -45,7 +45,7 @@ __global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
 
 long long grpic_launches = 0;
 
-enum { PH_PREDICT = 0, PH_SORT, PH_PUSH, PH_DEPOSIT, PH_ADVANCE, PH_KERNEL, PH_N };
+enum { PH_PREDICT = 0, PH_SORT, PH_PUSH, PH_DEPOSIT, PH_ADVANCE, PH_KERNEL, PH_INJECT, PH_N };
 
 struct grpic_ctx {
   grpic_config cfg;
@@ -61,7 +61,7 @@ struct grpic_ctx {
   double field_b0 = 1.0;  // amplitude of the analytic field in the planes (1 for user fields)
   size_t off_planes = 0, off_tab = 0, off_polar = 0, off_dt = 0, off_diag = 0, off_ptab = 0;
   size_t off_keys[2] = {}, off_vals[2] = {}, off_hist = 0, off_bsum = 0, off_alive = 0;
-  size_t off_stage = 0, off_rho = 0;
+  size_t off_stage = 0, off_rho = 0, off_inj = 0;
   int64_t load_chunk = 0;
   int64_t max_cap = 0;
   FieldPtrsT<double> F64;
@@ -395,6 +395,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
     }
   }
   ctx->off_rho = off; off += 6 * up(ps * 8) + up(64);  // FP64 charge planes of the check
+  ctx->off_inj = off; off += up(inject_scratch_bytes(g));  // pair injection per-cell scratch
   ctx->load_chunk = ctx->max_cap < ((int64_t)1 << 20) ? ctx->max_cap : ((int64_t)1 << 20);
   ctx->off_stage = off; off += 6 * up((size_t)ctx->load_chunk * 8);
   ctx->need = off;
@@ -756,6 +757,42 @@ grpic_status grpic_step(grpic_ctx *ctx, int n_steps) {
   return GRPIC_OK;
 }
 
+grpic_status grpic_inject(grpic_ctx *ctx, int species_e, int species_p, double sigma0,
+                          double sigma_th, double B0, const double *pool, int64_t pool_n,
+                          int64_t pool_offset) {
+  grpic_status s = need_fields(ctx);
+  if (s) return s;
+  if ((s = need_species(ctx, species_e)) || (s = need_species(ctx, species_p))) return s;
+  if (species_e == species_p) return fail(ctx, GRPIC_EINVAL, "one species for both members");
+  SpeciesState &se = ctx->sp[species_e], &sp = ctx->sp[species_p];
+  if (se.massless || sp.massless) return fail(ctx, GRPIC_EINVAL, "massless species");
+  if (!pool || pool_n <= 0) return fail(ctx, GRPIC_EINVAL, "empty pool");
+  if (!(sigma0 > 0.0) || !(sigma_th > 0.0) || !(B0 != 0.0) || !isfinite(sigma0) ||
+      !isfinite(sigma_th) || !isfinite(B0))
+    return fail(ctx, GRPIC_EINVAL, "bad sigma0, sigma_th or B0");
+  PhaseTimer t(ctx, PH_INJECT);
+  unsigned char *scratch = reinterpret_cast<unsigned char *>(ctx->arena + ctx->off_inj);
+  if (ctx->mixed)
+    CK(launch_inject<float>(ctx->g, ctx->F32, dev_view<float>(se, se.live),
+                            dev_view<float>(sp, sp.live), se.loaded ? se.n_bound : 0,
+                            sp.loaded ? sp.n_bound : 0, se.cap, sp.cap, sigma0, sigma_th, B0,
+                            pool, pool_n, pool_offset, scratch, ctx->diag, ctx->stream));
+  else
+    CK(launch_inject<double>(ctx->g, ctx->F64, dev_view<double>(se, se.live),
+                             dev_view<double>(sp, sp.live), se.loaded ? se.n_bound : 0,
+                             sp.loaded ? sp.n_bound : 0, se.cap, sp.cap, sigma0, sigma_th, B0,
+                             pool, pool_n, pool_offset, scratch, ctx->diag, ctx->stream));
+  // counts stay on the device; the host keeps upper bounds for the launch sizes
+  const int64_t nc = (int64_t)ctx->g.n_r * ctx->g.n_th;
+  for (SpeciesState *q : {&se, &sp}) {
+    const int64_t b = (q->loaded ? q->n_bound : 0) + nc;
+    q->n_bound = b < q->cap ? b : q->cap;
+    q->loaded = true;
+    q->tiles_valid = false;
+  }
+  return GRPIC_OK;
+}
+
 grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double out[4]) {
   grpic_status s = need_fields(ctx);
   if (s) return s;
@@ -823,6 +860,8 @@ grpic_status grpic_get_diagnostics(grpic_ctx *ctx, grpic_diag *out) {
   out->left_outer = (int64_t)h[DG_LEFT_OUTER];
   out->reflections = (int64_t)h[DG_REFLECT];
   out->nonfinite = (int64_t)h[DG_NONFINITE];
+  out->injected = (int64_t)h[DG_INJECTED];
+  out->inject_dropped = (int64_t)h[DG_INJECT_DROPPED];
   return GRPIC_OK;
 }
 
@@ -852,6 +891,7 @@ grpic_status grpic_get_timing(grpic_ctx *ctx, grpic_timing *out) {
   out->deposit_ms = ms[PH_DEPOSIT];
   out->advance_ms = ms[PH_ADVANCE];
   out->kernel_ms = ms[PH_KERNEL];
+  out->inject_ms = ms[PH_INJECT];
   out->push_calls = ctx->push_calls;
   out->launches = grpic_launches;
   ctx->push_calls = 0;

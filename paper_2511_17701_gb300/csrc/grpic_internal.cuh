@@ -78,7 +78,8 @@ struct SpeciesDevT {
 using SpeciesDev = SpeciesDevT<double>;
 
 // Diagnostics counters on the device (unsigned long long for atomicAdd).
-enum { DG_LEFT_INNER = 0, DG_LEFT_OUTER, DG_REFLECT, DG_NONFINITE, DG_N };
+enum { DG_LEFT_INNER = 0, DG_LEFT_OUTER, DG_REFLECT, DG_NONFINITE, DG_INJECTED,
+       DG_INJECT_DROPPED, DG_N };
 
 // ---------------------------------------------------------------------------------
 // Metric of Appendix A, written directly in the code-unit (xi, eta) form of the
@@ -327,6 +328,14 @@ cudaError_t launch_filter(const GridP &g, T *const a[3], T *const s[3], const in
                           bool *in_s);
 template <typename T>
 cudaError_t launch_filter_currents(const GridP &g, FieldPtrsT<T> &F, cudaStream_t st);
+// pair injection (inject.cu): scratch bytes it needs, and the launch
+size_t inject_scratch_bytes(const GridP &g);
+template <typename T>
+cudaError_t launch_inject(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> se,
+                          SpeciesDevT<T> sp, int64_t n_bound_e, int64_t n_bound_p,
+                          int64_t cap_e, int64_t cap_p, double sigma0, double sigma_th,
+                          double B0, const double *pool, int64_t pool_n, int64_t pool_offset,
+                          unsigned char *scratch, unsigned long long *diag, cudaStream_t st);
 template <typename T>
 cudaError_t launch_zero(T *p, int64_t n, cudaStream_t st);
 
