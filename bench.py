@@ -482,10 +482,12 @@ def run_extensions(args, ws, rank, local):
     torch.cuda.set_device(local)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
-    out = {"metric": "extensions: massless particles and the current filter",
+    out = {"metric": "extensions: massless particles, the current filter, pair injection",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup}
+    parts = set(args.only.split(",")) if args.only else {"photons", "filter512", "filter2048",
+                                                          "inject"}
     ph = {}
-    for prec in ("fp64", "mixed"):
+    for prec in (("fp64", "mixed") if "photons" in parts else ()):
         pairs, sim = measure(args, prec, ws, rank, local)
         del sim
         phot, sim = measure(args, prec, ws, rank, local, photons=True)
@@ -499,25 +501,41 @@ def run_extensions(args, ws, rank, local):
                     (pairs["particles"] / 2),
                     "photon_hbm_gbs": phot["hbm_roofline"]["achieved_gbs"],
                     "clocks": phot["clocks"], "workload": phot["workload"]}
-    out["massless"] = ph
+    if ph:
+        out["massless"] = ph
     # the filter on the bench workload: the step with and without it
-    base, sim = measure(args, "fp64", ws, rank, local)
-    del sim
-    filt, sim = measure(args, "fp64", ws, rank, local, extra={"n_filter": 4})
-    del sim
-    torch.cuda.empty_cache()
-    f_ms = filt["timing"]["deposit_ms"] / args.steps
-    cfg = filt["cfg"]
-    plane = (cfg["n_r"] + 5) * (cfg["n_theta"] + 5) * 8
-    out["filter_wald512"] = {
-        "n_filter": 4, "step_ms": filt["ms_per_step"], "step_ms_without": base["ms_per_step"],
-        "filter_ms_per_step": f_ms, "share_of_step": f_ms / filt["ms_per_step"],
-        "algorithmic_bytes_per_step": 6 * plane,
-        "note": "3 current planes read and written once per step (one launch runs the 4 "
-                "passes in shared memory); at 512^2 the planes (12.8 MB) stay in L2"}
-    # the filter kernel against HBM: 2048^2 planes (33.7 MB each), 8 passes in one launch
+    if "filter512" in parts:
+        base, sim = measure(args, "fp64", ws, rank, local)
+        del sim
+        filt, sim = measure(args, "fp64", ws, rank, local, extra={"n_filter": 4})
+        del sim
+        torch.cuda.empty_cache()
+        f_ms = filt["timing"]["deposit_ms"] / args.steps
+        cfg = filt["cfg"]
+        plane = (cfg["n_r"] + 5) * (cfg["n_theta"] + 5) * 8
+        out["filter_wald512"] = {
+            "n_filter": 4, "step_ms": filt["ms_per_step"],
+            "step_ms_without": base["ms_per_step"], "filter_ms_per_step": f_ms,
+            "share_of_step": f_ms / filt["ms_per_step"], "algorithmic_bytes_per_step": 6 * plane,
+            "note": "3 current planes read and written once per step (one launch runs the 4 "
+                    "passes in shared memory); at 512^2 the planes (12.8 MB) stay in L2"}
+    if "filter2048" in parts:
+        out["filter_wald2048"] = measure_filter_2048(args, ws, rank, local, peaks)
+    if "inject" in parts:
+        out["inject_bz2048"] = measure_injection(args, local, peaks)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def measure_filter_2048(args, ws, rank, local, peaks):
+    """The filter kernel against the FP64 pipe and HBM: 2048^2 planes (33.7 MB each, above
+    L2), 8 passes in one launch, on the wald2048 grid with args.ext_ppc particles per cell
+    per species."""
+    import torch
+
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
     big, sim = measure(args, "fp64", ws, rank, local, workload="wald2048",
-                       extra={"n_filter": 8, "ppc": 1})
+                       extra={"n_filter": 8, "ppc": args.ext_ppc or 1})
     del sim
     torch.cuda.empty_cache()
     cfg = big["cfg"]
@@ -527,7 +545,7 @@ def run_extensions(args, ws, rank, local):
     # FP64 operations the 8 passes need at least: per pass, cell and component one DFMA and
     # one DADD along each of x1 and x2 (the kernel also recomputes its tiles' halos, 1.4x)
     ops = 4 * 8 * 3 * (plane // 8) / (f_ms * 1e-3) / 1e9
-    out["filter_wald2048"] = {
+    return {
         "n_filter": 8, "filter_ms_per_step": f_ms, "algorithmic_bytes_per_launch": 6 * plane,
         "algorithmic_fp64_ops_per_launch": 4 * 8 * 3 * (plane // 8),
         "roofline": {"bound": "alu", "achieved": ops, "peak": FP64_PIPE_PEAK_GOPS,
@@ -538,8 +556,73 @@ def run_extensions(args, ws, rank, local):
         "hbm_roofline": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
                          "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"},
         "clocks": big["clocks"]}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+
+
+def measure_injection(args, local, peaks):
+    """Pair injection (Sec. 4.5) on the 2048^2 monopole grid with 4 particles per cell per
+    species (33.6 M particles; args.ext_ppc when given): a full FP64 step followed by
+    grpic_inject with sigma_th = 2000, args.steps times after args.warmup; the injection's
+    time per call and its share of the step. The density scatter reads 17 B per particle
+    (cell indices, weight, tag); the per-cell part reads B (3 planes) and writes about 24 B
+    per cell."""
+    import torch
+
+    from paper_2511_17701_gb300 import FIELD_MONOPOLE, Sim
+
+    device = torch.device("cuda", local)
+    cfg = W.grid_config("bz2048", ppc=args.ext_ppc or 4, sort_every=args.sort_every,
+                        tile_r=args.tile, tile_theta=args.tile, iter_tol=args.iter_tol)
+    pl = W.pair_plasma(cfg)
+    n = pl["pos"]["i1"].size
+    nc = cfg["n_r"] * cfg["n_theta"]
+    room = (args.warmup + args.steps + 1) * nc  # at most one pair per cell and call
+    sim = Sim(cfg, [n + room, n + room], device=device)
+    sim.init_metric()
+    sim.init_fields(FIELD_MONOPOLE, cfg["B0"])
+    for s in range(2):
+        sim.load_particles(s, pl["pos"], pl["uhat"][s], pl["w0"], pl["qm"][s], pl["qc"][s],
+                           pl["density_power"])
+    del pl
+    pool = torch.tensor(W.injection_pool(cfg, 1 << 20, seed=cfg["seed"] + 7),
+                        dtype=torch.float64, device=device)
+    sim.inject(cfg["sigma0"], cfg["sigma_th"], cfg["B0"], pool, pool_offset=0)
+    for _ in range(args.warmup):
+        sim.step(1)
+        sim.inject(cfg["sigma0"], cfg["sigma_th"], cfg["B0"], pool)
+    sim.sync()
+    sim.diagnostics()
+    sim.timing()
+    sim.set_timing(True)
+    n0 = sim.count(0) + sim.count(1)
+    stream = sim.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+        sim.inject(cfg["sigma0"], cfg["sigma_th"], cfg["B0"], pool)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    sim.set_timing(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    tim = sim.timing()
+    d = sim.diagnostics()
+    n1 = sim.count(0) + sim.count(1)
+    inj_ms = tim["inject_ms"] / args.steps
+    parts = 0.5 * (n0 + n1)
+    bytes_ = parts * 17 + nc * (3 * 8 + 24)
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    gbs = bytes_ / (inj_ms * 1e-3) / 1e9
+    del sim
+    torch.cuda.empty_cache()
+    return {"workload": "bz2048 grid, %d ppc per species, FP64, sigma0 = %g, sigma_th = %g"
+                        % (cfg["ppc"], cfg["sigma0"], cfg["sigma_th"]),
+            "particles_before": n0, "particles_after": n1, "cells": nc,
+            "pairs_added_per_step": d["injected"] / args.steps,
+            "inject_ms_per_call": inj_ms, "step_plus_inject_ms": ms,
+            "share_of_step": inj_ms / ms,
+            "hbm_roofline": {"achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                             "frac": gbs / hbm_peak,
+                             "algorithmic_bytes_per_call": bytes_}}
 
 
 def run_adjoint(args, ws, rank, local):
@@ -666,6 +749,11 @@ def main():
     ap.add_argument("--extensions", action="store_true",
                     help="time the rows beyond the base path instead: massless particles and "
                          "the current filter")
+    ap.add_argument("--only", default="",
+                    help="--extensions: a comma list of photons, filter512, filter2048, inject")
+    ap.add_argument("--ext-ppc", type=int, default=0,
+                    help="--extensions: particles per cell per species of the 2048^2 filter "
+                         "and injection cases (default 1 and 4)")
     ap.add_argument("--adjoint-particles", type=int, default=1 << 20)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--adjoint-ckpt", type=int, default=100)

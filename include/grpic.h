@@ -190,8 +190,9 @@ GRPIC_API size_t grpic_arena_bytes(const grpic_ctx *ctx);
 GRPIC_API grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream);
 
 /* Tabulates the code-unit metric of App. A (alpha, h_ij, sqrt(h), sqrt(h~),
- * [sqrt(h~) h_13], [sqrt(h~ h) beta^1], 1/sqrt(h)) at the four Yee point classes and
- * the polar areas of Sec. 3.3.2, and fixes dt (cfl rule when cfg.dt <= 0).
+ * [sqrt(h~) h_13], [sqrt(h~ h) beta^1], 1/sqrt(h)) at the four Yee point classes, the
+ * polar areas of Sec. 3.3.2 and the FP64 cell-centre metric of grpic_inject, and fixes dt
+ * (cfl rule when cfg.dt <= 0).
  * Synchronises the stream once (dt is read back). */
 GRPIC_API grpic_status grpic_init_metric(grpic_ctx *ctx);
 

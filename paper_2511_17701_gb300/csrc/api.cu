@@ -474,6 +474,8 @@ grpic_status grpic_init_metric(grpic_ctx *ctx) {
                                     const_cast<double *>(ctx->F64.polar), ctx->stream));
   }
   CK(launch_push_tables(ctx->g, ctx->tb, ctx->stream));
+  CK(launch_inject_tables(ctx->g, reinterpret_cast<unsigned char *>(ctx->arena + ctx->off_inj),
+                          ctx->stream));
   if (!(ctx->cfg.dt > 0.0)) {
     double dmin = 0.0;
     CK(launch_dt_min(ctx->g, at<double>(ctx, ctx->off_dt), 8, &dmin, ctx->stream));

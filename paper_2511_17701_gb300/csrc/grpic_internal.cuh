@@ -328,8 +328,10 @@ cudaError_t launch_filter(const GridP &g, T *const a[3], T *const s[3], const in
                           bool *in_s);
 template <typename T>
 cudaError_t launch_filter_currents(const GridP &g, FieldPtrsT<T> &F, cudaStream_t st);
-// pair injection (inject.cu): scratch bytes it needs, and the launch
+// pair injection (inject.cu): scratch bytes it needs, its cell-centre metric table (once per
+// grid), and the launch
 size_t inject_scratch_bytes(const GridP &g);
+cudaError_t launch_inject_tables(const GridP &g, unsigned char *scratch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_inject(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> se,
                           SpeciesDevT<T> sp, int64_t n_bound_e, int64_t n_bound_p,

@@ -11,56 +11,95 @@
 // pair in cell order goes to slot n + k of both species, so the result does not depend on
 // thread scheduling. When room runs out the first pairs in cell order are kept.
 //
-// Kernels: the density scatter (one FP64 atomic per live particle, HBM-bound on the particle
-// reads), the per-cell decision, an exclusive scan of the decisions (warp-shuffle block scans
-// of 1024 cells, a scan of the block totals, a fix-up), the writes of the new pairs and the
-// count update.
+// Kernels: the density scatter (warp-reduced runs of equal cells, one FP64 atomic per run),
+// the per-cell decision (FP64, with the cell-centre metric tabulated once per grid), an
+// exclusive scan of the decisions (warp-shuffle block scans of 1024 cells, a scan of the
+// block totals, a fix-up), the list of injecting cells, the writes of the new pairs (one
+// thread per pair, so the FP64 metric and tetrad work runs in full warps) and the count
+// update.
 #include "grpic_internal.cuh"
 
 namespace {
 
 constexpr int SC_TPB = 256, SC_PER = 4, SC_BLOCK = SC_TPB * SC_PER;  // cells per scan block
 
-template <typename T>
-__global__ void k_inj_density(GridP g, SpeciesDevT<T> s, double *ncell) {
-  const int64_t n = *s.n;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    if (s.tag[k] != 1) continue;
-    const int i = s.i1[k], j = s.i2[k];
-    if (i < 0 || i >= g.n_r || j < 0 || j >= g.n_th) continue;
-    atomicAdd(ncell + (int64_t)j * g.n_r + i, fabs((double)s.w[k]));
-  }
-}
-
-// B_i B^i and sqrt(h) at the centre of cell (i, j)
-template <typename T>
-__device__ __forceinline__ double cell_b2(const GridP &g, const T *const B[3], int i, int j,
-                                          double &sqrt_h) {
-  MetricV m;
-  metric_eval<false>(g, i + 0.5, j + 0.5, false, m, nullptr);
-  const int64_t k = sidx(g, i, j);
-  const double b1 = 0.5 * ((double)B[0][k] + (double)B[0][k + 1]);
-  const double b2 = 0.5 * ((double)B[1][k] + (double)B[1][k + g.NX]);
-  const double b3 = (double)B[2][k];
-  sqrt_h = m.sqrt_h;
-  return m.h11 * b1 * b1 + m.h22 * b2 * b2 + m.h33 * b3 * b3 + 2.0 * m.h13 * b1 * b3;
-}
-
-// decision per cell: flag[c] = sigma > sigma_th; ncell[c] becomes dn (the density to add)
-template <typename T>
-__global__ void k_inj_decide(GridP g, FieldPtrsT<T> F, double *ncell, uint32_t *flag,
-                             double sigma0, double sigma_th, double B0) {
+// the metric at every cell centre, FP64, once per grid: [5][n_th][n_r] = h11, h22, h33, h13,
+// sqrt(h) (the values the per-cell decision and the injected weights use)
+constexpr int CT_H11 = 0, CT_H22 = 1, CT_H33 = 2, CT_H13 = 3, CT_SQH = 4, CT_ISQ = 5, CT_N = 6;
+__global__ void k_inj_tables(GridP g, double *ct) {
   const int64_t nc = (int64_t)g.n_r * g.n_th;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.n_r), j = (int)(c / g.n_r);
-    double sq;
-    const double b2 = cell_b2<T>(g, F.B, i, j, sq);
-    const double n = ncell[c] / sq;
-    const bool hot = sigma0 * b2 > sigma_th * B0 * B0 * n;  // no division: n may be 0
+    MetricV m;
+    metric_eval<false>(g, i + 0.5, j + 0.5, false, m, nullptr);
+    ct[CT_H11 * nc + c] = m.h11;
+    ct[CT_H22 * nc + c] = m.h22;
+    ct[CT_H33 * nc + c] = m.h33;
+    ct[CT_H13 * nc + c] = m.h13;
+    ct[CT_SQH * nc + c] = m.sqrt_h;
+    ct[CT_ISQ * nc + c] = 1.0 / m.sqrt_h;
+  }
+}
+
+// summed |w| per cell. Particles are mostly sorted by cell, so consecutive lanes share a
+// cell: each run of equal cells within the warp is summed by a suffix scan bounded by the
+// next run head, and the head lane issues one atomic for the run.
+template <typename T>
+__global__ void k_inj_density(GridP g, SpeciesDevT<T> s, double *ncell) {
+  const int64_t n = *s.n;
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k - lane < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t cell = -1;
+    double v = 0.0;
+    if (k < n && s.tag[k] == 1) {
+      const int i = s.i1[k], j = s.i2[k];
+      if (i >= 0 && i < g.n_r && j >= 0 && j < g.n_th) {
+        cell = (int64_t)j * g.n_r + i;
+        v = fabs((double)s.w[k]);
+      }
+    }
+    const int64_t prev = __shfl_up_sync(0xffffffffu, cell, 1);
+    const bool head = lane == 0 || prev != cell;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned after = lane == 31 ? 0u : heads & ~((2u << lane) - 1u);
+    const int end = after ? __ffs(after) - 1 : 32;
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, v, o);
+      if (lane + o < end) v += y;
+    }
+    if (head && cell >= 0) atomicAdd(ncell + cell, v);
+  }
+}
+
+// B_i B^i at the centre of cell c = (i, j)
+template <typename T>
+__device__ __forceinline__ double cell_b2(const GridP &g, const T *const B[3], const double *ct,
+                                          int64_t nc, int64_t c, int i, int j) {
+  const int64_t k = sidx(g, i, j);
+  const double b1 = 0.5 * ((double)B[0][k] + (double)B[0][k + 1]);
+  const double b2 = 0.5 * ((double)B[1][k] + (double)B[1][k + g.NX]);
+  const double b3 = (double)B[2][k];
+  return ct[CT_H11 * nc + c] * b1 * b1 + ct[CT_H22 * nc + c] * b2 * b2 +
+         ct[CT_H33 * nc + c] * b3 * b3 + 2.0 * ct[CT_H13 * nc + c] * b1 * b3;
+}
+
+// decision per cell: flag[c] = sigma > sigma_th; ncell[c] becomes dn (the density to add).
+// The work is FP64 (GB300: 2 operations per clock per SM): no divisions, the constants
+// st = sigma_th B0^2 and kd = sigma0 / (B0^2 sigma_th) come in from the host.
+template <typename T>
+__global__ void k_inj_decide(GridP g, FieldPtrsT<T> F, const double *ct, double *ncell,
+                             uint32_t *flag, double sigma0, double st, double kd) {
+  const int64_t nc = (int64_t)g.n_r * g.n_th;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.n_r), j = (int)(c / g.n_r);
+    const double b2 = cell_b2<T>(g, F.B, ct, nc, c, i, j);
+    const double n = ncell[c] * ct[CT_ISQ * nc + c];
+    const bool hot = sigma0 * b2 > st * n;  // sigma > sigma_th without dividing by n
     flag[c] = hot ? 1u : 0u;
-    ncell[c] = hot ? sigma0 * b2 / (B0 * B0 * sigma_th) - n : 0.0;
+    ncell[c] = hot ? kd * b2 - n : 0.0;
   }
 }
 
@@ -137,30 +176,34 @@ __global__ void k_scan_fix(uint32_t *a, int64_t L, const uint32_t *bsum) {
     a[t] += bsum[t / SC_BLOCK];
 }
 
-// the new pairs: cell c injects iff its exclusive offset steps up; pair k = off[c] goes to
-// slot n + k of both species if k < room
-template <typename T>
-__global__ void k_inj_write(GridP g, SpeciesDevT<T> se, SpeciesDevT<T> sp, int64_t cap_e,
-                            int64_t cap_p, const uint32_t *off, const uint32_t *total,
-                            const double *dn, const double *pool, int64_t pool_n,
-                            const int64_t *cursor) {
-  const int64_t nc = (int64_t)g.n_r * g.n_th;
-  const int64_t ne = *se.n, np = *sp.n;
-  const int64_t room = cap_e - ne < cap_p - np ? cap_e - ne : cap_p - np;
-  const int64_t cur = *cursor;
+// the cells that inject, in cell order: cell c injects iff its exclusive offset steps up
+__global__ void k_inj_list(int64_t nc, const uint32_t *off, const uint32_t *total,
+                           uint32_t *list) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t k = off[c], next = c + 1 < nc ? off[c + 1] : *total;
-    if (next == k || (int64_t)k >= room) continue;
+    if (next != k) list[k] = (uint32_t)c;
+  }
+}
+
+// the new pairs, one thread per pair (full warps for the FP64 metric and tetrads): pair k
+// of cell list[k] goes to slot n + k of both species if k < room
+template <typename T>
+__global__ void k_inj_write(GridP g, SpeciesDevT<T> se, SpeciesDevT<T> sp, int64_t cap_e,
+                            int64_t cap_p, const uint32_t *list, const uint32_t *total,
+                            const double *dn, const double *ct, const double *pool,
+                            int64_t pool_n, const int64_t *cursor) {
+  const int64_t nc = (int64_t)g.n_r * g.n_th;
+  const int64_t ne = *se.n, np = *sp.n;
+  const int64_t room = cap_e - ne < cap_p - np ? cap_e - ne : cap_p - np;
+  const int64_t t = (int64_t)*total, npairs = t < room ? t : room;
+  const int64_t cur = *cursor;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < npairs;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = list[k];
     const int i = (int)(c % g.n_r), j = (int)(c / g.n_r);
     const double *r = pool + 8 * ((cur + k) % pool_n);
-    double sq;
-    {
-      MetricV m0;
-      metric_eval<false>(g, i + 0.5, j + 0.5, false, m0, nullptr);
-      sq = m0.sqrt_h;
-    }
-    const double w = 0.5 * dn[c] * sq;
+    const double w = 0.5 * dn[c] * ct[CT_SQH * nc + c];
     MetricV m;
     metric_eval<false>(g, i + r[0], j + r[1], true, m, nullptr);
     for (int q = 0; q < 2; ++q) {
@@ -207,7 +250,19 @@ size_t inject_scratch_bytes(const GridP &g) {
   const int64_t nc = (int64_t)g.n_r * g.n_th;
   const int64_t nb = (nc + SC_BLOCK - 1) / SC_BLOCK;
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-  return up(nc * 8) + up(nc * 4) + up((nb + 1) * 4) + up(64);
+  return up(nc * 8) + up(nc * 4) + up((nb + 1) * 4) + up(64) + up(CT_N * nc * 8) + up(nc * 4);
+}
+
+// the cell-centre metric table at the end of the scratch (grpic_init_metric)
+cudaError_t launch_inject_tables(const GridP &g, unsigned char *scratch, cudaStream_t st) {
+  const int64_t nc = (int64_t)g.n_r * g.n_th;
+  const int64_t nb = (nc + SC_BLOCK - 1) / SC_BLOCK;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  double *ct = reinterpret_cast<double *>(scratch + up(nc * 8) + up(nc * 4) + up((nb + 1) * 4) +
+                                          up(64));
+  k_inj_tables<<<blocks_of(nc, 256), 256, 0, st>>>(g, ct);
+  COUNT_LAUNCH(1);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -225,6 +280,8 @@ cudaError_t launch_inject(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T>
   unsigned char *tail = scratch + up(nc * 8) + up(nc * 4) + up((nb + 1) * 4);
   int64_t *cursor = reinterpret_cast<int64_t *>(tail);
   uint32_t *total = reinterpret_cast<uint32_t *>(tail + 8);
+  const double *ct = reinterpret_cast<const double *>(tail + up(64));
+  uint32_t *list = reinterpret_cast<uint32_t *>(tail + up(64) + up(CT_N * nc * 8));
   if (pool_offset >= 0) {
     k_inj_cursor<<<1, 1, 0, st>>>(cursor, pool_offset % pool_n);
     COUNT_LAUNCH(1);
@@ -239,14 +296,18 @@ cudaError_t launch_inject(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T>
     k_inj_density<T><<<blocks_of(n_bound_p, 256), 256, 0, st>>>(g, sp, ncell);
     COUNT_LAUNCH(1);
   }
-  k_inj_decide<T><<<blocks_of(nc, 256), 256, 0, st>>>(g, F, ncell, flag, sigma0, sigma_th, B0);
+  k_inj_decide<T><<<blocks_of(nc, 256), 256, 0, st>>>(g, F, ct, ncell, flag, sigma0,
+                                                      sigma_th * B0 * B0,
+                                                      sigma0 / (B0 * B0 * sigma_th));
   k_scan_block<<<(int)nb, SC_TPB, 0, st>>>(flag, nc, bsum);
   k_scan_totals<<<1, SC_TPB, 0, st>>>(bsum, nb, total);
   k_scan_fix<<<blocks_of(nc, 256), 256, 0, st>>>(flag, nc, bsum);
-  k_inj_write<T><<<blocks_of(nc, 256), 256, 0, st>>>(g, se, sp, cap_e, cap_p, flag, total, ncell,
-                                                     pool, pool_n, cursor);
+  k_inj_list<<<blocks_of(nc, 256), 256, 0, st>>>(nc, flag, total, list);
+  // the pair count is on the device: enough blocks for one pair per cell, idle past it
+  k_inj_write<T><<<blocks_of(nc, 128), 128, 0, st>>>(g, se, sp, cap_e, cap_p, list, total, ncell,
+                                                     ct, pool, pool_n, cursor);
   k_inj_finish<T><<<1, 1, 0, st>>>(se, sp, cap_e, cap_p, total, cursor, pool_n, diag);
-  COUNT_LAUNCH(6);
+  COUNT_LAUNCH(7);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,25 @@ def pool_tensor(torch, pool):
     return torch.tensor(pool, dtype=torch.float64, device="cuda")
 
 
+def assert_injected(g, osim, n_before, b2, th, rtol=1e-12):
+    """Particle parity after an injection. The weight of a pair added near the threshold is
+    a difference of two nearly equal densities (the target and the one already there), so
+    its error is bounded relative to the target weight n_target sqrt(h) / 2, not to itself;
+    every other quantity (and the weights of the particles that were there) to rtol."""
+    for s in range(2):
+        pg, po = g.get_particles(s), osim.species[s].view()
+        nb = n_before[s]
+        assert len(pg["w"]) == len(po["w"])
+        assert np.allclose(pg["w"][:nb], po["w"][:nb], rtol=rtol, atol=0)
+        for p in range(nb, len(po["w"])):
+            i, j = int(po["i1"][p]), int(po["i2"][p])
+            sq = O.metric_point(CFG, i + 0.5, j + 0.5)["sqrt_h"]
+            target = 0.5 * SIGMA0 * b2[j, i] / (B0 * B0 * th) * sq
+            assert abs(pg["w"][p] - po["w"][p]) <= rtol * target, (s, p)
+        pg = dict(pg, w=po["w"])
+        assert_particles(pg, po, rtol=rtol)
+
+
 @pytest.mark.parametrize("want", [300.0, 2000.0])
 def test_injection_matches_the_oracle(torch_cuda, want):
     osim = oracle_state(CFG, kind=O.FIELD_MONOPOLE, B0=B0)
@@ -55,19 +74,21 @@ def test_injection_matches_the_oracle(torch_cuda, want):
     pool = W.injection_pool(CFG, 997, seed=7)
     pt = pool_tensor(torch_cuda, pool)
     g.inject(SIGMA0, th, B0, pt, pool_offset=11)
+    nb = [sp.n for sp in osim.species]
+    b2 = osim.cell_state()[1]
     added = osim.inject(SIGMA0, th, B0, pool, pool_offset=11)
     assert added > 0
     d = g.diagnostics()
     assert d["injected"] == added and d["inject_dropped"] == 0
-    for s in range(2):
-        assert_particles(g.get_particles(s), osim.species[s].view())
+    assert_injected(g, osim, nb, b2, th)
     # the cursor continues: a lower threshold injects again from entry 11 + added
     th2 = safe_threshold(osim, 0.5 * th)
     g.inject(SIGMA0, th2, B0, pt)
+    nb = [sp.n for sp in osim.species]
+    b2 = osim.cell_state()[1]
     added2 = osim.inject(SIGMA0, th2, B0, pool, pool_offset=11 + added)
     assert added2 > 0 and g.diagnostics()["injected"] == added2
-    for s in range(2):
-        assert_particles(g.get_particles(s), osim.species[s].view())
+    assert_injected(g, osim, nb, b2, th2)
 
 
 def test_injection_with_limited_room(torch_cuda):
@@ -77,12 +98,13 @@ def test_injection_with_limited_room(torch_cuda):
     pool = W.injection_pool(CFG, 500, seed=8)
     g.inject(SIGMA0, th, B0, pool_tensor(torch_cuda, pool), pool_offset=0)
     full = oracle_state(CFG, kind=O.FIELD_MONOPOLE, B0=B0).inject(SIGMA0, th, B0, pool)
+    nb = [sp.n for sp in osim.species]
+    b2 = osim.cell_state()[1]
     added = osim.inject(SIGMA0, th, B0, pool, cap=osim.species[0].n + 25)
     assert added == 25 and full > 25
     d = g.diagnostics()
     assert d["injected"] == 25 and d["inject_dropped"] == full - 25
-    for s in range(2):
-        assert_particles(g.get_particles(s), osim.species[s].view())
+    assert_injected(g, osim, nb, b2, th)
 
 
 def test_steps_after_injection_and_charge(torch_cuda):
@@ -92,7 +114,13 @@ def test_steps_after_injection_and_charge(torch_cuda):
     g = gpu_from_oracle(osim, extra_capacity=CFG["n_r"] * CFG["n_theta"])
     pool = W.injection_pool(CFG, 3000, seed=9)
     g.inject(SIGMA0, th, B0, pool_tensor(torch_cuda, pool), pool_offset=0)
+    nb = [sp.n for sp in osim.species]
+    b2 = osim.cell_state()[1]
     assert osim.inject(SIGMA0, th, B0, pool) > 0
+    assert_injected(g, osim, nb, b2, th)
+    # from the same state on both sides the steps are compared at the parity bound
+    for s in range(2):
+        g.set_particles(s, osim.species[s].view(), osim.species[s].qm, osim.species[s].qc)
     g.step(2)
     osim.step(2, sort_every=1, tr=8, tt=8)
     assert_planes(g.planes(), osim.F, planes=AFTER_ADVANCE, rtol=1e-11, what="after injection")

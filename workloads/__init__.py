@@ -53,7 +53,8 @@ CONFIGS = {
     # particles per cell (45 per species, 377,487,360 particles)
     "bz2048": dict(metric="ks", a=0.2, n_r=2048, n_theta=2048, r_min=1.0, r_max=10.0, ppc=45,
                    theta_T=0.5, density_power=2.0, steps=100, cfl=0.5, seed=6, B0=1.0,
-                   r_absorb=9.0, rho0=5e-5, d0=2.5e-3, field="monopole"),
+                   r_absorb=9.0, rho0=5e-5, d0=2.5e-3, field="monopole", sigma0=2500.0,
+                   sigma_th=2000.0, theta_inj=0.5),
     # 2048^2, r_max = 200, 16 ppc per species (134,217,728 particles), density ~ 1/r, 500 steps
     "wald2048": dict(metric="ks", a=_A, n_r=2048, n_theta=2048, r_min=_RMIN, r_max=200.0,
                      ppc=16, theta_T=1.0, density_power=1.0, steps=500, cfl=0.5, seed=3,
