@@ -27,11 +27,17 @@ static double PI_ = 3.14159265358979323846;
 
 /* ------------------------------------------------------------------------ */
 /* grid geometry: code coordinates are uniform (Sec. 3, "code units"); the    */
-/* quasi-spherical map of Appendix A with r0 = 0, h0 = 0 gives                */
-/*   r = exp(xi), xi = log r_min + x1 dxi,  theta = x2 dtheta.                */
+/* quasi-spherical map of Appendix A:                                          */
+/*   r = r0 + exp(xi), xi = log(r_min - r0) + x1 dxi,                          */
+/*   theta = eta + 2 h0 eta (pi - 2 eta)(pi - eta) / pi^2, eta = x2 deta,      */
+/* with dxi = log((r_max - r0)/(r_min - r0)) / n_r and deta = pi / n_theta.    */
+/* r0 = h0 = 0 is the plain log-r grid with uniform theta. The map's          */
+/* functions are in pusher_generic.inc (they serve both instances).           */
 /* ------------------------------------------------------------------------ */
-static double dxi_of(const ora_params *p) { return log(p->r_max / p->r_min) / p->n_r; }
-static double dth_of(const ora_params *p) { return PI_ / p->n_th; }
+static double dxi_of(const ora_params *p) {
+  return log((p->r_max - p->r0) / (p->r_min - p->r0)) / p->n_r;
+}
+static double dth_of(const ora_params *p) { return PI_ / p->n_th; } /* deta */
 static int NX_of(const ora_params *p) { return p->n_r + 2 * G + 1; }
 static int NY_of(const ora_params *p) { return p->n_th + 2 * G + 1; }
 static int64_t plane_size(const ora_params *p) { return (int64_t)NX_of(p) * NY_of(p); }
@@ -94,10 +100,25 @@ typedef struct {
 static double polar_area(const ora_params *p, double x1) {
   const double M = p->metric == 1 ? 1.0 : 0.0;
   const double a = p->metric == 1 ? p->a : 0.0;
-  double r = p->r_min * exp(x1 * dxi_of(p));
-  double f = dxi_of(p) * r;
-  return f * (r * r + a * a) * sqrt(1.0 + 2.0 * M * r / (r * r + a * a)) *
-         (1.0 - cos(0.5 * dth_of(p)));
+  double r, f, th, g, gp;
+  map_r(p, x1, &r, &f);
+  map_th(p, 0.5, &th, &g, &gp); /* theta at the half cell's edge; x2 -> theta is monotone */
+  return f * (r * r + a * a) * sqrt(1.0 + 2.0 * M * r / (r * r + a * a)) * (1.0 - cos(th));
+}
+
+/* theta(eta_j) + theta(eta_{j+1}) and theta(eta_{j+1}) - theta(eta_j) of the face rows j,
+ * j + 1, with the cubic's difference expanded so that nothing cancels:
+ * p(eta + d) - p(eta) = d (pi^2 - 6 pi eta + 6 eta^2) + d^2 (6 eta - 3 pi) + 2 d^3 for
+ * p(eta) = eta (pi - 2 eta)(pi - eta) = pi^2 eta - 3 pi eta^2 + 2 eta^3. */
+static double theta_sum(const ora_params *p, int j) {
+  const double de = dth_of(p), e0 = j * de, e1 = (j + 1) * de, k = 2.0 * p->h0 / (PI_ * PI_);
+  const double p0 = e0 * (PI_ - 2.0 * e0) * (PI_ - e0), p1 = e1 * (PI_ - 2.0 * e1) * (PI_ - e1);
+  return (2 * j + 1) * de + k * (p0 + p1);
+}
+static double theta_diff(const ora_params *p, int j) {
+  const double de = dth_of(p), e0 = j * de, k = 2.0 * p->h0 / (PI_ * PI_);
+  return de + k * (de * (PI_ * PI_ - 6.0 * PI_ * e0 + 6.0 * e0 * e0) +
+                   de * de * (6.0 * e0 - 3.0 * PI_) + 2.0 * de * de * de);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -110,8 +131,9 @@ static void wald_potential_c(const ora_params *p, int kind, double B0, cplx x1, 
                              cplx *A0, cplx *A1, cplx *A3) {
   const double M = p->metric == 1 ? 1.0 : 0.0;
   const double a = p->metric == 1 ? p->a : 0.0;
-  cplx r = p->r_min * cexp(x1 * dxi_of(p));
-  cplx th = x2 * dth_of(p);
+  cplx r, f, th, g, gp;
+  map_r_cs(p, x1, &r, &f);
+  map_th_cs(p, x2, &th, &g, &gp);
   cplx s = csin(th), c = ccos(th), s2 = s * s;
   if (kind == 2) { /* vertical: A_phi = B0 r^2 sin^2(theta) / 2 */
     *A0 = 0.0; *A1 = 0.0; *A3 = 0.5 * B0 * r * r * s2;
@@ -125,8 +147,7 @@ static void wald_potential_c(const ora_params *p, int kind, double B0, cplx x1, 
   cplx Del = r * r - 2.0 * M * r + a * a;
   cplx AA = (r * r + a * a) * (r * r + a * a) - a * a * Del * s2;
   cplx z = 2.0 * M * r / Sig;
-  cplx f = dxi_of(p) * r;                 /* dr/dx1 */
-  cplx h13 = -f * a * (1.0 + z) * s2;     /* code-unit h_13 (dphi = 1) */
+  cplx h13 = -f * a * (1.0 + z) * s2;     /* code-unit h_13 (dphi = 1), f = dr/dx1 */
   cplx h11 = f * f * (1.0 + z);
   cplx h33 = AA * s2 / Sig;
   cplx beta1 = z / (1.0 + z) / f;
@@ -143,35 +164,35 @@ static void wald_potential(const ora_params *p, int kind, double B0, double x1, 
   A[0] = creal(A0); A[1] = creal(A1); A[2] = creal(A3);
 }
 
-/* The difference A_1(x1, (j+1) dtheta) - A_1(x1, j dtheta) of the Wald potential, for the
+/* The difference A_1(x1, theta_{j+1}) - A_1(x1, theta_j) of the Wald potential, for the
  * discrete curl that gives B^3. With A_1 = (B0/2) a f (2 M r (1 + cos^2)/Sigma - sin^2) and
  * sin^2(b) - sin^2(a) = sin(b - a) sin(b + a), cos^2(b) - cos^2(a) = -(sin^2(b) - sin^2(a)):
  *   dA_1 = -(B0/2) a f D (1 + 2 M r (r^2 - a^2) / (Sigma_a Sigma_b)),
- *   D = sin(dtheta) sin((2 j + 1) dtheta),
+ *   D = sin(theta_{j+1} - theta_j) sin(theta_{j+1} + theta_j),
  * exact in real arithmetic; the plain difference of the two values loses about 1/dtheta^2
  * of its digits next to the axes, where A_1 varies as theta^2. */
 static double wald_dA1_theta(const ora_params *p, int kind, double B0, double x1, int j) {
   if (kind != 1) return 0.0; /* the vertical field has A_1 = 0 */
   const double M = p->metric == 1 ? 1.0 : 0.0;
   const double a = p->metric == 1 ? p->a : 0.0;
-  const double dth = dth_of(p);
-  const double r = p->r_min * exp(x1 * dxi_of(p));
-  const double f = dxi_of(p) * r;
-  const double ca = cos(j * dth), cb = cos((j + 1) * dth);
+  double r, f, tha, thb, g, gp;
+  map_r(p, x1, &r, &f);
+  map_th(p, j, &tha, &g, &gp);
+  map_th(p, j + 1, &thb, &g, &gp);
+  const double ca = cos(tha), cb = cos(thb);
   const double Sa = r * r + a * a * ca * ca, Sb = r * r + a * a * cb * cb;
-  const double D = sin(dth) * sin((2 * j + 1) * dth);
+  const double D = sin(theta_diff(p, j)) * sin(theta_sum(p, j));
   return -0.5 * B0 * a * f * D * (1.0 + 2.0 * M * r * (r * r - a * a) / (Sa * Sb));
 }
 
-/* The difference A_3(x1, (j+1) dtheta) - A_3(x1, j dtheta) for the discrete curl that gives
- * B^1. For the monopole, -B0 (cos((j+1) dtheta) - cos(j dtheta)) = 2 B0 sin((j + 1/2) dtheta)
- * sin(dtheta / 2) in product form: the plain difference of the cosines loses about
- * 1/dtheta^2 of its digits next to the axes. Other kinds: the plain difference. */
+/* The difference A_3(x1, theta_{j+1}) - A_3(x1, theta_j) for the discrete curl that gives
+ * B^1. For the monopole, -B0 (cos(theta_{j+1}) - cos(theta_j)) = 2 B0 sin((theta_j +
+ * theta_{j+1}) / 2) sin((theta_{j+1} - theta_j) / 2) in product form: the plain difference
+ * of the cosines loses about 1/dtheta^2 of its digits next to the axes. Other kinds: the
+ * plain difference. */
 static double dA3_theta(const ora_params *p, int kind, double B0, double x1, int j) {
-  if (kind == 4) {
-    const double dth = dth_of(p);
-    return 2.0 * B0 * sin((j + 0.5) * dth) * sin(0.5 * dth);
-  }
+  if (kind == 4)
+    return 2.0 * B0 * sin(0.5 * theta_sum(p, j)) * sin(0.5 * theta_diff(p, j));
   double A[3], Ab[3];
   wald_potential(p, kind, B0, x1, j, A);
   wald_potential(p, kind, B0, x1, j + 1, Ab);
@@ -563,7 +584,8 @@ static void bc_match(const ora_params *p, double *Fc[3], const double *Fi[3], co
   for (int c = 0; c < 3; ++c)
     for (int j = 0; j <= p->n_th; ++j)
       for (int i = -G; i <= p->n_r + G; ++i) {
-        double r = p->r_min * exp((i + S[c][0]) * dxi_of(p));
+        double r, f;
+        map_r(p, i + S[c][0], &r, &f);
         if (r <= p->r_absorb) continue;
         double x = (r - p->r_absorb) / (p->r_max - p->r_absorb);
         if (x > 1.0) x = 1.0;
@@ -1111,4 +1133,4 @@ void ora_push_frozen_cs(const ora_params *p, const double *F, double scale_re, d
   }
 }
 
-int ora_version(void) { return 5; }
+int ora_version(void) { return 6; }

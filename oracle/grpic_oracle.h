@@ -40,6 +40,8 @@ typedef struct {
   int n_f;             /* number of current filters (sets the horizon layer)           */
   double r_absorb;     /* start of the absorbing (MATCH) layer                         */
   double absorb_coef;  /* strength of the absorbing layer                              */
+  double r0, h0;       /* quasi-spherical map (App. A): r = r0 + exp(xi), theta(eta) with
+                          the equatorial concentration h0; 0, 0 = plain log-r, uniform theta */
 } ora_params;
 
 typedef struct {

@@ -45,7 +45,8 @@ class Params(C.Structure):
     _fields_ = [("metric", C.c_int), ("a", C.c_double), ("n_r", C.c_int), ("n_th", C.c_int),
                 ("r_min", C.c_double), ("r_max", C.c_double), ("dt", C.c_double),
                 ("n_iter", C.c_int), ("small_angle", C.c_double), ("n_f", C.c_int),
-                ("r_absorb", C.c_double), ("absorb_coef", C.c_double)]
+                ("r_absorb", C.c_double), ("absorb_coef", C.c_double), ("r0", C.c_double),
+                ("h0", C.c_double)]
 
 
 _MFIELDS = ["r", "th", "f", "g", "h11", "h22", "h33", "h13", "H11", "H22", "H33", "H13",
@@ -131,12 +132,13 @@ def _dp(a):
 
 def make_params(cfg: dict) -> Params:
     """cfg keys: metric ('ks' | 'ks0'), a, n_r, n_theta, r_min, r_max, dt, n_iter,
-    small_angle, n_filter, r_absorb, absorb_coef."""
+    small_angle, n_filter, r_absorb, absorb_coef, r0, h0 (quasi-spherical map)."""
     return Params(1 if cfg.get("metric", "ks") == "ks" else 0, float(cfg.get("a", 0.0)),
                   int(cfg["n_r"]), int(cfg["n_theta"]), float(cfg["r_min"]), float(cfg["r_max"]),
                   float(cfg.get("dt", 0.0)), int(cfg.get("n_iter", 10)),
                   float(cfg.get("small_angle", 1e-5)), int(cfg.get("n_filter", 0)),
-                  float(cfg.get("r_absorb", 1e300)), float(cfg.get("absorb_coef", 1.0)))
+                  float(cfg.get("r_absorb", 1e300)), float(cfg.get("absorb_coef", 1.0)),
+                  float(cfg.get("r0", 0.0)), float(cfg.get("h0", 0.0)))
 
 
 def metric_point(cfg, x1, x2, clamp=False):

@@ -18,6 +18,9 @@ CASES = [
     dict(metric="ks", a=0.995, n_r=512, n_theta=512, r_min=1.0, r_max=15.0),
     dict(metric="ks", a=0.0, n_r=100, n_theta=80, r_min=1.8, r_max=20.0),
     dict(metric="ks0", a=0.0, n_r=50, n_theta=40, r_min=1.0, r_max=20.0),
+    # quasi-spherical grids of App. A: radial offset r0 and equatorial concentration h0
+    dict(metric="ks", a=0.9, n_r=64, n_theta=64, r_min=1.3641, r_max=10.0, r0=0.4, h0=0.45),
+    dict(metric="ks", a=0.5, n_r=80, n_theta=60, r_min=1.2, r_max=30.0, r0=-1.0, h0=0.8),
 ]
 PTS = [(0.3, 0.7), (10.5, 3.25), (33.3, 17.9), (40.0, 31.5), (47.9, 5.1)]
 
@@ -64,7 +67,7 @@ def test_inverse_and_determinant(cfg, pt):
     assert math.isclose(m["sqrt_h"], m["sqrt_ht"] * math.sin(m["th"]), rel_tol=1e-14)
 
 
-@pytest.mark.parametrize("cfg", CASES[:3])
+@pytest.mark.parametrize("cfg", CASES[:3] + CASES[4:])
 @pytest.mark.parametrize("pt", PTS)
 def test_split_reproduces_appendix_4metric(cfg, pt):
     """g^00 = -1/alpha^2, g^0i = beta^i/alpha^2, g^ij = h^ij - beta^i beta^j/alpha^2,
@@ -127,7 +130,7 @@ def test_derivatives_against_finite_differences(cfg):
                 assert abs(fd - an) <= 1e-8 * scale + 1e-14, (cfg, pt, d, k, fd, an)
 
 
-@pytest.mark.parametrize("cfg", [CASES[0], CASES[2], CASES[3]])
+@pytest.mark.parametrize("cfg", [CASES[0], CASES[2], CASES[3], CASES[4], CASES[5]])
 def test_polar_area(cfg):
     """A(x1) = integral_0^{1/2} sqrt(h) dx2 (Sec. 3.3.2). Exact for a = 0 or flat; with
     spin the closed form takes Sigma on the axis, so it agrees to O(a^2 dtheta^2)."""
@@ -137,7 +140,8 @@ def test_polar_area(cfg):
         integral = np.sum(0.5 * (vals[1:] + vals[:-1]) * np.diff(xs))
         A = O.polar_area(cfg, x1)
         r = O.metric_point(cfg, x1, 0.25)["r"]
-        tol = cfg["a"] ** 2 * (0.5 * math.pi / cfg["n_theta"]) ** 2 / r ** 2 + 1e-7
+        th_half = O.metric_point(cfg, x1, 0.5)["th"]  # the half cell's polar extent
+        tol = cfg["a"] ** 2 * th_half ** 2 / r ** 2 + 1e-7
         assert abs(A - integral) <= tol * integral
 
 
