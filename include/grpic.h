@@ -130,6 +130,11 @@ typedef struct {
                            of them): the FP64 fixed point to about rho iter_tol (rho < 1 the
                            contraction of the iteration), in fewer FP64 operations. Must be
                            below 1e-6                                                          */
+  double r0, h0;        /* quasi-spherical Kerr-Schild grid (App. A): r = r0 + exp(xi), xi
+                           uniform in x1 (r0 < r_min); theta = eta + 2 h0 eta (pi - 2 eta)
+                           (pi - eta) / pi^2, eta uniform in x2 (-1/2 < h0 < 1; h0 > 0 puts
+                           cells toward the equator). 0, 0: the plain log-r grid with uniform
+                           theta. The adjoint entry points need 0, 0                          */
   int massless[GRPIC_MAX_SPECIES]; /* 1: a species of massless particles (photons): gamma =
                            sqrt(h^ij u_i u_j) (Sec. 2.3), no field interpolation and no EM
                            push (Sec. 3.1), only the two geodesic substeps and phi; they are
@@ -352,8 +357,8 @@ GRPIC_API grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double
  * State layout (device, caller-owned): [6][n] doubles, rows x1, x2 (absolute code
  * coordinates), phi, u_1, u_2, u_3 (covariant momenta per unit mass). The fields are the
  * em planes (B, D) times b0 / field_b0, where field_b0 is the amplitude given to
- * grpic_init_fields (1 for GRPIC_FIELD_USER); the Wald, vertical and monopole fields are linear in B0,
- * so b0 is the field amplitude. Both implicit substeps iterate to an exact repeat of the
+ * grpic_init_fields (1 for GRPIC_FIELD_USER); the Wald, vertical and monopole fields are
+ * linear in B0, so b0 is the field amplitude. Both implicit substeps iterate to an exact repeat of the
  * iterate, at most n_iter times. A particle whose step would leave 0 <= x1 < n_r,
  * 0 <= x2 <= n_theta (the horizon layer, the outer edge or an axis, where the boundary rules
  * of Sec. 3.3.3 act) is frozen and reported as NaN.
@@ -362,7 +367,8 @@ GRPIC_API grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double
  * at steps 0, ckpt_every, 2 ckpt_every, ... < n_steps: ceil(n_steps / ckpt_every) x 6 x n
  * doubles (may be null when n_steps == 0).
  * Errors: GRPIC_ESTATE (mixed context, fields not initialised), GRPIC_EINVAL (n < 0,
- * n_steps < 0, ckpt_every < 1, n_iter outside [1, 1000], field_b0 = 0, null buffers). */
+ * n_steps < 0, ckpt_every < 1, n_iter outside [1, 1000], field_b0 = 0, null buffers, a
+ * quasi-spherical grid with r0 or h0 != 0). */
 GRPIC_API grpic_status grpic_adjoint_forward(grpic_ctx *ctx, int64_t n, double qm, double b0,
                                              int n_steps, int ckpt_every, int n_iter,
                                              const double *state0, double *state_out,

@@ -50,7 +50,7 @@ class Config(C.Structure):
                 ("sort_every", C.c_int), ("tile_r", C.c_int), ("tile_theta", C.c_int),
                 ("precision", C.c_int), ("full_iterations", C.c_int),
                 ("fp64_guard_cells", C.c_int), ("tiled_push", C.c_int), ("iter_tol", C.c_double),
-                ("massless", C.c_int * MAX_SPECIES)]
+                ("r0", C.c_double), ("h0", C.c_double), ("massless", C.c_int * MAX_SPECIES)]
 
 
 _VP = C.c_void_p
@@ -165,6 +165,8 @@ def make_config(cfg: dict, capacities) -> Config:
     c.fp64_guard_cells = int(cfg.get("fp64_guard_cells", 0))
     c.tiled_push = int(cfg.get("tiled_push", 0))
     c.iter_tol = float(cfg.get("iter_tol", 0.0))
+    c.r0 = float(cfg.get("r0", 0.0))
+    c.h0 = float(cfg.get("h0", 0.0))
     # species indices of massless particles (photons)
     for i in cfg.get("massless", ()):
         c.massless[int(i)] = 1

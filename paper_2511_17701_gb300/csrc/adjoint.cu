@@ -26,12 +26,19 @@ constexpr int TPB_ADJ = 64;
 using D2 = Dual<2>;
 using D4 = Dual<4>;
 
-// r, sin(theta), cos(theta) at absolute code coordinates; theta clamped to
-// [small_angle, pi - small_angle] for the metric (Sec. 3.3.2), with zero derivative there.
+// the point at absolute code coordinates on the plain log-r grid (the adjoint's entry points
+// reject quasi-spherical grids): r, sin(theta), cos(theta) with theta clamped to
+// [small_angle, pi - small_angle] for the metric (Sec. 3.3.2), with zero derivative there,
+// and the map's factors f = dxi r, gg = dtheta
 template <typename R>
-__device__ __forceinline__ void rsc_abs(const GridP &g, const R &x1, const R &x2, R &r, R &s,
-                                        R &c) {
-  r = g.r_min * exp_(x1 * g.dxi);
+__device__ __forceinline__ void rsc_abs(const GridP &g, const R &x1, const R &x2, Pt<R> &p) {
+  const R e = g.r_min * exp_(x1 * g.dxi);
+  p.r = e;
+  p.f = g.dxi * e;
+  p.gg = R(g.dth);
+  p.igg = R(g.ig2);
+  p.gp = R(0.0);
+  R &s = p.s, &c = p.c;
   const R th = x2 * g.dth;
   const double tv = val(th);
   if (tv < g.small_angle || tv > GRPIC_PI - g.small_angle) {
@@ -76,9 +83,9 @@ __device__ __forceinline__ void frame_at(const GridP &g, const FieldPtrsT<double
   Dv[0] = interp_abs(F.D[0], g.NX, x[0], x[1], 0.5, 0.0);
   Dv[1] = interp_abs(F.D[1], g.NX, x[0], x[1], 0.0, 0.5);
   Dv[2] = interp_abs(F.D[2], g.NX, x[0], x[1], 0.0, 0.0);
-  R r, s, c;
-  rsc_abs(g, x[0], x[1], r, s, c);
-  local_full(g, r, s, c, fr.L);
+  Pt<R> p;
+  rsc_abs(g, x[0], x[1], p);
+  local_full(g, p, fr.L);
   vec_hat(fr.L, Bv, fr.Bh1);
   vec_hat(fr.L, Dv, fr.Dh1);
   for (int i = 0; i < 3; ++i) {
@@ -109,9 +116,9 @@ __device__ __forceinline__ void velocity(const Geo<M> &o, const R u[3], R &v1, R
 }
 template <typename R>
 __device__ __forceinline__ void geo_abs(const GridP &g, const R &x1, const R &x2, Geo<R> &o) {
-  R r, s, c;
-  rsc_abs(g, x1, x2, r, s, c);
-  geo_from_rsc(g, r, s, c, o);
+  Pt<R> p;
+  rsc_abs(g, x1, x2, p);
+  geo_from_rsc(g, p, o);
 }
 
 // dphi/dt of Eq. (discretized-geodesic-x-phi) at a point

@@ -301,13 +301,16 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   if ((int64_t)(c.n_r + 2 * G_ + 1) * (c.n_theta + 2 * G_ + 1) >= ((int64_t)1 << 31))
     return GRPIC_EINVAL;
   if (!(c.r_min > 0.0) || !(c.r_max > c.r_min)) return GRPIC_EINVAL;
+  // the quasi-spherical map (App. A): r0 below r_min; theta(eta) monotone for -1/2 < h0 < 1
+  if (!(c.r0 < c.r_min) || !isfinite(c.r0) || !(c.h0 > -0.5 && c.h0 < 1.0)) return GRPIC_EINVAL;
   if (c.metric == GRPIC_METRIC_KS && !(c.a >= 0.0 && c.a < 1.0)) return GRPIC_EINVAL;
   if (c.n_iter < 1 || c.n_iter > 1000) return GRPIC_EINVAL;
   if (!(c.small_angle > 0.0 && c.small_angle < 0.1)) return GRPIC_EINVAL;
   if (c.n_filter < 0 || c.n_filter + 2 >= c.n_r || c.n_filter > 64) return GRPIC_EINVAL;
   // Sec. 3.3.3: the inner boundary lies at least n_f + 1 cells inside the event horizon
   if (c.metric == GRPIC_METRIC_KS &&
-      !(c.r_min * exp((c.n_filter + 1) * log(c.r_max / c.r_min) / c.n_r) <= 1.0 + sqrt(1.0 - c.a * c.a)))
+      !(c.r0 + (c.r_min - c.r0) * exp((c.n_filter + 1) * log((c.r_max - c.r0) / (c.r_min - c.r0)) /
+                                      c.n_r) <= 1.0 + sqrt(1.0 - c.a * c.a)))
     return GRPIC_EINVAL;
   if (c.n_species < 1 || c.n_species > GRPIC_MAX_SPECIES) return GRPIC_EINVAL;
   if (c.precision != GRPIC_FP64 && c.precision != GRPIC_MIXED) return GRPIC_EINVAL;
@@ -333,7 +336,11 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   g.stop_on_repeat = c.full_iterations ? 0 : 1;
   g.iter_tol = c.iter_tol;
   g.r_min = c.r_min; g.r_max = c.r_max;
-  g.dxi = log(c.r_max / c.r_min) / c.n_r;
+  g.r0 = c.r0; g.h0 = c.h0;
+  g.e_min = c.r_min - c.r0;
+  g.qks = (c.r0 != 0.0 || c.h0 != 0.0) ? 1 : 0;
+  g.c3 = 4.0 * c.h0 / (GRPIC_PI * GRPIC_PI);
+  g.dxi = log((c.r_max - c.r0) / (c.r_min - c.r0)) / c.n_r;
   g.dth = GRPIC_PI / c.n_theta;
   g.ig2 = 1.0 / (g.dth * g.dth);
   g.a = c.metric == GRPIC_METRIC_KS ? c.a : 0.0;
@@ -349,7 +356,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   int ih = -1000000;
   if (g.M > 0.0) {
     const double rh = 1.0 + sqrt(1.0 - g.a * g.a);
-    ih = (int)floor(log(rh / g.r_min) / g.dxi);
+    ih = (int)floor(log((rh - g.r0) / (g.r_min - g.r0)) / g.dxi);
   }
   ctx->tb.guard_ilo = ih - guard;
   ctx->tb.guard_ihi = ih + guard + 1;
@@ -360,7 +367,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   ctx->off_planes = off; off += up(ps * fs) * 36;
   ctx->off_tab = off;    off += up(ps * fs) * 4 * T_NQ;
   ctx->off_polar = off;  off += up((size_t)g.NX * fs);
-  ctx->off_ptab = off;   off += 6 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 8);
+  ctx->off_ptab = off;   off += 10 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 8);
   ctx->off_dt = off;     off += up(64);
   ctx->off_diag = off;   off += up(DG_N * 8);
   ctx->max_cap = 1;
@@ -422,6 +429,10 @@ grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream)
   ctx->tb.r64 = at<double>(ctx, ctx->off_ptab + 3 * tstride);
   ctx->tb.s64 = at<double>(ctx, ctx->off_ptab + 4 * tstride);
   ctx->tb.c64 = at<double>(ctx, ctx->off_ptab + 5 * tstride);
+  ctx->tb.t1 = at<float>(ctx, ctx->off_ptab + 6 * tstride);
+  ctx->tb.t2 = at<float>(ctx, ctx->off_ptab + 7 * tstride);
+  ctx->tb.t1_64 = at<double>(ctx, ctx->off_ptab + 8 * tstride);
+  ctx->tb.t2_64 = at<double>(ctx, ctx->off_ptab + 9 * tstride);
   if (ctx->mixed) {
     for (int s = 0; s < ctx->cfg.n_species; ++s) {
       SpeciesState &sp = ctx->sp[s];
@@ -816,6 +827,7 @@ static grpic_status adjoint_args(grpic_ctx *ctx, int64_t n, double b0, int n_ste
     return fail(ctx, GRPIC_EINVAL, "bad adjoint sizes");
   if (!(ctx->field_b0 != 0.0) || !isfinite(b0))
     return fail(ctx, GRPIC_EINVAL, "field amplitude %g against planes of %g", b0, ctx->field_b0);
+  if (ctx->g.qks) return fail(ctx, GRPIC_EINVAL, "the adjoint takes the plain log-r grid (r0 = h0 = 0)");
   return GRPIC_OK;
 }
 

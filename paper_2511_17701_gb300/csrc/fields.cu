@@ -17,7 +17,8 @@ __device__ __forceinline__ T tabv(const T *tab, const GridP &g, int cls, int q, 
 // ---------------------------------------------------------------------------------
 // Tables: per Yee class, alpha, h_11, h_22, h_33, sqrt(h~), [sqrt(h~) h_13],
 // [sqrt(h~ h) beta^1], 1/sqrt(h) at every stored point; the polar area
-// A(x1) = dr (r^2 + a^2) sqrt(1 + 2 M r/(r^2 + a^2)) (1 - cos(dtheta/2)) (App. A, per unit phi).
+// A(x1) = dr (r^2 + a^2) sqrt(1 + 2 M r/(r^2 + a^2)) (1 - cos(theta(x2 = 1/2))) (App. A, per
+// unit phi; theta(1/2) = dtheta/2 on the plain grid).
 // ---------------------------------------------------------------------------------
 template <typename T>
 __global__ void k_metric_tables(GridP g, T *tab, T *polar) {
@@ -41,9 +42,9 @@ __global__ void k_metric_tables(GridP g, T *tab, T *polar) {
     o[T_WB1 * ps] = (T)(m.sqrt_ht * m.sqrt_h * m.beta1);
     o[T_ISH * ps] = (T)(1.0 / m.sqrt_h);
     if (cls == CLS_HN && j == 0) {
-      const double r = g.r_min * exp((i + 0.5) * g.dxi), a2 = g.a * g.a;
-      polar[i + G_] = (T)(g.dxi * r * (r * r + a2) * sqrt(1.0 + 2.0 * g.M * r / (r * r + a2)) *
-                          (1.0 - cos(0.5 * g.dth)));
+      const double e = map_e(g, i + 0.5), r = g.r0 + e, a2 = g.a * g.a;
+      polar[i + G_] = (T)(g.dxi * e * (r * r + a2) * sqrt(1.0 + 2.0 * g.M * r / (r * r + a2)) *
+                          (1.0 - cos(map_theta(g, 0.5))));
     }
   }
 }
@@ -91,16 +92,34 @@ __device__ double inv_sqrt_h(const GridP &g, double x1, double x2) {
   return 1.0 / m.sqrt_h;
 }
 
-// A_1(x1, j + 1) - A_1(x1, j) of the Wald potential (Eq. Wald) for the discrete curl that
-// gives B^3, in product form: with A_1 = (B0/2) a f (2 M r (1 + cos^2)/Sigma - sin^2) and
-// sin^2(b) - sin^2(a) = sin(b - a) sin(b + a) = -(cos^2(b) - cos^2(a)),
-//   dA_1 = -(B0/2) a f D (1 + 2 M r (r^2 - a^2) / (Sigma_a Sigma_b)), D = sin(dth) sin((2j+1) dth);
+// theta_j + theta_{j+1} and theta_{j+1} - theta_j of two face rows; with h0 the cubic's
+// difference p(eta + d) - p(eta) = d (pi^2 - 6 pi eta + 6 eta^2) + d^2 (6 eta - 3 pi) + 2 d^3
+// (p(eta) = eta (pi - 2 eta)(pi - eta)) is expanded so that nothing cancels
+__device__ double theta_sum(const GridP &g, int j) {
+  const double de = g.dth, e0 = j * de, e1 = (j + 1) * de, k = 2.0 * g.h0 / (GRPIC_PI * GRPIC_PI);
+  const double p0 = e0 * (GRPIC_PI - 2.0 * e0) * (GRPIC_PI - e0);
+  const double p1 = e1 * (GRPIC_PI - 2.0 * e1) * (GRPIC_PI - e1);
+  return (2 * j + 1) * de + k * (p0 + p1);
+}
+__device__ double theta_diff(const GridP &g, int j) {
+  const double de = g.dth, e0 = j * de, k = 2.0 * g.h0 / (GRPIC_PI * GRPIC_PI);
+  return de + k * (de * (GRPIC_PI * GRPIC_PI - 6.0 * GRPIC_PI * e0 + 6.0 * e0 * e0) +
+                   de * de * (6.0 * e0 - 3.0 * GRPIC_PI) + 2.0 * de * de * de);
+}
+
+// A_1(x1, theta_{j+1}) - A_1(x1, theta_j) of the Wald potential (Eq. Wald) for the discrete
+// curl that gives B^3, in product form: with A_1 = (B0/2) a f (2 M r (1 + cos^2)/Sigma -
+// sin^2) and sin^2(b) - sin^2(a) = sin(b - a) sin(b + a) = -(cos^2(b) - cos^2(a)),
+//   dA_1 = -(B0/2) a f D (1 + 2 M r (r^2 - a^2) / (Sigma_a Sigma_b)),
+//   D = sin(theta_{j+1} - theta_j) sin(theta_{j+1} + theta_j);
 // the plain difference loses ~1/dth^2 of its digits next to the axes (A_1 ~ theta^2 there).
-// A_3(x1, j + 1) - A_3(x1, j) for the discrete curl that gives B^1; for the monopole,
-// -B0 (cos((j+1) dth) - cos(j dth)) = 2 B0 sin((j + 1/2) dth) sin(dth / 2) in product form
-// (the plain difference of the cosines loses ~1/dth^2 of its digits next to the axes)
+// A_3(x1, theta_{j+1}) - A_3(x1, theta_j) for the discrete curl that gives B^1; for the
+// monopole, -B0 (cos(theta_{j+1}) - cos(theta_j)) = 2 B0 sin((theta_j + theta_{j+1}) / 2)
+// sin((theta_{j+1} - theta_j) / 2) in product form (the plain difference of the cosines
+// loses ~1/dth^2 of its digits next to the axes)
 __device__ double dA3_theta(const GridP &g, int kind, double B0, int i, int j) {
-  if (kind == GRPIC_FIELD_MONOPOLE) return 2.0 * B0 * sin((j + 0.5) * g.dth) * sin(0.5 * g.dth);
+  if (kind == GRPIC_FIELD_MONOPOLE)
+    return 2.0 * B0 * sin(0.5 * theta_sum(g, j)) * sin(0.5 * theta_diff(g, j));
   Pot pa, pb;
   potential(g, kind, B0, i, j, false, pa);
   potential(g, kind, B0, i, j + 1, false, pb);
@@ -110,10 +129,10 @@ __device__ double dA3_theta(const GridP &g, int kind, double B0, int i, int j) {
 __device__ double dA1_theta(const GridP &g, int kind, double B0, double x1, int j) {
   if (kind != GRPIC_FIELD_WALD) return 0.0;  // the vertical field has A_1 = 0
   const double a = g.a, M = g.M;
-  const double r = g.r_min * exp(x1 * g.dxi), f = g.dxi * r;
-  const double ca = cos(j * g.dth), cb = cos((j + 1) * g.dth);
+  const double e = map_e(g, x1), r = g.r0 + e, f = g.dxi * e;
+  const double ca = cos(map_theta(g, j)), cb = cos(map_theta(g, j + 1));
   const double Sa = r * r + a * a * ca * ca, Sb = r * r + a * a * cb * cb;
-  const double D = sin(g.dth) * sin((2 * j + 1) * g.dth);
+  const double D = sin(theta_diff(g, j)) * sin(theta_sum(g, j));
   return -0.5 * B0 * a * f * D * (1.0 + 2.0 * M * r * (r * r - a * a) / (Sa * Sb));
 }
 
@@ -299,7 +318,7 @@ __global__ void k_aux_H(GridP g, Pair3<T> B, Pair3<T> D, const T *tab, T *H1, T 
 template <typename T>
 __device__ __forceinline__ T match(const GridP &g, T v, T vi, double x1, int j) {
   if (!(g.r_absorb < g.r_max) || j < 0 || j > g.n_th) return v;
-  const double r = g.r_min * exp(x1 * g.dxi);
+  const double r = g.r0 + map_e(g, x1);
   if (r <= g.r_absorb) return v;
   double x = (r - g.r_absorb) / (g.r_max - g.r_absorb);
   x = fmin(x, 1.0);

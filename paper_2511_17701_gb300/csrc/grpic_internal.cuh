@@ -2,8 +2,10 @@
 // translation units of libgrpic (not installed, not part of the C ABI).
 //
 // Geometry follows Appendix A of arXiv:2511.17701 in code units: the quasi-spherical
-// Kerr-Schild map with r0 = 0, h0 = 0 (r = r_min exp(x1 dxi), theta = x2 dtheta,
-// dphi = 1), with mass M = 1 (Kerr-Schild) or M = 0 and a = 0 (kerr_schild_0, flat).
+// Kerr-Schild map r = r0 + exp(xi), xi = log(r_min - r0) + x1 dxi, theta = eta +
+// 2 h0 eta (pi - 2 eta)(pi - eta) / pi^2 with eta = x2 deta (deta = pi / n_theta, called dth
+// here), dphi = 1; r0 = h0 = 0 is the plain log-r grid with uniform theta. Mass M = 1
+// (Kerr-Schild) or M = 0 and a = 0 (kerr_schild_0, flat).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -21,14 +23,51 @@ struct GridP {
                        // once the update is at most iter_tol max(1, |value|)
   double r_min, r_max, dxi, dth, a, M, dt, small_angle, r_absorb, absorb_coef;
   double ig2;  // 1 / dth^2
+  // quasi-spherical map: radial offset, equatorial concentration, qks = (r0 != 0 || h0 != 0),
+  // c3 = 4 h0 / pi^2 (the cubic coefficient of theta(eta_j + d) - theta(eta_j))
+  double r0, h0, c3;
+  double e_min;  // r_min - r0 = exp(xi) at x1 = 0
+  int qks;
   // FP32 copies for the mixed path (read from the kernel parameters, no conversions)
-  float f_a, f_M, f_dxi, f_dth, f_ig2, f_dt, f_idt;
+  float f_a, f_M, f_dxi, f_dth, f_ig2, f_dt, f_idt, f_r0, f_c3;
 };
 
 // Fill the FP32 copies once a, M, dxi, dth and dt are set.
 inline void grid_float_copies(GridP &g) {
   g.f_a = (float)g.a; g.f_M = (float)g.M; g.f_dxi = (float)g.dxi; g.f_dth = (float)g.dth;
   g.f_ig2 = (float)g.ig2; g.f_dt = (float)g.dt; g.f_idt = g.dt > 0.0 ? (float)(1.0 / g.dt) : 0.0f;
+  g.f_r0 = (float)g.r0; g.f_c3 = (float)g.c3;
+}
+
+// The quasi-spherical map at a point (App. A): r with e = exp(xi) = r - r0 and f = dr/dx1 =
+// dxi e; theta, g = dtheta/dx2 and gp = dg/dx2. theta is formed in the operation order of
+// the plain definition, each operation rounded (no contraction): near theta = pi sin(theta)
+// is ill-conditioned in theta and every other rounding of it shows at ~1e-13.
+__host__ __device__ inline double map_e(const GridP &g, double x1) {
+  return g.e_min * exp(x1 * g.dxi);
+}
+// Q = false: the plain grid is known at compile time (the hot kernels' instantiation for
+// it); Q = true decides at run time
+template <bool Q = true>
+__device__ __forceinline__ double map_theta(const GridP &g, double x2) {
+  const double eta = __dmul_rn(x2, g.dth);
+  if (!(Q && g.qks)) return eta;
+  const double q = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, g.h0), eta),
+                                       __dadd_rn(GRPIC_PI, -__dmul_rn(2.0, eta))),
+                             __dadd_rn(GRPIC_PI, -eta));
+  return __dadd_rn(eta, __ddiv_rn(q, __dmul_rn(GRPIC_PI, GRPIC_PI)));
+}
+// g = deta (1 + 2 h0 + 12 h0 (eta/pi)(eta/pi - 1)), gp = deta^2 12 h0 (2 eta/pi^2 - 1/pi)
+template <bool Q = true>
+__device__ __forceinline__ void map_g(const GridP &g, double x2, double &gg, double &gp) {
+  if (!(Q && g.qks)) {
+    gg = g.dth;
+    gp = 0.0;
+    return;
+  }
+  const double eta = x2 * g.dth, u = eta / GRPIC_PI;
+  gg = g.dth * (1.0 + 2.0 * g.h0 + 12.0 * g.h0 * u * (u - 1.0));
+  gp = g.dth * g.dth * 12.0 * g.h0 * (2.0 * u - 1.0) / GRPIC_PI;
 }
 
 // The grid constants in the arithmetic type R.
@@ -97,9 +136,11 @@ template <bool DERIV>
 __device__ __forceinline__ void metric_eval(const GridP &g, double x1, double x2, bool clamp,
                                             MetricV &m, MetricD *d) {
   const double a = g.a, M = g.M, a2 = a * a;
-  const double r = g.r_min * exp(x1 * g.dxi);
-  double th = x2 * g.dth;
+  const double e = map_e(g, x1), r = g.r0 + e;
+  double th = map_theta(g, x2);
   if (clamp) th = fmin(fmax(th, g.small_angle), GRPIC_PI - g.small_angle);
+  double gg, gp;
+  map_g(g, x2, gg, gp);
   double s, c;
   sincos(th, &s, &c);
   const double s2 = s * s, r2 = r * r;
@@ -109,8 +150,7 @@ __device__ __forceinline__ void metric_eval(const GridP &g, double x1, double x2
   const double iSig = 1.0 / Sig;
   const double z = 2.0 * M * r * iSig;
   const double al2 = 1.0 / (1.0 + z);          // alpha^2 = 1/(1+z)
-  const double f = g.dxi * r, fi = 1.0 / f;     // d xi e^xi and its inverse
-  const double gg = g.dth;                      // d eta (d theta / d eta), h0 = 0
+  const double f = g.dxi * e, fi = 1.0 / f;     // d xi e^xi and its inverse
   m.alpha = sqrt(al2);
   m.h11 = f * f * (1.0 + z);
   m.h13 = -f * a * (1.0 + z) * s2;
@@ -136,7 +176,7 @@ __device__ __forceinline__ void metric_eval(const GridP &g, double x1, double x2
                2.0 * g.dxi * m.H11;
     d->d2H11 = (P * deA - 2.0 * A * deS * (M * r + Sig)) * iP2 * fi * fi;
     d->d1H22 = -dxS * iS2 / (gg * gg);
-    d->d2H22 = -deS * iS2 / (gg * gg);
+    d->d2H22 = -deS * iS2 / (gg * gg) - 2.0 * m.H22 * gp / gg;  // dg/dx2 = gp (h0 != 0)
     d->d1H33 = -dxS * iS2 / s2;
     d->d2H33 = -(deS + 2.0 * (c / s) * Sig * gg) * iS2 / s2;
     d->d1H13 = -a * iS2 * dxS * fi - g.dxi * a * iSig * fi;
@@ -160,10 +200,12 @@ struct Pot {
 __device__ __forceinline__ void potential(const GridP &g, int kind, double B0, double x1, double x2, bool derivs,
                           Pot &p) {
   const double a = g.a, M = g.M, a2 = a * a;
-  const double r = g.r_min * exp(x1 * g.dxi), th = x2 * g.dth;
+  const double e = map_e(g, x1), r = g.r0 + e, th = map_theta(g, x2);
   double s, c;
   sincos(th, &s, &c);
-  const double s2 = s * s, f = g.dxi * r, gg = g.dth;
+  double gg, gp;
+  map_g(g, x2, gg, gp);
+  const double s2 = s * s, f = g.dxi * e;
   if (kind == GRPIC_FIELD_VERTICAL) {
     p.A0 = 0.0; p.A1 = 0.0; p.A3 = 0.5 * B0 * r * r * s2;
     p.d1A0 = p.d2A0 = p.d2A1 = 0.0;
@@ -272,8 +314,13 @@ using FieldPtrs = FieldPtrsT<double>;
 // Per-cell tables of the FP32 pusher (mixed precision), computed in FP64: r at x1 = i,
 // sin and cos of theta at x2 = j, for stored i, j.
 struct PushTables {
-  const float *r, *s, *c;           // r at cell corners i, sin/cos(theta) at corners j
+  const float *r, *s, *c;           // e = r - r0 at cell corners i, sin/cos(theta) at corners j
   const double *r64, *s64, *c64;    // the same in FP64, for the guard zones
+  // quasi-spherical theta: per corner row j, theta(eta_j + d) - theta(eta_j) =
+  // d (t1_j + d (t2_j + d c3)) for an offset d in eta (t1 = dtheta/deta, t2 = its half
+  // derivative); 1 and 0 on the plain grid
+  const float *t1, *t2;
+  const double *t1_64, *t2_64;
   int guard_ilo, guard_ihi;  // cells guard_ilo <= i1 < guard_ihi (around the horizon) and
   int guard_j;               // within guard_j of an axis evaluate the metric in FP64
 };

@@ -21,14 +21,14 @@ __device__ __forceinline__ void count(unsigned long long *diag, int which) {
 // FP64 routine. r and sin/cos at the iterates follow from their values at x^n by the
 // exponential and angle-addition formulas with short Taylor series of the small offsets
 // (|eps| <= 0.02: truncation below 1e-18); CUDA's exp/sincos beyond that and in the
-// SMALL_ANGLE_GR clamp. theta at every point is formed as one rounded product x2 dtheta
-// with x2 rounded as the oracle rounds it, and its offset from theta(x^n) is exact
-// (Sterbenz): near theta = pi sin(theta) is ill-conditioned in theta, so any other way of
-// forming theta would move the result by ~1e-12 relative.
+// SMALL_ANGLE_GR clamp. theta at every point is formed as the oracle forms it (map_theta:
+// x2 dtheta, then the quasi-spherical cubic, each operation rounded), and its offset from
+// theta(x^n) is exact (Sterbenz): near theta = pi sin(theta) is ill-conditioned in theta,
+// so any other way of forming theta would move the result by ~1e-12 relative.
 // =================================================================================
 struct Base {
   double x1, th0;     // x^n and theta(x^n) (not clamped)
-  double r0, s0, c0;  // r, sin(theta), cos(theta) at x^n
+  double e0, s0, c0;  // exp(xi) = r - r0, sin(theta), cos(theta) at x^n
 };
 
 __device__ __forceinline__ double exp_small(double e) {  // exp(e), |e| <= 0.02
@@ -42,25 +42,37 @@ __device__ __forceinline__ double exp_small(double e) {  // exp(e), |e| <= 0.02
   return fma(p, e, 1.0);
 }
 
+template <bool Q = true>
 __device__ __forceinline__ Base make_base(const GridP &g, double x1, double x2) {
   Base b;
   b.x1 = x1;
-  b.th0 = __dmul_rn(x2, g.dth);
-  b.r0 = g.r_min * exp(x1 * g.dxi);
+  b.th0 = map_theta<Q>(g, x2);
+  b.e0 = map_e(g, x1);
   sincos(b.th0, &b.s0, &b.c0);
   return b;
 }
 
-// r, sin(theta), cos(theta) at code position (x1t, x2t), theta clamped to
-// [small_angle, pi - small_angle]
+// the point (x1t, x2t): r, sin(theta), cos(theta) with theta clamped to [small_angle,
+// pi - small_angle], and the map's factors
+template <bool Q = true>
 __device__ __forceinline__ void local_rsc(const GridP &g, const Base &b, double x1t, double x2t,
-                                          double &r, double &s, double &c) {
+                                          Pt<double> &p) {
   const double e1 = (x1t - b.x1) * g.dxi;
-  r = fabs(e1) <= 0.02 ? b.r0 * exp_small(e1) : g.r_min * exp(x1t * g.dxi);
-  const double th = __dmul_rn(x2t, g.dth);
+  const double ex = fabs(e1) <= 0.02 ? b.e0 * exp_small(e1) : map_e(g, x1t);
+  p.r = Q ? g.r0 + ex : ex;
+  p.f = g.dxi * ex;
+  if (Q && g.qks) {
+    map_g<Q>(g, x2t, p.gg, p.gp);
+    p.igg = 1.0 / (p.gg * p.gg);
+  } else {
+    p.gg = g.dth;
+    p.igg = g.ig2;
+    p.gp = 0.0;
+  }
+  const double th = map_theta<Q>(g, x2t);
   const double e2 = th - b.th0;
   if (th < g.small_angle || th > GRPIC_PI - g.small_angle) {
-    sincos(fmin(fmax(th, g.small_angle), GRPIC_PI - g.small_angle), &s, &c);
+    sincos(fmin(fmax(th, g.small_angle), GRPIC_PI - g.small_angle), &p.s, &p.c);
   } else if (fabs(e2) <= 0.02) {
     const double q = e2 * e2;
     double sp = -1.0 / 5040.0;
@@ -72,21 +84,22 @@ __device__ __forceinline__ void local_rsc(const GridP &g, const Base &b, double 
     cp = fma(cp, q, 1.0 / 24.0);
     cp = fma(cp, q, -0.5);
     const double ce = fma(cp, q, 1.0);      // cos(e2)
-    s = fma(b.s0, ce, b.c0 * se);
-    c = fma(b.c0, ce, -b.s0 * se);
+    p.s = fma(b.s0, ce, b.c0 * se);
+    p.c = fma(b.c0, ce, -b.s0 * se);
   } else {
-    sincos(th, &s, &c);
+    sincos(th, &p.s, &p.c);
   }
 }
 
 // dphi/dt = alpha/gamma h^{3j} u_j at (x1t, x2t) (Eq. discretized-geodesic-x-phi; q times
 // it is J^3 / sqrt(h) w, Sec. 3.2); alpha/gamma = 1/sqrt((1+z) gamma^2).
+template <bool Q = true>
 __device__ __forceinline__ double phi_rate64(const GridP &g, const Base &b, double x1t,
                                              double x2t, const double u[3], double m2) {
-  double r, sn, cs;
-  local_rsc(g, b, x1t, x2t, r, sn, cs);
+  Pt<double> p;
+  local_rsc<Q>(g, b, x1t, x2t, p);
   Geo<double> o;
-  geo_from_rsc(g, r, sn, cs, o);
+  geo_from_rsc(g, p, o);
   const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1], fma(o.H33 * u[2], u[2],
                    fma(2.0 * o.H13 * u[0], u[2], m2))));
   return rsqrt(o.opz * q) * fma(o.H13, u[0], o.H33 * u[2]);
@@ -177,14 +190,15 @@ __device__ __forceinline__ bool method_converges(double d1, double D1, double D2
   return (float)d1 * exp2f((float)n_iter * log2f(rho)) <= (float)(0.1 * tol * scale);
 }
 
+template <bool Q = true>
 __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTables &tb, int i1,
                                                  int i2, float o1, float o2,
                                                  const Local<double> &L, double u[3],
                                                  double m2) {
-  float r, sn, cs;
-  rsc32(g, tb, i1, i2, o1, o2, r, sn, cs);
+  Pt<float> pf;
+  rsc32<Q>(g, tb, i1, i2, o1, o2, pf);
   Local<float> Lf;
-  local_full(g, r, sn, cs, Lf);
+  local_full<Q>(g, pf, Lf);
   const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
   const GeoMap<float> mf(g, Lf, uf, (float)m2);
   float p0 = uf[0], p1 = uf[1], d1 = 0.0f;
@@ -227,6 +241,7 @@ __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTable
 // The coordinate substep, Eq. (discretized-geodesic-x), as the method iterates it: metric at
 // x_bar = (x^n + x~)/2, the first iterate x^n itself (metric L.G), n_iter iterations or
 // until an exact repeat. t1, t2: the new offsets from cell (i1, i2).
+template <bool Q = true>
 __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const Local<double> &L,
                                             int i1, int i2, double dx1, double dx2,
                                             const double u[3], double m2, double &t1,
@@ -239,11 +254,11 @@ __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const
     if (it == 0) {
       o = L.G;
     } else {
-      double r, s_, c_;
+      Pt<double> p;
       // x_bar = i + (dx + x~)/2, rounded in that order
-      local_rsc(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
-                __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), r, s_, c_);
-      geo_from_rsc(g, r, s_, c_, o);
+      local_rsc<Q>(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
+                   __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), p);
+      geo_from_rsc(g, p, o);
     }
     const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
                      fma(o.H33 * u[2], u[2], fma(o.H13, uu0, m2))));
@@ -260,6 +275,7 @@ __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const
 // the coordinate substep's refined iterations; t1, t2: the new offsets from cell (i1, i2)
 // v3 (dphi/dt) comes back from the metric of the last FP64 iteration, whose midpoint is within
 // iter_tol of the final one (or is NaN when the method's iteration ran instead).
+template <bool Q = true>
 __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &tb, const Base &b,
                                               const Local<double> &L, int i1, int i2,
                                               double dx1, double dx2, const double u[3],
@@ -269,10 +285,10 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
   const float uuf = 2.0f * uf[0] * uf[2];
   float p1 = a1, p2 = a2, d1 = 0.0f;
   for (int it = 0; it < g.n_iter; ++it) {
-    float r, s_, c_;
-    rsc32(g, tb, i1, i2, 0.5f * (a1 + p1), 0.5f * (a2 + p2), r, s_, c_);
+    Pt<float> pf;
+    rsc32<Q>(g, tb, i1, i2, 0.5f * (a1 + p1), 0.5f * (a2 + p2), pf);
     Geo<float> o;
-    geo_from_rsc(g, r, s_, c_, o);
+    geo_from_rsc(g, pf, o);
     const float q = fmaf(o.H11 * uf[0], uf[0], fmaf(o.H22 * uf[1], uf[1],
                     fmaf(o.H33 * uf[2], uf[2], fmaf(o.H13, uuf, (float)m2))));
     const float ag = rsqrtf(o.opz * q);
@@ -293,11 +309,11 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
   const double uu0 = 2.0 * u[0] * u[2];
   double D1 = 0.0, D2 = 0.0;
   for (int it = 0; it < g.n_iter; ++it) {
-    double r, s_, c_;
-    local_rsc(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
-              __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), r, s_, c_);
+    Pt<double> p;
+    local_rsc<Q>(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
+                 __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), p);
     Geo<double> o;
-    geo_from_rsc(g, r, s_, c_, o);
+    geo_from_rsc(g, p, o);
     const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
                      fma(o.H33 * u[2], u[2], fma(o.H13, uu0, m2))));
     const double ag = rsqrt(o.opz * q);
@@ -314,14 +330,14 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
   }
   const double scale = fmax(1.0, fmax(fabs(t1), fabs(t2)));
   if (!method_converges(d1, D1, D2, g.n_iter, g.iter_tol, scale)) {
-    coord_exact(g, b, L, i1, i2, dx1, dx2, u, m2, t1, t2);  // the method's n_iter iterations
+    coord_exact<Q>(g, b, L, i1, i2, dx1, dx2, u, m2, t1, t2);  // the method's iterations
     v3 = NAN;
   }
 }
 
 // One particle in FP64: steps 2-11 of Sec. 3.1, the boundaries of Sec. 3.3.3, and
 // (DEPOSIT) the deposit of its move. T is the storage type of state and fields.
-template <typename T, bool DEPOSIT>
+template <bool Q, typename T, bool DEPOSIT>
 __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
                                        const PushTables &tb, const SpeciesDevT<T> &s,
                                        int64_t k, unsigned long long *diag) {
@@ -329,11 +345,11 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   const double dx1 = (double)s.dx1[k], dx2 = (double)s.dx2[k];
   const double x1 = i1 + dx1, x2 = i2 + dx2;
   const bool em = s.m2 != 0.0;  // massless particles skip the EM push (Sec. 3.1)
-  const Base b = make_base(g, x1, x2);
-  double sn, cs, r0;
-  local_rsc(g, b, x1, x2, r0, sn, cs);  // clamps theta near the axes
+  const Base b = make_base<Q>(g, x1, x2);
+  Pt<double> p0;
+  local_rsc<Q>(g, b, x1, x2, p0);  // clamps theta near the axes
   Local<double> L;
-  local_full(g, b.r0, sn, cs, L);
+  local_full<Q>(g, p0, L);
   double Bh[3], Dh[3], uh[3], u[3] = {(double)s.u1[k], (double)s.u2[k], (double)s.u3[k]};
   const double hq = s.qm * L.alpha * 0.5 * g.dt;
   if (em) {
@@ -356,7 +372,7 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   // (metric terms ~ 1/sin^2(theta)) has more than one fixed point within reach, and the
   // method's answer is the one its iteration from x^n finds
   const bool refine = g.iter_tol > 0.0 && i2 >= 2 && i2 < g.n_th - 2;
-  if (refine) geodesic_refined(g, tb, i1, i2, (float)dx1, (float)dx2, L, u, s.m2);
+  if (refine) geodesic_refined<Q>(g, tb, i1, i2, (float)dx1, (float)dx2, L, u, s.m2);
   else geodesic_momentum(g, L, u, s.m2);  // step 6
   if (em) {
     cov_hat(L, u, uh);         // step 7
@@ -365,8 +381,8 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   }
   // step 10: implicit coordinate push, Eq. (discretized-geodesic-x)
   double t1 = dx1, t2 = dx2, v3r = NAN;
-  if (refine) coord_refined(g, tb, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2, v3r);
-  else coord_exact(g, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2);
+  if (refine) coord_refined<Q>(g, tb, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2, v3r);
+  else coord_exact<Q>(g, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2);
   if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(t1) && isfinite(t2) &&
         fabs(t1) < 1e6 && fabs(t2) < 1e6)) {
     s.tag[k] = 0;
@@ -391,7 +407,7 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   // step 11: phi at x^{n+1/2}, the midpoint of the stored x^n and the final x^{n+1}
   const double xb1 = j1 + e1, xb2 = j2 + e2;
   const double v3 = isnan(v3r)
-      ? phi_rate64(g, b, 0.5 * __dadd_rn(x1, xb1), 0.5 * __dadd_rn(x2, xb2), u, s.m2) : v3r;
+      ? phi_rate64<Q>(g, b, 0.5 * __dadd_rn(x1, xb1), 0.5 * __dadd_rn(x2, xb2), u, s.m2) : v3r;
   s.phi[k] = (T)((double)s.phi[k] + g.dt * v3);
   if (DEPOSIT) deposit64(g, F, s.qc * (double)s.w[k], i1, i2, x1, x2, j1, j2, xb1, xb2, v3);
 }
@@ -405,13 +421,30 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
 // =================================================================================
 // The guard-zone form of rsc32: r, sin and cos in FP64 from the FP64 corner tables, with
 // theta clamped to [small_angle, pi - small_angle] as in the FP64 routine.
+template <bool Q = true>
 __device__ __forceinline__ void rsc64(const GridP &g, const PushTables &tb, int i, int j,
-                                      float o1, float o2, double &r, double &s, double &c) {
+                                      float o1, float o2, Pt<double> &p) {
   const double e = (double)o1 * g.dxi;
-  r = fabs(e) <= 0.05 ? __ldg(tb.r64 + i + G_) * exp_small(e)  // truncation < 1e-15
-                      : g.r_min * exp(((double)i + (double)o1) * g.dxi);
-  const double th = ((double)j + (double)o2) * g.dth;
-  const double d = (double)o2 * g.dth;
+  const double ex = fabs(e) <= 0.05 ? __ldg(tb.r64 + i + G_) * exp_small(e)  // < 1e-15
+                                    : map_e(g, (double)i + (double)o1);
+  p.r = Q ? g.r0 + ex : ex;
+  p.f = g.dxi * ex;
+  double d = (double)o2 * g.dth;  // the offset in eta, then in theta
+  double th;
+  if (Q && g.qks) {
+    const double x2 = (double)j + (double)o2;
+    map_g<Q>(g, x2, p.gg, p.gp);
+    p.igg = 1.0 / (p.gg * p.gg);
+    th = map_theta<Q>(g, x2);
+    const double t1 = __ldg(tb.t1_64 + j + G_), t2 = __ldg(tb.t2_64 + j + G_);
+    d = d * fma(d, fma(g.c3, d, t2), t1);
+  } else {
+    p.gg = g.dth;
+    p.igg = g.ig2;
+    p.gp = 0.0;
+    th = ((double)j + (double)o2) * g.dth;
+  }
+  double &s = p.s, &c = p.c;
   if (th < g.small_angle || th > GRPIC_PI - g.small_angle) {
     sincos(fmin(fmax(th, g.small_angle), GRPIC_PI - g.small_angle), &s, &c);
   } else if (fabs(d) <= 0.1) {
@@ -454,19 +487,19 @@ __device__ __forceinline__ void narrow(const Local<double> &a, Local<float> &b) 
 
 // The contravariant metric, shift and 1 + z at a cell-relative point, evaluated in FP64
 // (G64: guard zones) or in FP32, as FP32 values.
-template <bool G64>
+template <bool Q, bool G64>
 __device__ __forceinline__ void geo_at(const GridP &g, const PushTables &tb, int i, int j,
                                        float o1, float o2, Geo<float> &o) {
   if constexpr (G64) {
-    double r, s_, c_;
-    rsc64(g, tb, i, j, o1, o2, r, s_, c_);
+    Pt<double> p;
+    rsc64<Q>(g, tb, i, j, o1, o2, p);
     Geo<double> od;
-    geo_from_rsc(g, r, s_, c_, od);
+    geo_from_rsc(g, p, od);
     narrow(od, o);
   } else {
-    float r, s_, c_;
-    rsc32(g, tb, i, j, o1, o2, r, s_, c_);
-    geo_from_rsc(g, r, s_, c_, o);
+    Pt<float> p;
+    rsc32<Q>(g, tb, i, j, o1, o2, p);
+    geo_from_rsc(g, p, o);
   }
 }
 
@@ -659,11 +692,11 @@ __device__ __forceinline__ void deposit32_warp(const GridP &g, const Sink &sink,
   }
 }
 
-template <bool G64>
+template <bool Q, bool G64>
 __device__ __forceinline__ float phi_rate32(const GridP &g, const PushTables &tb, int i, int j,
                                             float o1, float o2, const float u[3], float m2) {
   Geo<float> o;
-  geo_at<G64>(g, tb, i, j, o1, o2, o);
+  geo_at<Q, G64>(g, tb, i, j, o1, o2, o);
   const float q = fmaf(o.H11 * u[0], u[0], fmaf(o.H22 * u[1], u[1],
                   fmaf(o.H33 * u[2], u[2], fmaf(o.H13, 2.0f * u[0] * u[2], m2))));
   return rsqrtf(o.opz * q) * fmaf(o.H13, u[0], o.H33 * u[2]);
@@ -676,7 +709,7 @@ __device__ __forceinline__ float phi_rate32(const GridP &g, const PushTables &tb
 // enters dphi/dt divided by r sin(theta), which has no lower bound in those rows; one row
 // or more away sin(theta) >= dtheta and dt <= CFL r dtheta bound the phi error per step
 // by about eps CFL.
-template <bool G64, class Fields>
+template <bool Q, bool G64, class Fields>
 __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const PushTables &tb,
                                        const SpeciesDevT<float> &s, int64_t k,
                                        unsigned long long *diag, Move32 &mv) {
@@ -685,15 +718,15 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
   const bool em = s.f_m2 != 0.0f;  // massless particles skip the EM push (Sec. 3.1)
   Local<float> L;
   if constexpr (G64) {
-    double r0, sn, cs;
-    rsc64(g, tb, i1, i2, dx1, dx2, r0, sn, cs);
+    Pt<double> p;
+    rsc64<Q>(g, tb, i1, i2, dx1, dx2, p);
     Local<double> Ld;
-    local_full(g, r0, sn, cs, Ld);
+    local_full<Q>(g, p, Ld);
     narrow(Ld, L);
   } else {
-    float r0, sn, cs;
-    rsc32(g, tb, i1, i2, dx1, dx2, r0, sn, cs);
-    local_full(g, r0, sn, cs, L);
+    Pt<float> p;
+    rsc32<Q>(g, tb, i1, i2, dx1, dx2, p);
+    local_full<Q>(g, p, L);
   }
   float Bh[3], Dh[3], uh[3], u[3] = {s.u1[k], s.u2[k], s.u3[k]};
   const float hq = s.f_qm * L.alpha * 0.5f * g.f_dt;
@@ -723,7 +756,7 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
   for (int it = 0; it < g.n_iter; ++it) {
     Geo<float> o;
     if (it == 0) o = L.G;
-    else geo_at<G64>(g, tb, i1, i2, 0.5f * (dx1 + t1), 0.5f * (dx2 + t2), o);
+    else geo_at<Q, G64>(g, tb, i1, i2, 0.5f * (dx1 + t1), 0.5f * (dx2 + t2), o);
     const float q = fmaf(o.H11 * u[0], u[0], fmaf(o.H22 * u[1], u[1],
                     fmaf(o.H33 * u[2], u[2], fmaf(o.H13, uu0, s.f_m2))));
     const float ag = rsqrtf(o.opz * q);
@@ -759,7 +792,7 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
   else if (j1 >= g.n_r) { s.tag[k] = 2; count(diag, DG_LEFT_OUTER); }
   // phi at the midpoint, relative to the start cell
   const float b1 = (float)di + e1, b2 = (float)dj + e2;
-  const float v3 = phi_rate32<G64>(g, tb, i1, i2, 0.5f * (dx1 + b1), 0.5f * (dx2 + b2), u,
+  const float v3 = phi_rate32<Q, G64>(g, tb, i1, i2, 0.5f * (dx1 + b1), 0.5f * (dx2 + b2), u,
                                    s.f_m2);
   s.phi[k] = fmaf(dt, v3, s.phi[k]);
   mv = Move32{i1, i2, di, dj, dx1, dx2, b1, b2, s.f_qc * s.w[k], v3};
@@ -775,8 +808,8 @@ __device__ __forceinline__ int guard_zone(const PushTables &tb, const GridP &g, 
 }
 
 // FP64 path: one thread per particle, step 1 (previous location) then the FP64 routine.
-template <bool DEPOSIT>
-__global__ void __launch_bounds__(TPB) k_push(GridP g, FieldPtrsT<double> F, PushTables tb,
+template <bool DEPOSIT, bool Q>
+__global__ void __launch_bounds__(TPB, DEPOSIT ? 4 : 3) k_push(GridP g, FieldPtrsT<double> F, PushTables tb,
                                               SpeciesDevT<double> s, unsigned long long *diag) {
   const int64_t n = *s.n;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -788,7 +821,7 @@ __global__ void __launch_bounds__(TPB) k_push(GridP g, FieldPtrsT<double> F, Pus
       if (tag != 0) s.tag[k] = 0;
       continue;
     }
-    push64<double, DEPOSIT>(g, F, tb, s, k, diag);
+    push64<Q, double, DEPOSIT>(g, F, tb, s, k, diag);
   }
 }
 
@@ -824,8 +857,8 @@ __global__ void __launch_bounds__(TPB) k_classify(GridP g, SpeciesDevT<float> s,
 // Mixed path, FP32 kernel: step 1 and the FP32 routine for every unlisted particle (it runs
 // concurrently with the guard kernels, which own the listed ones). The loop runs while the
 // warp's first particle exists, so the whole warp reaches the cooperative deposit.
-template <bool DEPOSIT>
-__global__ void __launch_bounds__(TPB) k_push32(GridP g, FieldPtrsT<float> F,
+template <bool DEPOSIT, bool Q>
+__global__ void __launch_bounds__(TPB, 6) k_push32(GridP g, FieldPtrsT<float> F,
                                                 SpeciesDevT<float> s, PushTables tb,
                                                 GuardList gl, unsigned long long *diag) {
   const int64_t n = *s.n;
@@ -838,7 +871,7 @@ __global__ void __launch_bounds__(TPB) k_push32(GridP g, FieldPtrsT<float> F,
       const int i1 = s.i1[k], i2 = s.i2[k];
       s.i1p[k] = i1; s.i2p[k] = i2; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
       const uint8_t tag = s.tag[k];
-      if (tag == 1) on = push32<false>(g, GlobalFields(g, F), tb, s, k, diag, mv);
+      if (tag == 1) on = push32<Q, false>(g, GlobalFields(g, F), tb, s, k, diag, mv);
       else if (tag != 0) s.tag[k] = 0;
     }
     if (DEPOSIT) deposit32_warp(g, GlobalSink(g, F), mv, on);
@@ -852,7 +885,7 @@ __global__ void __launch_bounds__(TPB) k_push32(GridP g, FieldPtrsT<float> F,
 // whose cell has drifted out of the window gathers from, and deposits to, global memory.
 constexpr int TILE_HALO = 6;
 constexpr int TILE_TPB = 256;
-template <bool DEPOSIT>
+template <bool DEPOSIT, bool Q>
 __global__ void __launch_bounds__(TILE_TPB) k_push32_tiled(GridP g, FieldPtrsT<float> F,
                                                           SpeciesDevT<float> s, PushTables tb,
                                                           GuardList gl, TileInfo ti,
@@ -890,8 +923,8 @@ __global__ void __launch_bounds__(TILE_TPB) k_push32_tiled(GridP g, FieldPtrsT<f
       if (tag == 1) {
         // the interpolation reads cells i +- 1, j +- 1
         const bool inside = i1 - 1 >= iw0 && i1 + 1 < iw0 + W1 && i2 - 1 >= jw0 && i2 + 1 < jw0 + W2;
-        on = inside ? push32<false>(g, wf, tb, s, k, diag, mv)
-                    : push32<false>(g, gf, tb, s, k, diag, mv);
+        on = inside ? push32<Q, false>(g, wf, tb, s, k, diag, mv)
+                    : push32<Q, false>(g, gf, tb, s, k, diag, mv);
       } else if (tag != 0) {
         s.tag[k] = 0;
       }
@@ -916,7 +949,7 @@ size_t tiled_smem_bytes(const TileInfo &ti) {
 
 // Mixed path, guard kernels (side stream): step 1 and the routine of the listed particles,
 // zone 1 with the metric in FP64, zone 2 with the FP64 routine.
-template <bool DEPOSIT>
+template <bool DEPOSIT, bool Q>
 __global__ void __launch_bounds__(TPB) k_push_guard(GridP g, FieldPtrsT<float> F,
                                                     SpeciesDevT<float> s, PushTables tb,
                                                     GuardList gl, unsigned long long *diag) {
@@ -929,13 +962,13 @@ __global__ void __launch_bounds__(TPB) k_push_guard(GridP g, FieldPtrsT<float> F
     if (t < n) {
       const int64_t k = gl.idx[t];
       s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
-      on = push32<true>(g, GlobalFields(g, F), tb, s, k, diag, mv);
+      on = push32<Q, true>(g, GlobalFields(g, F), tb, s, k, diag, mv);
     }
     if (DEPOSIT) deposit32_warp(g, GlobalSink(g, F), mv, on);
   }
 }
 
-template <bool DEPOSIT>
+template <bool DEPOSIT, bool Q>
 __global__ void __launch_bounds__(TPB) k_push_axis(GridP g, FieldPtrsT<float> F,
                                                    SpeciesDevT<float> s, PushTables tb,
                                                    GuardList gl, unsigned long long *diag) {
@@ -944,7 +977,7 @@ __global__ void __launch_bounds__(TPB) k_push_axis(GridP g, FieldPtrsT<float> F,
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = gl.idx[gl.cap - 1 - t];
     s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
-    push64<float, DEPOSIT>(g, F, tb, s, k, diag);
+    push64<Q, float, DEPOSIT>(g, F, tb, s, k, diag);
   }
 }
 
@@ -970,8 +1003,8 @@ __global__ void __launch_bounds__(TPB) k_deposit(GridP g, FieldPtrsT<T> F, Speci
         const float b1 = (float)(ib - ia) + s.dx1[k], b2 = (float)(jb - ja) + s.dx2[k];
         const float u[3] = {s.u1[k], s.u2[k], s.u3[k]};
         const float m1 = 0.5f * (a1 + b1), m2 = 0.5f * (a2 + b2);
-        const float v3 = zone ? phi_rate32<true>(g, tb, ia, ja, m1, m2, u, s.f_m2)
-                              : phi_rate32<false>(g, tb, ia, ja, m1, m2, u, s.f_m2);
+        const float v3 = zone ? phi_rate32<true, true>(g, tb, ia, ja, m1, m2, u, s.f_m2)
+                              : phi_rate32<true, false>(g, tb, ia, ja, m1, m2, u, s.f_m2);
         mv = Move32{ia, ja, ib - ia, jb - ja, a1, a2, b1, b2, s.f_qc * s.w[k], v3};
       }
       deposit32_warp(g, GlobalSink(g, F), mv, on);
@@ -1007,7 +1040,7 @@ __global__ void k_load(GridP g, SpeciesDevT<T> s, int64_t k0, int64_t n, const d
     s.u1[k] = (T)u[0]; s.u2[k] = (T)u[1]; s.u3[k] = (T)u[2];
     MetricV m0;
     metric_eval<false>(g, x1, x2, false, m0, nullptr);
-    const double r = g.r_min * exp(x1 * g.dxi);
+    const double r = g.r0 + map_e(g, x1);
     s.w[k] = (T)(w0[t] * pow(r, -dpow) * m0.sqrt_h);
     s.phi[k] = (T)0;
     s.tag[k] = 1;
@@ -1042,18 +1075,27 @@ __global__ void k_invariants(GridP g, SpeciesDevT<T> s, int kind, double B0, dou
 __global__ void k_push_tables(GridP g, PushTables tb) {
   const int n = max(g.NX, g.NY);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    if (t < g.NX) {
-      const double r = g.r_min * exp((t - G_) * g.dxi);
-      const_cast<double *>(tb.r64)[t] = r;
-      const_cast<float *>(tb.r)[t] = (float)r;
+    if (t < g.NX) {  // exp(xi) = r - r0 at the corner column
+      const double e = map_e(g, t - G_);
+      const_cast<double *>(tb.r64)[t] = e;
+      const_cast<float *>(tb.r)[t] = (float)e;
     }
     if (t < g.NY) {
       double s, c;
-      sincos((t - G_) * g.dth, &s, &c);
+      sincos(map_theta(g, t - G_), &s, &c);
       const_cast<double *>(tb.s64)[t] = s;
       const_cast<double *>(tb.c64)[t] = c;
       const_cast<float *>(tb.s)[t] = (float)s;
       const_cast<float *>(tb.c)[t] = (float)c;
+      // theta(eta_j + d) - theta(eta_j) = d (t1 + d (t2 + d c3)): t1 = dtheta/deta at eta_j,
+      // t2 = k (6 eta_j - 3 pi), k = 2 h0 / pi^2 (1 and 0 on the plain grid)
+      const double eta = (t - G_) * g.dth, k = 2.0 * g.h0 / (GRPIC_PI * GRPIC_PI);
+      const double t1 = 1.0 + k * (GRPIC_PI * GRPIC_PI - 6.0 * GRPIC_PI * eta + 6.0 * eta * eta);
+      const double t2 = k * (6.0 * eta - 3.0 * GRPIC_PI);
+      const_cast<double *>(tb.t1_64)[t] = t1;
+      const_cast<double *>(tb.t2_64)[t] = t2;
+      const_cast<float *>(tb.t1)[t] = (float)t1;
+      const_cast<float *>(tb.t2)[t] = (float)t2;
     }
   }
 }
@@ -1083,11 +1125,12 @@ cudaError_t launch_load(const GridP &g, SpeciesDevT<T> s, int64_t k0, int64_t n,
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
-                        const PushTables &tb, const GuardList &gl, const TileInfo &ti,
-                        int64_t n_bound, bool deposit, unsigned long long *diag,
-                        const PushStreams &ps) {
+// the push kernels for a grid kind known at compile time (Q: quasi-spherical)
+template <typename T, bool Q>
+cudaError_t push_impl(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
+                      const PushTables &tb, const GuardList &gl, const TileInfo &ti,
+                      int64_t n_bound, bool deposit, unsigned long long *diag,
+                      const PushStreams &ps) {
   if (n_bound <= 0) {  // keep a requested event pair recorded (zero duration)
     if (ps.t0) cudaEventRecord(ps.t0, ps.main);
     if (ps.t1) cudaEventRecord(ps.t1, ps.main);
@@ -1095,8 +1138,8 @@ cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s
   }
   if constexpr (sizeof(T) == 8) {
     if (ps.t0) cudaEventRecord(ps.t0, ps.main);
-    if (deposit) k_push<true><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, tb, s, diag);
-    else k_push<false><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, tb, s, diag);
+    if (deposit) k_push<true, Q><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, tb, s, diag);
+    else k_push<false, Q><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, tb, s, diag);
     if (ps.t1) cudaEventRecord(ps.t1, ps.main);
     COUNT_LAUNCH(1);
   } else {
@@ -1109,36 +1152,45 @@ cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s
     // the guard kernels are FP64-pipe bound: a few one-warp blocks per SM reach every SM
     // sub-partition's FP64 unit and leave the registers to the concurrent FP32 kernel
     if (deposit) {
-      k_push_guard<true><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
-      k_push_axis<true><<<152 * 4, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+      k_push_guard<true, Q><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+      k_push_axis<true, Q><<<152 * 4, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
     } else {
-      k_push_guard<false><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
-      k_push_axis<false><<<152 * 4, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+      k_push_guard<false, Q><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+      k_push_axis<false, Q><<<152 * 4, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
     }
     // the tiled kernel needs the tile ranges of a sort and a window that fits in shared memory
     const size_t smem = tiled_smem_bytes(ti);
     const bool tiled = ti.start != nullptr && smem <= 200 * 1024;
     if (tiled && smem > 48 * 1024) {
-      if ((e = cudaFuncSetAttribute(k_push32_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if ((e = cudaFuncSetAttribute(k_push32_tiled<true, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem)) != cudaSuccess) return e;
-      if ((e = cudaFuncSetAttribute(k_push32_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if ((e = cudaFuncSetAttribute(k_push32_tiled<false, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem)) != cudaSuccess) return e;
     }
     if (ps.t0) cudaEventRecord(ps.t0, ps.main);
     if (tiled) {
       if (deposit)
-        k_push32_tiled<true><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
+        k_push32_tiled<true, Q><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
       else
-        k_push32_tiled<false><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
+        k_push32_tiled<false, Q><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
     } else {
-      if (deposit) k_push32<true><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
-      else k_push32<false><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
+      if (deposit) k_push32<true, Q><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
+      else k_push32<false, Q><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
     }
     if (ps.t1) cudaEventRecord(ps.t1, ps.main);
     if ((e = cudaEventRecord(ps.done, ps.side)) != cudaSuccess) return e;
     COUNT_LAUNCH(4);
   }
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_push(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
+                        const PushTables &tb, const GuardList &gl, const TileInfo &ti,
+                        int64_t n_bound, bool deposit, unsigned long long *diag,
+                        const PushStreams &ps) {
+  return g.qks ? push_impl<T, true>(g, F, s, tb, gl, ti, n_bound, deposit, diag, ps)
+               : push_impl<T, false>(g, F, s, tb, gl, ti, n_bound, deposit, diag, ps);
 }
 
 template <typename T>

@@ -14,24 +14,32 @@ __device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
 __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
 
 // =================================================================================
-// Metric pieces shared by both precisions (App. A, quasi-spherical Kerr-Schild with
-// r0 = h0 = 0, mass M explicit). All reciprocals of one evaluation come from one division.
+// Metric pieces shared by both precisions (App. A, quasi-spherical Kerr-Schild, mass M
+// explicit). All reciprocals of one evaluation come from one division.
 // =================================================================================
 
-// The contravariant metric, shift and 1 + z = 1/alpha^2 from r, sin, cos.
+// A point of the grid: r, sin(theta), cos(theta) and the map's factors f = dr/dx1 =
+// dxi (r - r0), gg = dtheta/dx2, igg = 1/gg^2 and gp = dgg/dx2 (gg = dtheta, gp = 0 on the
+// plain grid).
+template <typename R>
+struct Pt {
+  R r, s, c, f, gg, igg, gp;
+};
+
+// The contravariant metric, shift and 1 + z = 1/alpha^2 at a point.
 template <typename R>
 struct Geo {
   R H11, H13, H22, H33, beta1, opz;
 };
 template <typename R>
-__device__ __forceinline__ void geo_from_rsc(const GridP &g, R r, R s, R c, Geo<R> &o) {
+__device__ __forceinline__ void geo_from_rsc(const GridP &g, const Pt<R> &p, Geo<R> &o) {
   const Cst<R> k = cst<R>(g);
   const R a = k.a, M = k.M, a2 = a * a;
-  const R r2 = r * r, s2 = s * s;
-  const R Sig = fma_(a2, c * c, r2);
+  const R r = p.r, s2 = p.s * p.s, r2 = r * r;
+  const R Sig = fma_(a2, p.c * p.c, r2);
   const R S2 = fma_((R)2 * M, r, Sig);  // Sigma + 2 M r
   const R A = (r2 + a2) * (r2 + a2) - a2 * (r2 - (R)2 * M * r + a2) * s2;
-  const R f = k.dxi * r;
+  const R f = p.f;
   const R u = Sig * S2 * f;
   const R iQ = (R)1 / (u * s2);         // the one division
   const R iu = iQ * s2;                 // 1 / (Sigma S2 f)
@@ -39,7 +47,7 @@ __device__ __forceinline__ void geo_from_rsc(const GridP &g, R r, R s, R c, Geo<
   o.opz = S2 * iSig;
   o.H11 = A * iSig * iS2 * fi * fi;
   o.H13 = a * iSig * fi;
-  o.H22 = iSig * k.ig2;
+  o.H22 = iSig * p.igg;
   o.H33 = iQ * u * iSig;                // 1 / (Sigma s^2)
   o.beta1 = (R)2 * M * r * iS2 * fi;
 }
@@ -54,16 +62,16 @@ struct Local {
   R d2H11, d2H22, d2H33, d2H13, d2alpha, d2beta1;
   R rH11, sH11, rh22, sh22, rh33, sh33, k13, m13;
 };
-template <typename R>
-__device__ __forceinline__ void local_full(const GridP &g, R r, R s, R c, Local<R> &L) {
+template <bool Q = true, typename R>
+__device__ __forceinline__ void local_full(const GridP &g, const Pt<R> &p, Local<R> &L) {
   const Cst<R> k = cst<R>(g);
-  const R a = k.a, M = k.M, a2 = a * a, gg = k.dth, dxi = k.dxi;
-  const R r2 = r * r, s2 = s * s;
+  const R a = k.a, M = k.M, a2 = a * a, gg = p.gg, dxi = k.dxi;
+  const R r = p.r, s = p.s, c = p.c, r2 = r * r, s2 = s * s;
   const R Sig = fma_(a2, c * c, r2);
   const R S2 = fma_((R)2 * M, r, Sig);
   const R Del = r2 - (R)2 * M * r + a2;
   const R A = (r2 + a2) * (r2 + a2) - a2 * Del * s2;
-  const R f = dxi * r;
+  const R f = p.f;
   const R u = Sig * S2 * f;
   const R iQ = (R)1 / (u * s2);
   const R iu = iQ * s2;
@@ -73,7 +81,7 @@ __device__ __forceinline__ void local_full(const GridP &g, R r, R s, R c, Local<
   o.opz = S2 * iSig;
   o.H11 = A * iSig * iS2 * fi * fi;
   o.H13 = a * iSig * fi;
-  o.H22 = iSig * k.ig2;
+  o.H22 = iSig * p.igg;
   o.H33 = iSig * is2;
   o.beta1 = (R)2 * M * r * iS2 * fi;
   const R al2 = Sig * iS2;
@@ -88,8 +96,9 @@ __device__ __forceinline__ void local_full(const GridP &g, R r, R s, R c, Local<
   L.d1H11 = (P * dxA - (R)2 * A * (M * r * dxS + Sig * (dxS + M * f))) * iP2 * fi2 -
             (R)2 * dxi * o.H11;
   L.d2H11 = (P * deA - (R)2 * A * deS * (M * r + Sig)) * iP2 * fi2;
-  L.d1H22 = -dxS * iSg2 * k.ig2;
-  L.d2H22 = -deS * iSg2 * k.ig2;
+  L.d1H22 = -dxS * iSg2 * p.igg;
+  L.d2H22 = -deS * iSg2 * p.igg;
+  if (Q && g.qks) L.d2H22 = L.d2H22 - (R)2 * o.H22 * p.gp * gg * p.igg;  // h^22 = h^tt/gg^2
   L.d1H33 = -dxS * iSg2 * is2;
   L.d2H33 = -(deS + (R)2 * c * s * is2 * Sig * gg) * iSg2 * is2;
   L.d1H13 = -a * fi * iSig * (iSig * dxS + dxi);
@@ -217,12 +226,12 @@ __device__ __forceinline__ void geodesic_momentum(const GridP &g, const Local<R>
   u[1] = t1;
 }
 
-// FP32 r, sin(theta), cos(theta) from FP64-computed per-cell tables and short Taylor series of
-// the offset from the cell corner (mixed path; and the FP32 predictor of the FP64 path's
-// refined implicit iterations).
-// r at x1 = i + o1 and sin/cos of theta at x2 = j + o2 (offsets from the corner of cell i, j)
+// FP32 r, sin(theta), cos(theta) and the map's factors from FP64-computed per-cell tables and
+// short Taylor series of the offset from the cell corner (mixed path; and the FP32 predictor
+// of the FP64 path's refined implicit iterations), at x1 = i + o1, x2 = j + o2.
+template <bool Q = true>
 __device__ __forceinline__ void rsc32(const GridP &g, const PushTables &tb, int i, int j,
-                                      float o1, float o2, float &r, float &s, float &c) {
+                                      float o1, float o2, Pt<float> &pt) {
   const float e = o1 * g.f_dxi;  // |e| <= 2 dxi
   float p = 1.0f / 720.0f;
   p = fmaf(p, e, 1.0f / 120.0f);
@@ -230,15 +239,28 @@ __device__ __forceinline__ void rsc32(const GridP &g, const PushTables &tb, int 
   p = fmaf(p, e, 1.0f / 6.0f);
   p = fmaf(p, e, 0.5f);
   p = fmaf(p, e, 1.0f);
-  r = __ldg(tb.r + i + G_) * fmaf(p, e, 1.0f);
-  const float d = o2 * g.f_dth;  // |d| <= 2 dtheta
+  const float ex = __ldg(tb.r + i + G_) * fmaf(p, e, 1.0f);  // r - r0
+  pt.r = Q ? g.f_r0 + ex : ex;
+  pt.f = g.f_dxi * ex;
+  float d = o2 * g.f_dth;  // |d| <= 2 dtheta: the offset in eta, then in theta
+  if (Q && g.qks) {
+    const float t1 = __ldg(tb.t1 + j + G_), t2 = __ldg(tb.t2 + j + G_), c3 = g.f_c3;
+    pt.gg = g.f_dth * fmaf(d, fmaf(3.0f * c3, d, 2.0f * t2), t1);
+    pt.igg = 1.0f / (pt.gg * pt.gg);
+    pt.gp = g.f_dth * g.f_dth * fmaf(6.0f * c3, d, 2.0f * t2);
+    d = d * fmaf(d, fmaf(c3, d, t2), t1);
+  } else {
+    pt.gg = g.f_dth;
+    pt.igg = g.f_ig2;
+    pt.gp = 0.0f;
+  }
   const float q = d * d;
   const float se = fmaf(fmaf(fmaf(-1.0f / 5040.0f, q, 1.0f / 120.0f), q, -1.0f / 6.0f) * q, d, d);
   const float ce = fmaf(fmaf(fmaf(fmaf(1.0f / 40320.0f, q, -1.0f / 720.0f), q, 1.0f / 24.0f), q,
                              -0.5f), q, 1.0f);
   const float s0 = __ldg(tb.s + j + G_), c0 = __ldg(tb.c + j + G_);
-  s = fmaf(s0, ce, c0 * se);
-  c = fmaf(c0, ce, -s0 * se);
+  pt.s = fmaf(s0, ce, c0 * se);
+  pt.c = fmaf(c0, ce, -s0 * se);
 }
 
 }  // namespace

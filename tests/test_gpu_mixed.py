@@ -1,7 +1,7 @@
 """Mixed precision (FP32 fields, momenta, offsets and currents; FP64 near the horizon and
 the axes) against the FP64 oracle, through the C ABI.
 
-The bound is the spec one: at most 1e-5 relative error per step on the particle
+The bound: at most 1e-5 relative error per step on the particle
 state. Both sides start from the same oracle-built state, rounded to FP32 so that it is
 exactly representable on both (next to theta = pi the dynamics amplify a rounding of the
 input offset by ~1e2, which would otherwise dominate). Field planes are held to 1e-5
