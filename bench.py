@@ -482,10 +482,11 @@ def run_extensions(args, ws, rank, local):
     torch.cuda.set_device(local)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
-    out = {"metric": "extensions: massless particles, the current filter, pair injection",
+    out = {"metric": "extensions: massless particles, the current filter, pair injection, "
+                     "quasi-spherical grids",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup}
     parts = set(args.only.split(",")) if args.only else {"photons", "filter512", "filter2048",
-                                                          "inject"}
+                                                          "inject", "qks"}
     ph = {}
     for prec in (("fp64", "mixed") if "photons" in parts else ()):
         pairs, sim = measure(args, prec, ws, rank, local)
@@ -523,6 +524,21 @@ def run_extensions(args, ws, rank, local):
         out["filter_wald2048"] = measure_filter_2048(args, ws, rank, local, peaks)
     if "inject" in parts:
         out["inject_bz2048"] = measure_injection(args, local, peaks)
+    if "qks" in parts:
+        # the bench workload on a quasi-spherical grid (App. A): r0 = 0.4, h0 = 0.45
+        q = {}
+        for prec in ("fp64", "mixed"):
+            base, sim = measure(args, prec, ws, rank, local)
+            del sim
+            qk, sim = measure(args, prec, ws, rank, local, extra={"r0": 0.4, "h0": 0.45})
+            del sim
+            torch.cuda.empty_cache()
+            q[prec] = {"particle_steps_per_s": qk["value"], "plain_grid": base["value"],
+                       "ratio": qk["value"] / base["value"],
+                       "push_kernel_ms": qk["roofline"]["avg_launch_ms"],
+                       "push_kernel_ms_plain": base["roofline"]["avg_launch_ms"],
+                       "clocks": qk["clocks"]}
+        out["qks_wald512"] = q
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -750,7 +766,8 @@ def main():
                     help="time the rows beyond the base path instead: massless particles and "
                          "the current filter")
     ap.add_argument("--only", default="",
-                    help="--extensions: a comma list of photons, filter512, filter2048, inject")
+                    help="--extensions: a comma list of photons, filter512, filter2048, inject, "
+                         "qks")
     ap.add_argument("--ext-ppc", type=int, default=0,
                     help="--extensions: particles per cell per species of the 2048^2 filter "
                          "and injection cases (default 1 and 4)")

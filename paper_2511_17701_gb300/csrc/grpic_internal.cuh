@@ -65,9 +65,10 @@ __device__ __forceinline__ void map_g(const GridP &g, double x2, double &gg, dou
     gp = 0.0;
     return;
   }
-  const double eta = x2 * g.dth, u = eta / GRPIC_PI;
+  constexpr double inv_pi = 1.0 / GRPIC_PI;  // multiplications only: no FP64 division
+  const double eta = x2 * g.dth, u = eta * inv_pi;
   gg = g.dth * (1.0 + 2.0 * g.h0 + 12.0 * g.h0 * u * (u - 1.0));
-  gp = g.dth * g.dth * 12.0 * g.h0 * (2.0 * u - 1.0) / GRPIC_PI;
+  gp = g.dth * g.dth * 12.0 * g.h0 * (2.0 * u - 1.0) * inv_pi;
 }
 
 // The grid constants in the arithmetic type R.

@@ -63,7 +63,6 @@ __device__ __forceinline__ void local_rsc(const GridP &g, const Base &b, double 
   p.f = g.dxi * ex;
   if (Q && g.qks) {
     map_g<Q>(g, x2t, p.gg, p.gp);
-    p.igg = 1.0 / (p.gg * p.gg);
   } else {
     p.gg = g.dth;
     p.igg = g.ig2;
@@ -99,7 +98,7 @@ __device__ __forceinline__ double phi_rate64(const GridP &g, const Base &b, doub
   Pt<double> p;
   local_rsc<Q>(g, b, x1t, x2t, p);
   Geo<double> o;
-  geo_from_rsc(g, p, o);
+  geo_from_rsc<Q>(g, p, o);
   const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1], fma(o.H33 * u[2], u[2],
                    fma(2.0 * o.H13 * u[0], u[2], m2))));
   return rsqrt(o.opz * q) * fma(o.H13, u[0], o.H33 * u[2]);
@@ -258,7 +257,7 @@ __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const
       // x_bar = i + (dx + x~)/2, rounded in that order
       local_rsc<Q>(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
                    __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), p);
-      geo_from_rsc(g, p, o);
+      geo_from_rsc<Q>(g, p, o);
     }
     const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
                      fma(o.H33 * u[2], u[2], fma(o.H13, uu0, m2))));
@@ -288,7 +287,7 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
     Pt<float> pf;
     rsc32<Q>(g, tb, i1, i2, 0.5f * (a1 + p1), 0.5f * (a2 + p2), pf);
     Geo<float> o;
-    geo_from_rsc(g, pf, o);
+    geo_from_rsc<Q>(g, pf, o);
     const float q = fmaf(o.H11 * uf[0], uf[0], fmaf(o.H22 * uf[1], uf[1],
                     fmaf(o.H33 * uf[2], uf[2], fmaf(o.H13, uuf, (float)m2))));
     const float ag = rsqrtf(o.opz * q);
@@ -313,7 +312,7 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
     local_rsc<Q>(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
                  __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), p);
     Geo<double> o;
-    geo_from_rsc(g, p, o);
+    geo_from_rsc<Q>(g, p, o);
     const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
                      fma(o.H33 * u[2], u[2], fma(o.H13, uu0, m2))));
     const double ag = rsqrt(o.opz * q);
@@ -434,7 +433,6 @@ __device__ __forceinline__ void rsc64(const GridP &g, const PushTables &tb, int 
   if (Q && g.qks) {
     const double x2 = (double)j + (double)o2;
     map_g<Q>(g, x2, p.gg, p.gp);
-    p.igg = 1.0 / (p.gg * p.gg);
     th = map_theta<Q>(g, x2);
     const double t1 = __ldg(tb.t1_64 + j + G_), t2 = __ldg(tb.t2_64 + j + G_);
     d = d * fma(d, fma(g.c3, d, t2), t1);
@@ -494,12 +492,12 @@ __device__ __forceinline__ void geo_at(const GridP &g, const PushTables &tb, int
     Pt<double> p;
     rsc64<Q>(g, tb, i, j, o1, o2, p);
     Geo<double> od;
-    geo_from_rsc(g, p, od);
+    geo_from_rsc<Q>(g, p, od);
     narrow(od, o);
   } else {
     Pt<float> p;
     rsc32<Q>(g, tb, i, j, o1, o2, p);
-    geo_from_rsc(g, p, o);
+    geo_from_rsc<Q>(g, p, o);
   }
 }
 

@@ -19,8 +19,8 @@ __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
 // =================================================================================
 
 // A point of the grid: r, sin(theta), cos(theta) and the map's factors f = dr/dx1 =
-// dxi (r - r0), gg = dtheta/dx2, igg = 1/gg^2 and gp = dgg/dx2 (gg = dtheta, gp = 0 on the
-// plain grid).
+// dxi (r - r0), gg = dtheta/dx2, gp = dgg/dx2, and igg = 1/gg^2 on the plain grid (gg =
+// dtheta, gp = 0 there; on a quasi-spherical grid 1/gg^2 shares the metric's one division).
 template <typename R>
 struct Pt {
   R r, s, c, f, gg, igg, gp;
@@ -31,7 +31,7 @@ template <typename R>
 struct Geo {
   R H11, H13, H22, H33, beta1, opz;
 };
-template <typename R>
+template <bool Q = true, typename R>
 __device__ __forceinline__ void geo_from_rsc(const GridP &g, const Pt<R> &p, Geo<R> &o) {
   const Cst<R> k = cst<R>(g);
   const R a = k.a, M = k.M, a2 = a * a;
@@ -41,13 +41,22 @@ __device__ __forceinline__ void geo_from_rsc(const GridP &g, const Pt<R> &p, Geo
   const R A = (r2 + a2) * (r2 + a2) - a2 * (r2 - (R)2 * M * r + a2) * s2;
   const R f = p.f;
   const R u = Sig * S2 * f;
-  const R iQ = (R)1 / (u * s2);         // the one division
+  R iQ, igg;
+  if (Q && g.qks) {
+    const R g2 = p.gg * p.gg;
+    const R iX = (R)1 / (u * s2 * g2);  // the one division
+    iQ = iX * g2;
+    igg = iX * u * s2;
+  } else {
+    iQ = (R)1 / (u * s2);               // the one division
+    igg = p.igg;
+  }
   const R iu = iQ * s2;                 // 1 / (Sigma S2 f)
   const R iSig = iu * S2 * f, iS2 = iu * Sig * f, fi = iu * Sig * S2;
   o.opz = S2 * iSig;
   o.H11 = A * iSig * iS2 * fi * fi;
   o.H13 = a * iSig * fi;
-  o.H22 = iSig * p.igg;
+  o.H22 = iSig * igg;
   o.H33 = iQ * u * iSig;                // 1 / (Sigma s^2)
   o.beta1 = (R)2 * M * r * iS2 * fi;
 }
@@ -73,7 +82,16 @@ __device__ __forceinline__ void local_full(const GridP &g, const Pt<R> &p, Local
   const R A = (r2 + a2) * (r2 + a2) - a2 * Del * s2;
   const R f = p.f;
   const R u = Sig * S2 * f;
-  const R iQ = (R)1 / (u * s2);
+  R iQ, igg;
+  if (Q && g.qks) {
+    const R g2 = gg * gg;
+    const R iX = (R)1 / (u * s2 * g2);
+    iQ = iX * g2;
+    igg = iX * u * s2;
+  } else {
+    iQ = (R)1 / (u * s2);
+    igg = p.igg;
+  }
   const R iu = iQ * s2;
   const R iSig = iu * S2 * f, iS2 = iu * Sig * f, fi = iu * Sig * S2;
   const R is2 = iQ * u;
@@ -81,7 +99,7 @@ __device__ __forceinline__ void local_full(const GridP &g, const Pt<R> &p, Local
   o.opz = S2 * iSig;
   o.H11 = A * iSig * iS2 * fi * fi;
   o.H13 = a * iSig * fi;
-  o.H22 = iSig * p.igg;
+  o.H22 = iSig * igg;
   o.H33 = iSig * is2;
   o.beta1 = (R)2 * M * r * iS2 * fi;
   const R al2 = Sig * iS2;
@@ -96,9 +114,9 @@ __device__ __forceinline__ void local_full(const GridP &g, const Pt<R> &p, Local
   L.d1H11 = (P * dxA - (R)2 * A * (M * r * dxS + Sig * (dxS + M * f))) * iP2 * fi2 -
             (R)2 * dxi * o.H11;
   L.d2H11 = (P * deA - (R)2 * A * deS * (M * r + Sig)) * iP2 * fi2;
-  L.d1H22 = -dxS * iSg2 * p.igg;
-  L.d2H22 = -deS * iSg2 * p.igg;
-  if (Q && g.qks) L.d2H22 = L.d2H22 - (R)2 * o.H22 * p.gp * gg * p.igg;  // h^22 = h^tt/gg^2
+  L.d1H22 = -dxS * iSg2 * igg;
+  L.d2H22 = -deS * iSg2 * igg;
+  if (Q && g.qks) L.d2H22 = L.d2H22 - (R)2 * o.H22 * p.gp * gg * igg;  // h^22 = h^tt/gg^2
   L.d1H33 = -dxS * iSg2 * is2;
   L.d2H33 = -(deS + (R)2 * c * s * is2 * Sig * gg) * iSg2 * is2;
   L.d1H13 = -a * fi * iSig * (iSig * dxS + dxi);
@@ -246,7 +264,6 @@ __device__ __forceinline__ void rsc32(const GridP &g, const PushTables &tb, int 
   if (Q && g.qks) {
     const float t1 = __ldg(tb.t1 + j + G_), t2 = __ldg(tb.t2 + j + G_), c3 = g.f_c3;
     pt.gg = g.f_dth * fmaf(d, fmaf(3.0f * c3, d, 2.0f * t2), t1);
-    pt.igg = 1.0f / (pt.gg * pt.gg);
     pt.gp = g.f_dth * g.f_dth * fmaf(6.0f * c3, d, 2.0f * t2);
     d = d * fmaf(d, fmaf(c3, d, t2), t1);
   } else {
