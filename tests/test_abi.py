@@ -85,6 +85,17 @@ def test_create_requires_room_for_the_filter_inside_the_horizon():
     assert create(dict(good_cfg(), n_filter=4, metric="ks0", r_min=1.0))[0] == B.OK
 
 
+def test_every_workload_and_the_smoke_case_are_accepted():
+    import workloads as W
+    import __graft_entry__ as ge
+    cases = [W.grid_config(name) for name in W.CONFIGS] + [ge.smoke_config()]
+    for cfg in cases:
+        for prec in ("fp64", "mixed"):
+            st, ctx = create(dict(cfg, precision=prec), caps=(10, 10))
+            assert st == B.OK, (cfg, prec)
+            B.lib().grpic_destroy(ctx)
+
+
 def test_create_rejects_bad_species():
     assert create(good_cfg(), caps=())[0] == B.EINVAL
     assert create(good_cfg(), caps=(1,) * 9)[0] == B.EINVAL
