@@ -368,32 +368,42 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
     return out, sim
 
 
+# the particle state a step reads: position, momenta, phi, weight, tag (the previous
+# position is written by the step's push, Sec. 3.2, so it is not an input)
+STATE_ARRAYS = ("i1", "i2", "dx1", "dx2", "u1", "u2", "u3", "phi", "w", "tag")
+
+
 def end_to_end(args, sim, psteps, ws, device):
-    """Through the C ABI with host buffers: per step the particle state goes from pinned
-    host memory to the device, one full step runs, and the state comes back."""
+    """Through the C ABI with host buffers: per step the particle state (the arrays the step
+    reads) goes from pinned host memory to the device, one full step runs, and the state
+    comes back."""
     import torch
     host = []
+    types = [(k, t) for k, t in sim.ptypes if k in STATE_ARRAYS]
     for s in range(2):
         st = sim.get_particles(s)
         hs = {}
-        for k, t in sim.ptypes:
+        for k, t in types:
             ht = torch.empty(st[k].shape, dtype=getattr(torch, np.dtype(t).name),
                              pin_memory=True)
             ht.numpy()[:] = st[k]
             hs[k] = ht
         host.append((hs, len(st["i1"])))
-    bi = sum(n_s * sum(np.dtype(t).itemsize for _, t in sim.ptypes) for _, n_s in host)
+    bi = sum(n_s * sum(np.dtype(t).itemsize for _, t in types) for _, n_s in host)
     torch.cuda.synchronize(device)
     barrier(ws)
     t0 = time.perf_counter()
+    count = [n_s for _, n_s in host]
     for _ in range(args.steps):
         for s in range(2):
-            sim.set_particles(s, host[s][0], sim.qm[s], sim.qc[s])
+            sim.set_particles(s, {k: a[: count[s]] for k, a in host[s][0].items()},
+                              sim.qm[s], sim.qc[s])
         sim.step(1)
         for s in range(2):
             v = sim.species_views(s)
-            for k, _ in sim.ptypes:
-                host[s][0][k][: v[k].numel()].copy_(v[k], non_blocking=True)
+            count[s] = v["i1"].numel()  # the live count after the step (removals, sorts)
+            for k, _ in types:
+                host[s][0][k][: count[s]].copy_(v[k], non_blocking=True)
         torch.cuda.synchronize(device)
     t_e2e = time.perf_counter() - t0
     t_e2e = allreduce_max(ws, t_e2e, device)

@@ -223,7 +223,11 @@ GRPIC_API grpic_status grpic_load_particles(grpic_ctx *ctx, int species, int64_t
                                   double density_power, const grpic_particle_init *in);
 
 /* Sets the full state of a species (every array of grpic_particles), host or device
- * pointers. Used for restarts and to feed identical states to parity checks. */
+ * pointers. Used for restarts and to feed identical states to parity checks. The four
+ * previous-position arrays (i1p, i2p, dx1p, dx2p) may all be null: the previous position is
+ * then set to the position on the device (the push writes it anyway, Sec. 3.2); either all
+ * four or none. Errors: GRPIC_ECAPACITY (n > capacity), GRPIC_EINVAL (a null array among the
+ * first ten, or some but not all of the last four). */
 GRPIC_API grpic_status grpic_set_particles(grpic_ctx *ctx, int species, int64_t n, double qm, double qc,
                                  const grpic_particles *in);
 

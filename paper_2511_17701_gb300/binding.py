@@ -258,15 +258,19 @@ class Sim:
         self.sync()
 
     def set_particles(self, s, arrays: dict, qm, qc):
-        """Full species state from host (numpy) or device (torch) arrays."""
+        """Full species state from host (numpy) or device (torch) arrays. Without i1p, i2p,
+        dx1p, dx2p the previous position is set to the position on the device."""
         keep = []
         for k, t in self.ptypes:
+            if k not in arrays and k in ("i1p", "i2p", "dx1p", "dx2p"):
+                keep.append(None)
+                continue
             a = arrays[k]
             if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
                 a = np.ascontiguousarray(a, dtype=t)
             keep.append(a)
         n = len(keep[0])
-        p = Particles(*[_ptr(a) for a in keep])
+        p = Particles(*[None if a is None else _ptr(a) for a in keep])
         self._check(self.L.grpic_set_particles(self.ctx, s, n, qm, qc, C.byref(p)), "set_particles")
         self.qm[s], self.qc[s] = qm, qc
         self.sync()

@@ -576,10 +576,20 @@ grpic_status grpic_set_particles(grpic_ctx *ctx, int species, int64_t n, double 
   grpic_particles &L = sp.soa[sp.live];
   const cudaStream_t st = ctx->stream;
   if (n > 0) {
-    for (int a = 0; a < NARR; ++a) {
+    // i1p, i2p, dx1p, dx2p (the last four arrays) may all be null: the previous position
+    // is then the position, copied on the device
+    const bool prev = in->i1p || in->i2p || in->dx1p || in->dx2p;
+    const int n_in = prev ? NARR : NARR - 4;
+    for (int a = 0; a < n_in; ++a) {
       const void *src = cslot(*in, a);
       if (!src) return fail(ctx, GRPIC_EINVAL, "null particle array %d", a);
       CK(copy(*slot(L, a), src, (size_t)n * elem_bytes(ctx, a), st));
+    }
+    if (!prev) {
+      const int from[4] = {0, 1, 2, 3};  // i1, i2, dx1, dx2 -> i1p, i2p, dx1p, dx2p
+      for (int q = 0; q < 4; ++q)
+        CK(copy(*slot(L, NARR - 4 + q), *slot(L, from[q]), (size_t)n * elem_bytes(ctx, from[q]),
+                st));
     }
   }
   k_set_i64<<<1, 1, 0, st>>>(sp.n_dev, n);

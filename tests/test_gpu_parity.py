@@ -310,3 +310,20 @@ def test_refined_iterations_edge_particles(torch_cuda):
         g.push(0)
         osim.push(0)
         assert_particles(g.get_particles(0), osim.species[0].view())
+
+
+def test_set_particles_without_previous_position(torch_cuda):
+    """grpic_set_particles with null i1p, i2p, dx1p, dx2p sets the previous position to the
+    position; a push from there is the push of the full state."""
+    osim = oracle_state(BASE)
+    osim.predict()
+    sp = osim.species[0]
+    g = gpu_from_oracle(osim)
+    state = {k: v for k, v in sp.view().items() if k not in ("i1p", "i2p", "dx1p", "dx2p")}
+    g.set_particles(0, state, sp.qm, sp.qc)
+    got = g.get_particles(0)
+    for a, b in (("i1p", "i1"), ("i2p", "i2"), ("dx1p", "dx1"), ("dx2p", "dx2")):
+        assert np.array_equal(got[a], got[b]), a
+    g.push(0)
+    osim.push(0)
+    assert_particles(g.get_particles(0), sp.view())
