@@ -91,9 +91,10 @@ typedef struct {
   int metric;          /* grpic_metric_kind: kerr_schild_0 (flat) or Kerr-Schild, App. A   */
   double a;            /* black-hole spin, 0 <= a < 1 (ignored for KS0)                     */
   int n_r, n_theta;    /* cells along x1 (radial) and x2 (polar), Sec. 3                    */
-  double r_min, r_max; /* x1 in [0, n_r] maps to r = r_min exp(x1 dxi), dxi = ln(r_max/r_min)/n_r
-                          (quasi-spherical map of App. A with r0 = 0, h0 = 0);
-                          x2 in [0, n_theta] maps to theta = x2 pi / n_theta                 */
+  double r_min, r_max; /* x1 in [0, n_r] maps to r = r0 + (r_min - r0) exp(x1 dxi), dxi =
+                          ln((r_max - r0)/(r_min - r0))/n_r (quasi-spherical map of App. A;
+                          r0, h0 below); x2 in [0, n_theta] maps to eta = x2 pi / n_theta and
+                          theta(eta) (theta = eta when h0 = 0)                                */
   double cfl;          /* used when dt <= 0: dt = cfl * min over cells of
                           1 / (alpha sqrt(h^11 + h^22) + |beta^1|)                           */
   double dt;           /* time step; > 0 overrides cfl                                       */

@@ -33,7 +33,7 @@ typedef struct {
   int metric;          /* 0: flat spacetime (kerr_schild_0), 1: Kerr-Schild           */
   double a;            /* spin (ignored for metric 0)                                  */
   int n_r, n_th;       /* cells in x1 (radial) and x2 (polar)                          */
-  double r_min, r_max; /* radial extent; x1 -> r = r_min exp(x1 dxi)                   */
+  double r_min, r_max; /* radial extent; x1 -> r = r0 + (r_min - r0) exp(x1 dxi)      */
   double dt;           /* time step                                                    */
   int n_iter;          /* fixed iteration count of both implicit pushes                */
   double small_angle;  /* SMALL_ANGLE_GR                                               */

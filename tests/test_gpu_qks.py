@@ -142,3 +142,20 @@ def test_adjoint_refuses_quasi_spherical_grids(torch_cuda):
     st[1] += 20.0
     with pytest.raises(GrpicError):
         g.adjoint_forward(st, qm=1.0, b0=1.0, n_steps=2, ckpt_every=1, n_iter=10)
+
+
+def test_filter_and_photons_on_a_quasi_spherical_grid(torch_cuda):
+    """The widened rows together: n_f = 2 current-filter passes, a photon species beside the
+    pairs, on the quasi-spherical grid; full steps in FP64 against the oracle."""
+    cfg = dict(QKS, r_min=1.2, n_filter=2, sort_every=2, tile_r=8, tile_theta=8)
+    osim = oracle_state(cfg)
+    pl = W.pair_plasma(cfg)
+    uh = W.maxwell_juttner(np.random.default_rng(4), pl["pos"]["i1"].size, 2.0)
+    osim.add_species(pl["pos"], uh, pl["w0"], pl["qm"][1], pl["qc"][1], pl["density_power"],
+                     massless=True)
+    g = gpu_from_oracle(osim, massless=[2])
+    g.step(2)
+    osim.step(2, sort_every=2, tr=8, tt=8)
+    assert_planes(g.planes(), osim.F, planes=AFTER_ADVANCE, rtol=1e-11, what="qks+filter")
+    for s in range(3):
+        assert_particles(g.get_particles(s), osim.species[s].view(), rtol=1e-11)
