@@ -54,9 +54,9 @@ FP64_FLOP_PER_PARTICLE_STEP = {True: 1155, False: 1620}
 SMS, MAX_SM_GHZ = 152, 2.07
 FP64_PIPE_PEAK_GOPS = 2 * SMS * MAX_SM_GHZ  # 629 G operations/s
 # Warp instructions issued per particle by k_push32<deposit> on the wald512 workload (ncu:
-# 440.7 M over 8.39 M particles with 12 resident blocks per SM, spills included); an SM
+# 394.9 M over 8.39 M particles with 12 resident blocks per SM, spills included); an SM
 # issues at most 4 warp instructions per clock.
-MIXED_WARP_INST_PER_PARTICLE = 52.5
+MIXED_WARP_INST_PER_PARTICLE = 47.1
 ISSUE_PEAK_GINST = 4 * SMS * MAX_SM_GHZ  # 1259 G warp instructions/s
 
 

@@ -57,6 +57,7 @@ struct grpic_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;  // guard kernels of the mixed push
   cudaEvent_t ev_fork[GRPIC_MAX_SPECIES] = {}, ev_done[GRPIC_MAX_SPECIES] = {};
+  cudaEvent_t ev_class[GRPIC_MAX_SPECIES] = {};
   bool bound = false, metric_ready = false, fields_ready = false;
   double field_b0 = 1.0;  // amplitude of the analytic field in the planes (1 for user fields)
   size_t off_planes = 0, off_tab = 0, off_polar = 0, off_dt = 0, off_diag = 0, off_ptab = 0;
@@ -231,11 +232,12 @@ struct PhaseTimer {
 
 // --- precision-dispatched pieces of the hot path
 template <typename T>
-cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, int k, bool deposit) {
+cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, int k, bool deposit, int stage = PUSH_ALL) {
   SpeciesState &sp = c->sp[k];
-  const std::pair<cudaEvent_t, cudaEvent_t> *kt = next_events(c, PH_KERNEL);
-  const PushStreams ps{c->stream, c->side, c->ev_fork[k], c->ev_done[k],
-                       kt ? kt->first : nullptr, kt ? kt->second : nullptr};
+  const std::pair<cudaEvent_t, cudaEvent_t> *kt =
+      stage == PUSH_GUARD ? nullptr : next_events(c, PH_KERNEL);
+  const PushStreams ps{c->stream, c->side, c->ev_fork[k], c->ev_done[k], c->ev_class[k],
+                       kt ? kt->first : nullptr, kt ? kt->second : nullptr, stage};
   const int tr = c->cfg.tile_r, tt = c->cfg.tile_theta;
   const int ntr = (c->g.n_r + tr - 1) / tr, ntt = (c->g.n_th + tt - 1) / tt;
   const TileInfo ti{sp.tiles_valid && c->cfg.tiled_push ? sp.tile_start : nullptr, tr, tt, ntr,
@@ -366,7 +368,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   size_t off = 0;
   ctx->off_planes = off; off += up(ps * fs) * 36;
   ctx->off_tab = off;    off += up(ps * fs) * 4 * T_NQ;
-  ctx->off_polar = off;  off += up((size_t)g.NX * fs);
+  ctx->off_polar = off;  off += up((size_t)3 * g.NX * fs);
   ctx->off_ptab = off;   off += 10 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 8);
   ctx->off_dt = off;     off += up(64);
   ctx->off_diag = off;   off += up(DG_N * 8);
@@ -451,6 +453,7 @@ grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream)
       for (int s = 0; s < GRPIC_MAX_SPECIES; ++s) {
         CK(cudaEventCreateWithFlags(&ctx->ev_fork[s], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ctx->ev_done[s], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_class[s], cudaEventDisableTiming));
       }
     }
   }
@@ -711,7 +714,12 @@ grpic_status grpic_field_step(grpic_ctx *ctx, int phase) {
   return GRPIC_OK;
 }
 
-grpic_status grpic_sort(grpic_ctx *ctx, int species) {
+}  // extern "C"
+
+namespace {
+// the cell sort of one species; with_prev false inside grpic_step, whose push of the species
+// follows and rewrites the previous positions before anything reads them
+grpic_status sort_species(grpic_ctx *ctx, int species, bool with_prev) {
   grpic_status s = need_bound(ctx);
   if (s) return s;
   if ((s = need_species(ctx, species))) return s;
@@ -721,16 +729,21 @@ grpic_status grpic_sort(grpic_ctx *ctx, int species) {
   if (ctx->mixed) {
     CK(launch_sort<float>(ctx->g, ctx->cfg.tile_r, ctx->cfg.tile_theta, dev_view<float>(sp, sp.live),
                           dev_view<float>(sp, 1 - sp.live), sp.n_bound, sp.n_dev, ctx->S,
-                          sp.tile_start, ctx->stream));
+                          sp.tile_start, ctx->stream, with_prev));
     sp.tiles_valid = true;
   } else {
     CK(launch_sort<double>(ctx->g, ctx->cfg.tile_r, ctx->cfg.tile_theta,
                            dev_view<double>(sp, sp.live), dev_view<double>(sp, 1 - sp.live),
-                           sp.n_bound, sp.n_dev, ctx->S, nullptr, ctx->stream));
+                           sp.n_bound, sp.n_dev, ctx->S, nullptr, ctx->stream, with_prev));
   }
   sp.live = 1 - sp.live;
   return GRPIC_OK;
 }
+}  // namespace
+
+extern "C" {
+
+grpic_status grpic_sort(grpic_ctx *ctx, int species) { return sort_species(ctx, species, true); }
 
 grpic_status grpic_step(grpic_ctx *ctx, int n_steps) {
   grpic_status s = need_fields(ctx);
@@ -744,19 +757,23 @@ grpic_status grpic_step(grpic_ctx *ctx, int n_steps) {
     }
     if (ctx->cfg.sort_every > 0 && ctx->step % ctx->cfg.sort_every == 0)
       for (int k = 0; k < ctx->cfg.n_species; ++k)
-        if ((s = grpic_sort(ctx, k))) return s;
+        if ((s = sort_species(ctx, k, false))) return s;
     {
       PhaseTimer t(ctx, PH_PUSH);  // fused push + deposit of every species
       if (ctx->mixed) CK(do_zero_J(ctx, ctx->F32));
       else CK(do_zero_J(ctx, ctx->F64));
+      // mixed: the guard stages of all species first, so that their FP64 kernels (the longer
+      // chain, on the side stream) run beside all the FP32 kernels instead of trailing the last
+      if (ctx->mixed)
+        for (int k = 0; k < ctx->cfg.n_species; ++k)
+          if (ctx->sp[k].loaded) CK(do_push(ctx, ctx->F32, k, true, PUSH_GUARD));
       for (int k = 0; k < ctx->cfg.n_species; ++k) {
         SpeciesState &sp = ctx->sp[k];
         if (!sp.loaded) continue;
-        if (ctx->mixed) CK(do_push(ctx, ctx->F32, k, true));
+        if (ctx->mixed) CK(do_push(ctx, ctx->F32, k, true, PUSH_MAIN));
         else CK(do_push(ctx, ctx->F64, k, true));
         ++ctx->push_calls;
       }
-      // the guard kernels of one species overlap the FP32 kernel of the next
       for (int k = 0; k < ctx->cfg.n_species; ++k)
         if (ctx->sp[k].loaded) CK(join_push(ctx, k));
     }
@@ -940,6 +957,7 @@ void grpic_destroy(grpic_ctx *ctx) {
     for (int s = 0; s < GRPIC_MAX_SPECIES; ++s) {
       cudaEventDestroy(ctx->ev_fork[s]);
       cudaEventDestroy(ctx->ev_done[s]);
+      cudaEventDestroy(ctx->ev_class[s]);
     }
   }
   delete ctx;

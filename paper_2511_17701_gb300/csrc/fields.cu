@@ -20,6 +20,18 @@ __device__ __forceinline__ T tabv(const T *tab, const GridP &g, int cls, int q, 
 // A(x1) = dr (r^2 + a^2) sqrt(1 + 2 M r/(r^2 + a^2)) (1 - cos(theta(x2 = 1/2))) (App. A, per
 // unit phi; theta(1/2) = dtheta/2 on the plain grid).
 // ---------------------------------------------------------------------------------
+// The absorbing layer (MATCH, Sec. 3.3.3): a field value v relaxes towards its initial value
+// vi as v - k (v - vi), k = absorb_coef x^3, x = (r - r_absorb) / (r_max - r_absorb) capped at
+// 1, beyond r_absorb. k depends on x1 alone, so it is tabulated per column.
+__device__ __forceinline__ double absorb_factor(const GridP &g, double x1) {
+  if (!(g.r_absorb < g.r_max)) return 0.0;
+  const double r = g.r0 + map_e(g, x1);
+  if (r <= g.r_absorb) return 0.0;
+  double x = (r - g.r_absorb) / (g.r_max - g.r_absorb);
+  x = fmin(x, 1.0);
+  return g.absorb_coef * x * x * x;
+}
+
 template <typename T>
 __global__ void k_metric_tables(GridP g, T *tab, T *polar) {
   const int64_t ps = plane_size(g);
@@ -45,7 +57,9 @@ __global__ void k_metric_tables(GridP g, T *tab, T *polar) {
       const double e = map_e(g, i + 0.5), r = g.r0 + e, a2 = g.a * g.a;
       polar[i + G_] = (T)(g.dxi * e * (r * r + a2) * sqrt(1.0 + 2.0 * g.M * r / (r * r + a2)) *
                           (1.0 - cos(map_theta(g, 0.5))));
+      polar[2 * g.NX + i + G_] = (T)absorb_factor(g, i + 0.5);
     }
+    if (cls == CLS_NN && j == 0) polar[g.NX + i + G_] = (T)absorb_factor(g, i);
   }
 }
 
@@ -316,21 +330,18 @@ __global__ void k_aux_H(GridP g, Pair3<T> B, Pair3<T> D, const T *tab, T *H1, T 
 // MATCH absorbing layer (reading of paper I's form): F <- F - lambda (F - F_init),
 // lambda = coef min(1, ((r - r_abs)/(r_max - r_abs)))^3 for r > r_absorb, rows [0, n_theta].
 template <typename T>
-__device__ __forceinline__ T match(const GridP &g, T v, T vi, double x1, int j) {
-  if (!(g.r_absorb < g.r_max) || j < 0 || j > g.n_th) return v;
-  const double r = g.r0 + map_e(g, x1);
-  if (r <= g.r_absorb) return v;
-  double x = (r - g.r_absorb) / (g.r_max - g.r_absorb);
-  x = fmin(x, 1.0);
-  return v - (T)(g.absorb_coef * x * x * x) * (v - vi);
+__device__ __forceinline__ T match(const GridP &g, T v, T vi, const T *absorb, int i, int j) {
+  if (j < 0 || j > g.n_th) return v;
+  const T k = __ldg(absorb + i + G_);  // the factor at this column (absorb_factor)
+  return k == (T)0 ? v : v - k * (v - vi);
 }
 
 // Faraday, Eq. (discretized-faraday): Bout = Bin - dt curl E / sqrt(h) on the evolved
 // points, Bout = Bin elsewhere; B^2 is not evolved on the axes. Covers every stored point.
 template <typename T>
 __global__ void k_faraday(GridP g, Pair3<T> Bin, const T *E1, const T *E2, const T *E3,
-                          const T *tab, T *B1, T *B2, T *B3, const T *Bi1, const T *Bi2,
-                          const T *Bi3, int do_match) {
+                          const T *tab, const T *absorb, T *B1, T *B2, T *B3, const T *Bi1,
+                          const T *Bi2, const T *Bi3, int do_match) {
   const int64_t n = plane_size(g);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -347,9 +358,9 @@ __global__ void k_faraday(GridP g, Pair3<T> Bin, const T *E1, const T *E2, const
       b3 -= dt * ((E2[k + 1] - E2[k]) - (E1[k + g.NX] - E1[k])) *
             tabv(tab, g, CLS_HH, T_ISH, i, j);
     if (do_match) {
-      b1 = match(g, b1, Bi1[k], i, j);
-      b2 = match(g, b2, Bi2[k], i + 0.5, j);
-      b3 = match(g, b3, Bi3[k], i + 0.5, j);
+      b1 = match(g, b1, Bi1[k], absorb, i, j);
+      b2 = match(g, b2, Bi2[k], absorb + g.NX, i, j);
+      b3 = match(g, b3, Bi3[k], absorb + g.NX, i, j);
     }
     B1[k] = b1; B2[k] = b2; B3[k] = b3;
   }
@@ -385,9 +396,9 @@ __global__ void k_ampere(GridP g, Pair3<T> Din, const T *H1, const T *H2, const 
       d3 += dt * ((H2[k] - H2[k - 1]) - (H1[k] - H1[k - g.NX]) - fpi * pv(J, 2, k)) *
             tabv(tab, g, CLS_NN, T_ISH, i, j);
     if (do_match) {
-      d1 = match(g, d1, Di1[k], i + 0.5, j);
-      d2 = match(g, d2, Di2[k], i, j);
-      d3 = match(g, d3, Di3[k], i, j);
+      d1 = match(g, d1, Di1[k], polar + 2 * g.NX, i, j);
+      d2 = match(g, d2, Di2[k], polar + g.NX, i, j);
+      d3 = match(g, d3, Di3[k], polar + g.NX, i, j);
     }
     D1[k] = d1; D2[k] = d2; D3[k] = d3;
   }
@@ -528,8 +539,9 @@ cudaError_t launch_predict(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t 
   auxE(g, one(F.B), mean(F.D0, F.D), F, st);
   const Pair3<T> Bm = mean(F.B0, F.B);
   const int64_t ps = plane_size(g);
-  k_faraday<T><<<blocks_for(ps), TPB, 0, st>>>(g, Bm, F.E[0], F.E[1], F.E[2], F.tab, F.Bn[0],
-                                               F.Bn[1], F.Bn[2], nullptr, nullptr, nullptr, 0);
+  k_faraday<T><<<blocks_for(ps), TPB, 0, st>>>(g, Bm, F.E[0], F.E[1], F.E[2], F.tab, nullptr,
+                                               F.Bn[0], F.Bn[1], F.Bn[2], nullptr, nullptr,
+                                               nullptr, 0);
   COUNT_LAUNCH(1);
   horizon(g, F.Bn, st);
   axis(g, F.Bn, 1, st);
@@ -545,8 +557,8 @@ cudaError_t launch_advance(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t 
   auxE(g, one(F.Bn), one(F.D), F, st);
   auxH(g, one(F.Bn), one(F.D), F, st);
   k_faraday<T><<<blocks_for(ps), TPB, 0, st>>>(g, one(F.B), F.E[0], F.E[1], F.E[2], F.tab,
-                                               F.B0[0], F.B0[1], F.B0[2], F.Bi[0], F.Bi[1],
-                                               F.Bi[2], 1);
+                                               F.polar + g.NX, F.B0[0], F.B0[1], F.B0[2],
+                                               F.Bi[0], F.Bi[1], F.Bi[2], 1);
   COUNT_LAUNCH(1);
   horizon(g, F.B0, st);
   axis(g, F.B0, 1, st);

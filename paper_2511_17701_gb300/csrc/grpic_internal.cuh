@@ -308,7 +308,8 @@ struct FieldPtrsT {
   T *B[3], *D[3], *B0[3], *D0[3], *J[3], *J0[3], *Bn[3], *Bi[3], *Di[3];
   T *E[3], *H[3], *Dh[3];
   const T *tab;    // [4 classes][T_NQ][plane]
-  const T *polar;  // [NX], polar area at x1 = i + 1/2 stored at i
+  const T *polar;  // [3][NX]: the polar area at x1 = i + 1/2, then the absorber factor
+                   // absorb_coef x^3 at x1 = i and at x1 = i + 1/2 (stored at i)
 };
 using FieldPtrs = FieldPtrsT<double>;
 
@@ -348,10 +349,16 @@ struct TileInfo {
 // Streams of one push: the FP64-pipe-bound guard kernels run on `side`, forked from
 // `main` after the classification by `fork`; `done` is recorded on `side` after them and
 // the caller makes `main` wait on it before anything reads the currents or the particles.
+// which part of a push to launch: the mixed path's guard stage (classify, then the FP64
+// guard kernels, all on `side`) and its main FP32 kernel (on `main`, after the classify) can
+// be issued separately, so that the guard stages of all species start before the first FP32
+// kernel
+enum { PUSH_ALL = 0, PUSH_GUARD = 1, PUSH_MAIN = 2 };
 struct PushStreams {
   cudaStream_t main, side;
-  cudaEvent_t fork, done;
+  cudaEvent_t fork, done, classified;  // side after main; guard kernels done; classify done
   cudaEvent_t t0, t1;  // when not null: recorded on `main` around the main push kernel
+  int stage = PUSH_ALL;
 };
 
 template <typename T>
@@ -433,7 +440,9 @@ struct SortScratch {
 };
 int64_t sort_hist_entries(int64_t max_n);
 int64_t sort_bsum_entries(int64_t max_n);
+// with_prev false: the previous-position arrays are left out of the gather (the caller
+// pushes the species next, and the push rewrites them first)
 template <typename T>
 cudaError_t launch_sort(const GridP &g, int tile_r, int tile_t, SpeciesDevT<T> in,
                         SpeciesDevT<T> out, int64_t n_bound, int64_t *n_dev, const SortScratch &S,
-                        uint32_t *tile_start, cudaStream_t st);
+                        uint32_t *tile_start, cudaStream_t st, bool with_prev = true);

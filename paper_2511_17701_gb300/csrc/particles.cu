@@ -690,6 +690,33 @@ __device__ __forceinline__ void deposit32_warp(const GridP &g, const Sink &sink,
   }
 }
 
+// Stop rule of the FP32 implicit iterations: the update within ITER_TOL32 max(1, |value|),
+// two FP32 ulps at 1. The remaining error, rho / (1 - rho) of that update (rho the
+// contraction), is then below the rounding of the stored values.
+constexpr float ITER_TOL32 = 0x1p-22f;
+__device__ __forceinline__ bool settled32(float n0, float t0, float n1, float t1) {
+  return fabsf(n0 - t0) <= ITER_TOL32 * fmaxf(1.0f, fabsf(n0)) &&
+         fabsf(n1 - t1) <= ITER_TOL32 * fmaxf(1.0f, fabsf(n1));
+}
+
+// The FP32 momentum substep: n_iter applications of the geodesic map, or fewer under the
+// stop rule above.
+__device__ __forceinline__ void geodesic_momentum32(const GridP &g, const Local<float> &L,
+                                                    float u[3], float m2) {
+  const GeoMap<float> m(g, L, u, m2);
+  float t0 = u[0], t1 = u[1];
+  for (int it = 0; it < g.n_iter; ++it) {
+    float n0, n1;
+    m.apply(t0, t1, n0, n1);
+    const bool done = settled32(n0, t0, n1, t1);
+    t0 = n0;
+    t1 = n1;
+    if (done && g.stop_on_repeat) break;
+  }
+  u[0] = t0;
+  u[1] = t1;
+}
+
 template <bool Q, bool G64>
 __device__ __forceinline__ float phi_rate32(const GridP &g, const PushTables &tb, int i, int j,
                                             float o1, float o2, const float u[3], float m2) {
@@ -742,7 +769,7 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
     boris(uh, Dh, Bh, hq);
     hat_cov(L, uh, u);
   }
-  geodesic_momentum(g, L, u, s.f_m2);
+  geodesic_momentum32(g, L, u, s.f_m2);
   if (em) {
     cov_hat(L, u, uh);
     boris(uh, Dh, Bh, hq);
@@ -750,7 +777,9 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
   }
   const float dt = g.f_dt;
   const float uu0 = 2.0f * u[0] * u[2];
-  float t1 = dx1, t2 = dx2;
+  // the coordinate iteration under the FP32 stop rule; dphi/dt then comes from the metric of
+  // its last iteration, whose midpoint is within the update of the final one
+  float t1 = dx1, t2 = dx2, v3 = NAN;
   for (int it = 0; it < g.n_iter; ++it) {
     Geo<float> o;
     if (it == 0) o = L.G;
@@ -760,10 +789,13 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
     const float ag = rsqrtf(o.opz * q);
     const float n1 = fmaf(dt, fmaf(ag, fmaf(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
     const float n2 = fmaf(dt, ag * o.H22 * u[1], dx2);
-    const bool fixed = (n1 == t1) && (n2 == t2);
+    const bool done = settled32(n1, t1, n2, t2);
     t1 = n1;
     t2 = n2;
-    if (fixed && g.stop_on_repeat) break;
+    if (done && g.stop_on_repeat) {
+      v3 = ag * fmaf(o.H13, u[0], o.H33 * u[2]);
+      break;
+    }
   }
   if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(t1) && isfinite(t2) &&
         fabsf(t1) < 1e6f && fabsf(t2) < 1e6f)) {
@@ -788,10 +820,10 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
   s.u1[k] = u[0]; s.u2[k] = u[1]; s.u3[k] = u[2];
   if (j1 < 0) { s.tag[k] = 2; count(diag, DG_LEFT_INNER); }
   else if (j1 >= g.n_r) { s.tag[k] = 2; count(diag, DG_LEFT_OUTER); }
-  // phi at the midpoint, relative to the start cell
+  // phi at the midpoint, relative to the start cell (when the iteration ran to n_iter)
   const float b1 = (float)di + e1, b2 = (float)dj + e2;
-  const float v3 = phi_rate32<Q, G64>(g, tb, i1, i2, 0.5f * (dx1 + b1), 0.5f * (dx2 + b2), u,
-                                   s.f_m2);
+  if (isnan(v3))
+    v3 = phi_rate32<Q, G64>(g, tb, i1, i2, 0.5f * (dx1 + b1), 0.5f * (dx2 + b2), u, s.f_m2);
   s.phi[k] = fmaf(dt, v3, s.phi[k]);
   mv = Move32{i1, i2, di, dj, dx1, dx2, b1, b2, s.f_qc * s.w[k], v3};
   return true;
@@ -824,30 +856,59 @@ __global__ void __launch_bounds__(TPB, DEPOSIT ? 4 : 3) k_push(GridP g, FieldPtr
 }
 
 // Mixed path, classification: zone 1 and zone 2 particles are appended to their lists
-// (warp-aggregated) and marked in the mask, one ballot word per warp (blockDim and the grid
-// stride are multiples of 32, so a warp covers particles 32w .. 32w + 31).
+// (warp-aggregated) and marked in the mask, one word per 32 consecutive particles (bit k & 31
+// of word k >> 5; a warp's 32 lanes cover one word). The kernel is bound by load latency, so
+// each thread takes CL_U particles a grid stride apart and issues all their loads before
+// using any; the loop is uniform over the warp (its first particle decides).
+constexpr int CL_U = 8;
+// one-warp blocks per SM of the zone-1 and zone-2 guard kernels (launch shape)
+#ifndef GRPIC_GUARD_BLOCKS_PER_SM
+#define GRPIC_GUARD_BLOCKS_PER_SM 8
+#endif
+#ifndef GRPIC_AXIS_BLOCKS_PER_SM
+#define GRPIC_AXIS_BLOCKS_PER_SM 4
+#endif
 __global__ void __launch_bounds__(TPB) k_classify(GridP g, SpeciesDevT<float> s, PushTables tb,
                                                   GuardList gl) {
   const int64_t n = *s.n;
   const int lane = threadIdx.x & 31;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int zone = s.tag[k] == 1 ? guard_zone(tb, g, s.i1[k], s.i2[k]) : 0;
-    const unsigned act = __activemask();
-    const unsigned m1 = __ballot_sync(act, zone == 1), m2 = __ballot_sync(act, zone == 2);
-    const int leader = __ffs(act) - 1;
-    if (lane == leader) gl.mask[k >> 5] = m1 | m2;
-    if (m1 | m2) {
-      unsigned long long b1 = 0, b2 = 0;
-      if (lane == leader) {
-        if (m1) b1 = atomicAdd(gl.count, (unsigned long long)__popc(m1));
-        if (m2) b2 = atomicAdd(gl.count + 1, (unsigned long long)__popc(m2));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); w0 < n;
+       w0 += CL_U * stride) {
+    uint8_t tag[CL_U];
+    int a[CL_U], b[CL_U];
+#pragma unroll
+    for (int q = 0; q < CL_U; ++q) {
+      const int64_t k = w0 + q * stride + lane;
+      tag[q] = 0;
+      a[q] = b[q] = 0;
+      if (k < n) {
+        tag[q] = s.tag[k];
+        a[q] = s.i1[k];
+        b[q] = s.i2[k];
       }
-      b1 = __shfl_sync(act, b1, leader);
-      b2 = __shfl_sync(act, b2, leader);
-      const unsigned below = (1u << lane) - 1u;
-      if (zone == 1) gl.idx[b1 + __popc(m1 & below)] = (uint32_t)k;
-      if (zone == 2) gl.idx[gl.cap - 1 - (int64_t)(b2 + __popc(m2 & below))] = (uint32_t)k;
+    }
+#pragma unroll
+    for (int q = 0; q < CL_U; ++q) {
+      const int64_t kw = w0 + q * stride;  // the warp's first particle
+      if (kw >= n) break;
+      const int zone = tag[q] == 1 ? guard_zone(tb, g, a[q], b[q]) : 0;
+      const unsigned m1 = __ballot_sync(0xffffffffu, zone == 1);
+      const unsigned m2 = __ballot_sync(0xffffffffu, zone == 2);
+      if (lane == 0) gl.mask[kw >> 5] = m1 | m2;
+      if (m1 | m2) {
+        unsigned long long b1 = 0, b2 = 0;
+        if (lane == 0) {
+          if (m1) b1 = atomicAdd(gl.count, (unsigned long long)__popc(m1));
+          if (m2) b2 = atomicAdd(gl.count + 1, (unsigned long long)__popc(m2));
+        }
+        b1 = __shfl_sync(0xffffffffu, b1, 0);
+        b2 = __shfl_sync(0xffffffffu, b2, 0);
+        const unsigned below = (1u << lane) - 1u;
+        const uint32_t k = (uint32_t)(kw + lane);
+        if (zone == 1) gl.idx[b1 + __popc(m1 & below)] = k;
+        if (zone == 2) gl.idx[gl.cap - 1 - (int64_t)(b2 + __popc(m2 & below))] = k;
+      }
     }
   }
 }
@@ -1132,33 +1193,46 @@ cudaError_t push_impl(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
                       const PushTables &tb, const GuardList &gl, const TileInfo &ti,
                       int64_t n_bound, bool deposit, unsigned long long *diag,
                       const PushStreams &ps) {
+  const bool main_stage = ps.stage != PUSH_GUARD, guard_stage = ps.stage != PUSH_MAIN;
   if (n_bound <= 0) {  // keep a requested event pair recorded (zero duration)
-    if (ps.t0) cudaEventRecord(ps.t0, ps.main);
-    if (ps.t1) cudaEventRecord(ps.t1, ps.main);
+    if (main_stage && ps.t0) cudaEventRecord(ps.t0, ps.main);
+    if (main_stage && ps.t1) cudaEventRecord(ps.t1, ps.main);
     return cudaGetLastError();
   }
   if constexpr (sizeof(T) == 8) {
+    if (!main_stage) return cudaSuccess;  // the FP64 path has no guard stage
     if (ps.t0) cudaEventRecord(ps.t0, ps.main);
     if (deposit) k_push<true, Q><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, tb, s, diag);
     else k_push<false, Q><<<blocks_for(n_bound), TPB, 0, ps.main>>>(g, F, tb, s, diag);
     if (ps.t1) cudaEventRecord(ps.t1, ps.main);
     COUNT_LAUNCH(1);
   } else {
-    cudaError_t e = cudaMemsetAsync(gl.count, 0, 2 * sizeof(unsigned long long), ps.main);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     const int nb = blocks_for(n_bound);
-    k_classify<<<nb, TPB, 0, ps.main>>>(g, s, tb, gl);
-    if ((e = cudaEventRecord(ps.fork, ps.main)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(ps.side, ps.fork, 0)) != cudaSuccess) return e;
-    // the guard kernels are FP64-pipe bound: a few one-warp blocks per SM reach every SM
-    // sub-partition's FP64 unit and leave the registers to the concurrent FP32 kernel
-    if (deposit) {
-      k_push_guard<true, Q><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
-      k_push_axis<true, Q><<<152 * 4, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
-    } else {
-      k_push_guard<false, Q><<<152 * 8, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
-      k_push_axis<false, Q><<<152 * 4, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+    if (guard_stage) {
+      // the whole stage runs on the side stream, after everything issued so far on main
+      if ((e = cudaEventRecord(ps.fork, ps.main)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(ps.side, ps.fork, 0)) != cudaSuccess) return e;
+      if ((e = cudaMemsetAsync(gl.count, 0, 2 * sizeof(unsigned long long), ps.side)) != cudaSuccess)
+        return e;
+      k_classify<<<blocks_for((n_bound + CL_U - 1) / CL_U), TPB, 0, ps.side>>>(g, s, tb, gl);
+      if ((e = cudaEventRecord(ps.classified, ps.side)) != cudaSuccess) return e;
+      // the guard kernels are FP64-pipe bound: a few one-warp blocks per SM reach every SM
+      // sub-partition's FP64 unit and leave the registers to the concurrent FP32 kernel
+      constexpr int gb = 152 * GRPIC_GUARD_BLOCKS_PER_SM, ab = 152 * GRPIC_AXIS_BLOCKS_PER_SM;
+      if (deposit) {
+        k_push_guard<true, Q><<<gb, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+        k_push_axis<true, Q><<<ab, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+      } else {
+        k_push_guard<false, Q><<<gb, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+        k_push_axis<false, Q><<<ab, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
+      }
+      if ((e = cudaEventRecord(ps.done, ps.side)) != cudaSuccess) return e;
+      COUNT_LAUNCH(3);
     }
+    if (!main_stage) return cudaGetLastError();
+    // the FP32 kernel reads the mask the classify writes
+    if ((e = cudaStreamWaitEvent(ps.main, ps.classified, 0)) != cudaSuccess) return e;
     // the tiled kernel needs the tile ranges of a sort and a window that fits in shared memory
     const size_t smem = tiled_smem_bytes(ti);
     const bool tiled = ti.start != nullptr && smem <= 200 * 1024;
@@ -1179,8 +1253,7 @@ cudaError_t push_impl(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
       else k_push32<false, Q><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
     }
     if (ps.t1) cudaEventRecord(ps.t1, ps.main);
-    if ((e = cudaEventRecord(ps.done, ps.side)) != cudaSuccess) return e;
-    COUNT_LAUNCH(4);
+    COUNT_LAUNCH(1);
   }
   return cudaGetLastError();
 }

@@ -161,8 +161,9 @@ __global__ void k_scan_add(uint32_t *a, int64_t L, const uint32_t *bsum) {
   if (t < L) a[t] += bsum[t / SCAN_SEG];
 }
 
-// gather every array of the species by the final permutation
-template <typename T>
+// gather every array of the species by the final permutation (PREV false: all but the
+// previous position)
+template <typename T, bool PREV>
 __global__ void k_gather(SpeciesDevT<T> in, SpeciesDevT<T> out, const uint32_t *perm,
                          const int64_t *n_dev) {
   const int64_t n = *n_dev;
@@ -173,8 +174,10 @@ __global__ void k_gather(SpeciesDevT<T> in, SpeciesDevT<T> out, const uint32_t *
     out.dx1[k] = in.dx1[p]; out.dx2[k] = in.dx2[p];
     out.u1[k] = in.u1[p]; out.u2[k] = in.u2[p]; out.u3[k] = in.u3[p];
     out.phi[k] = in.phi[p]; out.w[k] = in.w[p]; out.tag[k] = in.tag[p];
-    out.i1p[k] = in.i1p[p]; out.i2p[k] = in.i2p[p];
-    out.dx1p[k] = in.dx1p[p]; out.dx2p[k] = in.dx2p[p];
+    if (PREV) {
+      out.i1p[k] = in.i1p[p]; out.i2p[k] = in.i2p[p];
+      out.dx1p[k] = in.dx1p[p]; out.dx2p[k] = in.dx2p[p];
+    }
   }
 }
 
@@ -201,7 +204,7 @@ int64_t sort_bsum_entries(int64_t max_n) {
 template <typename T>
 cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDevT<T> in, SpeciesDevT<T> out,
                         int64_t n_bound, int64_t *n_dev, const SortScratch &S,
-                        uint32_t *tile_start, cudaStream_t st) {
+                        uint32_t *tile_start, cudaStream_t st, bool with_prev) {
   if (n_bound <= 0) return cudaGetLastError();
   // number of key bits: keys of alive particles are < tiles * tr * tt; 0xFFFFFFFF must
   // sort after them, i.e. its low bits must exceed every alive key
@@ -240,7 +243,8 @@ cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDevT<T> in, Speci
                                                              (uint32_t)(tr * tt), tile_start);
     COUNT_LAUNCH(1);
   }
-  k_gather<T><<<grid_for(n_bound, TPB), TPB, 0, st>>>(in, out, S.vals[cur], in.n);
+  if (with_prev) k_gather<T, true><<<grid_for(n_bound, TPB), TPB, 0, st>>>(in, out, S.vals[cur], in.n);
+  else k_gather<T, false><<<grid_for(n_bound, TPB), TPB, 0, st>>>(in, out, S.vals[cur], in.n);
   COUNT_LAUNCH(1);
   k_set_n<<<1, 1, 0, st>>>(n_dev, alive);
   COUNT_LAUNCH(1);
@@ -249,10 +253,10 @@ cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDevT<T> in, Speci
 
 template cudaError_t launch_sort<double>(const GridP &, int, int, SpeciesDevT<double>,
                                          SpeciesDevT<double>, int64_t, int64_t *,
-                                         const SortScratch &, uint32_t *, cudaStream_t);
+                                         const SortScratch &, uint32_t *, cudaStream_t, bool);
 template cudaError_t launch_sort<float>(const GridP &, int, int, SpeciesDevT<float>,
                                         SpeciesDevT<float>, int64_t, int64_t *,
-                                        const SortScratch &, uint32_t *, cudaStream_t);
+                                        const SortScratch &, uint32_t *, cudaStream_t, bool);
 
 // ---------------------------------------------------------------------------------
 // grpic_sort_permutation_noalloc: the same stable cell sort, for callers that cannot
