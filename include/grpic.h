@@ -285,6 +285,25 @@ GRPIC_API grpic_status grpic_sort(grpic_ctx *ctx, int species);
  * push + deposit of all species, ADVANCE. */
 GRPIC_API grpic_status grpic_step(grpic_ctx *ctx, int n_steps);
 
+/* One full PIC step (Sec. 3.4, as grpic_step with n_steps = 1) with the particle state
+ * streamed through host memory; the paper has no counterpart to the streaming. state[k]
+ * (k < n_species) holds host arrays i1, i2, dx1, dx2, u1, u2, u3, phi, w, tag in the
+ * context's precision (as in grpic_set_particles; i1p .. dx2p are not used), n[k] the
+ * particles they hold. Species k's arrays go to the device on a copy stream, and the step
+ * waits for them only before it sorts or pushes that species; its state comes back into
+ * the same arrays on a second copy stream as soon as its push is done, so the copies of
+ * one species overlap the work on another. An FP64 context streams each species as four
+ * particle ranges, each pushed once its copies are in and copied back once pushed (a sort
+ * in the step waits for all four). Returns when all is done, with n[k] = the count
+ * after the step (a sort in the step drops the particles that left); the arrays hold n[k]
+ * elements on entry and at most that many are written. Page-locked host memory lets the
+ * copies run asynchronously (pageable memory works, serialised). Each species with
+ * n[k] > 0 must have been loaded or set before: its q/m and deposit coefficient are kept.
+ * Errors: GRPIC_ESTATE (fields not initialised, a species never loaded), GRPIC_ECAPACITY
+ * (n[k] > capacity), GRPIC_EINVAL (null state, counts or array). */
+GRPIC_API grpic_status grpic_step_host(grpic_ctx *ctx, const grpic_particles *state,
+                                       int64_t *n);
+
 /* --- allocation-free sort ------------------------------------------------------- */
 
 /* Largest particle count grpic_sort_permutation_noalloc accepts. */

@@ -31,7 +31,7 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_get_diagnostics", "grpic_set_timing", "grpic_get_timing", "grpic_last_error",
            "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants",
            "grpic_adjoint_forward", "grpic_adjoint_backward", "grpic_charge_check",
-           "grpic_config_bytes", "grpic_inject"]
+           "grpic_config_bytes", "grpic_inject", "grpic_step_host"]
 
 
 ADJOINT_SCRATCH_PER_STEP = 36  # doubles per particle and step of grpic_adjoint_backward
@@ -121,6 +121,7 @@ def lib(build: bool = True):
         L.grpic_field_step.argtypes = [P, C.c_int]
         L.grpic_sort.argtypes = [P, C.c_int]
         L.grpic_step.argtypes = [P, C.c_int]
+        L.grpic_step_host.argtypes = [P, C.POINTER(Particles), C.POINTER(C.c_int64)]
         L.grpic_get_diagnostics.argtypes = [P, C.POINTER(Diag)]
         L.grpic_set_timing.argtypes = [P, C.c_int]
         L.grpic_get_timing.argtypes = [P, C.POINTER(Timing)]
@@ -412,6 +413,31 @@ class Sim:
 
     def step(self, n=1):
         self._check(self.L.grpic_step(self.ctx, n), "step")
+
+    def step_host(self, states, counts):
+        """One step with the particle state streamed through host memory (grpic_step_host).
+        states[k]: dict of host arrays (numpy, or torch tensors in page-locked memory) i1, i2,
+        dx1, dx2, u1, u2, u3, phi, w, tag of the context's types, read and then overwritten in
+        place; counts[k]: the particles they hold. Returns the counts after the step."""
+        ns = len(self.qm)
+        P = (Particles * ns)()
+        keep = []
+        for k in range(ns):
+            ptrs = []
+            for name, t in self.ptypes:
+                a = states[k].get(name) if name not in ("i1p", "i2p", "dx1p", "dx2p") else None
+                if a is None:
+                    ptrs.append(None)
+                    continue
+                if isinstance(a, np.ndarray):
+                    if a.dtype != np.dtype(t) or not a.flags.c_contiguous:
+                        raise GrpicError("step_host: %s must be a contiguous %s array" % (name, t))
+                keep.append(a)
+                ptrs.append(_ptr(a))
+            P[k] = Particles(*ptrs)
+        n = (C.c_int64 * ns)(*[int(c) for c in counts])
+        self._check(self.L.grpic_step_host(self.ctx, P, n), "step_host")
+        return [int(x) for x in n]
 
     def diagnostics(self) -> dict:
         d = Diag()

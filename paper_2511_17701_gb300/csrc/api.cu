@@ -41,11 +41,25 @@ size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 __global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
 
+// the alive particles in each of the ranges [c len, (c + 1) len) of a species holding *n
+__global__ void k_chunk_counts(const int64_t *n, int64_t *out, int64_t len, int chunks) {
+  const int c = threadIdx.x;
+  if (c < chunks) {
+    const int64_t m = *n - c * len;
+    out[c] = m < 0 ? 0 : (m > len ? len : m);
+  }
+}
+
 }  // namespace
 
 long long grpic_launches = 0;
 
 enum { PH_PREDICT = 0, PH_SORT, PH_PUSH, PH_DEPOSIT, PH_ADVANCE, PH_KERNEL, PH_INJECT, PH_N };
+
+// grpic_step_host streams each FP64 species in this many particle ranges, so that the copies
+// of one range overlap the push of another (the mixed push, with its guard lists, streams
+// whole species)
+constexpr int HOST_CHUNKS = 4;
 
 struct grpic_ctx {
   grpic_config cfg;
@@ -58,6 +72,13 @@ struct grpic_ctx {
   cudaStream_t side = nullptr;  // guard kernels of the mixed push
   cudaEvent_t ev_fork[GRPIC_MAX_SPECIES] = {}, ev_done[GRPIC_MAX_SPECIES] = {};
   cudaEvent_t ev_class[GRPIC_MAX_SPECIES] = {};
+  // grpic_step_host: copy streams, events and pinned counts, created on its first call;
+  // device counts of the particle ranges it streams (in the arena)
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_in[GRPIC_MAX_SPECIES][HOST_CHUNKS] = {},
+              ev_pushed[GRPIC_MAX_SPECIES][HOST_CHUNKS] = {};
+  int64_t *host_n = nullptr;
+  size_t off_chunk = 0;
   bool bound = false, metric_ready = false, fields_ready = false;
   double field_b0 = 1.0;  // amplitude of the analytic field in the planes (1 for user fields)
   size_t off_planes = 0, off_tab = 0, off_polar = 0, off_dt = 0, off_diag = 0, off_ptab = 0;
@@ -372,6 +393,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   ctx->off_ptab = off;   off += 10 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 8);
   ctx->off_dt = off;     off += up(64);
   ctx->off_diag = off;   off += up(DG_N * 8);
+  ctx->off_chunk = off;  off += up(GRPIC_MAX_SPECIES * HOST_CHUNKS * 8);
   ctx->max_cap = 1;
   for (int s = 0; s < c.n_species; ++s) {
     SpeciesState &sp = ctx->sp[s];
@@ -745,55 +767,218 @@ extern "C" {
 
 grpic_status grpic_sort(grpic_ctx *ctx, int species) { return sort_species(ctx, species, true); }
 
+}  // extern "C"
+
+namespace {
+
+// The particle state of grpic_step_host: host arrays per species and the counts they hold.
+struct HostIO {
+  const grpic_particles *st;
+  const int64_t *n_in;
+};
+
+int host_chunks(const grpic_ctx *c) { return c->mixed ? 1 : HOST_CHUNKS; }
+int64_t chunk_len(int64_t n, int chunks) { return (n + chunks - 1) / chunks; }
+
+// the state arrays of particles [a, b) of species k between host and device
+grpic_status host_copy(grpic_ctx *ctx, int k, const HostIO &io, int64_t a, int64_t b, bool in,
+                       cudaStream_t st) {
+  const grpic_particles &L = ctx->sp[k].soa[ctx->sp[k].live];
+  for (int q = 0; q < NARR - 4; ++q) {
+    const size_t eb = elem_bytes(ctx, q);
+    char *dev = static_cast<char *>(const_cast<void *>(cslot(L, q))) + a * eb;
+    char *host = static_cast<char *>(const_cast<void *>(cslot(io.st[k], q))) + a * eb;
+    CK(in ? copy(dev, host, (size_t)(b - a) * eb, st) : copy(host, dev, (size_t)(b - a) * eb, st));
+  }
+  return GRPIC_OK;
+}
+
+// FP64 push of particles [a, a + m) of species k, their alive count at n_chunk (device)
+cudaError_t push_range(grpic_ctx *c, int k, int64_t a, int64_t m, const int64_t *n_chunk) {
+  SpeciesState &sp = c->sp[k];
+  SpeciesDevT<double> v = dev_view<double>(sp, sp.live);
+  v.i1 += a; v.i2 += a; v.dx1 += a; v.dx2 += a; v.u1 += a; v.u2 += a; v.u3 += a;
+  v.phi += a; v.w += a; v.tag += a; v.i1p += a; v.i2p += a; v.dx1p += a; v.dx2p += a;
+  v.n = n_chunk;
+  const PushStreams ps{c->stream, c->side, c->ev_fork[k], c->ev_done[k], c->ev_class[k],
+                       nullptr, nullptr, PUSH_ALL};
+  const TileInfo ti{nullptr, c->cfg.tile_r, c->cfg.tile_theta, 0, 0};
+  return launch_push<double>(c->g, c->F64, v, c->tb, sp.gl, ti, m, !sp.massless, c->diag, ps);
+}
+
+// species k of grpic_step_host: range c is pushed once its copies to the device are done and
+// goes back to the host arrays on the d2h stream once its push is done (both streams of the
+// mixed push). A sort in the step reads the whole species, so it waits for every range; the
+// ranges then follow the sorted order, with the alive count of each taken on the device
+// (ranges past the count push nothing and bring back stale values the count excludes).
+grpic_status host_species(grpic_ctx *ctx, int k, const HostIO &io, bool sort_now) {
+  grpic_status s;
+  SpeciesState &sp = ctx->sp[k];
+  const int C = host_chunks(ctx);
+  const int64_t nk = io.n_in[k], len = chunk_len(nk, C);
+  if (sort_now)
+    for (int c = 0; c < C; ++c) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_in[k][c], 0));
+  k_set_i64<<<1, 1, 0, ctx->stream>>>(sp.n_dev, nk);
+  COUNT_LAUNCH(1);
+  CK(cudaGetLastError());
+  sp.n_bound = nk;
+  sp.tiles_valid = false;
+  if (sort_now && (s = sort_species(ctx, k, false))) return s;
+  int64_t *cn = at<int64_t>(ctx, ctx->off_chunk) + k * HOST_CHUNKS;
+  if (C > 1) {
+    k_chunk_counts<<<1, 32, 0, ctx->stream>>>(sp.n_dev, cn, len, C);
+    COUNT_LAUNCH(1);
+    CK(cudaGetLastError());
+  }
+  for (int c = 0; c < C; ++c) {
+    const int64_t a = c * len, b = a + len < nk ? a + len : nk;
+    if (b <= a) break;
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_in[k][c], 0));
+    {
+      PhaseTimer t(ctx, PH_PUSH);
+      if (ctx->mixed) CK(do_push(ctx, ctx->F32, k, true));
+      else if (C == 1) CK(do_push(ctx, ctx->F64, k, true));
+      else CK(push_range(ctx, k, a, b - a, cn + c));
+      ++ctx->push_calls;
+    }
+    CK(cudaEventRecord(ctx->ev_pushed[k][c], ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->d2h, ctx->ev_pushed[k][c], 0));
+    if (ctx->mixed) CK(cudaStreamWaitEvent(ctx->d2h, ctx->ev_done[k], 0));
+    if ((s = host_copy(ctx, k, io, a, b, false, ctx->d2h))) return s;
+  }
+  CK(cudaMemcpyAsync(ctx->host_n + k, sp.n_dev, 8, cudaMemcpyDeviceToHost, ctx->d2h));
+  return GRPIC_OK;
+}
+
+// the copies of every species' ranges to the device, each range's event after its copies
+grpic_status host_in(grpic_ctx *ctx, const HostIO &io) {
+  grpic_status s;
+  for (int k = 0; k < ctx->cfg.n_species; ++k) {
+    if (!ctx->sp[k].loaded) continue;
+    const int C = host_chunks(ctx);
+    const int64_t nk = io.n_in[k], len = chunk_len(nk, C);
+    for (int c = 0; c < C; ++c) {
+      const int64_t a = c * len, b = a + len < nk ? a + len : nk;
+      if (b > a && (s = host_copy(ctx, k, io, a, b, true, ctx->h2d))) return s;
+      CK(cudaEventRecord(ctx->ev_in[k][c], ctx->h2d));
+    }
+  }
+  return GRPIC_OK;
+}
+
+// One full PIC step (Sec. 3.4). With io, every species first waits for its state to arrive
+// from the host, and is sorted and pushed before the next species is touched, so that the
+// copies of one species overlap the work on another.
+grpic_status step_once(grpic_ctx *ctx, const HostIO *io) {
+  grpic_status s;
+  {
+    PhaseTimer t(ctx, PH_PREDICT);
+    if (ctx->mixed) CK(launch_predict<float>(ctx->g, ctx->F32, ctx->stream));
+    else CK(launch_predict<double>(ctx->g, ctx->F64, ctx->stream));
+  }
+  const bool sort_now = ctx->cfg.sort_every > 0 && ctx->step % ctx->cfg.sort_every == 0;
+  if (!io) {
+    if (sort_now)
+      for (int k = 0; k < ctx->cfg.n_species; ++k)
+        if ((s = sort_species(ctx, k, false))) return s;
+    PhaseTimer t(ctx, PH_PUSH);  // fused push + deposit of every species
+    if (ctx->mixed) CK(do_zero_J(ctx, ctx->F32));
+    else CK(do_zero_J(ctx, ctx->F64));
+    // mixed: the guard stages of all species first, so that their FP64 kernels (the longer
+    // chain, on the side stream) run beside all the FP32 kernels instead of trailing the last
+    if (ctx->mixed)
+      for (int k = 0; k < ctx->cfg.n_species; ++k)
+        if (ctx->sp[k].loaded) CK(do_push(ctx, ctx->F32, k, true, PUSH_GUARD));
+    for (int k = 0; k < ctx->cfg.n_species; ++k) {
+      SpeciesState &sp = ctx->sp[k];
+      if (!sp.loaded) continue;
+      if (ctx->mixed) CK(do_push(ctx, ctx->F32, k, true, PUSH_MAIN));
+      else CK(do_push(ctx, ctx->F64, k, true));
+      ++ctx->push_calls;
+    }
+    for (int k = 0; k < ctx->cfg.n_species; ++k)
+      if (ctx->sp[k].loaded) CK(join_push(ctx, k));
+  } else {
+    if (ctx->mixed) CK(do_zero_J(ctx, ctx->F32));
+    else CK(do_zero_J(ctx, ctx->F64));
+    for (int k = 0; k < ctx->cfg.n_species; ++k)
+      if (ctx->sp[k].loaded && (s = host_species(ctx, k, *io, sort_now))) return s;
+    for (int k = 0; k < ctx->cfg.n_species; ++k)
+      if (ctx->sp[k].loaded) CK(join_push(ctx, k));
+  }
+  if (ctx->g.n_f > 0) {
+    PhaseTimer t(ctx, PH_DEPOSIT);  // the current filter, the deposit's last part
+    if (ctx->mixed) CK(launch_filter_currents<float>(ctx->g, ctx->F32, ctx->stream));
+    else CK(launch_filter_currents<double>(ctx->g, ctx->F64, ctx->stream));
+  }
+  {
+    PhaseTimer t(ctx, PH_ADVANCE);
+    if (ctx->mixed) {
+      CK(launch_advance<float>(ctx->g, ctx->F32, ctx->stream));
+      rotate(ctx->F32);
+    } else {
+      CK(launch_advance<double>(ctx->g, ctx->F64, ctx->stream));
+      rotate(ctx->F64);
+    }
+  }
+  ++ctx->step;
+  return GRPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 grpic_status grpic_step(grpic_ctx *ctx, int n_steps) {
   grpic_status s = need_fields(ctx);
   if (s) return s;
   if (n_steps < 0) return fail(ctx, GRPIC_EINVAL, "negative step count");
-  for (int n = 0; n < n_steps; ++n) {
-    {
-      PhaseTimer t(ctx, PH_PREDICT);
-      if (ctx->mixed) CK(launch_predict<float>(ctx->g, ctx->F32, ctx->stream));
-      else CK(launch_predict<double>(ctx->g, ctx->F64, ctx->stream));
-    }
-    if (ctx->cfg.sort_every > 0 && ctx->step % ctx->cfg.sort_every == 0)
-      for (int k = 0; k < ctx->cfg.n_species; ++k)
-        if ((s = sort_species(ctx, k, false))) return s;
-    {
-      PhaseTimer t(ctx, PH_PUSH);  // fused push + deposit of every species
-      if (ctx->mixed) CK(do_zero_J(ctx, ctx->F32));
-      else CK(do_zero_J(ctx, ctx->F64));
-      // mixed: the guard stages of all species first, so that their FP64 kernels (the longer
-      // chain, on the side stream) run beside all the FP32 kernels instead of trailing the last
-      if (ctx->mixed)
-        for (int k = 0; k < ctx->cfg.n_species; ++k)
-          if (ctx->sp[k].loaded) CK(do_push(ctx, ctx->F32, k, true, PUSH_GUARD));
-      for (int k = 0; k < ctx->cfg.n_species; ++k) {
-        SpeciesState &sp = ctx->sp[k];
-        if (!sp.loaded) continue;
-        if (ctx->mixed) CK(do_push(ctx, ctx->F32, k, true, PUSH_MAIN));
-        else CK(do_push(ctx, ctx->F64, k, true));
-        ++ctx->push_calls;
-      }
-      for (int k = 0; k < ctx->cfg.n_species; ++k)
-        if (ctx->sp[k].loaded) CK(join_push(ctx, k));
-    }
-    if (ctx->g.n_f > 0) {
-      PhaseTimer t(ctx, PH_DEPOSIT);  // the current filter, the deposit's last part
-      if (ctx->mixed) CK(launch_filter_currents<float>(ctx->g, ctx->F32, ctx->stream));
-      else CK(launch_filter_currents<double>(ctx->g, ctx->F64, ctx->stream));
-    }
-    {
-      PhaseTimer t(ctx, PH_ADVANCE);
-      if (ctx->mixed) {
-        CK(launch_advance<float>(ctx->g, ctx->F32, ctx->stream));
-        rotate(ctx->F32);
-      } else {
-        CK(launch_advance<double>(ctx->g, ctx->F64, ctx->stream));
-        rotate(ctx->F64);
-      }
-    }
-    ++ctx->step;
+  for (int n = 0; n < n_steps; ++n)
+    if ((s = step_once(ctx, nullptr))) return s;
+  return GRPIC_OK;
+}
+
+grpic_status grpic_step_host(grpic_ctx *ctx, const grpic_particles *state, int64_t *n) {
+  grpic_status s = need_fields(ctx);
+  if (s) return s;
+  if (!state || !n) return fail(ctx, GRPIC_EINVAL, "null state or counts");
+  for (int k = 0; k < ctx->cfg.n_species; ++k) {
+    const SpeciesState &sp = ctx->sp[k];
+    if (n[k] < 0 || n[k] > sp.cap)
+      return fail(ctx, GRPIC_ECAPACITY, "species %d: %lld particles, capacity %lld", k,
+                  (long long)n[k], (long long)sp.cap);
+    if (n[k] > 0 && !sp.loaded)
+      return fail(ctx, GRPIC_ESTATE, "species %d was never loaded or set", k);
+    for (int a = 0; a < NARR - 4 && n[k] > 0; ++a)
+      if (!cslot(state[k], a)) return fail(ctx, GRPIC_EINVAL, "species %d: null array %d", k, a);
   }
+  if (!ctx->h2d) {
+    CK(cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->d2h, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
+    for (int k = 0; k < GRPIC_MAX_SPECIES; ++k)
+      for (int c = 0; c < HOST_CHUNKS; ++c) {
+        CK(cudaEventCreateWithFlags(&ctx->ev_in[k][c], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_pushed[k][c], cudaEventDisableTiming));
+      }
+    void *hn = nullptr;
+    CK(cudaMallocHost(&hn, GRPIC_MAX_SPECIES * sizeof(int64_t)));
+    ctx->host_n = static_cast<int64_t *>(hn);
+  }
+  // the copies in start after everything issued before on the context's stream
+  CK(cudaEventRecord(ctx->ev_start, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->h2d, ctx->ev_start, 0));
+  const HostIO io{state, n};
+  s = host_in(ctx, io);
+  if (!s) s = step_once(ctx, &io);
+  // on an error the copies already issued finish before the caller's arrays are released
+  const cudaError_t e1 = cudaStreamSynchronize(ctx->d2h), e2 = cudaStreamSynchronize(ctx->h2d);
+  if (s) return s;
+  CK(e1);
+  CK(e2);
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < ctx->cfg.n_species; ++k)
+    if (ctx->sp[k].loaded) n[k] = ctx->host_n[k];
   return GRPIC_OK;
 }
 
@@ -946,6 +1131,19 @@ size_t grpic_config_bytes(void) { return sizeof(grpic_config); }
 
 void grpic_destroy(grpic_ctx *ctx) {
   if (!ctx) return;
+  if (ctx->h2d) {
+    cudaStreamSynchronize(ctx->h2d);
+    cudaStreamSynchronize(ctx->d2h);
+    cudaStreamDestroy(ctx->h2d);
+    cudaStreamDestroy(ctx->d2h);
+    cudaEventDestroy(ctx->ev_start);
+    for (int k = 0; k < GRPIC_MAX_SPECIES; ++k)
+      for (int c = 0; c < HOST_CHUNKS; ++c) {
+        cudaEventDestroy(ctx->ev_in[k][c]);
+        cudaEventDestroy(ctx->ev_pushed[k][c]);
+      }
+    cudaFreeHost(ctx->host_n);
+  }
   for (int ph = 0; ph < PH_N; ++ph)
     for (auto &e : ctx->ev[ph]) {
       cudaEventDestroy(e.first);

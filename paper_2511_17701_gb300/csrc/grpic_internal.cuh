@@ -346,9 +346,9 @@ struct TileInfo {
   int tr, tt, ntr, n_tiles;
 };
 
-// Streams of one push: the FP64-pipe-bound guard kernels run on `side`, forked from
-// `main` after the classification by `fork`; `done` is recorded on `side` after them and
-// the caller makes `main` wait on it before anything reads the currents or the particles.
+// Streams of one push: the classification and the FP64-pipe-bound guard kernels run on
+// `side`, forked from `main` by `fork`; `done` is recorded on `side` after them and the
+// caller makes `main` wait on it before anything reads the currents or the particles.
 // which part of a push to launch: the mixed path's guard stage (classify, then the FP64
 // guard kernels, all on `side`) and its main FP32 kernel (on `main`, after the classify) can
 // be issued separately, so that the guard stages of all species start before the first FP32
