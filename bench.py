@@ -46,11 +46,12 @@ FP64_BYTES_PER_PARTICLE_STEP = 65 + 81
 MIXED_BYTES_PER_PARTICLE_STEP = 37 + 48
 # FP64 pipe operations (DFMA + DMUL + DADD thread instructions) per particle-step of
 # k_push<deposit> on the wald512 workload, counted by ncu, and as flops (2 DFMA + DMUL +
-# DADD): with the implicit iterations refined from an FP32 predictor (iter_tol > 0):
-# 331 + 383 + 109 = 823 (1155 flop); stopped at an exact repeat (iter_tol = 0): 476 + 548 +
-# 120 = 1144 (1620 flop). The FP64 pipe issues 2 such operations per clock per SM.
-FP64_PIPE_OPS_PER_PARTICLE_STEP = {True: 823, False: 1144}
-FP64_FLOP_PER_PARTICLE_STEP = {True: 1155, False: 1620}
+# DADD): with the implicit iterations refined from an FP32 predictor and one Newton step on
+# its FP32 Jacobian (iter_tol > 0): 303 + 354 + 109 = 767 (1070 flop); stopped at an exact
+# repeat (iter_tol = 0): 476 + 548 + 120 = 1144 (1620 flop). The FP64 pipe issues 2 such
+# operations per clock per SM.
+FP64_PIPE_OPS_PER_PARTICLE_STEP = {True: 767, False: 1144}
+FP64_FLOP_PER_PARTICLE_STEP = {True: 1070, False: 1620}
 SMS, MAX_SM_GHZ = 152, 2.07
 FP64_PIPE_PEAK_GOPS = 2 * SMS * MAX_SM_GHZ  # 629 G operations/s
 # Warp instructions issued per particle by k_push32<deposit> on the wald512 workload (ncu:

@@ -129,11 +129,12 @@ typedef struct {
                            measures faster on GB300 for this pusher                            */
   double iter_tol;      /* the implicit pushes (steps 6 and 10 of Sec. 3.1): 0 (default) = the
                            stop rule of full_iterations; > 0 = an FP32 predictor iterates each
-                           to an exact FP32 repeat, then FP64 iterations start from it and stop
-                           once the update is at most iter_tol max(1, |value|) (at most n_iter
-                           of them): the FP64 fixed point to about rho iter_tol (rho < 1 the
-                           contraction of the iteration), in fewer FP64 operations. Must be
-                           below 1e-6                                                          */
+                           to an exact FP32 repeat and gives the map's Jacobian there; one FP64
+                           evaluation at that point, one Newton step, then FP64 iterations
+                           until the update is at most iter_tol max(1, |value|) (at most n_iter
+                           evaluations in all): the FP64 fixed point to about rho iter_tol
+                           (rho < 1 the contraction of the iteration), in fewer FP64
+                           operations. Must be below 1e-6                                      */
   double r0, h0;        /* quasi-spherical Kerr-Schild grid (App. A): r = r0 + exp(xi), xi
                            uniform in x1 (r0 < r_min); theta = eta + 2 h0 eta (pi - 2 eta)
                            (pi - eta) / pi^2, eta uniform in x2 (-1/2 < h0 < 1; h0 > 0 puts

@@ -169,24 +169,47 @@ __device__ __forceinline__ void deposit64(const GridP &g, const FieldPtrsT<T> &F
 }
 
 // Refined form of the two implicit substeps (iter_tol > 0): an FP32 predictor iterates the
-// same map to an exact FP32 repeat (metric from the FP32 cell tables), then FP64 iterations
-// start from it and stop once the update is at most iter_tol max(1, |value|); the result is
-// the FP64 fixed point to about rho iter_tol, rho the contraction of the map, whatever the
-// start (mixed-precision iterative refinement: the predictor only saves FP64 iterations).
+// same map to an exact FP32 repeat (metric from the FP32 cell tables) and gives the map's
+// Jacobian J there (FP32, analytic). The FP64 map is evaluated at the predictor's point; one
+// Newton step with J on that residual lands within about |J error| times the predictor's
+// rounding of the FP64 fixed point, and a second FP64 evaluation there verifies it: the
+// result is taken once an FP64 update is at most iter_tol max(1, |value|), with plain FP64
+// iterations after the second evaluation while it is not (at most n_iter evaluations in
+// all). The result is the FP64 fixed point to about rho iter_tol, rho < 1 the contraction,
+// whatever the start: J and the predictor only save FP64 work (mixed-precision refinement).
 __device__ __forceinline__ bool converged(double n, double t, double tol) {
   return fabs(n - t) <= tol * fmax(1.0, fabs(n));
 }
+// the largest eigenvalue modulus of a 2 x 2 matrix: the asymptotic contraction of a map
+// with that Jacobian
+__device__ __forceinline__ float spectral_radius(const float J[2][2]) {
+  const float tr = J[0][0] + J[1][1], det = fmaf(J[0][0], J[1][1], -J[0][1] * J[1][0]);
+  const float disc = fmaf(tr, tr, -4.0f * det);
+  return disc >= 0.0f ? 0.5f * (fabsf(tr) + sqrtf(disc)) : sqrtf(fmaxf(det, 0.0f));
+}
 // Whether the method's n_iter iterations from its start come within a tenth of tol of the
 // fixed point, so that the refined result stands for the method's n_iter result: d1 is the
-// method's first update (from the FP32 predictor's first step), rho = D2 / D1 the
-// contraction measured by the first two FP64 updates, the remainder d1 rho^n_iter.
-__device__ __forceinline__ bool method_converges(double d1, double D1, double D2, int n_iter,
-                                                 double tol, double scale) {
-  if (!(D1 > 1e-14 * scale)) return true;  // the predictor already sat on the fixed point
-  const float rho = (float)(D2 / D1);  // an estimate: FP32 (and the XU pipe) is enough
+// method's first update (from the FP32 predictor's first step), rho the contraction (the
+// spectral radius of J), the remainder d1 rho^n_iter.
+__device__ __forceinline__ bool method_converges(float d1, float rho, int n_iter, double tol,
+                                                 double scale) {
   if (!(rho < 0.5f)) return false;
   if (!(rho > 0.0f)) return true;
-  return (float)d1 * exp2f((float)n_iter * log2f(rho)) <= (float)(0.1 * tol * scale);
+  return d1 * exp2f((float)n_iter * log2f(rho)) <= (float)(0.1 * tol * scale);
+}
+// t + (I - J)^{-1} (n - t): the Newton step of t = G(t) from the residual n - t; the plain
+// iteration step (n itself) when the result is not finite
+__device__ __forceinline__ void newton_step(const float J[2][2], double t0, double t1, double n0,
+                                            double n1, double &s0, double &s1) {
+  const float a = 1.0f - J[0][0], d = 1.0f - J[1][1];
+  const float idet = 1.0f / fmaf(a, d, -J[0][1] * J[1][0]);
+  const double r0 = n0 - t0, r1 = n1 - t1;
+  s0 = t0 + fma((double)(idet * d), r0, (double)(idet * J[0][1]) * r1);
+  s1 = t1 + fma((double)(idet * J[1][0]), r0, (double)(idet * a) * r1);
+  if (!(isfinite(s0) && isfinite(s1))) {
+    s0 = n0;
+    s1 = n1;
+  }
 }
 
 template <bool Q = true>
@@ -212,29 +235,55 @@ __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTable
   }
   const GeoMap<double> m(g, L, u, m2);
   double t0 = u[0], t1 = u[1];
+  float J[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   if (isfinite(p0) && isfinite(p1)) {
     t0 = p0;
     t1 = p1;
+    mf.jacobian(p0, p1, J);
   }
-  double D1 = 0.0, D2 = 0.0;
-  for (int it = 0; it < g.n_iter; ++it) {
-    double n0, n1;
-    m.apply(t0, t1, n0, n1);
-    const double d = fmax(fabs(n0 - t0), fabs(n1 - t1));
-    if (it == 0) D1 = d;
-    else if (it == 1) D2 = d;
-    const bool conv = converged(n0, t0, g.iter_tol) && converged(n1, t1, g.iter_tol);
-    t0 = n0;
-    t1 = n1;
-    if (conv && it >= 1) break;
+  double n0, n1, s0, s1;
+  m.apply(t0, t1, n0, n1);
+  newton_step(J, t0, t1, n0, n1, s0, s1);
+  bool conv = false;
+  for (int it = 1; it < g.n_iter && !conv; ++it) {
+    m.apply(s0, s1, n0, n1);
+    conv = converged(n0, s0, g.iter_tol) && converged(n1, s1, g.iter_tol);
+    s0 = n0;
+    s1 = n1;
   }
-  const double scale = fmax(1.0, fmax(fabs(t0), fabs(t1)));
-  if (!method_converges(d1, D1, D2, g.n_iter, g.iter_tol, scale)) {
+  const double scale = fmax(1.0, fmax(fabs(s0), fabs(s1)));
+  if (!method_converges(d1, spectral_radius(J), g.n_iter, g.iter_tol, scale)) {
     geodesic_momentum(g, L, u, m2);  // the method's n_iter iterations from u
     return;
   }
-  u[0] = t0;
-  u[1] = t1;
+  u[0] = s0;
+  u[1] = s1;
+}
+
+// dt/2 times the derivative of the coordinate velocity V of Eq. (discretized-geodesic-x) at
+// the point of L for the momentum u: the Jacobian of the map t -> x^n + dt V((x^n + t)/2).
+// V^1 = (alpha/gamma) (h^11 u_1 + h^13 u_3) - beta^1, V^2 = (alpha/gamma) h^22 u_2, with
+// alpha/gamma = (q / alpha^2)^(-1/2), q = m2 + h^ij u_i u_j.
+__device__ __forceinline__ void coord_jacobian(const GridP &g, const Local<float> &L,
+                                               const float u[3], float m2, float J[2][2]) {
+  const Geo<float> &o = L.G;
+  const float uu = 2.0f * u[0] * u[2], u00 = u[0] * u[0], u11 = u[1] * u[1], u22 = u[2] * u[2];
+  const float q = fmaf(o.H11, u00, fmaf(o.H22, u11, fmaf(o.H33, u22, fmaf(o.H13, uu, m2))));
+  const float ag = rsqrtf(o.opz * q);
+  const float w1 = fmaf(o.H11, u[0], o.H13 * u[2]), w2 = o.H22 * u[1];
+  const float ia = L.alpha * o.opz;           // 1 / alpha
+  const float hq = 0.5f * ag * ag * o.opz;    // 1 / (2 q)
+  const float hdt = 0.5f * g.f_dt;
+  const float dH11[2] = {L.d1H11, L.d2H11}, dH22[2] = {L.d1H22, L.d2H22};
+  const float dH33[2] = {L.d1H33, L.d2H33}, dH13[2] = {L.d1H13, L.d2H13};
+  const float dal[2] = {L.d1alpha, L.d2alpha}, dbe[2] = {L.d1beta1, L.d2beta1};
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float dq = fmaf(dH11[j], u00, fmaf(dH22[j], u11, fmaf(dH33[j], u22, dH13[j] * uu)));
+    const float dag = ag * fmaf(dal[j], ia, -dq * hq);
+    J[0][j] = hdt * (fmaf(dag, w1, ag * fmaf(dH11[j], u[0], dH13[j] * u[2])) - dbe[j]);
+    J[1][j] = hdt * fmaf(dag, w2, ag * dH22[j] * u[1]);
+  }
 }
 
 // The coordinate substep, Eq. (discretized-geodesic-x), as the method iterates it: metric at
@@ -271,9 +320,29 @@ __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const
   }
 }
 
+// One FP64 evaluation of the coordinate map at the iterate (t1, t2): the new offsets (n1, n2)
+// and dphi/dt (v3) at its midpoint x_bar = i + (dx + t)/2
+template <bool Q = true>
+__device__ __forceinline__ void coord_map64(const GridP &g, const Base &b, int i1, int i2,
+                                            double dx1, double dx2, const double u[3],
+                                            double m2, double t1, double t2, double &n1,
+                                            double &n2, double &v3) {
+  Pt<double> p;
+  local_rsc<Q>(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
+               __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), p);
+  Geo<double> o;
+  geo_from_rsc<Q>(g, p, o);
+  const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
+                   fma(o.H33 * u[2], u[2], fma(o.H13, 2.0 * u[0] * u[2], m2))));
+  const double ag = rsqrt(o.opz * q);
+  n1 = fma(g.dt, fma(ag, fma(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
+  n2 = fma(g.dt, ag * o.H22 * u[1], dx2);
+  v3 = ag * fma(o.H13, u[0], o.H33 * u[2]);  // Eq. (discretized-geodesic-x-phi) at x_bar
+}
+
 // the coordinate substep's refined iterations; t1, t2: the new offsets from cell (i1, i2)
-// v3 (dphi/dt) comes back from the metric of the last FP64 iteration, whose midpoint is within
-// iter_tol of the final one (or is NaN when the method's iteration ran instead).
+// v3 (dphi/dt) comes back from the metric of the last FP64 evaluation, whose midpoint is
+// within iter_tol of the final one (or is NaN when the method's iteration ran instead).
 template <bool Q = true>
 __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &tb, const Base &b,
                                               const Local<double> &L, int i1, int i2,
@@ -301,34 +370,30 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
   }
   t1 = dx1;
   t2 = dx2;
+  float J[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   if (isfinite(p1) && isfinite(p2) && fabsf(p1) < 4.0f && fabsf(p2) < 4.0f) {
     t1 = p1;
     t2 = p2;
+    Pt<float> pf;  // the Jacobian at the predictor's midpoint
+    rsc32<Q>(g, tb, i1, i2, 0.5f * (a1 + p1), 0.5f * (a2 + p2), pf);
+    Local<float> Lf;
+    local_full<Q>(g, pf, Lf);
+    coord_jacobian(g, Lf, uf, (float)m2, J);
   }
-  const double uu0 = 2.0 * u[0] * u[2];
-  double D1 = 0.0, D2 = 0.0;
-  for (int it = 0; it < g.n_iter; ++it) {
-    Pt<double> p;
-    local_rsc<Q>(g, b, __dadd_rn((double)i1, 0.5 * __dadd_rn(dx1, t1)),
-                 __dadd_rn((double)i2, 0.5 * __dadd_rn(dx2, t2)), p);
-    Geo<double> o;
-    geo_from_rsc<Q>(g, p, o);
-    const double q = fma(o.H11 * u[0], u[0], fma(o.H22 * u[1], u[1],
-                     fma(o.H33 * u[2], u[2], fma(o.H13, uu0, m2))));
-    const double ag = rsqrt(o.opz * q);
-    const double n1 = fma(g.dt, fma(ag, fma(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
-    const double n2 = fma(g.dt, ag * o.H22 * u[1], dx2);
-    const double d = fmax(fabs(n1 - t1), fabs(n2 - t2));
-    if (it == 0) D1 = d;
-    else if (it == 1) D2 = d;
-    const bool conv = converged(n1, t1, g.iter_tol) && converged(n2, t2, g.iter_tol);
-    t1 = n1;
-    t2 = n2;
-    v3 = ag * fma(o.H13, u[0], o.H33 * u[2]);  // Eq. (discretized-geodesic-x-phi) at x_bar
-    if (conv && it >= 1) break;
+  double n1, n2, s1, s2;
+  coord_map64<Q>(g, b, i1, i2, dx1, dx2, u, m2, t1, t2, n1, n2, v3);
+  newton_step(J, t1, t2, n1, n2, s1, s2);
+  bool conv = false;
+  for (int it = 1; it < g.n_iter && !conv; ++it) {
+    coord_map64<Q>(g, b, i1, i2, dx1, dx2, u, m2, s1, s2, n1, n2, v3);
+    conv = converged(n1, s1, g.iter_tol) && converged(n2, s2, g.iter_tol);
+    s1 = n1;
+    s2 = n2;
   }
+  t1 = s1;
+  t2 = s2;
   const double scale = fmax(1.0, fmax(fabs(t1), fabs(t2)));
-  if (!method_converges(d1, D1, D2, g.n_iter, g.iter_tol, scale)) {
+  if (!method_converges(d1, spectral_radius(J), g.n_iter, g.iter_tol, scale)) {
     coord_exact<Q>(g, b, L, i1, i2, dx1, dx2, u, m2, t1, t2);  // the method's iterations
     v3 = NAN;
   }

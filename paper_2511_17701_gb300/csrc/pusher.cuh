@@ -222,6 +222,25 @@ struct GeoMap {
     n0 = fma_(b0, D1b, fma_(-gb, D1a, fma_(-ha, k1, u0)));
     n1 = fma_(b0, D2b, fma_(-gb, D2a, fma_(-ha, k2, u1)));
   }
+  // J[i][j] = d n_i / d t_j of apply at t (the map depends on t through b = (t + u)/2)
+  __device__ __forceinline__ void jacobian(R t0, R t1, R J[2][2]) const {
+    const R b0 = fma_((R)0.5, t0, hu0), b1 = fma_((R)0.5, t1, hu1);
+    const R b1s = b1 * b1;
+    const R q = fma_(b0, fma_(H11, b0, c1), fma_(H22, b1s, c0));
+    const R ig = rsqrt_(q);
+    const R ha = hdt * ig;
+    const R k1 = fma_(b0, fma_(d1H11, b0, e2), fma_(d1H22, b1s, e1));
+    const R k2 = fma_(b0, fma_(d2H11, b0, f2), fma_(d2H22, b1s, f1));
+    const R q0 = fma_((R)2 * H11, b0, c1), q1 = (R)2 * H22 * b1;  // dq/db
+    const R hg = (R)0.5 * ig, hh = (R)-0.5 * ha * ig * ig;       // d gamma/dq, d ha/dq
+    const R g0 = hg * q0, g1 = hg * q1, a0 = hh * q0, a1 = hh * q1;
+    const R k10 = fma_((R)2 * d1H11, b0, e2), k11 = (R)2 * d1H22 * b1;
+    const R k20 = fma_((R)2 * d2H11, b0, f2), k21 = (R)2 * d2H22 * b1;
+    J[0][0] = (R)0.5 * (D1b - g0 * D1a - a0 * k1 - ha * k10);
+    J[0][1] = (R)0.5 * (-g1 * D1a - a1 * k1 - ha * k11);
+    J[1][0] = (R)0.5 * (D2b - g0 * D2a - a0 * k2 - ha * k20);
+    J[1][1] = (R)0.5 * (-g1 * D2a - a1 * k2 - ha * k21);
+  }
 };
 
 // The geodesic substep: n_iter applications of G from t = u.
