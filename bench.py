@@ -58,6 +58,13 @@ FP64_PIPE_PEAK_GOPS = 2 * SMS * MAX_SM_GHZ  # 629 G operations/s
 # 394.9 M over 8.39 M particles with 12 resident blocks per SM, spills included); an SM
 # issues at most 4 warp instructions per clock.
 MIXED_WARP_INST_PER_PARTICLE = 47.1
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per particle of the dominant
+# kernels on the wald512 workload, from one ncu capture each: k_push<deposit> at 4 particles
+# per cell and species (87.5 + 32.5 MB over 1,048,576 particles; traffic grows with the
+# particles, so a full launch is this times its particles), k_push32<deposit> at the full
+# size (314.5 + 592.3 MB over 8,388,608 particles).
+TRAFFIC_BYTES_PER_PARTICLE = {"fp64": (87.5e6 + 32.5e6) / 1048576,
+                              "mixed": (314.5e6 + 592.3e6) / 8388608}
 ISSUE_PEAK_GINST = 4 * SMS * MAX_SM_GHZ  # 1259 G warp instructions/s
 
 
@@ -354,6 +361,11 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
                     "kernel": "k_push32<deposit> (FP32 push + warp-reduced deposit; the "
                               "guard-zone kernels run beside it on a second stream)"}
     roofline["avg_launch_ms"] = kernel_ms
+    if (workload == "wald512" and args.iter_tol == 1e-12 and not photons and not extra
+            and not args.ppc):
+        roofline["traffic"] = TRAFFIC_BYTES_PER_PARTICLE[precision] * parts_per_launch
+        roofline["traffic_source"] = ("ncu dram bytes per particle of the same kernel on this "
+                                      "workload, times the particles of one launch")
     hbm = {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak or 6800.0,
            "frac": hbm_achieved / (hbm_peak or 6800.0),
            "peak_source": "measured" if hbm_peak else "fallback",
