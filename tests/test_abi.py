@@ -101,3 +101,16 @@ def test_create_rejects_bad_species():
     assert create(good_cfg(), caps=(1,) * 9)[0] == B.EINVAL
     assert create(good_cfg(), caps=(-1,))[0] == B.EINVAL
     assert create(good_cfg(), caps=(1 << 31,))[0] == B.EINVAL
+
+
+def test_host_streamed_step_needs_a_ready_context():
+    """grpic_step_host checks its prerequisites on the host before any CUDA work: an unbound
+    context (no fields) is refused with GRPIC_ESTATE and nothing is touched."""
+    st, ctx = create(good_cfg())
+    assert st == B.OK
+    n = (C.c_int64 * 2)(10, 10)
+    states = (B.Particles * 2)()
+    assert B.lib().grpic_step_host(ctx, states, n) == B.ESTATE
+    assert B.lib().grpic_step_host(ctx, None, None) == B.ESTATE
+    assert list(n) == [10, 10]
+    B.lib().grpic_destroy(ctx)
