@@ -933,6 +933,17 @@ constexpr int CL_U = 8;
 #ifndef GRPIC_AXIS_BLOCKS_PER_SM
 #define GRPIC_AXIS_BLOCKS_PER_SM 4
 #endif
+// their register caps as resident one-warp blocks per SM (65536 / (32 x this) registers):
+// the registers they hold while resident are taken from the concurrent FP32 kernel. The
+// zone-1 kernel capped at 80 (a few spills) left the FP32 kernel enough to make the mixed
+// step 2% faster on GB300 than uncapped (119) or at 64; capping the zone-2 kernel cost more
+// than it gave.
+#ifndef GRPIC_GUARD_MIN_BLOCKS
+#define GRPIC_GUARD_MIN_BLOCKS 24
+#endif
+#ifndef GRPIC_AXIS_MIN_BLOCKS
+#define GRPIC_AXIS_MIN_BLOCKS 1
+#endif
 __global__ void __launch_bounds__(TPB) k_classify(GridP g, SpeciesDevT<float> s, PushTables tb,
                                                   GuardList gl) {
   const int64_t n = *s.n;
@@ -1077,7 +1088,7 @@ size_t tiled_smem_bytes(const TileInfo &ti) {
 // Mixed path, guard kernels (side stream): step 1 and the routine of the listed particles,
 // zone 1 with the metric in FP64, zone 2 with the FP64 routine.
 template <bool DEPOSIT, bool Q>
-__global__ void __launch_bounds__(TPB) k_push_guard(GridP g, FieldPtrsT<float> F,
+__global__ void __launch_bounds__(32, GRPIC_GUARD_MIN_BLOCKS) k_push_guard(GridP g, FieldPtrsT<float> F,
                                                     SpeciesDevT<float> s, PushTables tb,
                                                     GuardList gl, unsigned long long *diag) {
   const int64_t n = (int64_t)gl.count[0];
@@ -1096,7 +1107,7 @@ __global__ void __launch_bounds__(TPB) k_push_guard(GridP g, FieldPtrsT<float> F
 }
 
 template <bool DEPOSIT, bool Q>
-__global__ void __launch_bounds__(TPB) k_push_axis(GridP g, FieldPtrsT<float> F,
+__global__ void __launch_bounds__(32, GRPIC_AXIS_MIN_BLOCKS) k_push_axis(GridP g, FieldPtrsT<float> F,
                                                    SpeciesDevT<float> s, PushTables tb,
                                                    GuardList gl, unsigned long long *diag) {
   const int64_t n = (int64_t)gl.count[1];
