@@ -55,16 +55,16 @@ FP64_FLOP_PER_PARTICLE_STEP = {True: 1070, False: 1620}
 SMS, MAX_SM_GHZ = 152, 2.07
 FP64_PIPE_PEAK_GOPS = 2 * SMS * MAX_SM_GHZ  # 629 G operations/s
 # Warp instructions issued per particle by k_push32<deposit> on the wald512 workload (ncu:
-# 394.9 M over 8.39 M particles with 12 resident blocks per SM, spills included); an SM
+# 384.9 M over 8.39 M particles with 12 resident blocks per SM, spills included); an SM
 # issues at most 4 warp instructions per clock.
-MIXED_WARP_INST_PER_PARTICLE = 47.1
+MIXED_WARP_INST_PER_PARTICLE = 45.9
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per particle of the dominant
 # kernels on the wald512 workload, from one ncu capture each: k_push<deposit> at 4 particles
 # per cell and species (87.5 + 32.5 MB over 1,048,576 particles; traffic grows with the
 # particles, so a full launch is this times its particles), k_push32<deposit> at the full
-# size (314.5 + 592.3 MB over 8,388,608 particles).
+# size (314.6 + 615.9 MB over 8,388,608 particles).
 TRAFFIC_BYTES_PER_PARTICLE = {"fp64": (87.5e6 + 32.5e6) / 1048576,
-                              "mixed": (314.5e6 + 592.3e6) / 8388608}
+                              "mixed": (314.6e6 + 615.9e6) / 8388608}
 ISSUE_PEAK_GINST = 4 * SMS * MAX_SM_GHZ  # 1259 G warp instructions/s
 
 

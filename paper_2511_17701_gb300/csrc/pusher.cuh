@@ -12,6 +12,12 @@ __device__ __forceinline__ double fma_(double a, double b, double c) { return fm
 __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
 __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
+// a / b: exact in FP64 (and for the adjoint's dual numbers); CUDA's fast FP32 division
+// (within 2 ulp) in FP32, whose arithmetic carries ~1e-7 relative errors anyway
+template <typename R>
+__device__ __forceinline__ R div_(R a, R b) { return a / b; }
+template <>
+__device__ __forceinline__ float div_<float>(float a, float b) { return __fdividef(a, b); }
 
 // =================================================================================
 // Metric pieces shared by both precisions (App. A, quasi-spherical Kerr-Schild, mass M
@@ -44,11 +50,11 @@ __device__ __forceinline__ void geo_from_rsc(const GridP &g, const Pt<R> &p, Geo
   R iQ, igg;
   if (Q && g.qks) {
     const R g2 = p.gg * p.gg;
-    const R iX = (R)1 / (u * s2 * g2);  // the one division
+    const R iX = div_((R)1, u * s2 * g2);  // the one division
     iQ = iX * g2;
     igg = iX * u * s2;
   } else {
-    iQ = (R)1 / (u * s2);               // the one division
+    iQ = div_((R)1, u * s2);               // the one division
     igg = p.igg;
   }
   const R iu = iQ * s2;                 // 1 / (Sigma S2 f)
@@ -85,11 +91,11 @@ __device__ __forceinline__ void local_full(const GridP &g, const Pt<R> &p, Local
   R iQ, igg;
   if (Q && g.qks) {
     const R g2 = gg * gg;
-    const R iX = (R)1 / (u * s2 * g2);
+    const R iX = div_((R)1, u * s2 * g2);
     iQ = iX * g2;
     igg = iX * u * s2;
   } else {
-    iQ = (R)1 / (u * s2);
+    iQ = div_((R)1, u * s2);
     igg = p.igg;
   }
   const R iu = iQ * s2;
@@ -165,7 +171,7 @@ __device__ __forceinline__ void boris(R u[3], const R D[3], const R B[3], R hq) 
   const R m0 = fma_(e, D[0], u[0]), m1 = fma_(e, D[1], u[1]), m2 = fma_(e, D[2], u[2]);
   const R ig = rsqrt_(fma_(m0, m0, fma_(m1, m1, fma_(m2, m2, (R)1))));
   const R t0 = e * B[0] * ig, t1 = e * B[1] * ig, t2 = e * B[2] * ig;
-  const R sf = (R)2 / fma_(t0, t0, fma_(t1, t1, fma_(t2, t2, (R)1)));
+  const R sf = div_((R)2, fma_(t0, t0, fma_(t1, t1, fma_(t2, t2, (R)1))));
   const R p0 = m0 + (m1 * t2 - m2 * t1);
   const R p1 = m1 + (m2 * t0 - m0 * t2);
   const R p2 = m2 + (m0 * t1 - m1 * t0);
