@@ -758,6 +758,119 @@ def run_adjoint(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def bz_diagnostics(sim, cfg, radii):
+    """The closed-form quantities of Sec. 4.5 from one snapshot of the em planes: per radius,
+    the field-line angular velocity Omega = -E_theta / (sqrt(h) B^r) averaged over theta in
+    [pi/6, 5 pi/6] with weight sin^2(theta) (BZ: omega_h / 2 at every latitude to O(a^2)), the
+    amplitude of H_phi fitted to sin^2(theta) by least squares (BZ: -B0 a / 8), and the
+    Poynting flux L = 2 pi int P^r sqrt(h) dtheta = (1/2) int (E_theta H_phi - E_phi H_theta)
+    dtheta. In the code coordinates E_theta dtheta = E_2 dx2 and H_phi = H_3, so L is half the
+    sum over rows of E_2 H_3 - E_3 H_2; E_2, B^1 at (i, j + 1/2), H_3 at (i + 1/2, j + 1/2)
+    and H_2 at (i + 1/2, j) are averaged to column i. sqrt(h) is the Kerr-Schild volume
+    element sin(theta) Sigma sqrt(1 + 2 r / Sigma) times dr/dx1 dtheta/dx2."""
+    F = sim.planes()
+    E, H = sim.aux_fields()
+    a, nr, nt, G = cfg["a"], cfg["n_r"], cfg["n_theta"], 2
+    dxi = math.log(cfg["r_max"] / cfg["r_min"]) / nr
+    dth = math.pi / nt
+    thc = (np.arange(nt) + 0.5) * dth
+    out = {}
+    for rr in radii:
+        i = int(round(math.log(rr / cfg["r_min"]) / dxi))
+        r = cfg["r_min"] * math.exp(i * dxi)
+        sig = r * r + a * a * np.cos(thc) ** 2
+        sq = dxi * r * dth * sig * np.sin(thc) * np.sqrt(1.0 + 2.0 * r / sig)
+        om = -E[1][G:G + nt, G + i] / (sq * F[0][G:G + nt, G + i])
+        mid = (thc > math.pi / 6) & (thc < 5 * math.pi / 6)
+        w = np.sin(thc[mid]) ** 2
+        h3 = 0.5 * (H[2][G:G + nt, G + i - 1] + H[2][G:G + nt, G + i])
+        s2 = np.sin(thc) ** 2
+        h2 = 0.5 * (H[1][G:G + nt + 1, G + i - 1] + H[1][G:G + nt + 1, G + i])
+        wn = np.ones(nt + 1)
+        wn[0] = wn[-1] = 0.5
+        out[rr] = {"omega": float(np.sum(w * om[mid]) / np.sum(w)),
+                   "hphi_amp": float(np.sum(h3 * s2) / np.sum(s2 * s2)),
+                   "L": float(0.5 * (np.sum(E[1][G:G + nt, G + i] * h3) -
+                                     np.sum(wn * E[2][G:G + nt + 1, G + i] * h2)))}
+    return out
+
+
+def run_bz_physics(args, local):
+    """The BZ monopole test of Sec. 4.5: the monopole A_phi = -B0 cos(theta) on the Kerr (a =
+    0.2) log-r grid r in [1, 10] with its absorbing layer, a thin e+- plasma (density ~ r^-2)
+    and pair injection where sigma > sigma_th = 2000 after every step, run to args.bz_time
+    r_g; then Omega / omega_h (BZ: 1/2), H_phi / (-B0 a / 8) (BZ: 1) and L / L_BZ, L_BZ =
+    B0^2 omega_h^2 / 6 (BZ: 1), each averaged over snapshots every r_g in the last third of
+    the run. omega_h = a / (2 r_h) = -g_03 / g_33 at the horizon (M = 1)."""
+    import torch
+
+    from paper_2511_17701_gb300 import FIELD_MONOPOLE, Sim
+
+    device = torch.device("cuda", local)
+    n_g = args.bz_n
+    prec = args.bz_precision
+    cfg = W.grid_config("bz1024", n_r=n_g, n_theta=n_g, ppc=2, sort_every=args.sort_every,
+                        tile_r=args.tile, tile_theta=args.tile, precision=prec,
+                        iter_tol=args.iter_tol if prec == "fp64" else 0.0)
+    a, B0 = cfg["a"], cfg["B0"]
+    rh = 1.0 + math.sqrt(1.0 - a * a)
+    wh = a / (2.0 * rh)
+    LBZ = B0 * B0 * wh * wh / 6.0
+    pl = W.pair_plasma(cfg)
+    n = pl["pos"]["i1"].size
+    cap = n + 48 * n_g * n_g
+    sim = Sim(cfg, [cap, cap], device=device)
+    sim.init_metric()
+    sim.init_fields(FIELD_MONOPOLE, B0)
+    for sp in range(2):
+        sim.load_particles(sp, pl["pos"], pl["uhat"][sp], pl["w0"], pl["qm"][sp], pl["qc"][sp],
+                           pl["density_power"])
+    del pl
+    pool = torch.tensor(W.injection_pool(cfg, 1 << 22, seed=cfg["seed"] + 7),
+                        dtype=torch.float64, device=device)
+    radii = (2.0, 3.0, 5.0, 8.0)
+    dt = sim.dt
+    t0 = time.perf_counter()
+    sim.inject(cfg["sigma0"], cfg["sigma_th"], B0, pool, pool_offset=0)
+    t, snaps = 0.0, []
+    n_mark = int(math.floor(args.bz_time))
+    for mark in range(1, n_mark + 1):
+        k = int(round((mark - t) / dt))
+        for _ in range(k):
+            sim.step(1)
+            sim.inject(cfg["sigma0"], cfg["sigma_th"], B0, pool)
+        t += k * dt
+        if mark > 2 * n_mark / 3:
+            snaps.append(bz_diagnostics(sim, cfg, radii))
+    sim.sync()
+    wall = time.perf_counter() - t0
+    d = sim.diagnostics()
+
+    def avg(key, norm):
+        return {str(rr): float(np.mean([sn[rr][key] for sn in snaps]) / norm) for rr in radii}
+
+    def spread(key, norm):
+        return {str(rr): float(np.std([sn[rr][key] for sn in snaps]) / abs(norm)) for rr in radii}
+
+    line = {"metric": "BZ monopole closed-form checks (Sec. 4.5)", "n_gpus": 1,
+            "precision": prec, "data": "synthetic (seeded workload generator)",
+            "config": {"workload": "bz monopole, Kerr a=%.1f, %dx%d log-r grid, r in [1, 10], "
+                                   "absorbing layer from r=9, rho0=5e-5, d0=2.5e-3, sigma0=2500, "
+                                   "sigma_th=2000, initial e+- 2 per cell per species, density "
+                                   "~ r^-2" % (a, n_g, n_g),
+                       "t_end_rg": t, "dt": dt, "average_over_rg": [t - len(snaps), t],
+                       "omega_h": wh, "L_BZ": LBZ},
+            "omega_over_omega_h": avg("omega", wh), "omega_spread": spread("omega", wh),
+            "hphi_over_bz": avg("hphi_amp", -B0 * a / 8.0),
+            "hphi_spread": spread("hphi_amp", -B0 * a / 8.0),
+            "L_over_LBZ": avg("L", LBZ), "L_spread": spread("L", LBZ),
+            "expected": {"omega_over_omega_h": 0.5, "hphi_over_bz": 1.0, "L_over_LBZ": 1.0},
+            "particles": [sim.count(0), sim.count(1)], "injected": d["injected"],
+            "inject_dropped": d["inject_dropped"], "nonfinite": d["nonfinite"],
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -797,6 +910,11 @@ def main():
     ap.add_argument("--tiled-push", action="store_true",
                     help="mixed path: the shared-memory tiled FP32 kernel instead of the default "
                          "one thread per particle")
+    ap.add_argument("--bz-physics", action="store_true",
+                    help="run the BZ monopole test of Sec. 4.5 and report its closed-form checks")
+    ap.add_argument("--bz-n", type=int, default=512, help="--bz-physics: cells per direction")
+    ap.add_argument("--bz-time", type=float, default=60.0, help="--bz-physics: run time, r_g")
+    ap.add_argument("--bz-precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -807,6 +925,9 @@ def main():
         run_adjoint(args, ws, rank, local)
     elif args.extensions:
         run_extensions(args, ws, rank, local)
+    elif args.bz_physics:
+        if rank == 0:
+            run_bz_physics(args, local)
     else:
         run_gpu(args, ws, rank, local)
     if ws > 1:

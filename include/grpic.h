@@ -244,6 +244,15 @@ GRPIC_API grpic_status grpic_get_particles(grpic_ctx *ctx, int species, grpic_pa
 GRPIC_API grpic_status grpic_species_arrays(grpic_ctx *ctx, int species, grpic_particles *out,
                                   int64_t *n);
 
+/* The auxiliary fields of Sec. 2 (Eqs. discretized-auxE and discretized-auxH: E_i =
+ * alpha h_ij D^j + ... and H_i = alpha h_ij B^j - ..., with the spatial averages of those
+ * equations) of the em planes as they stand (B^{n+1/2}, D^{n+1} after a step), copied into
+ * E[c], H[c] (c = 0, 1, 2: the x1, x2, x3 covariant components), each a full plane in the
+ * plane layout of grpic_plane_ptr, host or device memory. For diagnostics such as the
+ * field-line angular velocity and the Poynting flux of Sec. 4.5; synchronises. Errors:
+ * GRPIC_ESTATE (fields not initialised), GRPIC_EINVAL (a null pointer). */
+GRPIC_API grpic_status grpic_aux_fields(grpic_ctx *ctx, void *const E[3], void *const H[3]);
+
 /* Device pointer of a field plane inside the arena (valid until the next ADVANCE,
  * which rotates em/em0 and cur/cur0); elements are double (GRPIC_FP64) or float
  * (GRPIC_MIXED). */

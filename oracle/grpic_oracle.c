@@ -1133,4 +1133,22 @@ void ora_push_frozen_cs(const ora_params *p, const double *F, double scale_re, d
   }
 }
 
+/* The auxiliary fields E, H of the em planes (B, D) as they stand, Eqs. (discretized-auxE)
+ * and (discretized-auxH): E and H each 3 planes (E_1, E_2, E_3), zero where not computed. */
+void ora_aux_fields(const ora_params *p, const double *F, double *E, double *H) {
+  const int64_t PS = plane_size(p);
+  const double *B[3], *D[3];
+  double *e[3], *h[3];
+  for (int c = 0; c < 3; ++c) {
+    B[c] = F + (ORA_B1 + c) * PS;
+    D[c] = F + (ORA_D1 + c) * PS;
+    e[c] = E + c * PS;
+    h[c] = H + c * PS;
+    memset(e[c], 0, sizeof(double) * PS);
+    memset(h[c], 0, sizeof(double) * PS);
+  }
+  aux_E(p, B, D, e);
+  aux_H(p, B, D, h);
+}
+
 int ora_version(void) { return 6; }

@@ -107,6 +107,7 @@ def lib():
         L.ora_charge.argtypes = [P, PP, C.c_int, C.c_int, _PD]
         L.ora_field_predict.argtypes = [P, _PD]
         L.ora_field_advance.argtypes = [P, _PD]
+        L.ora_aux_fields.argtypes = [P, _PD, _PD, _PD]
         L.ora_sort.argtypes = [P, PP, C.c_int, C.c_int, C.POINTER(C.c_int64)]
         L.ora_sort.restype = C.c_int64
         L.ora_sort_key.argtypes = [P, C.c_int, C.c_int, C.c_int32, C.c_int32, C.c_uint8]
@@ -337,6 +338,14 @@ class OracleSim:
         f = np.ascontiguousarray(plane, dtype=np.float64).copy()
         lib().ora_filter_plane(C.byref(self.p), _dp(f), int(half), float(parity), int(n))
         return f
+
+    def aux_fields(self):
+        """E and H (each (3, NY, NX)) of the em planes as they stand (Eqs. discretized-auxE,
+        discretized-auxH), zero where the solver does not compute them."""
+        E = np.zeros((3, self.NY, self.NX))
+        H = np.zeros((3, self.NY, self.NX))
+        lib().ora_aux_fields(C.byref(self.p), _dp(self.F), _dp(E), _dp(H))
+        return E, H
 
     def advance(self):
         lib().ora_field_advance(C.byref(self.p), _dp(self.F))

@@ -31,7 +31,7 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_get_diagnostics", "grpic_set_timing", "grpic_get_timing", "grpic_last_error",
            "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants",
            "grpic_adjoint_forward", "grpic_adjoint_backward", "grpic_charge_check",
-           "grpic_config_bytes", "grpic_inject", "grpic_step_host"]
+           "grpic_config_bytes", "grpic_inject", "grpic_step_host", "grpic_aux_fields"]
 
 
 ADJOINT_SCRATCH_PER_STEP = 36  # doubles per particle and step of grpic_adjoint_backward
@@ -122,6 +122,7 @@ def lib(build: bool = True):
         L.grpic_sort.argtypes = [P, C.c_int]
         L.grpic_step.argtypes = [P, C.c_int]
         L.grpic_step_host.argtypes = [P, C.POINTER(Particles), C.POINTER(C.c_int64)]
+        L.grpic_aux_fields.argtypes = [P, C.c_void_p * 3, C.c_void_p * 3]
         L.grpic_get_diagnostics.argtypes = [P, C.POINTER(Diag)]
         L.grpic_set_timing.argtypes = [P, C.c_int]
         L.grpic_get_timing.argtypes = [P, C.POINTER(Timing)]
@@ -317,6 +318,17 @@ class Sim:
         """Host copy of all field planes as float64, shape (NPLANES, NY, NX) (synchronises)."""
         self.sync()
         return np.stack([self.plane(k).cpu().numpy().astype(np.float64) for k in range(NPLANES)])
+
+    def aux_fields(self):
+        """Host copies of the auxiliary E and H planes (grpic_aux_fields) of the em planes as
+        they stand, float64 arrays of shape (3, NY, NX) each."""
+        NY, NX = self.NY, self.NX
+        E = np.zeros((3, NY, NX), dtype=self.fdtype)
+        H = np.zeros((3, NY, NX), dtype=self.fdtype)
+        pe = (C.c_void_p * 3)(*[E[c].ctypes.data for c in range(3)])
+        ph = (C.c_void_p * 3)(*[H[c].ctypes.data for c in range(3)])
+        self._check(self.L.grpic_aux_fields(self.ctx, pe, ph), "aux_fields")
+        return E.astype(np.float64), H.astype(np.float64)
 
     def set_planes(self, F: np.ndarray, which=range(NPLANES)):
         for k in which:

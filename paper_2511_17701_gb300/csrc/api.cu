@@ -654,6 +654,30 @@ grpic_status grpic_get_particles(grpic_ctx *ctx, int species, grpic_particles *o
   return GRPIC_OK;
 }
 
+grpic_status grpic_aux_fields(grpic_ctx *ctx, void *const E[3], void *const H[3]) {
+  grpic_status s = need_fields(ctx);
+  if (s) return s;
+  if (!E || !H) return fail(ctx, GRPIC_EINVAL, "null E or H");
+  for (int c = 0; c < 3; ++c)
+    if (!E[c] || !H[c]) return fail(ctx, GRPIC_EINVAL, "null plane %d", c);
+  const size_t bytes = (size_t)plane_size(ctx->g) * ctx->fsz;
+  if (ctx->mixed) {
+    CK(launch_aux_fields<float>(ctx->g, ctx->F32, ctx->stream));
+    for (int c = 0; c < 3; ++c) {
+      CK(copy(E[c], ctx->F32.E[c], bytes, ctx->stream));
+      CK(copy(H[c], ctx->F32.H[c], bytes, ctx->stream));
+    }
+  } else {
+    CK(launch_aux_fields<double>(ctx->g, ctx->F64, ctx->stream));
+    for (int c = 0; c < 3; ++c) {
+      CK(copy(E[c], ctx->F64.E[c], bytes, ctx->stream));
+      CK(copy(H[c], ctx->F64.H[c], bytes, ctx->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GRPIC_OK;
+}
+
 grpic_status grpic_plane_ptr(grpic_ctx *ctx, int plane, void **out) {
   grpic_status s = need_bound(ctx);
   if (s) return s;

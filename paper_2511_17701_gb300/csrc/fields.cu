@@ -579,6 +579,15 @@ cudaError_t launch_advance(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t 
   return cudaGetLastError();
 }
 
+// The auxiliary fields E and H (Eqs. discretized-auxE, discretized-auxH) of the em planes as
+// they stand (B^{n+1/2} and D^{n+1} after a step), into the E and H scratch planes.
+template <typename T>
+cudaError_t launch_aux_fields(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st) {
+  auxE(g, one(F.B), one(F.D), F, st);
+  auxH(g, one(F.B), one(F.D), F, st);
+  return cudaGetLastError();
+}
+
 #define INSTANTIATE_FIELDS(T)                                                                    \
   template cudaError_t launch_metric_tables<T>(const GridP &, T *, T *, cudaStream_t);         \
   template cudaError_t launch_zero<T>(T *, int64_t, cudaStream_t);                              \
@@ -587,6 +596,7 @@ cudaError_t launch_advance(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t 
   template cudaError_t launch_field_finish_init<T>(const GridP &, const FieldPtrsT<T> &, int,   \
                                                    cudaStream_t);                               \
   template cudaError_t launch_predict<T>(const GridP &, const FieldPtrsT<T> &, cudaStream_t);   \
-  template cudaError_t launch_advance<T>(const GridP &, const FieldPtrsT<T> &, cudaStream_t);
+  template cudaError_t launch_advance<T>(const GridP &, const FieldPtrsT<T> &, cudaStream_t);   \
+  template cudaError_t launch_aux_fields<T>(const GridP &, const FieldPtrsT<T> &, cudaStream_t);
 INSTANTIATE_FIELDS(double)
 INSTANTIATE_FIELDS(float)

@@ -375,6 +375,8 @@ template <typename T>
 cudaError_t launch_predict(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st);
 template <typename T>
 cudaError_t launch_advance(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st);
+template <typename T>
+cudaError_t launch_aux_fields(const GridP &g, const FieldPtrsT<T> &F, cudaStream_t st);
 // current filter (filter.cu): n passes on n_comp planes a (scratch s; in_s: see filter.cu),
 // and the n_f passes on J (may trade the J and E plane pointers of F)
 template <typename T>

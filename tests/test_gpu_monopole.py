@@ -86,3 +86,43 @@ def test_schwarzschild_monopole_stays_on_gpu(torch_cuda):
     assert np.abs(F[O.B1] - F0[O.B1]).max() < 1e-13 * b
     for k in (O.B2, O.B3, O.D1, O.D2, O.D3):
         assert np.abs(F[k]).max() < 1e-13 * b, k
+
+
+def aux_region(cfg):
+    """Stored rows and columns where both sides compute every auxiliary component: rows
+    j in [0, n_theta - 1], columns i in [-1, n_r + 1]."""
+    G = O.G
+    return slice(G, G + cfg["n_theta"]), slice(G - 1, G + cfg["n_r"] + 2)
+
+
+@pytest.mark.parametrize("cfg", [BZ64, BZ_RAGGED])
+def test_aux_fields_match_the_oracle(torch_cuda, cfg):
+    """grpic_aux_fields: E and H (Eqs. discretized-auxE, discretized-auxH) of the em planes, on
+    the same state to rounding, and after two full steps with plasma to the per-step bound."""
+    osim = oracle_state(cfg, kind=O.FIELD_MONOPOLE)
+    g = gpu_from_oracle(osim)
+    J, I = aux_region(cfg)
+    for when in ("initial", "after two steps"):
+        E, H = g.aux_fields()
+        Eo, Ho = osim.aux_fields()
+        tol = 1e-13 if when == "initial" else 1e-11
+        for name, a, b in (("E", E, Eo), ("H", H, Ho)):
+            for c in range(3):
+                scale = np.abs(b[c][J, I]).max() + 1e-300
+                err = np.abs(a[c][J, I] - b[c][J, I]).max() / scale
+                assert err <= tol, (when, name, c, err)
+        g.step(2)
+        osim.step(2)
+
+
+def test_aux_fields_mixed(torch_cuda):
+    osim = oracle_state(BZ64, kind=O.FIELD_MONOPOLE)
+    round_state_fp32(osim)
+    g = gpu_from_oracle(osim, precision="mixed")
+    J, I = aux_region(BZ64)
+    E, H = g.aux_fields()
+    Eo, Ho = osim.aux_fields()
+    for a, b in ((E, Eo), (H, Ho)):
+        for c in range(3):
+            scale = np.abs(b[c][J, I]).max() + 1e-300
+            assert np.abs(a[c][J, I] - b[c][J, I]).max() / scale <= 1e-5
