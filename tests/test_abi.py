@@ -114,3 +114,13 @@ def test_host_streamed_step_needs_a_ready_context():
     assert B.lib().grpic_step_host(ctx, None, None) == B.ESTATE
     assert list(n) == [10, 10]
     B.lib().grpic_destroy(ctx)
+
+
+def test_aux_fields_need_a_ready_context():
+    """grpic_aux_fields refuses a context without fields (GRPIC_ESTATE) before any CUDA work."""
+    st, ctx = create(good_cfg())
+    assert st == B.OK
+    E = (C.c_void_p * 3)(1, 1, 1)
+    H = (C.c_void_p * 3)(1, 1, 1)
+    assert B.lib().grpic_aux_fields(ctx, E, H) == B.ESTATE
+    B.lib().grpic_destroy(ctx)
