@@ -904,7 +904,10 @@ __device__ __forceinline__ int guard_zone(const PushTables &tb, const GridP &g, 
 
 // FP64 path: one thread per particle, step 1 (previous location) then the FP64 routine.
 template <bool DEPOSIT, bool Q>
-__global__ void __launch_bounds__(TPB, DEPOSIT ? 4 : 3) k_push(GridP g, FieldPtrsT<double> F, PushTables tb,
+#ifndef GRPIC_PUSH64_MIN_BLOCKS  // resident blocks per SM the fused FP64 kernel is built for
+#define GRPIC_PUSH64_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(TPB, DEPOSIT ? GRPIC_PUSH64_MIN_BLOCKS : 3) k_push(GridP g, FieldPtrsT<double> F, PushTables tb,
                                               SpeciesDevT<double> s, unsigned long long *diag) {
   const int64_t n = *s.n;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
