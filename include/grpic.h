@@ -248,7 +248,9 @@ GRPIC_API grpic_status grpic_species_arrays(grpic_ctx *ctx, int species, grpic_p
  * alpha h_ij D^j + ... and H_i = alpha h_ij B^j - ..., with the spatial averages of those
  * equations) of the em planes as they stand (B^{n+1/2}, D^{n+1} after a step), copied into
  * E[c], H[c] (c = 0, 1, 2: the x1, x2, x3 covariant components), each a full plane in the
- * plane layout of grpic_plane_ptr, host or device memory. For diagnostics such as the
+ * plane layout of grpic_plane_ptr, host or device memory; the values are defined on the
+ * stored columns -1 .. n_r + 1 and rows 0 .. n_theta (the half-row components on rows
+ * 0 .. n_theta - 1), the rest of each plane is scratch. For diagnostics such as the
  * field-line angular velocity and the Poynting flux of Sec. 4.5; synchronises. Errors:
  * GRPIC_ESTATE (fields not initialised), GRPIC_EINVAL (a null pointer). */
 GRPIC_API grpic_status grpic_aux_fields(grpic_ctx *ctx, void *const E[3], void *const H[3]);
