@@ -116,10 +116,12 @@ typedef struct {
   int precision;       /* grpic_precision                                                     */
   int full_iterations; /* 0: the implicit pushes stop once an iterate repeats bit for bit (every
                           later iteration would return the same bits, so the result equals the
-                          n_iter result exactly), except the FP32 iterations of GRPIC_MIXED,
-                          which stop once the update is within 2^-22 max(1, |value|) (the
-                          remaining error, a fraction rho / (1 - rho) of that, is below the
-                          rounding of the stored values); 1: always run n_iter iterations     */
+                          n_iter result exactly), except in GRPIC_MIXED: its FP32 iterations
+                          stop once the update is within 2^-22 max(1, |value|), the FP64
+                          iterations of its axis rows (stored in FP32) within 2^-26 max(1,
+                          |value|) (the remaining error, a fraction rho / (1 - rho) of that,
+                          is below the rounding of the stored values); 1: always run n_iter
+                          iterations                                                         */
   int fp64_guard_cells; /* GRPIC_MIXED: cells from the horizon and from each axis where the
                            metric is evaluated in FP64 (default 4 when 0)                     */
   int tiled_push;       /* GRPIC_MIXED: 1 = after a sort, push each sort tile in one CTA with

@@ -286,6 +286,36 @@ __device__ __forceinline__ void coord_jacobian(const GridP &g, const Local<float
   }
 }
 
+// The FP64 routine on FP32 storage (the mixed path's axis rows) stops its iterations once the
+// update is within SETTLE32 max(1, |value|), far below what the stored FP32 result resolves;
+// the FP64 path (settle 0) stops at an exact repeat only.
+constexpr double SETTLE32 = 0x1p-26;
+__device__ __forceinline__ bool settled64(double n0, double t0, double n1, double t1,
+                                          double settle) {
+  return fabs(n0 - t0) <= settle * fmax(1.0, fabs(n0)) &&
+         fabs(n1 - t1) <= settle * fmax(1.0, fabs(n1));
+}
+// the geodesic momentum substep with that stop rule (settle 0: geodesic_momentum itself)
+__device__ __forceinline__ void geodesic_momentum_settle(const GridP &g, const Local<double> &L,
+                                                         double u[3], double m2, double settle) {
+  if (settle == 0.0) {
+    geodesic_momentum(g, L, u, m2);
+    return;
+  }
+  const GeoMap<double> m(g, L, u, m2);
+  double t0 = u[0], t1 = u[1];
+  for (int it = 0; it < g.n_iter; ++it) {
+    double n0, n1;
+    m.apply(t0, t1, n0, n1);
+    const bool fixed = settled64(n0, t0, n1, t1, settle);
+    t0 = n0;
+    t1 = n1;
+    if (fixed && g.stop_on_repeat) break;
+  }
+  u[0] = t0;
+  u[1] = t1;
+}
+
 // The coordinate substep, Eq. (discretized-geodesic-x), as the method iterates it: metric at
 // x_bar = (x^n + x~)/2, the first iterate x^n itself (metric L.G), n_iter iterations or
 // until an exact repeat. t1, t2: the new offsets from cell (i1, i2).
@@ -293,7 +323,7 @@ template <bool Q = true>
 __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const Local<double> &L,
                                             int i1, int i2, double dx1, double dx2,
                                             const double u[3], double m2, double &t1,
-                                            double &t2) {
+                                            double &t2, double settle = 0.0) {
   const double uu0 = 2.0 * u[0] * u[2];
   t1 = dx1;
   t2 = dx2;
@@ -313,7 +343,9 @@ __device__ __forceinline__ void coord_exact(const GridP &g, const Base &b, const
     const double ag = rsqrt(o.opz * q);  // alpha / gamma
     const double n1 = fma(g.dt, fma(ag, fma(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
     const double n2 = fma(g.dt, ag * o.H22 * u[1], dx2);
-    const bool fixed = (n1 == t1) && (n2 == t2);  // exact repeat: later iterations are no-ops
+    // exact repeat: later iterations are no-ops; or (settle > 0) an update below settle
+    const bool fixed = settle > 0.0 ? settled64(n1, t1, n2, t2, settle)
+                                    : (n1 == t1) && (n2 == t2);
     t1 = n1;
     t2 = n2;
     if (fixed && g.stop_on_repeat) break;
@@ -409,6 +441,7 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   const double dx1 = (double)s.dx1[k], dx2 = (double)s.dx2[k];
   const double x1 = i1 + dx1, x2 = i2 + dx2;
   const bool em = s.m2 != 0.0;  // massless particles skip the EM push (Sec. 3.1)
+  const double settle = sizeof(T) == 4 ? SETTLE32 : 0.0;  // FP32 storage: see SETTLE32
   const Base b = make_base<Q>(g, x1, x2);
   Pt<double> p0;
   local_rsc<Q>(g, b, x1, x2, p0);  // clamps theta near the axes
@@ -437,7 +470,7 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   // method's answer is the one its iteration from x^n finds
   const bool refine = g.iter_tol > 0.0 && i2 >= 2 && i2 < g.n_th - 2;
   if (refine) geodesic_refined<Q>(g, tb, i1, i2, (float)dx1, (float)dx2, L, u, s.m2);
-  else geodesic_momentum(g, L, u, s.m2);  // step 6
+  else geodesic_momentum_settle(g, L, u, s.m2, settle);  // step 6
   if (em) {
     cov_hat(L, u, uh);         // step 7
     boris(uh, Dh, Bh, hq);     // step 8
@@ -446,7 +479,7 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   // step 10: implicit coordinate push, Eq. (discretized-geodesic-x)
   double t1 = dx1, t2 = dx2, v3r = NAN;
   if (refine) coord_refined<Q>(g, tb, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2, v3r);
-  else coord_exact<Q>(g, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2);
+  else coord_exact<Q>(g, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2, settle);
   if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(t1) && isfinite(t2) &&
         fabs(t1) < 1e6 && fabs(t2) < 1e6)) {
     s.tag[k] = 0;
