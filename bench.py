@@ -842,6 +842,13 @@ def run_bz_physics(args, local):
         t += k * dt
         if mark > 2 * n_mark / 3:
             snaps.append(bz_diagnostics(sim, cfg, radii))
+            sn = snaps[-1]
+            print(json.dumps({"t": t, "omega_over_omega_h": {str(r): sn[r]["omega"] / wh
+                                                             for r in radii},
+                              "hphi_over_bz": {str(r): sn[r]["hphi_amp"] / (-B0 * a / 8.0)
+                                               for r in radii},
+                              "L_over_LBZ": {str(r): sn[r]["L"] / LBZ for r in radii}}),
+                  file=sys.stderr, flush=True)
     sim.sync()
     wall = time.perf_counter() - t0
     d = sim.diagnostics()
