@@ -1027,10 +1027,10 @@ __global__ void __launch_bounds__(TPB) k_classify(GridP g, SpeciesDevT<float> s,
 
 // Mixed path, FP32 kernel: step 1 and the FP32 routine for every unlisted particle (it runs
 // concurrently with the guard kernels, which own the listed ones). The loop runs while the
-// warp's first particle exists, so the whole warp reaches the cooperative deposit. The
-// kernel waits on gathers and atomics more than on its arithmetic: 12 resident blocks per
-// SM (40 registers, a few spills to L1) measured 0.60 ms per 8.4 M particles against 0.71
-// ms with 6 (80 registers, no spills) on GB300.
+// warp's first particle exists, so the whole warp reaches the cooperative deposit. Its
+// gathers and atomics need many resident warps to hide their latency: 12 blocks per SM (40
+// registers, a few spills to L1) measured 0.60 ms per 8.4 M particles against 0.71 ms with
+// 6 (80 registers, no spills) on GB300; at 12 it is bound by instruction issue.
 template <bool DEPOSIT, bool Q>
 __global__ void __launch_bounds__(TPB, 12) k_push32(GridP g, FieldPtrsT<float> F,
                                                 SpeciesDevT<float> s, PushTables tb,
