@@ -186,14 +186,19 @@ typedef struct {
 
 /* --- set-up ----------------------------------------------------------------------- */
 
-/* Validates cfg and creates a host context (no CUDA work). *out owns host memory
- * only. Errors: GRPIC_EINVAL (bad sizes, spin, radii, species counts). */
+/* Validates cfg (the problem parameters of Secs. 3.1-3.4 and App. A: spin, grid map, time
+ * step rule, iterations, boundaries; see grpic_config) and creates a host context (no CUDA
+ * work). *out owns host memory only; release it with grpic_destroy. Errors: GRPIC_EINVAL
+ * (bad sizes, spin, radii, species counts). */
 GRPIC_API grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out);
 
-/* Bytes of device memory the context needs (256-byte aligned sub-buffers). */
+/* Bytes of device memory the context needs (256-byte aligned sub-buffers): field planes,
+ * metric tables, particle arrays (two copies for the sort), scratch. Memory management,
+ * with no counterpart in the paper. No CUDA work; 0 for a null context. */
 GRPIC_API size_t grpic_arena_bytes(const grpic_ctx *ctx);
 
-/* Binds the caller-owned device arena (>= grpic_arena_bytes, 256-byte aligned)
+/* (Memory and stream management, no counterpart in the paper.)
+ * Binds the caller-owned device arena (>= grpic_arena_bytes, 256-byte aligned)
  * and the CUDA stream (cudaStream_t, NULL = legacy default) on the current device.
  * With GRPIC_MIXED the first bind also creates one internal stream and event pairs
  * (no device memory): the push forks the FP64 guard-zone kernels onto it and joins
@@ -208,7 +213,10 @@ GRPIC_API grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, voi
  * Synchronises the stream once (dt is read back). */
 GRPIC_API grpic_status grpic_init_metric(grpic_ctx *ctx);
 
-/* The time step in use (after grpic_init_metric). */
+/* The time step in use after grpic_init_metric (0 before): cfg.dt, or cfl times the
+ * smallest light-crossing time of a cell, min over cell centres of 1 / (alpha sqrt(h^11 +
+ * h^22) + |beta^1|) in code units (Sec. 3 fixes the time step of the leap-frog scheme but
+ * gives no rule for it: this Courant rule is a reading). No CUDA work. */
 GRPIC_API double grpic_dt(const grpic_ctx *ctx);
 
 /* Initial fields (Sec. 4.1.2, 4.2): B^1, B^2 from the discrete curl of A_3 at the nodes,
@@ -238,11 +246,16 @@ GRPIC_API grpic_status grpic_load_particles(grpic_ctx *ctx, int species, int64_t
 GRPIC_API grpic_status grpic_set_particles(grpic_ctx *ctx, int species, int64_t n, double qm, double qc,
                                  const grpic_particles *in);
 
-/* Copies a species' state out into caller arrays (host or device), and its count. */
+/* Copies a species' state out into caller arrays (host or device; null array pointers
+ * are skipped), in the layout of grpic_particles, and its count into *n. State I/O, with no
+ * counterpart in the paper. Synchronises the stream. Errors: GRPIC_ESTATE (not bound),
+ * GRPIC_EINVAL (species out of range). */
 GRPIC_API grpic_status grpic_get_particles(grpic_ctx *ctx, int species, grpic_particles *out,
                                  int64_t *n);
 
-/* Device pointers of a species' arrays inside the arena (valid until the next sort). */
+/* Device pointers of a species' arrays inside the arena (valid until the next sort, which
+ * moves the species to the other copy) and its live count (synchronises when n is given).
+ * No counterpart in the paper. Errors: GRPIC_ESTATE (not bound), GRPIC_EINVAL (species). */
 GRPIC_API grpic_status grpic_species_arrays(grpic_ctx *ctx, int species, grpic_particles *out,
                                   int64_t *n);
 
@@ -259,7 +272,10 @@ GRPIC_API grpic_status grpic_aux_fields(grpic_ctx *ctx, void *const E[3], void *
 
 /* Device pointer of a field plane inside the arena (valid until the next ADVANCE,
  * which rotates em/em0 and cur/cur0); elements are double (GRPIC_FP64) or float
- * (GRPIC_MIXED). */
+ * (GRPIC_MIXED). The planes are the state of the loop of Sec. 3.4 (em, em0, cur, cur0,
+ * B^n) and the initial field the absorbing layer relaxes to (Sec. 3.3.3), GRPIC_NPLANES in
+ * all, each [n_theta + 5][n_r + 5] with 2 ghost cells per side. Errors: GRPIC_ESTATE (not
+ * bound), GRPIC_EINVAL (plane out of range, null out). */
 GRPIC_API grpic_status grpic_plane_ptr(grpic_ctx *ctx, int plane, void **out);
 
 /* Conserved energy and angular momentum per unit mass of each particle of a species
@@ -292,7 +308,9 @@ GRPIC_API grpic_status grpic_deposit(grpic_ctx *ctx);
 GRPIC_API grpic_status grpic_field_step(grpic_ctx *ctx, int phase);
 
 /* Stable sort of a species by tile-major cell key; particles not alive go last and
- * are dropped (the count shrinks). Integer work: the permutation is unique. */
+ * are dropped (the count shrinks). Integer work: the permutation is unique. The paper has
+ * no sort; it keeps the particles of a cell together for the gathers and the deposit.
+ * Errors: GRPIC_ESTATE (not bound), GRPIC_EINVAL (species out of range). */
 GRPIC_API grpic_status grpic_sort(grpic_ctx *ctx, int species);
 
 /* n_steps full PIC steps (Sec. 3.4): PREDICT, sort every cfg.sort_every steps, fused
@@ -415,7 +433,8 @@ GRPIC_API grpic_status grpic_adjoint_forward(grpic_ctx *ctx, int64_t n, double q
                                              const double *state0, double *state_out,
                                              double *ckpt);
 
-/* The reverse sweep of the same push (same n, qm, b0, n_steps, ckpt_every, n_iter and the
+/* The reverse sweep of the same push (the push of Sec. 3.1 over frozen fields; the paper
+ * has no adjoint) (same n, qm, b0, n_steps, ckpt_every, n_iter and the
  * ckpt written by grpic_adjoint_forward): given grad_out = dL/d(final state) ([6][n]),
  * writes grad_state0 = dL/d(initial state) ([6][n]), grad_b0_pp[k] = particle k's part of
  * dL/db0 ([n]) and grad_b0[0] = their sum (deterministic order). Each checkpoint segment is
@@ -446,7 +465,8 @@ typedef struct {
   double inject_ms;     /* grpic_inject                                               */
 } grpic_timing;
 
-/* Enables (1) or disables (0) the per-phase events. Off by default. */
+/* Enables (1) or disables (0) the per-phase events. Off by default. Instrumentation, with
+ * no counterpart in the paper (as the timing and diagnostics calls below). */
 GRPIC_API grpic_status grpic_set_timing(grpic_ctx *ctx, int enable);
 
 /* Sums the recorded phases and resets the sums and the launch counter.
@@ -456,11 +476,18 @@ GRPIC_API grpic_status grpic_get_timing(grpic_ctx *ctx, grpic_timing *out);
 /* Counters accumulated since the last call, and live counts. Synchronises the stream. */
 GRPIC_API grpic_status grpic_get_diagnostics(grpic_ctx *ctx, grpic_diag *out);
 
+/* A one-line description of the last error returned on this context (empty when none),
+ * owned by the context and valid until its next call. No counterpart in the paper. */
 GRPIC_API const char *grpic_last_error(const grpic_ctx *ctx);
+
+/* Waits for the context's streams and frees what it owns on the host and its streams and
+ * events; the arena stays the caller's. A null context is ignored. No counterpart in the
+ * paper. */
 GRPIC_API void grpic_destroy(grpic_ctx *ctx);
 
 /* sizeof(grpic_config) as this library was compiled: bindings compare it with their own
- * layout of the struct before the first grpic_create. No CUDA work. */
+ * layout of the struct before the first grpic_create. No CUDA work; no counterpart in the
+ * paper. */
 GRPIC_API size_t grpic_config_bytes(void);
 
 #ifdef __cplusplus
