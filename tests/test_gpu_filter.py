@@ -7,12 +7,11 @@ check. Grids start far enough inside the horizon for the filter (r(n_f + 1) <= r
 * full steps with a sort, FP64 (1e-12 per step) and mixed precision (1e-5);
 * the charge check: the filtered currents conserve the filtered charge to rounding.
 """
-import numpy as np
 import pytest
 
 import workloads as W
 from oracle import oracle as O
-from parity import (RTOL, assert_currents, assert_particles, assert_planes, gpu_from_oracle,
+from parity import (assert_currents, assert_particles, assert_planes, gpu_from_oracle,
                     oracle_state, particle_errors, plane_errors, round_state_fp32)
 
 pytestmark = pytest.mark.gpu

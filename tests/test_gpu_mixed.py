@@ -15,7 +15,7 @@ import pytest
 
 import workloads as W
 from oracle import oracle as O
-from parity import (G, gpu_from_oracle, oracle_state, particle_errors, plane_errors,
+from parity import (gpu_from_oracle, oracle_state, particle_errors, plane_errors,
                     round_state_fp32)
 
 pytestmark = pytest.mark.gpu

@@ -12,7 +12,7 @@ import pytest
 
 import workloads as W
 from oracle import oracle as O
-from parity import (RTOL, assert_currents, assert_particles, assert_planes, gpu_from_oracle,
+from parity import (assert_currents, assert_particles, assert_planes, gpu_from_oracle,
                     oracle_state)
 
 pytestmark = pytest.mark.gpu

@@ -9,7 +9,6 @@ checks that the returned permutation reproduces grpic_sort's result exactly (the
 is unique, so the comparison is bit-exact), on two calls in a row with different sizes
 so that nothing left in the shared scratch by the first call leaks into the second.
 """
-import ctypes as C
 
 import numpy as np
 import pytest
