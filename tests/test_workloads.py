@@ -45,3 +45,22 @@ def test_pair_plasma_layout():
         assert np.array_equal(pos[k], b["pos"][k])
     for s in range(2):
         assert np.array_equal(a["uhat"][s], b["uhat"][s])
+
+
+def test_injection_pool_draws():
+    """[n, 8]: uniform cell offsets, then the e- and e+ tetrad-frame momenta, Maxwell-Juttner
+    at the injection temperature (theta = 0.5 on the monopole workload, Sec. 4.5)."""
+    cfg = W.grid_config("bz1024")
+    n = 200_000
+    pool = W.injection_pool(cfg, n, seed=3)
+    assert pool.shape == (n, 8)
+    assert np.array_equal(pool, W.injection_pool(cfg, n, seed=3))
+    for c in (0, 1):
+        assert np.all((pool[:, c] >= 0.0) & (pool[:, c] < 1.0))
+        assert abs(pool[:, c].mean() - 0.5) < 5.0 * math.sqrt(1.0 / 12.0 / n)
+    theta = cfg["theta_inj"]
+    mean = 3.0 * theta + special.kn(1, 1.0 / theta) / special.kn(2, 1.0 / theta)
+    for lo in (2, 5):
+        u = pool[:, lo:lo + 3]
+        gamma = np.sqrt(1.0 + np.sum(u * u, axis=1))
+        assert abs(gamma.mean() - mean) < 5.0 * gamma.std() / math.sqrt(n) + 1e-4 * mean
