@@ -696,33 +696,29 @@ static double filter_ext(const ora_params *p, const double *f, int i, int j, int
   return v;
 }
 
-/* n passes of the filter on one plane; half = 1 for a half-row component. The (1 2 1) x
- * (1 2 1)/16 stencil is applied as its two factors: (1 2 1)/4 along x1, then (1 2 1)/4 along
- * x2 on the mirror-extended rows (the same values in exact arithmetic). */
+/* n passes of the filter on one plane; half = 1 for a half-row component. One pass is the
+ * plain 3 x 3 binomial stencil (1 2 1) x (1 2 1) / 16 on the mirror-extended grid. */
 void ora_filter_plane(const ora_params *p, double *f, int half, double parity, int n) {
   const int NX = NX_of(p), N = p->n_th;
   const int64_t PS = plane_size(p);
-  double *t = malloc(sizeof(double) * PS);
+  double *src = malloc(sizeof(double) * PS);
+  const double w[3] = {1.0, 2.0, 1.0};
   const int jmax = half ? N - 1 : N;
   for (int pass = 0; pass < n; ++pass) {
-    memset(t, 0, sizeof(double) * PS);
-    for (int j = 0; j <= jmax; ++j)
-      for (int i = -G; i <= p->n_r + G; ++i) {
-        double a = i > -G ? AT(f, i - 1, j) : 0.0;
-        double c = i < p->n_r + G ? AT(f, i + 1, j) : 0.0;
-        AT(t, i, j) = ((a + 2.0 * AT(f, i, j)) + c) * 0.25;
-      }
+    memcpy(src, f, sizeof(double) * PS);
     memset(f, 0, sizeof(double) * PS);
     for (int j = 0; j <= jmax; ++j)
       for (int i = -G; i <= p->n_r + G; ++i) {
-        double acc = ((filter_ext(p, t, i, j - 1, half, parity) +
-                       2.0 * filter_ext(p, t, i, j, half, parity)) +
-                      filter_ext(p, t, i, j + 1, half, parity)) * 0.25;
+        double acc = 0.0;
+        for (int b = -1; b <= 1; ++b)
+          for (int a = -1; a <= 1; ++a)
+            acc += w[a + 1] * w[b + 1] * filter_ext(p, src, i + a, j + b, half, parity);
+        acc /= 16.0;
         if (!half && (j == 0 || j == N)) acc *= 0.5; /* back to the half cell */
         AT(f, i, j) = acc;
       }
   }
-  free(t);
+  free(src);
 }
 
 /* the n_f passes on the currents J^1 (node rows, even), J^2 (half rows, odd), J^3 (node rows,
