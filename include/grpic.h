@@ -112,7 +112,9 @@ typedef struct {
   int n_species;       /* 1 .. GRPIC_MAX_SPECIES                                             */
   int64_t capacity[GRPIC_MAX_SPECIES]; /* particles per species the arena holds              */
   int sort_every;      /* grpic_step sorts particles by cell every k steps (0: never)        */
-  int tile_r, tile_theta; /* sort tile, in cells                                             */
+  int tile_r, tile_theta; /* sort tile, in cells: 1 .. 65536, with the tile-padded cell count
+                             ceil(n_r/tile_r) ceil(n_theta/tile_theta) tile_r tile_theta at most
+                             2^31 - 1 (else GRPIC_EINVAL)                                      */
   int precision;       /* grpic_precision                                                     */
   int full_iterations; /* 0: the implicit pushes stop once an iterate repeats bit for bit (every
                           later iteration would return the same bits, so the result equals the
@@ -357,8 +359,14 @@ GRPIC_API grpic_status grpic_step_host(grpic_ctx *ctx, const grpic_particles *st
  * (cudaGetSymbolAddress); make that first call before any stream capture. All calls on a
  * device share the array, so calls whose work overlaps on the GPU (other streams, other
  * host threads) race; serialise them. The entry point calls no cudaMalloc or cudaFree.
- * Errors: GRPIC_ECAPACITY when n > GRPIC_NOALLOC_SORT_MAX, GRPIC_EINVAL for bad sizes or
- * null pointers, GRPIC_ECUDA when a CUDA call fails. */
+ * Errors: GRPIC_ECAPACITY when n > GRPIC_NOALLOC_SORT_MAX; GRPIC_EINVAL for sizes below 1,
+ * n_r, n_theta, tile_r or tile_theta above 65536, a tile-padded cell count
+ * ceil(n_r/tile_r) ceil(n_theta/tile_theta) tile_r tile_theta above 2^31 - 1 (the keys would
+ * reach the key of dead particles), or null pointers; GRPIC_ECUDA when a CUDA call of this
+ * entry point fails. A CUDA error already pending on the calling thread when the call starts
+ * (cudaPeekAtLastError) is not cleared: the call returns GRPIC_ECUDA at once, queues nothing
+ * and leaves that error for its owner to read. n = 0 queues one kernel that sets *n_alive
+ * to 0. */
 GRPIC_API grpic_status grpic_sort_permutation_noalloc(int n_r, int n_theta, int tile_r,
                                                       int tile_theta, const int32_t *i1,
                                                       const int32_t *i2, const uint8_t *tag,

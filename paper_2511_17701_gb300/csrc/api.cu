@@ -338,6 +338,13 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   if (c.n_species < 1 || c.n_species > GRPIC_MAX_SPECIES) return GRPIC_EINVAL;
   if (c.precision != GRPIC_FP64 && c.precision != GRPIC_MIXED) return GRPIC_EINVAL;
   if (c.tile_r < 1 || c.tile_theta < 1 || c.sort_every < 0) return GRPIC_EINVAL;
+  if (c.tile_r > 65536 || c.tile_theta > 65536) return GRPIC_EINVAL;
+  {  // the sort's largest live key (the tile-padded cell count) below the dead key, in int range
+    const uint64_t ntr = (uint64_t)((c.n_r + c.tile_r - 1) / c.tile_r);
+    const uint64_t ntt = (uint64_t)((c.n_theta + c.tile_theta - 1) / c.tile_theta);
+    if (ntr * ntt * (uint64_t)c.tile_r * (uint64_t)c.tile_theta > (uint64_t)INT32_MAX)
+      return GRPIC_EINVAL;
+  }
   if (!(c.dt > 0.0) && !(c.cfl > 0.0 && c.cfl <= 1.0)) return GRPIC_EINVAL;
   if (c.fp64_guard_cells < 0 || 2 * c.fp64_guard_cells >= c.n_theta) return GRPIC_EINVAL;
   if (!(c.iter_tol >= 0.0 && c.iter_tol < 1e-6)) return GRPIC_EINVAL;

@@ -295,8 +295,18 @@ extern "C" GRPIC_API grpic_status grpic_sort_permutation_noalloc(
     int n_r, int n_theta, int tile_r, int tile_theta, const int32_t *i1, const int32_t *i2,
     const uint8_t *tag, int64_t n, uint32_t *perm, int64_t *n_alive, void *stream) {
   if (n_r < 1 || n_theta < 1 || tile_r < 1 || tile_theta < 1 || n < 0) return GRPIC_EINVAL;
+  if (n_r > 65536 || n_theta > 65536 || tile_r > 65536 || tile_theta > 65536)
+    return GRPIC_EINVAL;
+  // every key of a live particle (below the tile-padded cell count) must stay below the
+  // dead key 0xFFFFFFFF and inside the int range the key arithmetic uses
+  const int64_t ntr = (n_r + tile_r - 1) / tile_r, ntt = (n_theta + tile_theta - 1) / tile_theta;
+  const uint64_t maxkey = (uint64_t)ntr * ntt * tile_r * tile_theta;
+  if (maxkey > (uint64_t)INT32_MAX) return GRPIC_EINVAL;
   if (n > NA_MAX) return GRPIC_ECAPACITY;
   if (!n_alive || (n > 0 && (!i1 || !i2 || !tag || !perm))) return GRPIC_EINVAL;
+  // an error left pending by earlier work on this thread is not this call's: leave it for
+  // its owner to read and queue nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return GRPIC_ECUDA;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   // set-up, once per device with that device current: the device address of the
   // scratch array (its host-side name is only a stand-in for it)
@@ -333,8 +343,6 @@ extern "C" GRPIC_API grpic_status grpic_sort_permutation_noalloc(
   s.i2 = const_cast<int32_t *>(i2);
   s.tag = const_cast<uint8_t *>(tag);
   s.n = n_dev;
-  const int64_t ntr = (n_r + tile_r - 1) / tile_r, ntt = (n_theta + tile_theta - 1) / tile_theta;
-  const uint64_t maxkey = (uint64_t)ntr * ntt * tile_r * tile_theta;
   int bits = 1;
   while (((uint64_t)1 << bits) - 1 < maxkey + 1 && bits < 32) ++bits;
   const int passes = (bits + 7) / 8;

@@ -124,3 +124,32 @@ def test_aux_fields_need_a_ready_context():
     H = (C.c_void_p * 3)(1, 1, 1)
     assert B.lib().grpic_aux_fields(ctx, E, H) == B.ESTATE
     B.lib().grpic_destroy(ctx)
+
+
+def test_create_rejects_sort_keys_beyond_the_dead_key():
+    """The sort's keys of live particles run up to the tile-padded cell count, which must stay
+    within int range and below the key of dead particles (0xFFFFFFFF)."""
+    assert create(dict(good_cfg(), tile_r=70000))[0] == B.EINVAL
+    assert create(dict(good_cfg(), tile_theta=65537))[0] == B.EINVAL
+    big = dict(good_cfg(), n_r=50000, n_theta=50000, tile_r=1, tile_theta=1)
+    assert create(big, caps=(1, 1))[0] == B.EINVAL
+    ok = dict(big, tile_r=16, tile_theta=16)  # 3125^2 tiles of 256 cells: 2.5e9 keys, too many
+    assert create(ok, caps=(1, 1))[0] == B.EINVAL
+    assert create(dict(good_cfg(), n_r=40000, n_theta=40000, tile_r=16, tile_theta=16),
+                  caps=(1, 1))[0] == B.OK
+
+
+def test_noalloc_sort_validates_before_any_cuda_work():
+    """The allocation-free sort refuses bad sizes on the host (no GPU is touched)."""
+    L = B.lib()
+    p = 256  # never dereferenced: every call below is refused first
+    assert L.grpic_sort_permutation_noalloc(37, 23, 0, 4, p, p, p, 10, p, p, None) == B.EINVAL
+    assert L.grpic_sort_permutation_noalloc(0, 23, 8, 4, p, p, p, 10, p, p, None) == B.EINVAL
+    assert L.grpic_sort_permutation_noalloc(37, 23, 8, 4, p, p, p, -1, p, p, None) == B.EINVAL
+    assert L.grpic_sort_permutation_noalloc(65537, 8, 1, 1, p, p, p, 4, p, p, None) == B.EINVAL
+    assert L.grpic_sort_permutation_noalloc(37, 23, 65537, 4, p, p, p, 4, p, p, None) == B.EINVAL
+    assert L.grpic_sort_permutation_noalloc(50000, 50000, 1, 1, p, p, p, 4, p, p, None) == B.EINVAL
+    assert L.grpic_sort_permutation_noalloc(37, 23, 8, 4, p, p, p, (1 << 20) + 1, p, p,
+                                            None) == B.ECAPACITY
+    assert L.grpic_sort_permutation_noalloc(37, 23, 8, 4, None, p, p, 10, p, p, None) == B.EINVAL
+    assert L.grpic_sort_permutation_noalloc(37, 23, 8, 4, p, p, p, 10, p, None, None) == B.EINVAL

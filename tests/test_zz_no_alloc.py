@@ -82,3 +82,45 @@ def test_noalloc_sort_rejects_too_many(torch_cuda):
     p = dummy.data_ptr()
     assert lib.grpic_sort_permutation_noalloc(37, 23, 8, 4, p, p, p, big, p, p, None) == B.ECAPACITY
     assert lib.grpic_sort_permutation_noalloc(37, 23, 0, 4, p, p, p, 10, p, p, None) == B.EINVAL
+
+
+def test_noalloc_sort_at_its_maximum_size(torch_cuda):
+    """n = GRPIC_NOALLOC_SORT_MAX, where the fixed scratch (digit histograms, scan sums) is
+    full: the permutation reproduces grpic_sort's result."""
+    from paper_2511_17701_gb300 import Sim
+    n = 1 << 20
+    sim = Sim(CFG, [n])
+    state = random_state(n, 3)
+    sim.set_particles(0, state, 1.0, 1.0)
+    perm, n_alive = noalloc_permutation(torch_cuda, sim, n)
+    sim.sort(0)
+    after = sim.get_particles(0)
+    assert n_alive == len(after["i1"]) == int(np.sum(state["tag"] == 1))
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    for k, v in after.items():
+        assert np.array_equal(v, state[k][perm[:n_alive]]), k
+    sim.close()
+
+
+def test_noalloc_sort_of_nothing_sets_zero_alive(torch_cuda):
+    from paper_2511_17701_gb300 import binding as B
+    lib = B.lib()
+    n_alive = torch_cuda.full((1,), -7, dtype=torch_cuda.int64, device="cuda:0")
+    st = lib.grpic_sort_permutation_noalloc(37, 23, 8, 4, None, None, None, 0, None,
+                                            n_alive.data_ptr(), None)
+    assert st == B.OK
+    torch_cuda.cuda.synchronize()
+    assert int(n_alive.item()) == 0
+
+
+def test_noalloc_sort_rejects_keys_beyond_the_dead_key(torch_cuda):
+    """A tile-padded cell count above 2^31 - 1 would let live keys reach the key of dead
+    particles: refused before any work."""
+    from paper_2511_17701_gb300 import binding as B
+    lib = B.lib()
+    dummy = torch_cuda.zeros(8, dtype=torch_cuda.int64, device="cuda:0")
+    p = dummy.data_ptr()
+    assert lib.grpic_sort_permutation_noalloc(65536, 65536, 1, 1, p, p, p, 4, p, p, None) == B.EINVAL
+    assert lib.grpic_sort_permutation_noalloc(65537, 8, 1, 1, p, p, p, 4, p, p, None) == B.EINVAL
+    assert lib.grpic_sort_permutation_noalloc(37, 23, 65537, 4, p, p, p, 4, p, p, None) == B.EINVAL
+    assert lib.grpic_sort_permutation_noalloc(50000, 50000, 1, 1, p, p, p, 4, p, p, None) == B.EINVAL
