@@ -1,23 +1,28 @@
 """Throughput of the GR PIC hot path (push + deposit + field update) on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                [--workload wald512] [--precision both|fp64|mixed] [--sort-every 10]
+                [--workload wald2048] [--precision both|fp64|mixed] [--sort-every 10]
 
-A step is one full PIC step (Sec. 3.4 of arXiv:2511.17701) over the whole workload:
-field predict, (sort), fused push + deposit of both species, field advance. The default
-workload is the 512^2 Kerr (a = 0.9) Wald configuration with 32 particles per cell per
-species (16,777,216 particles), synthetic and seeded. By default it is timed in FP64 (the
-line's value, with the end-to-end leg and the CPU oracle beside it) and then in mixed
-precision on the same workload (the "mixed" object). Prints one JSON line.
+A step is one full PIC step (Sec. 3.4 of arXiv:2511.17701) over the whole workload: field
+predict, (sort), fused push + deposit of both species, field advance. The default workload
+is the 2048^2 Kerr (a = 0.9) Wald configuration: r in [0.95 r_h, 200], 16 particles per cell
+per species (134,217,728 particles), density ~ 1/r, Maxwell-Juttner theta_T = 1, synthetic
+and seeded. It is timed in FP64 (the line's value, with the end-to-end leg through the C ABI
+and the CPU oracle beside it) and then in mixed precision on the same workload (the "mixed"
+object, with its per-step error against the FP64 path and the invariant drift of both
+precisions). The rooflines divide by peaks measured in the same run: the FP64 and FP32 FMA
+rates of the library's probe kernel, and the HBM copy bandwidth of MEASURED_PEAKS.json.
+Prints one JSON line.
 
---impl reference times the CPU oracle (FP64, OpenMP over particles) on the host cores,
-each step on a bounded sample of the same workload.
+--impl reference times the CPU oracle (FP64, OpenMP over particles) on the host cores on a
+bounded sample of the same workload.
 Under torchrun with N > 1 every rank runs an independent replica of the workload on its
 own GPU (weak scaling, no data-path collective).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -35,37 +40,38 @@ import workloads as W  # noqa: E402
 
 METRIC = ("particle-steps/sec (push+deposit+field) & % HBM roofline, FP64 vs mixed, 1 GB300")
 
-# Algorithmic bytes of one particle-step of the dominant kernel of each precision.
-# FP64 k_push<deposit> (SoA; read: i1, i2, dx1, dx2, u1, u2, u3, phi, w, tag; write: the same
-# minus w plus the previous position i1p, i2p, dx1p, dx2p): 4+4+8+8+24+8+8+1 = 65 B read,
-# 4+4+8+8+24+8+1 + 4+4+8+8 = 81 B written.
-FP64_BYTES_PER_PARTICLE_STEP = 65 + 81
-# Mixed k_push32<deposit> (FP32 offsets, momenta, phi and w; the guard bitmask): 4+4+4+4+12+4+4
-# +1 + 1/8 = 37 B read; i1p, i2p, dx1p, dx2p, i1, i2, dx1, dx2 (32) + u (12) + phi (4) = 48 B
-# written.
-MIXED_BYTES_PER_PARTICLE_STEP = 37 + 48
-# FP64 pipe operations (DFMA + DMUL + DADD thread instructions) per particle-step of
-# k_push<deposit> on the wald512 workload, counted by ncu, and as flops (2 DFMA + DMUL +
-# DADD): with the implicit iterations refined from an FP32 predictor and one Newton step on
-# its FP32 Jacobian (iter_tol > 0): 303 + 354 + 109 = 767 (1070 flop); stopped at an exact
-# repeat (iter_tol = 0): 476 + 548 + 120 = 1144 (1620 flop). The FP64 pipe issues 2 such
-# operations per clock per SM.
-FP64_PIPE_OPS_PER_PARTICLE_STEP = {True: 767, False: 1144}
-FP64_FLOP_PER_PARTICLE_STEP = {True: 1070, False: 1620}
-SMS, MAX_SM_GHZ = 152, 2.07
-FP64_PIPE_PEAK_GOPS = 2 * SMS * MAX_SM_GHZ  # 629 G operations/s
-# Warp instructions issued per particle by k_push32<deposit> on the wald512 workload (ncu:
-# 384.9 M over 8.39 M particles with 12 resident blocks per SM, spills included); an SM
-# issues at most 4 warp instructions per clock.
-MIXED_WARP_INST_PER_PARTICLE = 45.9
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per particle of the dominant
-# kernels on the wald512 workload, from one ncu capture each: k_push<deposit> at 4 particles
-# per cell and species (87.5 + 32.5 MB over 1,048,576 particles; traffic grows with the
-# particles, so a full launch is this times its particles), k_push32<deposit> at the full
-# size (314.6 + 615.9 MB over 8,388,608 particles).
-TRAFFIC_BYTES_PER_PARTICLE = {"fp64": (87.5e6 + 32.5e6) / 1048576,
-                              "mixed": (314.6e6 + 615.9e6) / 8388608}
-ISSUE_PEAK_GINST = 4 * SMS * MAX_SM_GHZ  # 1259 G warp instructions/s
+# Algorithmic bytes of one particle-step of the dominant kernel of each precision, as the
+# bench runs it (the fused push + deposit stores no previous positions):
+# FP64 k_push<deposit> reads i1, i2, dx1, dx2, u1, u2, u3, phi, w, tag (4+4+8+8+24+8+8+1 =
+# 65 B) and writes all of them but w (57 B): 122 B.
+FP64_BYTES_PER_PARTICLE_STEP = 65 + 57
+# Mixed k_push32<deposit>: FP32 offsets, momenta, phi and w and the guard bitmask read
+# (4+4+4+4+12+4+4+1 + 1/8 = 37 B), the same but w and the mask written (33 B): 70 B.
+MIXED_BYTES_PER_PARTICLE_STEP = 37 + 33
+# The grid's share of a step: em (6 planes), em0 (6), cur0 (3) and cur (3) read, em, em0 and
+# cur0 written: 33 plane elements per cell (264 B in FP64, 132 B in FP32), per particle the
+# cell's share 264 / (particles per cell).
+GRID_BYTES_PER_CELL = {"fp64": 33 * 8, "mixed": 33 * 4}
+
+# Executed work and DRAM traffic per particle of the dominant kernels, from ncu captures of
+# the kernel sources whose digest is `src` (profiles/): FP64-pipe operations (DFMA + DMUL +
+# DADD thread instructions) of k_push<deposit>, warp instructions of k_push32<deposit>, and
+# dram__bytes_read.sum + dram__bytes_write.sum per particle. When the sources change the
+# counts are reported as stale and the traffic as null until they are captured again.
+KERNEL_COUNTS = {
+    "fp64": {"src": "", "workload": "", "fp64_ops": 767, "flop": 1070, "dram_bytes": None},
+    "mixed": {"src": "", "workload": "", "warp_inst": 45.9, "dram_bytes": None},
+}
+KERNEL_SOURCES = ("particles.cu", "pusher.cuh", "grpic_internal.cuh")
+
+
+def kernel_src_digest() -> str:
+    """sha256 (first 16 hex digits) of the sources that define the push kernels."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2511_17701_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -73,6 +79,14 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth, else the stated fallback."""
+    p = measured_peaks().get("hbm_gbs")
+    if p:
+        return float(p), "measured (MEASURED_PEAKS.json: device copy on this pool's GB300s)"
+    return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement; no MEASURED_PEAKS.json)"
 
 
 class ClockSampler:
@@ -113,12 +127,8 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             p = [x.strip() for x in line.split(",")]
-            if len(p) < 9:
-                continue
-            try:
+            if len(p) >= 9:
                 rows.append(p)
-            except ValueError:
-                pass
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
@@ -201,6 +211,9 @@ def workload_desc(name, cfg, n_total, precision="fp64"):
                     cfg.get("density_power", 0.0), PRECISION_DESC[precision]))
 
 
+# ---------------------------------------------------------------------------------------
+# The CPU oracle (cpu_baseline and the reference arm only)
+# ---------------------------------------------------------------------------------------
 def oracle_workload(cfg, frac, seed=99):
     """The oracle holding the workload's grid and, when frac < 1, the particles of a
     seeded random fraction of the cells (a bounded sample)."""
@@ -217,47 +230,160 @@ def oracle_workload(cfg, frac, seed=99):
     return osim
 
 
-def oracle_steps(osim, steps):
-    """Seconds of each of `steps` full oracle PIC steps, and the particles pushed."""
-    times, parts = [], 0
-    for _ in range(steps):
-        parts += sum(s.n for s in osim.species)
-        t0 = time.perf_counter()
-        osim.step(1)
-        times.append(time.perf_counter() - t0)
-    return times, parts
+def oracle_phases(osim, threads):
+    """One oracle PIC step in its phases, timed: (field seconds: predict + advance,
+    particle seconds: both pushes + the deposit, particles pushed)."""
+    from oracle import oracle as O
+    O.set_threads(threads)
+    n = sum(s.n for s in osim.species)
+    t0 = time.perf_counter()
+    osim.predict()
+    t1 = time.perf_counter()
+    for s in range(len(osim.species)):
+        osim.push(s)
+    osim.deposit()
+    t2 = time.perf_counter()
+    osim.advance()
+    t3 = time.perf_counter()
+    return (t1 - t0) + (t3 - t2), t2 - t1, n
 
 
 def host_cores():
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    from oracle import oracle as O
+    return O.max_threads()
+
+
+def projected_rate(n_total, t_field, t_part, n_sample):
+    """Particle-steps/s of a full-workload step from a step on the whole grid with a sample
+    of the particles: the particle phases scale with the particles, the field phases do not."""
+    return n_total / (t_field + t_part * n_total / n_sample)
+
+
+def cpu_baseline(args):
+    """The oracle as it stands on the host cores: 2 full steps on the workload's whole grid
+    with the particles of a seeded fraction of the cells (all cores), then the particle phases
+    of one more step on one core; the particle phases projected to the full workload."""
+    cfg = W.grid_config(args.workload)
+    if args.ppc:
+        cfg["ppc"] = args.ppc
+    n_total = 2 * cfg["n_r"] * cfg["n_theta"] * cfg["ppc"]
+    t_set = time.perf_counter()
+    osim = oracle_workload(cfg, args.cpu_frac)
+    setup = time.perf_counter() - t_set
+    cores = host_cores()
+    tf = tp = 0.0
+    n_s = 0
+    for _ in range(args.cpu_steps):
+        f, p, n_s = oracle_phases(osim, cores)
+        tf += f
+        tp += p
+    tf /= args.cpu_steps
+    tp /= args.cpu_steps
+    all_core = projected_rate(n_total, tf, tp, n_s)
+    from oracle import oracle as O
+    O.set_threads(1)
+    t0 = time.perf_counter()
+    for s in range(len(osim.species)):
+        osim.push(s)
+    osim.deposit()
+    tp1 = time.perf_counter() - t0
+    O.set_threads(cores)
+    one_core = projected_rate(n_total, tf, tp1, n_s)
+    sample = ("%s: the full %dx%d grid (field predict + advance, which the oracle runs on one "
+              "core, %.2f s per step) with the particles of %.1f%% of the cells (%d particles, "
+              "seeded), %d full steps on %d cores (push + deposit %.2f s per step) and the "
+              "particle phases of one more step on 1 core (%.2f s); particle phases scaled "
+              "to the %d particles of the workload; set-up %.0f s"
+              % (args.workload, cfg["n_r"], cfg["n_theta"], tf, 100 * args.cpu_frac, n_s,
+                 args.cpu_steps, cores, tp, tp1, n_total, setup))
+    return {"value": all_core, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+            "sample": sample, "one_core": {"value": one_core, "cores": 1},
+            "field_s_per_step": tf, "particle_s_per_sample_step": tp,
+            "particle_s_per_sample_step_1core": tp1, "sample_particles": n_s}
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the oracle timed on the host cores. Each step runs the particle
+    phases (push of both species + deposit) on a bounded sample of the workload's particles;
+    the field phases on the whole grid (one core in the oracle, several seconds at 2048^2)
+    are timed on the first timed step and charged to every step."""
     if rank != 0:
         return
     cfg = W.grid_config(args.workload)
     frac = args.ref_frac
+    n_total = 2 * cfg["n_r"] * cfg["n_theta"] * cfg["ppc"]
     osim = oracle_workload(cfg, frac)
+    cores = host_cores()
     n = sum(s.n for s in osim.species)
-    oracle_steps(osim, args.warmup)
-    times, parts = oracle_steps(osim, args.steps)
-    value = parts / sum(times)
+
+    def particles_only():
+        t0 = time.perf_counter()
+        for s in range(len(osim.species)):
+            osim.push(s)
+        osim.deposit()
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        particles_only()
+    tf, tp0, n = oracle_phases(osim, cores)
+    tps = [tp0] + [particles_only() for _ in range(args.steps - 1)]
+    step_s = [tf + t * n_total / n for t in tps]
+    value = n_total * len(step_s) / sum(step_s)
     line = {"metric": METRIC, "value": value,
             "unit": "particle-steps/s", "n_gpus": 0, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(step_s)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_desc(args.workload, cfg,
-                                                 2 * cfg["n_r"] * cfg["n_theta"] * cfg["ppc"])},
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": host_cores(),
+            "config": {"workload": workload_desc(args.workload, cfg, n_total)},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores,
                              "kind": "oracle",
-                             "sample": "full %dx%d grid with the particles of %.1f%% of the "
-                                       "cells (%d particles), %d warm-up + %d timed steps" % (
-                                           cfg["n_r"], cfg["n_theta"], 100 * frac, n,
-                                           args.warmup, args.steps)},
+                             "sample": "full %dx%d grid (field phases timed once, %.2f s, "
+                                       "charged to every step) with the particles of %.1f%% "
+                                       "of the cells (%d particles, push + deposit timed "
+                                       "every step, scaled to %d particles); %d warm-up + %d "
+                                       "timed steps" % (cfg["n_r"], cfg["n_theta"], tf,
+                                                         100 * frac, n, n_total, args.warmup,
+                                                         args.steps)},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU measurements
+# ---------------------------------------------------------------------------------------
+def device_facts(device):
+    import torch
+    p = torch.cuda.get_device_properties(device)
+    return {"name": p.name, "sms": int(p.multi_processor_count)}
+
+
+def measure_alu_peaks(device, launches=5):
+    """FMA throughput of the library's probe kernel (grpic_probe_fma), timed with CUDA events
+    on the current stream: FP64 (FMA thread operations/s, the FP64 pipe) and FP32 (as warp
+    instructions/s, the issue peak). Each launch runs ~0.1 s; the median of `launches`
+    launches after one warm-up."""
+    import torch
+
+    from paper_2511_17701_gb300.binding import probe_fma
+    stream = torch.cuda.current_stream(device)
+    sink = torch.zeros(1, dtype=torch.float64, device=device)
+    sms = device_facts(device)["sms"]
+    out = {}
+    for prec, iters in (("fp64", max(1, int(800 * 152 / sms))),
+                        ("fp32", max(1, int(50000 * 152 / sms)))):
+        probe_fma(prec, iters, 8, sink, stream)
+        rates = []
+        for _ in range(launches):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = probe_fma(prec, iters, 8, sink, stream)
+            e1.record(stream)
+            e1.synchronize()
+            rates.append(ops / (e0.elapsed_time(e1) * 1e-3))
+        out[prec] = float(np.median(rates))
+    return {"fp64_gops": out["fp64"] / 1e9, "warp_ginst": out["fp32"] / 32 / 1e9,
+            "fp32_gops": out["fp32"] / 1e9, "sms": sms}
 
 
 _PLASMA = {}
@@ -281,7 +407,7 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
         cfg["ppc"] = args.ppc
     cfg.update(extra or {})
     # the seeded plasma of a workload is drawn once per process (the two precisions and the
-    # photon run share it: drawing 377 M particles takes a minute and a half)
+    # photon run share it: drawing 134 M particles takes most of a minute)
     key = (workload, cfg["seed"] + 1000 * rank, cfg["ppc"], cfg["n_r"], cfg["n_theta"])
     if key not in _PLASMA:
         _PLASMA.clear()
@@ -295,6 +421,8 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
     for s in range(nsp):
         sim.load_particles(s, pl["pos"], pl["uhat"][s], pl["w0"], pl["qm"][s], pl["qc"][s],
                            pl["density_power"])
+    # nothing reads the previous positions inside the timed steps: the fused push skips them
+    sim.set_keep_prev(False)
     for _ in range(args.warmup):
         sim.step(1)
     sim.sync()
@@ -333,45 +461,13 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
     ms_max = allreduce_max(ws, ms, device)
     psteps = allreduce_sum(ws, psteps_local, device)
     value = psteps / (ms_max * 1e-3)
-
     # the dominant kernel, timed by the library's events around each launch on its stream
     calls = max(tim["push_calls"], 1)
     kernel_ms = tim["kernel_ms"] / calls
     parts_per_launch = 0.5 * (n_before + n_after) / nsp
-    peaks = measured_peaks()
-    hbm_peak = peaks.get("hbm_gbs")
-    bpp = FP64_BYTES_PER_PARTICLE_STEP if precision == "fp64" else MIXED_BYTES_PER_PARTICLE_STEP
-    hbm_achieved = parts_per_launch * bpp / (kernel_ms * 1e-3) / 1e9
-    if precision == "fp64":
-        refined = args.iter_tol > 0
-        ops = parts_per_launch * FP64_PIPE_OPS_PER_PARTICLE_STEP[refined] / (kernel_ms * 1e-3) / 1e9
-        roofline = {"bound": "alu", "achieved": ops, "peak": FP64_PIPE_PEAK_GOPS,
-                    "unit": "G FP64-pipe op/s", "frac": ops / FP64_PIPE_PEAK_GOPS,
-                    "traffic": None,
-                    "peak_source": "nominal: 2 FP64 operations/clk/SM x 152 SMs x 2.07 GHz",
-                    "tflops": parts_per_launch * FP64_FLOP_PER_PARTICLE_STEP[refined]
-                    / (kernel_ms * 1e-3) / 1e12,
-                    "kernel": "k_push<deposit> (fused FP64 push + deposit)"}
-    else:
-        gi = parts_per_launch * MIXED_WARP_INST_PER_PARTICLE / (kernel_ms * 1e-3) / 1e9
-        roofline = {"bound": "alu", "achieved": gi, "peak": ISSUE_PEAK_GINST,
-                    "unit": "G warp-instructions/s", "frac": gi / ISSUE_PEAK_GINST,
-                    "traffic": None,
-                    "peak_source": "nominal: 4 warp instructions/clk/SM x 152 SMs x 2.07 GHz",
-                    "kernel": "k_push32<deposit> (FP32 push + warp-reduced deposit; the "
-                              "guard-zone kernels run beside it on a second stream)"}
-    roofline["avg_launch_ms"] = kernel_ms
-    if (workload == "wald512" and args.iter_tol == 1e-12 and not photons and not extra
-            and not args.ppc):
-        roofline["traffic"] = TRAFFIC_BYTES_PER_PARTICLE[precision] * parts_per_launch
-        roofline["traffic_source"] = ("ncu dram bytes per particle of the same kernel on this "
-                                      "workload, times the particles of one launch")
-    hbm = {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak or 6800.0,
-           "frac": hbm_achieved / (hbm_peak or 6800.0),
-           "peak_source": "measured" if hbm_peak else "fallback",
-           "bytes_per_particle_step": bpp, "kernel": roofline["kernel"]}
-    out = {"value": value, "ms_per_step": ms_max / args.steps, "roofline": roofline,
-           "hbm_roofline": hbm,
+    ppc_total = nsp * cfg["ppc"]
+    out = {"value": value, "ms_per_step": ms_max / args.steps, "kernel_ms": kernel_ms,
+           "parts_per_launch": parts_per_launch, "ppc_total": ppc_total,
            "phase_ms_per_step": {k: tim[k] / args.steps for k in
                                  ("predict_ms", "sort_ms", "push_ms", "advance_ms")},
            "gpu_launches": tim["launches"], "clocks": clk.summary(),
@@ -379,6 +475,60 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
            "particles": nsp * n, "psteps": psteps, "timing": tim, "cfg": cfg,
            "pusher_ns_per_particle": push_ms * 1e6 / max(push_n, 1)}
     return out, sim
+
+
+def rooflines(out, precision, alu, args, photons=False):
+    """roofline (the bound that applies to the dominant kernel, against the peak measured in
+    this run), hbm_roofline (the dominant kernel's algorithmic bytes against the HBM peak)
+    and hbm_roofline_step (the whole step's algorithmic bytes per particle-step, grid
+    included, at the line's particle-steps/s)."""
+    kc = KERNEL_COUNTS[precision]
+    fresh = kc["src"] == kernel_src_digest() and not photons
+    kms, parts = out["kernel_ms"], out["parts_per_launch"]
+    sms = alu.get("sms")
+    mhz = out["clocks"].get("sm_mhz")
+    if precision == "fp64":
+        ach = parts * kc["fp64_ops"] / (kms * 1e-3) / 1e9
+        peak = alu.get("fp64_gops")
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G FP64-pipe op/s",
+                "frac": ach / peak if peak else None,
+                "peak_source": "measured in this run: grpic_probe_fma FP64 (8 independent "
+                               "FMA chains per thread, %d SMs x 8 blocks of 256 threads)" % sms,
+                "nominal_peak_at_sampled_clock": 2 * sms * mhz / 1e3 if (sms and mhz) else None,
+                "ops_per_particle": kc["fp64_ops"],
+                "tflops": parts * kc["flop"] / (kms * 1e-3) / 1e12,
+                "kernel": "k_push<deposit> (fused FP64 push + deposit)"}
+        bpp = FP64_BYTES_PER_PARTICLE_STEP
+    else:
+        ach = parts * kc["warp_inst"] / (kms * 1e-3) / 1e9
+        peak = alu.get("warp_ginst")
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G warp-instructions/s",
+                "frac": ach / peak if peak else None,
+                "peak_source": "measured in this run: grpic_probe_fma FP32 (one warp FMA "
+                               "instruction per clock per SM sub-partition), / 32 lanes",
+                "nominal_peak_at_sampled_clock": 4 * sms * mhz / 1e3 if (sms and mhz) else None,
+                "warp_inst_per_particle": kc["warp_inst"],
+                "kernel": "k_push32<deposit> (FP32 push + warp-reduced deposit; the "
+                          "guard-zone kernels run beside it on a second stream)"}
+        bpp = MIXED_BYTES_PER_PARTICLE_STEP
+    roof["avg_launch_ms"] = kms
+    roof["traffic"] = kc["dram_bytes"] * parts if (fresh and kc["dram_bytes"]) else None
+    roof["counts"] = ("ncu, kernel sources %s (%s)" % (kc["src"], kc["workload"]) if fresh else
+                      "stale: ncu counts of kernel sources %s, now %s"
+                      % (kc["src"] or "-", kernel_src_digest()))
+    hp, hsrc = hbm_peak()
+    gbs = parts * bpp / (kms * 1e-3) / 1e9
+    hbm = {"achieved_gbs": gbs, "peak_gbs": hp, "frac": gbs / hp, "peak_source": hsrc,
+           "bytes_per_particle_step": bpp, "kernel": roof["kernel"]}
+    step_bpp = bpp + GRID_BYTES_PER_CELL[precision] / out["ppc_total"]
+    sgbs = out["value"] * step_bpp / 1e9
+    step = {"achieved_gbs": sgbs, "peak_gbs": hp, "frac": sgbs / hp,
+            "bytes_per_particle_step": step_bpp,
+            "bytes": "%d B per particle (dominant kernel) + %d B per cell / %d particles per "
+                     "cell (field planes)" % (bpp, GRID_BYTES_PER_CELL[precision],
+                                              out["ppc_total"]),
+            "timed": "the line's particle-steps/s over the whole timed step"}
+    return roof, hbm, step
 
 
 # the particle state a step reads: position, momenta, phi, weight, tag (the previous
@@ -403,6 +553,7 @@ def end_to_end(args, sim, psteps, ws, device):
             ht.numpy()[:] = st[k]
             hs[k] = ht
         host.append((hs, len(st["i1"])))
+        del st
     bi = sum(n_s * sum(np.dtype(t).itemsize for _, t in types) for _, n_s in host)
     torch.cuda.synchronize(device)
     barrier(ws)
@@ -416,37 +567,127 @@ def end_to_end(args, sim, psteps, ws, device):
             "d2h_bytes_per_step": bi, "api": "grpic_step_host"}
 
 
+def mixed_step_error(sim64, sim32):
+    """Per-result error of one mixed-precision step against the FP64 path from the same
+    state: the mixed context's particles and planes after its timed steps are copied, widened,
+    into the FP64 context; both run predict, the push of each species, the deposit and the
+    advance; then per quantity the largest difference over all particles (positions x = i +
+    dx relative to max(1, |x|), momenta relative to |u_c| + median |u_c|, phi relative to
+    max(1, |phi|)) and per field plane the normwise difference. The FP64 path matches the
+    oracle to 1e-12 per step (tests), so these are the errors against the FP64 oracle to that
+    level."""
+    import torch
+
+    from paper_2511_17701_gb300 import NPLANES
+    for s in range(2):
+        v = sim32.species_views(s)
+        arrays = {k: (t.double() if t.dtype == torch.float32 else t.clone())
+                  for k, t in v.items()}
+        sim64.set_particles(s, arrays, sim32.qm[s], sim32.qc[s])
+        del arrays
+    for k in range(NPLANES):
+        sim64.plane(k).copy_(sim32.plane(k))
+    for sim in (sim64, sim32):
+        sim.set_keep_prev(True)
+        sim.predict()
+        for s in range(2):
+            sim.push(s)
+        sim.deposit()
+        sim.advance()
+        sim.sync()
+    err = {}
+    for s in range(2):
+        a, b = sim32.species_views(s), sim64.species_views(s)
+        if not torch.equal(a["tag"], b["tag"]):
+            err["tag_mismatch_species_%d" % s] = int((a["tag"] != b["tag"]).sum())
+        for i, d in (("i1", "dx1"), ("i2", "dx2")):
+            xa = a[i].double() + a[d].double()
+            xb = b[i].double() + b[d]
+            e = float(((xa - xb).abs() / xb.abs().clamp(min=1.0)).max())
+            err["x" + i[1]] = max(err.get("x" + i[1], 0.0), e)
+        for c in ("u1", "u2", "u3"):
+            sc = float(b[c].abs().median())
+            e = float(((a[c].double() - b[c]).abs() / (b[c].abs() + sc + 1e-300)).max())
+            err[c] = max(err.get(c, 0.0), e)
+        e = float(((a["phi"].double() - b["phi"]).abs() / b["phi"].abs().clamp(min=1.0)).max())
+        err["phi"] = max(err.get("phi", 0.0), e)
+    names = {0: "B1", 1: "B2", 2: "B3", 3: "D1", 4: "D2", 5: "D3"}
+    for k, nm in names.items():
+        pa, pb = sim32.plane(k).double(), sim64.plane(k)
+        err["plane_" + nm] = float((pa - pb).abs().max() / pb.abs().max().clamp(min=1e-300))
+    return err
+
+
+def invariant_drift(device, steps=10000):
+    """Relative drift of the conserved energy and angular momentum (Sec. 2.3) of 4096 test
+    particles over `steps` pushes in the frozen Wald field, FP64 and mixed: a = 0.9 on a
+    128^2 grid, r in [0.95 r_h, 20], particles at x1 in [40, 100], x2 in [20, 108],
+    tetrad-frame |u| uniform in [0, 0.5]; the largest and the median |E1/E0 - 1|, |L1/L0 - 1|
+    over the particles that stay inside (x1 in (10, 118))."""
+    import torch
+
+    from paper_2511_17701_gb300 import FIELD_WALD, Sim
+    cfg = W.grid_config("wald64", n_r=128, n_theta=128, r_max=20.0, r_absorb=1e300)
+    tp = W.probe_particles(cfg, 4096, 7, (40.0, 100.0), (20.0, 108.0), 0.5)
+    qm, qc = W.species_coefficients(1.0)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        sim = Sim(dict(cfg, precision=prec), [4096], device=device)
+        sim.init_metric()
+        sim.init_fields(FIELD_WALD, 1.0)
+        sim.load_particles(0, tp["pos"], tp["uhat"], tp["w0"], qm, qc)
+        sim.predict()
+        sim.push(0)
+        E0, L0 = sim.invariants(0, FIELD_WALD, 1.0)
+        for _ in range(steps - 1):
+            sim.push(0)
+        E1, L1 = sim.invariants(0, FIELD_WALD, 1.0)
+        p = sim.get_particles(0)
+        keep = (p["tag"] == 1) & (p["i1"] > 10) & (p["i1"] < 118)
+        dE = np.abs(E1[keep] / E0[keep] - 1)
+        dL = np.abs(L1[keep] / L0[keep] - 1)
+        out[prec] = {"E_max": float(dE.max()), "E_median": float(np.median(dE)),
+                     "L_max": float(dL.max()), "L_median": float(np.median(dL)),
+                     "particles": int(keep.sum())}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    out["mixed_over_fp64"] = {k: out["mixed"][k] / out["fp64"][k]
+                              for k in ("E_max", "E_median", "L_max", "L_median")}
+    out["setup"] = ("4096 test particles, frozen Wald field (a = 0.9, 128^2 grid, r in [0.95 "
+                    "r_h, 20]), %d pushes" % steps)
+    return out
+
+
 def run_gpu(args, ws, rank, local):
     import torch
 
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
+    alu = measure_alu_peaks(device) if not args.no_probe else {"sms": device_facts(device)["sms"]}
     precisions = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
-    res = {}
+    res, sims = {}, {}
     e2e = None
     for prec in precisions:
         out, sim = measure(args, prec, ws, rank, local)
         if prec == precisions[0] and not args.no_e2e:
             e2e = end_to_end(args, sim, out["psteps"], ws, device)
-        del sim
-        torch.cuda.empty_cache()
         res[prec] = out
+        sims[prec] = sim
+    err = None
+    if len(precisions) == 2 and not args.no_error:
+        err = mixed_step_error(sims["fp64"], sims["mixed"])
+    for s in sims.values():
+        s.close()
+    del sims
+    torch.cuda.empty_cache()
+    drift = invariant_drift(device) if len(precisions) == 2 and not args.no_drift else None
     main = res[precisions[0]]
+    roof, hbm, step = rooflines(main, precisions[0], alu, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        ocfg = W.grid_config(args.workload)
-        if args.ppc:
-            ocfg["ppc"] = args.ppc
-        osim = oracle_workload(ocfg, args.cpu_frac)
-        times, parts = oracle_steps(osim, args.cpu_steps)
-        cpu = {"value": parts / sum(times), "unit": "particle-steps/s", "cores": host_cores(),
-               "kind": "oracle",
-               "sample": "%d full FP64 PIC steps of the %s workload (%d particles%s), %.1f s" % (
-                   args.cpu_steps, args.workload, parts // max(args.cpu_steps, 1),
-                   "" if args.cpu_frac >= 1 else ", particles of %.1f%% of the cells"
-                   % (100 * args.cpu_frac), sum(times))}
-        del osim
+        cpu = cpu_baseline(args)
     if rank == 0:
         line = {"metric": METRIC, "precision": precisions[0],
                 "value": main["value"], "unit": "particle-steps/s", "n_gpus": ws,
@@ -458,9 +699,10 @@ def run_gpu(args, ws, rank, local):
                            "sort_every": args.sort_every, "tile": args.tile,
                            "iter_tol": args.iter_tol,
                            "l2": "inputs larger than L2: particle state %.2f GB" % (
-                               main["particles"] * (89 if precisions[0] == "fp64" else 49) / 1e9),
+                               main["particles"] * (65 if precisions[0] == "fp64" else 37) / 1e9),
                            "parallelism": "replica per GPU" if ws > 1 else "1 GPU"},
-                "roofline": main["roofline"], "hbm_roofline": main["hbm_roofline"],
+                "roofline": roof, "hbm_roofline": hbm, "hbm_roofline_step": step,
+                "alu_peaks_measured": alu,
                 "phase_ms_per_step": main["phase_ms_per_step"],
                 "pusher_ns_per_particle": main["pusher_ns_per_particle"],
                 "gpu_launches": main["gpu_launches"], "e2e": e2e, "cpu_baseline": cpu,
@@ -470,20 +712,28 @@ def run_gpu(args, ws, rank, local):
                 "pusher_ns_per_particle": 6.2, "hardware": "1x A100, precision not stated",
                 "workload": "BZ monopole test, 2048^2 log-r mesh, 90 particles per cell "
                             "(Sec. 3.5)"}
+        else:
+            line["paper_context"] = {
+                "pusher_ns_per_particle": 6.2, "hardware": "1x A100, precision not stated",
+                "workload": "BZ monopole test, 2048^2 log-r mesh, 90 particles per cell "
+                            "(Sec. 3.5); bench.py --workload bz2048 times that shape"}
         if len(precisions) == 2:
             m = res["mixed"]
+            mroof, mhbm, mstep = rooflines(m, "mixed", alu, args)
             line["mixed"] = {"value": m["value"], "unit": "particle-steps/s",
                              "ms_per_step": m["ms_per_step"],
                              "speedup_vs_fp64": m["value"] / main["value"],
-                             "workload": m["workload"], "roofline": m["roofline"],
-                             "hbm_roofline": m["hbm_roofline"],
+                             "workload": m["workload"], "roofline": mroof,
+                             "hbm_roofline": mhbm, "hbm_roofline_step": mstep,
                              "phase_ms_per_step": m["phase_ms_per_step"],
                              "pusher_ns_per_particle": m["pusher_ns_per_particle"],
                              "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
-                             "error_bound": "<= 1e-5 relative per step on particle state vs "
-                                            "the FP64 oracle (tests/test_gpu_mixed.py)"}
+                             "error_per_step_vs_fp64": err,
+                             "error_bound": "<= 1e-5 relative per step on particle state "
+                                            "(north-star bound; the FP64 path is the oracle "
+                                            "to 1e-12)",
+                             "invariant_drift": drift}
         print(json.dumps(line), flush=True)
-
 
 def run_extensions(args, ws, rank, local):
     """The rows beyond the base path, each on the bench's grid: (1) massless particles: one
@@ -496,8 +746,7 @@ def run_extensions(args, ws, rank, local):
     import torch
 
     torch.cuda.set_device(local)
-    peaks = measured_peaks()
-    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    alu = measure_alu_peaks(torch.device("cuda", local))
     out = {"metric": "extensions: massless particles, the current filter, pair injection, "
                      "quasi-spherical grids",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup}
@@ -512,11 +761,11 @@ def run_extensions(args, ws, rank, local):
         torch.cuda.empty_cache()
         ph[prec] = {"photon_steps_per_s": phot["value"],
                     "pair_particle_steps_per_s": pairs["value"],
-                    "push_kernel_ns_per_photon": phot["roofline"]["avg_launch_ms"] * 1e6 /
-                    (phot["particles"]),
-                    "push_kernel_ns_per_pair_particle": pairs["roofline"]["avg_launch_ms"] * 1e6 /
+                    "push_kernel_ns_per_photon": phot["kernel_ms"] * 1e6 / (phot["particles"]),
+                    "push_kernel_ns_per_pair_particle": pairs["kernel_ms"] * 1e6 /
                     (pairs["particles"] / 2),
-                    "photon_hbm_gbs": phot["hbm_roofline"]["achieved_gbs"],
+                    "photon_hbm_gbs": rooflines(phot, prec, alu, args, photons=True)[1][
+                        "achieved_gbs"],
                     "clocks": phot["clocks"], "workload": phot["workload"]}
     if ph:
         out["massless"] = ph
@@ -537,9 +786,9 @@ def run_extensions(args, ws, rank, local):
             "note": "3 current planes read and written once per step (one launch runs the 4 "
                     "passes in shared memory); at 512^2 the planes (12.8 MB) stay in L2"}
     if "filter2048" in parts:
-        out["filter_wald2048"] = measure_filter_2048(args, ws, rank, local, peaks)
+        out["filter_wald2048"] = measure_filter_2048(args, ws, rank, local, alu)
     if "inject" in parts:
-        out["inject_bz2048"] = measure_injection(args, local, peaks)
+        out["inject_bz2048"] = measure_injection(args, local)
     if "qks" in parts:
         # the bench workload on a quasi-spherical grid (App. A): r0 = 0.4, h0 = 0.45
         q = {}
@@ -551,21 +800,21 @@ def run_extensions(args, ws, rank, local):
             torch.cuda.empty_cache()
             q[prec] = {"particle_steps_per_s": qk["value"], "plain_grid": base["value"],
                        "ratio": qk["value"] / base["value"],
-                       "push_kernel_ms": qk["roofline"]["avg_launch_ms"],
-                       "push_kernel_ms_plain": base["roofline"]["avg_launch_ms"],
+                       "push_kernel_ms": qk["kernel_ms"],
+                       "push_kernel_ms_plain": base["kernel_ms"],
                        "clocks": qk["clocks"]}
         out["qks_wald512"] = q
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def measure_filter_2048(args, ws, rank, local, peaks):
+def measure_filter_2048(args, ws, rank, local, alu):
     """The filter kernel against the FP64 pipe and HBM: 2048^2 planes (33.7 MB each, above
     L2), 8 passes in one launch, on the wald2048 grid with args.ext_ppc particles per cell
     per species."""
     import torch
 
-    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    hp, hsrc = hbm_peak()
     big, sim = measure(args, "fp64", ws, rank, local, workload="wald2048",
                        extra={"n_filter": 8, "ppc": args.ext_ppc or 1})
     del sim
@@ -580,17 +829,17 @@ def measure_filter_2048(args, ws, rank, local, peaks):
     return {
         "n_filter": 8, "filter_ms_per_step": f_ms, "algorithmic_bytes_per_launch": 6 * plane,
         "algorithmic_fp64_ops_per_launch": 4 * 8 * 3 * (plane // 8),
-        "roofline": {"bound": "alu", "achieved": ops, "peak": FP64_PIPE_PEAK_GOPS,
-                     "unit": "G FP64-pipe op/s", "frac": ops / FP64_PIPE_PEAK_GOPS,
+        "roofline": {"bound": "alu", "achieved": ops, "peak": alu["fp64_gops"],
+                     "unit": "G FP64-pipe op/s", "frac": ops / alu["fp64_gops"],
                      "traffic": None,
-                     "peak_source": "nominal: 2 FP64 operations/clk/SM x 152 SMs x 2.07 GHz",
+                     "peak_source": "measured in this run: grpic_probe_fma FP64",
                      "kernel": "k_filter<double> (8 passes fused in shared memory)"},
-        "hbm_roofline": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
-                         "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"},
+        "hbm_roofline": {"achieved_gbs": gbs, "peak_gbs": hp, "frac": gbs / hp,
+                         "peak_source": hsrc},
         "clocks": big["clocks"]}
 
 
-def measure_injection(args, local, peaks):
+def measure_injection(args, local):
     """Pair injection (Sec. 4.5) on the 2048^2 monopole grid with 4 particles per cell per
     species (33.6 M particles; args.ext_ppc when given): a full FP64 step followed by
     grpic_inject with sigma_th = 2000, args.steps times after args.warmup; the injection's
@@ -642,7 +891,7 @@ def measure_injection(args, local, peaks):
     inj_ms = tim["inject_ms"] / args.steps
     parts = 0.5 * (n0 + n1)
     bytes_ = parts * 17 + nc * (3 * 8 + 24)
-    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    hp, _ = hbm_peak()
     gbs = bytes_ / (inj_ms * 1e-3) / 1e9
     del sim
     torch.cuda.empty_cache()
@@ -652,8 +901,8 @@ def measure_injection(args, local, peaks):
             "pairs_added_per_step": d["injected"] / args.steps,
             "inject_ms_per_call": inj_ms, "step_plus_inject_ms": ms,
             "share_of_step": inj_ms / ms,
-            "hbm_roofline": {"achieved_gbs": gbs, "peak_gbs": hbm_peak,
-                             "frac": gbs / hbm_peak,
+            "hbm_roofline": {"achieved_gbs": gbs, "peak_gbs": hp,
+                             "frac": gbs / hp,
                              "algorithmic_bytes_per_call": bytes_}}
 
 
@@ -884,17 +1133,18 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="wald512", choices=sorted(W.CONFIGS))
+    ap.add_argument("--workload", default=None, choices=sorted(W.CONFIGS),
+                    help="default wald2048 (--extensions: wald512)")
     ap.add_argument("--sort-every", type=int, default=10)
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"],
                     help="both: FP64 (the line's value) and then mixed on the same workload")
     ap.add_argument("--ppc", type=int, default=0, help="override particles per cell per species "
                     "(a smaller case of the same workload, e.g. for profiling)")
-    ap.add_argument("--cpu-frac", type=float, default=1.0,
+    ap.add_argument("--cpu-frac", type=float, default=0.03,
                     help="fraction of the cells whose particles the CPU baseline pushes")
     ap.add_argument("--cpu-steps", type=int, default=2)
-    ap.add_argument("--ref-frac", type=float, default=0.25,
+    ap.add_argument("--ref-frac", type=float, default=0.01,
                     help="fraction of the cells whose particles the reference arm pushes")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the adjoint of the pusher over a frozen field instead")
@@ -924,7 +1174,15 @@ def main():
     ap.add_argument("--bz-precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-probe", action="store_true",
+                    help="skip the FMA-throughput probe (the ALU rooflines then have no peak)")
+    ap.add_argument("--no-error", action="store_true",
+                    help="skip the mixed path's per-step error against the FP64 path")
+    ap.add_argument("--no-drift", action="store_true",
+                    help="skip the 10^4-step invariant drift of test particles")
     args = ap.parse_args()
+    if args.workload is None:
+        args.workload = "wald512" if args.extensions else "wald2048"
     ws, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -473,6 +473,31 @@ typedef struct {
   double inject_ms;     /* grpic_inject                                               */
 } grpic_timing;
 
+/* Step 1 of Sec. 3.1 saves each particle's previous position for the deposit. A push that
+ * deposits its own move (the fused push + deposit of grpic_step and grpic_step_host) reads
+ * it from registers, so storing it only serves later calls that read the previous positions
+ * (grpic_deposit, grpic_invariants, grpic_charge_check). keep = 1 (the default): the fused
+ * push stores them (i1p, i2p, dx1p, dx2p, 16 or 24 bytes per particle); keep = 0: it skips
+ * the stores, and until the next grpic_push, grpic_load_particles or grpic_set_particles of a
+ * species those three calls return GRPIC_ESTATE and the previous-position arrays returned by
+ * grpic_get_particles are stale. grpic_push (no deposit) always stores them. Errors:
+ * GRPIC_EINVAL (null ctx). */
+GRPIC_API grpic_status grpic_set_keep_prev(grpic_ctx *ctx, int keep);
+
+/* Throughput probe of the arithmetic pipes that bound the pusher kernels; no counterpart in
+ * the paper (it supplies the measured denominator of their rooflines). Queues on `stream`
+ * (cudaStream_t; null: the default stream) one kernel of blocks_per_sm x (SM count) blocks of
+ * 256 threads on the current device, each thread running 8 independent FMA chains of
+ * 32 x iters steps: precision GRPIC_FP64 in double (the FP64 pipe's FMA rate), GRPIC_MIXED in
+ * float (the FP32 pipe, at one warp instruction per clock per SM sub-partition, i.e. the
+ * instruction-issue peak). *ops receives the FMA operations the launch performs; time it
+ * with events on the stream. sink: one device double, never written in practice (it keeps
+ * the chains live). Allocates nothing. Errors: GRPIC_EINVAL (iters < 1, blocks_per_sm not
+ * in 1 .. 64, null sink or ops, other precision), GRPIC_ECUDA (a CUDA error pending before
+ * the call, which it leaves in place, or a failed launch). */
+GRPIC_API grpic_status grpic_probe_fma(int precision, int64_t iters, int blocks_per_sm,
+                                       double *sink, void *stream, int64_t *ops);
+
 /* Enables (1) or disables (0) the per-phase events. Off by default. Instrumentation, with
  * no counterpart in the paper (as the timing and diagnostics calls below). */
 GRPIC_API grpic_status grpic_set_timing(grpic_ctx *ctx, int enable);

@@ -20,6 +20,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define G ORA_G
 
@@ -1148,3 +1151,19 @@ void ora_aux_fields(const ora_params *p, const double *F, double *E, double *H) 
 }
 
 int ora_version(void) { return 6; }
+
+/* Threads of the OpenMP loops (the particle push and the charge sums); timing only. */
+void ora_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+int ora_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

@@ -98,6 +98,9 @@ def lib():
         L.ora_u_lower0.restype = C.c_double
         L.ora_invariants.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                      _PD, _PD]
+        L.ora_set_threads.argtypes = [C.c_int]
+        L.ora_set_threads.restype = None
+        L.ora_max_threads.restype = C.c_int
         L.ora_time_step.argtypes = [P, C.c_double]
         L.ora_time_step.restype = C.c_double
         L.ora_init_fields.argtypes = [P, _PD, C.c_int, C.c_double]
@@ -189,6 +192,15 @@ def invariants(cfg, kind, B0, qm, x1, x2, u):
     lib().ora_invariants(C.byref(make_params(cfg)), kind, B0, qm, x1, x2,
                          _dp(np.asarray(u, np.float64)), _dp(out))
     return out
+
+
+def set_threads(n: int):
+    """Threads of the oracle's OpenMP loops (for timing it on 1 or all host cores)."""
+    lib().ora_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().ora_max_threads())
 
 
 def time_step(cfg, cfl):

@@ -31,7 +31,8 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_get_diagnostics", "grpic_set_timing", "grpic_get_timing", "grpic_last_error",
            "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants",
            "grpic_adjoint_forward", "grpic_adjoint_backward", "grpic_charge_check",
-           "grpic_config_bytes", "grpic_inject", "grpic_step_host", "grpic_aux_fields"]
+           "grpic_config_bytes", "grpic_inject", "grpic_step_host", "grpic_aux_fields",
+           "grpic_set_keep_prev", "grpic_probe_fma"]
 
 
 ADJOINT_SCRATCH_PER_STEP = 36  # doubles per particle and step of grpic_adjoint_backward
@@ -125,6 +126,8 @@ def lib(build: bool = True):
         L.grpic_aux_fields.argtypes = [P, C.c_void_p * 3, C.c_void_p * 3]
         L.grpic_get_diagnostics.argtypes = [P, C.POINTER(Diag)]
         L.grpic_set_timing.argtypes = [P, C.c_int]
+        L.grpic_set_keep_prev.argtypes = [P, C.c_int]
+        L.grpic_probe_fma.argtypes = [C.c_int, C.c_int64, C.c_int, P, P, C.POINTER(C.c_int64)]
         L.grpic_get_timing.argtypes = [P, C.POINTER(Timing)]
         L.grpic_last_error.argtypes = [P]
         L.grpic_last_error.restype = C.c_char_p
@@ -459,6 +462,10 @@ class Sim:
                 "alive": [d.alive[i] for i in range(self.n_species)],
                 "injected": d.injected, "inject_dropped": d.inject_dropped}
 
+    def set_keep_prev(self, keep: bool):
+        """grpic_set_keep_prev: whether the fused push + deposit stores previous positions."""
+        self._check(self.L.grpic_set_keep_prev(self.ctx, int(bool(keep))), "set_keep_prev")
+
     def set_timing(self, on: bool):
         self._check(self.L.grpic_set_timing(self.ctx, int(bool(on))), "set_timing")
 
@@ -469,3 +476,16 @@ class Sim:
 
     def sync(self):
         self.stream.synchronize()
+
+
+def probe_fma(precision: str, iters: int, blocks_per_sm: int, sink, stream) -> int:
+    """grpic_probe_fma: queue the FMA-throughput probe kernel on `stream` (a torch stream);
+    sink: a float64 device tensor of at least one element. Returns the FMA operations the
+    launch performs (threads x chains x iters)."""
+    ops = C.c_int64()
+    st = lib().grpic_probe_fma(MIXED if precision == "fp32" else FP64, int(iters),
+                               int(blocks_per_sm), sink.data_ptr(), stream.cuda_stream,
+                               C.byref(ops))
+    if st != OK:
+        raise GrpicError("grpic_probe_fma failed (status %d)" % st)
+    return ops.value

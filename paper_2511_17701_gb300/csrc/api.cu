@@ -35,6 +35,9 @@ struct SpeciesState {
   size_t off_tiles = 0;       // tile ranges of the last sort (mixed path)
   uint32_t *tile_start = nullptr;
   bool tiles_valid = false;
+  // the previous-position arrays hold the positions before the last push (false after a
+  // fused push + deposit that did not store them)
+  bool prev_valid = true;
 };
 
 size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
@@ -94,6 +97,7 @@ struct grpic_ctx {
   unsigned long long *diag = nullptr;
   int64_t step = 0;
   bool timing = false;
+  bool keep_prev = true;  // the fused push + deposit stores the previous positions
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PH_N];
   size_t ev_used[PH_N] = {};
   int64_t push_calls = 0;
@@ -263,9 +267,16 @@ cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, int k, bool deposit, int sta
   const int ntr = (c->g.n_r + tr - 1) / tr, ntt = (c->g.n_th + tt - 1) / tt;
   const TileInfo ti{sp.tiles_valid && c->cfg.tiled_push ? sp.tile_start : nullptr, tr, tt, ntr,
                     ntr * ntt};
+  // step 1 of Sec. 3.1 stores the previous position for the deposit; a push that deposits
+  // its own move needs it only when a later call reads it (grpic_set_keep_prev): null
+  // previous-position arrays tell the kernels to skip the stores
+  SpeciesDevT<T> v = dev_view<T>(sp, sp.live);
+  const bool write_prev = !deposit || c->keep_prev;
+  if (!write_prev) v.i1p = v.i2p = nullptr, v.dx1p = v.dx2p = nullptr;
+  if (stage != PUSH_GUARD) sp.prev_valid = write_prev;
   // massless particles are neutral: their push deposits nothing
-  return launch_push<T>(c->g, F, dev_view<T>(sp, sp.live), c->tb, sp.gl, ti, sp.n_bound,
-                        deposit && !sp.massless, c->diag, ps);
+  return launch_push<T>(c->g, F, v, c->tb, sp.gl, ti, sp.n_bound, deposit && !sp.massless,
+                        c->diag, ps);
 }
 // the main stream waits for the guard kernels of species k (mixed path)
 cudaError_t join_push(grpic_ctx *c, int k) {
@@ -592,6 +603,7 @@ grpic_status grpic_load_particles(grpic_ctx *ctx, int species, int64_t n, double
   CK(cudaGetLastError());
   sp.n_bound = n;
   sp.loaded = true;
+  sp.prev_valid = true;
   sp.tiles_valid = false;  // new particles: no tile ranges until the next sort
   return GRPIC_OK;
 }
@@ -629,6 +641,7 @@ grpic_status grpic_set_particles(grpic_ctx *ctx, int species, int64_t n, double 
   CK(cudaGetLastError());
   sp.n_bound = n;
   sp.loaded = true;
+  sp.prev_valid = true;
   sp.tiles_valid = false;  // new particles: no tile ranges until the next sort
   return GRPIC_OK;
 }
@@ -693,11 +706,21 @@ grpic_status grpic_plane_ptr(grpic_ctx *ctx, int plane, void **out) {
   return GRPIC_OK;
 }
 
+// the entry points that read the previous positions refuse them when the last push did not
+// store them
+static grpic_status need_prev(grpic_ctx *ctx, int k) {
+  if (ctx->sp[k].loaded && !ctx->sp[k].prev_valid)
+    return fail(ctx, GRPIC_ESTATE, "species %d: the last push did not store the previous "
+                "positions (grpic_set_keep_prev)", k);
+  return GRPIC_OK;
+}
+
 grpic_status grpic_invariants(grpic_ctx *ctx, int species, int kind, double B0, double *E,
                               double *L) {
   grpic_status s = need_bound(ctx);
   if (s) return s;
   if ((s = need_species(ctx, species))) return s;
+  if ((s = need_prev(ctx, species))) return s;
   if (!ctx->metric_ready) return fail(ctx, GRPIC_ESTATE, "metric not initialised");
   if (!E || !L) return fail(ctx, GRPIC_EINVAL, "null output");
   SpeciesState &sp = ctx->sp[species];
@@ -727,6 +750,8 @@ grpic_status grpic_push(grpic_ctx *ctx, int species) {
 grpic_status grpic_deposit(grpic_ctx *ctx) {
   grpic_status s = need_fields(ctx);
   if (s) return s;
+  for (int k = 0; k < ctx->cfg.n_species; ++k)
+    if (!ctx->sp[k].massless && (s = need_prev(ctx, k))) return s;
   PhaseTimer t(ctx, PH_DEPOSIT);
   if (ctx->mixed) CK(do_zero_J(ctx, ctx->F32));
   else CK(do_zero_J(ctx, ctx->F64));
@@ -1053,6 +1078,8 @@ grpic_status grpic_charge_check(grpic_ctx *ctx, int after_step, double out[4]) {
   grpic_status s = need_fields(ctx);
   if (s) return s;
   if (!out) return GRPIC_EINVAL;
+  for (int k = 0; k < ctx->cfg.n_species; ++k)
+    if (!ctx->sp[k].massless && (s = need_prev(ctx, k))) return s;
   double *dev = at<double>(ctx, ctx->off_rho + 6 * up((size_t)plane_size(ctx->g) * 8));
   if (ctx->mixed) CK(charge_check(ctx, ctx->F32, after_step != 0, dev));
   else CK(charge_check(ctx, ctx->F64, after_step != 0, dev));
@@ -1119,6 +1146,12 @@ grpic_status grpic_get_diagnostics(grpic_ctx *ctx, grpic_diag *out) {
   out->nonfinite = (int64_t)h[DG_NONFINITE];
   out->injected = (int64_t)h[DG_INJECTED];
   out->inject_dropped = (int64_t)h[DG_INJECT_DROPPED];
+  return GRPIC_OK;
+}
+
+grpic_status grpic_set_keep_prev(grpic_ctx *ctx, int keep) {
+  if (!ctx) return GRPIC_EINVAL;
+  ctx->keep_prev = keep != 0;
   return GRPIC_OK;
 }
 

@@ -945,8 +945,9 @@ __global__ void __launch_bounds__(TPB, DEPOSIT ? GRPIC_PUSH64_MIN_BLOCKS : 3) k_
   const int64_t n = *s.n;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const int i1 = s.i1[k], i2 = s.i2[k];
-    s.i1p[k] = i1; s.i2p[k] = i2; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+    if (s.i1p) {  // step 1: the previous position, when a later call reads it
+      s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+    }
     const uint8_t tag = s.tag[k];
     if (tag != 1) {
       if (tag != 0) s.tag[k] = 0;
@@ -1042,8 +1043,9 @@ __global__ void __launch_bounds__(TPB, 12) k_push32(GridP g, FieldPtrsT<float> F
     Move32 mv;
     bool on = false;
     if (k < n && !((__ldg(gl.mask + (k >> 5)) >> lane) & 1u)) {
-      const int i1 = s.i1[k], i2 = s.i2[k];
-      s.i1p[k] = i1; s.i2p[k] = i2; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+      if (s.i1p) {
+        s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+      }
       const uint8_t tag = s.tag[k];
       if (tag == 1) on = push32<Q, false>(g, GlobalFields(g, F), tb, s, k, diag, mv);
       else if (tag != 0) s.tag[k] = 0;
@@ -1091,11 +1093,13 @@ __global__ void __launch_bounds__(TILE_TPB) k_push32_tiled(GridP g, FieldPtrsT<f
     Move32 mv;
     bool on = false;
     if (k < end && !((__ldg(gl.mask + (k >> 5)) >> (k & 31)) & 1u)) {
-      const int i1 = s.i1[k], i2 = s.i2[k];
-      s.i1p[k] = i1; s.i2p[k] = i2; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+      if (s.i1p) {
+        s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+      }
       const uint8_t tag = s.tag[k];
       if (tag == 1) {
         // the interpolation reads cells i +- 1, j +- 1
+        const int i1 = s.i1[k], i2 = s.i2[k];
         const bool inside = i1 - 1 >= iw0 && i1 + 1 < iw0 + W1 && i2 - 1 >= jw0 && i2 + 1 < jw0 + W2;
         on = inside ? push32<Q, false>(g, wf, tb, s, k, diag, mv)
                     : push32<Q, false>(g, gf, tb, s, k, diag, mv);
@@ -1135,7 +1139,9 @@ __global__ void __launch_bounds__(32, GRPIC_GUARD_MIN_BLOCKS) k_push_guard(GridP
     bool on = false;
     if (t < n) {
       const int64_t k = gl.idx[t];
-      s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+      if (s.i1p) {
+        s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+      }
       on = push32<Q, true>(g, GlobalFields(g, F), tb, s, k, diag, mv);
     }
     if (DEPOSIT) deposit32_warp(g, GlobalSink(g, F), mv, on);
@@ -1150,7 +1156,9 @@ __global__ void __launch_bounds__(32, GRPIC_AXIS_MIN_BLOCKS) k_push_axis(GridP g
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = gl.idx[gl.cap - 1 - t];
-    s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+    if (s.i1p) {
+      s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
+    }
     push64<Q, float, DEPOSIT>(g, F, tb, s, k, diag);
   }
 }

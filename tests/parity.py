@@ -71,11 +71,14 @@ def assert_currents(Fg, Fo, rtol=RTOL):
         assert np.all(d <= lim), ("J%d" % (c + 1), float((d / (Fo[O.JA1 + c] + 1e-300)).max()))
 
 
-def assert_particles(pg: dict, po: dict, rtol=RTOL, exact_order=True):
+def assert_particles(pg: dict, po: dict, rtol=RTOL, exact_order=True, prev=True):
+    """prev: also compare the previous positions (False after a fused step that skipped
+    storing them, grpic_set_keep_prev(0))."""
     n = len(po["i1"])
     assert len(pg["i1"]) == n
     assert np.array_equal(pg["tag"], po["tag"])
-    for a, b in (("i1", "dx1"), ("i2", "dx2"), ("i1p", "dx1p"), ("i2p", "dx2p")):
+    pairs = (("i1", "dx1"), ("i2", "dx2")) + ((("i1p", "dx1p"), ("i2p", "dx2p")) if prev else ())
+    for a, b in pairs:
         xg = pg[a].astype(np.float64) + pg[b]
         xo = po[a].astype(np.float64) + po[b]
         err = np.abs(xg - xo) / np.maximum(1.0, np.abs(xo))

@@ -1,6 +1,7 @@
 """Parity at the workloads' full sizes, in the launch configuration the bench times (a sort
-every 10 steps in 16 x 16 tiles, so the first step sorts; fused push + deposit; the FP64
-implicit iterations refined from an FP32 predictor to iter_tol = 1e-12).
+every 10 steps in 16 x 16 tiles, so the first step sorts; fused push + deposit that stores no
+previous positions; the FP64 implicit iterations refined from an FP32 predictor to iter_tol =
+1e-12).
 
 * wald512 (512^2, 16,777,216 particles): one full step on both sides, every particle and
   every field plane compared, in FP64 (1e-12) and in mixed precision (1e-5 against the
@@ -37,11 +38,12 @@ def test_wald512_full_step_fp64(torch_cuda):
     cfg = W.grid_config("wald512", **BENCH)
     osim = oracle_state(cfg)
     g = gpu_from_oracle(osim)
+    g.set_keep_prev(False)
     g.step(1)
     osim.step(1, sort_every=10, tr=16, tt=16)
     assert_planes(g.planes(), osim.F, planes=AFTER_ADVANCE, what="wald512 step")
     for s in range(2):
-        assert_particles(g.get_particles(s), osim.species[s].view())
+        assert_particles(g.get_particles(s), osim.species[s].view(), prev=False)
 
 
 def test_wald512_full_step_mixed(torch_cuda):
@@ -49,6 +51,7 @@ def test_wald512_full_step_mixed(torch_cuda):
     osim = oracle_state(cfg)
     round_state_fp32(osim)
     g = gpu_from_oracle(osim, precision="mixed")
+    g.set_keep_prev(False)
     g.step(1)
     osim.step(1, sort_every=10, tr=16, tt=16)
     for s in range(2):

@@ -327,3 +327,37 @@ def test_set_particles_without_previous_position(torch_cuda):
     g.push(0)
     osim.push(0)
     assert_particles(g.get_particles(0), sp.view())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fused_step_without_previous_positions(torch_cuda, precision):
+    """grpic_set_keep_prev(0): the fused push + deposit skips the previous-position stores.
+    From the same state the particles come out with the same bits (only the stores differ),
+    the fields within the parity bound (atomic order), and the calls that read the previous
+    positions refuse them until a separate push stores them again."""
+    from paper_2511_17701_gb300 import FIELD_WALD, GrpicError
+    cfg = dict(BASE, precision=precision, sort_every=1, tile_r=8, tile_theta=8)
+    osim = oracle_state(cfg)
+    if precision == "mixed":
+        from parity import round_state_fp32
+        round_state_fp32(osim)
+    a, b = gpu_from_oracle(osim), gpu_from_oracle(osim)
+    b.set_keep_prev(False)
+    a.step(1)
+    b.step(1)
+    for s in range(2):
+        pa, pb = a.get_particles(s), b.get_particles(s)
+        for k in ("i1", "i2", "dx1", "dx2", "u1", "u2", "u3", "phi", "w", "tag"):
+            assert np.array_equal(pa[k], pb[k]), (s, k)
+    rt = 1e-12 if precision == "fp64" else 1e-5
+    assert_planes(b.planes(), a.planes(), planes=AFTER_ADVANCE, rtol=rt, what="keep_prev")
+    for call in (lambda: b.deposit(), lambda: b.invariants(0, FIELD_WALD, 1.0),
+                 lambda: b.charge_check(after_step=True)):
+        with pytest.raises(GrpicError, match="status 4"):
+            call()
+    b.predict()
+    for s in range(2):
+        b.push(s)  # a separate push stores them
+    b.deposit()
+    b.charge_check(after_step=False)
+    b.invariants(0, FIELD_WALD, 1.0)

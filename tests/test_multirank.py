@@ -58,7 +58,7 @@ def test_reference_arm_under_torchrun_two_ranks():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(free_port()), "bench.py",
            "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
-           "--ref-frac", "0.002"]
+           "--ref-frac", "0.05", "--workload", "wald64"]
     env = dict(os.environ, OMP_NUM_THREADS="2")
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900, env=env)
     assert r.returncode == 0, r.stderr[-3000:]
