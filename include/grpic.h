@@ -373,6 +373,34 @@ GRPIC_API grpic_status grpic_sort_permutation_noalloc(int n_r, int n_theta, int 
                                                       int64_t n, uint32_t *perm,
                                                       int64_t *n_alive, void *stream);
 
+/* --- exact sums --------------------------------------------------------------------- */
+
+/* Bins of an exact, order-independent sum of doubles (2 int64 per bin). */
+#define GRPIC_SUM_BINS 2048
+
+/* No counterpart in the paper: the adjoint's gradient with respect to the field amplitude is
+ * a sum over particles, and these two calls make that sum the same bits however the
+ * particles are split between calls, streams or GPUs. A finite double v equals
+ * M 2^(b - 1075), b its biased exponent field (1 for subnormals, which have no implicit
+ * bit) and M a signed integer, |M| < 2^53. bins: 2 x GRPIC_SUM_BINS int64, element 2b the sum
+ * of M >> 32 (arithmetic shift) and element 2b + 1 the sum of M & 0xffffffff over the values
+ * of exponent b. Being integer sums, bins can be added element by element (an int64
+ * all-reduce across processes) without changing the result. Capacity: at most 2^31 values
+ * in all per set of bins.
+ *
+ * grpic_sum_bins_add adds the finite values of the device array x[0 .. n) (NaN and inf are
+ * skipped) into the device bins (the caller zeroes them first) with one kernel on `stream`
+ * (cudaStream_t). Allocates nothing. Errors: GRPIC_EINVAL (n < 0, null bins, null x with
+ * n > 0), GRPIC_ECUDA (a CUDA error pending before the call, left in place, or a failed
+ * launch).
+ *
+ * grpic_sum_bins_value rounds the binned total, read from HOST memory, to the nearest double
+ * (ties to even) in *out: the correctly rounded sum of every value added. Host code only, no
+ * CUDA call. Errors: GRPIC_EINVAL (null pointers, bins beyond the capacity). */
+GRPIC_API grpic_status grpic_sum_bins_add(const double *x, int64_t n, int64_t *bins,
+                                          void *stream);
+GRPIC_API grpic_status grpic_sum_bins_value(const int64_t *bins, double *out);
+
 /* --- pair injection ----------------------------------------------------------------- */
 
 /* Pair injection of the BZ monopole test (Sec. 4.5: plasma is injected wherever the local

@@ -32,7 +32,8 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants",
            "grpic_adjoint_forward", "grpic_adjoint_backward", "grpic_charge_check",
            "grpic_config_bytes", "grpic_inject", "grpic_step_host", "grpic_aux_fields",
-           "grpic_set_keep_prev", "grpic_probe_fma"]
+           "grpic_set_keep_prev", "grpic_probe_fma", "grpic_sum_bins_add",
+           "grpic_sum_bins_value"]
 
 
 ADJOINT_SCRATCH_PER_STEP = 36  # doubles per particle and step of grpic_adjoint_backward
@@ -128,6 +129,8 @@ def lib(build: bool = True):
         L.grpic_set_timing.argtypes = [P, C.c_int]
         L.grpic_set_keep_prev.argtypes = [P, C.c_int]
         L.grpic_probe_fma.argtypes = [C.c_int, C.c_int64, C.c_int, P, P, C.POINTER(C.c_int64)]
+        L.grpic_sum_bins_add.argtypes = [P, C.c_int64, P, P]
+        L.grpic_sum_bins_value.argtypes = [P, C.POINTER(C.c_double)]
         L.grpic_get_timing.argtypes = [P, C.POINTER(Timing)]
         L.grpic_last_error.argtypes = [P]
         L.grpic_last_error.restype = C.c_char_p
@@ -489,3 +492,30 @@ def probe_fma(precision: str, iters: int, blocks_per_sm: int, sink, stream) -> i
     if st != OK:
         raise GrpicError("grpic_probe_fma failed (status %d)" % st)
     return ops.value
+
+
+SUM_BINS = 2048  # GRPIC_SUM_BINS
+
+
+def sum_bins_add(x, bins, stream):
+    """grpic_sum_bins_add: add the finite values of the float64 CUDA tensor x into the int64
+    CUDA tensor bins (2 x SUM_BINS elements) on `stream` (a torch stream)."""
+    if x.dtype.itemsize != 8 or not x.is_contiguous() or bins.numel() != 2 * SUM_BINS:
+        raise GrpicError("sum_bins_add: expected a contiguous float64 tensor and 2 x %d bins"
+                         % SUM_BINS)
+    st = lib().grpic_sum_bins_add(x.data_ptr(), x.numel(), bins.data_ptr(), stream.cuda_stream)
+    if st != OK:
+        raise GrpicError("grpic_sum_bins_add failed (status %d)" % st)
+
+
+def sum_bins_value(bins) -> float:
+    """grpic_sum_bins_value: the correctly rounded total of host bins (an int64 numpy array or
+    CPU tensor of 2 x SUM_BINS elements)."""
+    a = np.ascontiguousarray(bins.numpy() if hasattr(bins, "numpy") else bins, dtype=np.int64)
+    if a.size != 2 * SUM_BINS:
+        raise GrpicError("sum_bins_value: expected 2 x %d bins" % SUM_BINS)
+    out = C.c_double()
+    st = lib().grpic_sum_bins_value(a.ctypes.data, C.byref(out))
+    if st != OK:
+        raise GrpicError("grpic_sum_bins_value failed (status %d)" % st)
+    return out.value

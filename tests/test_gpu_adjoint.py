@@ -165,13 +165,19 @@ def test_boundary_particles(setup):
 
 def test_adjoint_long_horizon_matches_oracle_on_the_512_grid(torch_cuda):
     """The adjoint workload's grid (512^2, r_max = 50) and horizon (2000 steps): the reverse
-    sweep against the oracle's complex-step Jacobian for a handful of particles."""
+    sweep against the oracle's complex-step Jacobian for 320 particles (at least 256 stay in
+    the domain), and against central differences of the GPU forward with their own error
+    estimate: per particle the differences at h, h/2 and h/4 (h = 4e-6) give two Richardson
+    extrapolations whose spread U estimates what the difference quotient itself can resolve.
+    Every particle agrees within 1e-6 of its gradient's scale, or its quotient's U is above
+    1e-6 and the agreement is within 3 U (the quotient, not the adjoint, is uncertain there:
+    the +-h orbits straddle kinks of the bilinear interpolation over 2000 steps)."""
     from paper_2511_17701_gb300 import FIELD_USER, Sim
     torch = torch_cuda
     cfg = W.grid_config("wald512", r_absorb=1e300)
     osim = O.OracleSim(cfg)
     osim.init_fields(O.FIELD_WALD, 1.0)
-    tp = W.probe_particles(cfg, 12, 21, (0.2 * cfg["n_r"], 0.8 * cfg["n_r"]),
+    tp = W.probe_particles(cfg, 320, 21, (0.2 * cfg["n_r"], 0.8 * cfg["n_r"]),
                            (0.15 * cfg["n_theta"], 0.85 * cfg["n_theta"]), 0.5)
     qm, qc = W.species_coefficients(1.0)
     v = osim.add_species(tp["pos"], tp["uhat"], tp["w0"], qm, qc).view()
@@ -183,17 +189,91 @@ def test_adjoint_long_horizon_matches_oracle_on_the_512_grid(torch_cuda):
     n_steps = 2000
     fin, J = O.frozen_jacobian(osim, st0, 1.0, qm, n_steps, 60)
     ok = ~np.isnan(fin[0])
-    assert ok.sum() >= 8
+    assert ok.sum() >= 256
     cot = np.random.default_rng(22).standard_normal(st0.shape)
     cot[:, ~ok] = 0.0
     st0_t = torch.tensor(st0, dtype=torch.float64, device="cuda")
     out, ckpt = g.adjoint_forward(st0_t, qm, 1.0, n_steps, 100, N_ITER)
-    gin, gpp, _ = g.adjoint_backward(ckpt, torch.tensor(cot, device="cuda"), qm, 1.0, n_steps,
-                                     100, N_ITER)
+    assert np.array_equal(np.isnan(out[0].cpu().numpy()), ~ok)
+    cot_t = torch.tensor(cot, device="cuda")
+    gin, gpp, _ = g.adjoint_backward(ckpt, cot_t, qm, 1.0, n_steps, 100, N_ITER)
     gin, gpp = gin.cpu().numpy(), gpp.cpu().numpy()
-    ref_in = np.einsum("kqi,qk->ik", J[:, :, :6], cot)
-    ref_b0 = np.einsum("kq,qk->k", J[:, :, 6], cot)
-    for k in np.flatnonzero(ok):
-        sc = max(np.abs(ref_in[:, k]).max(), abs(ref_b0[k]))
-        assert np.max(np.abs(gin[:, k] - ref_in[:, k])) / sc < 1e-6, k
-        assert abs(gpp[k] - ref_b0[k]) / sc < 1e-6, k
+    ad = np.concatenate([gin, gpp[None]])  # (7, n)
+    ref = np.concatenate([np.einsum("kqi,qk->ik", J[:, :, :6], cot),
+                          np.einsum("kq,qk->k", J[:, :, 6], cot)[None]])
+    sc = np.abs(ref).max(axis=0) + 1e-300
+    exact_err = (np.abs(ad - ref).max(axis=0) / sc)[ok]
+    assert exact_err.max() < 1e-6, exact_err.max()
+
+    def loss(st, b):
+        o, _ = g.adjoint_forward(st, qm, b, n_steps, 100, N_ITER)
+        return (o * cot_t).sum(dim=0)
+
+    def central(h):
+        fd = torch.zeros((7, st0.shape[1]), dtype=torch.float64, device="cuda")
+        for q in range(6):
+            sp_, sm_ = st0_t.clone(), st0_t.clone()
+            sp_[q] += h
+            sm_[q] -= h
+            fd[q] = (loss(sp_, 1.0) - loss(sm_, 1.0)) / (2 * h)
+        fd[6] = (loss(st0_t, 1.0 + h) - loss(st0_t, 1.0 - h)) / (2 * h)
+        return fd.cpu().numpy()
+
+    h = 4e-6
+    d1, d2, d4 = central(h), central(h / 2), central(h / 4)
+    r1, r2 = (4 * d2 - d1) / 3, (4 * d4 - d2) / 3
+    U = np.abs(r2 - r1).max(axis=0) / sc
+    fd_err = np.abs(ad - r2).max(axis=0) / sc
+    sel = ok & np.isfinite(U) & np.isfinite(fd_err)
+    assert sel.sum() >= 250
+    within = fd_err[sel] <= 1e-6
+    explained = (U[sel] > 1e-6) & (fd_err[sel] <= 3 * U[sel])
+    print("adjoint vs Richardson central differences over 2000 steps: %d particles, %.1f%% "
+          "within 1e-6 (median %.2e), the rest within 3x their quotient's uncertainty: %s"
+          % (sel.sum(), 100 * within.mean(), np.median(fd_err[sel]), bool(np.all(within | explained))))
+    assert np.all(within | explained)
+    assert within.mean() >= 0.75
+
+
+def test_gpu_sum_bins_match_their_definition(torch_cuda):
+    """grpic_sum_bins_add on the GPU fills the bins exactly as their definition (a
+    normal, wide-exponent, subnormal and non-finite mixture), in any split."""
+    torch = torch_cuda
+    from paper_2511_17701_gb300.binding import SUM_BINS, sum_bins_add, sum_bins_value
+    from test_sharded_adjoint import bins_of
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.normal(size=300000), rng.normal(size=5000) * 1e-310,
+                        rng.normal(size=5000) * np.exp(rng.uniform(-600, 600, size=5000)),
+                        [np.nan, np.inf, -np.inf, 0.0, -0.0]])
+    rng.shuffle(x)
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    bins = torch.zeros(2 * SUM_BINS, dtype=torch.int64, device="cuda")
+    sum_bins_add(xt, bins, st)
+    want = bins_of(x)
+    assert np.array_equal(bins.cpu().numpy(), want)
+    b2 = torch.zeros_like(bins)
+    for part in torch.tensor_split(xt, 5):
+        sum_bins_add(part.contiguous(), b2, st)
+    assert torch.equal(b2, bins)
+    import math
+    assert sum_bins_value(bins.cpu()) == math.fsum(x[np.isfinite(x)])
+
+
+def test_sharded_adjoint_one_rank_on_the_gpu(setup):
+    """The sharded adjoint's GPU path with one rank: the B0 gradient is the correctly rounded
+    sum of the library's per-particle terms, within rounding of the library's own sum."""
+    import math
+    from paper_2511_17701_gb300.sharded import library_adjoint, sharded_adjoint
+    osim, g, st0, st0_t, qm = setup
+    torch = g.torch
+    cot = torch.tensor(np.random.default_rng(3).standard_normal(st0.shape), device="cuda")
+    out, gin, gb0 = sharded_adjoint(library_adjoint(g, qm, 1.0, N_STEPS, 10, N_ITER), st0_t, cot)
+    ok = ~torch.isnan(out[0])
+    _, ckpt = g.adjoint_forward(st0_t, qm, 1.0, N_STEPS, 10, N_ITER)
+    gin2, gpp, gsum = g.adjoint_backward(ckpt, (cot * ok).contiguous(), qm, 1.0, N_STEPS, 10,
+                                         N_ITER)
+    p = gpp.cpu().numpy()
+    assert gb0 == math.fsum(p[np.isfinite(p)])
+    assert abs(gb0 - float(gsum[0])) <= 1e-12 * np.abs(p).sum()
+    assert torch.equal(gin, gin2)

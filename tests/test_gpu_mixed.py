@@ -135,5 +135,9 @@ def test_invariant_drift_fp64_and_mixed(torch_cuda):
         drift[prec] = (float(np.max(np.abs(E1[keep] / E0[keep] - 1))),
                        float(np.max(np.abs(L1[keep] / L0[keep] - 1))))
     print("invariant drift over 1e4 steps (E, L):", drift)
-    assert drift["fp64"][0] < 1e-2 and drift["fp64"][1] < 1e-2
-    assert drift["mixed"][0] < 1e-2 and drift["mixed"][1] < 1e-2
+    # the drift is the scheme's (second order in dt, the same for both precisions), not the
+    # rounding's: the mixed path stays within 1.5x of the FP64 drift (measured 1.4x for E and
+    # 1.0x for L), and both stay small
+    assert drift["fp64"][0] < 2e-3 and drift["fp64"][1] < 2e-3
+    assert drift["mixed"][0] <= 1.5 * drift["fp64"][0] + 1e-6
+    assert drift["mixed"][1] <= 1.5 * drift["fp64"][1] + 1e-6
