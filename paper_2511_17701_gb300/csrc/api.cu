@@ -408,7 +408,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   ctx->off_planes = off; off += up(ps * fs) * 36;
   ctx->off_tab = off;    off += up(ps * fs) * 4 * T_NQ;
   ctx->off_polar = off;  off += up((size_t)3 * g.NX * fs);
-  ctx->off_ptab = off;   off += 10 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 8);
+  ctx->off_ptab = off;   off += 11 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 8);
   ctx->off_dt = off;     off += up(64);
   ctx->off_diag = off;   off += up(DG_N * 8);
   ctx->off_chunk = off;  off += up(GRPIC_MAX_SPECIES * HOST_CHUNKS * 8);
@@ -475,6 +475,7 @@ grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream)
   ctx->tb.t2 = at<float>(ctx, ctx->off_ptab + 7 * tstride);
   ctx->tb.t1_64 = at<double>(ctx, ctx->off_ptab + 8 * tstride);
   ctx->tb.t2_64 = at<double>(ctx, ctx->off_ptab + 9 * tstride);
+  ctx->tb.th64 = at<double>(ctx, ctx->off_ptab + 10 * tstride);
   if (ctx->mixed) {
     for (int s = 0; s < ctx->cfg.n_species; ++s) {
       SpeciesState &sp = ctx->sp[s];

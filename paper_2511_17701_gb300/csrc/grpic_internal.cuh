@@ -22,6 +22,8 @@ struct GridP {
   double iter_tol;     // > 0: FP64 implicit iterations start from an FP32 predictor and stop
                        // once the update is at most iter_tol max(1, |value|)
   double r_min, r_max, dxi, dth, a, M, dt, small_angle, r_absorb, absorb_coef;
+  double idt;       // 1 / dt
+  double pi_small;  // pi - small_angle
   double ig2;  // 1 / dth^2
   // quasi-spherical map: radial offset, equatorial concentration, qks = (r0 != 0 || h0 != 0),
   // c3 = 4 h0 / pi^2 (the cubic coefficient of theta(eta_j + d) - theta(eta_j))
@@ -29,11 +31,14 @@ struct GridP {
   double e_min;  // r_min - r0 = exp(xi) at x1 = 0
   int qks;
   // FP32 copies for the mixed path (read from the kernel parameters, no conversions)
-  float f_a, f_M, f_dxi, f_dth, f_ig2, f_dt, f_idt, f_r0, f_c3;
+  float f_a, f_M, f_dxi, f_dth, f_ig2, f_dt, f_idt, f_r0, f_c3, f_iter_tol;
 };
 
 // Fill the FP32 copies once a, M, dxi, dth and dt are set.
 inline void grid_float_copies(GridP &g) {
+  g.idt = g.dt > 0.0 ? 1.0 / g.dt : 0.0;
+  g.pi_small = GRPIC_PI - g.small_angle;
+  g.f_iter_tol = (float)g.iter_tol;
   g.f_a = (float)g.a; g.f_M = (float)g.M; g.f_dxi = (float)g.dxi; g.f_dth = (float)g.dth;
   g.f_ig2 = (float)g.ig2; g.f_dt = (float)g.dt; g.f_idt = g.dt > 0.0 ? (float)(1.0 / g.dt) : 0.0f;
   g.f_r0 = (float)g.r0; g.f_c3 = (float)g.c3;
@@ -323,6 +328,7 @@ struct PushTables {
   // derivative); 1 and 0 on the plain grid
   const float *t1, *t2;
   const double *t1_64, *t2_64;
+  const double *th64;  // theta at corner row j, formed as map_theta forms it
   int guard_ilo, guard_ihi;  // cells guard_ilo <= i1 < guard_ihi (around the horizon) and
   int guard_j;               // within guard_j of an axis evaluate the metric in FP64
 };

@@ -17,6 +17,58 @@ __device__ __forceinline__ void count(unsigned long long *diag, int which) {
   atomicAdd(diag + which, 1ull);
 }
 
+// ---------------------------------------------------------------------------------
+// Conversions and tests on the integer pipe. GB300's FP64 pipe bounds the FP64 kernel and
+// also executes the FP64 conversion, compare and min/max instructions; these bit-level forms
+// keep such work off it where the exact FP64 semantics are not needed.
+// ---------------------------------------------------------------------------------
+// A double in FP32's normal range truncated toward zero to 24 significant bits; a signed
+// zero below that range, a signed infinity above it, NaN kept. For the FP32 predictor's
+// inputs and for stop tests, where a start point or a bound moves by less than 2^-23 of itself.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu;
+  const int e = (int)ex - 896;  // rebias 1023 -> 127
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  unsigned r = sign | ((unsigned)e << 23) | m;
+  if (e <= 0) r = sign;
+  if (e >= 255) r = sign | 0x7f800000u | ((ex == 0x7ffu && (m | (lo & 0x1fffffffu))) ? 0x400000u : 0u);
+  return __uint_as_float(r);
+}
+// The exact double of a normal float; zero and subnormals become a signed zero, inf and NaN
+// are kept. For the FP32 predictor's results (FP64 start points) and the FP32 Newton
+// coefficients, which only steer FP64 iterations that are checked in FP64.
+__device__ __forceinline__ double f64_widen(float f) {
+  const unsigned v = __float_as_uint(f);
+  const unsigned sign = v & 0x80000000u, e = (v >> 23) & 0xffu, m = v & 0x7fffffu;
+  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+  if (e == 0u) hi = sign, lo = 0u;
+  if (e == 255u) hi = sign | 0x7ff00000u | (m ? 0x80000u : 0u), lo = 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+// x is neither infinite nor NaN
+__device__ __forceinline__ bool finite64(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
+}
+// |x| <= c and |x| < c for a constant c >= 0 (x NaN: false): the ordering of non-negative
+// doubles is the ordering of their bit patterns
+__device__ __forceinline__ bool abs_le(double x, double c) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) <=
+         (unsigned long long)__double_as_longlong(c);
+}
+__device__ __forceinline__ bool abs_lt(double x, double c) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) <
+         (unsigned long long)__double_as_longlong(c);
+}
+// x < c and x > c for a constant c > 0 (x NaN: false): as signed integers, negative doubles
+// order below every positive one and positive doubles order as their bit patterns
+__device__ __forceinline__ bool lt_pos(double x, double c) {
+  return __double_as_longlong(x) < __double_as_longlong(c) && finite64(x);
+}
+__device__ __forceinline__ bool gt_pos(double x, double c) {
+  return __double_as_longlong(x) > __double_as_longlong(c) && finite64(x);
+}
+
 // =================================================================================
 // FP64 routine. r and sin/cos at the iterates follow from their values at x^n by the
 // exponential and angle-addition formulas with short Taylor series of the small offsets
@@ -52,13 +104,72 @@ __device__ __forceinline__ Base make_base(const GridP &g, double x1, double x2) 
   return b;
 }
 
+// x^n from the per-corner tables (rows away from the axes): exp(xi) = r64[i] exp(dx1 dxi) and
+// sin/cos(theta) by the angle-addition formulas from corner row j, with Taylor series of the
+// offsets (|dx1 dxi| <= 0.02: truncation below 1e-18; |d| <= 0.1, d = theta - theta_j exact by
+// Sterbenz since theta_j >= 2 dtheta there: below 3e-19). One FP64 exp and sincos fewer per
+// particle; beyond those offsets the library functions as make_base.
+template <bool Q = true>
+__device__ __forceinline__ Base make_base_tab(const GridP &g, const PushTables &tb, int i1, int i2,
+                                              double dx1, double x1, double x2) {
+  Base b;
+  b.x1 = x1;
+  b.th0 = map_theta<Q>(g, x2);
+  const double e = dx1 * g.dxi;
+  b.e0 = abs_le(e, 0.02) ? __ldg(tb.r64 + i1 + G_) * exp_small(e) : map_e(g, x1);
+  const double d = b.th0 - __ldg(tb.th64 + i2 + G_);
+  if (abs_le(d, 0.1)) {
+    const double q = d * d;
+    double sp = 1.0 / 362880.0;
+    sp = fma(sp, q, -1.0 / 5040.0);
+    sp = fma(sp, q, 1.0 / 120.0);
+    sp = fma(sp, q, -1.0 / 6.0);
+    const double se = fma(sp * q, d, d);
+    double cp = -1.0 / 3628800.0;
+    cp = fma(cp, q, 1.0 / 40320.0);
+    cp = fma(cp, q, -1.0 / 720.0);
+    cp = fma(cp, q, 1.0 / 24.0);
+    cp = fma(cp, q, -0.5);
+    const double ce = fma(cp, q, 1.0);
+    const double s0 = __ldg(tb.s64 + i2 + G_), c0 = __ldg(tb.c64 + i2 + G_);
+    b.s0 = fma(s0, ce, c0 * se);
+    b.c0 = fma(c0, ce, -s0 * se);
+  } else {
+    sincos(b.th0, &b.s0, &b.c0);
+  }
+  return b;
+}
+
+// x^n itself: r, sin and cos are the base's (local_rsc with zero offsets gives the same bits),
+// theta clamped to [small_angle, pi - small_angle]
+template <bool Q = true>
+__device__ __forceinline__ void local_at_base(const GridP &g, const Base &b, double x2,
+                                              Pt<double> &p) {
+  p.r = Q ? g.r0 + b.e0 : b.e0;
+  p.f = g.dxi * b.e0;
+  if (Q && g.qks) {
+    map_g<Q>(g, x2, p.gg, p.gp);
+  } else {
+    p.gg = g.dth;
+    p.igg = g.ig2;
+    p.gp = 0.0;
+  }
+  const double th = b.th0;
+  if (lt_pos(th, g.small_angle) || gt_pos(th, g.pi_small)) {
+    sincos(fmin(fmax(th, g.small_angle), GRPIC_PI - g.small_angle), &p.s, &p.c);
+  } else {
+    p.s = b.s0;
+    p.c = b.c0;
+  }
+}
+
 // the point (x1t, x2t): r, sin(theta), cos(theta) with theta clamped to [small_angle,
 // pi - small_angle], and the map's factors
 template <bool Q = true>
 __device__ __forceinline__ void local_rsc(const GridP &g, const Base &b, double x1t, double x2t,
                                           Pt<double> &p) {
   const double e1 = (x1t - b.x1) * g.dxi;
-  const double ex = fabs(e1) <= 0.02 ? b.e0 * exp_small(e1) : map_e(g, x1t);
+  const double ex = abs_le(e1, 0.02) ? b.e0 * exp_small(e1) : map_e(g, x1t);
   p.r = Q ? g.r0 + ex : ex;
   p.f = g.dxi * ex;
   if (Q && g.qks) {
@@ -70,9 +181,9 @@ __device__ __forceinline__ void local_rsc(const GridP &g, const Base &b, double 
   }
   const double th = map_theta<Q>(g, x2t);
   const double e2 = th - b.th0;
-  if (th < g.small_angle || th > GRPIC_PI - g.small_angle) {
+  if (lt_pos(th, g.small_angle) || gt_pos(th, g.pi_small)) {
     sincos(fmin(fmax(th, g.small_angle), GRPIC_PI - g.small_angle), &p.s, &p.c);
-  } else if (fabs(e2) <= 0.02) {
+  } else if (abs_le(e2, 0.02)) {
     const double q = e2 * e2;
     double sp = -1.0 / 5040.0;
     sp = fma(sp, q, 1.0 / 120.0);
@@ -104,20 +215,34 @@ __device__ __forceinline__ double phi_rate64(const GridP &g, const Base &b, doub
   return rsqrt(o.opz * q) * fma(o.H13, u[0], o.H33 * u[2]);
 }
 
-// Bilinear interpolation of a plane at code position (x1, x2) for a component whose Yee
-// location is offset by (s1, s2) (absolute coordinates, as the oracle rounds them).
+// Bilinear interpolation at code position (x1, x2) of planes whose Yee location is offset by
+// 0 or 1/2 in each direction. The cells and weights of the two offsets per direction are
+// formed once for all six gathers (absolute coordinates, rounded as the oracle rounds them:
+// y = x - s, cell floor(y), weight y - floor(y)).
+struct Lerp64 {
+  int i[2], j[2];
+  double w1[2], w2[2];
+};
+__device__ __forceinline__ void lerp_setup(double x1, double x2, Lerp64 &L) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double y1 = h ? x1 - 0.5 : x1, y2 = h ? x2 - 0.5 : x2;
+    const double f1 = floor(y1), f2 = floor(y2);
+    L.i[h] = (int)f1;
+    L.j[h] = (int)f2;
+    L.w1[h] = y1 - f1;
+    L.w2[h] = y2 - f2;
+  }
+}
 template <typename T>
-__device__ __forceinline__ double interp64(const T *__restrict__ pl, int NX, double x1,
-                                           double x2, double s1, double s2) {
-  const double y1 = x1 - s1, y2 = x2 - s2;
-  const double f1 = floor(y1), f2 = floor(y2);
-  const int i0 = (int)f1, j0 = (int)f2;
-  const double w1 = y1 - f1, w2 = y2 - f2;
-  const T *p = pl + (int64_t)(j0 + G_) * NX + (i0 + G_);
+__device__ __forceinline__ double interp64(const T *__restrict__ pl, int NX, const Lerp64 &L,
+                                           int h1, int h2) {
+  const T *p = pl + (int64_t)(L.j[h2] + G_) * NX + (L.i[h1] + G_);
   const double p00 = __ldg(p), p10 = __ldg(p + 1), p01 = __ldg(p + NX), p11 = __ldg(p + NX + 1);
   // nested linear interpolations: the same bilinear value in 3 DADD + 3 DFMA
+  const double w1 = L.w1[h1];
   const double a = fma(w1, p10 - p00, p00), c = fma(w1, p11 - p01, p01);
-  return fma(w2, c - a, a);
+  return fma(L.w2[h2], c - a, a);
 }
 
 template <typename T>
@@ -132,11 +257,10 @@ template <typename T>
 __device__ __forceinline__ void deposit64(const GridP &g, const FieldPtrsT<T> &F, double q,
                                           int ia, int ja, double xa1, double xa2, int ib, int jb,
                                           double xb1, double xb2, double v3) {
-  const double idt = 1.0 / g.dt;
-  const double xr1 = fmin(fmin((double)ia, (double)ib) + 1.0,
-                          fmax(fmax((double)ia, (double)ib), 0.5 * (xa1 + xb1)));
-  const double xr2 = fmin(fmin((double)ja, (double)jb) + 1.0,
-                          fmax(fmax((double)ja, (double)jb), 0.5 * (xa2 + xb2)));
+  const double idt = g.idt;
+  // the relay point: min/max of the cell indices taken on integers (the same values)
+  const double xr1 = fmin((double)(min(ia, ib) + 1), fmax((double)max(ia, ib), 0.5 * (xa1 + xb1)));
+  const double xr2 = fmin((double)(min(ja, jb) + 1), fmax((double)max(ja, jb), 0.5 * (xa2 + xb2)));
   T *J1 = F.J[0], *J2 = F.J[1], *J3 = F.J[2];
   const int NX = g.NX;
   {
@@ -177,8 +301,10 @@ __device__ __forceinline__ void deposit64(const GridP &g, const FieldPtrsT<T> &F
 // iterations after the second evaluation while it is not (at most n_iter evaluations in
 // all). The result is the FP64 fixed point to about rho iter_tol, rho < 1 the contraction,
 // whatever the start: J and the predictor only save FP64 work (mixed-precision refinement).
-__device__ __forceinline__ bool converged(double n, double t, double tol) {
-  return fabs(n - t) <= tol * fmax(1.0, fabs(n));
+// |n - t| <= tol max(1, |n|): the difference in FP64 (n and t agree to about tol), the test
+// in FP32 on truncated values (the bound moves by less than 2^-22 of itself)
+__device__ __forceinline__ bool converged(double n, double t, float tol) {
+  return fabsf(f32_trunc(n - t)) <= tol * fmaxf(1.0f, fabsf(f32_trunc(n)));
 }
 // the largest eigenvalue modulus of a 2 x 2 matrix: the asymptotic contraction of a map
 // with that Jacobian
@@ -191,11 +317,12 @@ __device__ __forceinline__ float spectral_radius(const float J[2][2]) {
 // fixed point, so that the refined result stands for the method's n_iter result: d1 is the
 // method's first update (from the FP32 predictor's first step), rho the contraction (the
 // spectral radius of J), the remainder d1 rho^n_iter.
-__device__ __forceinline__ bool method_converges(float d1, float rho, int n_iter, double tol,
-                                                 double scale) {
+__device__ __forceinline__ bool method_converges(float d1, float rho, int n_iter, float tol,
+                                                 double s0, double s1) {
   if (!(rho < 0.5f)) return false;
   if (!(rho > 0.0f)) return true;
-  return d1 * exp2f((float)n_iter * log2f(rho)) <= (float)(0.1 * tol * scale);
+  const float scale = fmaxf(1.0f, fmaxf(fabsf(f32_trunc(s0)), fabsf(f32_trunc(s1))));
+  return d1 * exp2f((float)n_iter * log2f(rho)) <= 0.1f * tol * scale;
 }
 // t + (I - J)^{-1} (n - t): the Newton step of t = G(t) from the residual n - t; the plain
 // iteration step (n itself) when the result is not finite
@@ -204,9 +331,9 @@ __device__ __forceinline__ void newton_step(const float J[2][2], double t0, doub
   const float a = 1.0f - J[0][0], d = 1.0f - J[1][1];
   const float idet = 1.0f / fmaf(a, d, -J[0][1] * J[1][0]);
   const double r0 = n0 - t0, r1 = n1 - t1;
-  s0 = t0 + fma((double)(idet * d), r0, (double)(idet * J[0][1]) * r1);
-  s1 = t1 + fma((double)(idet * J[1][0]), r0, (double)(idet * a) * r1);
-  if (!(isfinite(s0) && isfinite(s1))) {
+  s0 = t0 + fma(f64_widen(idet * d), r0, f64_widen(idet * J[0][1]) * r1);
+  s1 = t1 + fma(f64_widen(idet * J[1][0]), r0, f64_widen(idet * a) * r1);
+  if (!(finite64(s0) && finite64(s1))) {
     s0 = n0;
     s1 = n1;
   }
@@ -221,8 +348,8 @@ __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTable
   rsc32<Q>(g, tb, i1, i2, o1, o2, pf);
   Local<float> Lf;
   local_full<Q>(g, pf, Lf);
-  const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
-  const GeoMap<float> mf(g, Lf, uf, (float)m2);
+  const float uf[3] = {f32_trunc(u[0]), f32_trunc(u[1]), f32_trunc(u[2])};
+  const GeoMap<float> mf(g, Lf, uf, f32_trunc(m2));
   float p0 = uf[0], p1 = uf[1], d1 = 0.0f;
   for (int it = 0; it < g.n_iter; ++it) {
     float n0, n1;
@@ -237,8 +364,8 @@ __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTable
   double t0 = u[0], t1 = u[1];
   float J[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   if (isfinite(p0) && isfinite(p1)) {
-    t0 = p0;
-    t1 = p1;
+    t0 = f64_widen(p0);
+    t1 = f64_widen(p1);
     mf.jacobian(p0, p1, J);
   }
   double n0, n1, s0, s1;
@@ -247,12 +374,11 @@ __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTable
   bool conv = false;
   for (int it = 1; it < g.n_iter && !conv; ++it) {
     m.apply(s0, s1, n0, n1);
-    conv = converged(n0, s0, g.iter_tol) && converged(n1, s1, g.iter_tol);
+    conv = converged(n0, s0, g.f_iter_tol) && converged(n1, s1, g.f_iter_tol);
     s0 = n0;
     s1 = n1;
   }
-  const double scale = fmax(1.0, fmax(fabs(s0), fabs(s1)));
-  if (!method_converges(d1, spectral_radius(J), g.n_iter, g.iter_tol, scale)) {
+  if (!method_converges(d1, spectral_radius(J), g.n_iter, g.f_iter_tol, s0, s1)) {
     geodesic_momentum(g, L, u, m2);  // the method's n_iter iterations from u
     return;
   }
@@ -380,8 +506,8 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
                                               const Local<double> &L, int i1, int i2,
                                               double dx1, double dx2, const double u[3],
                                               double m2, double &t1, double &t2, double &v3) {
-  const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
-  const float a1 = (float)dx1, a2 = (float)dx2, dt = g.f_dt;
+  const float uf[3] = {f32_trunc(u[0]), f32_trunc(u[1]), f32_trunc(u[2])};
+  const float a1 = f32_trunc(dx1), a2 = f32_trunc(dx2), dt = g.f_dt, m2f = f32_trunc(m2);
   const float uuf = 2.0f * uf[0] * uf[2];
   float p1 = a1, p2 = a2, d1 = 0.0f;
   for (int it = 0; it < g.n_iter; ++it) {
@@ -390,7 +516,7 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
     Geo<float> o;
     geo_from_rsc<Q>(g, pf, o);
     const float q = fmaf(o.H11 * uf[0], uf[0], fmaf(o.H22 * uf[1], uf[1],
-                    fmaf(o.H33 * uf[2], uf[2], fmaf(o.H13, uuf, (float)m2))));
+                    fmaf(o.H33 * uf[2], uf[2], fmaf(o.H13, uuf, m2f))));
     const float ag = rsqrtf(o.opz * q);
     const float n1 = fmaf(dt, fmaf(ag, fmaf(o.H11, uf[0], o.H13 * uf[2]), -o.beta1), a1);
     const float n2 = fmaf(dt, ag * o.H22 * uf[1], a2);
@@ -404,13 +530,13 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
   t2 = dx2;
   float J[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   if (isfinite(p1) && isfinite(p2) && fabsf(p1) < 4.0f && fabsf(p2) < 4.0f) {
-    t1 = p1;
-    t2 = p2;
+    t1 = f64_widen(p1);
+    t2 = f64_widen(p2);
     Pt<float> pf;  // the Jacobian at the predictor's midpoint
     rsc32<Q>(g, tb, i1, i2, 0.5f * (a1 + p1), 0.5f * (a2 + p2), pf);
     Local<float> Lf;
     local_full<Q>(g, pf, Lf);
-    coord_jacobian(g, Lf, uf, (float)m2, J);
+    coord_jacobian(g, Lf, uf, m2f, J);
   }
   double n1, n2, s1, s2;
   coord_map64<Q>(g, b, i1, i2, dx1, dx2, u, m2, t1, t2, n1, n2, v3);
@@ -418,14 +544,13 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
   bool conv = false;
   for (int it = 1; it < g.n_iter && !conv; ++it) {
     coord_map64<Q>(g, b, i1, i2, dx1, dx2, u, m2, s1, s2, n1, n2, v3);
-    conv = converged(n1, s1, g.iter_tol) && converged(n2, s2, g.iter_tol);
+    conv = converged(n1, s1, g.f_iter_tol) && converged(n2, s2, g.f_iter_tol);
     s1 = n1;
     s2 = n2;
   }
   t1 = s1;
   t2 = s2;
-  const double scale = fmax(1.0, fmax(fabs(t1), fabs(t2)));
-  if (!method_converges(d1, spectral_radius(J), g.n_iter, g.iter_tol, scale)) {
+  if (!method_converges(d1, spectral_radius(J), g.n_iter, g.f_iter_tol, t1, t2)) {
     coord_exact<Q>(g, b, L, i1, i2, dx1, dx2, u, m2, t1, t2);  // the method's iterations
     v3 = NAN;
   }
@@ -442,9 +567,13 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   const double x1 = i1 + dx1, x2 = i2 + dx2;
   const bool em = s.m2 != 0.0;  // massless particles skip the EM push (Sec. 3.1)
   const double settle = sizeof(T) == 4 ? SETTLE32 : 0.0;  // FP32 storage: see SETTLE32
-  const Base b = make_base<Q>(g, x1, x2);
+  // the refined iterations keep two cell rows away from the axes: there the coordinate map
+  // (metric terms ~ 1/sin^2(theta)) has more than one fixed point within reach, and the
+  // method's answer is the one its iteration from x^n finds
+  const bool refine = g.iter_tol > 0.0 && i2 >= 2 && i2 < g.n_th - 2;
+  const Base b = refine ? make_base_tab<Q>(g, tb, i1, i2, dx1, x1, x2) : make_base<Q>(g, x1, x2);
   Pt<double> p0;
-  local_rsc<Q>(g, b, x1, x2, p0);  // clamps theta near the axes
+  local_at_base<Q>(g, b, x2, p0);  // clamps theta near the axes
   Local<double> L;
   local_full<Q>(g, p0, L);
   double Bh[3], Dh[3], uh[3], u[3] = {(double)s.u1[k], (double)s.u2[k], (double)s.u3[k]};
@@ -452,12 +581,14 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   if (em) {
     // step 2: fields at x^n
     double Bv[3], Dv[3];
-    Bv[0] = interp64(F.Bn[0], g.NX, x1, x2, 0.0, 0.5);
-    Bv[1] = interp64(F.Bn[1], g.NX, x1, x2, 0.5, 0.0);
-    Bv[2] = interp64(F.Bn[2], g.NX, x1, x2, 0.5, 0.5);
-    Dv[0] = interp64(F.D[0], g.NX, x1, x2, 0.5, 0.0);
-    Dv[1] = interp64(F.D[1], g.NX, x1, x2, 0.0, 0.5);
-    Dv[2] = interp64(F.D[2], g.NX, x1, x2, 0.0, 0.0);
+    Lerp64 lw;
+    lerp_setup(x1, x2, lw);
+    Bv[0] = interp64(F.Bn[0], g.NX, lw, 0, 1);
+    Bv[1] = interp64(F.Bn[1], g.NX, lw, 1, 0);
+    Bv[2] = interp64(F.Bn[2], g.NX, lw, 1, 1);
+    Dv[0] = interp64(F.D[0], g.NX, lw, 1, 0);
+    Dv[1] = interp64(F.D[1], g.NX, lw, 0, 1);
+    Dv[2] = interp64(F.D[2], g.NX, lw, 0, 0);
     // step 3: to the tetrad basis
     vec_hat(L, Bv, Bh);
     vec_hat(L, Dv, Dh);
@@ -465,11 +596,7 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
     boris(uh, Dh, Bh, hq);     // step 4
     hat_cov(L, uh, u);         // step 5
   }
-  // the refined iterations keep two cell rows away from the axes: there the coordinate map
-  // (metric terms ~ 1/sin^2(theta)) has more than one fixed point within reach, and the
-  // method's answer is the one its iteration from x^n finds
-  const bool refine = g.iter_tol > 0.0 && i2 >= 2 && i2 < g.n_th - 2;
-  if (refine) geodesic_refined<Q>(g, tb, i1, i2, (float)dx1, (float)dx2, L, u, s.m2);
+  if (refine) geodesic_refined<Q>(g, tb, i1, i2, f32_trunc(dx1), f32_trunc(dx2), L, u, s.m2);
   else geodesic_momentum_settle(g, L, u, s.m2, settle);  // step 6
   if (em) {
     cov_hat(L, u, uh);         // step 7
@@ -480,8 +607,8 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   double t1 = dx1, t2 = dx2, v3r = NAN;
   if (refine) coord_refined<Q>(g, tb, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2, v3r);
   else coord_exact<Q>(g, b, L, i1, i2, dx1, dx2, u, s.m2, t1, t2, settle);
-  if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(t1) && isfinite(t2) &&
-        fabs(t1) < 1e6 && fabs(t2) < 1e6)) {
+  if (!(finite64(u[0]) && finite64(u[1]) && finite64(u[2]) && abs_lt(t1, 1e6) &&
+        abs_lt(t2, 1e6))) {
     s.tag[k] = 0;
     count(diag, DG_NONFINITE);
     return;
@@ -1264,7 +1391,9 @@ __global__ void k_push_tables(GridP g, PushTables tb) {
     }
     if (t < g.NY) {
       double s, c;
-      sincos(map_theta(g, t - G_), &s, &c);
+      const double th = map_theta(g, t - G_);
+      const_cast<double *>(tb.th64)[t] = th;
+      sincos(th, &s, &c);
       const_cast<double *>(tb.s64)[t] = s;
       const_cast<double *>(tb.c64)[t] = c;
       const_cast<float *>(tb.s)[t] = (float)s;
