@@ -359,31 +359,34 @@ def device_facts(device):
 
 
 def measure_alu_peaks(device, launches=5):
-    """FMA throughput of the library's probe kernel (grpic_probe_fma), timed with CUDA events
-    on the current stream: FP64 (FMA thread operations/s, the FP64 pipe) and FP32 (as warp
-    instructions/s, the issue peak). Each launch runs ~0.1 s; the median of `launches`
-    launches after one warm-up."""
+    """Throughput of the library's probe kernel (grpic_probe_alu), timed with CUDA events on
+    the current stream: FP64 fused multiply-add, multiply and add (thread operations/s; the
+    FP64 pipe's peak is the fastest of them, the rate the FP64 kernel's DFMA/DMUL/DADD mixture
+    is measured against) and FP32 fused multiply-add as warp instructions/s (the issue peak).
+    Each launch runs ~0.1 s; the median of `launches` launches after one warm-up."""
     import torch
 
-    from paper_2511_17701_gb300.binding import probe_fma
+    from paper_2511_17701_gb300.binding import probe_alu
     stream = torch.cuda.current_stream(device)
     sink = torch.zeros(1, dtype=torch.float64, device=device)
     sms = device_facts(device)["sms"]
     out = {}
-    for prec, iters in (("fp64", max(1, int(800 * 152 / sms))),
-                        ("fp32", max(1, int(50000 * 152 / sms)))):
-        probe_fma(prec, iters, 8, sink, stream)
+    for prec, op, iters in (("fp64", "fma", 800), ("fp64", "mul", 800), ("fp64", "add", 800),
+                            ("fp32", "fma", 50000)):
+        iters = max(1, int(iters * 152 / sms))
+        probe_alu(prec, op, iters, 8, sink, stream)
         rates = []
         for _ in range(launches):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ops = probe_fma(prec, iters, 8, sink, stream)
+            ops = probe_alu(prec, op, iters, 8, sink, stream)
             e1.record(stream)
             e1.synchronize()
             rates.append(ops / (e0.elapsed_time(e1) * 1e-3))
-        out[prec] = float(np.median(rates))
-    return {"fp64_gops": out["fp64"] / 1e9, "warp_ginst": out["fp32"] / 32 / 1e9,
-            "fp32_gops": out["fp32"] / 1e9, "sms": sms}
+        out[prec + "_" + op] = float(np.median(rates)) / 1e9
+    fp64 = {k: out["fp64_" + k] for k in ("fma", "mul", "add")}
+    return {"fp64_gops": max(fp64.values()), "fp64_by_op_gops": fp64,
+            "warp_ginst": out["fp32_fma"] / 32, "fp32_gops": out["fp32_fma"], "sms": sms}
 
 
 _PLASMA = {}
@@ -402,7 +405,7 @@ def measure(args, precision, ws, rank, local, workload=None, photons=False, extr
     workload = workload or args.workload
     cfg = W.grid_config(workload, sort_every=args.sort_every, tile_r=args.tile,
                         tile_theta=args.tile, precision=precision,
-                        tiled_push=1 if args.tiled_push else 0, iter_tol=args.iter_tol)
+                        tiled_push=args.tiled_push, iter_tol=args.iter_tol)
     if args.ppc and workload == args.workload:
         cfg["ppc"] = args.ppc
     cfg.update(extra or {})
@@ -492,8 +495,9 @@ def rooflines(out, precision, alu, args, photons=False):
         peak = alu.get("fp64_gops")
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G FP64-pipe op/s",
                 "frac": ach / peak if peak else None,
-                "peak_source": "measured in this run: grpic_probe_fma FP64 (8 independent "
-                               "FMA chains per thread, %d SMs x 8 blocks of 256 threads)" % sms,
+                "peak_source": "measured in this run: grpic_probe_alu FP64, the fastest of "
+                               "DFMA, DMUL and DADD chains (8 per thread, %d SMs x 8 blocks of "
+                               "256 threads)" % sms,
                 "nominal_peak_at_sampled_clock": 2 * sms * mhz / 1e3 if (sms and mhz) else None,
                 "ops_per_particle": kc["fp64_ops"],
                 "tflops": parts * kc["flop"] / (kms * 1e-3) / 1e12,
@@ -504,7 +508,7 @@ def rooflines(out, precision, alu, args, photons=False):
         peak = alu.get("warp_ginst")
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G warp-instructions/s",
                 "frac": ach / peak if peak else None,
-                "peak_source": "measured in this run: grpic_probe_fma FP32 (one warp FMA "
+                "peak_source": "measured in this run: grpic_probe_alu FP32 (one warp FMA "
                                "instruction per clock per SM sub-partition), / 32 lanes",
                 "nominal_peak_at_sampled_clock": 4 * sms * mhz / 1e3 if (sms and mhz) else None,
                 "warp_inst_per_particle": kc["warp_inst"],
@@ -832,7 +836,7 @@ def measure_filter_2048(args, ws, rank, local, alu):
         "roofline": {"bound": "alu", "achieved": ops, "peak": alu["fp64_gops"],
                      "unit": "G FP64-pipe op/s", "frac": ops / alu["fp64_gops"],
                      "traffic": None,
-                     "peak_source": "measured in this run: grpic_probe_fma FP64",
+                     "peak_source": "measured in this run: grpic_probe_alu FP64",
                      "kernel": "k_filter<double> (8 passes fused in shared memory)"},
         "hbm_roofline": {"achieved_gbs": gbs, "peak_gbs": hp, "frac": gbs / hp,
                          "peak_source": hsrc},
@@ -1083,11 +1087,15 @@ def run_bz_physics(args, local):
     sim.inject(cfg["sigma0"], cfg["sigma_th"], B0, pool, pool_offset=0)
     t, snaps = 0.0, []
     n_mark = int(math.floor(args.bz_time))
+    every = max(1, args.bz_inject_every)
+    n_step = 0
     for mark in range(1, n_mark + 1):
         k = int(round((mark - t) / dt))
         for _ in range(k):
             sim.step(1)
-            sim.inject(cfg["sigma0"], cfg["sigma_th"], B0, pool)
+            n_step += 1
+            if n_step % every == 0:
+                sim.inject(cfg["sigma0"], cfg["sigma_th"], B0, pool)
         t += k * dt
         if mark > 2 * n_mark / 3:
             snaps.append(bz_diagnostics(sim, cfg, radii))
@@ -1113,7 +1121,7 @@ def run_bz_physics(args, local):
             "config": {"workload": "bz monopole, Kerr a=%.1f, %dx%d log-r grid, r in [1, 10], "
                                    "absorbing layer from r=9, rho0=5e-5, d0=2.5e-3, sigma0=2500, "
                                    "sigma_th=2000, initial e+- 2 per cell per species, density "
-                                   "~ r^-2" % (a, n_g, n_g),
+                                   "~ r^-2, injection after every %d step(s)" % (a, n_g, n_g, every),
                        "t_end_rg": t, "dt": dt, "average_over_rg": [t - len(snaps), t],
                        "omega_h": wh, "L_BZ": LBZ},
             "omega_over_omega_h": avg("omega", wh), "omega_spread": spread("omega", wh),
@@ -1164,14 +1172,17 @@ def main():
     ap.add_argument("--iter-tol", type=float, default=1e-12,
                     help="implicit pushes: FP64 iterations from an FP32 predictor to this "
                          "tolerance (0: exact-repeat stop, bit-identical to n_iter iterations)")
-    ap.add_argument("--tiled-push", action="store_true",
-                    help="mixed path: the shared-memory tiled FP32 kernel instead of the default "
-                         "one thread per particle")
+    ap.add_argument("--tiled-push", type=int, default=0, choices=[0, 1, 2],
+                    help="mixed path: 1 = the shared-memory tiled FP32 kernel (window loaded by "
+                         "the CTA's threads), 2 = the same with the window loaded by TMA bulk "
+                         "tensor copies; 0 (default) = one thread per particle")
     ap.add_argument("--bz-physics", action="store_true",
                     help="run the BZ monopole test of Sec. 4.5 and report its closed-form checks")
     ap.add_argument("--bz-n", type=int, default=512, help="--bz-physics: cells per direction")
     ap.add_argument("--bz-time", type=float, default=60.0, help="--bz-physics: run time, r_g")
     ap.add_argument("--bz-precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--bz-inject-every", type=int, default=1,
+                    help="--bz-physics: pair injection after every k-th step (reading R32: 1)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true",

@@ -128,9 +128,14 @@ typedef struct {
                            metric is evaluated in FP64 (default 4 when 0)                     */
   int tiled_push;       /* GRPIC_MIXED: 1 = after a sort, push each sort tile in one CTA with
                            the fields of the tile and a 6-cell halo staged in shared memory and
-                           the currents accumulated there; 0 (default) = one thread per
-                           particle over the whole species with gathers through L1/L2, which
-                           measures faster on GB300 for this pusher                            */
+                           the currents accumulated there (the window loaded by the CTA's
+                           threads); 2 = the same with the window loaded by the tensor memory
+                           accelerator (one thread issues one bulk tensor copy per field plane
+                           from a copy of the planes with rows padded to 16 bytes, made before
+                           each push; needs tile_r a multiple of 4, else GRPIC_EINVAL);
+                           0 (default) = one thread per particle over the whole species with
+                           gathers through L1/L2, which measures faster on GB300 for this
+                           pusher                                                             */
   double iter_tol;      /* the implicit pushes (steps 6 and 10 of Sec. 3.1): 0 (default) = the
                            stop rule of full_iterations; > 0 = an FP32 predictor iterates each
                            to an exact FP32 repeat and gives the map's Jacobian there; one FP64
@@ -184,6 +189,9 @@ typedef struct {
   int64_t alive[GRPIC_MAX_SPECIES];
   int64_t injected;      /* pairs added by grpic_inject                             */
   int64_t inject_dropped; /* pairs grpic_inject found no room for                   */
+  int64_t stage_timeouts; /* tile windows whose tensor copies did not complete within the
+                             kernel's bounded wait (tiled_push = 2; the tile's particles were
+                             left unpushed); 0 in a healthy run                            */
 } grpic_diag;
 
 /* --- set-up ----------------------------------------------------------------------- */
@@ -515,15 +523,16 @@ GRPIC_API grpic_status grpic_set_keep_prev(grpic_ctx *ctx, int keep);
 /* Throughput probe of the arithmetic pipes that bound the pusher kernels; no counterpart in
  * the paper (it supplies the measured denominator of their rooflines). Queues on `stream`
  * (cudaStream_t; null: the default stream) one kernel of blocks_per_sm x (SM count) blocks of
- * 256 threads on the current device, each thread running 8 independent FMA chains of
- * 32 x iters steps: precision GRPIC_FP64 in double (the FP64 pipe's FMA rate), GRPIC_MIXED in
- * float (the FP32 pipe, at one warp instruction per clock per SM sub-partition, i.e. the
- * instruction-issue peak). *ops receives the FMA operations the launch performs; time it
- * with events on the stream. sink: one device double, never written in practice (it keeps
- * the chains live). Allocates nothing. Errors: GRPIC_EINVAL (iters < 1, blocks_per_sm not
- * in 1 .. 64, null sink or ops, other precision), GRPIC_ECUDA (a CUDA error pending before
- * the call, which it leaves in place, or a failed launch). */
-GRPIC_API grpic_status grpic_probe_fma(int precision, int64_t iters, int blocks_per_sm,
+ * 256 threads on the current device, each thread running 8 independent chains of 32 x iters
+ * operations op (0: fused multiply-add, 1: multiply, 2: add): precision GRPIC_FP64 in double
+ * (the FP64 pipe's rate for that operation), GRPIC_MIXED in float (the FP32 pipe, at one warp
+ * instruction per clock per SM sub-partition, i.e. the instruction-issue peak). *ops
+ * receives the operations the launch performs; time it with events on the stream. sink: one
+ * device double, never written in practice (it keeps the chains live). Allocates nothing.
+ * Errors: GRPIC_EINVAL (iters < 1, blocks_per_sm not in 1 .. 64, op not in 0 .. 2, null sink
+ * or ops, other precision), GRPIC_ECUDA (a CUDA error pending before the call, which it
+ * leaves in place, or a failed launch). */
+GRPIC_API grpic_status grpic_probe_alu(int precision, int op, int64_t iters, int blocks_per_sm,
                                        double *sink, void *stream, int64_t *ops);
 
 /* Enables (1) or disables (0) the per-phase events. Off by default. Instrumentation, with

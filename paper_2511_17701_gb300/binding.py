@@ -32,7 +32,7 @@ EXPORTS = ["grpic_create", "grpic_arena_bytes", "grpic_bind", "grpic_init_metric
            "grpic_destroy", "grpic_sort_permutation_noalloc", "grpic_invariants",
            "grpic_adjoint_forward", "grpic_adjoint_backward", "grpic_charge_check",
            "grpic_config_bytes", "grpic_inject", "grpic_step_host", "grpic_aux_fields",
-           "grpic_set_keep_prev", "grpic_probe_fma", "grpic_sum_bins_add",
+           "grpic_set_keep_prev", "grpic_probe_alu", "grpic_sum_bins_add",
            "grpic_sum_bins_value"]
 
 
@@ -82,7 +82,7 @@ class Diag(C.Structure):
     _fields_ = [("left_inner", C.c_int64), ("left_outer", C.c_int64),
                 ("reflections", C.c_int64), ("nonfinite", C.c_int64),
                 ("alive", C.c_int64 * MAX_SPECIES), ("injected", C.c_int64),
-                ("inject_dropped", C.c_int64)]
+                ("inject_dropped", C.c_int64), ("stage_timeouts", C.c_int64)]
 
 
 _lib = None
@@ -128,7 +128,8 @@ def lib(build: bool = True):
         L.grpic_get_diagnostics.argtypes = [P, C.POINTER(Diag)]
         L.grpic_set_timing.argtypes = [P, C.c_int]
         L.grpic_set_keep_prev.argtypes = [P, C.c_int]
-        L.grpic_probe_fma.argtypes = [C.c_int, C.c_int64, C.c_int, P, P, C.POINTER(C.c_int64)]
+        L.grpic_probe_alu.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int, P, P,
+                                      C.POINTER(C.c_int64)]
         L.grpic_sum_bins_add.argtypes = [P, C.c_int64, P, P]
         L.grpic_sum_bins_value.argtypes = [P, C.POINTER(C.c_double)]
         L.grpic_get_timing.argtypes = [P, C.POINTER(Timing)]
@@ -463,7 +464,8 @@ class Sim:
         return {"left_inner": d.left_inner, "left_outer": d.left_outer,
                 "reflections": d.reflections, "nonfinite": d.nonfinite,
                 "alive": [d.alive[i] for i in range(self.n_species)],
-                "injected": d.injected, "inject_dropped": d.inject_dropped}
+                "injected": d.injected, "inject_dropped": d.inject_dropped,
+                "stage_timeouts": d.stage_timeouts}
 
     def set_keep_prev(self, keep: bool):
         """grpic_set_keep_prev: whether the fused push + deposit stores previous positions."""
@@ -481,16 +483,19 @@ class Sim:
         self.stream.synchronize()
 
 
-def probe_fma(precision: str, iters: int, blocks_per_sm: int, sink, stream) -> int:
-    """grpic_probe_fma: queue the FMA-throughput probe kernel on `stream` (a torch stream);
-    sink: a float64 device tensor of at least one element. Returns the FMA operations the
-    launch performs (threads x chains x iters)."""
+PROBE_OPS = {"fma": 0, "mul": 1, "add": 2}
+
+
+def probe_alu(precision: str, op: str, iters: int, blocks_per_sm: int, sink, stream) -> int:
+    """grpic_probe_alu: queue the arithmetic-throughput probe kernel on `stream` (a torch
+    stream); precision "fp64" or "fp32", op "fma", "mul" or "add"; sink: a float64 device
+    tensor of at least one element. Returns the operations the launch performs."""
     ops = C.c_int64()
-    st = lib().grpic_probe_fma(MIXED if precision == "fp32" else FP64, int(iters),
+    st = lib().grpic_probe_alu(MIXED if precision == "fp32" else FP64, PROBE_OPS[op], int(iters),
                                int(blocks_per_sm), sink.data_ptr(), stream.cuda_stream,
                                C.byref(ops))
     if st != OK:
-        raise GrpicError("grpic_probe_fma failed (status %d)" % st)
+        raise GrpicError("grpic_probe_alu failed (status %d)" % st)
     return ops.value
 
 

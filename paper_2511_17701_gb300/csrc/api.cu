@@ -12,6 +12,8 @@
 #include <utility>
 #include <vector>
 
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
+
 #include "grpic_internal.cuh"
 
 namespace {
@@ -98,6 +100,10 @@ struct grpic_ctx {
   int64_t step = 0;
   bool timing = false;
   bool keep_prev = true;  // the fused push + deposit stores the previous positions
+  // tiled_push = 2: the padded copy of B^n and D the tensor copies read, and its tensor map
+  size_t off_pad = 0;
+  int NXp = 0;
+  alignas(64) CUtensorMap tmap;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PH_N];
   size_t ev_used[PH_N] = {};
   int64_t push_calls = 0;
@@ -265,8 +271,18 @@ cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, int k, bool deposit, int sta
                        kt ? kt->first : nullptr, kt ? kt->second : nullptr, stage};
   const int tr = c->cfg.tile_r, tt = c->cfg.tile_theta;
   const int ntr = (c->g.n_r + tr - 1) / tr, ntt = (c->g.n_th + tt - 1) / tt;
-  const TileInfo ti{sp.tiles_valid && c->cfg.tiled_push ? sp.tile_start : nullptr, tr, tt, ntr,
-                    ntr * ntt};
+  TileInfo ti{};
+  ti.start = sp.tiles_valid && c->cfg.tiled_push ? sp.tile_start : nullptr;
+  ti.tr = tr;
+  ti.tt = tt;
+  ti.ntr = ntr;
+  ti.n_tiles = ntr * ntt;
+  if (c->cfg.tiled_push == 2) {
+    ti.tma = 1;
+    ti.map = c->tmap;
+    ti.pad = at<float>(c, c->off_pad);
+    ti.NXp = c->NXp;
+  }
   // step 1 of Sec. 3.1 stores the previous position for the deposit; a push that deposits
   // its own move needs it only when a later call reads it (grpic_set_keep_prev): null
   // previous-position arrays tell the kernels to skip the stores
@@ -349,6 +365,13 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   if (c.n_species < 1 || c.n_species > GRPIC_MAX_SPECIES) return GRPIC_EINVAL;
   if (c.precision != GRPIC_FP64 && c.precision != GRPIC_MIXED) return GRPIC_EINVAL;
   if (c.tile_r < 1 || c.tile_theta < 1 || c.sort_every < 0) return GRPIC_EINVAL;
+  // the TMA-staged tiled push: the window's first column (tile start - halo + ghosts) must be
+  // a multiple of 4 floats, the 16 bytes a tensor copy's innermost coordinate needs
+  if (c.tiled_push < 0 || c.tiled_push > 2) return GRPIC_EINVAL;
+  if (c.tiled_push == 2 && (c.precision != GRPIC_MIXED || c.tile_r % 4 != 0 ||
+                            (G_ - TILE_HALO) % 4 != 0 || c.tile_r + 2 * TILE_HALO > 256 ||
+                            c.tile_theta + 2 * TILE_HALO > 256))
+    return GRPIC_EINVAL;
   if (c.tile_r > 65536 || c.tile_theta > 65536) return GRPIC_EINVAL;
   {  // the sort's largest live key (the tile-padded cell count) below the dead key, in int range
     const uint64_t ntr = (uint64_t)((c.n_r + c.tile_r - 1) / c.tile_r);
@@ -445,6 +468,10 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   }
   ctx->off_rho = off; off += 6 * up(ps * 8) + up(64);  // FP64 charge planes of the check
   ctx->off_inj = off; off += up(inject_scratch_bytes(g));  // pair injection per-cell scratch
+  if (c.tiled_push == 2) {  // [6][NY][NXp] floats, rows padded to 16 bytes
+    ctx->NXp = (g.NX + 3) / 4 * 4;
+    ctx->off_pad = off; off += up((size_t)6 * g.NY * ctx->NXp * 4);
+  }
   ctx->load_chunk = ctx->max_cap < ((int64_t)1 << 20) ? ctx->max_cap : ((int64_t)1 << 20);
   ctx->off_stage = off; off += 6 * up((size_t)ctx->load_chunk * 8);
   ctx->need = off;
@@ -476,6 +503,28 @@ grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream)
   ctx->tb.t1_64 = at<double>(ctx, ctx->off_ptab + 8 * tstride);
   ctx->tb.t2_64 = at<double>(ctx, ctx->off_ptab + 9 * tstride);
   ctx->tb.th64 = at<double>(ctx, ctx->off_ptab + 10 * tstride);
+  if (ctx->cfg.tiled_push == 2) {
+    // tensor map of the padded planes [6][NY][NXp] (FP32), box one window plane W1 x W2 x 1;
+    // the encoder comes from the driver through the runtime (no link to the driver library)
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return fail(ctx, GRPIC_ECUDA, "cuTensorMapEncodeTiled is not available");
+    const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t NXp = (cuuint64_t)ctx->NXp, NY = (cuuint64_t)ctx->g.NY;
+    const cuuint64_t dims[3] = {NXp, NY, 6};
+    const cuuint64_t strides[2] = {NXp * 4, NXp * NY * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)(ctx->cfg.tile_r + 2 * TILE_HALO),
+                               (cuuint32_t)(ctx->cfg.tile_theta + 2 * TILE_HALO), 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = encode(&ctx->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                              at<float>(ctx, ctx->off_pad), dims, strides, box, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, GRPIC_ECUDA, "tensor map encoding failed (%d)", (int)r);
+  }
   if (ctx->mixed) {
     for (int s = 0; s < ctx->cfg.n_species; ++s) {
       SpeciesState &sp = ctx->sp[s];
@@ -859,7 +908,9 @@ cudaError_t push_range(grpic_ctx *c, int k, int64_t a, int64_t m, const int64_t 
   v.n = n_chunk;
   const PushStreams ps{c->stream, c->side, c->ev_fork[k], c->ev_done[k], c->ev_class[k],
                        nullptr, nullptr, PUSH_ALL};
-  const TileInfo ti{nullptr, c->cfg.tile_r, c->cfg.tile_theta, 0, 0};
+  TileInfo ti{};
+  ti.tr = c->cfg.tile_r;
+  ti.tt = c->cfg.tile_theta;
   return launch_push<double>(c->g, c->F64, v, c->tb, sp.gl, ti, m, !sp.massless, c->diag, ps);
 }
 
@@ -1147,6 +1198,7 @@ grpic_status grpic_get_diagnostics(grpic_ctx *ctx, grpic_diag *out) {
   out->nonfinite = (int64_t)h[DG_NONFINITE];
   out->injected = (int64_t)h[DG_INJECTED];
   out->inject_dropped = (int64_t)h[DG_INJECT_DROPPED];
+  out->stage_timeouts = (int64_t)h[DG_STAGE_TIMEOUT];
   return GRPIC_OK;
 }
 

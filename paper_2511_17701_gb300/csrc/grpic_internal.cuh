@@ -7,6 +7,7 @@
 // here), dphi = 1; r0 = h0 = 0 is the plain log-r grid with uniform theta. Mass M = 1
 // (Kerr-Schild) or M = 0 and a = 0 (kerr_schild_0, flat).
 #pragma once
+#include <cuda.h>  // CUtensorMap (the tensor-map descriptor of the TMA-staged tiled push)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,6 +25,7 @@ struct GridP {
   double r_min, r_max, dxi, dth, a, M, dt, small_angle, r_absorb, absorb_coef;
   double idt;       // 1 / dt
   double pi_small;  // pi - small_angle
+  double a2, M2;    // a^2 and 2 M
   double ig2;  // 1 / dth^2
   // quasi-spherical map: radial offset, equatorial concentration, qks = (r0 != 0 || h0 != 0),
   // c3 = 4 h0 / pi^2 (the cubic coefficient of theta(eta_j + d) - theta(eta_j))
@@ -31,13 +33,17 @@ struct GridP {
   double e_min;  // r_min - r0 = exp(xi) at x1 = 0
   int qks;
   // FP32 copies for the mixed path (read from the kernel parameters, no conversions)
-  float f_a, f_M, f_dxi, f_dth, f_ig2, f_dt, f_idt, f_r0, f_c3, f_iter_tol;
+  float f_a, f_M, f_dxi, f_dth, f_ig2, f_dt, f_idt, f_r0, f_c3, f_iter_tol, f_a2, f_M2;
 };
 
 // Fill the FP32 copies once a, M, dxi, dth and dt are set.
 inline void grid_float_copies(GridP &g) {
   g.idt = g.dt > 0.0 ? 1.0 / g.dt : 0.0;
   g.pi_small = GRPIC_PI - g.small_angle;
+  g.a2 = g.a * g.a;
+  g.M2 = 2.0 * g.M;
+  g.f_a2 = g.f_a * g.f_a;
+  g.f_M2 = 2.0f * g.f_M;
   g.f_iter_tol = (float)g.iter_tol;
   g.f_a = (float)g.a; g.f_M = (float)g.M; g.f_dxi = (float)g.dxi; g.f_dth = (float)g.dth;
   g.f_ig2 = (float)g.ig2; g.f_dt = (float)g.dt; g.f_idt = g.dt > 0.0 ? (float)(1.0 / g.dt) : 0.0f;
@@ -77,21 +83,22 @@ __device__ __forceinline__ void map_g(const GridP &g, double x2, double &gg, dou
 }
 
 // The grid constants in the arithmetic type R.
+// (a2 = a a and M2 = 2 M, rounded as the products the metric would form)
 template <typename R>
 struct Cst {
-  R a, M, dxi, dth, ig2, dt;
+  R a, M, dxi, dth, ig2, dt, a2, M2;
 };
 template <typename R>
 __device__ __forceinline__ Cst<R> cst(const GridP &g) {  // other arithmetic types (duals)
-  return {R(g.a), R(g.M), R(g.dxi), R(g.dth), R(g.ig2), R(g.dt)};
+  return {R(g.a), R(g.M), R(g.dxi), R(g.dth), R(g.ig2), R(g.dt), R(g.a2), R(g.M2)};
 }
 template <>
 __device__ __forceinline__ Cst<double> cst<double>(const GridP &g) {
-  return {g.a, g.M, g.dxi, g.dth, g.ig2, g.dt};
+  return {g.a, g.M, g.dxi, g.dth, g.ig2, g.dt, g.a2, g.M2};
 }
 template <>
 __device__ __forceinline__ Cst<float> cst<float>(const GridP &g) {
-  return {g.f_a, g.f_M, g.f_dxi, g.f_dth, g.f_ig2, g.f_dt};
+  return {g.f_a, g.f_M, g.f_dxi, g.f_dth, g.f_ig2, g.f_dt, g.f_a2, g.f_M2};
 }
 
 // Yee point classes of the metric tables: (i, j), (i+1/2, j), (i, j+1/2), (i+1/2, j+1/2).
@@ -124,7 +131,7 @@ using SpeciesDev = SpeciesDevT<double>;
 
 // Diagnostics counters on the device (unsigned long long for atomicAdd).
 enum { DG_LEFT_INNER = 0, DG_LEFT_OUTER, DG_REFLECT, DG_NONFINITE, DG_INJECTED,
-       DG_INJECT_DROPPED, DG_N };
+       DG_INJECT_DROPPED, DG_STAGE_TIMEOUT, DG_N };
 
 // ---------------------------------------------------------------------------------
 // Metric of Appendix A, written directly in the code-unit (xi, eta) form of the
@@ -347,10 +354,16 @@ struct GuardList {
 // The particle range of every sort tile (mixed path): particles tile_start[t] ..
 // tile_start[t+1] - 1 were in tile t at the last sort (start is null when no sort has run
 // since the particles were last set, and the push does not use tiles).
-struct TileInfo {
+// tma: the window comes from `pad` (the 6 planes B^n, D with rows padded to NXp floats, a
+// multiple of 4) by the tensor copies of `map` (a 3D map over [6][NY][NXp] with a box of
+// one window plane); the kernel takes it as a __grid_constant__ parameter.
+struct alignas(64) TileInfo {
+  CUtensorMap map;
   const uint32_t *start;
-  int tr, tt, ntr, n_tiles;
+  float *pad;
+  int tr, tt, ntr, n_tiles, tma, NXp;
 };
+constexpr int TILE_HALO = 6;  // cells of the window beyond the tile on every side
 
 // Streams of one push: the classification and the FP64-pipe-bound guard kernels run on
 // `side`, forked from `main` by `fork`; `done` is recorded on `side` after them and the

@@ -1159,8 +1159,11 @@ __global__ void __launch_bounds__(TPB) k_classify(GridP g, SpeciesDevT<float> s,
 // gathers and atomics need many resident warps to hide their latency: 12 blocks per SM (40
 // registers, a few spills to L1) measured 0.60 ms per 8.4 M particles against 0.71 ms with
 // 6 (80 registers, no spills) on GB300; at 12 it is bound by instruction issue.
+#ifndef GRPIC_PUSH32_MIN_BLOCKS  // resident blocks per SM the FP32 kernel is built for
+#define GRPIC_PUSH32_MIN_BLOCKS 12
+#endif
 template <bool DEPOSIT, bool Q>
-__global__ void __launch_bounds__(TPB, 12) k_push32(GridP g, FieldPtrsT<float> F,
+__global__ void __launch_bounds__(TPB, GRPIC_PUSH32_MIN_BLOCKS) k_push32(GridP g, FieldPtrsT<float> F,
                                                 SpeciesDevT<float> s, PushTables tb,
                                                 GuardList gl, unsigned long long *diag) {
   const int64_t n = *s.n;
@@ -1186,30 +1189,115 @@ __global__ void __launch_bounds__(TPB, 12) k_push32(GridP g, FieldPtrsT<float> F
 // are staged in shared memory; the deposit (after the warp reduction) accumulates in a
 // shared-memory window of the same extent, flushed to global memory at the end. A particle
 // whose cell has drifted out of the window gathers from, and deposits to, global memory.
-constexpr int TILE_HALO = 6;
+// The window is loaded by the CTA's threads, or (TMA) by the tensor memory accelerator: one
+// thread issues one bulk tensor copy per field plane, the others wait on an mbarrier.
 constexpr int TILE_TPB = 256;
-template <bool DEPOSIT, bool Q>
+
+// floats per window plane in shared memory: W1 x W2 rounded up to 128 bytes (the tensor
+// copies' destinations)
+__host__ __device__ inline int window_plane(int W1, int W2) { return (W1 * W2 + 31) / 32 * 32; }
+
+// The padded copy the tensor copies read: B^n and D ([NY][NX] each) into [6][NY][NXp], rows
+// padded with zeros to NXp (a multiple of 4 floats, so every row starts on 16 bytes).
+__global__ void __launch_bounds__(256) k_pad_fields(FieldPtrsT<float> F, float *pad, int NX,
+                                                   int NY, int NXp) {
+  const int64_t per = (int64_t)NY * NXp, n = 6 * per;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / per);
+    const int64_t r = t - c * per;
+    const int j = (int)(r / NXp), i = (int)(r - (int64_t)j * NXp);
+    pad[t] = i < NX ? __ldg((c < 3 ? F.Bn[c] : F.D[c - 3]) + (int64_t)j * NX + i) : 0.0f;
+  }
+}
+
+// The tile window by the tensor memory accelerator: thread 0 initialises the barrier, arms it
+// with the window's bytes and issues one 3D tensor copy per field plane (a box of W1 x W2 x 1
+// at column x0, row y0 of plane c of the padded copy; zeros outside it). Every thread then
+// polls the barrier's phase 0 for at most about a second of clock cycles. Returns false when
+// the copies did not complete (counted in the diagnostics, after a second bounded wait for
+// them); the CTA then leaves its tile.
+constexpr long long STAGE_WAIT_CYCLES = 2000000000ll;
+__device__ __forceinline__ bool wait_phase0(uint32_t bar) {
+  uint32_t done = 0;
+  const long long t0 = clock64();
+  while (!done && clock64() - t0 < STAGE_WAIT_CYCLES) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar)
+        : "memory");
+  }
+  return done != 0;
+}
+__device__ __forceinline__ bool stage_tma(const TileInfo &ti, float *fwin, int PL, int x0, int y0,
+                                          int W1, int W2, uint64_t *barp,
+                                          unsigned long long *diag) {
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(barp);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = 6u * (uint32_t)W1 * (uint32_t)W2 * 4u;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    const uint64_t map = reinterpret_cast<uint64_t>(&ti.map);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(fwin + c * PL);
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+          " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+          "l"(map), "r"(x0), "r"(y0), "r"(c), "r"(bar)
+          : "memory");
+    }
+  }
+  const bool ok = wait_phase0(bar);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicAdd(diag + DG_STAGE_TIMEOUT, 1ull);
+    wait_phase0(bar);  // the copies may still land: a second bounded wait before leaving
+    return false;
+  }
+  return true;
+}
+
+template <bool DEPOSIT, bool Q, bool TMA>
 __global__ void __launch_bounds__(TILE_TPB) k_push32_tiled(GridP g, FieldPtrsT<float> F,
                                                           SpeciesDevT<float> s, PushTables tb,
-                                                          GuardList gl, TileInfo ti,
+                                                          GuardList gl,
+                                                          const __grid_constant__ TileInfo ti,
                                                           unsigned long long *diag) {
-  extern __shared__ float sm[];
+  extern __shared__ float sm_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  // 128-byte aligned window planes (the launch adds the slack)
+  float *sm = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~static_cast<uintptr_t>(127));
   const int t = blockIdx.x;
   const int tx = t % ti.ntr, ty = t / ti.ntr;
-  const int W1 = ti.tr + 2 * TILE_HALO, W2 = ti.tt + 2 * TILE_HALO, plane = W1 * W2;
+  const int W1 = ti.tr + 2 * TILE_HALO, W2 = ti.tt + 2 * TILE_HALO;
+  const int plane = window_plane(W1, W2);
   const int iw0 = tx * ti.tr - TILE_HALO, jw0 = ty * ti.tt - TILE_HALO;
   float *fwin = sm, *jwin = sm + 6 * plane;
-  // stage the fields (zero outside the stored planes) and clear the current window
-  for (int e = threadIdx.x; e < 6 * plane; e += blockDim.x) {
-    const int c = e / plane, r = e - c * plane, wj = r / W1, wi = r - wj * W1;
-    const int i = iw0 + wi, j = jw0 + wj;
-    float v = 0.0f;
-    if (i >= -G_ && i < g.NX - G_ && j >= -G_ && j < g.NY - G_)
-      v = __ldg((c < 3 ? F.Bn[c] : F.D[c - 3]) + sidx(g, i, j));
-    fwin[e] = v;
-  }
   if (DEPOSIT)
     for (int e = threadIdx.x; e < 3 * plane; e += blockDim.x) jwin[e] = 0.0f;
+  if constexpr (TMA) {
+    // window node (0, 0) is storage column iw0 + G, row jw0 + G (a multiple of 4 columns)
+    if (!stage_tma(ti, fwin, plane, iw0 + G_, jw0 + G_, W1, W2, &bar, diag)) return;
+  } else {
+    // stage the fields (zero outside the stored planes)
+    for (int e = threadIdx.x; e < 6 * W1 * W2; e += blockDim.x) {
+      const int c = e / (W1 * W2), r = e - c * (W1 * W2), wj = r / W1, wi = r - wj * W1;
+      const int i = iw0 + wi, j = jw0 + wj;
+      float v = 0.0f;
+      if (i >= -G_ && i < g.NX - G_ && j >= -G_ && j < g.NY - G_)
+        v = __ldg((c < 3 ? F.Bn[c] : F.D[c - 3]) + sidx(g, i, j));
+      fwin[c * plane + r] = v;
+    }
+  }
   __syncthreads();
   const WindowFields wf{fwin, W1, plane, iw0, jw0};
   const GlobalFields gf(g, F);
@@ -1239,9 +1327,10 @@ __global__ void __launch_bounds__(TILE_TPB) k_push32_tiled(GridP g, FieldPtrsT<f
   if (DEPOSIT) {
     __syncthreads();
     for (int e = threadIdx.x; e < 3 * plane; e += blockDim.x) {
+      const int c = e / plane, r = e - c * plane;
       const float v = jwin[e];
-      if (v != 0.0f) {
-        const int c = e / plane, r = e - c * plane, wj = r / W1, wi = r - wj * W1;
+      if (v != 0.0f && r < W1 * W2) {
+        const int wj = r / W1, wi = r - wj * W1;
         atomicAdd(F.J[c] + sidx(g, iw0 + wi, jw0 + wj), v);
       }
     }
@@ -1249,7 +1338,8 @@ __global__ void __launch_bounds__(TILE_TPB) k_push32_tiled(GridP g, FieldPtrsT<f
 }
 
 size_t tiled_smem_bytes(const TileInfo &ti) {
-  return (size_t)9 * (ti.tr + 2 * TILE_HALO) * (ti.tt + 2 * TILE_HALO) * sizeof(float);
+  return (size_t)9 * window_plane(ti.tr + 2 * TILE_HALO, ti.tt + 2 * TILE_HALO) * sizeof(float) +
+         128;
 }
 
 // Mixed path, guard kernels (side stream): step 1 and the routine of the listed particles,
@@ -1486,17 +1576,29 @@ cudaError_t push_impl(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
     const size_t smem = tiled_smem_bytes(ti);
     const bool tiled = ti.start != nullptr && smem <= 200 * 1024;
     if (tiled && smem > 48 * 1024) {
-      if ((e = cudaFuncSetAttribute(k_push32_tiled<true, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem)) != cudaSuccess) return e;
-      if ((e = cudaFuncSetAttribute(k_push32_tiled<false, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem)) != cudaSuccess) return e;
+      void (*const kern[4])(GridP, FieldPtrsT<float>, SpeciesDevT<float>, PushTables, GuardList,
+                            const TileInfo, unsigned long long *) = {
+          k_push32_tiled<true, Q, false>, k_push32_tiled<false, Q, false>,
+          k_push32_tiled<true, Q, true>, k_push32_tiled<false, Q, true>};
+      for (auto *f : kern)
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess) return e;
+    }
+    if (tiled && ti.tma) {  // the padded copy the tensor copies read
+      k_pad_fields<<<152 * 8, 256, 0, ps.main>>>(F, ti.pad, g.NX, g.NY, ti.NXp);
+      COUNT_LAUNCH(1);
     }
     if (ps.t0) cudaEventRecord(ps.t0, ps.main);
-    if (tiled) {
+    if (tiled && ti.tma) {
       if (deposit)
-        k_push32_tiled<true, Q><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
+        k_push32_tiled<true, Q, true><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
       else
-        k_push32_tiled<false, Q><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
+        k_push32_tiled<false, Q, true><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
+    } else if (tiled) {
+      if (deposit)
+        k_push32_tiled<true, Q, false><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
+      else
+        k_push32_tiled<false, Q, false><<<ti.n_tiles, TILE_TPB, smem, ps.main>>>(g, F, s, tb, gl, ti, diag);
     } else {
       if (deposit) k_push32<true, Q><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);
       else k_push32<false, Q><<<nb, TPB, 0, ps.main>>>(g, F, s, tb, gl, diag);

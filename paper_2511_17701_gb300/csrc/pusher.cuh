@@ -40,11 +40,11 @@ struct Geo {
 template <bool Q = true, typename R>
 __device__ __forceinline__ void geo_from_rsc(const GridP &g, const Pt<R> &p, Geo<R> &o) {
   const Cst<R> k = cst<R>(g);
-  const R a = k.a, M = k.M, a2 = a * a;
+  const R a = k.a, a2 = k.a2, M2 = k.M2;
   const R r = p.r, s2 = p.s * p.s, r2 = r * r;
   const R Sig = fma_(a2, p.c * p.c, r2);
-  const R S2 = fma_((R)2 * M, r, Sig);  // Sigma + 2 M r
-  const R A = (r2 + a2) * (r2 + a2) - a2 * (r2 - (R)2 * M * r + a2) * s2;
+  const R S2 = fma_(M2, r, Sig);  // Sigma + 2 M r
+  const R A = (r2 + a2) * (r2 + a2) - a2 * (r2 - M2 * r + a2) * s2;
   const R f = p.f;
   const R u = Sig * S2 * f;
   R iQ, igg;
@@ -64,7 +64,7 @@ __device__ __forceinline__ void geo_from_rsc(const GridP &g, const Pt<R> &p, Geo
   o.H13 = a * iSig * fi;
   o.H22 = iSig * igg;
   o.H33 = iQ * u * iSig;                // 1 / (Sigma s^2)
-  o.beta1 = (R)2 * M * r * iS2 * fi;
+  o.beta1 = M2 * r * iS2 * fi;
 }
 
 // The metric at x^n with the derivatives the momentum push needs, and the tetrad
@@ -80,11 +80,11 @@ struct Local {
 template <bool Q = true, typename R>
 __device__ __forceinline__ void local_full(const GridP &g, const Pt<R> &p, Local<R> &L) {
   const Cst<R> k = cst<R>(g);
-  const R a = k.a, M = k.M, a2 = a * a, gg = p.gg, dxi = k.dxi;
+  const R a = k.a, M = k.M, a2 = k.a2, M2 = k.M2, gg = p.gg, dxi = k.dxi;
   const R r = p.r, s = p.s, c = p.c, r2 = r * r, s2 = s * s;
   const R Sig = fma_(a2, c * c, r2);
-  const R S2 = fma_((R)2 * M, r, Sig);
-  const R Del = r2 - (R)2 * M * r + a2;
+  const R S2 = fma_(M2, r, Sig);
+  const R Del = r2 - M2 * r + a2;
   const R A = (r2 + a2) * (r2 + a2) - a2 * Del * s2;
   const R f = p.f;
   const R u = Sig * S2 * f;
@@ -107,7 +107,7 @@ __device__ __forceinline__ void local_full(const GridP &g, const Pt<R> &p, Local
   o.H13 = a * iSig * fi;
   o.H22 = iSig * igg;
   o.H33 = iSig * is2;
-  o.beta1 = (R)2 * M * r * iS2 * fi;
+  o.beta1 = M2 * r * iS2 * fi;
   const R al2 = Sig * iS2;
   L.alpha = rsqrt_(o.opz);
   const R dxS = (R)2 * r * f, deS = (R)-2 * a2 * s * c * gg;
@@ -130,7 +130,7 @@ __device__ __forceinline__ void local_full(const GridP &g, const Pt<R> &p, Local
   const R fsr = f * Sig - r * dxS;
   L.d1alpha = -M * fsr * iSg2 * al3;
   L.d2alpha = M * r * deS * iSg2 * al3;
-  L.d1beta1 = (R)2 * M * fi * fsr * iS2 * iS2 - dxi * o.beta1;
+  L.d1beta1 = M2 * fi * fsr * iS2 * iS2 - dxi * o.beta1;
   L.d2beta1 = (R)-2 * M * fi * r * deS * iS2 * iS2;
   const R h22 = gg * gg * Sig, h33 = A * s2 * iSig, h13 = -f * a * o.opz * s2;
   L.rH11 = rsqrt_(o.H11);

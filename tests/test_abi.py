@@ -55,7 +55,10 @@ def test_create_and_arena_size():
 @pytest.mark.parametrize("bad", [dict(a=1.0), dict(a=-0.1), dict(n_r=2), dict(r_min=0.0),
                                  dict(r_max=1.0), dict(n_iter=0), dict(small_angle=0.0),
                                  dict(cfl=0.0), dict(cfl=1.5), dict(tile_r=0),
-                                 dict(n_filter=62)])
+                                 dict(n_filter=62), dict(tiled_push=3),
+                                 dict(tiled_push=2, precision="fp64"),
+                                 dict(tiled_push=2, precision="mixed", tile_r=6),
+                                 dict(tiled_push=2, precision="mixed", tile_r=248)])
 def test_create_rejects_bad_configs(bad):
     cfg = dict(good_cfg(), **bad)
     st, ctx = create(cfg)
@@ -153,3 +156,9 @@ def test_noalloc_sort_validates_before_any_cuda_work():
                                             None) == B.ECAPACITY
     assert L.grpic_sort_permutation_noalloc(37, 23, 8, 4, None, p, p, 10, p, p, None) == B.EINVAL
     assert L.grpic_sort_permutation_noalloc(37, 23, 8, 4, p, p, p, 10, p, None, None) == B.EINVAL
+
+
+def test_create_accepts_the_tma_tiled_push():
+    st, ctx = create(dict(good_cfg(), tiled_push=2, precision="mixed", tile_r=16, tile_theta=10))
+    assert st == B.OK
+    B.lib().grpic_destroy(ctx)
