@@ -164,14 +164,19 @@ def test_boundary_particles(setup):
 
 
 def test_adjoint_long_horizon_matches_oracle_on_the_512_grid(torch_cuda):
-    """The adjoint workload's grid (512^2, r_max = 50) and horizon (2000 steps): the reverse
-    sweep against the oracle's complex-step Jacobian for 320 particles (at least 256 stay in
-    the domain), and against central differences of the GPU forward with their own error
-    estimate: per particle the differences at h, h/2 and h/4 (h = 4e-6) give two Richardson
-    extrapolations whose spread U estimates what the difference quotient itself can resolve.
-    Every particle agrees within 1e-6 of its gradient's scale, or its quotient's U is above
-    1e-6 and the agreement is within 3 U (the quotient, not the adjoint, is uncertain there:
-    the +-h orbits straddle kinks of the bilinear interpolation over 2000 steps)."""
+    """The adjoint workload's grid (512^2, r_max = 50) and horizon (2000 steps), 320 particles
+    (at least 256 stay in the domain).
+
+    Against the oracle's complex-step Jacobian (the exact derivative of the oracle's map):
+    every particle within 1e-10 of its gradient's scale (measured: 1e-13).
+
+    Against central differences of the GPU forward: over 2000 steps the +-h orbits cross
+    kinks of the bilinear interpolation, so the difference quotient converges to the
+    derivative only as h shrinks (measured on this set: 60% of particles within 1e-6 at
+    h = 3.2e-5, 85% at 1e-6, 97% at 6.25e-8, where the rounding of the loss is still ~1e-9 of
+    the scale). At h = 6.25e-8 at least 95% must agree within 1e-6, and wherever a particle
+    does not, the quotient itself must be off the exact derivative by more than 1e-6 and by
+    about the same amount (the disagreement is the quotient's, not the adjoint's)."""
     from paper_2511_17701_gb300 import FIELD_USER, Sim
     torch = torch_cuda
     cfg = W.grid_config("wald512", r_absorb=1e300)
@@ -203,36 +208,33 @@ def test_adjoint_long_horizon_matches_oracle_on_the_512_grid(torch_cuda):
                           np.einsum("kq,qk->k", J[:, :, 6], cot)[None]])
     sc = np.abs(ref).max(axis=0) + 1e-300
     exact_err = (np.abs(ad - ref).max(axis=0) / sc)[ok]
-    assert exact_err.max() < 1e-6, exact_err.max()
+    assert exact_err.max() < 1e-10, exact_err.max()
 
     def loss(st, b):
         o, _ = g.adjoint_forward(st, qm, b, n_steps, 100, N_ITER)
         return (o * cot_t).sum(dim=0)
 
-    def central(h):
-        fd = torch.zeros((7, st0.shape[1]), dtype=torch.float64, device="cuda")
-        for q in range(6):
-            sp_, sm_ = st0_t.clone(), st0_t.clone()
+    h = 6.25e-8
+    fd = np.zeros((7, st0.shape[1]))
+    for q in range(7):
+        sp_, sm_ = st0_t.clone(), st0_t.clone()
+        bp = bm = 1.0
+        if q < 6:
             sp_[q] += h
             sm_[q] -= h
-            fd[q] = (loss(sp_, 1.0) - loss(sm_, 1.0)) / (2 * h)
-        fd[6] = (loss(st0_t, 1.0 + h) - loss(st0_t, 1.0 - h)) / (2 * h)
-        return fd.cpu().numpy()
-
-    h = 4e-6
-    d1, d2, d4 = central(h), central(h / 2), central(h / 4)
-    r1, r2 = (4 * d2 - d1) / 3, (4 * d4 - d2) / 3
-    U = np.abs(r2 - r1).max(axis=0) / sc
-    fd_err = np.abs(ad - r2).max(axis=0) / sc
-    sel = ok & np.isfinite(U) & np.isfinite(fd_err)
-    assert sel.sum() >= 250
-    within = fd_err[sel] <= 1e-6
-    explained = (U[sel] > 1e-6) & (fd_err[sel] <= 3 * U[sel])
-    print("adjoint vs Richardson central differences over 2000 steps: %d particles, %.1f%% "
-          "within 1e-6 (median %.2e), the rest within 3x their quotient's uncertainty: %s"
-          % (sel.sum(), 100 * within.mean(), np.median(fd_err[sel]), bool(np.all(within | explained))))
-    assert np.all(within | explained)
-    assert within.mean() >= 0.75
+        else:
+            bp, bm = 1.0 + h, 1.0 - h
+        fd[q] = ((loss(sp_, bp) - loss(sm_, bm)) / (2 * h)).cpu().numpy()
+    fd_err = (np.abs(ad - fd).max(axis=0) / sc)[ok]
+    quotient_err = (np.abs(fd - ref).max(axis=0) / sc)[ok]
+    within = fd_err <= 1e-6
+    print("adjoint vs central differences (h = %g) over 2000 steps: %d particles, %.1f%% within "
+          "1e-6 (median %.2e); where not, the quotient is off the exact derivative by %s"
+          % (h, ok.sum(), 100 * within.mean(), np.median(fd_err),
+             np.round(quotient_err[~within], 8).tolist()))
+    assert within.mean() >= 0.95
+    assert np.all(quotient_err[~within] > 1e-6)
+    assert np.all(np.abs(quotient_err[~within] - fd_err[~within]) <= 1e-3 * fd_err[~within])
 
 
 def test_gpu_sum_bins_match_their_definition(torch_cuda):
