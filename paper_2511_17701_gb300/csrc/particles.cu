@@ -17,35 +17,6 @@ __device__ __forceinline__ void count(unsigned long long *diag, int which) {
   atomicAdd(diag + which, 1ull);
 }
 
-// ---------------------------------------------------------------------------------
-// Conversions and tests on the integer pipe. GB300's FP64 pipe bounds the FP64 kernel and
-// also executes the FP64 conversion, compare and min/max instructions; these bit-level forms
-// keep such work off it where the exact FP64 semantics are not needed.
-// ---------------------------------------------------------------------------------
-// A double in FP32's normal range truncated toward zero to 24 significant bits; a signed
-// zero below that range, a signed infinity above it, NaN kept. For the FP32 predictor's
-// inputs and for stop tests, where a start point or a bound moves by less than 2^-23 of itself.
-__device__ __forceinline__ float f32_trunc(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const unsigned sign = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu;
-  const int e = (int)ex - 896;  // rebias 1023 -> 127
-  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  unsigned r = sign | ((unsigned)e << 23) | m;
-  if (e <= 0) r = sign;
-  if (e >= 255) r = sign | 0x7f800000u | ((ex == 0x7ffu && (m | (lo & 0x1fffffffu))) ? 0x400000u : 0u);
-  return __uint_as_float(r);
-}
-// The exact double of a normal float; zero and subnormals become a signed zero, inf and NaN
-// are kept. For the FP32 predictor's results (FP64 start points) and the FP32 Newton
-// coefficients, which only steer FP64 iterations that are checked in FP64.
-__device__ __forceinline__ double f64_widen(float f) {
-  const unsigned v = __float_as_uint(f);
-  const unsigned sign = v & 0x80000000u, e = (v >> 23) & 0xffu, m = v & 0x7fffffu;
-  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
-  if (e == 0u) hi = sign, lo = 0u;
-  if (e == 255u) hi = sign | 0x7ff00000u | (m ? 0x80000u : 0u), lo = 0u;
-  return __hiloint2double((int)hi, (int)lo);
-}
 // x is neither infinite nor NaN
 __device__ __forceinline__ bool finite64(double x) {
   return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;

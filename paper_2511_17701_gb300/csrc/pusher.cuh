@@ -12,10 +12,55 @@ __device__ __forceinline__ double fma_(double a, double b, double c) { return fm
 __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
 __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
-// a / b: exact in FP64 (and for the adjoint's dual numbers); CUDA's fast FP32 division
-// (within 2 ulp) in FP32, whose arithmetic carries ~1e-7 relative errors anyway
+// ---------------------------------------------------------------------------------
+// Conversions and tests on the integer pipe. GB300's FP64 pipe bounds the FP64 kernel and
+// also executes the FP64 conversion, compare and min/max instructions; these bit-level forms
+// keep such work off it where the exact FP64 semantics are not needed.
+// ---------------------------------------------------------------------------------
+// A double in FP32's normal range truncated toward zero to 24 significant bits; a signed
+// zero below that range, a signed infinity above it, NaN kept. For the FP32 predictor's
+// inputs and for stop tests, where a start point or a bound moves by less than 2^-23 of itself.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu;
+  const int e = (int)ex - 896;  // rebias 1023 -> 127
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  unsigned r = sign | ((unsigned)e << 23) | m;
+  if (e <= 0) r = sign;
+  if (e >= 255) r = sign | 0x7f800000u | ((ex == 0x7ffu && (m | (lo & 0x1fffffffu))) ? 0x400000u : 0u);
+  return __uint_as_float(r);
+}
+// The exact double of a normal float; zero and subnormals become a signed zero, inf and NaN
+// are kept. For the FP32 predictor's results (FP64 start points) and the FP32 Newton
+// coefficients, which only steer FP64 iterations that are checked in FP64.
+__device__ __forceinline__ double f64_widen(float f) {
+  const unsigned v = __float_as_uint(f);
+  const unsigned sign = v & 0x80000000u, e = (v >> 23) & 0xffu, m = v & 0x7fffffu;
+  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+  if (e == 0u) hi = sign, lo = 0u;
+  if (e == 255u) hi = sign | 0x7ff00000u | (m ? 0x80000u : 0u), lo = 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+// 1/b in FP64 by Newton-Raphson iteration on the reciprocal (y <- y + y (1 - b y), each
+// step squaring the relative error) from an FP32 seed: b truncated to FP32 on the integer
+// pipe, CUDA's fast FP32 reciprocal (within 2 ulp, so a seed error below 2^-21), two FP64
+// steps (2^-42, then below the FP64 rounding): within about one ulp of the correctly rounded
+// quotient in four FMAs. A b outside FP32's normal range takes the IEEE division.
+__device__ __forceinline__ double rcp_nr(double b) {
+  const unsigned ex = ((unsigned)__double2hiint(b) >> 20) & 0x7ffu;
+  if (ex < 1023u - 125u || ex > 1023u + 126u) return 1.0 / b;
+  const double y0 = f64_widen(__fdividef(1.0f, f32_trunc(b)));
+  const double y1 = fma(y0, fma(-b, y0, 1.0), y0);
+  return fma(y1, fma(-b, y1, 1.0), y1);
+}
+
+// a / b for the pusher's quotients (a = 1 or 2): in FP64 a times rcp_nr(b) (a power of two:
+// exact); exact division for the adjoint's dual numbers; CUDA's fast FP32 division (within
+// 2 ulp) in FP32, whose arithmetic carries ~1e-7 relative errors anyway
 template <typename R>
 __device__ __forceinline__ R div_(R a, R b) { return a / b; }
+template <>
+__device__ __forceinline__ double div_<double>(double a, double b) { return a * rcp_nr(b); }
 template <>
 __device__ __forceinline__ float div_<float>(float a, float b) { return __fdividef(a, b); }
 
