@@ -26,6 +26,9 @@ struct GridP {
   double idt;       // 1 / dt
   double pi_small;  // pi - small_angle
   double a2, M2;    // a^2 and 2 M
+  // the same constants as pairs of floats (value hi + lo, about 48 bits) for the FP64
+  // pusher's double-float predictor: a, M, dxi, dth, 1/dth^2, dt, a^2, 2M
+  float d_a[2], d_M[2], d_dxi[2], d_dth[2], d_ig2[2], d_dt[2], d_a2[2], d_M2[2];
   double ig2;  // 1 / dth^2
   // quasi-spherical map: radial offset, equatorial concentration, qks = (r0 != 0 || h0 != 0),
   // c3 = 4 h0 / pi^2 (the cubic coefficient of theta(eta_j + d) - theta(eta_j))
@@ -44,6 +47,12 @@ inline void grid_float_copies(GridP &g) {
   g.M2 = 2.0 * g.M;
   g.f_a2 = g.f_a * g.f_a;
   g.f_M2 = 2.0f * g.f_M;
+  const double dv[8] = {g.a, g.M, g.dxi, g.dth, g.ig2, g.dt, g.a2, g.M2};
+  float *dp[8] = {g.d_a, g.d_M, g.d_dxi, g.d_dth, g.d_ig2, g.d_dt, g.d_a2, g.d_M2};
+  for (int k = 0; k < 8; ++k) {
+    dp[k][0] = (float)dv[k];
+    dp[k][1] = (float)(dv[k] - (double)dp[k][0]);
+  }
   g.f_iter_tol = (float)g.iter_tol;
   g.f_a = (float)g.a; g.f_M = (float)g.M; g.f_dxi = (float)g.dxi; g.f_dth = (float)g.dth;
   g.f_ig2 = (float)g.ig2; g.f_dt = (float)g.dt; g.f_idt = g.dt > 0.0 ? (float)(1.0 / g.dt) : 0.0f;
@@ -336,6 +345,8 @@ struct PushTables {
   const float *t1, *t2;
   const double *t1_64, *t2_64;
   const double *th64;  // theta at corner row j, formed as map_theta forms it
+  // exp(xi) at corner column i and sin, cos(theta) at corner row j as float pairs (hi, lo)
+  const float2 *r_df, *s_df, *c_df;
   int guard_ilo, guard_ihi;  // cells guard_ilo <= i1 < guard_ihi (around the horizon) and
   int guard_j;               // within guard_j of an axis evaluate the metric in FP64
 };
@@ -357,7 +368,7 @@ struct GuardList {
 // tma: the window comes from `pad` (the 6 planes B^n, D with rows padded to NXp floats, a
 // multiple of 4) by the tensor copies of `map` (a 3D map over [6][NY][NXp] with a box of
 // one window plane); the kernel takes it as a __grid_constant__ parameter.
-struct alignas(64) TileInfo {
+struct TileInfo {
   CUtensorMap map;
   const uint32_t *start;
   float *pad;

@@ -310,6 +310,98 @@ __device__ __forceinline__ void newton_step(const float J[2][2], double t0, doub
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Double-float predictor step of the refined iterations (plain grid). The implicit map is
+// evaluated once in float pairs (about 48 bits, dfloat.cuh) at the FP32 predictor's point,
+// and one Newton step with the FP32 Jacobian there lands within about 1e-14 of the FP64
+// fixed point (the predictor's 1e-7 error times the Jacobian's 1e-7 relative error, plus the
+// pairs' rounding): the FP64 evaluation that follows then usually meets the stop rule at
+// once, one FP64 map evaluation per substep instead of two. The arithmetic runs on the FP32
+// pipe, which the FP64 kernel otherwise leaves idle; the result is still the FP64 map's.
+// ---------------------------------------------------------------------------------
+// r, sin(theta), cos(theta) as pairs at x1 = i + o1, x2 = j + o2: the corner tables and
+// Taylor series of the offsets (|o1 dxi|, |o2 dtheta| <= 0.12: the series' truncation below
+// 1e-19)
+__device__ __forceinline__ void rsc_df(const GridP &g, const PushTables &tb, int i, int j, DF o1,
+                                       DF o2, Pt<DF> &p) {
+  const Cst<DF> k = cst<DF>(g);
+  const DF e = o1 * k.dxi;
+  DF x = dfc(1.0 / 362880.0);
+  x = fma_(x, e, dfc(1.0 / 40320.0));
+  x = fma_(x, e, dfc(1.0 / 5040.0));
+  x = fma_(x, e, dfc(1.0 / 720.0));
+  x = fma_(x, e, dfc(1.0 / 120.0));
+  x = fma_(x, e, dfc(1.0 / 24.0));
+  x = fma_(x, e, dfc(1.0 / 6.0));
+  x = fma_(x, e, DF(0.5f));
+  x = fma_(x, e, DF(1.0f));
+  x = fma_(x, e, DF(1.0f));  // exp(e)
+  const float2 rt = __ldg(tb.r_df + i + G_);
+  const DF ex = DF(rt.x, rt.y) * x;
+  p.r = ex;
+  p.f = k.dxi * ex;
+  p.gg = k.dth;
+  p.igg = k.ig2;
+  p.gp = DF(0.0f);
+  const DF d = o2 * k.dth, q = d * d;
+  DF sp = dfc(1.0 / 362880.0);
+  sp = fma_(sp, q, dfc(-1.0 / 5040.0));
+  sp = fma_(sp, q, dfc(1.0 / 120.0));
+  sp = fma_(sp, q, dfc(-1.0 / 6.0));
+  const DF se = fma_(sp * q, d, d);
+  DF cp = dfc(-1.0 / 3628800.0);
+  cp = fma_(cp, q, dfc(1.0 / 40320.0));
+  cp = fma_(cp, q, dfc(-1.0 / 720.0));
+  cp = fma_(cp, q, dfc(1.0 / 24.0));
+  cp = fma_(cp, q, DF(-0.5f));
+  const DF ce = fma_(cp, q, DF(1.0f));
+  const float2 st = __ldg(tb.s_df + j + G_), ct = __ldg(tb.c_df + j + G_);
+  const DF s0(st.x, st.y), c0(ct.x, ct.y);
+  p.s = s0 * ce + c0 * se;
+  p.c = c0 * ce - s0 * se;
+}
+__device__ __forceinline__ DF df_half(DF a) { return DF(0.5f * a.hi, 0.5f * a.lo); }
+
+// the coordinate map t -> dx + dt V((x^n + t)/2) of Eq. (discretized-geodesic-x) in pairs
+__device__ __forceinline__ void coord_map_df(const GridP &g, const PushTables &tb, int i1, int i2,
+                                             DF dx1, DF dx2, const DF u[3], DF m2, DF t1, DF t2,
+                                             DF &n1, DF &n2) {
+  Pt<DF> p;
+  rsc_df(g, tb, i1, i2, df_half(dx1 + t1), df_half(dx2 + t2), p);
+  Geo<DF> o;
+  geo_from_rsc<false>(g, p, o);
+  const DF uu = DF(2) * u[0] * u[2];
+  const DF q = fma_(o.H11 * u[0], u[0], fma_(o.H22 * u[1], u[1],
+               fma_(o.H33 * u[2], u[2], fma_(o.H13, uu, m2))));
+  const DF ag = rsqrt_(o.opz * q);
+  const DF dt = cst<DF>(g).dt;
+  n1 = fma_(dt, fma_(ag, fma_(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
+  n2 = fma_(dt, ag * o.H22 * u[1], dx2);
+}
+
+// t + (I - J)^{-1} (n - t) in pairs, the matrix from the FP32 Jacobian
+__device__ __forceinline__ void newton_df(const float J[2][2], DF t0, DF t1, DF n0, DF n1,
+                                          DF &s0, DF &s1) {
+  const float a = 1.0f - J[0][0], d = 1.0f - J[1][1];
+  const float idet = 1.0f / fmaf(a, d, -J[0][1] * J[1][0]);
+  const DF r0 = n0 - t0, r1 = n1 - t1;
+  s0 = t0 + (DF(idet * d) * r0 + DF(idet * J[0][1]) * r1);
+  s1 = t1 + (DF(idet * J[1][0]) * r0 + DF(idet * a) * r1);
+}
+
+// the metric pieces the momentum map reads, as pairs
+__device__ __forceinline__ void df_local(const Local<double> &L, Local<DF> &D) {
+  D.alpha = df_of(L.alpha);
+  D.G.H11 = df_of(L.G.H11);
+  D.G.H13 = df_of(L.G.H13);
+  D.G.H22 = df_of(L.G.H22);
+  D.G.H33 = df_of(L.G.H33);
+  D.d1H11 = df_of(L.d1H11); D.d1H22 = df_of(L.d1H22); D.d1H33 = df_of(L.d1H33);
+  D.d1H13 = df_of(L.d1H13); D.d1alpha = df_of(L.d1alpha); D.d1beta1 = df_of(L.d1beta1);
+  D.d2H11 = df_of(L.d2H11); D.d2H22 = df_of(L.d2H22); D.d2H33 = df_of(L.d2H33);
+  D.d2H13 = df_of(L.d2H13); D.d2alpha = df_of(L.d2alpha); D.d2beta1 = df_of(L.d2beta1);
+}
+
 template <bool Q = true>
 __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTables &tb, int i1,
                                                  int i2, float o1, float o2,
@@ -334,14 +426,31 @@ __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTable
   const GeoMap<double> m(g, L, u, m2);
   double t0 = u[0], t1 = u[1];
   float J[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+  double n0, n1, s0, s1;
+  bool df_start = false;
   if (isfinite(p0) && isfinite(p1)) {
+    mf.jacobian(p0, p1, J);
+    if constexpr (!Q) {  // the double-float predictor step (plain grid)
+      if (g.n_iter >= 2) {
+        Local<DF> Ld;
+        df_local(L, Ld);
+        const DF ud[3] = {df_of(u[0]), df_of(u[1]), df_of(u[2])};
+        const GeoMap<DF> md(g, Ld, ud, DF(f32_trunc(m2)));
+        DF n0d, n1d, s0d, s1d;
+        md.apply(DF(p0), DF(p1), n0d, n1d);
+        newton_df(J, DF(p0), DF(p1), n0d, n1d, s0d, s1d);
+        s0 = df_to_double(s0d);
+        s1 = df_to_double(s1d);
+        df_start = finite64(s0) && finite64(s1);
+      }
+    }
     t0 = f64_widen(p0);
     t1 = f64_widen(p1);
-    mf.jacobian(p0, p1, J);
   }
-  double n0, n1, s0, s1;
-  m.apply(t0, t1, n0, n1);
-  newton_step(J, t0, t1, n0, n1, s0, s1);
+  if (!df_start) {
+    m.apply(t0, t1, n0, n1);
+    newton_step(J, t0, t1, n0, n1, s0, s1);
+  }
   bool conv = false;
   for (int it = 1; it < g.n_iter && !conv; ++it) {
     m.apply(s0, s1, n0, n1);
@@ -500,6 +609,8 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
   t1 = dx1;
   t2 = dx2;
   float J[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+  double n1, n2, s1, s2;
+  bool df_start = false;
   if (isfinite(p1) && isfinite(p2) && fabsf(p1) < 4.0f && fabsf(p2) < 4.0f) {
     t1 = f64_widen(p1);
     t2 = f64_widen(p2);
@@ -508,10 +619,23 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
     Local<float> Lf;
     local_full<Q>(g, pf, Lf);
     coord_jacobian(g, Lf, uf, m2f, J);
+    if constexpr (!Q) {  // the double-float predictor step (plain grid)
+      if (g.n_iter >= 2) {
+        const DF ud[3] = {df_of(u[0]), df_of(u[1]), df_of(u[2])};
+        const DF d1d = df_of(dx1), d2d = df_of(dx2);
+        DF n1d, n2d, s1d, s2d;
+        coord_map_df(g, tb, i1, i2, d1d, d2d, ud, DF(m2f), DF(p1), DF(p2), n1d, n2d);
+        newton_df(J, DF(p1), DF(p2), n1d, n2d, s1d, s2d);
+        s1 = df_to_double(s1d);
+        s2 = df_to_double(s2d);
+        df_start = finite64(s1) && finite64(s2);
+      }
+    }
   }
-  double n1, n2, s1, s2;
-  coord_map64<Q>(g, b, i1, i2, dx1, dx2, u, m2, t1, t2, n1, n2, v3);
-  newton_step(J, t1, t2, n1, n2, s1, s2);
+  if (!df_start) {
+    coord_map64<Q>(g, b, i1, i2, dx1, dx2, u, m2, t1, t2, n1, n2, v3);
+    newton_step(J, t1, t2, n1, n2, s1, s2);
+  }
   bool conv = false;
   for (int it = 1; it < g.n_iter && !conv; ++it) {
     coord_map64<Q>(g, b, i1, i2, dx1, dx2, u, m2, s1, s2, n1, n2, v3);
@@ -1449,6 +1573,7 @@ __global__ void k_push_tables(GridP g, PushTables tb) {
       const double e = map_e(g, t - G_);
       const_cast<double *>(tb.r64)[t] = e;
       const_cast<float *>(tb.r)[t] = (float)e;
+      const_cast<float2 *>(tb.r_df)[t] = make_float2((float)e, (float)(e - (double)(float)e));
     }
     if (t < g.NY) {
       double s, c;
@@ -1457,6 +1582,8 @@ __global__ void k_push_tables(GridP g, PushTables tb) {
       sincos(th, &s, &c);
       const_cast<double *>(tb.s64)[t] = s;
       const_cast<double *>(tb.c64)[t] = c;
+      const_cast<float2 *>(tb.s_df)[t] = make_float2((float)s, (float)(s - (double)(float)s));
+      const_cast<float2 *>(tb.c_df)[t] = make_float2((float)c, (float)(c - (double)(float)c));
       const_cast<float *>(tb.s)[t] = (float)s;
       const_cast<float *>(tb.c)[t] = (float)c;
       // theta(eta_j + d) - theta(eta_j) = d (t1 + d (t2 + d c3)): t1 = dtheta/deta at eta_j,

@@ -3,6 +3,7 @@
 // the forward-mode dual numbers of the adjoint (dual.cuh). Included by particles.cu and
 // adjoint.cu; everything is inline device code.
 #pragma once
+#include "dfloat.cuh"
 #include "grpic_internal.cuh"
 
 namespace {
@@ -63,6 +64,20 @@ template <>
 __device__ __forceinline__ double div_<double>(double a, double b) { return a * rcp_nr(b); }
 template <>
 __device__ __forceinline__ float div_<float>(float a, float b) { return __fdividef(a, b); }
+
+}  // namespace
+
+// the grid constants as float pairs (split on the host)
+template <>
+__device__ __forceinline__ Cst<DF> cst<DF>(const GridP &g) {
+  return {DF(g.d_a[0], g.d_a[1]),     DF(g.d_M[0], g.d_M[1]),     DF(g.d_dxi[0], g.d_dxi[1]),
+          DF(g.d_dth[0], g.d_dth[1]), DF(g.d_ig2[0], g.d_ig2[1]), DF(g.d_dt[0], g.d_dt[1]),
+          DF(g.d_a2[0], g.d_a2[1]),   DF(g.d_M2[0], g.d_M2[1])};
+}
+
+namespace {
+// a pair as a double: both parts widen exactly on the integer pipe, one FP64 add
+__device__ __forceinline__ double df_to_double(DF a) { return f64_widen(a.hi) + f64_widen(a.lo); }
 
 // =================================================================================
 // Metric pieces shared by both precisions (App. A, quasi-spherical Kerr-Schild, mass M
