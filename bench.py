@@ -1039,7 +1039,9 @@ def run_adjoint(args, ws, rank, local):
 def bz_diagnostics(sim, cfg, radii):
     """The closed-form quantities of Sec. 4.5 from one snapshot of the em planes: per radius,
     the field-line angular velocity Omega = -E_theta / (sqrt(h) B^r) averaged over theta in
-    [pi/6, 5 pi/6] with weight sin^2(theta) (BZ: omega_h / 2 at every latitude to O(a^2)), the
+    [pi/6, 5 pi/6] with weight sin^2(theta) (BZ: omega_h / 2 at every latitude to O(a^2)) and
+    the peak of its theta profile (smoothed over 5 rows, theta in [0.1 pi, 0.9 pi]; the paper
+    states where the profile peaks), the
     amplitude of H_phi fitted to sin^2(theta) by least squares (BZ: -B0 a / 8), and the
     Poynting flux L = 2 pi int P^r sqrt(h) dtheta = (1/2) int (E_theta H_phi - E_phi H_theta)
     dtheta. In the code coordinates E_theta dtheta = E_2 dx2 and H_phi = H_3, so L is half the
@@ -1066,7 +1068,13 @@ def bz_diagnostics(sim, cfg, radii):
         h2 = 0.5 * (H[1][G:G + nt + 1, G + i - 1] + H[1][G:G + nt + 1, G + i])
         wn = np.ones(nt + 1)
         wn[0] = wn[-1] = 0.5
+        # the profile's peak (the paper's statement about Omega): the largest value of the
+        # profile smoothed over 5 rows, within theta in [0.1 pi, 0.9 pi]
+        sm = np.convolve(om, np.ones(5) / 5.0, mode="same")
+        band = (thc > 0.1 * math.pi) & (thc < 0.9 * math.pi)
+        kpk = int(np.argmax(np.where(band, sm, -np.inf)))
         out[rr] = {"omega": float(np.sum(w * om[mid]) / np.sum(w)),
+                   "omega_peak": float(sm[kpk]), "omega_peak_theta": float(thc[kpk]),
                    "hphi_amp": float(np.sum(h3 * s2) / np.sum(s2 * s2)),
                    "L": float(0.5 * (np.sum(E[1][G:G + nt, G + i] * h3) -
                                      np.sum(wn * E[2][G:G + nt + 1, G + i] * h2)))}
@@ -1127,6 +1135,8 @@ def run_bz_physics(args, local):
             sn = snaps[-1]
             print(json.dumps({"t": t, "omega_over_omega_h": {str(r): sn[r]["omega"] / wh
                                                              for r in radii},
+                              "omega_peak_over_omega_h": {str(r): sn[r]["omega_peak"] / wh
+                                                          for r in radii},
                               "hphi_over_bz": {str(r): sn[r]["hphi_amp"] / (-B0 * a / 8.0)
                                                for r in radii},
                               "L_over_LBZ": {str(r): sn[r]["L"] / LBZ for r in radii}}),
@@ -1150,6 +1160,8 @@ def run_bz_physics(args, local):
                        "t_end_rg": t, "dt": dt, "average_over_rg": [t - len(snaps), t],
                        "omega_h": wh, "L_BZ": LBZ},
             "omega_over_omega_h": avg("omega", wh), "omega_spread": spread("omega", wh),
+            "omega_peak_over_omega_h": avg("omega_peak", wh),
+            "omega_peak_theta": avg("omega_peak_theta", 1.0),
             "hphi_over_bz": avg("hphi_amp", -B0 * a / 8.0),
             "hphi_spread": spread("hphi_amp", -B0 * a / 8.0),
             "L_over_LBZ": avg("L", LBZ), "L_spread": spread("L", LBZ),
