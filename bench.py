@@ -59,12 +59,12 @@ GRID_BYTES_PER_CELL = {"fp64": 33 * 8, "mixed": 33 * 4}
 # dram__bytes_read.sum + dram__bytes_write.sum per particle. When the sources change the
 # counts are reported as stale and the traffic as null until they are captured again.
 KERNEL_COUNTS = {
-    "fp64": {"src": "4c463a0aa636ea0e",
+    "fp64": {"src": "c25bf7377ebb2809",
              "workload": "wald2048; operations from ncu --set full of one launch at 1 particle "
                          "per cell per species (4,194,304 particles), DRAM bytes from a one-pass "
                          "capture of a full launch (67,108,864 particles)",
-             "fp64_ops": 266.6 + 336.5 + 108.1, "flop": 2 * 266.6 + 336.5 + 108.1,
-             "dram_bytes": (4722394112 + 3815900416) / 67108864},
+             "fp64_ops": 201.7 + 271.6 + 93.1, "flop": 2 * 201.7 + 271.6 + 93.1,
+             "dram_bytes": (4726048512 + 3839292416) / 67108864},
     "mixed": {"src": "4c463a0aa636ea0e",
               "workload": "wald2048; warp instructions from ncu --set full of one launch at 1 "
                           "particle per cell per species, DRAM bytes from a one-pass capture of a "

@@ -431,7 +431,7 @@ grpic_status grpic_create(const grpic_config *cfg, grpic_ctx **out) {
   ctx->off_planes = off; off += up(ps * fs) * 36;
   ctx->off_tab = off;    off += up(ps * fs) * 4 * T_NQ;
   ctx->off_polar = off;  off += up((size_t)3 * g.NX * fs);
-  ctx->off_ptab = off;   off += 14 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 8);
+  ctx->off_ptab = off;   off += 16 * up((size_t)(g.NX > g.NY ? g.NX : g.NY) * 8);
   ctx->off_dt = off;     off += up(64);
   ctx->off_diag = off;   off += up(DG_N * 8);
   ctx->off_chunk = off;  off += up(GRPIC_MAX_SPECIES * HOST_CHUNKS * 8);
@@ -506,6 +506,8 @@ grpic_status grpic_bind(grpic_ctx *ctx, void *arena, size_t bytes, void *stream)
   ctx->tb.r_df = at<float2>(ctx, ctx->off_ptab + 11 * tstride);
   ctx->tb.s_df = at<float2>(ctx, ctx->off_ptab + 12 * tstride);
   ctx->tb.c_df = at<float2>(ctx, ctx->off_ptab + 13 * tstride);
+  ctx->tb.t1_df = at<float2>(ctx, ctx->off_ptab + 14 * tstride);
+  ctx->tb.t2_df = at<float2>(ctx, ctx->off_ptab + 15 * tstride);
   if (ctx->cfg.tiled_push == 2) {
     // tensor map of the padded planes [6][NY][NXp] (FP32), box one window plane W1 x W2 x 1;
     // the encoder comes from the driver through the runtime (no link to the driver library)

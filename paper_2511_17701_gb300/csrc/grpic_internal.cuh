@@ -28,7 +28,8 @@ struct GridP {
   double a2, M2;    // a^2 and 2 M
   // the same constants as pairs of floats (value hi + lo, about 48 bits) for the FP64
   // pusher's double-float predictor: a, M, dxi, dth, 1/dth^2, dt, a^2, 2M
-  float d_a[2], d_M[2], d_dxi[2], d_dth[2], d_ig2[2], d_dt[2], d_a2[2], d_M2[2];
+  float d_a[2], d_M[2], d_dxi[2], d_dth[2], d_ig2[2], d_dt[2], d_a2[2], d_M2[2], d_r0[2],
+      d_c3[2];
   double ig2;  // 1 / dth^2
   // quasi-spherical map: radial offset, equatorial concentration, qks = (r0 != 0 || h0 != 0),
   // c3 = 4 h0 / pi^2 (the cubic coefficient of theta(eta_j + d) - theta(eta_j))
@@ -47,9 +48,9 @@ inline void grid_float_copies(GridP &g) {
   g.M2 = 2.0 * g.M;
   g.f_a2 = g.f_a * g.f_a;
   g.f_M2 = 2.0f * g.f_M;
-  const double dv[8] = {g.a, g.M, g.dxi, g.dth, g.ig2, g.dt, g.a2, g.M2};
-  float *dp[8] = {g.d_a, g.d_M, g.d_dxi, g.d_dth, g.d_ig2, g.d_dt, g.d_a2, g.d_M2};
-  for (int k = 0; k < 8; ++k) {
+  const double dv[10] = {g.a, g.M, g.dxi, g.dth, g.ig2, g.dt, g.a2, g.M2, g.r0, g.c3};
+  float *dp[10] = {g.d_a, g.d_M, g.d_dxi, g.d_dth, g.d_ig2, g.d_dt, g.d_a2, g.d_M2, g.d_r0, g.d_c3};
+  for (int k = 0; k < 10; ++k) {
     dp[k][0] = (float)dv[k];
     dp[k][1] = (float)(dv[k] - (double)dp[k][0]);
   }
@@ -347,6 +348,7 @@ struct PushTables {
   const double *th64;  // theta at corner row j, formed as map_theta forms it
   // exp(xi) at corner column i and sin, cos(theta) at corner row j as float pairs (hi, lo)
   const float2 *r_df, *s_df, *c_df;
+  const float2 *t1_df, *t2_df;  // the quasi-spherical theta offset's t1, t2 as pairs
   int guard_ilo, guard_ihi;  // cells guard_ilo <= i1 < guard_ihi (around the horizon) and
   int guard_j;               // within guard_j of an axis evaluate the metric in FP64
 };

@@ -319,9 +319,11 @@ __device__ __forceinline__ void newton_step(const float J[2][2], double t0, doub
 // once, one FP64 map evaluation per substep instead of two. The arithmetic runs on the FP32
 // pipe, which the FP64 kernel otherwise leaves idle; the result is still the FP64 map's.
 // ---------------------------------------------------------------------------------
-// r, sin(theta), cos(theta) as pairs at x1 = i + o1, x2 = j + o2: the corner tables and
-// Taylor series of the offsets (|o1 dxi|, |o2 dtheta| <= 0.12: the series' truncation below
-// 1e-19)
+// r, sin(theta), cos(theta) and the map's factors as pairs at x1 = i + o1, x2 = j + o2: the
+// corner tables and Taylor series of the offsets (|o1 dxi|, |theta offset| <= 0.12: the
+// series' truncation below 1e-19), on a quasi-spherical grid with the theta offset's cubic in
+// the offset in eta and its derivatives
+template <bool Q>
 __device__ __forceinline__ void rsc_df(const GridP &g, const PushTables &tb, int i, int j, DF o1,
                                        DF o2, Pt<DF> &p) {
   const Cst<DF> k = cst<DF>(g);
@@ -338,12 +340,23 @@ __device__ __forceinline__ void rsc_df(const GridP &g, const PushTables &tb, int
   x = fma_(x, e, DF(1.0f));  // exp(e)
   const float2 rt = __ldg(tb.r_df + i + G_);
   const DF ex = DF(rt.x, rt.y) * x;
-  p.r = ex;
+  p.r = Q ? DF(g.d_r0[0], g.d_r0[1]) + ex : ex;
   p.f = k.dxi * ex;
-  p.gg = k.dth;
-  p.igg = k.ig2;
-  p.gp = DF(0.0f);
-  const DF d = o2 * k.dth, q = d * d;
+  DF d = o2 * k.dth;  // the offset in eta, then in theta
+  if (Q && g.qks) {
+    const float2 a1 = __ldg(tb.t1_df + j + G_), a2 = __ldg(tb.t2_df + j + G_);
+    const DF t1(a1.x, a1.y), t2(a2.x, a2.y), c3(g.d_c3[0], g.d_c3[1]);
+    const DF t22 = t2 + t2, c33 = DF(3) * c3;
+    p.gg = k.dth * fma_(d, fma_(c33, d, t22), t1);
+    p.gp = k.dth * k.dth * fma_(c33 + c33, d, t22);
+    p.igg = DF(0.0f);
+    d = d * fma_(d, fma_(c3, d, t2), t1);
+  } else {
+    p.gg = k.dth;
+    p.igg = k.ig2;
+    p.gp = DF(0.0f);
+  }
+  const DF q = d * d;
   DF sp = dfc(1.0 / 362880.0);
   sp = fma_(sp, q, dfc(-1.0 / 5040.0));
   sp = fma_(sp, q, dfc(1.0 / 120.0));
@@ -363,13 +376,14 @@ __device__ __forceinline__ void rsc_df(const GridP &g, const PushTables &tb, int
 __device__ __forceinline__ DF df_half(DF a) { return DF(0.5f * a.hi, 0.5f * a.lo); }
 
 // the coordinate map t -> dx + dt V((x^n + t)/2) of Eq. (discretized-geodesic-x) in pairs
+template <bool Q>
 __device__ __forceinline__ void coord_map_df(const GridP &g, const PushTables &tb, int i1, int i2,
                                              DF dx1, DF dx2, const DF u[3], DF m2, DF t1, DF t2,
                                              DF &n1, DF &n2) {
   Pt<DF> p;
-  rsc_df(g, tb, i1, i2, df_half(dx1 + t1), df_half(dx2 + t2), p);
+  rsc_df<Q>(g, tb, i1, i2, df_half(dx1 + t1), df_half(dx2 + t2), p);
   Geo<DF> o;
-  geo_from_rsc<false>(g, p, o);
+  geo_from_rsc<Q>(g, p, o);
   const DF uu = DF(2) * u[0] * u[2];
   const DF q = fma_(o.H11 * u[0], u[0], fma_(o.H22 * u[1], u[1],
                fma_(o.H33 * u[2], u[2], fma_(o.H13, uu, m2))));
@@ -430,7 +444,7 @@ __device__ __forceinline__ void geodesic_refined(const GridP &g, const PushTable
   bool df_start = false;
   if (isfinite(p0) && isfinite(p1)) {
     mf.jacobian(p0, p1, J);
-    if constexpr (!Q) {  // the double-float predictor step (plain grid)
+    {  // the double-float predictor step
       if (g.n_iter >= 2) {
         Local<DF> Ld;
         df_local(L, Ld);
@@ -619,12 +633,12 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
     Local<float> Lf;
     local_full<Q>(g, pf, Lf);
     coord_jacobian(g, Lf, uf, m2f, J);
-    if constexpr (!Q) {  // the double-float predictor step (plain grid)
+    {  // the double-float predictor step
       if (g.n_iter >= 2) {
         const DF ud[3] = {df_of(u[0]), df_of(u[1]), df_of(u[2])};
         const DF d1d = df_of(dx1), d2d = df_of(dx2);
         DF n1d, n2d, s1d, s2d;
-        coord_map_df(g, tb, i1, i2, d1d, d2d, ud, DF(m2f), DF(p1), DF(p2), n1d, n2d);
+        coord_map_df<Q>(g, tb, i1, i2, d1d, d2d, ud, DF(m2f), DF(p1), DF(p2), n1d, n2d);
         newton_df(J, DF(p1), DF(p2), n1d, n2d, s1d, s2d);
         s1 = df_to_double(s1d);
         s2 = df_to_double(s2d);
@@ -1595,6 +1609,8 @@ __global__ void k_push_tables(GridP g, PushTables tb) {
       const_cast<double *>(tb.t2_64)[t] = t2;
       const_cast<float *>(tb.t1)[t] = (float)t1;
       const_cast<float *>(tb.t2)[t] = (float)t2;
+      const_cast<float2 *>(tb.t1_df)[t] = make_float2((float)t1, (float)(t1 - (double)(float)t1));
+      const_cast<float2 *>(tb.t2_df)[t] = make_float2((float)t2, (float)(t2 - (double)(float)t2));
     }
   }
 }
