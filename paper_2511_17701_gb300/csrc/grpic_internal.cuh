@@ -38,6 +38,8 @@ struct GridP {
   int qks;
   // FP32 copies for the mixed path (read from the kernel parameters, no conversions)
   float f_a, f_M, f_dxi, f_dth, f_ig2, f_dt, f_idt, f_r0, f_c3, f_iter_tol, f_a2, f_M2;
+  // cells of x1 over which the coordinate velocities vary by order one: 1 / (4 dxi)
+  float f_x1_scale;
 };
 
 // Fill the FP32 copies once a, M, dxi, dth and dt are set.
@@ -58,6 +60,7 @@ inline void grid_float_copies(GridP &g) {
   g.f_a = (float)g.a; g.f_M = (float)g.M; g.f_dxi = (float)g.dxi; g.f_dth = (float)g.dth;
   g.f_ig2 = (float)g.ig2; g.f_dt = (float)g.dt; g.f_idt = g.dt > 0.0 ? (float)(1.0 / g.dt) : 0.0f;
   g.f_r0 = (float)g.r0; g.f_c3 = (float)g.c3;
+  g.f_x1_scale = g.dxi > 0.0 ? (float)(0.25 / g.dxi) : 1.0f;
 }
 
 // The quasi-spherical map at a point (App. A): r with e = exp(xi) = r - r0 and f = dr/dx1 =

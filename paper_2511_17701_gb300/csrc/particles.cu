@@ -263,14 +263,34 @@ __device__ __forceinline__ void deposit64(const GridP &g, const FieldPtrsT<T> &F
   add_(J3 + k + NX + 1, qv * w1 * w2);
 }
 
+// Stop rule of the FP32 implicit iterations: the update within ITER_TOL32 max(1, |value|),
+// two FP32 ulps at 1. The remaining error, rho / (1 - rho) of that update (rho the
+// contraction), is then below the rounding of the stored values.
+constexpr float ITER_TOL32 = 0x1p-22f;
+__device__ __forceinline__ bool settled32(float n0, float t0, float n1, float t1) {
+  return fabsf(n0 - t0) <= ITER_TOL32 * fmaxf(1.0f, fabsf(n0)) &&
+         fabsf(n1 - t1) <= ITER_TOL32 * fmaxf(1.0f, fabsf(n1));
+}
+// The coordinate iteration may also stop on an estimate of its remaining error: two successive
+// updates d_prev, d of a linearly converging iteration give its rate as about d / d_prev, so
+// the error left after the latest one is about d^2 / d_prev. Stop when sixteen times that is
+// below ITER_TOL32 (cell units). After the first metric evaluation at the midpoint, d_prev is
+// the particle's whole move and d about rho times it (rho ~ dt |dV/dx|, 1e-3 or less off the
+// guard zones), so most warps stop there instead of running a third evaluation for the few
+// lanes whose update is still above the plain rule's bound.
+__device__ __forceinline__ bool settled32_rate(float d, float d_prev) {
+  return 16.0f * d * d <= ITER_TOL32 * d_prev;
+}
+
 // Refined form of the two implicit substeps (iter_tol > 0): an FP32 predictor iterates the
-// same map to an exact FP32 repeat (metric from the FP32 cell tables) and gives the map's
-// Jacobian J there (FP32, analytic). The FP64 map is evaluated at the predictor's point; one
-// Newton step with J on that residual lands within about |J error| times the predictor's
-// rounding of the FP64 fixed point, and a second FP64 evaluation there verifies it: the
-// result is taken once an FP64 update is at most iter_tol max(1, |value|), with plain FP64
-// iterations after the second evaluation while it is not (at most n_iter evaluations in
-// all). The result is the FP64 fixed point to about rho iter_tol, rho < 1 the contraction,
+// same map to an exact FP32 repeat (metric from the FP32 cell tables; the coordinate
+// substep's also stops on the rate estimate above, which puts it within the rounding of its
+// FP32 values as well) and gives the map's Jacobian J there (FP32, analytic). The FP64 map
+// is evaluated at the predictor's point; one Newton step with J on that residual lands
+// within about |J error| times the predictor's rounding of the FP64 fixed point, and a
+// second FP64 evaluation there verifies it: the result is taken once an FP64 update is at
+// most iter_tol max(1, |value|), with plain FP64 iterations after the second evaluation
+// while it is not (at most n_iter evaluations in all). The result is the FP64 fixed point to about rho iter_tol, rho < 1 the contraction,
 // whatever the start: J and the predictor only save FP64 work (mixed-precision refinement).
 // |n - t| <= tol max(1, |n|): the difference in FP64 (n and t agree to about tol), the test
 // in FP32 on truncated values (the bound moves by less than 2^-22 of itself)
@@ -603,7 +623,7 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
   const float uf[3] = {f32_trunc(u[0]), f32_trunc(u[1]), f32_trunc(u[2])};
   const float a1 = f32_trunc(dx1), a2 = f32_trunc(dx2), dt = g.f_dt, m2f = f32_trunc(m2);
   const float uuf = 2.0f * uf[0] * uf[2];
-  float p1 = a1, p2 = a2, d1 = 0.0f;
+  float p1 = a1, p2 = a2, d1 = 0.0f, d_prev = 0.0f;
   for (int it = 0; it < g.n_iter; ++it) {
     Pt<float> pf;
     rsc32<Q>(g, tb, i1, i2, 0.5f * (a1 + p1), 0.5f * (a2 + p2), pf);
@@ -614,8 +634,10 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
     const float ag = rsqrtf(o.opz * q);
     const float n1 = fmaf(dt, fmaf(ag, fmaf(o.H11, uf[0], o.H13 * uf[2]), -o.beta1), a1);
     const float n2 = fmaf(dt, ag * o.H22 * uf[1], a2);
-    if (it == 0) d1 = fmaxf(fabsf(n1 - p1), fabsf(n2 - p2));
-    const bool fixed = n1 == p1 && n2 == p2;
+    const float d = fmaxf(fabsf(n1 - p1), fabsf(n2 - p2));
+    if (it == 0) d1 = d;
+    const bool fixed = (n1 == p1 && n2 == p2) || settled32_rate(d, d_prev);
+    d_prev = d;
     p1 = n1;
     p2 = n2;
     if (fixed) break;
@@ -1024,14 +1046,6 @@ __device__ __forceinline__ void deposit32_warp(const GridP &g, const Sink &sink,
   }
 }
 
-// Stop rule of the FP32 implicit iterations: the update within ITER_TOL32 max(1, |value|),
-// two FP32 ulps at 1. The remaining error, rho / (1 - rho) of that update (rho the
-// contraction), is then below the rounding of the stored values.
-constexpr float ITER_TOL32 = 0x1p-22f;
-__device__ __forceinline__ bool settled32(float n0, float t0, float n1, float t1) {
-  return fabsf(n0 - t0) <= ITER_TOL32 * fmaxf(1.0f, fabsf(n0)) &&
-         fabsf(n1 - t1) <= ITER_TOL32 * fmaxf(1.0f, fabsf(n1));
-}
 
 // The FP32 momentum substep: n_iter applications of the geodesic map, or fewer under the
 // stop rule above.
@@ -1111,9 +1125,13 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
   }
   const float dt = g.f_dt;
   const float uu0 = 2.0f * u[0] * u[2];
-  // the coordinate iteration under the FP32 stop rule; dphi/dt then comes from the metric of
-  // its last iteration, whose midpoint is within the update of the final one
-  float t1 = dx1, t2 = dx2, v3 = NAN;
+  // the coordinate iteration under the FP32 stop rules; dphi/dt then comes from the metric of
+  // its last iteration, whose midpoint is within half the final update of the final one. So
+  // the rate rule also wants that update below ITER_TOL32 times the cells over which dphi/dt
+  // changes by order one: the distance to the nearer axis in theta (dphi/dt ~ 1/sin^2(theta))
+  // and 1/(4 dxi) in x1 (~ 1/r^2), which keeps its relative error at FP32 rounding
+  const float d_cap = ITER_TOL32 * fminf((float)min(i2, g.n_th - 1 - i2), g.f_x1_scale);
+  float t1 = dx1, t2 = dx2, v3 = NAN, d_prev = 0.0f;
   for (int it = 0; it < g.n_iter; ++it) {
     Geo<float> o;
     if (it == 0) o = L.G;
@@ -1123,7 +1141,9 @@ __device__ __forceinline__ bool push32(const GridP &g, const Fields &F, const Pu
     const float ag = rsqrtf(o.opz * q);
     const float n1 = fmaf(dt, fmaf(ag, fmaf(o.H11, u[0], o.H13 * u[2]), -o.beta1), dx1);
     const float n2 = fmaf(dt, ag * o.H22 * u[1], dx2);
-    const bool done = settled32(n1, t1, n2, t2);
+    const float d = fmaxf(fabsf(n1 - t1), fabsf(n2 - t2));
+    const bool done = settled32(n1, t1, n2, t2) || (settled32_rate(d, d_prev) && d <= d_cap);
+    d_prev = d;
     t1 = n1;
     t2 = n2;
     if (done && g.stop_on_repeat) {
@@ -1266,10 +1286,12 @@ __global__ void __launch_bounds__(TPB) k_classify(GridP g, SpeciesDevT<float> s,
 // concurrently with the guard kernels, which own the listed ones). The loop runs while the
 // warp's first particle exists, so the whole warp reaches the cooperative deposit. Its
 // gathers and atomics need many resident warps to hide their latency: 12 blocks per SM (40
-// registers, a few spills to L1) measured 0.60 ms per 8.4 M particles against 0.71 ms with
-// 6 (80 registers, no spills) on GB300; at 12 it is bound by instruction issue.
+// registers, spills) measured 0.60 ms per 8.4 M particles against 0.71 ms with 6 (80
+// registers, no spills) on GB300, and on 67 M particles of the 2048^2 workload 10 blocks
+// (48 registers, fewer spills) 3.22 ms against 3.29 ms with 12, 3.28 with 9 and 3.35 with
+// 8; it is bound by instruction issue.
 #ifndef GRPIC_PUSH32_MIN_BLOCKS  // resident blocks per SM the FP32 kernel is built for
-#define GRPIC_PUSH32_MIN_BLOCKS 12
+#define GRPIC_PUSH32_MIN_BLOCKS 10
 #endif
 template <bool DEPOSIT, bool Q>
 __global__ void __launch_bounds__(TPB, GRPIC_PUSH32_MIN_BLOCKS) k_push32(GridP g, FieldPtrsT<float> F,
