@@ -270,9 +270,10 @@ def projected_rate(n_total, t_field, t_part, n_sample):
 
 
 def cpu_baseline(args):
-    """The oracle as it stands on the host cores: 2 full steps on the workload's whole grid
-    with the particles of a seeded fraction of the cells (all cores), then the particle phases
-    of one more step on one core; the particle phases projected to the full workload."""
+    """The oracle as it stands on the host cores: --cpu-steps full steps on the workload's
+    whole grid with the particles of a seeded fraction of the cells (all cores), then the
+    particle phases of --cpu-steps-1core more steps on one core; the particle phases projected
+    to the full workload (no projection at --cpu-frac 1)."""
     cfg = W.grid_config(args.workload)
     if args.ppc:
         cfg["ppc"] = args.ppc
@@ -293,19 +294,24 @@ def cpu_baseline(args):
     from oracle import oracle as O
     O.set_threads(1)
     t0 = time.perf_counter()
-    for s in range(len(osim.species)):
-        osim.push(s)
-    osim.deposit()
-    tp1 = time.perf_counter() - t0
+    for _ in range(args.cpu_steps_1core):
+        for s in range(len(osim.species)):
+            osim.push(s)
+        osim.deposit()
+    tp1 = (time.perf_counter() - t0) / args.cpu_steps_1core
     O.set_threads(cores)
     one_core = projected_rate(n_total, tf, tp1, n_s)
+    if n_s == n_total:
+        who = "all %d particles of the workload (no projection)" % n_total
+    else:
+        who = ("the particles of %.1f%% of the cells (%d particles, seeded); particle phases "
+               "scaled to the %d particles of the workload" % (100 * args.cpu_frac, n_s, n_total))
     sample = ("%s: the full %dx%d grid (field predict + advance, which the oracle runs on one "
-              "core, %.2f s per step) with the particles of %.1f%% of the cells (%d particles, "
-              "seeded), %d full steps on %d cores (push + deposit %.2f s per step) and the "
-              "particle phases of one more step on 1 core (%.2f s); particle phases scaled "
-              "to the %d particles of the workload; set-up %.0f s"
-              % (args.workload, cfg["n_r"], cfg["n_theta"], tf, 100 * args.cpu_frac, n_s,
-                 args.cpu_steps, cores, tp, tp1, n_total, setup))
+              "core, %.2f s per step) with %s: %d full steps on %d cores (push + deposit %.2f s "
+              "per step), then the particle phases of %d more step(s) on 1 core (%.2f s per "
+              "step); set-up %.0f s"
+              % (args.workload, cfg["n_r"], cfg["n_theta"], tf, who, args.cpu_steps, cores, tp,
+                 args.cpu_steps_1core, tp1, setup))
     return {"value": all_core, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
             "sample": sample, "one_core": {"value": one_core, "cores": 1},
             "field_s_per_step": tf, "particle_s_per_sample_step": tp,
@@ -1189,6 +1195,8 @@ def main():
     ap.add_argument("--cpu-frac", type=float, default=0.03,
                     help="fraction of the cells whose particles the CPU baseline pushes")
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-steps-1core", type=int, default=1, choices=range(1, 11),
+                    help="steps of the one-core particle phases in the CPU baseline")
     ap.add_argument("--ref-frac", type=float, default=0.01,
                     help="fraction of the cells whose particles the reference arm pushes")
     ap.add_argument("--adjoint", action="store_true",
