@@ -1192,9 +1192,12 @@ __device__ __forceinline__ int guard_zone(const PushTables &tb, const GridP &g, 
 }
 
 // FP64 path: one thread per particle, step 1 (previous location) then the FP64 routine.
+// Bound by the FP64 pipe; on 67 M particles of the 2048^2 workload 3 resident blocks per SM
+// (166 registers, no spills) measured 85.4 ms per launch against 86.9 ms with 4 (128
+// registers, spills) and 89.3 ms with 5 (96 registers).
 template <bool DEPOSIT, bool Q>
 #ifndef GRPIC_PUSH64_MIN_BLOCKS  // resident blocks per SM the fused FP64 kernel is built for
-#define GRPIC_PUSH64_MIN_BLOCKS 4
+#define GRPIC_PUSH64_MIN_BLOCKS 3
 #endif
 __global__ void __launch_bounds__(TPB, DEPOSIT ? GRPIC_PUSH64_MIN_BLOCKS : 3) k_push(GridP g, FieldPtrsT<double> F, PushTables tb,
                                               SpeciesDevT<double> s, unsigned long long *diag) {
