@@ -31,14 +31,31 @@ __global__ void __launch_bounds__(TPB) k_keys(SpeciesDevT<T> s, int n_r, int tr,
                                               uint32_t *keys, uint32_t *vals,
                                               unsigned long long *alive) {
   __shared__ unsigned wsum[NWARP];
+  constexpr int U = 4;  // elements per thread and trip, loaded before any is stored
   const int64_t n = *s.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned cnt = 0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const uint8_t tag = s.tag[k];
-    keys[k] = cell_key(s.i1[k], s.i2[k], tag, n_r, tr, tt);
-    vals[k] = (uint32_t)k;
-    cnt += tag == 1 ? 1u : 0u;
+  for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k0 < n; k0 += U * stride) {
+    int a1[U], a2[U];
+    uint8_t tg[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t k = k0 + u * stride;
+      if (k < n) {
+        tg[u] = s.tag[k];
+        a1[u] = s.i1[k];
+        a2[u] = s.i2[k];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t k = k0 + u * stride;
+      if (k < n) {
+        keys[k] = cell_key(a1[u], a2[u], tg[u], n_r, tr, tt);
+        vals[k] = (uint32_t)k;
+        cnt += tg[u] == 1 ? 1u : 0u;
+      }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
@@ -124,35 +141,79 @@ __global__ void k_scatter(const uint32_t *kin, const uint32_t *vin, uint32_t *ko
   }
 }
 
-// exclusive scan of a uint32 array in segments of SCAN_SEG, segment totals to bsum
-__global__ void k_scan_seg(uint32_t *a, int64_t L, uint32_t *bsum) {
-  __shared__ uint32_t s[SCAN_SEG];
-  const int64_t base = (int64_t)blockIdx.x * SCAN_SEG;
-  for (int t = threadIdx.x; t < SCAN_SEG; t += blockDim.x)
-    s[t] = (base + t < L) ? a[base + t] : 0u;
+// Exclusive scan of one value per thread across the block (blockDim.x a multiple of 32, at
+// most 1024): warp shuffles, then the warp totals scanned by the first warp. Returns the
+// thread's exclusive prefix and sets *total to the block's sum. Every thread calls it; the
+// shared array is reused, so calls are separated by a barrier.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ uint32_t ws[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) ws[w] = x;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int t = 0; t < SCAN_SEG; ++t) {
-      const uint32_t v = s[t];
-      s[t] = run;
-      run += v;
+  if (w == 0) {
+    uint32_t t = lane < nw ? ws[lane] : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, t, d);
+      if (lane >= d) t += y;
     }
-    bsum[blockIdx.x] = run;
+    ws[lane] = t;  // inclusive prefix of the warp totals
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < SCAN_SEG; t += blockDim.x)
-    if (base + t < L) a[base + t] = s[t];
+  *total = ws[nw - 1];
+  return (w ? ws[w - 1] : 0u) + x - v;
 }
 
-__global__ void k_scan_sums(uint32_t *bsum, int64_t S) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    uint32_t run = 0;
-    for (int64_t t = 0; t < S; ++t) {
-      const uint32_t v = bsum[t];
-      bsum[t] = run;
-      run += v;
+// exclusive scan of a uint32 array in segments of SCAN_SEG (blocks of SCAN_SEG / 4 threads,
+// four consecutive elements each), segment totals to bsum
+__global__ void __launch_bounds__(SCAN_SEG / 4) k_scan_seg(uint32_t *a, int64_t L,
+                                                           uint32_t *bsum) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_SEG + 4 * threadIdx.x;
+  uint32_t v[4], sum = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    v[j] = base + j < L ? a[base + j] : 0u;
+    sum += v[j];
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(sum, &total);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (base + j < L) a[base + j] = run;
+    run += v[j];
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// exclusive scan of the S segment totals: one block, 4 consecutive entries per thread and
+// chunk, a running carry across chunks
+constexpr int SCAN_SUMS_TPB = 1024;
+__global__ void __launch_bounds__(SCAN_SUMS_TPB) k_scan_sums(uint32_t *bsum, int64_t S) {
+  uint32_t carry = 0;
+  for (int64_t c0 = 0; c0 < S; c0 += 4 * (int64_t)blockDim.x) {
+    const int64_t base = c0 + 4 * threadIdx.x;
+    uint32_t v[4], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = base + j < S ? bsum[base + j] : 0u;
+      sum += v[j];
     }
+    uint32_t total;
+    uint32_t run = carry + block_exclusive_scan(sum, &total);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (base + j < S) bsum[base + j] = run;
+      run += v[j];
+    }
+    carry += total;
+    __syncthreads();  // the scan's shared array is read above before the next chunk writes it
   }
 }
 
@@ -162,21 +223,54 @@ __global__ void k_scan_add(uint32_t *a, int64_t L, const uint32_t *bsum) {
 }
 
 // gather every array of the species by the final permutation (PREV false: all but the
-// previous position)
+// previous position). Each thread takes GATHER_U elements a grid stride apart and issues all
+// their loads before any store, so that enough reads are in flight to cover the latency of
+// the permuted loads that depend on perm.
+constexpr int GATHER_U = 4;
 template <typename T, bool PREV>
-__global__ void k_gather(SpeciesDevT<T> in, SpeciesDevT<T> out, const uint32_t *perm,
-                         const int64_t *n_dev) {
+__global__ void __launch_bounds__(TPB) k_gather(SpeciesDevT<T> in, SpeciesDevT<T> out,
+                                                const uint32_t *__restrict__ perm,
+                                                const int64_t *n_dev) {
   const int64_t n = *n_dev;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t p = perm[k];
-    out.i1[k] = in.i1[p]; out.i2[k] = in.i2[p];
-    out.dx1[k] = in.dx1[p]; out.dx2[k] = in.dx2[p];
-    out.u1[k] = in.u1[p]; out.u2[k] = in.u2[p]; out.u3[k] = in.u3[p];
-    out.phi[k] = in.phi[p]; out.w[k] = in.w[p]; out.tag[k] = in.tag[p];
-    if (PREV) {
-      out.i1p[k] = in.i1p[p]; out.i2p[k] = in.i2p[p];
-      out.dx1p[k] = in.dx1p[p]; out.dx2p[k] = in.dx2p[p];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k0 < n;
+       k0 += GATHER_U * stride) {
+    uint32_t p[GATHER_U];
+    bool ok[GATHER_U];
+#pragma unroll
+    for (int u = 0; u < GATHER_U; ++u) {
+      ok[u] = k0 + u * stride < n;
+      p[u] = ok[u] ? __ldg(perm + k0 + u * stride) : 0u;
+    }
+    int32_t i1[GATHER_U], i2[GATHER_U], i1p[GATHER_U], i2p[GATHER_U];
+    T dx1[GATHER_U], dx2[GATHER_U], u1[GATHER_U], u2[GATHER_U], u3[GATHER_U], phi[GATHER_U],
+        w[GATHER_U], dx1p[GATHER_U], dx2p[GATHER_U];
+    uint8_t tag[GATHER_U];
+#pragma unroll
+    for (int u = 0; u < GATHER_U; ++u) {
+      if (!ok[u]) continue;
+      const uint32_t q = p[u];
+      i1[u] = in.i1[q]; i2[u] = in.i2[q];
+      dx1[u] = in.dx1[q]; dx2[u] = in.dx2[q];
+      u1[u] = in.u1[q]; u2[u] = in.u2[q]; u3[u] = in.u3[q];
+      phi[u] = in.phi[q]; w[u] = in.w[q]; tag[u] = in.tag[q];
+      if (PREV) {
+        i1p[u] = in.i1p[q]; i2p[u] = in.i2p[q];
+        dx1p[u] = in.dx1p[q]; dx2p[u] = in.dx2p[q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < GATHER_U; ++u) {
+      if (!ok[u]) continue;
+      const int64_t k = k0 + u * stride;
+      out.i1[k] = i1[u]; out.i2[k] = i2[u];
+      out.dx1[k] = dx1[u]; out.dx2[k] = dx2[u];
+      out.u1[k] = u1[u]; out.u2[k] = u2[u]; out.u3[k] = u3[u];
+      out.phi[k] = phi[u]; out.w[k] = w[u]; out.tag[k] = tag[u];
+      if (PREV) {
+        out.i1p[k] = i1p[u]; out.i2p[k] = i2p[u];
+        out.dx1p[k] = dx1p[u]; out.dx2p[k] = dx2p[u];
+      }
     }
   }
 }
@@ -226,9 +320,9 @@ cudaError_t launch_sort(const GridP &g, int tr, int tt, SpeciesDevT<T> in, Speci
     const int shift = 8 * p;
     k_hist<<<nblocks, TPB, 0, st>>>(S.keys[cur], in.n, shift, nblocks, S.hist);
     COUNT_LAUNCH(1);
-    k_scan_seg<<<(int)nseg, 256, 0, st>>>(S.hist, L, S.bsum);
+    k_scan_seg<<<(int)nseg, SCAN_SEG / 4, 0, st>>>(S.hist, L, S.bsum);
     COUNT_LAUNCH(1);
-    k_scan_sums<<<1, 32, 0, st>>>(S.bsum, nseg);
+    k_scan_sums<<<1, SCAN_SUMS_TPB, 0, st>>>(S.bsum, nseg);
     COUNT_LAUNCH(1);
     k_scan_add<<<(int)((L + 255) / 256), 256, 0, st>>>(S.hist, L, S.bsum);
     COUNT_LAUNCH(1);
@@ -355,8 +449,8 @@ extern "C" GRPIC_API grpic_status grpic_sort_permutation_noalloc(
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
     k_hist<<<nblocks, TPB, 0, st>>>(keys[cur], n_dev, shift, nblocks, hist);
-    k_scan_seg<<<(int)nseg, 256, 0, st>>>(hist, L, bsum);
-    k_scan_sums<<<1, 32, 0, st>>>(bsum, nseg);
+    k_scan_seg<<<(int)nseg, SCAN_SEG / 4, 0, st>>>(hist, L, bsum);
+    k_scan_sums<<<1, SCAN_SUMS_TPB, 0, st>>>(bsum, nseg);
     k_scan_add<<<(int)((L + 255) / 256), 256, 0, st>>>(hist, L, bsum);
     k_scatter<<<nblocks, TPB, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], n_dev,
                                        shift, nblocks, hist);
