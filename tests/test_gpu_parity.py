@@ -147,6 +147,38 @@ def test_sort_bit_exact(torch_cuda, n, tiles):
         assert np.array_equal(pg[k], po[k]), k
 
 
+def test_sort_beyond_one_chunk_of_the_total_scan(torch_cuda):
+    """68,000,000 particles: more segment totals of the digit histogram (one per four blocks
+    of 4096 keys) than the 4096 one pass of the totals' block scan covers, so the scan carries
+    its running total across chunks (a species of the 2048^2 workloads, 67,108,864 particles,
+    fills exactly one). The weight carries each particle's input index (exact in FP64): after
+    the sort the weights are the input indices in the stable order of the oracle's keys, the
+    dead particles dropped, and the cells follow them."""
+    from paper_2511_17701_gb300 import Sim
+    n, tiles = 68_000_000, (16, 16)
+    cfg = dict(BASE, tile_r=tiles[0], tile_theta=tiles[1], dt=0.01)
+    rng = np.random.default_rng(17)
+    i1 = rng.integers(0, cfg["n_r"], n, dtype=np.int32)
+    i2 = rng.integers(0, cfg["n_theta"], n, dtype=np.int32)
+    tag = (rng.random(n) < 0.9).astype(np.uint8)
+    arrays = {"i1": i1, "i2": i2, "tag": tag, "w": np.arange(n, dtype=np.float64)}
+    zero = np.zeros(n)
+    for k in ("dx1", "dx2", "u1", "u2", "u3", "phi"):
+        arrays[k] = zero
+    g = Sim(cfg, [n])
+    g.init_metric()
+    g.set_particles(0, arrays, 1.0, 1.0)
+    g.sort(0)
+    p = g.get_particles(0)
+    del g
+    keys = O.sort_keys(cfg, tiles[0], tiles[1], i1, i2, tag)
+    order = np.argsort(keys, kind="stable")
+    order = order[: int(np.count_nonzero(tag == 1))]  # dead keys (0xFFFFFFFF) sort last
+    assert len(p["w"]) == len(order)
+    assert np.array_equal(p["w"], order.astype(np.float64))
+    assert np.array_equal(p["i1"], i1[order]) and np.array_equal(p["i2"], i2[order])
+
+
 def test_full_step_with_sort(torch_cuda):
     cfg = dict(BASE, sort_every=1, tile_r=8, tile_theta=8)
     osim = oracle_state(cfg)
