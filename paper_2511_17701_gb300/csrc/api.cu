@@ -266,7 +266,7 @@ template <typename T>
 cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, int k, bool deposit, int stage = PUSH_ALL) {
   SpeciesState &sp = c->sp[k];
   const std::pair<cudaEvent_t, cudaEvent_t> *kt =
-      stage == PUSH_GUARD ? nullptr : next_events(c, PH_KERNEL);
+      push_main_stage(stage) ? next_events(c, PH_KERNEL) : nullptr;
   const PushStreams ps{c->stream, c->side, c->ev_fork[k], c->ev_done[k], c->ev_class[k],
                        kt ? kt->first : nullptr, kt ? kt->second : nullptr, stage};
   const int tr = c->cfg.tile_r, tt = c->cfg.tile_theta;
@@ -289,7 +289,7 @@ cudaError_t do_push(grpic_ctx *c, FieldPtrsT<T> &F, int k, bool deposit, int sta
   SpeciesDevT<T> v = dev_view<T>(sp, sp.live);
   const bool write_prev = !deposit || c->keep_prev;
   if (!write_prev) v.i1p = v.i2p = nullptr, v.dx1p = v.dx2p = nullptr;
-  if (stage != PUSH_GUARD) sp.prev_valid = write_prev;
+  if (push_main_stage(stage)) sp.prev_valid = write_prev;
   // massless particles are neutral: their push deposits nothing
   return launch_push<T>(c->g, F, v, c->tb, sp.gl, ti, sp.n_bound, deposit && !sp.massless,
                         c->diag, ps);
@@ -984,12 +984,18 @@ grpic_status host_in(grpic_ctx *ctx, const HostIO &io) {
 // copies of one species overlap the work on another.
 grpic_status step_once(grpic_ctx *ctx, const HostIO *io) {
   grpic_status s;
+  const bool sort_now = ctx->cfg.sort_every > 0 && ctx->step % ctx->cfg.sort_every == 0;
+  // mixed, no sort this step: classify every species on the side stream first, beside the
+  // field predict (it reads only the particles), so the first FP32 kernel need not wait for it
+  const bool early_classify = ctx->mixed && !io && !sort_now;
+  if (early_classify)
+    for (int k = 0; k < ctx->cfg.n_species; ++k)
+      if (ctx->sp[k].loaded) CK(do_push(ctx, ctx->F32, k, true, PUSH_CLASSIFY));
   {
     PhaseTimer t(ctx, PH_PREDICT);
     if (ctx->mixed) CK(launch_predict<float>(ctx->g, ctx->F32, ctx->stream));
     else CK(launch_predict<double>(ctx->g, ctx->F64, ctx->stream));
   }
-  const bool sort_now = ctx->cfg.sort_every > 0 && ctx->step % ctx->cfg.sort_every == 0;
   if (!io) {
     if (sort_now)
       for (int k = 0; k < ctx->cfg.n_species; ++k)
@@ -1001,7 +1007,8 @@ grpic_status step_once(grpic_ctx *ctx, const HostIO *io) {
     // chain, on the side stream) run beside all the FP32 kernels instead of trailing the last
     if (ctx->mixed)
       for (int k = 0; k < ctx->cfg.n_species; ++k)
-        if (ctx->sp[k].loaded) CK(do_push(ctx, ctx->F32, k, true, PUSH_GUARD));
+        if (ctx->sp[k].loaded)
+          CK(do_push(ctx, ctx->F32, k, true, early_classify ? PUSH_GUARD_KERNELS : PUSH_GUARD));
     for (int k = 0; k < ctx->cfg.n_species; ++k) {
       SpeciesState &sp = ctx->sp[k];
       if (!sp.loaded) continue;

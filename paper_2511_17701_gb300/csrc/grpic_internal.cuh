@@ -388,7 +388,16 @@ constexpr int TILE_HALO = 6;  // cells of the window beyond the tile on every si
 // guard kernels, all on `side`) and its main FP32 kernel (on `main`, after the classify) can
 // be issued separately, so that the guard stages of all species start before the first FP32
 // kernel
-enum { PUSH_ALL = 0, PUSH_GUARD = 1, PUSH_MAIN = 2 };
+// stages of a mixed push: PUSH_GUARD = PUSH_CLASSIFY then PUSH_GUARD_KERNELS (side stream),
+// PUSH_MAIN the FP32 kernel; PUSH_ALL all of them (the FP64 path has the main stage only)
+enum { PUSH_ALL = 0, PUSH_GUARD = 1, PUSH_MAIN = 2, PUSH_CLASSIFY = 3, PUSH_GUARD_KERNELS = 4 };
+__host__ __device__ inline bool push_main_stage(int s) { return s == PUSH_ALL || s == PUSH_MAIN; }
+__host__ __device__ inline bool push_classify_stage(int s) {
+  return s == PUSH_ALL || s == PUSH_GUARD || s == PUSH_CLASSIFY;
+}
+__host__ __device__ inline bool push_guard_kernels_stage(int s) {
+  return s == PUSH_ALL || s == PUSH_GUARD || s == PUSH_GUARD_KERNELS;
+}
 struct PushStreams {
   cudaStream_t main, side;
   cudaEvent_t fork, done, classified;  // side after main; guard kernels done; classify done

@@ -1671,7 +1671,9 @@ cudaError_t push_impl(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
                       const PushTables &tb, const GuardList &gl, const TileInfo &ti,
                       int64_t n_bound, bool deposit, unsigned long long *diag,
                       const PushStreams &ps) {
-  const bool main_stage = ps.stage != PUSH_GUARD, guard_stage = ps.stage != PUSH_MAIN;
+  const bool main_stage = push_main_stage(ps.stage);
+  const bool classify_stage = push_classify_stage(ps.stage);
+  const bool kernels_stage = push_guard_kernels_stage(ps.stage);
   if (n_bound <= 0) {  // keep a requested event pair recorded (zero duration)
     if (main_stage && ps.t0) cudaEventRecord(ps.t0, ps.main);
     if (main_stage && ps.t1) cudaEventRecord(ps.t1, ps.main);
@@ -1687,14 +1689,21 @@ cudaError_t push_impl(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
   } else {
     cudaError_t e;
     const int nb = blocks_for(n_bound);
-    if (guard_stage) {
-      // the whole stage runs on the side stream, after everything issued so far on main
+    if (classify_stage || kernels_stage) {
+      // each part runs on the side stream after everything issued so far on main (the
+      // classify reads only the particles, so a step may issue it before the field predict;
+      // the guard kernels read the predicted fields and add to the zeroed currents)
       if ((e = cudaEventRecord(ps.fork, ps.main)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(ps.side, ps.fork, 0)) != cudaSuccess) return e;
+    }
+    if (classify_stage) {
       if ((e = cudaMemsetAsync(gl.count, 0, 2 * sizeof(unsigned long long), ps.side)) != cudaSuccess)
         return e;
       k_classify<<<blocks_for((n_bound + CL_U - 1) / CL_U), TPB, 0, ps.side>>>(g, s, tb, gl);
       if ((e = cudaEventRecord(ps.classified, ps.side)) != cudaSuccess) return e;
+      COUNT_LAUNCH(1);
+    }
+    if (kernels_stage) {
       // the guard kernels are FP64-pipe bound: a few one-warp blocks per SM reach every SM
       // sub-partition's FP64 unit and leave the registers to the concurrent FP32 kernel
       constexpr int gb = 152 * GRPIC_GUARD_BLOCKS_PER_SM, ab = 152 * GRPIC_AXIS_BLOCKS_PER_SM;
@@ -1706,7 +1715,7 @@ cudaError_t push_impl(const GridP &g, const FieldPtrsT<T> &F, SpeciesDevT<T> s,
         k_push_axis<false, Q><<<ab, 32, 0, ps.side>>>(g, F, s, tb, gl, diag);
       }
       if ((e = cudaEventRecord(ps.done, ps.side)) != cudaSuccess) return e;
-      COUNT_LAUNCH(3);
+      COUNT_LAUNCH(2);
     }
     if (!main_stage) return cudaGetLastError();
     // the FP32 kernel reads the mask the classify writes
