@@ -15,10 +15,11 @@ __device__ __forceinline__ T tabv(const T *tab, const GridP &g, int cls, int q, 
 }
 
 // ---------------------------------------------------------------------------------
-// Tables: per Yee class, alpha, h_11, h_22, h_33, sqrt(h~), [sqrt(h~) h_13],
-// [sqrt(h~ h) beta^1], 1/sqrt(h) at every stored point; the polar area
-// A(x1) = dr (r^2 + a^2) sqrt(1 + 2 M r/(r^2 + a^2)) (1 - cos(theta(x2 = 1/2))) (App. A, per
-// unit phi; theta(1/2) = dtheta/2 on the plain grid).
+// Tables: per Yee class, alpha, h_11, h_22, h_33, 1/(2 sqrt(h~)) (the weight of the
+// volume-weighted averages, stored as a reciprocal so the field kernels multiply instead of
+// dividing), [sqrt(h~) h_13], [sqrt(h~ h) beta^1], 1/sqrt(h) at every stored point; the
+// polar area A(x1) = dr (r^2 + a^2) sqrt(1 + 2 M r/(r^2 + a^2)) (1 - cos(theta(x2 = 1/2)))
+// (App. A, per unit phi; theta(1/2) = dtheta/2 on the plain grid).
 // ---------------------------------------------------------------------------------
 // The absorbing layer (MATCH, Sec. 3.3.3): a field value v relaxes towards its initial value
 // vi as v - k (v - vi), k = absorb_coef x^3, x = (r - r_absorb) / (r_max - r_absorb) capped at
@@ -49,7 +50,7 @@ __global__ void k_metric_tables(GridP g, T *tab, T *polar) {
     o[T_H11 * ps] = (T)m.h11;
     o[T_H22 * ps] = (T)m.h22;
     o[T_H33 * ps] = (T)m.h33;
-    o[T_SHT * ps] = (T)m.sqrt_ht;
+    o[T_IHT2 * ps] = (T)(0.5 / m.sqrt_ht);
     o[T_WT13 * ps] = (T)(m.sqrt_ht * m.h13);
     o[T_WB1 * ps] = (T)(m.sqrt_ht * m.sqrt_h * m.beta1);
     o[T_ISH * ps] = (T)(1.0 / m.sqrt_h);
@@ -266,8 +267,8 @@ __global__ void k_aux_E(GridP g, Pair3<T> B, Pair3<T> D, const T *tab, T *E1, T 
     // E_1 at (i+1/2, j) = alpha [h_11 D^1 + <h_13 D^3>]
     {
       const T avg = (tabv(tab, g, CLS_NN, T_WT13, i, j) * pv(D, 2, k) +
-                          tabv(tab, g, CLS_NN, T_WT13, i + 1, j) * pv(D, 2, k + 1)) /
-                         ((T)2 * tabv(tab, g, CLS_HN, T_SHT, i, j));
+                     tabv(tab, g, CLS_NN, T_WT13, i + 1, j) * pv(D, 2, k + 1)) *
+                    tabv(tab, g, CLS_HN, T_IHT2, i, j);
       E1[k] = tabv(tab, g, CLS_HN, T_ALPHA, i, j) *
               (tabv(tab, g, CLS_HN, T_H11, i, j) * pv(D, 0, k) + avg);
     }
@@ -275,19 +276,19 @@ __global__ void k_aux_E(GridP g, Pair3<T> B, Pair3<T> D, const T *tab, T *E1, T 
     if (j == 0 || j == g.n_th) {
       E3[k] = (T)0;
     } else {
-      const T d2 = 2.0 * tabv(tab, g, CLS_NN, T_SHT, i, j);
+      const T w2 = tabv(tab, g, CLS_NN, T_IHT2, i, j);
       const T a13 = (tabv(tab, g, CLS_HN, T_WT13, i - 1, j) * pv(D, 0, k - 1) +
-                          tabv(tab, g, CLS_HN, T_WT13, i, j) * pv(D, 0, k)) / d2;
+                     tabv(tab, g, CLS_HN, T_WT13, i, j) * pv(D, 0, k)) * w2;
       const T ab2 = (tabv(tab, g, CLS_HN, T_WB1, i - 1, j) * pv(B, 1, k - 1) +
-                          tabv(tab, g, CLS_HN, T_WB1, i, j) * pv(B, 1, k)) / d2;
+                     tabv(tab, g, CLS_HN, T_WB1, i, j) * pv(B, 1, k)) * w2;
       E3[k] = tabv(tab, g, CLS_NN, T_ALPHA, i, j) *
                   (tabv(tab, g, CLS_NN, T_H33, i, j) * pv(D, 2, k) + a13) + ab2;
     }
     // E_2 at (i, j+1/2) = alpha h_22 D^2 - <sqrt(h) beta^1 B^3>
     if (j < g.n_th) {
       const T ab3 = (tabv(tab, g, CLS_HH, T_WB1, i - 1, j) * pv(B, 2, k - 1) +
-                          tabv(tab, g, CLS_HH, T_WB1, i, j) * pv(B, 2, k)) /
-                         ((T)2 * tabv(tab, g, CLS_NH, T_SHT, i, j));
+                     tabv(tab, g, CLS_HH, T_WB1, i, j) * pv(B, 2, k)) *
+                    tabv(tab, g, CLS_NH, T_IHT2, i, j);
       E2[k] = tabv(tab, g, CLS_NH, T_ALPHA, i, j) * tabv(tab, g, CLS_NH, T_H22, i, j) *
                   pv(D, 1, k) - ab3;
     }
@@ -305,23 +306,23 @@ __global__ void k_aux_H(GridP g, Pair3<T> B, Pair3<T> D, const T *tab, T *H1, T 
     if (j < g.n_th) {
       // H_1 at (i, j+1/2) = alpha [h_11 B^1 + <h_13 B^3>]
       const T a13 = (tabv(tab, g, CLS_HH, T_WT13, i - 1, j) * pv(B, 2, k - 1) +
-                          tabv(tab, g, CLS_HH, T_WT13, i, j) * pv(B, 2, k)) /
-                         ((T)2 * tabv(tab, g, CLS_NH, T_SHT, i, j));
+                     tabv(tab, g, CLS_HH, T_WT13, i, j) * pv(B, 2, k)) *
+                    tabv(tab, g, CLS_NH, T_IHT2, i, j);
       H1[k] = tabv(tab, g, CLS_NH, T_ALPHA, i, j) *
               (tabv(tab, g, CLS_NH, T_H11, i, j) * pv(B, 0, k) + a13);
       // H_3 at (i+1/2, j+1/2) = alpha [h_33 B^3 + <h_13 B^1>] - <sqrt(h) beta^1 D^2>
-      const T d3 = 2.0 * tabv(tab, g, CLS_HH, T_SHT, i, j);
+      const T w3 = tabv(tab, g, CLS_HH, T_IHT2, i, j);
       const T b13 = (tabv(tab, g, CLS_NH, T_WT13, i, j) * pv(B, 0, k) +
-                          tabv(tab, g, CLS_NH, T_WT13, i + 1, j) * pv(B, 0, k + 1)) / d3;
+                     tabv(tab, g, CLS_NH, T_WT13, i + 1, j) * pv(B, 0, k + 1)) * w3;
       const T bd2 = (tabv(tab, g, CLS_NH, T_WB1, i, j) * pv(D, 1, k) +
-                          tabv(tab, g, CLS_NH, T_WB1, i + 1, j) * pv(D, 1, k + 1)) / d3;
+                     tabv(tab, g, CLS_NH, T_WB1, i + 1, j) * pv(D, 1, k + 1)) * w3;
       H3[k] = tabv(tab, g, CLS_HH, T_ALPHA, i, j) *
                   (tabv(tab, g, CLS_HH, T_H33, i, j) * pv(B, 2, k) + b13) - bd2;
     }
     // H_2 at (i+1/2, j) = alpha h_22 B^2 + <sqrt(h) beta^1 D^3>
     const T bd3 = (tabv(tab, g, CLS_NN, T_WB1, i, j) * pv(D, 2, k) +
-                        tabv(tab, g, CLS_NN, T_WB1, i + 1, j) * pv(D, 2, k + 1)) /
-                       ((T)2 * tabv(tab, g, CLS_HN, T_SHT, i, j));
+                   tabv(tab, g, CLS_NN, T_WB1, i + 1, j) * pv(D, 2, k + 1)) *
+                  tabv(tab, g, CLS_HN, T_IHT2, i, j);
     H2[k] = tabv(tab, g, CLS_HN, T_ALPHA, i, j) * tabv(tab, g, CLS_HN, T_H22, i, j) *
                 pv(B, 1, k) + bd3;
   }

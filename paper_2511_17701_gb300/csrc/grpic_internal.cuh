@@ -117,7 +117,7 @@ __device__ __forceinline__ Cst<float> cst<float>(const GridP &g) {
 // Yee point classes of the metric tables: (i, j), (i+1/2, j), (i, j+1/2), (i+1/2, j+1/2).
 enum { CLS_NN = 0, CLS_HN = 1, CLS_NH = 2, CLS_HH = 3 };
 // Quantities tabulated per class (Eq. discretized-auxE/auxH and the curls).
-enum { T_ALPHA = 0, T_H11, T_H22, T_H33, T_SHT, T_WT13, T_WB1, T_ISH, T_NQ };
+enum { T_ALPHA = 0, T_H11, T_H22, T_H33, T_IHT2, T_WT13, T_WB1, T_ISH, T_NQ };
 
 __host__ __device__ inline int64_t plane_size(const GridP &g) { return (int64_t)g.NX * g.NY; }
 __host__ __device__ inline int64_t sidx(const GridP &g, int i, int j) {
