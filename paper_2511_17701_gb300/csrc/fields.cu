@@ -330,11 +330,13 @@ __global__ void k_aux_H(GridP g, Pair3<T> B, Pair3<T> D, const T *tab, T *H1, T 
 
 // MATCH absorbing layer (reading of paper I's form): F <- F - lambda (F - F_init),
 // lambda = coef min(1, ((r - r_abs)/(r_max - r_abs)))^3 for r > r_absorb, rows [0, n_theta].
+// The initial value is read only inside the layer (the factor is zero elsewhere).
 template <typename T>
-__device__ __forceinline__ T match(const GridP &g, T v, T vi, const T *absorb, int i, int j) {
+__device__ __forceinline__ T match(const GridP &g, T v, const T *init, int64_t idx,
+                                   const T *absorb, int i, int j) {
   if (j < 0 || j > g.n_th) return v;
   const T k = __ldg(absorb + i + G_);  // the factor at this column (absorb_factor)
-  return k == (T)0 ? v : v - k * (v - vi);
+  return k == (T)0 ? v : v - k * (v - __ldg(init + idx));
 }
 
 // Faraday, Eq. (discretized-faraday): Bout = Bin - dt curl E / sqrt(h) on the evolved
@@ -359,9 +361,9 @@ __global__ void k_faraday(GridP g, Pair3<T> Bin, const T *E1, const T *E2, const
       b3 -= dt * ((E2[k + 1] - E2[k]) - (E1[k + g.NX] - E1[k])) *
             tabv(tab, g, CLS_HH, T_ISH, i, j);
     if (do_match) {
-      b1 = match(g, b1, Bi1[k], absorb, i, j);
-      b2 = match(g, b2, Bi2[k], absorb + g.NX, i, j);
-      b3 = match(g, b3, Bi3[k], absorb + g.NX, i, j);
+      b1 = match(g, b1, Bi1, k, absorb, i, j);
+      b2 = match(g, b2, Bi2, k, absorb + g.NX, i, j);
+      b3 = match(g, b3, Bi3, k, absorb + g.NX, i, j);
     }
     B1[k] = b1; B2[k] = b2; B3[k] = b3;
   }
@@ -397,9 +399,9 @@ __global__ void k_ampere(GridP g, Pair3<T> Din, const T *H1, const T *H2, const 
       d3 += dt * ((H2[k] - H2[k - 1]) - (H1[k] - H1[k - g.NX]) - fpi * pv(J, 2, k)) *
             tabv(tab, g, CLS_NN, T_ISH, i, j);
     if (do_match) {
-      d1 = match(g, d1, Di1[k], polar + 2 * g.NX, i, j);
-      d2 = match(g, d2, Di2[k], polar + g.NX, i, j);
-      d3 = match(g, d3, Di3[k], polar + g.NX, i, j);
+      d1 = match(g, d1, Di1, k, polar + 2 * g.NX, i, j);
+      d2 = match(g, d2, Di2, k, polar + g.NX, i, j);
+      d3 = match(g, d3, Di3, k, polar + g.NX, i, j);
     }
     D1[k] = d1; D2[k] = d2; D3[k] = d3;
   }
