@@ -55,6 +55,30 @@ def test_mixed_full_step_error_per_step(torch_cuda, cfg):
 
 
 @pytest.mark.parametrize("cfg", [BASE, BIG])
+def test_mixed_step_stages_equal_separate_calls(torch_cuda, cfg):
+    """A fused step without a sort issues every species' classify ahead of the field predict
+    and the guard kernels after it; separate push calls classify inside each push. From the
+    same state one step gives the same particle bits either way (the pushes read the same
+    predicted fields; the fused deposit and the separate one differ only in the order of
+    their FP32 current sums)."""
+    osim = mixed_state(cfg)
+    g1 = gpu_from_oracle(osim, sort_every=0)
+    g2 = gpu_from_oracle(osim, sort_every=0)
+    g1.step(1)
+    g2.predict()
+    for s in range(2):
+        g2.push(s)
+    g2.deposit()
+    g2.advance()
+    for s in range(2):
+        p1, p2 = g1.get_particles(s), g2.get_particles(s)
+        for k in ("i1", "i2", "dx1", "dx2", "u1", "u2", "u3", "phi", "w", "tag"):
+            assert np.array_equal(p1[k], p2[k]), (s, k)
+    pe = plane_errors(g1.planes(), g2.planes(), AFTER_ADVANCE)
+    assert max(pe.values()) <= MIXED_RTOL, pe
+
+
+@pytest.mark.parametrize("cfg", [BASE, BIG])
 def test_mixed_push_and_deposit(torch_cuda, cfg):
     osim = mixed_state(cfg)
     osim.predict()
