@@ -688,8 +688,10 @@ __device__ __forceinline__ void coord_refined(const GridP &g, const PushTables &
 }
 
 // One particle in FP64: steps 2-11 of Sec. 3.1, the boundaries of Sec. 3.3.3, and
-// (DEPOSIT) the deposit of its move. T is the storage type of state and fields.
-template <bool Q, typename T, bool DEPOSIT>
+// (DEPOSIT) the deposit of its move. T is the storage type of state and fields. REFINE
+// false compiles the refined iterations out (a caller whose particles all sit in the two
+// cell rows next to an axis, where they never apply).
+template <bool Q, typename T, bool DEPOSIT, bool REFINE = true>
 __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
                                        const PushTables &tb, const SpeciesDevT<T> &s,
                                        int64_t k, unsigned long long *diag) {
@@ -701,7 +703,7 @@ __device__ __forceinline__ void push64(const GridP &g, const FieldPtrsT<T> &F,
   // the refined iterations keep two cell rows away from the axes: there the coordinate map
   // (metric terms ~ 1/sin^2(theta)) has more than one fixed point within reach, and the
   // method's answer is the one its iteration from x^n finds
-  const bool refine = g.iter_tol > 0.0 && i2 >= 2 && i2 < g.n_th - 2;
+  const bool refine = REFINE && g.iter_tol > 0.0 && i2 >= 2 && i2 < g.n_th - 2;
   const Base b = refine ? make_base_tab<Q>(g, tb, i1, i2, dx1, x1, x2) : make_base<Q>(g, x1, x2);
   Pt<double> p0;
   local_at_base<Q>(g, b, x2, p0);  // clamps theta near the axes
@@ -1510,7 +1512,7 @@ __global__ void __launch_bounds__(32, GRPIC_AXIS_MIN_BLOCKS) k_push_axis(GridP g
     if (s.i1p) {
       s.i1p[k] = s.i1[k]; s.i2p[k] = s.i2[k]; s.dx1p[k] = s.dx1[k]; s.dx2p[k] = s.dx2[k];
     }
-    push64<Q, float, DEPOSIT>(g, F, tb, s, k, diag);
+    push64<Q, float, DEPOSIT, false>(g, F, tb, s, k, diag);  // axis rows: never refined
   }
 }
 
