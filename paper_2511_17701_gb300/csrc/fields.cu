@@ -354,11 +354,11 @@ __global__ void k_faraday(GridP g, Pair3<T> Bin, const T *E1, const T *E2, const
     T b1 = pv(Bin, 0, k), b2 = pv(Bin, 1, k), b3 = pv(Bin, 2, k);
     const bool rows_half = (j >= 0 && j < g.n_th);
     if (rows_half && i >= 0 && i <= g.n_r)
-      b1 -= dt * (E3[k + g.NX] - E3[k]) * tabv(tab, g, CLS_NH, T_ISH, i, j);
+      b1 -= dt * (__ldg(E3 + k + g.NX) - __ldg(E3 + k)) * tabv(tab, g, CLS_NH, T_ISH, i, j);
     if (j >= 1 && j < g.n_th && i >= 0 && i < g.n_r)
-      b2 += dt * (E3[k + 1] - E3[k]) * tabv(tab, g, CLS_HN, T_ISH, i, j);
+      b2 += dt * (__ldg(E3 + k + 1) - __ldg(E3 + k)) * tabv(tab, g, CLS_HN, T_ISH, i, j);
     if (rows_half && i >= 0 && i < g.n_r)
-      b3 -= dt * ((E2[k + 1] - E2[k]) - (E1[k + g.NX] - E1[k])) *
+      b3 -= dt * ((__ldg(E2 + k + 1) - __ldg(E2 + k)) - (__ldg(E1 + k + g.NX) - __ldg(E1 + k))) *
             tabv(tab, g, CLS_HH, T_ISH, i, j);
     if (do_match) {
       b1 = match(g, b1, Bi1, k, absorb, i, j);
@@ -386,17 +386,19 @@ __global__ void k_ampere(GridP g, Pair3<T> Din, const T *H1, const T *H2, const 
     T d1 = pv(Din, 0, k), d2 = pv(Din, 1, k), d3 = pv(Din, 2, k);
     if (i >= 0 && i < g.n_r && j >= 0 && j <= g.n_th) {
       if (j == 0)
-        d1 += dt * (H3[k] - fpi * pv(J, 0, k)) / __ldg(polar + i + G_);
+        d1 += dt * (__ldg(H3 + k) - fpi * pv(J, 0, k)) / __ldg(polar + i + G_);
       else if (j == g.n_th)
-        d1 += dt * (-H3[k - g.NX] - fpi * pv(J, 0, k)) / __ldg(polar + i + G_);
+        d1 += dt * (-__ldg(H3 + k - g.NX) - fpi * pv(J, 0, k)) / __ldg(polar + i + G_);
       else
-        d1 += dt * ((H3[k] - H3[k - g.NX]) - fpi * pv(J, 0, k)) *
+        d1 += dt * ((__ldg(H3 + k) - __ldg(H3 + k - g.NX)) - fpi * pv(J, 0, k)) *
               tabv(tab, g, CLS_HN, T_ISH, i, j);
     }
     if (i >= 0 && i <= g.n_r && j >= 0 && j < g.n_th)
-      d2 += dt * (-(H3[k] - H3[k - 1]) - fpi * pv(J, 1, k)) * tabv(tab, g, CLS_NH, T_ISH, i, j);
+      d2 += dt * (-(__ldg(H3 + k) - __ldg(H3 + k - 1)) - fpi * pv(J, 1, k)) *
+            tabv(tab, g, CLS_NH, T_ISH, i, j);
     if (i >= 0 && i <= g.n_r && j >= 1 && j < g.n_th)
-      d3 += dt * ((H2[k] - H2[k - 1]) - (H1[k] - H1[k - g.NX]) - fpi * pv(J, 2, k)) *
+      d3 += dt * ((__ldg(H2 + k) - __ldg(H2 + k - 1)) - (__ldg(H1 + k) - __ldg(H1 + k - g.NX)) -
+                  fpi * pv(J, 2, k)) *
             tabv(tab, g, CLS_NN, T_ISH, i, j);
     if (do_match) {
       d1 = match(g, d1, Di1, k, polar + 2 * g.NX, i, j);
